@@ -1,0 +1,452 @@
+"""Benchmark of the per-level implicit diffusion solve on one GB300 (or N replicas).
+
+Default workload (one "step" = every row of the hot path over one batch):
+  512 independent single-level backward-Euler solves of ragged sizes (oct
+  counts log-uniform over 8^3..64^3 cells, near-cubic oct boxes), per-solve dt
+  log-uniform over 1e-3..1e2 x the explicit CFL step, K log-normal (sigma 1)
+  per cell, random Dirichlet / zero-flux walls; per step: build every level
+  operator and right-hand side on the device, then solve all 512 in one
+  batched, graph-replayed launch sequence in mixed precision (FP32 bulk, FP64
+  dots) with FP64 iterative refinement to ||r||/||r0|| <= 1e-10.
+
+Metric: level-solves/s (whole job), with the dominant kernel's achieved HBM
+bandwidth against the measured peak, the plain per-solve FP64 GPU path on the
+same mix, and the FP64 CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+For N > 1 it runs under torch.distributed.run; each rank solves its own
+512-solve batch (a different seed): independent problems, no data-path
+collective, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "stencil-PCG GB/s vs HBM peak; level-solves/s and p50/p99 latency vs plain FP64"
+UNIT = "level-solves/s"
+TOL = 1e-10
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+        }
+
+
+def _traffic_for(kernel: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if the
+    summary was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        import hashlib
+
+        src = open(os.path.join(ROOT, "paper_1401_1112_gb300", "csrc", "kernels.cu"), "rb").read()
+        if d.get("kernels_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        k = d["kernels"].get(kernel)
+        if not k:
+            return None
+        # scale the captured launch's DRAM bytes to this run's average launch
+        return k
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_1401_1112_gb300 import ats, build
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    solves = W.config4(n_solves=args.solves, seed=1404 + 1000 * rank)
+    n = len(solves)
+    sizes = [lv.n_cell for lv, _ in solves]
+    total_cells = int(sum(sizes))
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    fsz = [lv.n_face for lv, _ in solves]
+    foffs = np.concatenate([[0], np.cumsum(fsz)])
+
+    # device-resident inputs (flat, with per-solve views)
+    K_h = np.concatenate([st.K for _, st in solves])
+    E_h = np.concatenate([st.E for _, st in solves])
+    fE_h = np.concatenate([st.face_E for _, st in solves]) if foffs[-1] else np.zeros(1)
+    fF_h = np.concatenate([st.face_F for _, st in solves]) if foffs[-1] else np.zeros(1)
+    K_d = torch.from_numpy(K_h).to(dev)
+    E_d = torch.from_numpy(E_h).to(dev)
+    fE_d = torch.from_numpy(fE_h).to(dev)
+    fF_d = torch.from_numpy(fF_h).to(dev)
+    x_d = torch.empty_like(E_d)
+
+    ctx = ats.Context(local)
+    ctx.set_stream(stream.cuda_stream)
+    t0 = time.time()
+    levels = [ats.Level(ctx, lv) for lv, _ in solves]
+    layout_s = time.time() - t0
+
+    def view(t, a, b):
+        return t[int(a):int(b)]
+
+    def build_ops():
+        for k, (lv, st) in enumerate(solves):
+            fa, fb = foffs[k], foffs[k + 1]
+            has_f = fb > fa
+            levels[k].build(st.dt, view(K_d, offs[k], offs[k + 1]), view(E_d, offs[k], offs[k + 1]),
+                            face_E=view(fE_d, fa, fb) if has_f else None,
+                            face_F=view(fF_d, fa, fb) if has_f else None)
+
+    xs = [view(x_d, offs[k], offs[k + 1]) for k in range(n)]
+    build_ops()
+    batch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_RESIDUAL, precision=ats.ATS_PREC_MIXED,
+                      use_graph=1, check_every=args.check_every, mem=ats.ATS_MEM_DEVICE)
+
+    def step():
+        x_d.copy_(E_d)          # initial guess x0 = E^n
+        build_ops()             # coefficients, interface terms, right-hand side
+        code, stats = batch.solve(xs)
+        if code != 0:
+            raise RuntimeError(f"batch solve failed: {code} {ats.ats_last_error()}")
+        return stats
+
+    for _ in range(args.warmup):
+        stats = step()
+    torch.cuda.synchronize()
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    batch.set_profiling(True)
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    op_ms = upd_ms = op_bytes = upd_bytes = 0.0
+    launches = 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        stats = step()
+        ks = batch.kernel_stats()
+        op_ms += ks["op_ms"]
+        upd_ms += ks["upd_ms"]
+        op_bytes += ks["op_bytes"]
+        upd_bytes += ks["upd_bytes"]
+        launches += ks["launches"] + n + 2  # ticks + operator builds + init/final
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    batch.set_profiling(False)
+    value = n * args.steps * world / (ms / 1e3)
+    iters = [s["iterations"] for s in stats]
+    refs = [s["refinements"] for s in stats]
+    bounds = [s["res_norm"] / s["r0_norm"] if s["r0_norm"] > 0 else 0.0 for s in stats]
+
+    # dominant kernel roofline
+    peak, peak_kind = _peaks()
+    if op_ms >= upd_ms:
+        dom, dms, dbytes = "k_op<float>", op_ms, op_bytes
+    else:
+        dom, dms, dbytes = "k_upd<float>", upd_ms, upd_bytes
+    achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
+    tr = _traffic_for(dom)
+    roofline = {
+        "bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        "frac": round(achieved / peak, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+        "traffic": tr, "op_ms": round(op_ms, 3), "upd_ms": round(upd_ms, 3),
+        "op_GBps": round(op_bytes / (op_ms / 1e3) / 1e9, 1) if op_ms else None,
+        "upd_GBps": round(upd_bytes / (upd_ms / 1e3) / 1e9, 1) if upd_ms else None,
+    }
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        Kp = torch.from_numpy(K_h).pin_memory()
+        Ep = torch.from_numpy(E_h).pin_memory()
+        fEp = torch.from_numpy(fE_h).pin_memory()
+        fFp = torch.from_numpy(fF_h).pin_memory()
+        xp = torch.empty_like(Ep).pin_memory()
+        Kn, En, fEn, fFn, xn = Kp.numpy(), Ep.numpy(), fEp.numpy(), fFp.numpy(), xp.numpy()
+        hbatch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_RESIDUAL, precision=ats.ATS_PREC_MIXED,
+                           use_graph=1, check_every=args.check_every, mem=ats.ATS_MEM_HOST)
+        hx = [xn[offs[k]:offs[k + 1]] for k in range(n)]
+
+        def e2e_step():
+            for k, (lv, st) in enumerate(solves):
+                fa, fb = foffs[k], foffs[k + 1]
+                levels[k].build(st.dt, Kn[offs[k]:offs[k + 1]], En[offs[k]:offs[k + 1]],
+                                face_E=fEn[fa:fb] if fb > fa else None, face_F=fFn[fa:fb] if fb > fa else None)
+            np.copyto(xn, En)
+            code, _ = hbatch.solve(hx)
+            if code != 0:
+                raise RuntimeError("e2e solve failed")
+
+        e2e_step()
+        barrier()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        e_s = time.perf_counter() - t1
+        if dist is not None:
+            t = torch.tensor([e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        h2d = int(K_h.nbytes + E_h.nbytes + (fE_h.nbytes + fF_h.nbytes if foffs[-1] else 0) + E_h.nbytes)
+        e2e = {"value": round(n * args.steps * world / e_s, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": int(E_h.nbytes)}
+        hbatch.close()
+
+    # plain per-solve FP64 GPU path on the same mix (no batching, no graph)
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        build_ops()
+        x_d.copy_(E_d)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for k in range(n):
+            code, _ = ats.ats_solve(levels[k].handle, xs[k], opts=ats.make_opts(
+                tol=TOL, precision=ats.ATS_PREC_FP64, check_every=args.check_every, mem=ats.ATS_MEM_DEVICE))
+            if code != 0:
+                raise RuntimeError("fp64 solve failed")
+        torch.cuda.synchronize()
+        f_s = time.perf_counter() - t1
+        fp64 = {"value": round(n / f_s, 2), "unit": UNIT, "path": "plain per-solve FP64 PCG, one solve at a time"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(solves, budget_s=args.cpu_seconds)
+
+    batch.close()
+    for L in levels:
+        L.close()
+    ctx.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {
+            "workload": f"batched level solves: {n} ragged single-level backward-Euler solves, 8^3..64^3 cells, "
+                        f"mixed FP32/FP64 PCG + FP64 refinement to ||r||/||r0|| <= 1e-10, graph-replayed",
+            "solves": n, "cells": total_cells, "tol": TOL, "seed": 1404,
+            "l2": "inputs larger than L2 (working set ~%.2f GB)" % (total_cells * 64 / 1e9),
+            "parallelism": f"replicas x{world}",
+        },
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "fp64_per_solve": fp64,
+        "solve_stats": {"iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
+                        "refinements_mean": float(np.mean(refs)),
+                        "max_rel_residual": float(np.max(bounds)), "layout_s": round(layout_s, 3)},
+    }
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) arm
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(solves, budget_s=15.0, seed=7):
+    """The FP64 CPU oracle as it stands (assembly + Jacobi-PCG to the same
+    tolerance) on a random sample of the same solves, until ~budget_s."""
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(solves))
+    t0 = time.perf_counter()
+    done = 0
+    cells = 0
+    for k in order:
+        lv, st = solves[k]
+        S = oracle.assemble(lv, st.dt, st.K, st.E, face_K=st.face_K, face_E=st.face_E, face_F=st.face_F)
+        oracle.pcg(S, st.E, tol=TOL, stop_rule=oracle.STOP_RESIDUAL)
+        done += 1
+        cells += lv.n_cell
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(done / el, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {len(solves)} solves drawn at random ({cells} cells), FP64 assembly + Jacobi-PCG "
+                      f"to ||r||/||r0|| < 1e-10, single thread, {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    solves = W.config4(n_solves=args.solves, seed=1404)
+    import oracle
+
+    oracle.build()
+    per_step = max(1, args.ref_solves_per_step)
+    rng = np.random.default_rng(11)
+
+    def step():
+        idx = rng.choice(len(solves), size=per_step, replace=False)
+        for k in idx:
+            lv, st = solves[k]
+            S = oracle.assemble(lv, st.dt, st.K, st.E, face_K=st.face_K, face_E=st.face_E, face_F=st.face_F)
+            oracle.pcg(S, st.E, tol=TOL, stop_rule=oracle.STOP_RESIDUAL)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    v = per_step * args.steps / el
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched level solves: {args.solves} ragged single-level backward-Euler solves, "
+                               f"8^3..64^3 cells, FP64 CPU oracle, {per_step} random solves per step",
+                   "solves": args.solves, "tol": TOL, "seed": 1404},
+        "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} random solves of the {args.solves}-solve batch per step"},
+        "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--solves", type=int, default=512)
+    ap.add_argument("--check-every", type=int, default=16)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-solves-per-step", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = _dist()
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

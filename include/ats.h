@@ -1,0 +1,210 @@
+/*
+ * ats.h -- C ABI of the GB300 (sm_103a) per-level implicit diffusion solver.
+ *
+ * The operation: one backward-Euler step of the heat / flux-limited-diffusion
+ * operator restricted to one AMR level (Commerçon, Debout & Teyssier 2014,
+ * Sect. 3.1, Eq. Er_imp and Eq. Er_imp1),
+ *
+ *     (1 + s_i + sum_f w_f C_f) E_i - sum_{f same-level leaf} C_f E_j = b_i,
+ *
+ * with C_f = factor * dt / dx^2 * (K_i + K_j) / 2 (factor 1 for a same-level
+ * or restricted finer neighbour, 2/3 for a coarser neighbour, Sect. 3.1), the
+ * interface rows of Sect. 3.2 (Dirichlet: w = 1, b += C E_nb; Neumann: w = 0,
+ * b += F; Robin: w = alpha, b += alpha C E_nb + (1 - alpha) F), solved by
+ * conjugate gradient with a diagonal preconditioner and the stopping rule of
+ * Sect. 3.3.4.  The right-hand side is b_i = E^n_i + src_i + interface terms.
+ *
+ * Geometry (all arrays in "level order"):
+ *   a level is a list of n_oct octs of 2x2x2 cells; oct o has integer oct
+ *   coordinates (ox, oy, oz); its cell c = ix + 2 iy + 4 iz has the level
+ *   cell coordinates (2 ox + ix, 2 oy + iy, 2 oz + iz) and the cell index
+ *   8 o + c.  N = 8 n_oct.  Octs in Morton order give the best locality; any
+ *   order is correct.  Face directions: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z.
+ *   A cell is an unknown ("leaf") when its bit in leaf_mask is set.  A leaf
+ *   face whose neighbour is not a same-level leaf (missing oct, refined cell)
+ *   is an interface face: it takes the condition of its descriptor, or is a
+ *   zero-flux wall when it has none.
+ *
+ * Memory and ownership: the library owns every device buffer it allocates.
+ * Arguments marked "host" are read (or written) during the call only and stay
+ * the caller's.  Per-step arrays may be host or device pointers, as the
+ * caller's `mem` field says (ATS_MEM_HOST / ATS_MEM_DEVICE); device pointers
+ * are borrowed for the call and used in stream order on the context's stream.
+ *
+ * Errors: every entry point returns an ats_status; 0 is success, < 0 an
+ * error, > 0 a warning.  No C++ exception crosses this boundary.
+ * ats_last_error() gives a message for the calling thread's last failure.
+ * Threads: one context per thread; a context's objects are not thread-safe.
+ */
+#ifndef ATS_H
+#define ATS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ats_status;
+#define ATS_OK 0
+#define ATS_ERR_INVALID_ARG (-1)   /* bad argument or level description      */
+#define ATS_ERR_OOM (-2)           /* device allocation failed                */
+#define ATS_ERR_OVER_BUDGET (-3)   /* the context's memory budget is spent    */
+#define ATS_ERR_NOT_CONVERGED (-4) /* iteration / refinement cap reached      */
+#define ATS_ERR_BREAKDOWN (-5)     /* CG breakdown: p.Ap <= 0 or non-finite  */
+#define ATS_ERR_TIMEOUT (-6)       /* a bounded wait ran out                  */
+#define ATS_ERR_CUDA (-7)          /* a CUDA runtime call failed              */
+#define ATS_ERR_NO_DEVICE (-8)     /* no usable CUDA device                   */
+#define ATS_ERR_BAD_INPUT (-9)     /* non-finite value or K <= 0 on a leaf    */
+#define ATS_WARN_NEGATIVE 1        /* solution has a negative energy          */
+
+/* face kinds (Sect. 3.2) */
+#define ATS_FACE_DIRICHLET 0
+#define ATS_FACE_NEUMANN 1
+#define ATS_FACE_ROBIN 2
+/* face relations (Sect. 3.1): distance factor of the face coefficient */
+#define ATS_REL_SAME 0    /* physical wall, ghost value at distance dx: 1    */
+#define ATS_REL_COARSER 1 /* fine-to-coarse (Sect. 3.3.1): 2/3               */
+#define ATS_REL_FINER 2   /* coarse-to-fine, restricted finer cell: 1        */
+
+#define ATS_MEM_HOST 0
+#define ATS_MEM_DEVICE 1
+
+/* stopping rules (Sect. 3.3.4) */
+#define ATS_STOP_RESIDUAL 0  /* ||r_j||_2 <= tol ||r_0||_2 (the paper's L2 rule)  */
+#define ATS_STOP_CERTIFIED 1 /* ||b - A x||_2 <= tol ||x||_2; since the level      */
+                             /* matrix has lambda_min >= 1 this bounds the        */
+                             /* relative error of x by tol                          */
+#define ATS_STOP_PAPER 2     /* L2 rule AND max_i |x_j - x_{j-1}| / |x_{j-1}| < tol */
+
+/* precision of the CG bulk (vectors, stencil); dots are always FP64 */
+#define ATS_PREC_FP64 0  /* FP64 everywhere                                    */
+#define ATS_PREC_MIXED 1 /* FP32 vectors and stencil, FP64 dots, FP64 iterative */
+                         /* refinement r = b - (I + dt A) x on FP64 K, b and x  */
+
+typedef struct ats_context ats_context;
+typedef struct ats_level ats_level;
+typedef struct ats_batch ats_batch;
+
+/* Topology of one level (host arrays, read during ats_level_create only). */
+typedef struct {
+  int64_t n_oct;
+  const int32_t *oct_xyz;   /* host [n_oct * 3] oct coordinates, |coord| < 2^20 */
+  const uint8_t *leaf_mask; /* host [n_oct] bit c = cell c is a leaf; NULL = all */
+  double dx;                /* cell size of the level, > 0                       */
+  int64_t n_face;           /* interface-face descriptors                        */
+  const int32_t *face_cell; /* host [n_face] leaf cell index 8 o + c             */
+  const int8_t *face_dir;   /* host [n_face] 0..5                                */
+  const int8_t *face_kind;  /* host [n_face] ATS_FACE_*                          */
+  const int8_t *face_rel;   /* host [n_face] ATS_REL_*                           */
+  const double *face_alpha; /* host [n_face] Robin weight in [0,1]; NULL = 1     */
+} ats_level_desc;
+
+/* Per-step values of a level operator (Sect. 3.1-3.2, Sect. 3.3.4). */
+typedef struct {
+  double dt;            /* time step of the level, > 0                           */
+  int mem;              /* ATS_MEM_HOST or ATS_MEM_DEVICE for the arrays below   */
+  const double *K;      /* [N] cell diffusion coefficient, > 0 on leaf cells    */
+  const double *E_old;  /* [N] E^n                                              */
+  const double *s;      /* [N] diagonal shift (linearised coupling) or NULL     */
+  const double *src;    /* [N] extra right-hand side or NULL                     */
+  const double *face_K; /* [n_face] neighbour K of each descriptor, NULL = K_i   */
+  const double *face_E; /* [n_face] neighbour value E_nb, NULL = 0              */
+  const double *face_F; /* [n_face] imposed flux F (energy per unit volume into  */
+                        /* the cell over the step), NULL = 0                     */
+} ats_coef_desc;
+
+typedef struct {
+  double tol;        /* stopping tolerance (default 1e-10)                    */
+  int stop_rule;     /* ATS_STOP_*                                            */
+  int precision;     /* ATS_PREC_*                                            */
+  int max_iter;      /* cap on CG iterations per solve (0 = 20000)            */
+  int max_refine;    /* cap on FP64 residual passes (0 = 40)                 */
+  double inner_rtol; /* mixed: residual reduction per inner FP32 solve (0 = 1e-4) */
+  int tile_octs;     /* octs per work item, multiple of 32 (0 = autotuned)   */
+  int check_every;   /* ticks between host convergence polls (0 = 16)       */
+  int use_graph;     /* 1 = capture the poll interval as a CUDA graph        */
+  int mem;           /* ATS_MEM_HOST / ATS_MEM_DEVICE for x (and rhs)        */
+} ats_solve_opts;
+
+typedef struct {
+  int status;          /* ATS_OK or ATS_ERR_NOT_CONVERGED / _BREAKDOWN      */
+  int iterations;      /* CG iterations (all inner passes)                   */
+  int refinements;     /* FP64 true-residual passes                          */
+  int ticks;           /* device steps taken                                 */
+  double r0_norm;      /* ||b - A x_0||_2 (FP64)                             */
+  double res_norm;     /* final ||b - A x||_2 (FP64, true residual)          */
+  double x_norm;       /* ||x||_2                                            */
+  double err_bound;    /* res_norm / x_norm: bound on the relative error     */
+} ats_solve_stats;
+
+/* ---- context ------------------------------------------------------------ */
+/* Create a context on CUDA device `device` with a device-memory budget in
+ * bytes (0 = no limit).  The context creates its own non-blocking stream. */
+ats_status ats_context_create(int device, size_t mem_budget_bytes, ats_context **out);
+ats_status ats_context_destroy(ats_context *ctx);
+/* Use the caller's cudaStream_t (passed as void*) for all later work; NULL =
+ * the context's own stream. */
+ats_status ats_context_set_stream(ats_context *ctx, void *stream);
+/* Bytes currently allocated by the context, and its budget. */
+ats_status ats_context_memory(const ats_context *ctx, size_t *used, size_t *budget);
+
+/* ---- level (Sect. 3.1: the grid of one AMR level) ------------------------ */
+/* Build the oct neighbour table, the interface records and upload the
+ * topology.  Errors: ATS_ERR_INVALID_ARG for duplicate octs, descriptors on
+ * interior faces or non-leaf cells, duplicate descriptors, bad enums. */
+ats_status ats_level_create(ats_context *ctx, const ats_level_desc *desc, ats_level **out);
+ats_status ats_level_destroy(ats_level *lvl);
+ats_status ats_level_size(const ats_level *lvl, int64_t *n_oct, int64_t *n_cell, int64_t *n_face);
+
+/* Build the level operator for one step (kernel: coefficients, face
+ * coefficients, diagonal extras and the right-hand side b, Sect. 3.1-3.2).
+ * Errors: ATS_ERR_BAD_INPUT if K <= 0 on a leaf or any value is not finite. */
+ats_status ats_level_build_operator(ats_level *lvl, const ats_coef_desc *coef);
+
+/* Copy the assembled right-hand side b (FP64, [N]) out (mem = host/device). */
+ats_status ats_level_get_rhs(ats_level *lvl, double *b, int mem);
+
+/* y = (I + dt A) x in FP64 for a built level (x, y: [N], mem = host/device). */
+ats_status ats_level_apply(ats_level *lvl, const double *x, double *y, int mem);
+
+/* ---- solve (Sect. 3.3.4: diagonal-preconditioned CG) ---------------------- */
+/* Solve (I + dt A) x = b for one built level.  rhs_or_null: NULL = the b of
+ * ats_level_build_operator, else [N] replaces it for this call.  x_inout:
+ * [N] initial guess in, solution out (non-leaf entries are kept).  opts may
+ * be NULL (defaults).  stats may be NULL. */
+ats_status ats_solve(ats_level *lvl, const double *rhs_or_null, double *x_inout,
+                     const ats_solve_opts *opts, ats_solve_stats *stats);
+
+/* ---- batched launch: many independent level solves ------------------------ */
+/* Plan a batch over n built levels (one work list, one CUDA graph per poll
+ * interval).  The levels must stay alive while the batch exists. */
+ats_status ats_batch_create(ats_context *ctx, ats_level *const *levels, int n,
+                            const ats_solve_opts *opts, ats_batch **out);
+/* Solve all levels of the batch; x_inout[k] is solve k's [N_k] vector
+ * (initial guess in, solution out), host or device per opts->mem. stats: [n]
+ * or NULL.  Returns the first error status of any solve, else ATS_OK. */
+ats_status ats_batch_solve(ats_batch *batch, double *const *x_inout, ats_solve_stats *stats);
+ats_status ats_batch_destroy(ats_batch *batch);
+/* One-shot form: create, solve and destroy. */
+ats_status ats_batch_run(ats_context *ctx, ats_level *const *levels, int n, double *const *x_inout,
+                         const ats_solve_opts *opts, ats_solve_stats *stats);
+/* Kernel timing of the last ats_batch_solve (CUDA events around each launch
+ * when profiling is on): dominant-kernel time and its algorithmic bytes. */
+ats_status ats_batch_set_profiling(ats_batch *batch, int on);
+ats_status ats_batch_kernel_stats(const ats_batch *batch, double *op_ms, double *op_bytes,
+                                  double *upd_ms, double *upd_bytes, int *launches);
+
+/* ---- misc ------------------------------------------------------------------ */
+void ats_default_opts(ats_solve_opts *opts);
+const char *ats_status_string(ats_status s);
+const char *ats_last_error(void);
+/* Host-only layout helper (no device needed): the oct neighbour table of a
+ * level, nbr[6 o + dir] = neighbour oct index or -1. */
+ats_status ats_layout_neighbors(const ats_level_desc *desc, int32_t *nbr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ATS_H */

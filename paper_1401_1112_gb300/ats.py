@@ -1,0 +1,428 @@
+"""Thin ctypes binding of the C ABI in include/ats.h (argument marshalling only).
+
+Every function named ``ats_*`` here calls the C entry point of the same name.
+Arrays are either numpy arrays (host memory, ``ATS_MEM_HOST``) or CUDA torch
+tensors (device memory, ``ATS_MEM_DEVICE``); the binding passes their raw
+pointers and never computes anything of the method itself.  The classes
+``Context``, ``Level`` and ``Batch`` only own the C handles.
+
+The library must be built (``paper_1401_1112_gb300.build.build()``); when it
+is missing, ``lib()`` raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libats.so")
+
+ATS_OK = 0
+ATS_ERR_INVALID_ARG = -1
+ATS_ERR_OOM = -2
+ATS_ERR_OVER_BUDGET = -3
+ATS_ERR_NOT_CONVERGED = -4
+ATS_ERR_BREAKDOWN = -5
+ATS_ERR_TIMEOUT = -6
+ATS_ERR_CUDA = -7
+ATS_ERR_NO_DEVICE = -8
+ATS_ERR_BAD_INPUT = -9
+ATS_WARN_NEGATIVE = 1
+
+ATS_FACE_DIRICHLET, ATS_FACE_NEUMANN, ATS_FACE_ROBIN = 0, 1, 2
+ATS_REL_SAME, ATS_REL_COARSER, ATS_REL_FINER = 0, 1, 2
+ATS_MEM_HOST, ATS_MEM_DEVICE = 0, 1
+ATS_STOP_RESIDUAL, ATS_STOP_CERTIFIED, ATS_STOP_PAPER = 0, 1, 2
+ATS_PREC_FP64, ATS_PREC_MIXED = 0, 1
+
+P = ctypes.c_void_p
+
+
+class ats_level_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_oct", ctypes.c_int64), ("oct_xyz", P), ("leaf_mask", P), ("dx", ctypes.c_double),
+        ("n_face", ctypes.c_int64), ("face_cell", P), ("face_dir", P), ("face_kind", P),
+        ("face_rel", P), ("face_alpha", P),
+    ]
+
+
+class ats_coef_desc(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double), ("mem", ctypes.c_int), ("K", P), ("E_old", P), ("s", P),
+        ("src", P), ("face_K", P), ("face_E", P), ("face_F", P),
+    ]
+
+
+class ats_solve_opts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double), ("stop_rule", ctypes.c_int), ("precision", ctypes.c_int),
+        ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+        ("tile_octs", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
+        ("mem", ctypes.c_int),
+    ]
+
+
+class ats_solve_stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
+        ("ticks", ctypes.c_int), ("r0_norm", ctypes.c_double), ("res_norm", ctypes.c_double),
+        ("x_norm", ctypes.c_double), ("err_bound", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("ats_context_create", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(P)]),
+    ("ats_context_destroy", ctypes.c_int, [P]),
+    ("ats_context_set_stream", ctypes.c_int, [P, P]),
+    ("ats_context_memory", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    ("ats_level_create", ctypes.c_int, [P, ctypes.POINTER(ats_level_desc), ctypes.POINTER(P)]),
+    ("ats_level_destroy", ctypes.c_int, [P]),
+    ("ats_level_size", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("ats_level_build_operator", ctypes.c_int, [P, ctypes.POINTER(ats_coef_desc)]),
+    ("ats_level_get_rhs", ctypes.c_int, [P, P, ctypes.c_int]),
+    ("ats_level_apply", ctypes.c_int, [P, P, P, ctypes.c_int]),
+    ("ats_solve", ctypes.c_int, [P, P, P, ctypes.POINTER(ats_solve_opts), ctypes.POINTER(ats_solve_stats)]),
+    ("ats_batch_create", ctypes.c_int, [P, ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ats_solve_opts), ctypes.POINTER(P)]),
+    ("ats_batch_solve", ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(ats_solve_stats)]),
+    ("ats_batch_destroy", ctypes.c_int, [P]),
+    ("ats_batch_run", ctypes.c_int, [P, ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(ats_solve_opts), ctypes.POINTER(ats_solve_stats)]),
+    ("ats_batch_set_profiling", ctypes.c_int, [P, ctypes.c_int]),
+    ("ats_batch_kernel_stats", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    ("ats_default_opts", None, [ctypes.POINTER(ats_solve_opts)]),
+    ("ats_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("ats_last_error", ctypes.c_char_p, []),
+    ("ats_layout_neighbors", ctypes.c_int, [ctypes.POINTER(ats_level_desc), P]),
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load the built library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library not built: {LIB_PATH} is missing "
+                    "(run paper_1401_1112_gb300.build.build())"
+                )
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in _SIGS:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class AtsError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = lib().ats_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {lib().ats_status_string(code).decode()} ({code}): {msg}")
+
+
+def _check(code, where):
+    if code < 0:
+        raise AtsError(code, where)
+    return code
+
+
+# ---------------------------------------------------------------------------
+# pointer marshalling
+# ---------------------------------------------------------------------------
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
+
+
+def _mem_of(*arrays) -> int:
+    kinds = {(_is_torch_cuda(a)) for a in arrays if a is not None}
+    if len(kinds) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    return ATS_MEM_DEVICE if kinds == {True} else ATS_MEM_HOST
+
+
+def _ptr(a, dtype=np.float64, keep=None):
+    """Raw pointer of a numpy array (converted to a contiguous ``dtype``
+    array, kept alive in ``keep``) or of a CUDA torch tensor."""
+    if a is None:
+        return None
+    if _is_torch_cuda(a):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if keep is not None:
+        keep.append(arr)
+    return arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def _level_desc(level, keep):
+    d = ats_level_desc()
+    d.n_oct = int(level.oct_xyz.shape[0])
+    d.oct_xyz = _ptr(level.oct_xyz, np.int32, keep)
+    d.leaf_mask = _ptr(level.leaf, np.uint8, keep) if level.leaf is not None else None
+    d.dx = float(level.dx)
+    d.n_face = int(len(level.face_cell))
+    if d.n_face:
+        d.face_cell = _ptr(level.face_cell, np.int32, keep)
+        d.face_dir = _ptr(level.face_dir, np.int8, keep)
+        d.face_kind = _ptr(level.face_kind, np.int8, keep)
+        d.face_rel = _ptr(level.face_rel, np.int8, keep)
+        d.face_alpha = _ptr(level.face_alpha, np.float64, keep)
+    return d
+
+
+def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, max_iter=0, max_refine=0,
+              inner_rtol=0.0, tile_octs=0, check_every=0, use_graph=0, mem=ATS_MEM_HOST) -> ats_solve_opts:
+    o = ats_solve_opts()
+    lib().ats_default_opts(ctypes.byref(o))
+    o.tol = tol
+    o.stop_rule = stop_rule
+    o.precision = precision
+    if max_iter:
+        o.max_iter = max_iter
+    if max_refine:
+        o.max_refine = max_refine
+    if inner_rtol:
+        o.inner_rtol = inner_rtol
+    o.tile_octs = tile_octs
+    if check_every:
+        o.check_every = check_every
+    o.use_graph = use_graph
+    o.mem = mem
+    return o
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, same names
+# ---------------------------------------------------------------------------
+
+def ats_context_create(device: int = 0, mem_budget_bytes: int = 0):
+    h = P()
+    _check(lib().ats_context_create(device, mem_budget_bytes, ctypes.byref(h)), "ats_context_create")
+    return h
+
+
+def ats_context_destroy(ctx):
+    return _check(lib().ats_context_destroy(ctx), "ats_context_destroy")
+
+
+def ats_context_set_stream(ctx, stream_handle: Optional[int]):
+    return _check(lib().ats_context_set_stream(ctx, ctypes.c_void_p(stream_handle) if stream_handle else None),
+                  "ats_context_set_stream")
+
+
+def ats_context_memory(ctx):
+    u, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().ats_context_memory(ctx, ctypes.byref(u), ctypes.byref(b)), "ats_context_memory")
+    return u.value, b.value
+
+
+def ats_level_create(ctx, level):
+    keep = []
+    d = _level_desc(level, keep)
+    h = P()
+    _check(lib().ats_level_create(ctx, ctypes.byref(d), ctypes.byref(h)), "ats_level_create")
+    return h
+
+
+def ats_level_destroy(lvl):
+    return _check(lib().ats_level_destroy(lvl), "ats_level_destroy")
+
+
+def ats_level_size(lvl):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ats_level_size(lvl, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "ats_level_size")
+    return a.value, b.value, c.value
+
+
+def ats_level_build_operator(lvl, dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None):
+    keep = []
+    c = ats_coef_desc()
+    c.dt = float(dt)
+    c.mem = _mem_of(K, E_old, s, src, face_K, face_E, face_F)
+    c.K = _ptr(K, keep=keep)
+    c.E_old = _ptr(E_old, keep=keep)
+    c.s = _ptr(s, keep=keep)
+    c.src = _ptr(src, keep=keep)
+    c.face_K = _ptr(face_K, keep=keep)
+    c.face_E = _ptr(face_E, keep=keep)
+    c.face_F = _ptr(face_F, keep=keep)
+    return _check(lib().ats_level_build_operator(lvl, ctypes.byref(c)), "ats_level_build_operator")
+
+
+def ats_level_get_rhs(lvl, out):
+    mem = _mem_of(out)
+    return _check(lib().ats_level_get_rhs(lvl, _ptr(out), mem), "ats_level_get_rhs")
+
+
+def ats_level_apply(lvl, x, y):
+    mem = _mem_of(x, y)
+    keep = []
+    return _check(lib().ats_level_apply(lvl, _ptr(x, keep=keep), _ptr(y), mem), "ats_level_apply")
+
+
+def ats_solve(lvl, x_inout, rhs=None, opts: Optional[ats_solve_opts] = None):
+    """x_inout: float64 numpy array (host, updated in place) or CUDA tensor."""
+    if isinstance(x_inout, np.ndarray) and (x_inout.dtype != np.float64 or not x_inout.flags.c_contiguous):
+        raise ValueError("x_inout must be a contiguous float64 array")
+    o = opts if opts is not None else make_opts()
+    o.mem = _mem_of(x_inout, rhs)
+    keep = []
+    st = ats_solve_stats()
+    code = lib().ats_solve(lvl, _ptr(rhs, keep=keep), _ptr(x_inout), ctypes.byref(o), ctypes.byref(st))
+    return code, st.as_dict()
+
+
+def ats_batch_create(ctx, levels: Sequence, opts: Optional[ats_solve_opts] = None):
+    arr = (P * len(levels))(*[l.handle if isinstance(l, Level) else l for l in levels])
+    o = opts if opts is not None else make_opts()
+    h = P()
+    _check(lib().ats_batch_create(ctx, arr, len(levels), ctypes.byref(o), ctypes.byref(h)), "ats_batch_create")
+    return h
+
+
+def ats_batch_solve(batch, xs: Sequence):
+    arr = (P * len(xs))(*[_ptr(x) for x in xs])
+    st = (ats_solve_stats * len(xs))()
+    code = lib().ats_batch_solve(batch, arr, st)
+    return code, [s.as_dict() for s in st]
+
+
+def ats_batch_destroy(batch):
+    return _check(lib().ats_batch_destroy(batch), "ats_batch_destroy")
+
+
+def ats_batch_run(ctx, levels: Sequence, xs: Sequence, opts: Optional[ats_solve_opts] = None):
+    arr = (P * len(levels))(*[l.handle if isinstance(l, Level) else l for l in levels])
+    xa = (P * len(xs))(*[_ptr(x) for x in xs])
+    o = opts if opts is not None else make_opts()
+    st = (ats_solve_stats * len(xs))()
+    code = lib().ats_batch_run(ctx, arr, len(levels), xa, ctypes.byref(o), st)
+    return code, [s.as_dict() for s in st]
+
+
+def ats_batch_set_profiling(batch, on: bool):
+    return _check(lib().ats_batch_set_profiling(batch, 1 if on else 0), "ats_batch_set_profiling")
+
+
+def ats_batch_kernel_stats(batch):
+    v = [ctypes.c_double() for _ in range(4)]
+    n = ctypes.c_int()
+    _check(lib().ats_batch_kernel_stats(batch, *[ctypes.byref(x) for x in v], ctypes.byref(n)), "ats_batch_kernel_stats")
+    return {"op_ms": v[0].value, "op_bytes": v[1].value, "upd_ms": v[2].value, "upd_bytes": v[3].value,
+            "launches": n.value}
+
+
+def ats_default_opts() -> ats_solve_opts:
+    o = ats_solve_opts()
+    lib().ats_default_opts(ctypes.byref(o))
+    return o
+
+
+def ats_status_string(code: int) -> str:
+    return lib().ats_status_string(code).decode()
+
+
+def ats_last_error() -> str:
+    return lib().ats_last_error().decode(errors="replace")
+
+
+def ats_layout_neighbors(level) -> np.ndarray:
+    keep = []
+    d = _level_desc(level, keep)
+    out = np.empty(6 * d.n_oct, dtype=np.int32)
+    _check(lib().ats_layout_neighbors(ctypes.byref(d), out.ctypes.data_as(ctypes.c_void_p)), "ats_layout_neighbors")
+    return out.reshape(-1, 6)
+
+
+# ---------------------------------------------------------------------------
+# handle owners
+# ---------------------------------------------------------------------------
+
+class Context:
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: Optional[int] = None):
+        self.handle = ats_context_create(device, mem_budget_bytes)
+        if stream:
+            ats_context_set_stream(self.handle, stream)
+
+    def set_stream(self, stream_handle):
+        ats_context_set_stream(self.handle, stream_handle)
+
+    def memory(self):
+        return ats_context_memory(self.handle)
+
+    def close(self):
+        if self.handle:
+            ats_context_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Level:
+    def __init__(self, ctx: Context, level_desc):
+        self.ctx = ctx
+        self.desc = level_desc
+        self.handle = ats_level_create(ctx.handle, level_desc)
+        self.n_cell = 8 * int(level_desc.oct_xyz.shape[0])
+
+    def build(self, dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None):
+        return ats_level_build_operator(self.handle, dt, K, E_old, s=s, src=src, face_K=face_K, face_E=face_E,
+                                        face_F=face_F)
+
+    def rhs(self):
+        out = np.empty(self.n_cell)
+        ats_level_get_rhs(self.handle, out)
+        return out
+
+    def apply(self, x):
+        y = np.empty(self.n_cell) if not _is_torch_cuda(x) else x.new_empty(x.shape)
+        ats_level_apply(self.handle, x, y)
+        return y
+
+    def solve(self, x_inout, rhs=None, **opts):
+        return ats_solve(self.handle, x_inout, rhs=rhs, opts=make_opts(**opts))
+
+    def close(self):
+        if self.handle:
+            ats_level_destroy(self.handle)
+            self.handle = None
+
+
+class Batch:
+    def __init__(self, ctx: Context, levels: Sequence[Level], **opts):
+        self.ctx = ctx
+        self.levels = list(levels)
+        self.opts = make_opts(**opts)
+        self.handle = ats_batch_create(ctx.handle, self.levels, self.opts)
+
+    def solve(self, xs):
+        return ats_batch_solve(self.handle, xs)
+
+    def set_profiling(self, on=True):
+        ats_batch_set_profiling(self.handle, on)
+
+    def kernel_stats(self):
+        return ats_batch_kernel_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ats_batch_destroy(self.handle)
+            self.handle = None

@@ -1,0 +1,146 @@
+// Internal declarations of the sm_103a level-solve library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ats.h"
+
+namespace ats {
+
+constexpr int kThreads = 256;          // threads per CTA of the stencil kernels
+constexpr int kOctsPerPass = kThreads / 8;
+constexpr int kNumPartials = 4;        // FP64 partial sums per work item
+
+// Phases of the per-solve state machine advanced by each device "tick"
+// (one op kernel + one update kernel).
+enum Phase : int {
+  kRefine = 0,  // FP64 true residual r = b - A (x + e), z = D^-1 r
+  kInner = 1,   // one CG iteration on the correction e
+  kDone = 2,
+};
+
+// Static description of one solve, read-only on the device during a run.
+struct SolveDev {
+  const int32_t *nbr;   // [n_oct*6]
+  const int32_t *xrec;  // [n_oct] record of the diagonal extras or -1
+  const double *K64;    // [N]  K on leaves, -1 on non-leaf cells
+  const void *KT;       // [N]  K in the bulk precision (alias of K64 in FP64 mode)
+  const double *xd64;   // [n_rec*8] s_i + sum of interface w C
+  const void *xdT;      // same in the bulk precision
+  const double *b64;    // [N]
+  double *x64;          // [N]  the FP64 iterate
+  void *e;              // [N]  correction (bulk precision)
+  void *z;              // [N]  preconditioned residual (bulk precision)
+  void *p0;             // [N]  search direction, ping
+  void *p1;             // [N]  search direction, pong
+  double h;             // dt / dx^2 / 2, so an interior C = h (K_i + K_j)
+  double tol;
+  double inner_rtol;
+  double final_safety;  // inner target = max(inner_rtol r, final_safety * tol * ref)
+  int32_t n_oct;
+  int32_t item_begin;
+  int32_t n_items;
+  int32_t stop_rule;
+  int32_t max_iter;
+  int32_t max_refine;
+  int32_t inner_max;    // iterations per inner pass before a restart
+  int32_t pad;
+};
+
+// Mutable per-solve scalars (device).
+struct SolveScalars {
+  int32_t phase;
+  int32_t phase_next;
+  int32_t first;        // next op kernel starts a new direction (p = z)
+  int32_t pcur;         // which p buffer holds the current direction
+  int32_t iters;
+  int32_t inner_iters;
+  int32_t refines;
+  int32_t status;
+  int32_t counter;      // work items finished in the current kernel
+  int32_t final_pass;   // the next refine pass ends the solve
+  int32_t ticks;
+  int32_t pad;
+  double alpha;
+  double beta;
+  double rz;
+  double r0;
+  double inner_target;
+  double rnorm;         // last FP64 true residual norm
+  double xnorm;
+  double maxchg;
+};
+
+struct WorkItem {
+  int32_t solve;
+  int32_t oct_begin;
+  int32_t n_oct;
+  int32_t pad;
+};
+
+// ---- launchers (kernels.cu) ----
+struct CoefArgs {
+  int64_t n_oct;
+  const uint8_t *leaf;
+  const int32_t *frec;      // [n_oct] face record or -1
+  const int32_t *rec_face;  // [n_rec*48] descriptor id per (cell, dir) or -1
+  const int32_t *xrec;      // [n_oct] diagonal-extra record or -1
+  const int8_t *face_kind;
+  const int8_t *face_rel;
+  const double *face_alpha;
+  const double *face_K;
+  const double *face_E;
+  const double *face_F;
+  const double *K;
+  const double *E_old;
+  const double *s;
+  const double *src;
+  double h;
+  double *K64;
+  float *K32;
+  double *xd64;
+  float *xd32;
+  double *b64;
+  int *err_flag;
+};
+cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st);
+
+// One tick = k_op + k_upd over the work list.  Events (may be null) are
+// recorded before k_op, between the kernels and after k_upd; `capture` says
+// whether the stream is being captured into a graph.
+cudaError_t launch_tick(bool fp64, bool paper, const SolveDev *solves, SolveScalars *sc,
+                        const WorkItem *items, int n_items, double *partials, int *n_active,
+                        int grid, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
+                        cudaEvent_t ev2, bool capture, unsigned long long *cells_counter);
+
+// Start of a solve: e = 0 on every cell of every item, and x64 = src[solve]
+// where src (device array of device pointers) is non-null for that solve.
+cudaError_t launch_init(bool fp64, const SolveDev *solves, const WorkItem *items, int n_items,
+                        const double *const *src, int grid, cudaStream_t st);
+// End of a solve: dst[solve] = x64 where dst[solve] is non-null.
+cudaError_t launch_final(const SolveDev *solves, const WorkItem *items, int n_items,
+                         double *const *dst, int grid, cudaStream_t st);
+
+cudaError_t launch_apply64(const SolveDev *solve_host_copy, const double *x, double *y,
+                           cudaStream_t st);
+
+int tick_blocks_per_sm(bool fp64, bool paper);
+
+// ---- layout (layout.cpp) ----
+struct Layout {
+  int64_t n_oct = 0;
+  std::vector<int32_t> nbr;       // [n_oct*6]
+  std::vector<int32_t> frec;      // [n_oct]
+  std::vector<int32_t> rec_face;  // [n_rec*48]
+  int64_t n_rec = 0;
+};
+// Returns "" on success or an error message.
+std::string build_layout(const ats_level_desc &d, Layout &out);
+
+void set_error(const std::string &msg);
+
+}  // namespace ats

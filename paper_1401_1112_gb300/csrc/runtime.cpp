@@ -1,0 +1,1037 @@
+// Host runtime of the level-solve library: context, levels, operator build,
+// solve plans (single and batched), CUDA-graph replay and convergence polling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "ats_internal.h"
+
+namespace ats {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+}  // namespace ats
+
+using namespace ats;
+
+// ---------------------------------------------------------------------------
+// objects
+// ---------------------------------------------------------------------------
+
+struct ats_context {
+  int device = 0;
+  size_t budget = 0;
+  size_t used = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  std::unordered_map<void *, size_t> allocs;
+};
+
+struct Plan;
+
+struct ats_level {
+  ats_context *ctx = nullptr;
+  int64_t n_oct = 0, N = 0, n_face = 0, n_rec = 0;
+  double dx = 0.0;
+  // topology
+  int32_t *nbr = nullptr, *frec = nullptr, *rec_face = nullptr, *xrec_dense = nullptr;
+  uint8_t *leaf = nullptr;
+  int8_t *fkind = nullptr, *frel = nullptr;
+  double *falpha = nullptr;
+  // operator
+  bool built = false;
+  bool dense_xd = false;
+  double dt = 0.0;
+  double *K64 = nullptr, *xd64 = nullptr, *b64 = nullptr;
+  float *K32 = nullptr, *xd32 = nullptr;
+  int64_t xd_cap = 0;  // records allocated in xd64/xd32
+  int *err_flag = nullptr;
+  // host-pointer staging of per-step arrays
+  double *stage_cell = nullptr;  // 4 x N : K, E, s, src
+  double *stage_face = nullptr;  // 3 x n_face : K, E, F
+  // solve vectors: the FP64 iterate, and one set of CG vectors per bulk
+  // precision ([0] FP64, [1] FP32), allocated on first use
+  double *x64 = nullptr;
+  void *e[2] = {nullptr, nullptr}, *z[2] = {nullptr, nullptr};
+  void *p0[2] = {nullptr, nullptr}, *p1[2] = {nullptr, nullptr};
+  double *rhs_save = nullptr;  // b when a solve overrides it
+  Plan *solo = nullptr;        // cached single-solve plan
+};
+
+namespace {
+
+struct StatusError {
+  ats_status code;
+};
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess) {                                                             \
+      set_error(std::string("CUDA error: ") + cudaGetErrorString(_e) + " at " #expr);     \
+      return ATS_ERR_CUDA;                                                               \
+    }                                                                                    \
+  } while (0)
+
+ats_status dev_alloc(ats_context *ctx, size_t bytes, void **out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (ctx->budget && ctx->used + bytes > ctx->budget) {
+    set_error("device memory budget exceeded");
+    return ATS_ERR_OVER_BUDGET;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    return ATS_ERR_OOM;
+  }
+  ctx->allocs[p] = bytes;
+  ctx->used += bytes;
+  *out = p;
+  return ATS_OK;
+}
+
+template <typename P>
+ats_status dev_alloc_t(ats_context *ctx, size_t count, P **out) {
+  void *p = nullptr;
+  ats_status s = dev_alloc(ctx, count * sizeof(P), &p);
+  *out = (P *)p;
+  return s;
+}
+
+void dev_free(ats_context *ctx, void *p) {
+  if (!p) return;
+  auto it = ctx->allocs.find(p);
+  if (it != ctx->allocs.end()) {
+    ctx->used -= it->second;
+    ctx->allocs.erase(it);
+  }
+  cudaFree(p);
+}
+
+cudaMemcpyKind kind_of(int mem, bool to_device) {
+  if (mem == ATS_MEM_DEVICE) return cudaMemcpyDeviceToDevice;
+  return to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// solve plan: work list, per-solve device descriptors, graph
+// ---------------------------------------------------------------------------
+
+struct Plan {
+  ats_context *ctx = nullptr;
+  std::vector<ats_level *> levels;
+  ats_solve_opts opts{};
+  bool fp64 = true, paper = false;
+  int n = 0, n_items = 0, grid = 1;
+  SolveDev *d_solves = nullptr;
+  SolveScalars *d_sc = nullptr;
+  WorkItem *d_items = nullptr;
+  double *d_partials = nullptr;
+  int *d_active = nullptr;
+  unsigned long long *d_cells = nullptr;
+  const double **d_src = nullptr;  // [n] device pointers for x copy-in (or null)
+  double **d_dst = nullptr;        // [n] device pointers for x copy-out (or null)
+  int *h_active = nullptr;         // pinned [2]: one per poll slot
+  std::vector<SolveDev> h_solves;
+  std::vector<SolveScalars> h_sc;
+  cudaGraphExec_t exec = nullptr;
+  int graph_ticks = 0;
+  bool graph_profiled = false;
+  bool profiling = false;
+  std::vector<cudaEvent_t> evs;  // 3 per tick of a chunk
+  cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+  int slot = 0;
+  double op_ms = 0.0, upd_ms = 0.0, op_bytes = 0.0, upd_bytes = 0.0;
+  int launches = 0;
+};
+
+struct ats_batch {
+  Plan *plan = nullptr;
+};
+
+namespace {
+
+void fill_defaults(ats_solve_opts *o) {
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->stop_rule = ATS_STOP_RESIDUAL;
+  o->precision = ATS_PREC_FP64;
+  o->max_iter = 20000;
+  o->max_refine = 40;
+  o->inner_rtol = 1e-4;
+  o->tile_octs = 0;
+  o->check_every = 16;
+  o->use_graph = 0;
+  o->mem = ATS_MEM_HOST;
+}
+
+ats_solve_opts normalize(const ats_solve_opts *in) {
+  ats_solve_opts o;
+  fill_defaults(&o);
+  if (!in) return o;
+  o = *in;
+  if (!(o.tol > 0.0)) o.tol = 1e-10;
+  if (o.max_iter <= 0) o.max_iter = 20000;
+  if (o.max_refine <= 0) o.max_refine = 40;
+  if (!(o.inner_rtol > 0.0)) o.inner_rtol = 1e-4;
+  if (o.check_every <= 0) o.check_every = 16;
+  return o;
+}
+
+// Octs per work item: a multiple of 32 octs (one CTA pass = 32 octs).  Small
+// solves get one item; large ones are split so that every solve has enough
+// items to fill the GPU while the last-CTA reduction stays short.
+int choose_tile(int64_t n_oct, int requested) {
+  if (requested > 0) return std::max(32, (requested + 31) / 32 * 32);
+  if (n_oct <= 256) return 256;
+  if (n_oct <= 32768) return 128;
+  return 256;
+}
+
+ats_status ensure_vectors(ats_level *L, bool fp64) {
+  const int k = fp64 ? 0 : 1;
+  ats_context *ctx = L->ctx;
+  const size_t es = fp64 ? sizeof(double) : sizeof(float);
+  ats_status s;
+  if (!L->x64 && (s = dev_alloc_t(ctx, L->N, &L->x64)) != ATS_OK) return s;
+  if (!L->e[k] && (s = dev_alloc(ctx, es * L->N, &L->e[k])) != ATS_OK) return s;
+  if (!L->z[k] && (s = dev_alloc(ctx, es * L->N, &L->z[k])) != ATS_OK) return s;
+  if (!L->p0[k] && (s = dev_alloc(ctx, es * L->N, &L->p0[k])) != ATS_OK) return s;
+  if (!L->p1[k] && (s = dev_alloc(ctx, es * L->N, &L->p1[k])) != ATS_OK) return s;
+  return ATS_OK;
+}
+
+void plan_free(Plan *P) {
+  if (!P) return;
+  ats_context *ctx = P->ctx;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  for (auto e : P->evs) cudaEventDestroy(e);
+  for (auto e : P->poll_ev)
+    if (e) cudaEventDestroy(e);
+  dev_free(ctx, P->d_solves);
+  dev_free(ctx, P->d_sc);
+  dev_free(ctx, P->d_items);
+  dev_free(ctx, P->d_partials);
+  dev_free(ctx, P->d_active);
+  dev_free(ctx, P->d_cells);
+  dev_free(ctx, P->d_src);
+  dev_free(ctx, P->d_dst);
+  if (P->h_active) cudaFreeHost(P->h_active);
+  delete P;
+}
+
+ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const ats_solve_opts *opts_in,
+                       Plan **out) {
+  *out = nullptr;
+  if (!ctx || !levels || n <= 0) {
+    set_error("plan: bad arguments");
+    return ATS_ERR_INVALID_ARG;
+  }
+  ats_solve_opts o = normalize(opts_in);
+  if (o.precision != ATS_PREC_FP64 && o.precision != ATS_PREC_MIXED) {
+    set_error("bad precision");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (o.stop_rule < 0 || o.stop_rule > 2) {
+    set_error("bad stop_rule");
+    return ATS_ERR_INVALID_ARG;
+  }
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  Plan *P = new (std::nothrow) Plan();
+  if (!P) return ATS_ERR_OOM;
+  P->ctx = ctx;
+  P->opts = o;
+  P->fp64 = (o.precision == ATS_PREC_FP64);
+  P->paper = (o.stop_rule == ATS_STOP_PAPER);
+  P->n = n;
+  std::vector<WorkItem> items;
+  P->h_solves.resize(n);
+  P->h_sc.resize(n);
+  ats_status s;
+  for (int k = 0; k < n; ++k) {
+    ats_level *L = levels[k];
+    if (!L || L->ctx != ctx) {
+      plan_free(P);
+      set_error("plan: level is null or from another context");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (!L->built) {
+      plan_free(P);
+      set_error("plan: level operator not built");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if ((s = ensure_vectors(L, P->fp64)) != ATS_OK) {
+      plan_free(P);
+      return s;
+    }
+    P->levels.push_back(L);
+    SolveDev &sd = P->h_solves[k];
+    std::memset(&sd, 0, sizeof(sd));
+    sd.nbr = L->nbr;
+    sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
+    sd.K64 = L->K64;
+    sd.KT = P->fp64 ? (const void *)L->K64 : (const void *)L->K32;
+    sd.xd64 = L->xd64;
+    sd.xdT = P->fp64 ? (const void *)L->xd64 : (const void *)L->xd32;
+    sd.b64 = L->b64;
+    sd.x64 = L->x64;
+    const int vk = P->fp64 ? 0 : 1;
+    sd.e = L->e[vk];
+    sd.z = L->z[vk];
+    sd.p0 = L->p0[vk];
+    sd.p1 = L->p1[vk];
+    sd.h = 0.5 * L->dt / (L->dx * L->dx);
+    sd.tol = o.tol;
+    sd.inner_rtol = P->fp64 ? 0.0 : o.inner_rtol;
+    sd.final_safety = P->fp64 ? 1.0 : 0.5;
+    sd.n_oct = (int32_t)L->n_oct;
+    sd.stop_rule = o.stop_rule;
+    sd.max_iter = o.max_iter;
+    sd.max_refine = o.max_refine;
+    sd.inner_max = P->fp64 ? o.max_iter : 4000;
+    const int tile = choose_tile(L->n_oct, o.tile_octs);
+    sd.item_begin = (int32_t)items.size();
+    for (int64_t b = 0; b < L->n_oct; b += tile) {
+      WorkItem w;
+      w.solve = k;
+      w.oct_begin = (int32_t)b;
+      w.n_oct = (int32_t)std::min<int64_t>(tile, L->n_oct - b);
+      w.pad = 0;
+      items.push_back(w);
+    }
+    sd.n_items = (int32_t)items.size() - sd.item_begin;
+    SolveScalars &sc = P->h_sc[k];
+    std::memset(&sc, 0, sizeof(sc));
+    sc.phase = kRefine;
+    sc.status = ATS_OK;
+  }
+  P->n_items = (int)items.size();
+  const int bps = tick_blocks_per_sm(P->fp64, P->paper);
+  P->grid = std::max(1, std::min(P->n_items, bps * ctx->num_sms));
+  if ((s = dev_alloc_t(ctx, n, &P->d_solves)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, n, &P->d_sc)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, P->n_items, &P->d_items)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 4, &P->d_cells)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, n, &P->d_src)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, n, &P->d_dst)) != ATS_OK) {
+    plan_free(P);
+    return s;
+  }
+  if (cudaMallocHost(&P->h_active, 2 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    plan_free(P);
+    set_error("cudaMallocHost failed");
+    return ATS_ERR_OOM;
+  }
+  cudaStream_t st = ctx->stream;
+  CUDA_TRY(cudaMemcpyAsync(P->d_solves, P->h_solves.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaEventCreateWithFlags(&P->poll_ev[0], cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&P->poll_ev[1], cudaEventDisableTiming));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  *out = P;
+  return ATS_OK;
+}
+
+ats_status plan_ensure_events(Plan *P) {
+  const size_t need = 3 * (size_t)P->opts.check_every;
+  while (P->evs.size() < need) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreate(&e));
+    P->evs.push_back(e);
+  }
+  return ATS_OK;
+}
+
+// Enqueue one poll interval (check_every ticks) on the stream.
+ats_status plan_enqueue_chunk(Plan *P) {
+  cudaStream_t st = P->ctx->stream;
+  const int k = P->opts.check_every;
+  const bool prof = P->profiling;
+  if (P->opts.use_graph) {
+    if (P->exec && P->graph_profiled != prof) {
+      cudaGraphExecDestroy(P->exec);
+      P->exec = nullptr;
+    }
+    if (!P->exec) {
+      if (prof) {
+        ats_status s = plan_ensure_events(P);
+        if (s != ATS_OK) return s;
+      }
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t err = cudaSuccess;
+      for (int t = 0; t < k && err == cudaSuccess; ++t) {
+        err = launch_tick(P->fp64, P->paper, P->d_solves, P->d_sc, P->d_items, P->n_items, P->d_partials,
+                          P->d_active, P->grid, st, prof ? P->evs[3 * t] : nullptr,
+                          prof ? P->evs[3 * t + 1] : nullptr, prof ? P->evs[3 * t + 2] : nullptr, true,
+                          prof ? P->d_cells : nullptr);
+      }
+      cudaError_t err2 = cudaStreamEndCapture(st, &g);
+      if (err != cudaSuccess || err2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        set_error(std::string("graph capture failed: ") + cudaGetErrorString(err != cudaSuccess ? err : err2));
+        return ATS_ERR_CUDA;
+      }
+      err = cudaGraphInstantiate(&P->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (err != cudaSuccess) {
+        P->exec = nullptr;
+        set_error(std::string("graph instantiate failed: ") + cudaGetErrorString(err));
+        return ATS_ERR_CUDA;
+      }
+      P->graph_profiled = prof;
+      P->graph_ticks = k;
+    }
+    CUDA_TRY(cudaGraphLaunch(P->exec, st));
+  } else {
+    if (prof) {
+      ats_status s = plan_ensure_events(P);
+      if (s != ATS_OK) return s;
+    }
+    for (int t = 0; t < k; ++t) {
+      CUDA_TRY(launch_tick(P->fp64, P->paper, P->d_solves, P->d_sc, P->d_items, P->n_items, P->d_partials,
+                           P->d_active, P->grid, st, prof ? P->evs[3 * t] : nullptr,
+                           prof ? P->evs[3 * t + 1] : nullptr, prof ? P->evs[3 * t + 2] : nullptr, false,
+                           prof ? P->d_cells : nullptr));
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(P->h_active + P->slot, P->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaEventRecord(P->poll_ev[P->slot], st));
+  P->slot ^= 1;
+  return ATS_OK;
+}
+
+ats_status plan_collect_events(Plan *P) {
+  const int k = P->opts.check_every;
+  for (int t = 0; t < k; ++t) {
+    float a = 0.f, b = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&a, P->evs[3 * t], P->evs[3 * t + 1]));
+    CUDA_TRY(cudaEventElapsedTime(&b, P->evs[3 * t + 1], P->evs[3 * t + 2]));
+    P->op_ms += a;
+    P->upd_ms += b;
+    P->launches += 2;
+  }
+  return ATS_OK;
+}
+
+// Algorithmic bytes per cell of each kernel/phase (compulsory traffic of the
+// vectors and coefficients; neighbour tables and records not counted).
+void plan_bytes(const Plan *P, const unsigned long long cells[4], double *op_b, double *upd_b) {
+  const double w = P->fp64 ? 8.0 : 4.0;
+  // op inner: read z, p_old, K; write p_new.   op refine: read x64, e, K64, K_T, b64; write z
+  const double op_inner = 4 * w;
+  const double op_refine = 8 + w + 8 + (P->fp64 ? 0 : w) + 8 + w;
+  // upd inner: read p, K, z, e; write z, e.    upd refine: read/write x64 and e
+  const double upd_inner = 6 * w;
+  const double upd_refine = 16 + 2 * w;
+  *op_b = op_inner * cells[0] + op_refine * cells[1];
+  *upd_b = upd_inner * cells[2] + upd_refine * cells[3];
+}
+
+// Run a plan to completion.  x_inout[k] (host or device per opts.mem) or the
+// level's current rhs override is handled by the caller.
+ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
+  ats_context *ctx = P->ctx;
+  cudaStream_t st = ctx->stream;
+  const int n = P->n;
+  const bool dev = (P->opts.mem == ATS_MEM_DEVICE);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  // a level rebuilt with another dt (or another diagonal-extra layout) since
+  // the plan was made: refresh the solve descriptors
+  bool stale = false;
+  for (int k = 0; k < n; ++k) {
+    ats_level *L = P->levels[k];
+    SolveDev &sd = P->h_solves[k];
+    const double h = 0.5 * L->dt / (L->dx * L->dx);
+    const int32_t *xrec = L->dense_xd ? L->xrec_dense : L->frec;
+    const void *xdT = P->fp64 ? (const void *)L->xd64 : (const void *)L->xd32;
+    if (sd.h != h || sd.xrec != xrec || sd.xd64 != L->xd64 || sd.xdT != xdT) {
+      sd.h = h;
+      sd.xrec = xrec;
+      sd.xd64 = L->xd64;
+      sd.xdT = xdT;
+      stale = true;
+    }
+  }
+  if (stale)
+    CUDA_TRY(cudaMemcpyAsync(P->d_solves, P->h_solves.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice, st));
+  // copy-in of x
+  std::vector<const double *> src(n, nullptr);
+  std::vector<double *> dst(n, nullptr);
+  for (int k = 0; k < n; ++k) {
+    if (!x_inout || !x_inout[k]) {
+      set_error("x_inout[k] is NULL");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (dev) {
+      src[k] = x_inout[k];
+      dst[k] = x_inout[k];
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(P->levels[k]->x64, x_inout[k], sizeof(double) * P->levels[k]->N,
+                               cudaMemcpyHostToDevice, st));
+    }
+  }
+  if (dev) {
+    CUDA_TRY(cudaMemcpyAsync(P->d_src, src.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(P->d_dst, dst.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(launch_init(P->fp64, P->d_solves, P->d_items, P->n_items, dev ? P->d_src : nullptr, P->grid, st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_sc, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, 4 * sizeof(unsigned long long), st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_active, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+  P->op_ms = P->upd_ms = 0.0;
+  P->launches = 0;
+
+  // host guard: every solve ends within max_iter + 2 (max_refine + 1) ticks
+  const int64_t max_ticks = (int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2) + 2 * P->opts.check_every;
+  int64_t ticks = 0;
+  ats_status s;
+  // Keep one poll interval queued ahead of the one being polled, so the GPU
+  // never idles on the host's check (not when profiling: the per-tick events
+  // must be read back before they are recorded again).  Extra intervals after
+  // convergence are no-ops: every work item of a finished solve is skipped.
+  const bool pipelined = !P->profiling;
+  P->slot = 0;
+  int pending = 0;  // intervals enqueued but not yet polled
+  int poll_slot = 0;
+  if ((s = plan_enqueue_chunk(P)) != ATS_OK) return s;
+  ++pending;
+  ticks += P->opts.check_every;
+  if (pipelined) {
+    if ((s = plan_enqueue_chunk(P)) != ATS_OK) return s;
+    ++pending;
+    ticks += P->opts.check_every;
+  }
+  bool timed_out = false;
+  for (;;) {
+    CUDA_TRY(cudaEventSynchronize(P->poll_ev[poll_slot]));
+    const int active = P->h_active[poll_slot];
+    poll_slot ^= 1;
+    --pending;
+    if (P->profiling) {
+      if ((s = plan_collect_events(P)) != ATS_OK) return s;
+    }
+    if (active <= 0) break;
+    if (ticks >= max_ticks) {
+      timed_out = true;
+      break;
+    }
+    if ((s = plan_enqueue_chunk(P)) != ATS_OK) return s;
+    ++pending;
+    ticks += P->opts.check_every;
+  }
+  (void)pending;
+  // copy-out
+  if (dev) {
+    CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->grid, st));
+  } else {
+    for (int k = 0; k < n; ++k)
+      CUDA_TRY(cudaMemcpyAsync(x_inout[k], P->levels[k]->x64, sizeof(double) * P->levels[k]->N,
+                               cudaMemcpyDeviceToHost, st));
+  }
+  std::vector<SolveScalars> sc(n);
+  CUDA_TRY(cudaMemcpyAsync(sc.data(), P->d_sc, sizeof(SolveScalars) * n, cudaMemcpyDeviceToHost, st));
+  unsigned long long cells[4] = {0, 0, 0, 0};
+  if (P->profiling) CUDA_TRY(cudaMemcpyAsync(cells, P->d_cells, sizeof(cells), cudaMemcpyDeviceToHost, st));
+  std::vector<int> flags(n, 0);
+  for (int k = 0; k < n; ++k)
+    CUDA_TRY(cudaMemcpyAsync(&flags[k], P->levels[k]->err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (P->profiling) plan_bytes(P, cells, &P->op_bytes, &P->upd_bytes);
+  ats_status first_err = ATS_OK;
+  for (int k = 0; k < n; ++k) {
+    int status = sc[k].status;
+    if (flags[k]) status = ATS_ERR_BAD_INPUT;
+    if (timed_out && sc[k].phase != kDone) status = ATS_ERR_TIMEOUT;
+    if (stats) {
+      ats_solve_stats &o = stats[k];
+      o.status = status;
+      o.iterations = sc[k].iters;
+      o.refinements = sc[k].refines;
+      o.ticks = sc[k].ticks;
+      o.r0_norm = sc[k].r0;
+      o.res_norm = sc[k].rnorm;
+      o.x_norm = sc[k].xnorm;
+      o.err_bound = sc[k].xnorm > 0.0 ? sc[k].rnorm / sc[k].xnorm : 0.0;
+    }
+    if (status != ATS_OK && first_err == ATS_OK) first_err = status;
+  }
+  if (first_err != ATS_OK) set_error(std::string("solve failed: ") + ats_status_string(first_err));
+  return first_err;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void ats_default_opts(ats_solve_opts *opts) {
+  if (opts) fill_defaults(opts);
+}
+
+const char *ats_status_string(ats_status s) {
+  switch (s) {
+    case ATS_OK: return "ok";
+    case ATS_ERR_INVALID_ARG: return "invalid argument";
+    case ATS_ERR_OOM: return "out of device memory";
+    case ATS_ERR_OVER_BUDGET: return "device memory budget exceeded";
+    case ATS_ERR_NOT_CONVERGED: return "not converged";
+    case ATS_ERR_BREAKDOWN: return "CG breakdown";
+    case ATS_ERR_TIMEOUT: return "timeout";
+    case ATS_ERR_CUDA: return "CUDA error";
+    case ATS_ERR_NO_DEVICE: return "no CUDA device";
+    case ATS_ERR_BAD_INPUT: return "bad input (non-finite value or K <= 0)";
+    case ATS_WARN_NEGATIVE: return "warning: negative energy in solution";
+    default: return "unknown status";
+  }
+}
+
+const char *ats_last_error(void) { return g_last_error.c_str(); }
+
+ats_status ats_layout_neighbors(const ats_level_desc *desc, int32_t *nbr) {
+  if (!desc || !nbr) {
+    set_error("null argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  Layout lay;
+  std::string msg = build_layout(*desc, lay);
+  if (!msg.empty()) {
+    set_error(msg);
+    return ATS_ERR_INVALID_ARG;
+  }
+  std::memcpy(nbr, lay.nbr.data(), sizeof(int32_t) * lay.nbr.size());
+  return ATS_OK;
+}
+
+ats_status ats_context_create(int device, size_t budget, ats_context **out) {
+  if (!out) return ATS_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) {
+    cudaGetLastError();
+    set_error("no CUDA device");
+    return ATS_ERR_NO_DEVICE;
+  }
+  if (device < 0 || device >= count) {
+    set_error("device index out of range");
+    return ATS_ERR_INVALID_ARG;
+  }
+  CUDA_TRY(cudaSetDevice(device));
+  ats_context *ctx = new (std::nothrow) ats_context();
+  if (!ctx) return ATS_ERR_OOM;
+  ctx->device = device;
+  ctx->budget = budget;
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete ctx;
+    set_error(cudaGetErrorString(e));
+    return ATS_ERR_CUDA;
+  }
+  ctx->stream = ctx->own_stream;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (ctx->num_sms <= 0) ctx->num_sms = 1;
+  *out = ctx;
+  return ATS_OK;
+}
+
+ats_status ats_context_destroy(ats_context *ctx) {
+  if (!ctx) return ATS_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &kv : ctx->allocs) cudaFree(kv.first);
+  ctx->allocs.clear();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+  return ATS_OK;
+}
+
+ats_status ats_context_set_stream(ats_context *ctx, void *stream) {
+  if (!ctx) return ATS_ERR_INVALID_ARG;
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return ATS_OK;
+}
+
+ats_status ats_context_memory(const ats_context *ctx, size_t *used, size_t *budget) {
+  if (!ctx) return ATS_ERR_INVALID_ARG;
+  if (used) *used = ctx->used;
+  if (budget) *budget = ctx->budget;
+  return ATS_OK;
+}
+
+ats_status ats_level_create(ats_context *ctx, const ats_level_desc *desc, ats_level **out) {
+  if (!ctx || !desc || !out) {
+    set_error("null argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  Layout lay;
+  std::string msg = build_layout(*desc, lay);
+  if (!msg.empty()) {
+    set_error(msg);
+    return ATS_ERR_INVALID_ARG;
+  }
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  ats_level *L = new (std::nothrow) ats_level();
+  if (!L) return ATS_ERR_OOM;
+  L->ctx = ctx;
+  L->n_oct = desc->n_oct;
+  L->N = 8 * desc->n_oct;
+  L->n_face = desc->n_face;
+  L->n_rec = lay.n_rec;
+  L->dx = desc->dx;
+  cudaStream_t st = ctx->stream;
+  ats_status s;
+  auto fail = [&](ats_status code) {
+    ats_level_destroy(L);
+    return code;
+  };
+  if ((s = dev_alloc_t(ctx, 6 * L->n_oct, &L->nbr)) != ATS_OK) return fail(s);
+  if ((s = dev_alloc_t(ctx, L->n_oct, &L->frec)) != ATS_OK) return fail(s);
+  if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, 48 * L->n_rec), &L->rec_face)) != ATS_OK) return fail(s);
+  if ((s = dev_alloc_t(ctx, L->n_oct, &L->leaf)) != ATS_OK) return fail(s);
+  if ((s = dev_alloc_t(ctx, 1, &L->err_flag)) != ATS_OK) return fail(s);
+  std::vector<uint8_t> leaf(L->n_oct, 0xFF);
+  if (desc->leaf_mask) std::memcpy(leaf.data(), desc->leaf_mask, L->n_oct);
+  if (cudaMemcpyAsync(L->nbr, lay.nbr.data(), sizeof(int32_t) * lay.nbr.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(L->frec, lay.frec.data(), sizeof(int32_t) * lay.frec.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (L->n_rec > 0 && cudaMemcpyAsync(L->rec_face, lay.rec_face.data(), sizeof(int32_t) * lay.rec_face.size(),
+                                       cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      cudaMemcpyAsync(L->leaf, leaf.data(), L->n_oct, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(L->err_flag, 0, sizeof(int), st) != cudaSuccess) {
+    set_error("level upload failed");
+    return fail(ATS_ERR_CUDA);
+  }
+  if (L->n_face > 0) {
+    if ((s = dev_alloc_t(ctx, L->n_face, &L->fkind)) != ATS_OK) return fail(s);
+    if ((s = dev_alloc_t(ctx, L->n_face, &L->frel)) != ATS_OK) return fail(s);
+    if ((s = dev_alloc_t(ctx, L->n_face, &L->falpha)) != ATS_OK) return fail(s);
+    std::vector<double> alpha(L->n_face, 1.0);
+    if (desc->face_alpha) std::memcpy(alpha.data(), desc->face_alpha, sizeof(double) * L->n_face);
+    if (cudaMemcpyAsync(L->fkind, desc->face_kind, L->n_face, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(L->frel, desc->face_rel, L->n_face, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(L->falpha, alpha.data(), sizeof(double) * L->n_face, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      set_error("face upload failed");
+      return fail(ATS_ERR_CUDA);
+    }
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("level upload sync failed");
+    return fail(ATS_ERR_CUDA);
+  }
+  *out = L;
+  return ATS_OK;
+}
+
+ats_status ats_level_destroy(ats_level *L) {
+  if (!L) return ATS_ERR_INVALID_ARG;
+  ats_context *ctx = L->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (L->solo) plan_free(L->solo);
+  void *ptrs[] = {L->nbr, L->frec, L->rec_face, L->xrec_dense, L->leaf, L->fkind, L->frel,
+                  L->falpha, L->K64, L->xd64, L->b64, L->K32, L->xd32, L->err_flag,
+                  L->stage_cell, L->stage_face, L->x64, L->rhs_save,
+                  L->e[0], L->z[0], L->p0[0], L->p1[0], L->e[1], L->z[1], L->p0[1], L->p1[1]};
+  for (void *p : ptrs) dev_free(ctx, p);
+  delete L;
+  return ATS_OK;
+}
+
+ats_status ats_level_size(const ats_level *L, int64_t *n_oct, int64_t *n_cell, int64_t *n_face) {
+  if (!L) return ATS_ERR_INVALID_ARG;
+  if (n_oct) *n_oct = L->n_oct;
+  if (n_cell) *n_cell = L->N;
+  if (n_face) *n_face = L->n_face;
+  return ATS_OK;
+}
+
+ats_status ats_level_build_operator(ats_level *L, const ats_coef_desc *c) {
+  if (!L || !c) {
+    set_error("null argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (!(c->dt > 0.0) || !std::isfinite(c->dt)) {
+    set_error("dt must be finite and > 0");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (!c->K || !c->E_old) {
+    set_error("K and E_old are required");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (c->mem != ATS_MEM_HOST && c->mem != ATS_MEM_DEVICE) {
+    set_error("bad mem");
+    return ATS_ERR_INVALID_ARG;
+  }
+  ats_context *ctx = L->ctx;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  ats_status s;
+  const int64_t N = L->N;
+  if (!L->K64) {
+    if ((s = dev_alloc_t(ctx, N, &L->K64)) != ATS_OK) return s;
+    if ((s = dev_alloc_t(ctx, N, &L->K32)) != ATS_OK) return s;
+    if ((s = dev_alloc_t(ctx, N, &L->b64)) != ATS_OK) return s;
+  }
+  // diagonal extras: sparse records, or dense when a shift s is given
+  const bool dense = (c->s != nullptr);
+  const int64_t need = dense ? L->n_oct : L->n_rec;
+  if (need > L->xd_cap) {
+    dev_free(ctx, L->xd64);
+    dev_free(ctx, L->xd32);
+    L->xd64 = nullptr;
+    L->xd32 = nullptr;
+    L->xd_cap = 0;
+    if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, 8 * need), &L->xd64)) != ATS_OK) return s;
+    if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, 8 * need), &L->xd32)) != ATS_OK) return s;
+    L->xd_cap = need;
+  }
+  if (dense && !L->xrec_dense) {
+    if ((s = dev_alloc_t(ctx, L->n_oct, &L->xrec_dense)) != ATS_OK) return s;
+    std::vector<int32_t> id(L->n_oct);
+    for (int64_t o = 0; o < L->n_oct; ++o) id[o] = (int32_t)o;
+    CUDA_TRY(cudaMemcpyAsync(L->xrec_dense, id.data(), sizeof(int32_t) * L->n_oct, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  L->dense_xd = dense;
+
+  const double *K = c->K, *E = c->E_old, *sh = c->s, *src = c->src;
+  const double *fK = c->face_K, *fE = c->face_E, *fF = c->face_F;
+  if (c->mem == ATS_MEM_HOST) {
+    if (!L->stage_cell) {
+      if ((s = dev_alloc_t(ctx, 4 * N, &L->stage_cell)) != ATS_OK) return s;
+      if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, 3 * L->n_face), &L->stage_face)) != ATS_OK) return s;
+    }
+    double *dK = L->stage_cell, *dE = dK + N, *dS = dE + N, *dSrc = dS + N;
+    double *dfK = L->stage_face, *dfE = dfK + L->n_face, *dfF = dfE + L->n_face;
+    CUDA_TRY(cudaMemcpyAsync(dK, K, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(dE, E, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    K = dK;
+    E = dE;
+    if (sh) {
+      CUDA_TRY(cudaMemcpyAsync(dS, sh, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+      sh = dS;
+    }
+    if (src) {
+      CUDA_TRY(cudaMemcpyAsync(dSrc, src, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+      src = dSrc;
+    }
+    if (L->n_face > 0) {
+      if (fK) {
+        CUDA_TRY(cudaMemcpyAsync(dfK, fK, sizeof(double) * L->n_face, cudaMemcpyHostToDevice, st));
+        fK = dfK;
+      }
+      if (fE) {
+        CUDA_TRY(cudaMemcpyAsync(dfE, fE, sizeof(double) * L->n_face, cudaMemcpyHostToDevice, st));
+        fE = dfE;
+      }
+      if (fF) {
+        CUDA_TRY(cudaMemcpyAsync(dfF, fF, sizeof(double) * L->n_face, cudaMemcpyHostToDevice, st));
+        fF = dfF;
+      }
+    }
+  }
+  CoefArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_oct = L->n_oct;
+  a.leaf = L->leaf;
+  a.frec = L->frec;
+  a.rec_face = L->rec_face;
+  a.xrec = dense ? L->xrec_dense : L->frec;
+  a.face_kind = L->fkind;
+  a.face_rel = L->frel;
+  a.face_alpha = L->falpha;
+  a.face_K = L->n_face ? fK : nullptr;
+  a.face_E = L->n_face ? fE : nullptr;
+  a.face_F = L->n_face ? fF : nullptr;
+  a.K = K;
+  a.E_old = E;
+  a.s = sh;
+  a.src = src;
+  a.h = 0.5 * c->dt / (L->dx * L->dx);
+  a.K64 = L->K64;
+  a.K32 = L->K32;
+  a.xd64 = L->xd64;
+  a.xd32 = L->xd32;
+  a.b64 = L->b64;
+  a.err_flag = L->err_flag;
+  CUDA_TRY(cudaMemsetAsync(L->err_flag, 0, sizeof(int), st));
+  CUDA_TRY(launch_coef_build(a, st));
+  if (c->mem == ATS_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));  // staging reuse
+  L->dt = c->dt;
+  L->built = true;
+  return ATS_OK;
+}
+
+ats_status ats_level_get_rhs(ats_level *L, double *b, int mem) {
+  if (!L || !b || !L->built) return ATS_ERR_INVALID_ARG;
+  CUDA_TRY(cudaSetDevice(L->ctx->device));
+  CUDA_TRY(cudaMemcpyAsync(b, L->b64, sizeof(double) * L->N, kind_of(mem, false), L->ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(L->ctx->stream));
+  return ATS_OK;
+}
+
+ats_status ats_level_apply(ats_level *L, const double *x, double *y, int mem) {
+  if (!L || !x || !y || !L->built) return ATS_ERR_INVALID_ARG;
+  ats_context *ctx = L->ctx;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  double *dx = nullptr, *dy = nullptr;
+  ats_status s;
+  if (mem == ATS_MEM_HOST) {
+    if ((s = dev_alloc_t(ctx, L->N, &dx)) != ATS_OK) return s;
+    if ((s = dev_alloc_t(ctx, L->N, &dy)) != ATS_OK) {
+      dev_free(ctx, dx);
+      return s;
+    }
+    cudaMemcpyAsync(dx, x, sizeof(double) * L->N, cudaMemcpyHostToDevice, st);
+  }
+  SolveDev sd;
+  std::memset(&sd, 0, sizeof(sd));
+  sd.nbr = L->nbr;
+  sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
+  sd.K64 = L->K64;
+  sd.xd64 = L->xd64;
+  sd.h = 0.5 * L->dt / (L->dx * L->dx);
+  sd.n_oct = (int32_t)L->n_oct;
+  cudaError_t e = launch_apply64(&sd, mem == ATS_MEM_HOST ? dx : x, mem == ATS_MEM_HOST ? dy : y, st);
+  if (e == cudaSuccess && mem == ATS_MEM_HOST)
+    e = cudaMemcpyAsync(y, dy, sizeof(double) * L->N, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dev_free(ctx, dx);
+  dev_free(ctx, dy);
+  if (e != cudaSuccess) {
+    set_error(cudaGetErrorString(e));
+    return ATS_ERR_CUDA;
+  }
+  return ATS_OK;
+}
+
+ats_status ats_solve(ats_level *L, const double *rhs, double *x_inout, const ats_solve_opts *opts,
+                     ats_solve_stats *stats) {
+  if (!L || !x_inout) {
+    set_error("null argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (!L->built) {
+    set_error("level operator not built");
+    return ATS_ERR_INVALID_ARG;
+  }
+  ats_solve_opts o = normalize(opts);
+  ats_context *ctx = L->ctx;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  ats_status s;
+  // (re)use the cached single-solve plan when its options match
+  if (L->solo && (std::memcmp(&L->solo->opts, &o, sizeof(o)) != 0 ||
+                  L->solo->fp64 != (o.precision == ATS_PREC_FP64))) {
+    plan_free(L->solo);
+    L->solo = nullptr;
+  }
+  if (!L->solo) {
+    ats_level *arr[1] = {L};
+    if ((s = plan_create(ctx, arr, 1, &o, &L->solo)) != ATS_OK) return s;
+  }
+  if (rhs) {
+    if (!L->rhs_save && (s = dev_alloc_t(ctx, L->N, &L->rhs_save)) != ATS_OK) return s;
+    CUDA_TRY(cudaMemcpyAsync(L->rhs_save, L->b64, sizeof(double) * L->N, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(L->b64, rhs, sizeof(double) * L->N, kind_of(o.mem, true), st));
+  }
+  double *xs[1] = {x_inout};
+  s = plan_run(L->solo, xs, stats);
+  if (rhs) {
+    cudaMemcpyAsync(L->b64, L->rhs_save, sizeof(double) * L->N, cudaMemcpyDeviceToDevice, st);
+    cudaStreamSynchronize(st);
+  }
+  return s;
+}
+
+ats_status ats_batch_create(ats_context *ctx, ats_level *const *levels, int n, const ats_solve_opts *opts,
+                            ats_batch **out) {
+  if (!out) return ATS_ERR_INVALID_ARG;
+  *out = nullptr;
+  Plan *P = nullptr;
+  ats_status s = plan_create(ctx, levels, n, opts, &P);
+  if (s != ATS_OK) return s;
+  ats_batch *B = new (std::nothrow) ats_batch();
+  if (!B) {
+    plan_free(P);
+    return ATS_ERR_OOM;
+  }
+  B->plan = P;
+  *out = B;
+  return ATS_OK;
+}
+
+ats_status ats_batch_solve(ats_batch *B, double *const *x_inout, ats_solve_stats *stats) {
+  if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
+  for (ats_level *L : B->plan->levels) {
+    if (!L->built) {
+      set_error("level operator not built");
+      return ATS_ERR_INVALID_ARG;
+    }
+  }
+  return plan_run(B->plan, x_inout, stats);
+}
+
+ats_status ats_batch_destroy(ats_batch *B) {
+  if (!B) return ATS_ERR_INVALID_ARG;
+  if (B->plan) {
+    cudaSetDevice(B->plan->ctx->device);
+    cudaStreamSynchronize(B->plan->ctx->stream);
+    plan_free(B->plan);
+  }
+  delete B;
+  return ATS_OK;
+}
+
+ats_status ats_batch_run(ats_context *ctx, ats_level *const *levels, int n, double *const *x_inout,
+                         const ats_solve_opts *opts, ats_solve_stats *stats) {
+  ats_batch *B = nullptr;
+  ats_status s = ats_batch_create(ctx, levels, n, opts, &B);
+  if (s != ATS_OK) return s;
+  s = ats_batch_solve(B, x_inout, stats);
+  ats_batch_destroy(B);
+  return s;
+}
+
+ats_status ats_batch_set_profiling(ats_batch *B, int on) {
+  if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
+  B->plan->profiling = on != 0;
+  return ATS_OK;
+}
+
+ats_status ats_batch_kernel_stats(const ats_batch *B, double *op_ms, double *op_bytes, double *upd_ms,
+                                  double *upd_bytes, int *launches) {
+  if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
+  const Plan *P = B->plan;
+  if (op_ms) *op_ms = P->op_ms;
+  if (op_bytes) *op_bytes = P->op_bytes;
+  if (upd_ms) *upd_ms = P->upd_ms;
+  if (upd_bytes) *upd_bytes = P->upd_bytes;
+  if (launches) *launches = P->launches;
+  return ATS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (stated per test):
+  * operator / right-hand side: same FP64 arithmetic up to summation order,
+    relative 1e-13 per element (the coefficients are O(1e3) sums of O(1) terms);
+  * solves: both sides stop on the certified rule ||b - A x|| <= tol ||x||
+    with tol = 5e-11; the level matrix has lambda_min >= 1, so each solution is
+    within 5e-11 (relative) of the exact one and the two differ by <= 1e-10
+    relative L2 -- the benchmark spec's bound, for the FP64 and the refined mixed
+    path alike.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 5e-11
+PAR = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ats():
+    from paper_1401_1112_gb300 import ats as A
+    from paper_1401_1112_gb300 import build
+
+    build.build()
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(ats):
+    c = ats.Context(0)
+    yield c
+    c.close()
+
+
+def _faces(st):
+    return dict(face_K=st.face_K, face_E=st.face_E, face_F=st.face_F)
+
+
+def _oracle_solution(lv, st, tol=TOL):
+    S = oracle.assemble(lv, st.dt, st.K, st.E, s=st.s, src=st.src, **_faces(st))
+    x, info = oracle.pcg(S, st.E, tol=tol, stop_rule=oracle.STOP_CERTIFIED)
+    assert info["status"] == 0
+    return S, x
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6])
+def test_operator_and_rhs_match_oracle(ats, ctx, seed):
+    lv, st = W.random_amr_level(seed)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, **_faces(st))
+    S = oracle.assemble(lv, st.dt, st.K, st.E, **_faces(st))
+    b = L.rhs()
+    np.testing.assert_allclose(b, S.b, rtol=1e-13, atol=1e-13 * np.abs(S.b).max())
+    x = np.random.default_rng(seed).uniform(0.5, 1.5, lv.n_cell)
+    y = L.apply(x)
+    yr = S.matvec(x)
+    leaf = lv.leaf_cells()
+    scale = np.abs(S.val).max() * np.abs(x).max()
+    np.testing.assert_allclose(y[leaf], yr[leaf], rtol=0, atol=1e-13 * scale)
+    L.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("seed", [11, 12, 13, 14])
+def test_random_amr_levels_all_face_types(ats, ctx, prec, seed):
+    lv, st = W.random_amr_level(seed)
+    _, xr = _oracle_solution(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, **_faces(st))
+    x = st.E.copy()
+    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED,
+                          precision=ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED)
+    assert code == 0, stats
+    assert stats["err_bound"] <= TOL
+    assert _rel(x, xr) <= PAR
+    nl = ~lv.leaf_cells()
+    np.testing.assert_array_equal(x[nl], st.E[nl])  # non-leaf cells untouched
+    L.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config1_32cube_gaussian(ats, ctx, prec):
+    """32^3 unit box, K = 1, dt = 10 dx^2 / 2K, Gaussian + floor, zero-flux walls."""
+    lv, st = W.config1()
+    _, xr = _oracle_solution(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E)
+    x = st.E.copy()
+    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED,
+                          precision=ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED)
+    assert code == 0, stats
+    assert _rel(x, xr) <= PAR
+    # zero-flux walls conserve the total exactly (up to the solve tolerance)
+    assert abs(x.sum() - st.E.sum()) <= 1e-10 * st.E.sum()
+    L.close()
+
+
+def test_config1_paper_stopping_rule(ats, ctx):
+    """The paper's rule (L2 relative to r0 and L-inf relative change) at 1e-10."""
+    lv, st = W.config1()
+    S, xr = _oracle_solution(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E)
+    x = st.E.copy()
+    code, stats = L.solve(x, tol=1e-10, stop_rule=ats.ATS_STOP_PAPER, precision=ats.ATS_PREC_FP64)
+    assert code == 0, stats
+    assert stats["res_norm"] <= 1e-10 * stats["r0_norm"] * 1.0001
+    # the L2 rule alone bounds the error by ||r|| <= 1e-10 ||r0||
+    assert np.linalg.norm(x - xr) <= 1e-10 * stats["r0_norm"] + 5e-11 * np.linalg.norm(xr)
+    L.close()
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 37), (33, 1, 1), (3, 5, 7), (8, 8, 9)])
+def test_ragged_shapes_and_tails(ats, ctx, dims):
+    """1 oct, strips, oct counts that are not multiples of the 32-oct pass or
+    of the work-item tile."""
+    rng = np.random.default_rng(sum(dims))
+    lv, st = W.random_box_solve(rng, 1)
+    lv = W.box_level(*dims, 0.05, [(W.DIRICHLET, 1.0), None, (W.ROBIN, 0.3), (W.NEUMANN, 0.0), None, (W.DIRICHLET, 1.0)])
+    N, nf = lv.n_cell, lv.n_face
+    st = W.Step(dt=3.0 * 0.05 ** 2, K=np.exp(rng.standard_normal(N)), E=rng.uniform(0.5, 1.5, N),
+                face_K=np.exp(rng.standard_normal(nf)), face_E=rng.uniform(0, 2, nf), face_F=rng.uniform(-0.1, 0.1, nf))
+    _, xr = _oracle_solution(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, **_faces(st))
+    for prec, tile in ((ats.ATS_PREC_FP64, 0), (ats.ATS_PREC_MIXED, 32), (ats.ATS_PREC_MIXED, 64)):
+        x = st.E.copy()
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=prec, tile_octs=tile)
+        assert code == 0, stats
+        assert _rel(x, xr) <= PAR
+    L.close()
+
+
+def test_coupling_shift_and_source(ats, ctx):
+    """Diagonal shift s and extra source (the linearised coupling terms)."""
+    lv, st = W.random_amr_level(61)
+    rng = np.random.default_rng(61)
+    st.s = rng.uniform(0, 3, lv.n_cell)
+    st.src = rng.uniform(0, 1, lv.n_cell)
+    _, xr = _oracle_solution(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, s=st.s, src=st.src, **_faces(st))
+    for prec in (ats.ATS_PREC_FP64, ats.ATS_PREC_MIXED):
+        x = st.E.copy()
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=prec)
+        assert code == 0, stats
+        assert _rel(x, xr) <= PAR
+    L.close()
+
+
+def test_device_pointers_and_rhs_override(ats, ctx):
+    import torch
+
+    lv, st = W.random_amr_level(71)
+    S, xr = _oracle_solution(lv, st)
+    L = ats.Level(ctx, lv)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    L.build(st.dt, t(st.K), t(st.E), face_K=t(st.face_K), face_E=t(st.face_E), face_F=t(st.face_F))
+    torch.cuda.synchronize()
+    x = t(st.E.copy())
+    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED)
+    assert code == 0
+    assert _rel(x.cpu().numpy(), xr) <= PAR
+    # explicit right-hand side: 2 b gives 2 x on the leaf cells (the others
+    # keep their input value)
+    xb = t(st.E.copy())
+    code, _ = L.solve(xb, rhs=t(2 * S.b), tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED)
+    assert code == 0
+    leaf = lv.leaf_cells()
+    assert _rel(xb.cpu().numpy()[leaf], 2 * xr[leaf]) <= PAR
+    np.testing.assert_array_equal(xb.cpu().numpy()[~leaf], st.E[~leaf])
+    L.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_matches_oracle_and_is_invariant(ats, ctx, prec):
+    """A ragged batch: every solve matches the oracle, and each result is
+    bitwise the same alone and inside the batch (same work-item tiling,
+    fixed-order reductions)."""
+    rng = np.random.default_rng(77)
+    solves = [W.random_box_solve(rng, o) for o in (1, 7, 64, 100, 333, 900, 2)]
+    P = ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED
+    levels = []
+    for lv, st in solves:
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        levels.append(L)
+    xs = [st.E.copy() for _, st in solves]
+    B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, use_graph=1, check_every=8)
+    code, stats = B.solve(xs)
+    assert code == 0, stats
+    for (lv, st), x, s in zip(solves, xs, stats):
+        _, xr = _oracle_solution(lv, st)
+        assert _rel(x, xr) <= PAR, s
+    for k, ((lv, st), L) in enumerate(zip(solves, levels)):
+        x = st.E.copy()
+        code, _ = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P)
+        assert code == 0
+        np.testing.assert_array_equal(x, xs[k])
+    # run the batch a second time: identical results (deterministic)
+    xs2 = [st.E.copy() for _, st in solves]
+    B.solve(xs2)
+    for a, b in zip(xs, xs2):
+        np.testing.assert_array_equal(a, b)
+    B.close()
+    for L in levels:
+        L.close()
+
+
+def test_bad_input_and_caps(ats, ctx):
+    lv, st = W.random_amr_level(81)
+    L = ats.Level(ctx, lv)
+    K = st.K.copy()
+    K[np.nonzero(lv.leaf_cells())[0][0]] = -1.0
+    L.build(st.dt, K, st.E, **_faces(st))
+    x = st.E.copy()
+    code, _ = L.solve(x)
+    assert code == ats.ATS_ERR_BAD_INPUT
+    L.build(st.dt, st.K, st.E, **_faces(st))
+    x = st.E.copy()
+    code, stats = L.solve(x, tol=1e-14, max_iter=3)
+    assert code == ats.ATS_ERR_NOT_CONVERGED
+    assert stats["iterations"] == 3
+    L.close()
+
+
+def test_memory_budget(ats):
+    c = ats.Context(0, mem_budget_bytes=64 * 1024)
+    lv, st = W.config1()
+    with pytest.raises(ats.AtsError) as e:
+        ats.Level(c, lv)
+    assert e.value.code == ats.ATS_ERR_OVER_BUDGET
+    c.close()
