@@ -183,18 +183,23 @@ def run_ours(args, rank, world, local):
     def view(t, a, b):
         return t[int(a):int(b)]
 
-    def build_ops():
-        for k, (lv, st) in enumerate(solves):
-            fa, fb = foffs[k], foffs[k + 1]
-            has_f = fb > fa
-            levels[k].build(st.dt, view(K_d, offs[k], offs[k + 1]), view(E_d, offs[k], offs[k + 1]),
-                            face_E=view(fE_d, fa, fb) if has_f else None,
-                            face_F=view(fF_d, fa, fb) if has_f else None)
+    def coef_kwargs(k):
+        st = solves[k][1]
+        fa, fb = foffs[k], foffs[k + 1]
+        has_f = fb > fa
+        return dict(dt=st.dt, K=view(K_d, offs[k], offs[k + 1]), E_old=view(E_d, offs[k], offs[k + 1]),
+                    face_E=view(fE_d, fa, fb) if has_f else None, face_F=view(fF_d, fa, fb) if has_f else None)
 
     xs = [view(x_d, offs[k], offs[k + 1]) for k in range(n)]
-    build_ops()
+    for k in range(n):  # per-level entry point once (the plan needs built operators)
+        levels[k].build(**coef_kwargs(k))
     batch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_RESIDUAL, precision=ats.ATS_PREC_MIXED,
-                      use_graph=1, check_every=args.check_every, mem=ats.ATS_MEM_DEVICE)
+                      use_graph=1, check_every=args.check_every, mem=ats.ATS_MEM_DEVICE, tile_octs=args.tile,
+                      inner_rtol=args.inner_rtol)
+    coefs = batch.prepare_coefs([coef_kwargs(k) for k in range(n)])
+
+    def build_ops():
+        batch.build_operators(coefs)  # all levels' coefficients and right-hand sides, one launch
 
     def step():
         x_d.copy_(E_d)          # initial guess x0 = E^n
@@ -223,17 +228,15 @@ def run_ours(args, rank, world, local):
     sampler.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    op_ms = upd_ms = op_bytes = upd_bytes = 0.0
+    acc = {"op_ms": 0.0, "op_bytes": 0.0, "ref_ms": 0.0, "ref_bytes": 0.0, "upd_ms": 0.0, "upd_bytes": 0.0}
     launches = 0
     ev0.record(stream)
     for _ in range(args.steps):
         stats = step()
         ks = batch.kernel_stats()
-        op_ms += ks["op_ms"]
-        upd_ms += ks["upd_ms"]
-        op_bytes += ks["op_bytes"]
-        upd_bytes += ks["upd_bytes"]
-        launches += ks["launches"] + n + 2  # ticks + operator builds + init/final
+        for key in acc:
+            acc[key] += ks[key]
+        launches += ks["launches"] + 5  # tick kernels + operator build (2) + init, final, flag gather
     ev1.record(stream)
     barrier()
     clocks = sampler.stop()
@@ -248,20 +251,20 @@ def run_ours(args, rank, world, local):
     refs = [s["refinements"] for s in stats]
     bounds = [s["res_norm"] / s["r0_norm"] if s["r0_norm"] > 0 else 0.0 for s in stats]
 
-    # dominant kernel roofline
+    # dominant kernel roofline (algorithmic bytes / event-timed duration)
     peak, peak_kind = _peaks()
-    if op_ms >= upd_ms:
-        dom, dms, dbytes = "k_op<float>", op_ms, op_bytes
-    else:
-        dom, dms, dbytes = "k_upd<float>", upd_ms, upd_bytes
+    kern = {"k_op<float>": ("op_ms", "op_bytes"), "k_ref<float>": ("ref_ms", "ref_bytes"),
+            "k_upd<float>": ("upd_ms", "upd_bytes")}
+    dom = max(kern, key=lambda k: acc[kern[k][0]])
+    dms, dbytes = acc[kern[dom][0]], acc[kern[dom][1]]
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
-    tr = _traffic_for(dom)
     roofline = {
         "bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
         "frac": round(achieved / peak, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-        "traffic": tr, "op_ms": round(op_ms, 3), "upd_ms": round(upd_ms, 3),
-        "op_GBps": round(op_bytes / (op_ms / 1e3) / 1e9, 1) if op_ms else None,
-        "upd_GBps": round(upd_bytes / (upd_ms / 1e3) / 1e9, 1) if upd_ms else None,
+        "traffic": _traffic_for(dom),
+        "per_kernel": {k: {"ms": round(acc[a], 3),
+                           "GBps": round(acc[b] / (acc[a] / 1e3) / 1e9, 1) if acc[a] else None}
+                       for k, (a, b) in kern.items()},
     }
 
     # end to end through the public API with host buffers (pinned)
@@ -277,11 +280,13 @@ def run_ours(args, rank, world, local):
                            use_graph=1, check_every=args.check_every, mem=ats.ATS_MEM_HOST)
         hx = [xn[offs[k]:offs[k + 1]] for k in range(n)]
 
+        hcoefs = hbatch.prepare_coefs([
+            dict(dt=solves[k][1].dt, K=Kn[offs[k]:offs[k + 1]], E_old=En[offs[k]:offs[k + 1]],
+                 face_E=fEn[foffs[k]:foffs[k + 1]] if foffs[k + 1] > foffs[k] else None,
+                 face_F=fFn[foffs[k]:foffs[k + 1]] if foffs[k + 1] > foffs[k] else None) for k in range(n)])
+
         def e2e_step():
-            for k, (lv, st) in enumerate(solves):
-                fa, fb = foffs[k], foffs[k + 1]
-                levels[k].build(st.dt, Kn[offs[k]:offs[k + 1]], En[offs[k]:offs[k + 1]],
-                                face_E=fEn[fa:fb] if fb > fa else None, face_F=fFn[fa:fb] if fb > fa else None)
+            hbatch.build_operators(hcoefs)
             np.copyto(xn, En)
             code, _ = hbatch.solve(hx)
             if code != 0:
@@ -425,6 +430,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--solves", type=int, default=512)
     ap.add_argument("--check-every", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0, help="octs per work item (0 = library default)")
+    ap.add_argument("--inner-rtol", type=float, default=0.0, help="mixed inner reduction (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-solves-per-step", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")

@@ -121,7 +121,7 @@ typedef struct {
   int precision;     /* ATS_PREC_*                                            */
   int max_iter;      /* cap on CG iterations per solve (0 = 20000)            */
   int max_refine;    /* cap on FP64 residual passes (0 = 40)                 */
-  double inner_rtol; /* mixed: residual reduction per inner FP32 solve (0 = 1e-4) */
+  double inner_rtol; /* mixed: residual reduction per inner FP32 solve (0 = 1e-5) */
   int tile_octs;     /* octs per work item, multiple of 32 (0 = autotuned)   */
   int check_every;   /* ticks between host convergence polls (0 = 16)       */
   int use_graph;     /* 1 = capture the poll interval as a CUDA graph        */
@@ -187,14 +187,27 @@ ats_status ats_batch_create(ats_context *ctx, ats_level *const *levels, int n,
  * or NULL.  Returns the first error status of any solve, else ATS_OK. */
 ats_status ats_batch_solve(ats_batch *batch, double *const *x_inout, ats_solve_stats *stats);
 ats_status ats_batch_destroy(ats_batch *batch);
+/* Build the operators of every level of the batch in one kernel launch
+ * (same computation as ats_level_build_operator, Sect. 3.1-3.2): coefs[k]
+ * describes level k.  Errors as ats_level_build_operator; ATS_ERR_BAD_INPUT
+ * is reported per solve by the next ats_batch_solve. */
+ats_status ats_batch_build_operators(ats_batch *batch, const ats_coef_desc *coefs);
 /* One-shot form: create, solve and destroy. */
 ats_status ats_batch_run(ats_context *ctx, ats_level *const *levels, int n, double *const *x_inout,
                          const ats_solve_opts *opts, ats_solve_stats *stats);
-/* Kernel timing of the last ats_batch_solve (CUDA events around each launch
- * when profiling is on): dominant-kernel time and its algorithmic bytes. */
+/* Kernel timing of the last ats_batch_solve, when profiling is on: CUDA
+ * events around every tick kernel (also inside the replayed graphs), summed
+ * per kernel, with the algorithmic bytes each moved (compulsory traffic of
+ * the vectors and coefficients the kernel must read and write once). */
+typedef struct {
+  double op_ms, op_bytes;    /* CG op kernel: p = z + beta p, q = A p, p.q        */
+  double ref_ms, ref_bytes;  /* FP64 refinement residual kernel                  */
+  double upd_ms, upd_bytes;  /* update kernel: e, z, dots; x += e after refinement */
+  int launches;              /* tick-kernel launches                              */
+  int ticks;                 /* ticks enqueued                                    */
+} ats_kernel_stats;
 ats_status ats_batch_set_profiling(ats_batch *batch, int on);
-ats_status ats_batch_kernel_stats(const ats_batch *batch, double *op_ms, double *op_bytes,
-                                  double *upd_ms, double *upd_bytes, int *launches);
+ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out);
 
 /* ---- misc ------------------------------------------------------------------ */
 void ats_default_opts(ats_solve_opts *opts);

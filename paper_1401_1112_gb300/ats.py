@@ -66,6 +66,14 @@ class ats_solve_opts(ctypes.Structure):
     ]
 
 
+class ats_kernel_stats(ctypes.Structure):
+    _fields_ = [
+        ("op_ms", ctypes.c_double), ("op_bytes", ctypes.c_double), ("ref_ms", ctypes.c_double),
+        ("ref_bytes", ctypes.c_double), ("upd_ms", ctypes.c_double), ("upd_bytes", ctypes.c_double),
+        ("launches", ctypes.c_int), ("ticks", ctypes.c_int),
+    ]
+
+
 class ats_solve_stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
@@ -94,8 +102,9 @@ _SIGS = [
     ("ats_batch_solve", ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(ats_solve_stats)]),
     ("ats_batch_destroy", ctypes.c_int, [P]),
     ("ats_batch_run", ctypes.c_int, [P, ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(ats_solve_opts), ctypes.POINTER(ats_solve_stats)]),
+    ("ats_batch_build_operators", ctypes.c_int, [P, ctypes.POINTER(ats_coef_desc)]),
     ("ats_batch_set_profiling", ctypes.c_int, [P, ctypes.c_int]),
-    ("ats_batch_kernel_stats", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    ("ats_batch_kernel_stats", ctypes.c_int, [P, ctypes.POINTER(ats_kernel_stats)]),
     ("ats_default_opts", None, [ctypes.POINTER(ats_solve_opts)]),
     ("ats_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("ats_last_error", ctypes.c_char_p, []),
@@ -248,6 +257,23 @@ def ats_level_size(lvl):
     return a.value, b.value, c.value
 
 
+def coef_desc(dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None, keep=None):
+    """Fill an ats_coef_desc (``keep`` collects converted host arrays that
+    must outlive the call)."""
+    keep = [] if keep is None else keep
+    c = ats_coef_desc()
+    c.dt = float(dt)
+    c.mem = _mem_of(K, E_old, s, src, face_K, face_E, face_F)
+    c.K = _ptr(K, keep=keep)
+    c.E_old = _ptr(E_old, keep=keep)
+    c.s = _ptr(s, keep=keep)
+    c.src = _ptr(src, keep=keep)
+    c.face_K = _ptr(face_K, keep=keep)
+    c.face_E = _ptr(face_E, keep=keep)
+    c.face_F = _ptr(face_F, keep=keep)
+    return c
+
+
 def ats_level_build_operator(lvl, dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None):
     keep = []
     c = ats_coef_desc()
@@ -314,16 +340,19 @@ def ats_batch_run(ctx, levels: Sequence, xs: Sequence, opts: Optional[ats_solve_
     return code, [s.as_dict() for s in st]
 
 
+def ats_batch_build_operators(batch, coefs):
+    """coefs: a ctypes array of ats_coef_desc (see ``coef_desc``), one per level."""
+    return _check(lib().ats_batch_build_operators(batch, coefs), "ats_batch_build_operators")
+
+
 def ats_batch_set_profiling(batch, on: bool):
     return _check(lib().ats_batch_set_profiling(batch, 1 if on else 0), "ats_batch_set_profiling")
 
 
 def ats_batch_kernel_stats(batch):
-    v = [ctypes.c_double() for _ in range(4)]
-    n = ctypes.c_int()
-    _check(lib().ats_batch_kernel_stats(batch, *[ctypes.byref(x) for x in v], ctypes.byref(n)), "ats_batch_kernel_stats")
-    return {"op_ms": v[0].value, "op_bytes": v[1].value, "upd_ms": v[2].value, "upd_bytes": v[3].value,
-            "launches": n.value}
+    k = ats_kernel_stats()
+    _check(lib().ats_batch_kernel_stats(batch, ctypes.byref(k)), "ats_batch_kernel_stats")
+    return {name: getattr(k, name) for name, _ in k._fields_}
 
 
 def ats_default_opts() -> ats_solve_opts:
@@ -415,6 +444,16 @@ class Batch:
 
     def solve(self, xs):
         return ats_batch_solve(self.handle, xs)
+
+    def prepare_coefs(self, per_level):
+        """per_level: list of dicts of ``coef_desc`` keyword arguments.  The
+        returned object can be passed to ``build_operators`` repeatedly."""
+        keep = []
+        arr = (ats_coef_desc * len(per_level))(*[coef_desc(keep=keep, **kw) for kw in per_level])
+        return (arr, keep)
+
+    def build_operators(self, prepared):
+        return ats_batch_build_operators(self.handle, prepared[0])
 
     def set_profiling(self, on=True):
         ats_batch_set_profiling(self.handle, on)

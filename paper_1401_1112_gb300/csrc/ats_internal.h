@@ -11,8 +11,7 @@
 
 namespace ats {
 
-constexpr int kThreads = 256;          // threads per CTA of the stencil kernels
-constexpr int kOctsPerPass = kThreads / 8;
+constexpr int kThreads = 128;          // threads per CTA of the tick kernels (one oct each)
 constexpr int kNumPartials = 4;        // FP64 partial sums per work item
 
 // Phases of the per-solve state machine advanced by each device "tick"
@@ -82,6 +81,16 @@ struct WorkItem {
   int32_t pad;
 };
 
+// Active work lists, one per (parity, phase): k_op walks the CG-phase list,
+// k_ref the refinement-phase list and k_upd both; the last CTA of each solve
+// that stays active appends that solve's items to the next parity's list of
+// its new phase; the last CTA of k_upd flips the parity.
+struct TickCtl {
+  int32_t parity;
+  int32_t count[2][2];  // [parity][phase]
+  int32_t cta_done;
+};
+
 // ---- launchers (kernels.cu) ----
 struct CoefArgs {
   int64_t n_oct;
@@ -108,14 +117,19 @@ struct CoefArgs {
   int *err_flag;
 };
 cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st);
+// One launch for many levels (args, cell_off: device arrays, n levels) after
+// zeroing the levels' error flags (flags: device array of device pointers).
+cudaError_t launch_coef_build_batch(const CoefArgs *args, const int64_t *cell_off, int n, int64_t total_cells,
+                                    int *const *flags, cudaStream_t st);
+cudaError_t launch_gather_flags(const int *const *flags, int n, int *out, cudaStream_t st);
 
-// One tick = k_op + k_upd over the work list.  Events (may be null) are
-// recorded before k_op, between the kernels and after k_upd; `capture` says
-// whether the stream is being captured into a graph.
+// One tick = k_op (CG items) + k_ref (refinement items) + k_upd (all).
+// ev (null, or 4 events) is recorded before k_op, between the kernels and
+// after k_upd; `capture` says whether the stream is being captured.
 cudaError_t launch_tick(bool fp64, bool paper, const SolveDev *solves, SolveScalars *sc,
-                        const WorkItem *items, int n_items, double *partials, int *n_active,
-                        int grid, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
-                        cudaEvent_t ev2, bool capture, unsigned long long *cells_counter);
+                        const WorkItem *items, int32_t *lists, int n_items, TickCtl *ctl,
+                        double *partials, int *n_active, int grid, cudaStream_t st,
+                        cudaEvent_t *ev, bool capture, unsigned long long *cells_counter);
 
 // Start of a solve: e = 0 on every cell of every item, and x64 = src[solve]
 // where src (device array of device pointers) is non-null for that solve.

@@ -10,12 +10,16 @@
 //                iterative refinement (k_op) followed by x += e (k_upd).
 //
 // Layout: a level is an array of octs; cell c = ix + 2 iy + 4 iz of oct o is
-// element 8 o + c.  A CTA of 256 threads covers 32 octs per pass, one cell
-// per thread, so the eight cells of an oct are eight consecutive lanes and
-// the three in-oct neighbours of a cell are lanes c^1, c^2, c^4 (warp
-// shuffles).  The three out-of-oct neighbours come from the six-entry oct
-// neighbour table.  K < 0 marks a cell that is not an unknown of the level
-// (refined cell); its vectors are kept at zero so it drops out of the stencil.
+// element 8 o + c.  One thread owns one oct: its eight cells of every vector
+// come in as two float4 (four double2) loads, the twelve in-oct faces are
+// computed in registers, and the three out-of-oct faces of each cell come
+// from the six face-neighbour octs (index table), of which only the four
+// facing cells are loaded.  K < 0 marks a cell that is not an unknown of the
+// level (refined cell); its vectors are kept at zero so it drops out.
+//
+// Work: a solve is split into work items (runs of octs); the tick kernels
+// walk a device-side list of the items of the solves still running, which
+// the update kernel rebuilds as solves finish.
 //
 // The operator is matrix-free: an interior face contributes
 // C = dt/dx^2 (K_i + K_j)/2 = h (K_i + K_j); the diagonal is
@@ -37,6 +41,13 @@ namespace ats {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// resident CTAs per SM the tick kernels are compiled for (caps registers):
+// the FP32 CG path keeps its loads in flight with 5 CTAs of 128 threads; the
+// FP64 bulk path needs twice the registers per value.
+template <typename T>
+struct MinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? 5 : 3;
+};
 
 // FP64-quality dot-product accumulation.  FP32 bulk: each product is split
 // exactly (TwoProduct via FMA) and summed with TwoSum (Ogita, Rump & Oishi
@@ -66,7 +77,8 @@ struct Acc<float> {
 };
 
 // Block reduction of kNumPartials doubles (slot 2 optionally a max), fixed
-// order.  Result valid in thread 0.
+// order.  Result valid in thread 0.  Used where the partials are FP64 values
+// (refinement passes, the FP64 bulk path, the per-solve reduction).
 template <bool kSlot2Max>
 __device__ __forceinline__ void block_reduce(double (&v)[kNumPartials],
                                              double (*red)[kNumPartials]) {
@@ -91,6 +103,58 @@ __device__ __forceinline__ void block_reduce(double (&v)[kNumPartials],
       for (int w = 1; w < kThreads / 32; ++w) a = (kSlot2Max && k == 2) ? fmax(a, red[w][k]) : a + red[w][k];
       v[k] = a;
     }
+  }
+  __syncthreads();
+}
+
+// Warp reduction of a compensated FP32 accumulator: the (hi, lo) pairs are
+// combined with TwoSum (error-free), so no FP64 instruction is issued per
+// lane; lane 0 ends with the warp's pair.
+__device__ __forceinline__ void warp_reduce_acc(Acc<float> &a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float s2 = __shfl_down_sync(kFull, a.s, off);
+    const float c2 = __shfl_down_sync(kFull, a.c, off);
+    const float t = __fadd_rn(a.s, s2);
+    const float zz = __fsub_rn(t, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, zz)), __fsub_rn(s2, zz));
+    a.s = t;
+    a.c = __fadd_rn(a.c, __fadd_rn(c2, err));
+  }
+}
+__device__ __forceinline__ void warp_reduce_acc(Acc<double> &a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a.s += __shfl_down_sync(kFull, a.s, off);
+}
+
+// Block reduction of up to two dot accumulators and one FP64 max into the
+// kNumPartials doubles of thread 0 (slots 0, 1 and 2; slot 3 = 0).
+template <typename T>
+__device__ __forceinline__ void block_reduce_acc(Acc<T> &a0, Acc<T> &a1, double mx,
+                                                 double (&v)[kNumPartials],
+                                                 double (*red)[kNumPartials]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_reduce_acc(a0);
+  warp_reduce_acc(a1);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(kFull, mx, off));
+  if (lane == 0) {
+    red[warp][0] = a0.get();
+    red[warp][1] = a1.get();
+    red[warp][2] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = red[0][0], s1 = red[0][1], m = red[0][2];
+    for (int w = 1; w < kThreads / 32; ++w) {
+      s0 += red[w][0];
+      s1 += red[w][1];
+      m = fmax(m, red[w][2]);
+    }
+    v[0] = s0;
+    v[1] = s1;
+    v[2] = m;
+    v[3] = 0.0;
   }
   __syncthreads();
 }
@@ -130,360 +194,545 @@ __device__ __forceinline__ bool publish_item(double (&v)[kNumPartials], double *
 }
 
 // ---------------------------------------------------------------------------
-// one pass (32 octs) of each phase; the caller loops over an item's passes
+// oct-wise vector I/O (one thread owns the eight cells of one oct)
 // ---------------------------------------------------------------------------
 
-struct CellCtx {
-  int o;       // oct index (may be >= oct_end on a ragged tail)
-  int c;       // cell in oct
-  bool valid;  // o < oct_end
-  int64_t i;   // 8 o + c
-};
-
-__device__ __forceinline__ CellCtx cell_ctx(int ob, int oct_end) {
-  CellCtx x;
-  x.o = ob + ((int)threadIdx.x >> 3);
-  x.c = (int)threadIdx.x & 7;
-  x.valid = x.o < oct_end;
-  x.i = (int64_t)x.o * 8 + x.c;
-  return x;
+__device__ __forceinline__ void ld8_ro(const float *__restrict__ p, float (&v)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void ld8_ro(const double *__restrict__ p, double (&v)[8]) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  v[4] = c.x; v[5] = c.y; v[6] = d.x; v[7] = d.y;
+}
+__device__ __forceinline__ void ld8_rw(const float *p, float (&v)[8]) {
+  const float4 a = reinterpret_cast<const float4 *>(p)[0];
+  const float4 b = reinterpret_cast<const float4 *>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void ld8_rw(const double *p, double (&v)[8]) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  const double2 a = q[0], b = q[1], c = q[2], d = q[3];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  v[4] = c.x; v[5] = c.y; v[6] = d.x; v[7] = d.y;
+}
+__device__ __forceinline__ void st8(float *p, const float (&v)[8]) {
+  reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void st8(double *p, const double (&v)[8]) {
+  double2 *q = reinterpret_cast<double2 *>(p);
+  q[0] = make_double2(v[0], v[1]);
+  q[1] = make_double2(v[2], v[3]);
+  q[2] = make_double2(v[4], v[5]);
+  q[3] = make_double2(v[6], v[7]);
 }
 
-// The out-of-oct neighbour oct along each axis (the side this cell touches).
-__device__ __forceinline__ void load_nbr(const int32_t *__restrict__ nbr, const CellCtx &x,
-                                         int (&nb)[3]) {
+// Load the four cells of a neighbour oct that face this oct: the cells whose
+// bit A equals NB (A = axis, NB = 1 - side of this oct's face).  v[c] is set
+// for exactly those cells c.
+template <int A, int NB>
+__device__ __forceinline__ void ld_face(const float *__restrict__ p, float (&v)[8]) {
+  if (A == 0) {
+    ld8_ro(p, v);
+  } else if (A == 1) {
+    const float2 a = __ldg(reinterpret_cast<const float2 *>(p + 2 * NB));
+    const float2 b = __ldg(reinterpret_cast<const float2 *>(p + 4 + 2 * NB));
+    v[2 * NB] = a.x; v[2 * NB + 1] = a.y; v[4 + 2 * NB] = b.x; v[5 + 2 * NB] = b.y;
+  } else {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p + 4 * NB));
+    v[4 * NB] = a.x; v[4 * NB + 1] = a.y; v[4 * NB + 2] = a.z; v[4 * NB + 3] = a.w;
+  }
+}
+template <int A, int NB>
+__device__ __forceinline__ void ld_face(const double *__restrict__ p, double (&v)[8]) {
+  if (A == 0) {
+    ld8_ro(p, v);
+  } else if (A == 1) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p + 2 * NB));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 4 + 2 * NB));
+    v[2 * NB] = a.x; v[2 * NB + 1] = a.y; v[4 + 2 * NB] = b.x; v[5 + 2 * NB] = b.y;
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p + 4 * NB));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 4 * NB + 2));
+    v[4 * NB] = a.x; v[4 * NB + 1] = a.y; v[4 * NB + 2] = b.x; v[4 * NB + 3] = b.y;
+  }
+}
+
+__device__ __forceinline__ void load_nbr6(const int32_t *__restrict__ nbr, int o, int (&nb)[6]) {
+  const int2 *q = reinterpret_cast<const int2 *>(nbr + 6 * o);
+  const int2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+  nb[0] = a.x; nb[1] = a.y; nb[2] = b.x; nb[3] = b.y; nb[4] = c.x; nb[5] = c.y;
+}
+
+// The three in-oct faces of every cell, each cell pair once:
+// dsum += C, off += C * v(neighbour), with C = h (K_i + K_j) between leaves.
+template <typename T>
+__device__ __forceinline__ void in_oct_faces(const T (&K)[8], const T (&v)[8], T h, T (&dsum)[8],
+                                             T (&off)[8]) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-    nb[a] = x.valid ? __ldg(nbr + (int64_t)x.o * 6 + 2 * a + ((x.c >> a) & 1)) : -1;
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c & (1 << a)) continue;
+      const int d = c | (1 << a);
+      const T C = (K[c] >= T(0) && K[d] >= T(0)) ? h * (K[c] + K[d]) : T(0);
+      dsum[c] += C;
+      dsum[d] += C;
+      off[c] += C * v[d];
+      off[d] += C * v[c];
+    }
+  }
 }
 
-// k_op, CG phase: p_new = z + beta p_old (first: p_new = z), q = (I + dt A) p_new,
+// ---------------------------------------------------------------------------
+// per-oct work of each phase
+// ---------------------------------------------------------------------------
+
+// k_op, CG phase, out-of-oct face DIR: p_new of the neighbour's facing cells
+// is formed on the fly from its z and p_old.
+template <int DIR, typename T>
+__device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T *__restrict__ z,
+                                        const T *__restrict__ pold, bool first, T beta, T h,
+                                        const T (&K)[8], T (&dsum)[8], T (&off)[8]) {
+  constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
+  if (n < 0) return;
+  T Kn[8], Zn[8], Pn[8];
+  ld_face<A, NB>(KT + 8 * n, Kn);
+  ld_face<A, NB>(z + 8 * n, Zn);
+  if (!first) ld_face<A, NB>(pold + 8 * n, Pn);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (((c >> A) & 1) != S) continue;
+    const int j = c ^ (1 << A);
+    const T pj = first ? Zn[j] : fma(beta, Pn[j], Zn[j]);
+    const T C = (Kn[j] >= T(0)) ? h * (K[c] + Kn[j]) : T(0);
+    dsum[c] += C;
+    off[c] += C * pj;
+  }
+}
+
+// k_op, CG phase: p_new = z + beta p_old (first: z), q = (I + dt A) p_new,
 // partial p_new . q.
 template <typename T>
-__device__ __forceinline__ void op_inner_pass(const SolveDev &sd, int ob, int oct_end, T h, T beta,
-                                              bool first, const T *__restrict__ pold,
-                                              T *__restrict__ pnew, Acc<T> &pq) {
+__device__ __forceinline__ void op_inner_oct(const SolveDev &sd, int o, T h, T beta, bool first,
+                                             const T *__restrict__ pold, T *__restrict__ pnew,
+                                             Acc<T> &pq) {
   const T *__restrict__ KT = (const T *)sd.KT;
   const T *__restrict__ z = (const T *)sd.z;
-  const CellCtx x = cell_ctx(ob, oct_end);
-  int nb[3];
-  load_nbr(sd.nbr, x, nb);
-  T kv = T(-1), pv = T(0);
-  int rec = -1;
-  if (x.valid) {
-    kv = KT[x.i];
-    const T zv = z[x.i];
-    pv = first ? zv : zv + beta * pold[x.i];
-    rec = __ldg(sd.xrec + x.o);
-  }
-  // out-of-oct neighbours: issue all loads first
-  T kj[3], pj[3];
+  int nb[6];
+  load_nbr6(sd.nbr, o, nb);
+  const int rec = __ldg(sd.xrec + o);
+  T K[8], pv[8];
+  ld8_ro(KT + 8 * o, K);
+  ld8_ro(z + 8 * o, pv);
+  if (!first) {
+    T pp[8];
+    ld8_ro(pold + 8 * o, pp);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    kj[a] = T(-1);
-    pj[a] = T(0);
-    if (nb[a] >= 0) {
-      const int64_t j = (int64_t)nb[a] * 8 + (x.c ^ (1 << a));
-      kj[a] = KT[j];
-      const T zj = z[j];
-      pj[a] = first ? zj : zj + beta * pold[j];
-    }
+    for (int c = 0; c < 8; ++c) pv[c] = fma(beta, pp[c], pv[c]);
   }
-  T dsum = T(0), off = T(0);
+  T dsum[8], off[8];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const T pn = __shfl_xor_sync(kFull, pv, 1 << a);
-    const T kn = __shfl_xor_sync(kFull, kv, 1 << a);
-    if (kn >= T(0)) {
-      const T C = h * (kv + kn);
-      dsum += C;
-      off += C * pn;
-    }
-    if (kj[a] >= T(0)) {
-      const T C = h * (kv + kj[a]);
-      dsum += C;
-      off += C * pj[a];
-    }
+  for (int c = 0; c < 8; ++c) dsum[c] = off[c] = T(0);
+  in_oct_faces(K, pv, h, dsum, off);
+  op_face<0>(nb[0], KT, z, pold, first, beta, h, K, dsum, off);
+  op_face<1>(nb[1], KT, z, pold, first, beta, h, K, dsum, off);
+  op_face<2>(nb[2], KT, z, pold, first, beta, h, K, dsum, off);
+  op_face<3>(nb[3], KT, z, pold, first, beta, h, K, dsum, off);
+  op_face<4>(nb[4], KT, z, pold, first, beta, h, K, dsum, off);
+  op_face<5>(nb[5], KT, z, pold, first, beta, h, K, dsum, off);
+  T xd[8];
+  if (rec >= 0) {
+    ld8_ro((const T *)sd.xdT + 8 * rec, xd);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xd[c] = T(0);
   }
-  if (x.valid) {
-    if (kv >= T(0)) {
-      const T xd = rec >= 0 ? ((const T *)sd.xdT)[(int64_t)rec * 8 + x.c] : T(0);
-      const T d = T(1) + xd + dsum;
-      const T q = d * pv - off;
-      pnew[x.i] = pv;
-      pq.add(pv, q);
-    } else {
-      pnew[x.i] = T(0);
-    }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const T d = T(1) + xd[c] + dsum[c];
+    const T q = d * pv[c] - off[c];
+    if (K[c] >= T(0)) pq.add(pv[c], q);
+  }
+  st8(pnew + 8 * o, pv);  // non-leaf cells carry z = p = 0
+}
+
+// k_upd, CG phase, out-of-oct face DIR: neighbour p and K.
+template <int DIR, typename T>
+__device__ __forceinline__ void upd_face(int n, const T *__restrict__ KT, const T *__restrict__ p, T h,
+                                         const T (&K)[8], T (&dsum)[8], T (&off)[8]) {
+  constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
+  if (n < 0) return;
+  T Kn[8], Pn[8];
+  ld_face<A, NB>(KT + 8 * n, Kn);
+  ld_face<A, NB>(p + 8 * n, Pn);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (((c >> A) & 1) != S) continue;
+    const int j = c ^ (1 << A);
+    const T C = (Kn[j] >= T(0)) ? h * (K[c] + Kn[j]) : T(0);
+    dsum[c] += C;
+    off[c] += C * Pn[j];
   }
 }
 
 // k_upd, CG phase: q = (I + dt A) p, r = D z - alpha q, z = r / D, e += alpha p,
 // partials r.z, r.r (and the max relative change for the paper rule).
 template <typename T, bool kPaper>
-__device__ __forceinline__ void upd_inner_pass(const SolveDev &sd, int ob, int oct_end, T h, T alpha,
-                                               const T *__restrict__ p, Acc<T> &rz, Acc<T> &rr,
-                                               double &maxchg) {
+__device__ __forceinline__ void upd_inner_oct(const SolveDev &sd, int o, T h, T alpha,
+                                              const T *__restrict__ p, Acc<T> &rz, Acc<T> &rr,
+                                              double &maxchg) {
   const T *__restrict__ KT = (const T *)sd.KT;
-  T *__restrict__ z = (T *)sd.z;
-  T *__restrict__ e = (T *)sd.e;
-  const CellCtx x = cell_ctx(ob, oct_end);
-  int nb[3];
-  load_nbr(sd.nbr, x, nb);
-  T kv = T(-1), pv = T(0);
-  int rec = -1;
-  if (x.valid) {
-    kv = KT[x.i];
-    pv = p[x.i];
-    rec = __ldg(sd.xrec + x.o);
-  }
-  T kj[3], pj[3];
+  T *z = (T *)sd.z;
+  T *e = (T *)sd.e;
+  int nb[6];
+  load_nbr6(sd.nbr, o, nb);
+  const int rec = __ldg(sd.xrec + o);
+  T K[8], pv[8], zv[8], ev[8];
+  ld8_ro(KT + 8 * o, K);
+  ld8_ro(p + 8 * o, pv);
+  ld8_rw(z + 8 * o, zv);
+  ld8_rw(e + 8 * o, ev);
+  T dsum[8], off[8];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    kj[a] = T(-1);
-    pj[a] = T(0);
-    if (nb[a] >= 0) {
-      const int64_t j = (int64_t)nb[a] * 8 + (x.c ^ (1 << a));
-      kj[a] = KT[j];
-      pj[a] = p[j];
-    }
-  }
-  T dsum = T(0), off = T(0);
+  for (int c = 0; c < 8; ++c) dsum[c] = off[c] = T(0);
+  in_oct_faces(K, pv, h, dsum, off);
+  upd_face<0>(nb[0], KT, p, h, K, dsum, off);
+  upd_face<1>(nb[1], KT, p, h, K, dsum, off);
+  upd_face<2>(nb[2], KT, p, h, K, dsum, off);
+  upd_face<3>(nb[3], KT, p, h, K, dsum, off);
+  upd_face<4>(nb[4], KT, p, h, K, dsum, off);
+  upd_face<5>(nb[5], KT, p, h, K, dsum, off);
+  T xd[8];
+  if (rec >= 0) {
+    ld8_ro((const T *)sd.xdT + 8 * rec, xd);
+  } else {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const T pn = __shfl_xor_sync(kFull, pv, 1 << a);
-    const T kn = __shfl_xor_sync(kFull, kv, 1 << a);
-    if (kn >= T(0)) {
-      const T C = h * (kv + kn);
-      dsum += C;
-      off += C * pn;
-    }
-    if (kj[a] >= T(0)) {
-      const T C = h * (kv + kj[a]);
-      dsum += C;
-      off += C * pj[a];
-    }
+    for (int c = 0; c < 8; ++c) xd[c] = T(0);
   }
-  if (x.valid && kv >= T(0)) {
-    const T xd = rec >= 0 ? ((const T *)sd.xdT)[(int64_t)rec * 8 + x.c] : T(0);
-    const T d = T(1) + xd + dsum;
-    const T q = d * pv - off;
-    const T zv = z[x.i];
-    const T r = d * zv - alpha * q;
+  double xo[8];
+  if (kPaper) ld8_rw(sd.x64 + 8 * o, xo);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const bool leaf = K[c] >= T(0);
+    const T d = T(1) + xd[c] + dsum[c];
+    const T q = d * pv[c] - off[c];
+    const T r = d * zv[c] - alpha * q;
     const T zn = r / d;
-    const T ev = e[x.i];
-    const T step = alpha * pv;
-    e[x.i] = ev + step;
-    z[x.i] = zn;
-    rz.add(r, zn);
-    rr.add(r, r);
-    if (kPaper) {
-      const double xv = sd.x64[x.i] + (double)ev;
-      const double chg = fabs((double)step) / fabs(xv);
-      maxchg = fmax(maxchg, chg);
+    const T step = alpha * pv[c];
+    if (leaf) {
+      rz.add(r, zn);
+      rr.add(r, r);
+      if (kPaper) maxchg = fmax(maxchg, fabs((double)step) / fabs(xo[c] + (double)ev[c]));
+    }
+    zv[c] = leaf ? zn : T(0);
+    ev[c] = leaf ? ev[c] + step : T(0);
+  }
+  st8(z + 8 * o, zv);
+  st8(e + 8 * o, ev);
+}
+
+// k_op, refinement phase, out-of-oct face DIR (FP64 flux sums; bulk-precision
+// diagonal for the preconditioner).
+template <int DIR, typename T>
+__device__ __forceinline__ void ref_face(int n, const SolveDev &sd, const T *__restrict__ e,
+                                         const T *__restrict__ KT, T hT, const double (&K)[8],
+                                         const T (&KTo)[8], const double (&xv)[8], double (&acc)[8],
+                                         T (&dsT)[8]) {
+  constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
+  if (n < 0) return;
+  double Kn[8], Xn[8];
+  T En[8], KTn[8];
+  ld_face<A, NB>(sd.K64 + 8 * n, Kn);
+  ld_face<A, NB>(sd.x64 + 8 * n, Xn);
+  ld_face<A, NB>(e + 8 * n, En);
+  if (sizeof(T) != sizeof(double)) ld_face<A, NB>(KT + 8 * n, KTn);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (((c >> A) & 1) != S) continue;
+    const int j = c ^ (1 << A);
+    if (Kn[j] >= 0.0) {
+      const double xn = Xn[j] + (double)En[j];
+      acc[c] = fma(K[c] + Kn[j], xv[c] - xn, acc[c]);
+      if (sizeof(T) != sizeof(double)) dsT[c] += hT * (KTo[c] + KTn[j]);
+      else dsT[c] += (T)(K[c] + Kn[j]);
     }
   }
 }
 
 // k_op, refinement phase: x' = x + e, r = b - (I + dt A) x' in FP64 with the
-// FP64 K, xd and b; z = r / D_T in the bulk precision; partials r.r, x'.x', r.z.
+// FP64 K, xd and b, written as r = b - (1 + xd) x' - h sum_f (K_i + K_j)(x'_i - x'_j);
+// z = r / D_T in the bulk precision; partials r.r, x'.x', r.z.
 template <typename T>
-__device__ __forceinline__ void op_refine_pass(const SolveDev &sd, int ob, int oct_end, double h,
-                                               double &rr, double &xx, double &rz) {
+__device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, double &rr, double &xx,
+                                              double &rz) {
   const T *__restrict__ e = (const T *)sd.e;
   const T *__restrict__ KT = (const T *)sd.KT;
-  T *__restrict__ z = (T *)sd.z;
-  const CellCtx x = cell_ctx(ob, oct_end);
-  int nb[3];
-  load_nbr(sd.nbr, x, nb);
-  double kv = -1.0, xv = 0.0;
-  T kvT = T(-1);
-  int rec = -1;
-  if (x.valid) {
-    kv = sd.K64[x.i];
-    kvT = KT[x.i];
-    xv = sd.x64[x.i] + (double)e[x.i];
-    rec = __ldg(sd.xrec + x.o);
+  T *z = (T *)sd.z;
+  const bool mixed = sizeof(T) != sizeof(double);
+  const double h = sd.h;
+  const T hT = (T)sd.h;
+  int nb[6];
+  load_nbr6(sd.nbr, o, nb);
+  const int rec = __ldg(sd.xrec + o);
+  double K[8], xv[8], b[8];
+  T ev[8], KTo[8];
+  ld8_ro(sd.K64 + 8 * o, K);
+  ld8_rw(sd.x64 + 8 * o, xv);
+  ld8_ro(e + 8 * o, ev);
+  ld8_ro(sd.b64 + 8 * o, b);
+  if (mixed) ld8_ro(KT + 8 * o, KTo);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) xv[c] += (double)ev[c];
+  double acc[8];
+  T dsT[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    acc[c] = 0.0;
+    dsT[c] = T(0);
   }
-  double kj[3], xj[3];
-  T kjT[3];
+  // in-oct pairs: flux (K_c + K_d)(x_c - x_d) once per pair
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    kj[a] = -1.0;
-    xj[a] = 0.0;
-    kjT[a] = T(-1);
-    if (nb[a] >= 0) {
-      const int64_t j = (int64_t)nb[a] * 8 + (x.c ^ (1 << a));
-      kj[a] = sd.K64[j];
-      kjT[a] = KT[j];
-      xj[a] = sd.x64[j] + (double)e[j];
-    }
-  }
-  double dsum = 0.0, off = 0.0;
-  T dsumT = T(0);
-  const T hT = (T)h;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double xn = __shfl_xor_sync(kFull, xv, 1 << a);
-    const double kn = __shfl_xor_sync(kFull, kv, 1 << a);
-    const T knT = __shfl_xor_sync(kFull, kvT, 1 << a);
-    if (kn >= 0.0) {
-      const double C = h * (kv + kn);
-      dsum += C;
-      off += C * xn;
-      dsumT += hT * (kvT + knT);
-    }
-    if (kj[a] >= 0.0) {
-      const double C = h * (kv + kj[a]);
-      dsum += C;
-      off += C * xj[a];
-      dsumT += hT * (kvT + kjT[a]);
-    }
-  }
-  if (x.valid) {
-    if (kv >= 0.0) {
-      const double xd = rec >= 0 ? sd.xd64[(int64_t)rec * 8 + x.c] : 0.0;
-      const double d = 1.0 + xd + dsum;
-      const double q = d * xv - off;
-      const double r = sd.b64[x.i] - q;
-      T zT;
-      if (sizeof(T) == sizeof(double)) {
-        zT = (T)(r / d);
-      } else {
-        const T xdT = rec >= 0 ? ((const T *)sd.xdT)[(int64_t)rec * 8 + x.c] : T(0);
-        const T dT = T(1) + xdT + dsumT;
-        zT = (T)r / dT;
+    for (int c = 0; c < 8; ++c) {
+      if (c & (1 << a)) continue;
+      const int d = c | (1 << a);
+      if (K[c] >= 0.0 && K[d] >= 0.0) {
+        const double Ks = K[c] + K[d];
+        const double fl = Ks * (xv[c] - xv[d]);
+        acc[c] += fl;
+        acc[d] -= fl;
+        const T Ct = mixed ? hT * (KTo[c] + KTo[d]) : (T)Ks;
+        dsT[c] += Ct;
+        dsT[d] += Ct;
       }
-      z[x.i] = zT;
-      rr = fma(r, r, rr);
-      xx = fma(xv, xv, xx);
-      rz = fma(r, (double)zT, rz);
-    } else {
-      z[x.i] = T(0);
     }
   }
+  ref_face<0>(nb[0], sd, e, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<1>(nb[1], sd, e, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<2>(nb[2], sd, e, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<3>(nb[3], sd, e, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<4>(nb[4], sd, e, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<5>(nb[5], sd, e, KT, hT, K, KTo, xv, acc, dsT);
+  double xd[8];
+  T xdT[8];
+  if (rec >= 0) {
+    ld8_ro(sd.xd64 + 8 * rec, xd);
+    if (mixed) ld8_ro((const T *)sd.xdT + 8 * rec, xdT);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      xd[c] = 0.0;
+      xdT[c] = T(0);
+    }
+  }
+  T zo[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const bool leaf = K[c] >= 0.0;
+    const double r = fma(-h, acc[c], fma(-(1.0 + xd[c]), xv[c], b[c]));
+    T zc;
+    if (mixed) {
+      const T dT = T(1) + xdT[c] + dsT[c];
+      zc = (T)r / dT;
+    } else {
+      // FP64 bulk: dsT holds the plain K sums; D = 1 + xd + h sum
+      const double d = 1.0 + xd[c] + h * (double)dsT[c];
+      zc = (T)(r / d);
+    }
+    zo[c] = leaf ? zc : T(0);
+    if (leaf) {
+      rr = fma(r, r, rr);
+      xx = fma(xv[c], xv[c], xx);
+      rz = fma(r, (double)zc, rz);
+    }
+  }
+  st8(z + 8 * o, zo);
 }
 
 // k_upd, refinement phase: x += e, e = 0.
 template <typename T>
-__device__ __forceinline__ void upd_refine_pass(const SolveDev &sd, int ob, int oct_end) {
-  const CellCtx x = cell_ctx(ob, oct_end);
-  if (!x.valid) return;
-  T *__restrict__ e = (T *)sd.e;
-  const T ev = e[x.i];
-  sd.x64[x.i] += (double)ev;
-  e[x.i] = T(0);
+__device__ __forceinline__ void upd_refine_oct(const SolveDev &sd, int o) {
+  T *e = (T *)sd.e;
+  T ev[8];
+  double xv[8];
+  ld8_rw(e + 8 * o, ev);
+  ld8_rw(sd.x64 + 8 * o, xv);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    xv[c] += (double)ev[c];
+    ev[c] = T(0);
+  }
+  st8(sd.x64 + 8 * o, xv);
+  st8(e + 8 * o, ev);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// the two tick kernels (persistent grid, grid-stride over work items)
+// the two tick kernels (persistent grid, grid-stride over the active list)
 // ---------------------------------------------------------------------------
 
+// The list of one phase for the current parity: lists[(parity * 2 + phase) * n_items].
+__device__ __forceinline__ const int32_t *phase_list(const int32_t *lists, int n_items, int parity, int phase) {
+  return lists + (size_t)(parity * 2 + phase) * n_items;
+}
+
+// Last CTA of a solve in k_op / k_ref: reduce its partials and advance the
+// op-side scalars (alpha after a CG step; the refinement decision after a
+// true-residual pass).
+__device__ __forceinline__ void op_epilogue(const SolveDev &sd, SolveScalars *scs, int phase,
+                                            const double *partials, double (*red)[kNumPartials]) {
+  double tot[kNumPartials];
+  solve_reduce<false>(partials, sd.item_begin, sd.n_items, tot, red);
+  if (threadIdx.x == 0) {
+    scs->counter = 0;
+    if (phase == kInner) {
+      const double pq = tot[0];
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        scs->alpha = 0.0;
+        scs->status = ATS_ERR_BREAKDOWN;
+      } else {
+        scs->alpha = scs->rz / pq;
+      }
+    } else {
+      const double rnorm = sqrt(tot[0]);
+      const double xnorm = sqrt(tot[1]);
+      if (scs->refines == 0) scs->r0 = rnorm;
+      scs->refines += 1;
+      scs->rnorm = rnorm;
+      scs->xnorm = xnorm;
+      const double ref = (sd.stop_rule == ATS_STOP_CERTIFIED) ? xnorm : scs->r0;
+      const double target = sd.tol * ref;
+      if (scs->final_pass) {
+        scs->phase_next = kDone;
+      } else if (!isfinite(rnorm)) {
+        scs->status = ATS_ERR_BREAKDOWN;
+        scs->phase_next = kDone;
+      } else if (rnorm <= target) {
+        scs->phase_next = kDone;
+      } else if (scs->refines > sd.max_refine) {
+        scs->status = ATS_ERR_NOT_CONVERGED;
+        scs->phase_next = kDone;
+      } else if (!(tot[2] > 0.0)) {
+        scs->status = ATS_ERR_BREAKDOWN;
+        scs->phase_next = kDone;
+      } else {
+        scs->phase_next = kInner;
+        scs->rz = tot[2];
+        scs->first = 1;
+        scs->inner_iters = 0;
+        scs->inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// CG phase of the op side: p = z + beta p, q = (I + dt A) p, p.q.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_op(const SolveDev *__restrict__ solves,
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(const SolveDev *__restrict__ solves,
                                                  SolveScalars *__restrict__ sc,
-                                                 const WorkItem *__restrict__ items, int n_items,
-                                                 double *__restrict__ partials,
+                                                 const WorkItem *__restrict__ items,
+                                                 const int32_t *__restrict__ lists, int n_items,
+                                                 TickCtl *ctl, double *__restrict__ partials,
                                                  unsigned long long *__restrict__ cells) {
   __shared__ double red[kThreads / 32][kNumPartials];
   __shared__ int s_last;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  const int cur = __ldcg(&ctl->parity);
+  const int n_list = __ldcg(&ctl->count[cur][kInner]);
+  const int32_t *list = phase_list(lists, n_items, cur, kInner);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->count[cur ^ 1][0] = 0;
+    ctl->count[cur ^ 1][1] = 0;
+  }
+  for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+    const int it = __ldcg(list + li);
     const WorkItem item = items[it];
     const int s = item.solve;
     SolveScalars *scs = sc + s;
-    const int phase = scs->phase;
-    if (phase == kDone) continue;
     const SolveDev &sd = solves[s];
     const int oct_end = item.oct_begin + item.n_oct;
     double v[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
-    if (phase == kInner) {
-      const T h = (T)sd.h;
-      const T beta = (T)scs->beta;
-      const bool first = scs->first != 0;
-      const int pcur = scs->pcur;
-      const T *pold = (const T *)(pcur ? sd.p1 : sd.p0);
-      T *pnew = (T *)(pcur ? sd.p0 : sd.p1);
-      Acc<T> pq;
-      for (int ob = item.oct_begin; ob < oct_end; ob += kOctsPerPass)
-        op_inner_pass<T>(sd, ob, oct_end, h, beta, first, pold, pnew, pq);
-      v[0] = pq.get();
-      if (cells && threadIdx.x == 0) atomicAdd(cells + 0, (unsigned long long)item.n_oct * 8);
-    } else {
-      double rr = 0.0, xx = 0.0, rz = 0.0;
-      for (int ob = item.oct_begin; ob < oct_end; ob += kOctsPerPass)
-        op_refine_pass<T>(sd, ob, oct_end, sd.h, rr, xx, rz);
-      v[0] = rr;
-      v[1] = xx;
-      v[2] = rz;
-      if (cells && threadIdx.x == 0) atomicAdd(cells + 1, (unsigned long long)item.n_oct * 8);
-    }
-    block_reduce<false>(v, red);
+    const T h = (T)sd.h;
+    const T beta = (T)scs->beta;
+    const bool first = scs->first != 0;
+    const int pcur = scs->pcur;
+    const T *pold = (const T *)(pcur ? sd.p1 : sd.p0);
+    T *pnew = (T *)(pcur ? sd.p0 : sd.p1);
+    Acc<T> pq, none;
+    for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
+      op_inner_oct<T>(sd, o, h, beta, first, pold, pnew, pq);
+    block_reduce_acc<T>(pq, none, 0.0, v, red);
+    if (cells && threadIdx.x == 0) atomicAdd(cells + 0, (unsigned long long)item.n_oct * 8);
     if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
+    op_epilogue(sd, scs, kInner, partials, red);
+  }
+}
 
-    // ---- last CTA of solve s: advance the op-side scalars ----
-    double tot[kNumPartials];
-    solve_reduce<false>(partials, sd.item_begin, sd.n_items, tot, red);
-    if (threadIdx.x == 0) {
-      scs->counter = 0;
-      if (phase == kInner) {
-        const double pq = tot[0];
-        if (!(pq > 0.0) || !isfinite(pq)) {
-          scs->alpha = 0.0;
-          scs->status = ATS_ERR_BREAKDOWN;
-        } else {
-          scs->alpha = scs->rz / pq;
-        }
-      } else {
-        const double rnorm = sqrt(tot[0]);
-        const double xnorm = sqrt(tot[1]);
-        if (scs->refines == 0) scs->r0 = rnorm;
-        scs->refines += 1;
-        scs->rnorm = rnorm;
-        scs->xnorm = xnorm;
-        const double ref = (sd.stop_rule == ATS_STOP_CERTIFIED) ? xnorm : scs->r0;
-        const double target = sd.tol * ref;
-        if (scs->final_pass) {
-          scs->phase_next = kDone;
-        } else if (!isfinite(rnorm)) {
-          scs->status = ATS_ERR_BREAKDOWN;
-          scs->phase_next = kDone;
-        } else if (rnorm <= target) {
-          scs->phase_next = kDone;
-        } else if (scs->refines > sd.max_refine) {
-          scs->status = ATS_ERR_NOT_CONVERGED;
-          scs->phase_next = kDone;
-        } else if (!(tot[2] > 0.0)) {
-          scs->status = ATS_ERR_BREAKDOWN;
-          scs->phase_next = kDone;
-        } else {
-          scs->phase_next = kInner;
-          scs->rz = tot[2];
-          scs->first = 1;
-          scs->inner_iters = 0;
-          scs->inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
-        }
-      }
-    }
-    __syncthreads();
+// Refinement phase of the op side: FP64 true residual, z = D^-1 r.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_ref(const SolveDev *__restrict__ solves,
+                                                     SolveScalars *__restrict__ sc,
+                                                     const WorkItem *__restrict__ items,
+                                                     const int32_t *__restrict__ lists, int n_items,
+                                                     TickCtl *ctl, double *__restrict__ partials,
+                                                     unsigned long long *__restrict__ cells) {
+  __shared__ double red[kThreads / 32][kNumPartials];
+  __shared__ int s_last;
+  const int cur = __ldcg(&ctl->parity);
+  const int n_list = __ldcg(&ctl->count[cur][kRefine]);
+  const int32_t *list = phase_list(lists, n_items, cur, kRefine);
+  for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+    const int it = __ldcg(list + li);
+    const WorkItem item = items[it];
+    const int s = item.solve;
+    SolveScalars *scs = sc + s;
+    const SolveDev &sd = solves[s];
+    const int oct_end = item.oct_begin + item.n_oct;
+    double v[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
+    double rr = 0.0, xx = 0.0, rz = 0.0;
+    for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
+      op_refine_oct<T>(sd, o, rr, xx, rz);
+    v[0] = rr;
+    v[1] = xx;
+    v[2] = rz;
+    block_reduce<false>(v, red);
+    if (cells && threadIdx.x == 0) atomicAdd(cells + 1, (unsigned long long)item.n_oct * 8);
+    if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
+    op_epilogue(sd, scs, kRefine, partials, red);
   }
 }
 
 template <typename T, bool kPaper>
-__global__ void __launch_bounds__(kThreads) k_upd(const SolveDev *__restrict__ solves,
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(const SolveDev *__restrict__ solves,
                                                   SolveScalars *__restrict__ sc,
-                                                  const WorkItem *__restrict__ items, int n_items,
-                                                  double *__restrict__ partials, int *n_active,
+                                                  const WorkItem *__restrict__ items,
+                                                  int32_t *__restrict__ lists, int n_items,
+                                                  TickCtl *ctl, double *__restrict__ partials,
+                                                  int *n_active,
                                                   unsigned long long *__restrict__ cells) {
   __shared__ double red[kThreads / 32][kNumPartials];
   __shared__ int s_last;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  __shared__ int s_base;
+  __shared__ int s_phase;
+  const int cur = __ldcg(&ctl->parity);
+  const int n_in = __ldcg(&ctl->count[cur][kInner]);
+  const int n_list = n_in + __ldcg(&ctl->count[cur][kRefine]);
+  for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+    const int it = li < n_in ? __ldcg(phase_list(lists, n_items, cur, kInner) + li)
+                             : __ldcg(phase_list(lists, n_items, cur, kRefine) + (li - n_in));
     const WorkItem item = items[it];
     const int s = item.solve;
     SolveScalars *scs = sc + s;
     const int phase = scs->phase;
-    if (phase == kDone) continue;
     const SolveDev &sd = solves[s];
     const int oct_end = item.oct_begin + item.n_oct;
     double v[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
@@ -493,18 +742,14 @@ __global__ void __launch_bounds__(kThreads) k_upd(const SolveDev *__restrict__ s
       const T *p = (const T *)(scs->pcur ? sd.p0 : sd.p1);  // written by k_op this tick
       Acc<T> rz, rr;
       double maxchg = 0.0;
-      for (int ob = item.oct_begin; ob < oct_end; ob += kOctsPerPass)
-        upd_inner_pass<T, kPaper>(sd, ob, oct_end, h, alpha, p, rz, rr, maxchg);
-      v[0] = rz.get();
-      v[1] = rr.get();
-      v[2] = maxchg;
+      for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
+        upd_inner_oct<T, kPaper>(sd, o, h, alpha, p, rz, rr, maxchg);
+      block_reduce_acc<T>(rz, rr, maxchg, v, red);
       if (cells && threadIdx.x == 0) atomicAdd(cells + 2, (unsigned long long)item.n_oct * 8);
     } else {
-      for (int ob = item.oct_begin; ob < oct_end; ob += kOctsPerPass)
-        upd_refine_pass<T>(sd, ob, oct_end);
+      for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads) upd_refine_oct<T>(sd, o);
       if (cells && threadIdx.x == 0) atomicAdd(cells + 3, (unsigned long long)item.n_oct * 8);
     }
-    block_reduce<true>(v, red);
     if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
 
     double tot[kNumPartials];
@@ -542,8 +787,26 @@ __global__ void __launch_bounds__(kThreads) k_upd(const SolveDev *__restrict__ s
         scs->phase = scs->phase_next;
         if (scs->phase == kDone) atomicSub(n_active, 1);
       }
+      const int np = scs->phase;
+      s_phase = np;
+      s_base = (np != kDone) ? atomicAdd(&ctl->count[cur ^ 1][np], sd.n_items) : -1;
     }
     __syncthreads();
+    if (s_base >= 0) {
+      int32_t *next = lists + (size_t)((cur ^ 1) * 2 + s_phase) * n_items;
+      for (int k = threadIdx.x; k < sd.n_items; k += kThreads) next[s_base + k] = sd.item_begin + k;
+    }
+    __syncthreads();
+  }
+  // the last CTA of the grid flips the list parity for the next tick
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->cta_done, 1) == (int)gridDim.x - 1) {
+      ctl->cta_done = 0;
+      ctl->parity = cur ^ 1;
+      __threadfence();
+    }
   }
 }
 
@@ -551,9 +814,7 @@ __global__ void __launch_bounds__(kThreads) k_upd(const SolveDev *__restrict__ s
 // coefficient build (one thread per cell)
 // ---------------------------------------------------------------------------
 
-__global__ void k_coef_build(CoefArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 8 * a.n_oct) return;
+__device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
   const int64_t o = i >> 3;
   const int c = (int)(i & 7);
   const bool leaf = a.leaf ? ((a.leaf[o] >> c) & 1) : true;
@@ -606,6 +867,51 @@ __global__ void k_coef_build(CoefArgs a) {
     a.xd32[(int64_t)xr * 8 + c] = (float)xd;
   }
   if (!ok) atomicOr(a.err_flag, 1);
+}
+
+__global__ void k_coef_build(CoefArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 8 * a.n_oct) return;
+  coef_cell(a, i);
+}
+
+// All levels of a batch in one launch: cell g belongs to the level k with
+// cell_off[k] <= g < cell_off[k + 1].
+__global__ void k_coef_build_batch(const CoefArgs *__restrict__ args, const int64_t *__restrict__ cell_off,
+                                   int n) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cell_off[n]) return;
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cell_off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  coef_cell(args[lo], g - cell_off[lo]);
+}
+
+__global__ void k_zero_flags(int *const *__restrict__ flags, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) *flags[k] = 0;
+}
+
+__global__ void k_gather_flags(const int *const *__restrict__ flags, int n, int *__restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = *flags[k];
+}
+
+cudaError_t launch_coef_build_batch(const CoefArgs *args, const int64_t *cell_off, int n, int64_t total_cells,
+                                    int *const *flags, cudaStream_t st) {
+  k_zero_flags<<<(n + 255) / 256, 256, 0, st>>>(flags, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || total_cells == 0) return e;
+  k_coef_build_batch<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(args, cell_off, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_flags(const int *const *flags, int n, int *out, cudaStream_t st) {
+  k_gather_flags<<<(n + 255) / 256, 256, 0, st>>>(flags, n, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st) {
@@ -674,29 +980,32 @@ static cudaError_t record(cudaEvent_t ev, cudaStream_t st, bool capture) {
 
 template <typename T, bool kPaper>
 static cudaError_t tick_impl(const SolveDev *solves, SolveScalars *sc, const WorkItem *items,
-                             int n_items, double *partials, int *n_active, int grid,
-                             cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2,
+                             int32_t *lists, int n_items, TickCtl *ctl, double *partials,
+                             int *n_active, int grid, cudaStream_t st, cudaEvent_t *ev,
                              bool capture, unsigned long long *cells) {
   cudaError_t err;
-  if ((err = record(ev0, st, capture)) != cudaSuccess) return err;
-  k_op<T><<<grid, kThreads, 0, st>>>(solves, sc, items, n_items, partials, cells);
+  if ((err = record(ev ? ev[0] : nullptr, st, capture)) != cudaSuccess) return err;
+  k_op<T><<<grid, kThreads, 0, st>>>(solves, sc, items, lists, n_items, ctl, partials, cells);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  if ((err = record(ev1, st, capture)) != cudaSuccess) return err;
-  k_upd<T, kPaper><<<grid, kThreads, 0, st>>>(solves, sc, items, n_items, partials, n_active, cells);
+  if ((err = record(ev ? ev[1] : nullptr, st, capture)) != cudaSuccess) return err;
+  k_ref<T><<<grid, kThreads, 0, st>>>(solves, sc, items, lists, n_items, ctl, partials, cells);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  return record(ev2, st, capture);
+  if ((err = record(ev ? ev[2] : nullptr, st, capture)) != cudaSuccess) return err;
+  k_upd<T, kPaper><<<grid, kThreads, 0, st>>>(solves, sc, items, lists, n_items, ctl, partials, n_active, cells);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  return record(ev ? ev[3] : nullptr, st, capture);
 }
 
 cudaError_t launch_tick(bool fp64, bool paper, const SolveDev *solves, SolveScalars *sc,
-                        const WorkItem *items, int n_items, double *partials, int *n_active,
-                        int grid, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
-                        cudaEvent_t ev2, bool capture, unsigned long long *cells) {
+                        const WorkItem *items, int32_t *lists, int n_items, TickCtl *ctl,
+                        double *partials, int *n_active, int grid, cudaStream_t st,
+                        cudaEvent_t *ev, bool capture, unsigned long long *cells) {
   if (fp64) {
-    return paper ? tick_impl<double, true>(solves, sc, items, n_items, partials, n_active, grid, st, ev0, ev1, ev2, capture, cells)
-                 : tick_impl<double, false>(solves, sc, items, n_items, partials, n_active, grid, st, ev0, ev1, ev2, capture, cells);
+    return paper ? tick_impl<double, true>(solves, sc, items, lists, n_items, ctl, partials, n_active, grid, st, ev, capture, cells)
+                 : tick_impl<double, false>(solves, sc, items, lists, n_items, ctl, partials, n_active, grid, st, ev, capture, cells);
   }
-  return paper ? tick_impl<float, true>(solves, sc, items, n_items, partials, n_active, grid, st, ev0, ev1, ev2, capture, cells)
-               : tick_impl<float, false>(solves, sc, items, n_items, partials, n_active, grid, st, ev0, ev1, ev2, capture, cells);
+  return paper ? tick_impl<float, true>(solves, sc, items, lists, n_items, ctl, partials, n_active, grid, st, ev, capture, cells)
+               : tick_impl<float, false>(solves, sc, items, lists, n_items, ctl, partials, n_active, grid, st, ev, capture, cells);
 }
 
 // ---------------------------------------------------------------------------

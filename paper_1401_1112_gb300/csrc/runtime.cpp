@@ -144,6 +144,11 @@ struct Plan {
   double *d_partials = nullptr;
   int *d_active = nullptr;
   unsigned long long *d_cells = nullptr;
+  int32_t *d_lists = nullptr;      // [2 parities][2 phases][n_items] active work lists
+  int32_t *d_ident = nullptr;      // [n_items] 0..n_items-1 (the full list)
+  TickCtl *d_ctl = nullptr;
+  int **d_flag_ptrs = nullptr;     // [n] the levels' error flags
+  int *d_flags = nullptr;          // [n] gathered flags
   const double **d_src = nullptr;  // [n] device pointers for x copy-in (or null)
   double **d_dst = nullptr;        // [n] device pointers for x copy-out (or null)
   int *h_active = nullptr;         // pinned [2]: one per poll slot
@@ -153,15 +158,21 @@ struct Plan {
   int graph_ticks = 0;
   bool graph_profiled = false;
   bool profiling = false;
-  std::vector<cudaEvent_t> evs;  // 3 per tick of a chunk
+  std::vector<cudaEvent_t> evs;  // 4 per tick of a chunk
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   int slot = 0;
-  double op_ms = 0.0, upd_ms = 0.0, op_bytes = 0.0, upd_bytes = 0.0;
+  double op_ms = 0.0, ref_ms = 0.0, upd_ms = 0.0, op_bytes = 0.0, ref_bytes = 0.0, upd_bytes = 0.0;
   int launches = 0;
+  int ticks = 0;
 };
 
 struct ats_batch {
   Plan *plan = nullptr;
+  // batched operator build
+  CoefArgs *d_args = nullptr;
+  int64_t *d_cell_off = nullptr;
+  std::vector<CoefArgs> h_args;  // last uploaded arguments
+  int64_t total_cells = 0;
 };
 
 namespace {
@@ -173,7 +184,7 @@ void fill_defaults(ats_solve_opts *o) {
   o->precision = ATS_PREC_FP64;
   o->max_iter = 20000;
   o->max_refine = 40;
-  o->inner_rtol = 1e-4;
+  o->inner_rtol = 1e-5;
   o->tile_octs = 0;
   o->check_every = 16;
   o->use_graph = 0;
@@ -188,19 +199,18 @@ ats_solve_opts normalize(const ats_solve_opts *in) {
   if (!(o.tol > 0.0)) o.tol = 1e-10;
   if (o.max_iter <= 0) o.max_iter = 20000;
   if (o.max_refine <= 0) o.max_refine = 40;
-  if (!(o.inner_rtol > 0.0)) o.inner_rtol = 1e-4;
+  if (!(o.inner_rtol > 0.0)) o.inner_rtol = 1e-5;
   if (o.check_every <= 0) o.check_every = 16;
   return o;
 }
 
-// Octs per work item: a multiple of 32 octs (one CTA pass = 32 octs).  Small
-// solves get one item; large ones are split so that every solve has enough
-// items to fill the GPU while the last-CTA reduction stays short.
+// Octs per work item (one CTA of kThreads threads, one oct per thread and
+// pass).  Items of one pass keep every CTA's loads independent; very large
+// solves take longer items so their last-CTA reduction stays short.
 int choose_tile(int64_t n_oct, int requested) {
   if (requested > 0) return std::max(32, (requested + 31) / 32 * 32);
-  if (n_oct <= 256) return 256;
-  if (n_oct <= 32768) return 128;
-  return 256;
+  if (n_oct <= 131072) return 2 * kThreads;
+  return 8 * kThreads;
 }
 
 ats_status ensure_vectors(ats_level *L, bool fp64) {
@@ -229,6 +239,11 @@ void plan_free(Plan *P) {
   dev_free(ctx, P->d_partials);
   dev_free(ctx, P->d_active);
   dev_free(ctx, P->d_cells);
+  dev_free(ctx, P->d_lists);
+  dev_free(ctx, P->d_ident);
+  dev_free(ctx, P->d_ctl);
+  dev_free(ctx, P->d_flag_ptrs);
+  dev_free(ctx, P->d_flags);
   dev_free(ctx, P->d_src);
   dev_free(ctx, P->d_dst);
   if (P->h_active) cudaFreeHost(P->h_active);
@@ -329,6 +344,11 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 4, &P->d_cells)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 4 * (size_t)P->n_items, &P->d_lists)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, (size_t)P->n_items, &P->d_ident)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 1, &P->d_ctl)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, n, &P->d_flag_ptrs)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, n, &P->d_flags)) != ATS_OK ||
       (s = dev_alloc_t(ctx, n, &P->d_src)) != ATS_OK ||
       (s = dev_alloc_t(ctx, n, &P->d_dst)) != ATS_OK) {
     plan_free(P);
@@ -343,6 +363,18 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   cudaStream_t st = ctx->stream;
   CUDA_TRY(cudaMemcpyAsync(P->d_solves, P->h_solves.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st));
+  {
+    std::vector<int32_t> ident(P->n_items);
+    for (int i = 0; i < P->n_items; ++i) ident[i] = i;
+    CUDA_TRY(cudaMemcpyAsync(P->d_ident, ident.data(), sizeof(int32_t) * ident.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  {
+    std::vector<int *> fp(n);
+    for (int k = 0; k < n; ++k) fp[k] = P->levels[k]->err_flag;
+    CUDA_TRY(cudaMemcpyAsync(P->d_flag_ptrs, fp.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
   CUDA_TRY(cudaEventCreateWithFlags(&P->poll_ev[0], cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&P->poll_ev[1], cudaEventDisableTiming));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -351,7 +383,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
 }
 
 ats_status plan_ensure_events(Plan *P) {
-  const size_t need = 3 * (size_t)P->opts.check_every;
+  const size_t need = 4 * (size_t)P->opts.check_every;
   while (P->evs.size() < need) {
     cudaEvent_t e;
     CUDA_TRY(cudaEventCreate(&e));
@@ -379,9 +411,8 @@ ats_status plan_enqueue_chunk(Plan *P) {
       CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       cudaError_t err = cudaSuccess;
       for (int t = 0; t < k && err == cudaSuccess; ++t) {
-        err = launch_tick(P->fp64, P->paper, P->d_solves, P->d_sc, P->d_items, P->n_items, P->d_partials,
-                          P->d_active, P->grid, st, prof ? P->evs[3 * t] : nullptr,
-                          prof ? P->evs[3 * t + 1] : nullptr, prof ? P->evs[3 * t + 2] : nullptr, true,
+        err = launch_tick(P->fp64, P->paper, P->d_solves, P->d_sc, P->d_items, P->d_lists, P->n_items,
+                          P->d_ctl, P->d_partials, P->d_active, P->grid, st, prof ? &P->evs[4 * t] : nullptr, true,
                           prof ? P->d_cells : nullptr);
       }
       cudaError_t err2 = cudaStreamEndCapture(st, &g);
@@ -408,12 +439,13 @@ ats_status plan_enqueue_chunk(Plan *P) {
       if (s != ATS_OK) return s;
     }
     for (int t = 0; t < k; ++t) {
-      CUDA_TRY(launch_tick(P->fp64, P->paper, P->d_solves, P->d_sc, P->d_items, P->n_items, P->d_partials,
-                           P->d_active, P->grid, st, prof ? P->evs[3 * t] : nullptr,
-                           prof ? P->evs[3 * t + 1] : nullptr, prof ? P->evs[3 * t + 2] : nullptr, false,
+      CUDA_TRY(launch_tick(P->fp64, P->paper, P->d_solves, P->d_sc, P->d_items, P->d_lists, P->n_items,
+                           P->d_ctl, P->d_partials, P->d_active, P->grid, st, prof ? &P->evs[4 * t] : nullptr, false,
                            prof ? P->d_cells : nullptr));
     }
   }
+  P->ticks += k;
+  P->launches += 3 * k;
   CUDA_TRY(cudaMemcpyAsync(P->h_active + P->slot, P->d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaEventRecord(P->poll_ev[P->slot], st));
   P->slot ^= 1;
@@ -423,19 +455,20 @@ ats_status plan_enqueue_chunk(Plan *P) {
 ats_status plan_collect_events(Plan *P) {
   const int k = P->opts.check_every;
   for (int t = 0; t < k; ++t) {
-    float a = 0.f, b = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&a, P->evs[3 * t], P->evs[3 * t + 1]));
-    CUDA_TRY(cudaEventElapsedTime(&b, P->evs[3 * t + 1], P->evs[3 * t + 2]));
+    float a = 0.f, b = 0.f, c = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&a, P->evs[4 * t], P->evs[4 * t + 1]));
+    CUDA_TRY(cudaEventElapsedTime(&b, P->evs[4 * t + 1], P->evs[4 * t + 2]));
+    CUDA_TRY(cudaEventElapsedTime(&c, P->evs[4 * t + 2], P->evs[4 * t + 3]));
     P->op_ms += a;
-    P->upd_ms += b;
-    P->launches += 2;
+    P->ref_ms += b;
+    P->upd_ms += c;
   }
   return ATS_OK;
 }
 
 // Algorithmic bytes per cell of each kernel/phase (compulsory traffic of the
 // vectors and coefficients; neighbour tables and records not counted).
-void plan_bytes(const Plan *P, const unsigned long long cells[4], double *op_b, double *upd_b) {
+void plan_bytes(const Plan *P, const unsigned long long cells[4], double *op_b, double *ref_b, double *upd_b) {
   const double w = P->fp64 ? 8.0 : 4.0;
   // op inner: read z, p_old, K; write p_new.   op refine: read x64, e, K64, K_T, b64; write z
   const double op_inner = 4 * w;
@@ -443,7 +476,8 @@ void plan_bytes(const Plan *P, const unsigned long long cells[4], double *op_b, 
   // upd inner: read p, K, z, e; write z, e.    upd refine: read/write x64 and e
   const double upd_inner = 6 * w;
   const double upd_refine = 16 + 2 * w;
-  *op_b = op_inner * cells[0] + op_refine * cells[1];
+  *op_b = op_inner * cells[0];
+  *ref_b = op_refine * cells[1];
   *upd_b = upd_inner * cells[2] + upd_refine * cells[3];
 }
 
@@ -498,8 +532,18 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   CUDA_TRY(cudaMemcpyAsync(P->d_sc, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, 4 * sizeof(unsigned long long), st));
   CUDA_TRY(cudaMemcpyAsync(P->d_active, &n, sizeof(int), cudaMemcpyHostToDevice, st));
-  P->op_ms = P->upd_ms = 0.0;
+  {
+    // every item of every solve starts in the refinement phase (r0 = b - A x0)
+    TickCtl c0;
+    std::memset(&c0, 0, sizeof(c0));
+    c0.count[0][kRefine] = P->n_items;
+    CUDA_TRY(cudaMemcpyAsync(P->d_lists + (size_t)kRefine * P->n_items, P->d_ident,
+                             sizeof(int32_t) * P->n_items, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(P->d_ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+  }
+  P->op_ms = P->ref_ms = P->upd_ms = 0.0;
   P->launches = 0;
+  P->ticks = 0;
 
   // host guard: every solve ends within max_iter + 2 (max_refine + 1) ticks
   const int64_t max_ticks = (int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2) + 2 * P->opts.check_every;
@@ -553,10 +597,10 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   unsigned long long cells[4] = {0, 0, 0, 0};
   if (P->profiling) CUDA_TRY(cudaMemcpyAsync(cells, P->d_cells, sizeof(cells), cudaMemcpyDeviceToHost, st));
   std::vector<int> flags(n, 0);
-  for (int k = 0; k < n; ++k)
-    CUDA_TRY(cudaMemcpyAsync(&flags[k], P->levels[k]->err_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, n, P->d_flags, st));
+  CUDA_TRY(cudaMemcpyAsync(flags.data(), P->d_flags, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
-  if (P->profiling) plan_bytes(P, cells, &P->op_bytes, &P->upd_bytes);
+  if (P->profiling) plan_bytes(P, cells, &P->op_bytes, &P->ref_bytes, &P->upd_bytes);
   ats_status first_err = ATS_OK;
   for (int k = 0; k < n; ++k) {
     int status = sc[k].status;
@@ -767,7 +811,14 @@ ats_status ats_level_size(const ats_level *L, int64_t *n_oct, int64_t *n_cell, i
   return ATS_OK;
 }
 
-ats_status ats_level_build_operator(ats_level *L, const ats_coef_desc *c) {
+}  // extern "C"
+
+namespace {
+
+// Validate a coefficient description, allocate the level's operator arrays,
+// stage host arrays on the device, and fill the kernel arguments.  Enqueues
+// copies on the context stream; does not launch the kernel.
+ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out) {
   if (!L || !c) {
     set_error("null argument");
     return ATS_ERR_INVALID_ARG;
@@ -852,7 +903,7 @@ ats_status ats_level_build_operator(ats_level *L, const ats_coef_desc *c) {
       }
     }
   }
-  CoefArgs a;
+  CoefArgs &a = *out;
   std::memset(&a, 0, sizeof(a));
   a.n_oct = L->n_oct;
   a.leaf = L->leaf;
@@ -876,11 +927,24 @@ ats_status ats_level_build_operator(ats_level *L, const ats_coef_desc *c) {
   a.xd32 = L->xd32;
   a.b64 = L->b64;
   a.err_flag = L->err_flag;
-  CUDA_TRY(cudaMemsetAsync(L->err_flag, 0, sizeof(int), st));
-  CUDA_TRY(launch_coef_build(a, st));
-  if (c->mem == ATS_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));  // staging reuse
   L->dt = c->dt;
   L->built = true;
+  return ATS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ats_status ats_level_build_operator(ats_level *L, const ats_coef_desc *c) {
+  CoefArgs a;
+  ats_status s = prepare_operator(L, c, &a);
+  if (s != ATS_OK) return s;
+  cudaStream_t st = L->ctx->stream;
+  CUDA_TRY(cudaMemsetAsync(L->err_flag, 0, sizeof(int), st));
+  CUDA_TRY(launch_coef_build(a, st));
+  // host arrays: the caller may reuse them once the call returns
+  if (c->mem == ATS_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
   return ATS_OK;
 }
 
@@ -998,8 +1062,11 @@ ats_status ats_batch_solve(ats_batch *B, double *const *x_inout, ats_solve_stats
 ats_status ats_batch_destroy(ats_batch *B) {
   if (!B) return ATS_ERR_INVALID_ARG;
   if (B->plan) {
-    cudaSetDevice(B->plan->ctx->device);
-    cudaStreamSynchronize(B->plan->ctx->stream);
+    ats_context *ctx = B->plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, B->d_args);
+    dev_free(ctx, B->d_cell_off);
     plan_free(B->plan);
   }
   delete B;
@@ -1016,21 +1083,59 @@ ats_status ats_batch_run(ats_context *ctx, ats_level *const *levels, int n, doub
   return s;
 }
 
+ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
+  if (!B || !B->plan || !coefs) {
+    set_error("null argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  Plan *P = B->plan;
+  ats_context *ctx = P->ctx;
+  const int n = P->n;
+  std::vector<CoefArgs> args(n);
+  bool any_host = false;
+  for (int k = 0; k < n; ++k) {
+    ats_status s = prepare_operator(P->levels[k], &coefs[k], &args[k]);
+    if (s != ATS_OK) return s;
+    any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
+  }
+  cudaStream_t st = ctx->stream;
+  ats_status s;
+  if (!B->d_args) {
+    if ((s = dev_alloc_t(ctx, n, &B->d_args)) != ATS_OK) return s;
+    if ((s = dev_alloc_t(ctx, n + 1, &B->d_cell_off)) != ATS_OK) return s;
+    std::vector<int64_t> off(n + 1, 0);
+    for (int k = 0; k < n; ++k) off[k + 1] = off[k] + P->levels[k]->N;
+    B->total_cells = off[n];
+    CUDA_TRY(cudaMemcpyAsync(B->d_cell_off, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+  }
+  // upload the per-level arguments only when they changed (same buffers and
+  // dt from step to step is the common case)
+  if (B->h_args.size() != (size_t)n || std::memcmp(B->h_args.data(), args.data(), sizeof(CoefArgs) * n) != 0) {
+    B->h_args = args;
+    CUDA_TRY(cudaMemcpyAsync(B->d_args, B->h_args.data(), sizeof(CoefArgs) * n, cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(launch_coef_build_batch(B->d_args, B->d_cell_off, n, B->total_cells, P->d_flag_ptrs, st));
+  if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
+  return ATS_OK;
+}
+
 ats_status ats_batch_set_profiling(ats_batch *B, int on) {
   if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
   B->plan->profiling = on != 0;
   return ATS_OK;
 }
 
-ats_status ats_batch_kernel_stats(const ats_batch *B, double *op_ms, double *op_bytes, double *upd_ms,
-                                  double *upd_bytes, int *launches) {
-  if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
+ats_status ats_batch_kernel_stats(const ats_batch *B, ats_kernel_stats *out) {
+  if (!B || !B->plan || !out) return ATS_ERR_INVALID_ARG;
   const Plan *P = B->plan;
-  if (op_ms) *op_ms = P->op_ms;
-  if (op_bytes) *op_bytes = P->op_bytes;
-  if (upd_ms) *upd_ms = P->upd_ms;
-  if (upd_bytes) *upd_bytes = P->upd_bytes;
-  if (launches) *launches = P->launches;
+  out->op_ms = P->op_ms;
+  out->op_bytes = P->op_bytes;
+  out->ref_ms = P->ref_ms;
+  out->ref_bytes = P->ref_bytes;
+  out->upd_ms = P->upd_ms;
+  out->upd_bytes = P->upd_bytes;
+  out->launches = P->launches;
+  out->ticks = P->ticks;
   return ATS_OK;
 }
 
