@@ -209,6 +209,39 @@ typedef struct {
 ats_status ats_batch_set_profiling(ats_batch *batch, int on);
 ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out);
 
+/* ---- allocation-free solve ------------------------------------------------- */
+/* The paper has no counterpart to this entry point: it is a service for
+ * callers that cannot allocate device memory (code inside a CUDA stream
+ * capture, plug-ins confined to a memory pool owned by their host program,
+ * processes whose allocator belongs to another runtime).  It solves one level
+ * like ats_solve with ATS_PREC_FP64 and ATS_STOP_RESIDUAL, but calls no
+ * cudaMalloc or cudaFree: its CG vectors, partial sums, work list and
+ * scalars live in one fixed device array inside the library (about 8.5 MB,
+ * held by every GPU that loads the library until the process exits).
+ *
+ * Arguments (all arrays are DEVICE pointers, FP64, read in stream order on
+ * `stream`, a cudaStream_t or NULL for the default stream):
+ *   n_oct     octs of the level, 1 <= 8 n_oct <= ATS_NOALLOC_MAX_CELLS;
+ *   nbr       [6 n_oct] oct neighbour table (ats_layout_neighbors gives it);
+ *   K         [8 n_oct] cell K on leaf cells, a negative value on cells that
+ *             are not unknowns of the level;
+ *   xd        [8 n_oct] extra diagonal per cell (coupling shift plus the
+ *             interface terms w C of Sect. 3.2), or NULL for none;
+ *   h         dt / dx^2 / 2, so an interior face has C = h (K_i + K_j);
+ *   b         [8 n_oct] right-hand side;
+ *   x         [8 n_oct] initial guess in, solution out;
+ *   tol       ||r_j|| <= tol ||r_0||; max_iter: CG cap (<= 0: 20000).
+ * Returns ATS_ERR_INVALID_ARG for sizes above ATS_NOALLOC_MAX_CELLS.  The
+ * first call on each device looks up the array's device address with that
+ * device current: make it outside any stream capture.  Every call reuses the
+ * same array (its contents are the last call's; what must start at zero is
+ * cleared by each call), so calls that overlap on the GPU race: serialise
+ * them. */
+#define ATS_NOALLOC_MAX_CELLS 262144
+ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct, const int32_t *nbr,
+                             const double *K, const double *xd, double h, const double *b,
+                             double *x, double tol, int max_iter, ats_solve_stats *stats);
+
 /* ---- misc ------------------------------------------------------------------ */
 void ats_default_opts(ats_solve_opts *opts);
 const char *ats_status_string(ats_status s);

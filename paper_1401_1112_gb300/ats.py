@@ -109,7 +109,11 @@ _SIGS = [
     ("ats_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("ats_last_error", ctypes.c_char_p, []),
     ("ats_layout_neighbors", ctypes.c_int, [ctypes.POINTER(ats_level_desc), P]),
+    ("ats_solve_noalloc", ctypes.c_int, [ctypes.c_int, P, ctypes.c_int64, P, P, P, ctypes.c_double, P, P,
+                                         ctypes.c_double, ctypes.c_int, ctypes.POINTER(ats_solve_stats)]),
 ]
+
+ATS_NOALLOC_MAX_CELLS = 262144
 
 _lib = None
 _lock = threading.Lock()
@@ -375,6 +379,20 @@ def ats_layout_neighbors(level) -> np.ndarray:
     out = np.empty(6 * d.n_oct, dtype=np.int32)
     _check(lib().ats_layout_neighbors(ctypes.byref(d), out.ctypes.data_as(ctypes.c_void_p)), "ats_layout_neighbors")
     return out.reshape(-1, 6)
+
+
+def ats_solve_noalloc(device, stream, n_oct, nbr, K, xd, h, b, x, tol=1e-10, max_iter=0):
+    """The allocation-free solve (see include/ats.h): every array is a CUDA
+    tensor (nbr int32, the others float64), ``stream`` a cudaStream_t handle
+    or 0.  Returns (status, stats dict)."""
+    for name, t in (("nbr", nbr), ("K", K), ("b", b), ("x", x)) + ((("xd", xd),) if xd is not None else ()):
+        if not _is_torch_cuda(t):
+            raise ValueError(f"{name} must be a CUDA tensor")
+    st = ats_solve_stats()
+    code = lib().ats_solve_noalloc(int(device), ctypes.c_void_p(stream) if stream else None, int(n_oct),
+                                   _ptr(nbr), _ptr(K), _ptr(xd), float(h), _ptr(b), _ptr(x), float(tol),
+                                   int(max_iter), ctypes.byref(st))
+    return code, st.as_dict()
 
 
 # ---------------------------------------------------------------------------
