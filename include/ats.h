@@ -209,6 +209,48 @@ typedef struct {
 ats_status ats_batch_set_profiling(ats_batch *batch, int on);
 ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out);
 
+/* ---- AMR hierarchy and the level substep driver (Sect. 2.2, 3.3) ----------- */
+/* A hierarchy of levels l = 0 .. n_levels-1, dx halving per level; an oct at
+ * level l+1 with oct coordinates (x, y, z) refines cell (x, y, z) of level l,
+ * which must be marked non-leaf there.  Interface faces are derived from the
+ * geometry: a leaf next to a refined cell of its level gets a Dirichlet face
+ * with the restriction (mean of the 8 children) of that cell (coarse-to-fine,
+ * Sect. 3.3.2, factor 1); a leaf next to a coarser leaf gets a Dirichlet face
+ * with the coarse value (fine-to-coarse, Sect. 3.3.1, factor 2/3); faces on
+ * the base level's outer boundary are zero-flux walls.  2:1 balance is
+ * required (ATS_ERR_INVALID_ARG otherwise). */
+typedef struct ats_hierarchy ats_hierarchy;
+#define ATS_ORDER_FINE_FIRST 0   /* the paper: finer levels first, coarse value held at E^n   */
+#define ATS_ORDER_COARSE_FIRST 1 /* coarse step first, fine ghosts linear in time over it   */
+typedef struct {
+  int n_levels;
+  const ats_level_desc *levels; /* per level: n_oct, oct_xyz, leaf_mask, dx; face fields ignored */
+  int order;                    /* ATS_ORDER_*                                                   */
+} ats_hierarchy_desc;
+ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc, ats_hierarchy **out);
+ats_status ats_hierarchy_destroy(ats_hierarchy *h);
+/* The ats_level of one hierarchy level (owned by the hierarchy). */
+ats_status ats_hierarchy_level(ats_hierarchy *h, int level, ats_level **out);
+/* Set E and K ([N] of that level, host or device per mem); E is E^n. */
+ats_status ats_hierarchy_set_state(ats_hierarchy *h, int level, const double *E, const double *K, int mem);
+/* Copy E of a level out; refined cells carry the restriction of their children. */
+ats_status ats_hierarchy_get_state(ats_hierarchy *h, int level, double *E, int mem);
+/* Advance `level` by dt: with ATS_ORDER_FINE_FIRST the finer levels first take
+ * two substeps of dt/2 each (recursively), then this level is solved; with
+ * ATS_ORDER_COARSE_FIRST this level is solved first, then the finer levels
+ * take their substeps with this level's value linear in time.  Every solve is
+ * ats_solve with opts; stats accumulates iterations over all solves and keeps
+ * the worst status and residuals. */
+ats_status ats_level_advance(ats_hierarchy *h, int level, double dt, const ats_solve_opts *opts,
+                             ats_solve_stats *stats);
+/* Host-only (no device): the interface faces the hierarchy derives for one
+ * level.  Call with NULL arrays to get n_face first.  rel is ATS_REL_FINER
+ * (src_cell = refined cell of the same level) or ATS_REL_COARSER (src_cell =
+ * leaf of level - 1). */
+ats_status ats_hierarchy_plan_faces(const ats_hierarchy_desc *desc, int level, int64_t *n_face,
+                                    int32_t *face_cell, int8_t *face_dir, int8_t *face_rel,
+                                    int32_t *src_cell);
+
 /* ---- allocation-free solve ------------------------------------------------- */
 /* The paper has no counterpart to this entry point: it is a service for
  * callers that cannot allocate device memory (code inside a CUDA stream

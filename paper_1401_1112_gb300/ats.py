@@ -66,6 +66,13 @@ class ats_solve_opts(ctypes.Structure):
     ]
 
 
+class ats_hierarchy_desc(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int), ("levels", ctypes.POINTER(ats_level_desc)), ("order", ctypes.c_int)]
+
+
+ATS_ORDER_FINE_FIRST, ATS_ORDER_COARSE_FIRST = 0, 1
+
+
 class ats_kernel_stats(ctypes.Structure):
     _fields_ = [
         ("op_ms", ctypes.c_double), ("op_bytes", ctypes.c_double), ("ref_ms", ctypes.c_double),
@@ -109,6 +116,15 @@ _SIGS = [
     ("ats_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("ats_last_error", ctypes.c_char_p, []),
     ("ats_layout_neighbors", ctypes.c_int, [ctypes.POINTER(ats_level_desc), P]),
+    ("ats_hierarchy_create", ctypes.c_int, [P, ctypes.POINTER(ats_hierarchy_desc), ctypes.POINTER(P)]),
+    ("ats_hierarchy_destroy", ctypes.c_int, [P]),
+    ("ats_hierarchy_level", ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(P)]),
+    ("ats_hierarchy_set_state", ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int]),
+    ("ats_hierarchy_get_state", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
+    ("ats_level_advance", ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ats_solve_opts),
+                                         ctypes.POINTER(ats_solve_stats)]),
+    ("ats_hierarchy_plan_faces", ctypes.c_int, [ctypes.POINTER(ats_hierarchy_desc), ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_int64), P, P, P, P]),
     ("ats_solve_noalloc", ctypes.c_int, [ctypes.c_int, P, ctypes.c_int64, P, P, P, ctypes.c_double, P, P,
                                          ctypes.c_double, ctypes.c_int, ctypes.POINTER(ats_solve_stats)]),
 ]
@@ -395,6 +411,71 @@ def ats_solve_noalloc(device, stream, n_oct, nbr, K, xd, h, b, x, tol=1e-10, max
     return code, st.as_dict()
 
 
+def _hierarchy_desc(levels, order, keep):
+    arr = (ats_level_desc * len(levels))(*[_level_desc(l, keep) for l in levels])
+    keep.append(arr)
+    d = ats_hierarchy_desc()
+    d.n_levels = len(levels)
+    d.levels = ctypes.cast(arr, ctypes.POINTER(ats_level_desc))
+    d.order = order
+    return d
+
+
+def ats_hierarchy_create(ctx, levels, order=ATS_ORDER_FINE_FIRST):
+    keep = []
+    d = _hierarchy_desc(levels, order, keep)
+    h = P()
+    _check(lib().ats_hierarchy_create(ctx, ctypes.byref(d), ctypes.byref(h)), "ats_hierarchy_create")
+    return h
+
+
+def ats_hierarchy_destroy(h):
+    return _check(lib().ats_hierarchy_destroy(h), "ats_hierarchy_destroy")
+
+
+def ats_hierarchy_level(h, level):
+    out = P()
+    _check(lib().ats_hierarchy_level(h, level, ctypes.byref(out)), "ats_hierarchy_level")
+    return out
+
+
+def ats_hierarchy_set_state(h, level, E, K):
+    keep = []
+    mem = _mem_of(E, K)
+    return _check(lib().ats_hierarchy_set_state(h, level, _ptr(E, keep=keep), _ptr(K, keep=keep), mem),
+                  "ats_hierarchy_set_state")
+
+
+def ats_hierarchy_get_state(h, level, out):
+    mem = _mem_of(out)
+    return _check(lib().ats_hierarchy_get_state(h, level, _ptr(out), mem), "ats_hierarchy_get_state")
+
+
+def ats_level_advance(h, level, dt, opts: Optional[ats_solve_opts] = None):
+    o = opts if opts is not None else make_opts()
+    st = ats_solve_stats()
+    code = lib().ats_level_advance(h, level, float(dt), ctypes.byref(o), ctypes.byref(st))
+    return code, st.as_dict()
+
+
+def ats_hierarchy_plan_faces(levels, level, order=ATS_ORDER_FINE_FIRST):
+    """Host-only: (cell, dir, rel, src_cell) arrays of the interface faces the
+    library derives for one level."""
+    keep = []
+    d = _hierarchy_desc(levels, order, keep)
+    n = ctypes.c_int64()
+    _check(lib().ats_hierarchy_plan_faces(ctypes.byref(d), level, ctypes.byref(n), None, None, None, None),
+           "ats_hierarchy_plan_faces")
+    cell = np.empty(n.value, np.int32)
+    dr = np.empty(n.value, np.int8)
+    rel = np.empty(n.value, np.int8)
+    src = np.empty(n.value, np.int32)
+    _check(lib().ats_hierarchy_plan_faces(ctypes.byref(d), level, ctypes.byref(n), cell.ctypes.data_as(P),
+                                          dr.ctypes.data_as(P), rel.ctypes.data_as(P), src.ctypes.data_as(P)),
+           "ats_hierarchy_plan_faces")
+    return cell, dr, rel, src
+
+
 # ---------------------------------------------------------------------------
 # handle owners
 # ---------------------------------------------------------------------------
@@ -450,6 +531,29 @@ class Level:
     def close(self):
         if self.handle:
             ats_level_destroy(self.handle)
+            self.handle = None
+
+
+class Hierarchy:
+    def __init__(self, ctx: Context, levels, order=ATS_ORDER_FINE_FIRST):
+        self.ctx = ctx
+        self.levels = levels
+        self.handle = ats_hierarchy_create(ctx.handle, levels, order)
+
+    def set_state(self, level, E, K):
+        ats_hierarchy_set_state(self.handle, level, E, K)
+
+    def state(self, level):
+        out = np.empty(self.levels[level].n_cell)
+        ats_hierarchy_get_state(self.handle, level, out)
+        return out
+
+    def advance(self, level, dt, **opts):
+        return ats_level_advance(self.handle, level, dt, make_opts(**opts))
+
+    def close(self):
+        if self.handle:
+            ats_hierarchy_destroy(self.handle)
             self.handle = None
 
 

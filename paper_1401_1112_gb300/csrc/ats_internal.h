@@ -144,6 +144,13 @@ cudaError_t launch_apply64(const SolveDev *solve_host_copy, const double *x, dou
 
 int tick_blocks_per_sm(bool fp64, bool paper);
 
+// AMR coupling kernels (restriction of children, ghost gather of interface faces).
+cudaError_t launch_restrict(int n, const int32_t *cell, const int32_t *child, const double *Ef, const double *Kf,
+                            double *Ec, double *Kc, cudaStream_t st);
+cudaError_t launch_gather_faces(int n_face, const int8_t *src_rel, const int32_t *src_cell, const double *E_same,
+                                const double *K_same, const double *Ec_old, const double *Ec_new,
+                                const double *K_coarse, double theta, double *fE, double *fK, cudaStream_t st);
+
 // ---- layout (layout.cpp) ----
 struct Layout {
   int64_t n_oct = 0;
@@ -156,5 +163,25 @@ struct Layout {
 std::string build_layout(const ats_level_desc &d, Layout &out);
 
 void set_error(const std::string &msg);
+
+// Context services for other translation units (runtime.cpp).
+ats_status ctx_alloc(ats_context *ctx, size_t bytes, void **out);
+void ctx_free(ats_context *ctx, void *p);
+cudaStream_t ctx_stream(const ats_context *ctx);
+int ctx_device(const ats_context *ctx);
+
+// Interface faces of one level of a hierarchy (hierarchy.cpp): leaf faces whose
+// neighbour is a refined cell of the same level (rel = ATS_REL_FINER,
+// src_level = l) or a coarser leaf (rel = ATS_REL_COARSER, src_level = l - 1);
+// faces on the domain boundary are zero-flux walls (no entry).
+struct LevelFaces {
+  std::vector<int32_t> cell;
+  std::vector<int8_t> dir;
+  std::vector<int8_t> rel;
+  std::vector<int32_t> src_cell;   // cell index in the source level
+  std::vector<int32_t> restrict_cell;   // refined cells of this level ...
+  std::vector<int32_t> restrict_child;  // ... and their child oct at level l + 1
+};
+std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, LevelFaces &out);
 
 }  // namespace ats

@@ -1,0 +1,410 @@
+// AMR hierarchy and the level substep driver (adaptive time stepping).
+//
+// Sect. 2.2: a level l advances with its own time step, dt^l = dt^{l+1}_1 +
+// dt^{l+1}_2, finer levels first.  Sect. 3.3.1 (fine-to-coarse): a cell of
+// level l next to a coarser leaf sees a Dirichlet value, the coarse energy
+// held at E^n over both fine substeps, at distance 3 dx / 2 (factor 2/3).
+// Sect. 3.3.2 (coarse-to-fine): a cell next to a refined cell sees the
+// restriction of the refined cell (mean of its oct of children after the fine
+// update), factor 1, Dirichlet.  Each level is solved on its own (Sect. 3.1).
+//
+// Two orders are provided: ATS_ORDER_FINE_FIRST (the paper's) and
+// ATS_ORDER_COARSE_FIRST, where the coarse step is taken first and the fine
+// substeps see the coarse value linear in time across the coarse step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "ats_internal.h"
+
+using namespace ats;
+
+namespace {
+
+uint64_t key3(int64_t x, int64_t y, int64_t z) {
+  const int64_t off = int64_t(1) << 20;
+  return (uint64_t(x + off) << 42) | (uint64_t(y + off) << 21) | uint64_t(z + off);
+}
+
+int64_t floor_div2(int64_t v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+
+struct LevelIndex {
+  std::unordered_map<uint64_t, int32_t> oct;
+  const ats_level_desc *d = nullptr;
+  explicit LevelIndex(const ats_level_desc *desc) : d(desc) {
+    oct.reserve((size_t)desc->n_oct * 2);
+    for (int64_t o = 0; o < desc->n_oct; ++o)
+      oct.emplace(key3(desc->oct_xyz[3 * o], desc->oct_xyz[3 * o + 1], desc->oct_xyz[3 * o + 2]), (int32_t)o);
+  }
+  // cell index at this level of level cell coordinates (x, y, z), or -1
+  int64_t cell(int64_t x, int64_t y, int64_t z) const {
+    auto it = oct.find(key3(floor_div2(x), floor_div2(y), floor_div2(z)));
+    if (it == oct.end()) return -1;
+    const int c = (int)((x - 2 * floor_div2(x)) + 2 * (y - 2 * floor_div2(y)) + 4 * (z - 2 * floor_div2(z)));
+    return 8 * (int64_t)it->second + c;
+  }
+  bool leaf(int64_t cell) const { return !d->leaf_mask || ((d->leaf_mask[cell >> 3] >> (cell & 7)) & 1); }
+};
+
+constexpr int kAx[6] = {0, 0, 1, 1, 2, 2};
+constexpr int kSg[6] = {-1, 1, -1, 1, -1, 1};
+
+}  // namespace
+
+namespace ats {
+
+std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, LevelFaces &out) {
+  if (l < 0 || l >= n_levels) return "level out of range";
+  std::vector<LevelIndex> idx;
+  idx.reserve(n_levels);
+  for (int k = 0; k < n_levels; ++k) {
+    if (!levels[k].oct_xyz || levels[k].n_oct <= 0) return "level without octs";
+    idx.emplace_back(&levels[k]);
+  }
+  const ats_level_desc &d = levels[l];
+  out = LevelFaces();
+  for (int64_t o = 0; o < d.n_oct; ++o) {
+    for (int c = 0; c < 8; ++c) {
+      const int64_t cell = 8 * o + c;
+      if (!idx[l].leaf(cell)) continue;
+      const int64_t p[3] = {2 * (int64_t)d.oct_xyz[3 * o] + (c & 1), 2 * (int64_t)d.oct_xyz[3 * o + 1] + ((c >> 1) & 1),
+                            2 * (int64_t)d.oct_xyz[3 * o + 2] + ((c >> 2) & 1)};
+      for (int dir = 0; dir < 6; ++dir) {
+        int64_t q[3] = {p[0], p[1], p[2]};
+        q[kAx[dir]] += kSg[dir];
+        const int64_t j = idx[l].cell(q[0], q[1], q[2]);
+        if (j >= 0) {
+          if (idx[l].leaf(j)) continue;  // interior face
+          out.cell.push_back((int32_t)cell);
+          out.dir.push_back((int8_t)dir);
+          out.rel.push_back((int8_t)ATS_REL_FINER);
+          out.src_cell.push_back((int32_t)j);
+          continue;
+        }
+        if (l == 0) continue;  // outside the base level: domain wall (zero flux)
+        const int64_t m[3] = {floor_div2(q[0]), floor_div2(q[1]), floor_div2(q[2])};
+        const int64_t jc = idx[l - 1].cell(m[0], m[1], m[2]);
+        if (jc >= 0) {
+          if (!idx[l - 1].leaf(jc)) return "level " + std::to_string(l) + ": a refined coarse cell has no oct at this level";
+          out.cell.push_back((int32_t)cell);
+          out.dir.push_back((int8_t)dir);
+          out.rel.push_back((int8_t)ATS_REL_COARSER);
+          out.src_cell.push_back((int32_t)jc);
+          continue;
+        }
+        // no coarser cell either: 2:1 balance violated, or the domain wall
+        int64_t r[3] = {m[0], m[1], m[2]};
+        for (int k = l - 2; k >= 0; --k) {
+          for (int a = 0; a < 3; ++a) r[a] = floor_div2(r[a]);
+          if (idx[k].cell(r[0], r[1], r[2]) >= 0)
+            return "level " + std::to_string(l) + ": 2:1 balance violated (neighbour found at level " +
+                   std::to_string(k) + ")";
+        }
+      }
+    }
+  }
+  // refined cells of this level and their child octs
+  if (l + 1 < n_levels) {
+    const ats_level_desc &f = levels[l + 1];
+    for (int64_t o = 0; o < f.n_oct; ++o) {
+      const int64_t x = f.oct_xyz[3 * o], y = f.oct_xyz[3 * o + 1], z = f.oct_xyz[3 * o + 2];
+      const int64_t R = idx[l].cell(x, y, z);
+      if (R < 0) return "level " + std::to_string(l + 1) + ": oct without a parent cell";
+      if (idx[l].leaf(R)) return "level " + std::to_string(l) + ": a cell with children is marked as leaf";
+      out.restrict_cell.push_back((int32_t)R);
+      out.restrict_child.push_back((int32_t)o);
+    }
+  }
+  return std::string();
+}
+
+}  // namespace ats
+
+struct HLevel {
+  ats_level *lvl = nullptr;
+  int64_t N = 0, n_face = 0, n_restrict = 0;
+  double *E = nullptr, *E_prev = nullptr, *K = nullptr, *fE = nullptr, *fK = nullptr;
+  int8_t *src_rel = nullptr;  // 0 same level (FINER), 1 coarser
+  int32_t *src_cell = nullptr, *r_cell = nullptr, *r_child = nullptr;
+};
+
+struct ats_hierarchy {
+  ats_context *ctx = nullptr;
+  int order = ATS_ORDER_FINE_FIRST;
+  std::vector<HLevel> lv;
+};
+
+namespace {
+
+#define H_TRY(expr)                                                                   \
+  do {                                                                                \
+    cudaError_t _e = (expr);                                                          \
+    if (_e != cudaSuccess) {                                                          \
+      set_error(std::string("CUDA error: ") + cudaGetErrorString(_e) + " at " #expr); \
+      return ATS_ERR_CUDA;                                                            \
+    }                                                                                 \
+  } while (0)
+
+void hierarchy_free(ats_hierarchy *H) {
+  for (HLevel &h : H->lv) {
+    void *ptrs[] = {h.E, h.E_prev, h.K, h.fE, h.fK, h.src_rel, h.src_cell, h.r_cell, h.r_child};
+    for (void *p : ptrs) ctx_free(H->ctx, p);
+    if (h.lvl) ats_level_destroy(h.lvl);
+  }
+  delete H;
+}
+
+// restriction of level l+1 into the refined cells of level l
+ats_status restrict_into(ats_hierarchy *H, int l) {
+  if (l + 1 >= (int)H->lv.size()) return ATS_OK;
+  HLevel &c = H->lv[l], &f = H->lv[l + 1];
+  H_TRY(launch_restrict((int)c.n_restrict, c.r_cell, c.r_child, f.E, f.K, c.E, c.K, ctx_stream(H->ctx)));
+  return ATS_OK;
+}
+
+// one implicit solve of level l over dt; coarser values at theta of the
+// coarser level's step
+ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const ats_solve_opts *opts,
+                       ats_solve_stats *acc) {
+  HLevel &h = H->lv[l];
+  cudaStream_t st = ctx_stream(H->ctx);
+  ats_status s = restrict_into(H, l);
+  if (s != ATS_OK) return s;
+  const HLevel *coarse = l > 0 ? &H->lv[l - 1] : nullptr;
+  // fine first: the coarser level has not moved, its current E is E^n;
+  // coarse first: interpolate between its E^n (E_prev) and E^{n+1} (E)
+  const double *ec_old = !coarse ? nullptr : (H->order == ATS_ORDER_FINE_FIRST ? coarse->E : coarse->E_prev);
+  H_TRY(launch_gather_faces((int)h.n_face, h.src_rel, h.src_cell, h.E, h.K, ec_old, coarse ? coarse->E : nullptr,
+                            coarse ? coarse->K : nullptr, H->order == ATS_ORDER_FINE_FIRST ? 0.0 : theta, h.fE,
+                            h.fK, st));
+  H_TRY(cudaMemcpyAsync(h.E_prev, h.E, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, st));
+  ats_coef_desc c;
+  std::memset(&c, 0, sizeof(c));
+  c.dt = dt;
+  c.mem = ATS_MEM_DEVICE;
+  c.K = h.K;
+  c.E_old = h.E_prev;
+  c.face_K = h.n_face ? h.fK : nullptr;
+  c.face_E = h.n_face ? h.fE : nullptr;
+  if ((s = ats_level_build_operator(h.lvl, &c)) != ATS_OK) return s;
+  ats_solve_opts o;
+  if (opts) o = *opts;
+  else ats_default_opts(&o);
+  o.mem = ATS_MEM_DEVICE;
+  ats_solve_stats st1;
+  std::memset(&st1, 0, sizeof(st1));
+  s = ats_solve(h.lvl, nullptr, h.E, &o, &st1);
+  if (acc) {
+    acc->iterations += st1.iterations;
+    acc->refinements += st1.refinements;
+    acc->ticks += st1.ticks;
+    acc->r0_norm = std::max(acc->r0_norm, st1.r0_norm);
+    acc->res_norm = std::max(acc->res_norm, st1.res_norm);
+    acc->x_norm = std::max(acc->x_norm, st1.x_norm);
+    acc->err_bound = std::max(acc->err_bound, st1.err_bound);
+    if (acc->status == ATS_OK) acc->status = st1.status;
+  }
+  return s;
+}
+
+// advance level l (and, recursively, the finer ones) by dt; theta0/theta1:
+// the coarser level's time fraction at the start / end of this step
+ats_status advance(ats_hierarchy *H, int l, double dt, double theta1, const ats_solve_opts *opts,
+                   ats_solve_stats *acc) {
+  const bool has_fine = l + 1 < (int)H->lv.size();
+  ats_status s;
+  if (H->order == ATS_ORDER_FINE_FIRST) {
+    if (has_fine) {
+      if ((s = advance(H, l + 1, 0.5 * dt, 0.0, opts, acc)) != ATS_OK) return s;
+      if ((s = advance(H, l + 1, 0.5 * dt, 0.0, opts, acc)) != ATS_OK) return s;
+    }
+    // coarser value held at E^n (the coarser level has not moved yet)
+    return solve_level(H, l, dt, 0.0, opts, acc);
+  }
+  // coarse first: this level, then two substeps of the finer level with this
+  // level's value linear in time across [t^n, t^n + dt]
+  if ((s = solve_level(H, l, dt, theta1, opts, acc)) != ATS_OK) return s;
+  if (has_fine) {
+    if ((s = advance(H, l + 1, 0.5 * dt, 0.5, opts, acc)) != ATS_OK) return s;
+    if ((s = advance(H, l + 1, 0.5 * dt, 1.0, opts, acc)) != ATS_OK) return s;
+    if ((s = restrict_into(H, l)) != ATS_OK) return s;
+  }
+  return ATS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ats_status ats_hierarchy_plan_faces(const ats_hierarchy_desc *desc, int level, int64_t *n_face, int32_t *face_cell,
+                                    int8_t *face_dir, int8_t *face_rel, int32_t *src_cell) {
+  if (!desc || !n_face || desc->n_levels <= 0 || !desc->levels) {
+    set_error("null argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  LevelFaces lf;
+  std::string msg = plan_level_faces(desc->levels, desc->n_levels, level, lf);
+  if (!msg.empty()) {
+    set_error(msg);
+    return ATS_ERR_INVALID_ARG;
+  }
+  *n_face = (int64_t)lf.cell.size();
+  if (face_cell) std::copy(lf.cell.begin(), lf.cell.end(), face_cell);
+  if (face_dir) std::copy(lf.dir.begin(), lf.dir.end(), face_dir);
+  if (face_rel) std::copy(lf.rel.begin(), lf.rel.end(), face_rel);
+  if (src_cell) std::copy(lf.src_cell.begin(), lf.src_cell.end(), src_cell);
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc, ats_hierarchy **out) {
+  if (!ctx || !desc || !out || desc->n_levels <= 0 || !desc->levels) {
+    set_error("null argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (desc->order != ATS_ORDER_FINE_FIRST && desc->order != ATS_ORDER_COARSE_FIRST) {
+    set_error("bad order");
+    return ATS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  for (int l = 1; l < desc->n_levels; ++l) {
+    if (std::fabs(desc->levels[l].dx * 2.0 - desc->levels[l - 1].dx) > 1e-12 * desc->levels[l - 1].dx) {
+      set_error("each level must halve dx");
+      return ATS_ERR_INVALID_ARG;
+    }
+  }
+  ats_hierarchy *H = new (std::nothrow) ats_hierarchy();
+  if (!H) return ATS_ERR_OOM;
+  H->ctx = ctx;
+  H->order = desc->order;
+  H->lv.resize(desc->n_levels);
+  cudaStream_t st = ctx_stream(ctx);
+  for (int l = 0; l < desc->n_levels; ++l) {
+    LevelFaces lf;
+    std::string msg = plan_level_faces(desc->levels, desc->n_levels, l, lf);
+    if (!msg.empty()) {
+      set_error(msg);
+      hierarchy_free(H);
+      return ATS_ERR_INVALID_ARG;
+    }
+    HLevel &h = H->lv[l];
+    ats_level_desc d = desc->levels[l];
+    const int64_t nf = (int64_t)lf.cell.size();
+    std::vector<int8_t> kind(nf, ATS_FACE_DIRICHLET);
+    std::vector<double> alpha(nf, 1.0);
+    d.n_face = nf;
+    d.face_cell = lf.cell.data();
+    d.face_dir = lf.dir.data();
+    d.face_kind = kind.data();
+    d.face_rel = lf.rel.data();
+    d.face_alpha = alpha.data();
+    ats_status s = ats_level_create(ctx, &d, &h.lvl);
+    if (s != ATS_OK) {
+      hierarchy_free(H);
+      return s;
+    }
+    h.N = 8 * d.n_oct;
+    h.n_face = nf;
+    h.n_restrict = (int64_t)lf.restrict_cell.size();
+    void *p;
+    auto alloc = [&](size_t bytes, void **dst) {
+      ats_status r = ctx_alloc(ctx, bytes ? bytes : 16, &p);
+      *dst = p;
+      return r;
+    };
+    if ((s = alloc(sizeof(double) * h.N, (void **)&h.E)) != ATS_OK ||
+        (s = alloc(sizeof(double) * h.N, (void **)&h.E_prev)) != ATS_OK ||
+        (s = alloc(sizeof(double) * h.N, (void **)&h.K)) != ATS_OK ||
+        (s = alloc(sizeof(double) * nf, (void **)&h.fE)) != ATS_OK ||
+        (s = alloc(sizeof(double) * nf, (void **)&h.fK)) != ATS_OK ||
+        (s = alloc(sizeof(int8_t) * nf, (void **)&h.src_rel)) != ATS_OK ||
+        (s = alloc(sizeof(int32_t) * nf, (void **)&h.src_cell)) != ATS_OK ||
+        (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_cell)) != ATS_OK ||
+        (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_child)) != ATS_OK) {
+      hierarchy_free(H);
+      return s;
+    }
+    std::vector<int8_t> srel(nf);
+    for (int64_t f = 0; f < nf; ++f) srel[f] = lf.rel[f] == ATS_REL_COARSER ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    if (nf) {
+      e = cudaMemcpyAsync(h.src_rel, srel.data(), nf, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h.src_cell, lf.src_cell.data(), 4 * nf, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess && h.n_restrict) {
+      e = cudaMemcpyAsync(h.r_cell, lf.restrict_cell.data(), 4 * h.n_restrict, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.r_child, lf.restrict_child.data(), 4 * h.n_restrict, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error(cudaGetErrorString(e));
+      hierarchy_free(H);
+      return ATS_ERR_CUDA;
+    }
+  }
+  *out = H;
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_destroy(ats_hierarchy *H) {
+  if (!H) return ATS_ERR_INVALID_ARG;
+  cudaStreamSynchronize(ctx_stream(H->ctx));
+  hierarchy_free(H);
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_level(ats_hierarchy *H, int level, ats_level **out) {
+  if (!H || !out || level < 0 || level >= (int)H->lv.size()) return ATS_ERR_INVALID_ARG;
+  *out = H->lv[level].lvl;
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_set_state(ats_hierarchy *H, int level, const double *E, const double *K, int mem) {
+  if (!H || level < 0 || level >= (int)H->lv.size() || !E || !K) return ATS_ERR_INVALID_ARG;
+  HLevel &h = H->lv[level];
+  cudaStream_t st = ctx_stream(H->ctx);
+  const cudaMemcpyKind k = mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  H_TRY(cudaMemcpyAsync(h.E, E, sizeof(double) * h.N, k, st));
+  H_TRY(cudaMemcpyAsync(h.E_prev, E, sizeof(double) * h.N, k, st));
+  H_TRY(cudaMemcpyAsync(h.K, K, sizeof(double) * h.N, k, st));
+  H_TRY(cudaStreamSynchronize(st));
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_get_state(ats_hierarchy *H, int level, double *E, int mem) {
+  if (!H || level < 0 || level >= (int)H->lv.size() || !E) return ATS_ERR_INVALID_ARG;
+  // refined cells report the restriction of their children
+  for (int l = (int)H->lv.size() - 2; l >= level; --l) {
+    ats_status s = restrict_into(H, l);
+    if (s != ATS_OK) return s;
+  }
+  HLevel &h = H->lv[level];
+  cudaStream_t st = ctx_stream(H->ctx);
+  H_TRY(cudaMemcpyAsync(E, h.E, sizeof(double) * h.N,
+                        mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  H_TRY(cudaStreamSynchronize(st));
+  return ATS_OK;
+}
+
+ats_status ats_level_advance(ats_hierarchy *H, int level, double dt, const ats_solve_opts *opts,
+                             ats_solve_stats *stats) {
+  if (!H || level < 0 || level >= (int)H->lv.size() || !(dt > 0.0)) {
+    set_error("ats_level_advance: bad argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  ats_solve_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  acc.status = ATS_OK;
+  cudaSetDevice(ctx_device(H->ctx));
+  ats_status s = advance(H, level, dt, 1.0, opts, &acc);
+  if (stats) *stats = acc;
+  return s;
+}
+
+}  // extern "C"

@@ -76,10 +76,10 @@ struct Acc<float> {
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
-// Block reduction of kNumPartials doubles (slot 2 optionally a max), fixed
+// Block reduction of kNumPartials doubles (slot 3 optionally a max), fixed
 // order.  Result valid in thread 0.  Used where the partials are FP64 values
 // (refinement passes, the FP64 bulk path, the per-solve reduction).
-template <bool kSlot2Max>
+template <bool kSlot3Max>
 __device__ __forceinline__ void block_reduce(double (&v)[kNumPartials],
                                              double (*red)[kNumPartials]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -88,7 +88,7 @@ __device__ __forceinline__ void block_reduce(double (&v)[kNumPartials],
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       const double o = __shfl_down_sync(kFull, v[k], off);
-      v[k] = (kSlot2Max && k == 2) ? fmax(v[k], o) : v[k] + o;
+      v[k] = (kSlot3Max && k == 3) ? fmax(v[k], o) : v[k] + o;
     }
   }
   if (lane == 0) {
@@ -100,7 +100,7 @@ __device__ __forceinline__ void block_reduce(double (&v)[kNumPartials],
 #pragma unroll
     for (int k = 0; k < kNumPartials; ++k) {
       double a = red[0][k];
-      for (int w = 1; w < kThreads / 32; ++w) a = (kSlot2Max && k == 2) ? fmax(a, red[w][k]) : a + red[w][k];
+      for (int w = 1; w < kThreads / 32; ++w) a = (kSlot3Max && k == 3) ? fmax(a, red[w][k]) : a + red[w][k];
       v[k] = a;
     }
   }
@@ -127,40 +127,43 @@ __device__ __forceinline__ void warp_reduce_acc(Acc<double> &a) {
   for (int off = 16; off > 0; off >>= 1) a.s += __shfl_down_sync(kFull, a.s, off);
 }
 
-// Block reduction of up to two dot accumulators and one FP64 max into the
-// kNumPartials doubles of thread 0 (slots 0, 1 and 2; slot 3 = 0).
+// Block reduction of up to three dot accumulators and one FP64 max into the
+// kNumPartials doubles of thread 0 (slots 0, 1, 2 and the max in slot 3).
 template <typename T>
-__device__ __forceinline__ void block_reduce_acc(Acc<T> &a0, Acc<T> &a1, double mx,
+__device__ __forceinline__ void block_reduce_acc(Acc<T> &a0, Acc<T> &a1, Acc<T> &a2, double mx,
                                                  double (&v)[kNumPartials],
                                                  double (*red)[kNumPartials]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   warp_reduce_acc(a0);
   warp_reduce_acc(a1);
+  warp_reduce_acc(a2);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(kFull, mx, off));
   if (lane == 0) {
     red[warp][0] = a0.get();
     red[warp][1] = a1.get();
-    red[warp][2] = mx;
+    red[warp][2] = a2.get();
+    red[warp][3] = mx;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s0 = red[0][0], s1 = red[0][1], m = red[0][2];
+    double s0 = red[0][0], s1 = red[0][1], s2 = red[0][2], m = red[0][3];
     for (int w = 1; w < kThreads / 32; ++w) {
       s0 += red[w][0];
       s1 += red[w][1];
-      m = fmax(m, red[w][2]);
+      s2 += red[w][2];
+      m = fmax(m, red[w][3]);
     }
     v[0] = s0;
     v[1] = s1;
-    v[2] = m;
-    v[3] = 0.0;
+    v[2] = s2;
+    v[3] = m;
   }
   __syncthreads();
 }
 
 // Reduce the partials of all items of solve s (called by the last CTA).
-template <bool kSlot2Max>
+template <bool kSlot3Max>
 __device__ __forceinline__ void solve_reduce(const double *partials, int item_begin, int n_items,
                                              double (&out)[kNumPartials],
                                              double (*red)[kNumPartials]) {
@@ -169,10 +172,10 @@ __device__ __forceinline__ void solve_reduce(const double *partials, int item_be
 #pragma unroll
     for (int k = 0; k < kNumPartials; ++k) {
       const double p = __ldcg(partials + (size_t)it * kNumPartials + k);
-      v[k] = (kSlot2Max && k == 2) ? fmax(v[k], p) : v[k] + p;
+      v[k] = (kSlot3Max && k == 3) ? fmax(v[k], p) : v[k] + p;
     }
   }
-  block_reduce<kSlot2Max>(v, red);
+  block_reduce<kSlot3Max>(v, red);
 #pragma unroll
   for (int k = 0; k < kNumPartials; ++k) out[k] = v[k];
 }
@@ -438,58 +441,55 @@ __device__ __forceinline__ void upd_inner_oct(const SolveDev &sd, int o, T h, T 
   st8(e + 8 * o, ev);
 }
 
-// k_op, refinement phase, out-of-oct face DIR (FP64 flux sums; bulk-precision
-// diagonal for the preconditioner).
+// k_ref, out-of-oct face DIR: FP64 flux sums (K_i + K_j)(x_i - x_j) and the
+// bulk-precision diagonal for the preconditioner.
 template <int DIR, typename T>
-__device__ __forceinline__ void ref_face(int n, const SolveDev &sd, const T *__restrict__ e,
-                                         const T *__restrict__ KT, T hT, const double (&K)[8],
-                                         const T (&KTo)[8], const double (&xv)[8], double (&acc)[8],
-                                         T (&dsT)[8]) {
+__device__ __forceinline__ void ref_face(int n, const SolveDev &sd, const T *__restrict__ KT, T hT,
+                                         const double (&K)[8], const T (&KTo)[8],
+                                         const double (&xv)[8], double (&acc)[8], T (&dsT)[8]) {
   constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
+  constexpr bool mixed = sizeof(T) != sizeof(double);
   if (n < 0) return;
   double Kn[8], Xn[8];
-  T En[8], KTn[8];
+  T KTn[8];
   ld_face<A, NB>(sd.K64 + 8 * n, Kn);
   ld_face<A, NB>(sd.x64 + 8 * n, Xn);
-  ld_face<A, NB>(e + 8 * n, En);
-  if (sizeof(T) != sizeof(double)) ld_face<A, NB>(KT + 8 * n, KTn);
+  if (mixed) ld_face<A, NB>(KT + 8 * n, KTn);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (((c >> A) & 1) != S) continue;
     const int j = c ^ (1 << A);
     if (Kn[j] >= 0.0) {
-      const double xn = Xn[j] + (double)En[j];
-      acc[c] = fma(K[c] + Kn[j], xv[c] - xn, acc[c]);
-      if (sizeof(T) != sizeof(double)) dsT[c] += hT * (KTo[c] + KTn[j]);
-      else dsT[c] += (T)(K[c] + Kn[j]);
+      const double Ks = K[c] + Kn[j];
+      acc[c] = fma(Ks, xv[c] - Xn[j], acc[c]);
+      if (mixed) dsT[c] += hT * (KTo[c] + KTn[j]);
+      else dsT[c] += (T)Ks;
     }
   }
 }
 
-// k_op, refinement phase: x' = x + e, r = b - (I + dt A) x' in FP64 with the
-// FP64 K, xd and b, written as r = b - (1 + xd) x' - h sum_f (K_i + K_j)(x'_i - x'_j);
-// z = r / D_T in the bulk precision; partials r.r, x'.x', r.z.
+// k_ref: true residual r = b - (I + dt A) x in FP64 with the FP64 K, xd and b,
+// written as r = b - (1 + xd) x - h sum_f (K_i + K_j)(x_i - x_j) (every
+// product a DFMA); z = r / D_T in the bulk precision.  The correction e was
+// added to x by k_op in this tick.  Norms for the stopping test (r.r, x.x)
+// and r.z are accumulated with compensated bulk-precision dots.
 template <typename T>
-__device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, double &rr, double &xx,
-                                              double &rz) {
-  const T *__restrict__ e = (const T *)sd.e;
+__device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool want_x, Acc<T> &rr,
+                                              Acc<T> &xx, Acc<T> &rz) {
   const T *__restrict__ KT = (const T *)sd.KT;
   T *z = (T *)sd.z;
-  const bool mixed = sizeof(T) != sizeof(double);
+  constexpr bool mixed = sizeof(T) != sizeof(double);
   const double h = sd.h;
   const T hT = (T)sd.h;
   int nb[6];
   load_nbr6(sd.nbr, o, nb);
   const int rec = __ldg(sd.xrec + o);
   double K[8], xv[8], b[8];
-  T ev[8], KTo[8];
+  T KTo[8];
   ld8_ro(sd.K64 + 8 * o, K);
-  ld8_rw(sd.x64 + 8 * o, xv);
-  ld8_ro(e + 8 * o, ev);
+  ld8_ro(sd.x64 + 8 * o, xv);
   ld8_ro(sd.b64 + 8 * o, b);
   if (mixed) ld8_ro(KT + 8 * o, KTo);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) xv[c] += (double)ev[c];
   double acc[8];
   T dsT[8];
 #pragma unroll
@@ -497,7 +497,6 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, double 
     acc[c] = 0.0;
     dsT[c] = T(0);
   }
-  // in-oct pairs: flux (K_c + K_d)(x_c - x_d) once per pair
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -506,52 +505,51 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, double 
       const int d = c | (1 << a);
       if (K[c] >= 0.0 && K[d] >= 0.0) {
         const double Ks = K[c] + K[d];
-        const double fl = Ks * (xv[c] - xv[d]);
-        acc[c] += fl;
-        acc[d] -= fl;
+        const double df = xv[c] - xv[d];
+        acc[c] = fma(Ks, df, acc[c]);
+        acc[d] = fma(-Ks, df, acc[d]);
         const T Ct = mixed ? hT * (KTo[c] + KTo[d]) : (T)Ks;
         dsT[c] += Ct;
         dsT[d] += Ct;
       }
     }
   }
-  ref_face<0>(nb[0], sd, e, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<1>(nb[1], sd, e, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<2>(nb[2], sd, e, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<3>(nb[3], sd, e, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<4>(nb[4], sd, e, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<5>(nb[5], sd, e, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<0>(nb[0], sd, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<1>(nb[1], sd, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<2>(nb[2], sd, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<3>(nb[3], sd, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<4>(nb[4], sd, KT, hT, K, KTo, xv, acc, dsT);
+  ref_face<5>(nb[5], sd, KT, hT, K, KTo, xv, acc, dsT);
   double xd[8];
   T xdT[8];
   if (rec >= 0) {
     ld8_ro(sd.xd64 + 8 * rec, xd);
     if (mixed) ld8_ro((const T *)sd.xdT + 8 * rec, xdT);
-  } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      xd[c] = 0.0;
-      xdT[c] = T(0);
-    }
   }
   T zo[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const bool leaf = K[c] >= 0.0;
-    const double r = fma(-h, acc[c], fma(-(1.0 + xd[c]), xv[c], b[c]));
+    const double base = rec >= 0 ? fma(-(1.0 + xd[c]), xv[c], b[c]) : b[c] - xv[c];
+    const double r = fma(-h, acc[c], base);
+    const T rT = (T)r;
     T zc;
     if (mixed) {
-      const T dT = T(1) + xdT[c] + dsT[c];
-      zc = (T)r / dT;
+      const T dT = T(1) + (rec >= 0 ? xdT[c] : T(0)) + dsT[c];
+      zc = rT / dT;
     } else {
       // FP64 bulk: dsT holds the plain K sums; D = 1 + xd + h sum
-      const double d = 1.0 + xd[c] + h * (double)dsT[c];
+      const double d = 1.0 + (rec >= 0 ? xd[c] : 0.0) + h * (double)dsT[c];
       zc = (T)(r / d);
     }
     zo[c] = leaf ? zc : T(0);
     if (leaf) {
-      rr = fma(r, r, rr);
-      xx = fma(xv[c], xv[c], xx);
-      rz = fma(r, (double)zc, rz);
+      rr.add(rT, rT);
+      rz.add(rT, zc);
+      if (want_x) {
+        const T xT = (T)xv[c];
+        xx.add(xT, xT);
+      }
     }
   }
   st8(z + 8 * o, zo);
@@ -670,10 +668,21 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(const Solv
     Acc<T> pq, none;
     for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
       op_inner_oct<T>(sd, o, h, beta, first, pold, pnew, pq);
-    block_reduce_acc<T>(pq, none, 0.0, v, red);
+    block_reduce_acc<T>(pq, none, none, 0.0, v, red);
     if (cells && threadIdx.x == 0) atomicAdd(cells + 0, (unsigned long long)item.n_oct * 8);
     if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
     op_epilogue(sd, scs, kInner, partials, red);
+  }
+  // refinement items: fold the correction of the finished inner solve into x
+  // (x += e, e = 0) before k_ref forms the true residual
+  const int n_ref = __ldcg(&ctl->count[cur][kRefine]);
+  const int32_t *rlist = phase_list(lists, n_items, cur, kRefine);
+  for (int li = blockIdx.x; li < n_ref; li += gridDim.x) {
+    const WorkItem item = items[__ldcg(rlist + li)];
+    const SolveDev &sd = solves[item.solve];
+    const int oct_end = item.oct_begin + item.n_oct;
+    for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads) upd_refine_oct<T>(sd, o);
+    if (cells && threadIdx.x == 0) atomicAdd(cells + 3, (unsigned long long)item.n_oct * 8);
   }
 }
 
@@ -698,13 +707,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_ref(const SolveDev *__restrict_
     const SolveDev &sd = solves[s];
     const int oct_end = item.oct_begin + item.n_oct;
     double v[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
-    double rr = 0.0, xx = 0.0, rz = 0.0;
+    Acc<T> rr, xx, rz;
+    const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
     for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
-      op_refine_oct<T>(sd, o, rr, xx, rz);
-    v[0] = rr;
-    v[1] = xx;
-    v[2] = rz;
-    block_reduce<false>(v, red);
+      op_refine_oct<T>(sd, o, want_x, rr, xx, rz);
+    block_reduce_acc<T>(rr, xx, rz, 0.0, v, red);
     if (cells && threadIdx.x == 0) atomicAdd(cells + 1, (unsigned long long)item.n_oct * 8);
     if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
     op_epilogue(sd, scs, kRefine, partials, red);
@@ -744,11 +751,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(const Sol
       double maxchg = 0.0;
       for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
         upd_inner_oct<T, kPaper>(sd, o, h, alpha, p, rz, rr, maxchg);
-      block_reduce_acc<T>(rz, rr, maxchg, v, red);
+      Acc<T> none;
+      block_reduce_acc<T>(rz, rr, none, maxchg, v, red);
       if (cells && threadIdx.x == 0) atomicAdd(cells + 2, (unsigned long long)item.n_oct * 8);
-    } else {
-      for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads) upd_refine_oct<T>(sd, o);
-      if (cells && threadIdx.x == 0) atomicAdd(cells + 3, (unsigned long long)item.n_oct * 8);
     }
     if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
 
@@ -762,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(const Sol
         scs->inner_iters += 1;
         const double rz_new = tot[0];
         const double rnorm_in = sqrt(tot[1]);
-        scs->maxchg = tot[2];
+        scs->maxchg = tot[3];
         if (scs->status == ATS_ERR_BREAKDOWN || !isfinite(rz_new) || rz_new < 0.0) {
           scs->status = ATS_ERR_BREAKDOWN;
           scs->phase = kDone;
@@ -772,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(const Sol
           scs->rz = rz_new;
           scs->first = 0;
           scs->pcur ^= 1;
-          const bool conv = (rnorm_in <= scs->inner_target) && (!kPaper || tot[2] < sd.tol);
+          const bool conv = (rnorm_in <= scs->inner_target) && (!kPaper || tot[3] < sd.tol);
           if (conv || rz_new == 0.0) {
             scs->phase = kRefine;
           } else if (scs->iters >= sd.max_iter) {
@@ -919,6 +924,66 @@ cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st) {
   const int threads = 256;
   const int64_t blocks = (N + threads - 1) / threads;
   k_coef_build<<<(unsigned)blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// AMR level coupling (Sect. 3.3.1-3.3.2): restriction and ghost gather
+// ---------------------------------------------------------------------------
+
+// Restriction: the value of a refined cell R of level l is the mean of its
+// eight children (the child oct at level l+1), for E and for K.
+__global__ void k_restrict(int n, const int32_t *__restrict__ cell, const int32_t *__restrict__ child,
+                           const double *__restrict__ Ef, const double *__restrict__ Kf,
+                           double *__restrict__ Ec, double *__restrict__ Kc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t co = (int64_t)child[i] * 8;
+  double se = 0.0, sk = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    se += Ef[co + c];
+    sk += Kf[co + c];
+  }
+  Ec[cell[i]] = se * 0.125;
+  Kc[cell[i]] = sk * 0.125;
+}
+
+// Ghost gather: the neighbour value and K of every interface face of a level.
+// rel 0: a refined cell of the same level (its restricted value);
+// rel 1: a coarser leaf, at time t^n + theta (t^{n+1} - t^n) of the coarser
+// step (theta = 0 holds the coarse value at E^n).
+__global__ void k_gather_faces(int n_face, const int8_t *__restrict__ src_rel, const int32_t *__restrict__ src_cell,
+                               const double *__restrict__ E_same, const double *__restrict__ K_same,
+                               const double *__restrict__ Ec_old, const double *__restrict__ Ec_new,
+                               const double *__restrict__ K_coarse, double theta, double *__restrict__ fE,
+                               double *__restrict__ fK) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_face) return;
+  const int64_t j = src_cell[f];
+  if (src_rel[f] == 0) {
+    fE[f] = E_same[j];
+    fK[f] = K_same[j];
+  } else {
+    const double e0 = Ec_old[j];
+    fE[f] = theta == 0.0 ? e0 : e0 + theta * (Ec_new[j] - e0);
+    fK[f] = K_coarse[j];
+  }
+}
+
+cudaError_t launch_restrict(int n, const int32_t *cell, const int32_t *child, const double *Ef, const double *Kf,
+                            double *Ec, double *Kc, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_restrict<<<(n + 255) / 256, 256, 0, st>>>(n, cell, child, Ef, Kf, Ec, Kc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_faces(int n_face, const int8_t *src_rel, const int32_t *src_cell, const double *E_same,
+                                const double *K_same, const double *Ec_old, const double *Ec_new,
+                                const double *K_coarse, double theta, double *fE, double *fK, cudaStream_t st) {
+  if (n_face <= 0) return cudaSuccess;
+  k_gather_faces<<<(n_face + 255) / 256, 256, 0, st>>>(n_face, src_rel, src_cell, E_same, K_same, Ec_old, Ec_new,
+                                                        K_coarse, theta, fE, fK);
   return cudaGetLastError();
 }
 

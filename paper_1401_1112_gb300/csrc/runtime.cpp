@@ -128,6 +128,13 @@ cudaMemcpyKind kind_of(int mem, bool to_device) {
 
 }  // namespace
 
+namespace ats {
+ats_status ctx_alloc(ats_context *ctx, size_t bytes, void **out) { return dev_alloc(ctx, bytes, out); }
+void ctx_free(ats_context *ctx, void *p) { dev_free(ctx, p); }
+cudaStream_t ctx_stream(const ats_context *ctx) { return ctx->stream; }
+int ctx_device(const ats_context *ctx) { return ctx->device; }
+}  // namespace ats
+
 // ---------------------------------------------------------------------------
 // solve plan: work list, per-solve device descriptors, graph
 // ---------------------------------------------------------------------------
@@ -466,19 +473,17 @@ ats_status plan_collect_events(Plan *P) {
   return ATS_OK;
 }
 
-// Algorithmic bytes per cell of each kernel/phase (compulsory traffic of the
-// vectors and coefficients; neighbour tables and records not counted).
+// Algorithmic bytes per cell of each kernel and phase: the compulsory traffic
+// of the vectors and coefficients (neighbour tables and records not counted).
+//   k_op, CG:        read z, p_old, K_T; write p_new                (4 words)
+//   k_op, x += e:    read/write x (FP64) and e                        (16 B + 2 words)
+//   k_ref:           read K64, x64, b64 (+ K_T when mixed); write z   (24 B + 1-2 words)
+//   k_upd, CG:       read p, K_T, z, e; write z, e                   (6 words)
 void plan_bytes(const Plan *P, const unsigned long long cells[4], double *op_b, double *ref_b, double *upd_b) {
   const double w = P->fp64 ? 8.0 : 4.0;
-  // op inner: read z, p_old, K; write p_new.   op refine: read x64, e, K64, K_T, b64; write z
-  const double op_inner = 4 * w;
-  const double op_refine = 8 + w + 8 + (P->fp64 ? 0 : w) + 8 + w;
-  // upd inner: read p, K, z, e; write z, e.    upd refine: read/write x64 and e
-  const double upd_inner = 6 * w;
-  const double upd_refine = 16 + 2 * w;
-  *op_b = op_inner * cells[0];
-  *ref_b = op_refine * cells[1];
-  *upd_b = upd_inner * cells[2] + upd_refine * cells[3];
+  *op_b = 4 * w * cells[0] + (16 + 2 * w) * cells[3];
+  *ref_b = (24 + (P->fp64 ? 0 : w) + w) * cells[1];
+  *upd_b = 6 * w * cells[2];
 }
 
 // Run a plan to completion.  x_inout[k] (host or device per opts.mem) or the

@@ -333,3 +333,103 @@ def random_amr_level(seed: int, n_box: int = 3, refine_frac: float = 0.2, dx: fl
 def split_round_robin(n_units: int, world: int, rank: int) -> List[int]:
     """Units owned by ``rank`` when independent solves are sharded over ranks."""
     return list(range(rank, n_units, world))
+
+
+# ---------------------------------------------------------------------------
+# AMR hierarchies (levels of octs; level l+1 octs = refined cells of level l)
+# ---------------------------------------------------------------------------
+
+def _cells_of_octs(oct_xyz: np.ndarray) -> np.ndarray:
+    c = np.arange(8)
+    bits = np.stack([c & 1, (c >> 1) & 1, (c >> 2) & 1], axis=1)
+    return (2 * oct_xyz.astype(np.int64)[:, None, :] + bits[None]).reshape(-1, 3)
+
+
+def hierarchy_from_refined(base_octs: np.ndarray, refined_per_level, dx0: float):
+    """Levels from the base oct list and, per level l, the set of refined
+    cells (int64 [m, 3] level-l cell coordinates).  Returns a list of
+    LevelDesc (Morton-ordered octs, leaf masks, no face descriptors)."""
+    levels = []
+    octs = base_octs[morton_sort(base_octs)].astype(np.int32)
+    for l in range(len(refined_per_level) + 1):
+        ref = refined_per_level[l] if l < len(refined_per_level) else np.zeros((0, 3), np.int64)
+        cells = _cells_of_octs(octs)
+        if len(ref):
+            refset = set(map(tuple, np.asarray(ref, dtype=np.int64)))
+            is_ref = np.array([tuple(c) in refset for c in cells], dtype=bool)
+        else:
+            is_ref = np.zeros(len(cells), dtype=bool)
+        leaf = np.zeros(len(octs), dtype=np.uint8)
+        for c in range(8):
+            leaf |= ((~is_ref.reshape(-1, 8)[:, c]).astype(np.uint8) << np.uint8(c))
+        empty = np.zeros(0)
+        levels.append(LevelDesc(octs, leaf, dx0 / 2 ** l, empty.astype(np.int32), empty.astype(np.int8),
+                                empty.astype(np.int8), empty.astype(np.int8), empty.astype(np.float64)))
+        if len(ref):
+            nxt = np.asarray(ref, dtype=np.int64).astype(np.int32)
+            octs = nxt[morton_sort(nxt)]
+    return levels
+
+
+def balance_refinement(existing_cells: np.ndarray, want: np.ndarray, domain_cells: int) -> np.ndarray:
+    """Keep only the wanted refined cells whose face neighbours inside the
+    domain all exist at this level (so every fine-to-coarse face meets a
+    leaf one level down: 2:1 balance).  Coordinates are level cell coords;
+    the domain is [0, domain_cells)^3 at this level."""
+    have = set(map(tuple, existing_cells.tolist()))
+    keep = []
+    for c in want.tolist():
+        ok = True
+        for a in range(3):
+            for s in (-1, 1):
+                q = list(c)
+                q[a] += s
+                if 0 <= q[a] < domain_cells and tuple(q) not in have:
+                    ok = False
+        if ok:
+            keep.append(c)
+    return np.array(keep, dtype=np.int64).reshape(-1, 3)
+
+
+def config2(n0: int = 64, K: float = 1.0, cfl: float = 10.0, sigma: float = 0.05):
+    """Two-level heat test: base n0^3 on [-1/2, 1/2]^3, level 1 (2x) covering
+    the central 1/8 of the volume ([-1/4, 1/4]^3), constant K, Gaussian pulse
+    at the origin; dt_coarse = cfl dx0^2 / (2K), fine substeps dt/2.  Returns
+    (levels, per-level (E, K), dt_coarse)."""
+    dx0 = 1.0 / n0
+    base = box_octs(n0 // 2, n0 // 2, n0 // 2)
+    q0, q1 = n0 // 4, 3 * n0 // 4
+    g = np.stack(np.meshgrid(*[np.arange(q0, q1)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    levels = hierarchy_from_refined(base, [g], dx0)
+    states = []
+    for lv in levels:
+        xyz = cell_centres(lv, (-0.5, -0.5, -0.5))
+        states.append((gaussian(xyz, sigma=sigma), np.full(lv.n_cell, K)))
+    return levels, states, cfl * dx0 * dx0 / (2.0 * K)
+
+
+def random_hierarchy(seed: int, n0: int = 8, n_levels: int = 3, frac: float = 0.35):
+    """Small random 2:1-balanced hierarchy for parity tests: base n0^3 cells,
+    each further level refines a random blob (ball around a random centre) of
+    the previous one.  K log-normal, E random."""
+    rng = np.random.default_rng(seed)
+    dx0 = 1.0 / n0
+    base = box_octs(n0 // 2, n0 // 2, n0 // 2)
+    refined = []
+    octs = base.astype(np.int64)
+    for l in range(n_levels - 1):
+        cells = _cells_of_octs(octs)
+        nl = n0 * 2 ** l
+        centre = rng.uniform(0.3, 0.7, 3) * nl
+        r = np.linalg.norm(cells + 0.5 - centre, axis=1)
+        want = cells[r < np.quantile(r, frac)]
+        ref = balance_refinement(cells, want, nl)
+        if len(ref) == 0:
+            break
+        refined.append(ref)
+        octs = ref
+    levels = hierarchy_from_refined(base, refined, dx0)
+    states = []
+    for lv in levels:
+        states.append((rng.uniform(0.5, 1.5, lv.n_cell), np.exp(rng.standard_normal(lv.n_cell))))
+    return levels, states, float(rng.uniform(2.0, 20.0)) * dx0 * dx0 / 2.0
