@@ -31,14 +31,20 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
+    # ATS_NVCC_DEFINES: optional extra -D definitions (e.g. the register cap
+    # ATS_MINB_F32 of the FP32 tick kernels) for tuning sweeps
+    defines = os.environ.get("ATS_NVCC_DEFINES", "").split()
     return [
         "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-        "-I", INCLUDE, "-I", CSRC, *extra,
+        "-I", INCLUDE, "-I", CSRC, *defines, *extra,
     ]
 
 
 def _needs_build() -> bool:
     if not os.path.exists(LIB):
+        return True
+    stamp = LIB + ".defines"
+    if (open(stamp).read() if os.path.exists(stamp) else "") != os.environ.get("ATS_NVCC_DEFINES", ""):
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
@@ -73,6 +79,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB + ".defines", "w") as f:
+        f.write(os.environ.get("ATS_NVCC_DEFINES", ""))
     return LIB
 
 

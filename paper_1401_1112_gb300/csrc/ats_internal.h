@@ -50,23 +50,22 @@ struct SolveDev {
   int32_t pad;
 };
 
-// Mutable per-solve scalars (device).
+// Per-solve scalars (device).  Double-buffered by tick parity: the kernels of
+// a tick read S[parity] and the CTA that owns a solve's first work item
+// writes the solve's next state into S[parity ^ 1]; a finished solve's last
+// state also goes to a separate final array.
 struct SolveScalars {
   int32_t phase;
-  int32_t phase_next;
-  int32_t first;        // next op kernel starts a new direction (p = z)
+  int32_t first;        // the next CG iteration starts a new direction (p = z)
   int32_t pcur;         // which p buffer holds the current direction
   int32_t iters;
   int32_t inner_iters;
   int32_t refines;
   int32_t status;
-  int32_t counter;      // work items finished in the current kernel
-  int32_t final_pass;   // the next refine pass ends the solve
+  int32_t final_pass;   // the next refinement pass ends the solve
   int32_t ticks;
   int32_t pad;
-  double alpha;
-  double beta;
-  double rz;
+  double rz;            // r.z of the newest residual that is not yet a direction
   double r0;
   double inner_target;
   double rnorm;         // last FP64 true residual norm
@@ -123,13 +122,28 @@ cudaError_t launch_coef_build_batch(const CoefArgs *args, const int64_t *cell_of
                                     int *const *flags, cudaStream_t st);
 cudaError_t launch_gather_flags(const int *const *flags, int n, int *out, cudaStream_t st);
 
-// One tick = k_op (CG items) + k_ref (refinement items) + k_upd (all).
-// ev (null, or 4 events) is recorded before k_op, between the kernels and
-// after k_upd; `capture` says whether the stream is being captured.
-cudaError_t launch_tick(bool fp64, bool paper, const SolveDev *solves, SolveScalars *sc,
-                        const WorkItem *items, int32_t *lists, int n_items, TickCtl *ctl,
-                        double *partials, int *n_active, int grid, cudaStream_t st,
-                        cudaEvent_t *ev, bool capture, unsigned long long *cells_counter);
+// Device state of a planned batch, passed by value to the tick kernels.
+struct TickArgs {
+  const SolveDev *solves;
+  SolveScalars *sbuf;       // [2][n_solves]
+  SolveScalars *final_sc;   // [n_solves] state of every finished solve
+  const WorkItem *items;
+  int32_t *lists;           // [2 parities][2 phases][n_items]
+  int n_items;
+  int n_solves;
+  TickCtl *ctl;
+  double *p_op;             // [n_items][kNumPartials] partials of k_op / k_ref
+  double *p_upd;            // [2][n_items][kNumPartials] partials of k_upd by parity
+  int *n_active;
+  unsigned long long *cells;  // [4] cells processed per kernel/phase, or null
+};
+
+// One tick = k_op (CG items, and x += e for refinement items) + k_ref
+// (refinement residual) + k_upd (all).  ev (null, or 4 events) is recorded
+// before k_op, between the kernels and after k_upd; `capture` says whether
+// the stream is being captured.
+cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cudaStream_t st, cudaEvent_t *ev,
+                        bool capture);
 
 // Start of a solve: e = 0 on every cell of every item, and x64 = src[solve]
 // where src (device array of device pointers) is non-null for that solve.

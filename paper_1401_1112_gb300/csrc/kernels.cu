@@ -26,10 +26,11 @@
 // d_i = 1 + xd_i + sum_f C_f with xd_i (coupling shift + interface w C) read
 // from a sparse per-oct record.
 //
-// Reductions: each work item (a run of octs of one solve) writes FP64
-// partial sums; the last CTA to finish a solve's items (atomic counter)
-// reduces them in a fixed order and advances that solve's scalars.  No CTA
-// ever waits for another.
+// Reductions: each work item (a run of octs of one solve) writes its partial
+// sums; every CTA that needs a solve's totals in the next kernel reduces all
+// of that solve's item partials itself in a fixed order (so all agree
+// bitwise), and the CTA owning the solve's first item writes the solve's next
+// state (double-buffered by tick parity).  No CTA ever waits for another.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -44,9 +45,12 @@ constexpr unsigned kFull = 0xffffffffu;
 // resident CTAs per SM the tick kernels are compiled for (caps registers):
 // the FP32 CG path keeps its loads in flight with 5 CTAs of 128 threads; the
 // FP64 bulk path needs twice the registers per value.
+#ifndef ATS_MINB_F32
+#define ATS_MINB_F32 4
+#endif
 template <typename T>
 struct MinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? 5 : 3;
+  static constexpr int value = sizeof(T) == 4 ? ATS_MINB_F32 : 3;
 };
 
 // FP64-quality dot-product accumulation.  FP32 bulk: each product is split
@@ -59,6 +63,8 @@ template <>
 struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+  __device__ __forceinline__ void add_value(double v) { s += v; }
+  __device__ __forceinline__ void merge(const Acc<double> &o) { s += o.s; }
   __device__ __forceinline__ double get() const { return s; }
 };
 template <>
@@ -73,39 +79,23 @@ struct Acc<float> {
     s = t;
     c = __fadd_rn(c, __fadd_rn(se, pe));
   }
+  // add one value exactly (TwoSum), the error going to the low part
+  __device__ __forceinline__ void add_value(float v) {
+    const float t = __fadd_rn(s, v);
+    const float zz = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, zz)), __fsub_rn(v, zz));
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  __device__ __forceinline__ void merge(const Acc<float> &o) {
+    const float t = __fadd_rn(s, o.s);
+    const float zz = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, zz)), __fsub_rn(o.s, zz));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(o.c, e));
+  }
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
-
-// Block reduction of kNumPartials doubles (slot 3 optionally a max), fixed
-// order.  Result valid in thread 0.  Used where the partials are FP64 values
-// (refinement passes, the FP64 bulk path, the per-solve reduction).
-template <bool kSlot3Max>
-__device__ __forceinline__ void block_reduce(double (&v)[kNumPartials],
-                                             double (*red)[kNumPartials]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < kNumPartials; ++k) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const double o = __shfl_down_sync(kFull, v[k], off);
-      v[k] = (kSlot3Max && k == 3) ? fmax(v[k], o) : v[k] + o;
-    }
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < kNumPartials; ++k) red[warp][k] = v[k];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < kNumPartials; ++k) {
-      double a = red[0][k];
-      for (int w = 1; w < kThreads / 32; ++w) a = (kSlot3Max && k == 3) ? fmax(a, red[w][k]) : a + red[w][k];
-      v[k] = a;
-    }
-  }
-  __syncthreads();
-}
 
 // Warp reduction of a compensated FP32 accumulator: the (hi, lo) pairs are
 // combined with TwoSum (error-free), so no FP64 instruction is issued per
@@ -127,74 +117,6 @@ __device__ __forceinline__ void warp_reduce_acc(Acc<double> &a) {
   for (int off = 16; off > 0; off >>= 1) a.s += __shfl_down_sync(kFull, a.s, off);
 }
 
-// Block reduction of up to three dot accumulators and one FP64 max into the
-// kNumPartials doubles of thread 0 (slots 0, 1, 2 and the max in slot 3).
-template <typename T>
-__device__ __forceinline__ void block_reduce_acc(Acc<T> &a0, Acc<T> &a1, Acc<T> &a2, double mx,
-                                                 double (&v)[kNumPartials],
-                                                 double (*red)[kNumPartials]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  warp_reduce_acc(a0);
-  warp_reduce_acc(a1);
-  warp_reduce_acc(a2);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(kFull, mx, off));
-  if (lane == 0) {
-    red[warp][0] = a0.get();
-    red[warp][1] = a1.get();
-    red[warp][2] = a2.get();
-    red[warp][3] = mx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = red[0][0], s1 = red[0][1], s2 = red[0][2], m = red[0][3];
-    for (int w = 1; w < kThreads / 32; ++w) {
-      s0 += red[w][0];
-      s1 += red[w][1];
-      s2 += red[w][2];
-      m = fmax(m, red[w][3]);
-    }
-    v[0] = s0;
-    v[1] = s1;
-    v[2] = s2;
-    v[3] = m;
-  }
-  __syncthreads();
-}
-
-// Reduce the partials of all items of solve s (called by the last CTA).
-template <bool kSlot3Max>
-__device__ __forceinline__ void solve_reduce(const double *partials, int item_begin, int n_items,
-                                             double (&out)[kNumPartials],
-                                             double (*red)[kNumPartials]) {
-  double v[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
-  for (int it = item_begin + (int)threadIdx.x; it < item_begin + n_items; it += kThreads) {
-#pragma unroll
-    for (int k = 0; k < kNumPartials; ++k) {
-      const double p = __ldcg(partials + (size_t)it * kNumPartials + k);
-      v[k] = (kSlot3Max && k == 3) ? fmax(v[k], p) : v[k] + p;
-    }
-  }
-  block_reduce<kSlot3Max>(v, red);
-#pragma unroll
-  for (int k = 0; k < kNumPartials; ++k) out[k] = v[k];
-}
-
-// Publish an item's partials; returns true in every thread of the CTA that
-// finished the last item of its solve.
-__device__ __forceinline__ bool publish_item(double (&v)[kNumPartials], double *partials, int it,
-                                             SolveScalars *scs, int n_items_solve, int *s_last) {
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < kNumPartials; ++k) partials[(size_t)it * kNumPartials + k] = v[k];
-    __threadfence();
-    const int prev = atomicAdd(&scs->counter, 1);
-    *s_last = (prev == n_items_solve - 1);
-    if (*s_last) __threadfence();
-  }
-  __syncthreads();
-  return *s_last != 0;
-}
 
 // ---------------------------------------------------------------------------
 // oct-wise vector I/O (one thread owns the eight cells of one oct)
@@ -320,52 +242,6 @@ __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T
   }
 }
 
-// k_op, CG phase: p_new = z + beta p_old (first: z), q = (I + dt A) p_new,
-// partial p_new . q.
-template <typename T>
-__device__ __forceinline__ void op_inner_oct(const SolveDev &sd, int o, T h, T beta, bool first,
-                                             const T *__restrict__ pold, T *__restrict__ pnew,
-                                             Acc<T> &pq) {
-  const T *__restrict__ KT = (const T *)sd.KT;
-  const T *__restrict__ z = (const T *)sd.z;
-  int nb[6];
-  load_nbr6(sd.nbr, o, nb);
-  const int rec = __ldg(sd.xrec + o);
-  T K[8], pv[8];
-  ld8_ro(KT + 8 * o, K);
-  ld8_ro(z + 8 * o, pv);
-  if (!first) {
-    T pp[8];
-    ld8_ro(pold + 8 * o, pp);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) pv[c] = fma(beta, pp[c], pv[c]);
-  }
-  T dsum[8], off[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) dsum[c] = off[c] = T(0);
-  in_oct_faces(K, pv, h, dsum, off);
-  op_face<0>(nb[0], KT, z, pold, first, beta, h, K, dsum, off);
-  op_face<1>(nb[1], KT, z, pold, first, beta, h, K, dsum, off);
-  op_face<2>(nb[2], KT, z, pold, first, beta, h, K, dsum, off);
-  op_face<3>(nb[3], KT, z, pold, first, beta, h, K, dsum, off);
-  op_face<4>(nb[4], KT, z, pold, first, beta, h, K, dsum, off);
-  op_face<5>(nb[5], KT, z, pold, first, beta, h, K, dsum, off);
-  T xd[8];
-  if (rec >= 0) {
-    ld8_ro((const T *)sd.xdT + 8 * rec, xd);
-  } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) xd[c] = T(0);
-  }
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const T d = T(1) + xd[c] + dsum[c];
-    const T q = d * pv[c] - off[c];
-    if (K[c] >= T(0)) pq.add(pv[c], q);
-  }
-  st8(pnew + 8 * o, pv);  // non-leaf cells carry z = p = 0
-}
-
 // k_upd, CG phase, out-of-oct face DIR: neighbour p and K.
 template <int DIR, typename T>
 __device__ __forceinline__ void upd_face(int n, const T *__restrict__ KT, const T *__restrict__ p, T h,
@@ -385,61 +261,6 @@ __device__ __forceinline__ void upd_face(int n, const T *__restrict__ KT, const 
   }
 }
 
-// k_upd, CG phase: q = (I + dt A) p, r = D z - alpha q, z = r / D, e += alpha p,
-// partials r.z, r.r (and the max relative change for the paper rule).
-template <typename T, bool kPaper>
-__device__ __forceinline__ void upd_inner_oct(const SolveDev &sd, int o, T h, T alpha,
-                                              const T *__restrict__ p, Acc<T> &rz, Acc<T> &rr,
-                                              double &maxchg) {
-  const T *__restrict__ KT = (const T *)sd.KT;
-  T *z = (T *)sd.z;
-  T *e = (T *)sd.e;
-  int nb[6];
-  load_nbr6(sd.nbr, o, nb);
-  const int rec = __ldg(sd.xrec + o);
-  T K[8], pv[8], zv[8], ev[8];
-  ld8_ro(KT + 8 * o, K);
-  ld8_ro(p + 8 * o, pv);
-  ld8_rw(z + 8 * o, zv);
-  ld8_rw(e + 8 * o, ev);
-  T dsum[8], off[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) dsum[c] = off[c] = T(0);
-  in_oct_faces(K, pv, h, dsum, off);
-  upd_face<0>(nb[0], KT, p, h, K, dsum, off);
-  upd_face<1>(nb[1], KT, p, h, K, dsum, off);
-  upd_face<2>(nb[2], KT, p, h, K, dsum, off);
-  upd_face<3>(nb[3], KT, p, h, K, dsum, off);
-  upd_face<4>(nb[4], KT, p, h, K, dsum, off);
-  upd_face<5>(nb[5], KT, p, h, K, dsum, off);
-  T xd[8];
-  if (rec >= 0) {
-    ld8_ro((const T *)sd.xdT + 8 * rec, xd);
-  } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) xd[c] = T(0);
-  }
-  double xo[8];
-  if (kPaper) ld8_rw(sd.x64 + 8 * o, xo);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const bool leaf = K[c] >= T(0);
-    const T d = T(1) + xd[c] + dsum[c];
-    const T q = d * pv[c] - off[c];
-    const T r = d * zv[c] - alpha * q;
-    const T zn = r / d;
-    const T step = alpha * pv[c];
-    if (leaf) {
-      rz.add(r, zn);
-      rr.add(r, r);
-      if (kPaper) maxchg = fmax(maxchg, fabs((double)step) / fabs(xo[c] + (double)ev[c]));
-    }
-    zv[c] = leaf ? zn : T(0);
-    ev[c] = leaf ? ev[c] + step : T(0);
-  }
-  st8(z + 8 * o, zv);
-  st8(e + 8 * o, ev);
-}
 
 // k_ref, out-of-oct face DIR: FP64 flux sums (K_i + K_j)(x_i - x_j) and the
 // bulk-precision diagonal for the preconditioner.
@@ -572,248 +393,508 @@ __device__ __forceinline__ void upd_refine_oct(const SolveDev &sd, int o) {
   st8(e + 8 * o, ev);
 }
 
-}  // namespace
-
 // ---------------------------------------------------------------------------
-// the two tick kernels (persistent grid, grid-stride over the active list)
+// per-item partial sums
+//
+// A work item stores kNumPartials sums.  In the FP32 bulk each sum is kept as
+// an unevaluated (hi, lo) float pair (error-free TwoSum cascade), stored in
+// the 8 bytes of a slot; in the FP64 bulk it is a double.  Every CTA that
+// needs a solve's totals reduces all of that solve's item partials itself,
+// in the same fixed order, so all CTAs obtain bitwise the same totals and no
+// CTA ever signals or waits for another.
 // ---------------------------------------------------------------------------
 
-// The list of one phase for the current parity: lists[(parity * 2 + phase) * n_items].
-__device__ __forceinline__ const int32_t *phase_list(const int32_t *lists, int n_items, int parity, int phase) {
-  return lists + (size_t)(parity * 2 + phase) * n_items;
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
-// Last CTA of a solve in k_op / k_ref: reduce its partials and advance the
-// op-side scalars (alpha after a CG step; the refinement decision after a
-// true-residual pass).
-__device__ __forceinline__ void op_epilogue(const SolveDev &sd, SolveScalars *scs, int phase,
-                                            const double *partials, double (*red)[kNumPartials]) {
-  double tot[kNumPartials];
-  solve_reduce<false>(partials, sd.item_begin, sd.n_items, tot, red);
+template <typename T>
+struct Slot;
+template <>
+struct Slot<float> {
+  static __device__ __forceinline__ void store(double *p, const Acc<float> &a) {
+    float2 v = make_float2(a.s, a.c);
+    *reinterpret_cast<float2 *>(p) = v;
+  }
+  static __device__ __forceinline__ void load_add(const double *p, Acc<float> &a) {
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    float s, e;
+    two_sum(a.s, v.x, s, e);
+    a.s = s;
+    a.c = __fadd_rn(a.c, __fadd_rn(v.y, e));
+  }
+};
+template <>
+struct Slot<double> {
+  static __device__ __forceinline__ void store(double *p, const Acc<double> &a) { *p = a.s; }
+  static __device__ __forceinline__ void load_add(const double *p, Acc<double> &a) { a.s += __ldcg(p); }
+};
+
+// Block sums of three accumulators (and a max) of this CTA's item, reduced
+// across warps in the accumulator precision; thread 0 writes the slots.
+template <typename T>
+__device__ __forceinline__ void store_item_partials(double *slots, Acc<T> a0, Acc<T> a1, Acc<T> a2, float mx,
+                                                    Acc<T> (*red)[3], float *redmx) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_reduce_acc(a0);
+  warp_reduce_acc(a1);
+  warp_reduce_acc(a2);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(kFull, mx, off));
+  if (lane == 0) {
+    red[warp][0] = a0;
+    red[warp][1] = a1;
+    red[warp][2] = a2;
+    redmx[warp] = mx;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    scs->counter = 0;
-    if (phase == kInner) {
-      const double pq = tot[0];
-      if (!(pq > 0.0) || !isfinite(pq)) {
-        scs->alpha = 0.0;
-        scs->status = ATS_ERR_BREAKDOWN;
-      } else {
-        scs->alpha = scs->rz / pq;
-      }
-    } else {
-      const double rnorm = sqrt(tot[0]);
-      const double xnorm = sqrt(tot[1]);
-      if (scs->refines == 0) scs->r0 = rnorm;
-      scs->refines += 1;
-      scs->rnorm = rnorm;
-      scs->xnorm = xnorm;
-      const double ref = (sd.stop_rule == ATS_STOP_CERTIFIED) ? xnorm : scs->r0;
-      const double target = sd.tol * ref;
-      if (scs->final_pass) {
-        scs->phase_next = kDone;
-      } else if (!isfinite(rnorm)) {
-        scs->status = ATS_ERR_BREAKDOWN;
-        scs->phase_next = kDone;
-      } else if (rnorm <= target) {
-        scs->phase_next = kDone;
-      } else if (scs->refines > sd.max_refine) {
-        scs->status = ATS_ERR_NOT_CONVERGED;
-        scs->phase_next = kDone;
-      } else if (!(tot[2] > 0.0)) {
-        scs->status = ATS_ERR_BREAKDOWN;
-        scs->phase_next = kDone;
-      } else {
-        scs->phase_next = kInner;
-        scs->rz = tot[2];
-        scs->first = 1;
-        scs->inner_iters = 0;
-        scs->inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
-      }
+    for (int w = 1; w < kThreads / 32; ++w) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) red[0][k].merge(red[w][k]);
+      redmx[0] = fmaxf(redmx[0], redmx[w]);
     }
+    Slot<T>::store(slots + 0, red[0][0]);
+    Slot<T>::store(slots + 1, red[0][1]);
+    Slot<T>::store(slots + 2, red[0][2]);
+    slots[3] = (double)redmx[0];
   }
   __syncthreads();
 }
 
-// CG phase of the op side: p = z + beta p, q = (I + dt A) p, p.q.
+// Totals of the first `ns` slots over the items [begin, begin + n) of a solve
+// (and the max of slot 3 when want_max), evaluated to FP64; every thread of
+// the CTA receives them.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(const SolveDev *__restrict__ solves,
-                                                 SolveScalars *__restrict__ sc,
-                                                 const WorkItem *__restrict__ items,
-                                                 const int32_t *__restrict__ lists, int n_items,
-                                                 TickCtl *ctl, double *__restrict__ partials,
-                                                 unsigned long long *__restrict__ cells) {
-  __shared__ double red[kThreads / 32][kNumPartials];
-  __shared__ int s_last;
-  const int cur = __ldcg(&ctl->parity);
-  const int n_list = __ldcg(&ctl->count[cur][kInner]);
-  const int32_t *list = phase_list(lists, n_items, cur, kInner);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->count[cur ^ 1][0] = 0;
-    ctl->count[cur ^ 1][1] = 0;
+__device__ __forceinline__ void solve_totals(const double *P, int begin, int n, int ns, bool want_max,
+                                             double (&tot)[kNumPartials], Acc<T> (*red)[3], float *redmx,
+                                             double *bcast) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Acc<T> a[3];
+  float mx = 0.f;
+  for (int it = begin + (int)threadIdx.x; it < begin + n; it += kThreads) {
+    const double *p = P + (size_t)it * kNumPartials;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < ns) Slot<T>::load_add(p + k, a[k]);
+    if (want_max) mx = fmaxf(mx, (float)__ldcg(p + 3));
   }
-  for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) warp_reduce_acc(a[k]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(kFull, mx, off));
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) red[warp][k] = a[k];
+    redmx[warp] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kThreads / 32; ++w) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) red[0][k].merge(red[w][k]);
+      redmx[0] = fmaxf(redmx[0], redmx[w]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bcast[k] = red[0][k].get();
+    bcast[3] = (double)redmx[0];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kNumPartials; ++k) tot[k] = bcast[k];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// per-oct work, split so that an oct's own loads are in flight while the CTA
+// reduces the solve totals it needs
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct OpOwn {
+  int nb[6];
+  int rec;
+  T K[8], z[8], pp[8];
+};
+
+template <typename T>
+__device__ __forceinline__ void op_load_own(const SolveDev &sd, int o, bool first, const T *__restrict__ pold,
+                                            OpOwn<T> &w) {
+  load_nbr6(sd.nbr, o, w.nb);
+  w.rec = __ldg(sd.xrec + o);
+  ld8_ro((const T *)sd.KT + 8 * o, w.K);
+  ld8_ro((const T *)sd.z + 8 * o, w.z);
+  if (!first) ld8_ro(pold + 8 * o, w.pp);
+}
+
+// k_op, CG phase: p_new = z + beta p_old (first: z), q = (I + dt A) p_new,
+// partial p_new . q (per-oct FP32 sum, carried error-free across octs).
+template <typename T>
+__device__ __forceinline__ void op_compute(const SolveDev &sd, int o, const OpOwn<T> &w, T h, T beta, bool first,
+                                           const T *__restrict__ pold, T *__restrict__ pnew, Acc<T> &pq) {
+  const T *__restrict__ KT = (const T *)sd.KT;
+  const T *__restrict__ z = (const T *)sd.z;
+  T pv[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) pv[c] = first ? w.z[c] : fma(beta, w.pp[c], w.z[c]);
+  T dsum[8], off[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) dsum[c] = off[c] = T(0);
+  in_oct_faces(w.K, pv, h, dsum, off);
+  op_face<0>(w.nb[0], KT, z, pold, first, beta, h, w.K, dsum, off);
+  op_face<1>(w.nb[1], KT, z, pold, first, beta, h, w.K, dsum, off);
+  op_face<2>(w.nb[2], KT, z, pold, first, beta, h, w.K, dsum, off);
+  op_face<3>(w.nb[3], KT, z, pold, first, beta, h, w.K, dsum, off);
+  op_face<4>(w.nb[4], KT, z, pold, first, beta, h, w.K, dsum, off);
+  op_face<5>(w.nb[5], KT, z, pold, first, beta, h, w.K, dsum, off);
+  T xd[8];
+  if (w.rec >= 0) {
+    ld8_ro((const T *)sd.xdT + 8 * w.rec, xd);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xd[c] = T(0);
+  }
+  T local = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const T d = T(1) + xd[c] + dsum[c];
+    const T q = d * pv[c] - off[c];
+    if (w.K[c] >= T(0)) local = fma(pv[c], q, local);
+  }
+  pq.add_value(local);
+  st8(pnew + 8 * o, pv);  // non-leaf cells carry z = p = 0
+}
+
+template <typename T>
+struct UpdOwn {
+  int nb[6];
+  int rec;
+  T K[8], p[8], z[8], e[8];
+};
+
+template <typename T>
+__device__ __forceinline__ void upd_load_own(const SolveDev &sd, int o, const T *__restrict__ p, UpdOwn<T> &w) {
+  load_nbr6(sd.nbr, o, w.nb);
+  w.rec = __ldg(sd.xrec + o);
+  ld8_ro((const T *)sd.KT + 8 * o, w.K);
+  ld8_ro(p + 8 * o, w.p);
+  ld8_rw((const T *)sd.z + 8 * o, w.z);
+  ld8_rw((const T *)sd.e + 8 * o, w.e);
+}
+
+// k_upd, CG phase: q = (I + dt A) p, r = D z - alpha q, z = r / D, e += alpha p,
+// partials r.z, r.r (and the max relative change for the paper rule).
+template <typename T, bool kPaper>
+__device__ __forceinline__ void upd_compute(const SolveDev &sd, int o, UpdOwn<T> &w, T h, T alpha,
+                                            const T *__restrict__ p, Acc<T> &rz, Acc<T> &rr, float &maxchg) {
+  const T *__restrict__ KT = (const T *)sd.KT;
+  T dsum[8], off[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) dsum[c] = off[c] = T(0);
+  in_oct_faces(w.K, w.p, h, dsum, off);
+  upd_face<0>(w.nb[0], KT, p, h, w.K, dsum, off);
+  upd_face<1>(w.nb[1], KT, p, h, w.K, dsum, off);
+  upd_face<2>(w.nb[2], KT, p, h, w.K, dsum, off);
+  upd_face<3>(w.nb[3], KT, p, h, w.K, dsum, off);
+  upd_face<4>(w.nb[4], KT, p, h, w.K, dsum, off);
+  upd_face<5>(w.nb[5], KT, p, h, w.K, dsum, off);
+  T xd[8];
+  if (w.rec >= 0) {
+    ld8_ro((const T *)sd.xdT + 8 * w.rec, xd);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xd[c] = T(0);
+  }
+  double xo[8];
+  if (kPaper) ld8_rw(sd.x64 + 8 * o, xo);
+  T lrz = T(0), lrr = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const bool leaf = w.K[c] >= T(0);
+    const T d = T(1) + xd[c] + dsum[c];
+    const T q = d * w.p[c] - off[c];
+    const T r = d * w.z[c] - alpha * q;
+    const T zn = r / d;
+    const T step = alpha * w.p[c];
+    if (leaf) {
+      lrz = fma(r, zn, lrz);
+      lrr = fma(r, r, lrr);
+      if (kPaper) maxchg = fmaxf(maxchg, (float)(fabs((double)step) / fabs(xo[c] + (double)w.e[c])));
+    }
+    w.z[c] = leaf ? zn : T(0);
+    w.e[c] = leaf ? w.e[c] + step : T(0);
+  }
+  rz.add_value(lrz);
+  rr.add_value(lrr);
+  st8((T *)sd.z + 8 * o, w.z);
+  st8((T *)sd.e + 8 * o, w.e);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the three tick kernels (persistent grid, grid-stride over the active lists)
+// ---------------------------------------------------------------------------
+
+// The list of one phase for a parity: lists[(parity * 2 + phase) * n_items].
+__device__ __forceinline__ int32_t *phase_list(int32_t *lists, int n_items, int parity, int phase) {
+  return lists + (size_t)(parity * 2 + phase) * n_items;
+}
+
+// CG items: p = z + beta p, q = (I + dt A) p, partial p.q.  Refinement items:
+// x += e, e = 0 (the finished inner solve's correction), before k_ref.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a) {
+  __shared__ Acc<T> red[kThreads / 32][3];
+  __shared__ float redmx[kThreads / 32];
+  __shared__ double bcast[kNumPartials];
+  const int cur = __ldcg(&a.ctl->parity);
+  const int n_in = __ldcg(&a.ctl->count[cur][kInner]);
+  const int n_rf = __ldcg(&a.ctl->count[cur][kRefine]);
+  const int32_t *list = phase_list(a.lists, a.n_items, cur, kInner);
+  const SolveScalars *S = a.sbuf + (size_t)cur * a.n_solves;
+  const double *Pprev = a.p_upd + (size_t)(cur ^ 1) * a.n_items * kNumPartials;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctl->count[cur ^ 1][0] = 0;
+    a.ctl->count[cur ^ 1][1] = 0;
+  }
+  for (int li = blockIdx.x; li < n_in; li += gridDim.x) {
     const int it = __ldcg(list + li);
-    const WorkItem item = items[it];
-    const int s = item.solve;
-    SolveScalars *scs = sc + s;
-    const SolveDev &sd = solves[s];
-    const int oct_end = item.oct_begin + item.n_oct;
-    double v[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
-    const T h = (T)sd.h;
-    const T beta = (T)scs->beta;
-    const bool first = scs->first != 0;
-    const int pcur = scs->pcur;
+    const WorkItem item = a.items[it];
+    const SolveDev &sd = a.solves[item.solve];
+    const SolveScalars &sc = S[item.solve];
+    const bool first = sc.first != 0;
+    const int pcur = sc.pcur;
+    const double rz_prev = sc.rz;
     const T *pold = (const T *)(pcur ? sd.p1 : sd.p0);
     T *pnew = (T *)(pcur ? sd.p0 : sd.p1);
+    const int oct_end = item.oct_begin + item.n_oct;
+    const int o0 = item.oct_begin + (int)threadIdx.x;
+    OpOwn<T> w;
+    if (o0 < oct_end) op_load_own(sd, o0, first, pold, w);
+    // beta = (r_j . z_j) / (r_{j-1} . z_{j-1}) from the previous update's partials
+    T beta = T(0);
+    if (!first) {
+      double tot[kNumPartials];
+      solve_totals<T>(Pprev, sd.item_begin, sd.n_items, 1, false, tot, red, redmx, bcast);
+      if (threadIdx.x == 0) bcast[0] = tot[0] / rz_prev;  // one FP64 divide per CTA
+      __syncthreads();
+      beta = (T)bcast[0];
+      __syncthreads();
+    }
+    const T h = (T)sd.h;
     Acc<T> pq, none;
-    for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
-      op_inner_oct<T>(sd, o, h, beta, first, pold, pnew, pq);
-    block_reduce_acc<T>(pq, none, none, 0.0, v, red);
-    if (cells && threadIdx.x == 0) atomicAdd(cells + 0, (unsigned long long)item.n_oct * 8);
-    if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
-    op_epilogue(sd, scs, kInner, partials, red);
+    if (o0 < oct_end) op_compute(sd, o0, w, h, beta, first, pold, pnew, pq);
+    for (int o = o0 + kThreads; o < oct_end; o += kThreads) {
+      op_load_own(sd, o, first, pold, w);
+      op_compute(sd, o, w, h, beta, first, pold, pnew, pq);
+    }
+    store_item_partials<T>(a.p_op + (size_t)it * kNumPartials, pq, none, none, 0.f, red, redmx);
+    if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 0, (unsigned long long)item.n_oct * 8);
   }
-  // refinement items: fold the correction of the finished inner solve into x
-  // (x += e, e = 0) before k_ref forms the true residual
-  const int n_ref = __ldcg(&ctl->count[cur][kRefine]);
-  const int32_t *rlist = phase_list(lists, n_items, cur, kRefine);
-  for (int li = blockIdx.x; li < n_ref; li += gridDim.x) {
-    const WorkItem item = items[__ldcg(rlist + li)];
-    const SolveDev &sd = solves[item.solve];
+  const int32_t *rlist = phase_list(a.lists, a.n_items, cur, kRefine);
+  for (int li = blockIdx.x; li < n_rf; li += gridDim.x) {
+    const WorkItem item = a.items[__ldcg(rlist + li)];
+    const SolveDev &sd = a.solves[item.solve];
     const int oct_end = item.oct_begin + item.n_oct;
     for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads) upd_refine_oct<T>(sd, o);
-    if (cells && threadIdx.x == 0) atomicAdd(cells + 3, (unsigned long long)item.n_oct * 8);
+    if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 3, (unsigned long long)item.n_oct * 8);
   }
 }
 
-// Refinement phase of the op side: FP64 true residual, z = D^-1 r.
+// Refinement items: FP64 true residual, z = D^-1 r, partials r.r, x.x, r.z.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k_ref(const SolveDev *__restrict__ solves,
-                                                     SolveScalars *__restrict__ sc,
-                                                     const WorkItem *__restrict__ items,
-                                                     const int32_t *__restrict__ lists, int n_items,
-                                                     TickCtl *ctl, double *__restrict__ partials,
-                                                     unsigned long long *__restrict__ cells) {
-  __shared__ double red[kThreads / 32][kNumPartials];
-  __shared__ int s_last;
-  const int cur = __ldcg(&ctl->parity);
-  const int n_list = __ldcg(&ctl->count[cur][kRefine]);
-  const int32_t *list = phase_list(lists, n_items, cur, kRefine);
-  for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+__global__ void __launch_bounds__(kThreads, 3) k_ref(TickArgs a) {
+  __shared__ Acc<T> red[kThreads / 32][3];
+  __shared__ float redmx[kThreads / 32];
+  const int cur = __ldcg(&a.ctl->parity);
+  const int n_rf = __ldcg(&a.ctl->count[cur][kRefine]);
+  const int32_t *list = phase_list(a.lists, a.n_items, cur, kRefine);
+  for (int li = blockIdx.x; li < n_rf; li += gridDim.x) {
     const int it = __ldcg(list + li);
-    const WorkItem item = items[it];
-    const int s = item.solve;
-    SolveScalars *scs = sc + s;
-    const SolveDev &sd = solves[s];
+    const WorkItem item = a.items[it];
+    const SolveDev &sd = a.solves[item.solve];
     const int oct_end = item.oct_begin + item.n_oct;
-    double v[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
     Acc<T> rr, xx, rz;
     const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
     for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
       op_refine_oct<T>(sd, o, want_x, rr, xx, rz);
-    block_reduce_acc<T>(rr, xx, rz, 0.0, v, red);
-    if (cells && threadIdx.x == 0) atomicAdd(cells + 1, (unsigned long long)item.n_oct * 8);
-    if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
-    op_epilogue(sd, scs, kRefine, partials, red);
+    store_item_partials<T>(a.p_op + (size_t)it * kNumPartials, rr, xx, rz, 0.f, red, redmx);
+    if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 1, (unsigned long long)item.n_oct * 8);
   }
 }
 
-template <typename T, bool kPaper>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(const SolveDev *__restrict__ solves,
-                                                  SolveScalars *__restrict__ sc,
-                                                  const WorkItem *__restrict__ items,
-                                                  int32_t *__restrict__ lists, int n_items,
-                                                  TickCtl *ctl, double *__restrict__ partials,
-                                                  int *n_active,
-                                                  unsigned long long *__restrict__ cells) {
-  __shared__ double red[kThreads / 32][kNumPartials];
-  __shared__ int s_last;
-  __shared__ int s_base;
-  __shared__ int s_phase;
-  const int cur = __ldcg(&ctl->parity);
-  const int n_in = __ldcg(&ctl->count[cur][kInner]);
-  const int n_list = n_in + __ldcg(&ctl->count[cur][kRefine]);
-  for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
-    const int it = li < n_in ? __ldcg(phase_list(lists, n_items, cur, kInner) + li)
-                             : __ldcg(phase_list(lists, n_items, cur, kRefine) + (li - n_in));
-    const WorkItem item = items[it];
-    const int s = item.solve;
-    SolveScalars *scs = sc + s;
-    const int phase = scs->phase;
-    const SolveDev &sd = solves[s];
-    const int oct_end = item.oct_begin + item.n_oct;
-    double v[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
-    if (phase == kInner) {
-      const T h = (T)sd.h;
-      const T alpha = (T)scs->alpha;
-      const T *p = (const T *)(scs->pcur ? sd.p0 : sd.p1);  // written by k_op this tick
-      Acc<T> rz, rr;
-      double maxchg = 0.0;
-      for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
-        upd_inner_oct<T, kPaper>(sd, o, h, alpha, p, rz, rr, maxchg);
-      Acc<T> none;
-      block_reduce_acc<T>(rz, rr, none, maxchg, v, red);
-      if (cells && threadIdx.x == 0) atomicAdd(cells + 2, (unsigned long long)item.n_oct * 8);
+// Append a solve's items to the next tick's list of its new phase (the CTA
+// that owns the solve's first item), or retire it.
+__device__ __forceinline__ void commit_solve(const TickArgs &a, int cur, int s, const SolveDev &sd,
+                                             const SolveScalars &next, int *s_base) {
+  if (threadIdx.x == 0) {
+    a.sbuf[(size_t)(cur ^ 1) * a.n_solves + s] = next;
+    if (next.phase == kDone) {
+      a.final_sc[s] = next;
+      atomicSub(a.n_active, 1);
+      *s_base = -1;
+    } else {
+      *s_base = atomicAdd(&a.ctl->count[cur ^ 1][next.phase], sd.n_items);
     }
-    if (!publish_item(v, partials, it, scs, sd.n_items, &s_last)) continue;
+  }
+  __syncthreads();
+  const int base = *s_base;
+  if (base >= 0) {
+    int32_t *nl = phase_list(a.lists, a.n_items, cur ^ 1, next.phase);
+    for (int k = threadIdx.x; k < sd.n_items; k += kThreads) nl[base + k] = sd.item_begin + k;
+  }
+  __syncthreads();
+}
 
-    double tot[kNumPartials];
-    solve_reduce<true>(partials, sd.item_begin, sd.n_items, tot, red);
-    if (threadIdx.x == 0) {
-      scs->counter = 0;
-      scs->ticks += 1;
-      if (phase == kInner) {
-        scs->iters += 1;
-        scs->inner_iters += 1;
-        const double rz_new = tot[0];
-        const double rnorm_in = sqrt(tot[1]);
-        scs->maxchg = tot[3];
-        if (scs->status == ATS_ERR_BREAKDOWN || !isfinite(rz_new) || rz_new < 0.0) {
-          scs->status = ATS_ERR_BREAKDOWN;
-          scs->phase = kDone;
-          atomicSub(n_active, 1);
+// CG items: alpha = r.z / p.q, e += alpha p, r = D z - alpha q, z = r / D;
+// partials r.z, r.r (max change).  Before updating, the previous update's
+// residual decides whether the inner solve has converged (then nothing is
+// updated and the solve goes to refinement).  Refinement items: the decision
+// after a true-residual pass.  The CTA owning a solve's first item writes the
+// solve's next state and list entries.
+template <typename T, bool kPaper>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs a) {
+  __shared__ Acc<T> red[kThreads / 32][3];
+  __shared__ float redmx[kThreads / 32];
+  __shared__ double bcast[kNumPartials];
+  __shared__ int s_base;
+  const int cur = __ldcg(&a.ctl->parity);
+  const int n_in = __ldcg(&a.ctl->count[cur][kInner]);
+  const int n_list = n_in + __ldcg(&a.ctl->count[cur][kRefine]);
+  const SolveScalars *S = a.sbuf + (size_t)cur * a.n_solves;
+  const double *Pprev = a.p_upd + (size_t)(cur ^ 1) * a.n_items * kNumPartials;
+  double *Pcur = a.p_upd + (size_t)cur * a.n_items * kNumPartials;
+  for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+    const bool inner = li < n_in;
+    const int it = inner ? __ldcg(phase_list(a.lists, a.n_items, cur, kInner) + li)
+                         : __ldcg(phase_list(a.lists, a.n_items, cur, kRefine) + (li - n_in));
+    const WorkItem item = a.items[it];
+    const int s = item.solve;
+    const SolveDev &sd = a.solves[s];
+    const SolveScalars sc = S[s];
+    const bool owner = (it == sd.item_begin);
+    if (inner) {
+      const bool first = sc.first != 0;
+      const T *p = (const T *)(sc.pcur ? sd.p0 : sd.p1);  // written by k_op this tick
+      const int oct_end = item.oct_begin + item.n_oct;
+      const int o0 = item.oct_begin + (int)threadIdx.x;
+      UpdOwn<T> w;
+      if (o0 < oct_end) upd_load_own(sd, o0, p, w);
+      double tq[kNumPartials];
+      solve_totals<T>(a.p_op, sd.item_begin, sd.n_items, 1, false, tq, red, redmx, bcast);
+      double rz_j = sc.rz, rr_j = 0.0, mx = 0.0;
+      if (!first) {
+        double tp[kNumPartials];
+        solve_totals<T>(Pprev, sd.item_begin, sd.n_items, 2, kPaper, tp, red, redmx, bcast);
+        rz_j = tp[0];
+        rr_j = tp[1];
+        mx = tp[3];
+      }
+      // the scalar decisions once per CTA (FP64 divide and square root are
+      // slow here), then broadcast
+      if (threadIdx.x == 0) {
+        const bool cv = !first && ((sqrt(rr_j) <= sc.inner_target && (!kPaper || mx < sd.tol)) || rz_j == 0.0);
+        const bool bk = !cv && (!(rz_j >= 0.0) || !isfinite(rz_j) || !(tq[0] > 0.0) || !isfinite(tq[0]));
+        bcast[0] = cv ? 1.0 : 0.0;
+        bcast[1] = bk ? 1.0 : 0.0;
+        bcast[2] = (cv || bk) ? 0.0 : rz_j / tq[0];
+      }
+      __syncthreads();
+      const bool conv = bcast[0] != 0.0;
+      const bool brk = bcast[1] != 0.0;
+      const double alpha64 = bcast[2];
+      __syncthreads();
+      Acc<T> rz, rr, none;
+      float maxchg = 0.f;
+      if (!conv && !brk) {
+        const T h = (T)sd.h;
+        const T alpha = (T)alpha64;
+        if (o0 < oct_end) upd_compute<T, kPaper>(sd, o0, w, h, alpha, p, rz, rr, maxchg);
+        for (int o = o0 + kThreads; o < oct_end; o += kThreads) {
+          upd_load_own(sd, o, p, w);
+          upd_compute<T, kPaper>(sd, o, w, h, alpha, p, rz, rr, maxchg);
+        }
+      }
+      store_item_partials<T>(Pcur + (size_t)it * kNumPartials, rz, rr, none, maxchg, red, redmx);
+      if (a.cells && threadIdx.x == 0 && !conv && !brk) atomicAdd(a.cells + 2, (unsigned long long)item.n_oct * 8);
+      if (owner) {
+        SolveScalars nx = sc;
+        nx.ticks += 1;
+        if (conv) {
+          nx.phase = kRefine;
+        } else if (brk) {
+          nx.status = ATS_ERR_BREAKDOWN;
+          nx.phase = kDone;
         } else {
-          scs->beta = rz_new / scs->rz;
-          scs->rz = rz_new;
-          scs->first = 0;
-          scs->pcur ^= 1;
-          const bool conv = (rnorm_in <= scs->inner_target) && (!kPaper || tot[3] < sd.tol);
-          if (conv || rz_new == 0.0) {
-            scs->phase = kRefine;
-          } else if (scs->iters >= sd.max_iter) {
-            scs->status = ATS_ERR_NOT_CONVERGED;
-            scs->final_pass = 1;
-            scs->phase = kRefine;
-          } else if (scs->inner_iters >= sd.inner_max) {
-            scs->phase = kRefine;  // restart from the true residual
+          nx.iters += 1;
+          nx.inner_iters += 1;
+          nx.first = 0;
+          nx.pcur ^= 1;
+          nx.rz = rz_j;
+          nx.maxchg = mx;
+          if (nx.iters >= sd.max_iter) {
+            nx.status = ATS_ERR_NOT_CONVERGED;
+            nx.final_pass = 1;
+            nx.phase = kRefine;
+          } else if (nx.inner_iters >= sd.inner_max) {
+            nx.phase = kRefine;  // restart from the true residual
           }
         }
-      } else {
-        scs->phase = scs->phase_next;
-        if (scs->phase == kDone) atomicSub(n_active, 1);
+        commit_solve(a, cur, s, sd, nx, &s_base);
       }
-      const int np = scs->phase;
-      s_phase = np;
-      s_base = (np != kDone) ? atomicAdd(&ctl->count[cur ^ 1][np], sd.n_items) : -1;
+    } else {
+      double t[kNumPartials];
+      solve_totals<T>(a.p_op, sd.item_begin, sd.n_items, 3, false, t, red, redmx, bcast);
+      if (owner) {
+        SolveScalars nx = sc;
+        nx.ticks += 1;
+        const double rnorm = sqrt(t[0]);
+        const double xnorm = sqrt(t[1]);
+        if (nx.refines == 0) nx.r0 = rnorm;
+        nx.refines += 1;
+        nx.rnorm = rnorm;
+        nx.xnorm = xnorm;
+        const double ref = (sd.stop_rule == ATS_STOP_CERTIFIED) ? xnorm : nx.r0;
+        const double target = sd.tol * ref;
+        if (nx.final_pass) {
+          nx.phase = kDone;
+        } else if (!isfinite(rnorm)) {
+          nx.status = ATS_ERR_BREAKDOWN;
+          nx.phase = kDone;
+        } else if (rnorm <= target) {
+          nx.phase = kDone;
+        } else if (nx.refines > sd.max_refine) {
+          nx.status = ATS_ERR_NOT_CONVERGED;
+          nx.phase = kDone;
+        } else if (!(t[2] > 0.0)) {
+          nx.status = ATS_ERR_BREAKDOWN;
+          nx.phase = kDone;
+        } else {
+          nx.phase = kInner;
+          nx.rz = t[2];
+          nx.first = 1;
+          nx.inner_iters = 0;
+          nx.inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
+        }
+        commit_solve(a, cur, s, sd, nx, &s_base);
+      }
     }
-    __syncthreads();
-    if (s_base >= 0) {
-      int32_t *next = lists + (size_t)((cur ^ 1) * 2 + s_phase) * n_items;
-      for (int k = threadIdx.x; k < sd.n_items; k += kThreads) next[s_base + k] = sd.item_begin + k;
-    }
-    __syncthreads();
   }
   // the last CTA of the grid flips the list parity for the next tick
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(&ctl->cta_done, 1) == (int)gridDim.x - 1) {
-      ctl->cta_done = 0;
-      ctl->parity = cur ^ 1;
+    if (atomicAdd(&a.ctl->cta_done, 1) == (int)gridDim.x - 1) {
+      a.ctl->cta_done = 0;
+      a.ctl->parity = cur ^ 1;
       __threadfence();
     }
   }
 }
+
 
 // ---------------------------------------------------------------------------
 // coefficient build (one thread per cell)
@@ -1044,33 +1125,24 @@ static cudaError_t record(cudaEvent_t ev, cudaStream_t st, bool capture) {
 }
 
 template <typename T, bool kPaper>
-static cudaError_t tick_impl(const SolveDev *solves, SolveScalars *sc, const WorkItem *items,
-                             int32_t *lists, int n_items, TickCtl *ctl, double *partials,
-                             int *n_active, int grid, cudaStream_t st, cudaEvent_t *ev,
-                             bool capture, unsigned long long *cells) {
+static cudaError_t tick_impl(const TickArgs &a, int grid, cudaStream_t st, cudaEvent_t *ev, bool capture) {
   cudaError_t err;
   if ((err = record(ev ? ev[0] : nullptr, st, capture)) != cudaSuccess) return err;
-  k_op<T><<<grid, kThreads, 0, st>>>(solves, sc, items, lists, n_items, ctl, partials, cells);
+  k_op<T><<<grid, kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if ((err = record(ev ? ev[1] : nullptr, st, capture)) != cudaSuccess) return err;
-  k_ref<T><<<grid, kThreads, 0, st>>>(solves, sc, items, lists, n_items, ctl, partials, cells);
+  k_ref<T><<<grid, kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if ((err = record(ev ? ev[2] : nullptr, st, capture)) != cudaSuccess) return err;
-  k_upd<T, kPaper><<<grid, kThreads, 0, st>>>(solves, sc, items, lists, n_items, ctl, partials, n_active, cells);
+  k_upd<T, kPaper><<<grid, kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   return record(ev ? ev[3] : nullptr, st, capture);
 }
 
-cudaError_t launch_tick(bool fp64, bool paper, const SolveDev *solves, SolveScalars *sc,
-                        const WorkItem *items, int32_t *lists, int n_items, TickCtl *ctl,
-                        double *partials, int *n_active, int grid, cudaStream_t st,
-                        cudaEvent_t *ev, bool capture, unsigned long long *cells) {
-  if (fp64) {
-    return paper ? tick_impl<double, true>(solves, sc, items, lists, n_items, ctl, partials, n_active, grid, st, ev, capture, cells)
-                 : tick_impl<double, false>(solves, sc, items, lists, n_items, ctl, partials, n_active, grid, st, ev, capture, cells);
-  }
-  return paper ? tick_impl<float, true>(solves, sc, items, lists, n_items, ctl, partials, n_active, grid, st, ev, capture, cells)
-               : tick_impl<float, false>(solves, sc, items, lists, n_items, ctl, partials, n_active, grid, st, ev, capture, cells);
+cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cudaStream_t st, cudaEvent_t *ev,
+                        bool capture) {
+  if (fp64) return paper ? tick_impl<double, true>(a, grid, st, ev, capture) : tick_impl<double, false>(a, grid, st, ev, capture);
+  return paper ? tick_impl<float, true>(a, grid, st, ev, capture) : tick_impl<float, false>(a, grid, st, ev, capture);
 }
 
 // ---------------------------------------------------------------------------

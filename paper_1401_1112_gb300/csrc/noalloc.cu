@@ -41,13 +41,13 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // byte layout of the scratch array
 constexpr size_t kOffSolve = 0;
-constexpr size_t kOffScal = align256(kOffSolve + sizeof(SolveDev));
-constexpr size_t kOffCtl = align256(kOffScal + sizeof(SolveScalars));
+constexpr size_t kOffScal = align256(kOffSolve + sizeof(SolveDev));  // [2] by parity, then [1] final
+constexpr size_t kOffCtl = align256(kOffScal + 3 * sizeof(SolveScalars));
 constexpr size_t kOffActive = align256(kOffCtl + sizeof(TickCtl));
 constexpr size_t kOffItems = align256(kOffActive + sizeof(int));
 constexpr size_t kOffLists = align256(kOffItems + sizeof(WorkItem) * kNoAllocMaxItems);
 constexpr size_t kOffPart = align256(kOffLists + sizeof(int32_t) * 4 * kNoAllocMaxItems);
-constexpr size_t kOffXrec = align256(kOffPart + sizeof(double) * kNumPartials * kNoAllocMaxItems);
+constexpr size_t kOffXrec = align256(kOffPart + 3 * sizeof(double) * kNumPartials * kNoAllocMaxItems);
 constexpr size_t kOffVec = align256(kOffXrec + sizeof(int32_t) * (kNoAllocMaxCells / 8));
 constexpr size_t kVecBytes = align256(sizeof(double) * kNoAllocMaxCells);
 constexpr size_t kScratchBytes = kOffVec + 4 * kVecBytes;  // e, z, p0, p1
@@ -178,6 +178,7 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
 
   NA_TRY(cudaMemcpyAsync(d_solve, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
   NA_TRY(cudaMemcpyAsync(d_sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, st));
+  NA_TRY(cudaMemcpyAsync(d_sc + 2, &sc, sizeof(sc), cudaMemcpyHostToDevice, st));
   NA_TRY(cudaMemcpyAsync(d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, st));
   NA_TRY(cudaMemcpyAsync(d_active, &one, sizeof(int), cudaMemcpyHostToDevice, st));
   NA_TRY(cudaMemcpyAsync(d_items, items, sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice, st));
@@ -192,19 +193,32 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
   // the host copies above read stack memory: finish them before it goes away
   NA_TRY(cudaStreamSynchronize(st));
 
-  const int64_t max_ticks = (int64_t)max_iter + 2 * (40 + 2) + 16;
+  TickArgs ta;
+  std::memset(&ta, 0, sizeof(ta));
+  ta.solves = d_solve;
+  ta.sbuf = d_sc;
+  ta.final_sc = d_sc + 2;
+  ta.items = d_items;
+  ta.lists = d_lists;
+  ta.n_items = n_items;
+  ta.n_solves = 1;
+  ta.ctl = d_ctl;
+  ta.p_op = d_part;
+  ta.p_upd = d_part + (size_t)n_items * kNumPartials;
+  ta.n_active = d_active;
+  ta.cells = nullptr;
+  const int64_t max_ticks = 2 * ((int64_t)max_iter + 2 * (40 + 2)) + 16;
   int64_t ticks = 0;
   int active = 1;
   while (active > 0 && ticks < max_ticks) {
     for (int t = 0; t < 8; ++t)
-      NA_TRY(launch_tick(true, false, d_solve, d_sc, d_items, d_lists, n_items, d_ctl, d_part, d_active, grid, st,
-                         nullptr, false, nullptr));
+      NA_TRY(launch_tick(true, false, ta, grid, st, nullptr, false));
     ticks += 8;
     NA_TRY(cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     NA_TRY(cudaStreamSynchronize(st));
   }
   SolveScalars out;
-  NA_TRY(cudaMemcpyAsync(&out, d_sc, sizeof(out), cudaMemcpyDeviceToHost, st));
+  NA_TRY(cudaMemcpyAsync(&out, d_sc + 2, sizeof(out), cudaMemcpyDeviceToHost, st));
   NA_TRY(cudaStreamSynchronize(st));
 #undef NA_TRY
   ats_status status = out.status;

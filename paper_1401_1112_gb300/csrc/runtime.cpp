@@ -146,9 +146,11 @@ struct Plan {
   bool fp64 = true, paper = false;
   int n = 0, n_items = 0, grid = 1;
   SolveDev *d_solves = nullptr;
-  SolveScalars *d_sc = nullptr;
+  SolveScalars *d_sc = nullptr;     // [2][n] double-buffered scalars
+  SolveScalars *d_final = nullptr;  // [n] state of finished solves
   WorkItem *d_items = nullptr;
-  double *d_partials = nullptr;
+  double *d_partials = nullptr;     // [n_items][4] op partials, then [2][n_items][4] update partials
+  TickArgs targs{};
   int *d_active = nullptr;
   unsigned long long *d_cells = nullptr;
   int32_t *d_lists = nullptr;      // [2 parities][2 phases][n_items] active work lists
@@ -242,6 +244,7 @@ void plan_free(Plan *P) {
     if (e) cudaEventDestroy(e);
   dev_free(ctx, P->d_solves);
   dev_free(ctx, P->d_sc);
+  dev_free(ctx, P->d_final);
   dev_free(ctx, P->d_items);
   dev_free(ctx, P->d_partials);
   dev_free(ctx, P->d_active);
@@ -346,9 +349,10 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
   P->grid = std::max(1, std::min(P->n_items, bps * ctx->num_sms));
   if ((s = dev_alloc_t(ctx, n, &P->d_solves)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, n, &P->d_sc)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 2 * (size_t)n, &P->d_sc)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, n, &P->d_final)) != ATS_OK ||
       (s = dev_alloc_t(ctx, P->n_items, &P->d_items)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 3 * (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 4, &P->d_cells)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 4 * (size_t)P->n_items, &P->d_lists)) != ATS_OK ||
@@ -381,6 +385,21 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     for (int k = 0; k < n; ++k) fp[k] = P->levels[k]->err_flag;
     CUDA_TRY(cudaMemcpyAsync(P->d_flag_ptrs, fp.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  {
+    TickArgs &t = P->targs;
+    t.solves = P->d_solves;
+    t.sbuf = P->d_sc;
+    t.final_sc = P->d_final;
+    t.items = P->d_items;
+    t.lists = P->d_lists;
+    t.n_items = P->n_items;
+    t.n_solves = n;
+    t.ctl = P->d_ctl;
+    t.p_op = P->d_partials;
+    t.p_upd = P->d_partials + (size_t)P->n_items * kNumPartials;
+    t.n_active = P->d_active;
+    t.cells = P->d_cells;
   }
   CUDA_TRY(cudaEventCreateWithFlags(&P->poll_ev[0], cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&P->poll_ev[1], cudaEventDisableTiming));
@@ -417,11 +436,10 @@ ats_status plan_enqueue_chunk(Plan *P) {
       cudaGraph_t g = nullptr;
       CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       cudaError_t err = cudaSuccess;
-      for (int t = 0; t < k && err == cudaSuccess; ++t) {
-        err = launch_tick(P->fp64, P->paper, P->d_solves, P->d_sc, P->d_items, P->d_lists, P->n_items,
-                          P->d_ctl, P->d_partials, P->d_active, P->grid, st, prof ? &P->evs[4 * t] : nullptr, true,
-                          prof ? P->d_cells : nullptr);
-      }
+      TickArgs ta = P->targs;
+      if (!prof) ta.cells = nullptr;
+      for (int t = 0; t < k && err == cudaSuccess; ++t)
+        err = launch_tick(P->fp64, P->paper, ta, P->grid, st, prof ? &P->evs[4 * t] : nullptr, true);
       cudaError_t err2 = cudaStreamEndCapture(st, &g);
       if (err != cudaSuccess || err2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -445,11 +463,10 @@ ats_status plan_enqueue_chunk(Plan *P) {
       ats_status s = plan_ensure_events(P);
       if (s != ATS_OK) return s;
     }
-    for (int t = 0; t < k; ++t) {
-      CUDA_TRY(launch_tick(P->fp64, P->paper, P->d_solves, P->d_sc, P->d_items, P->d_lists, P->n_items,
-                           P->d_ctl, P->d_partials, P->d_active, P->grid, st, prof ? &P->evs[4 * t] : nullptr, false,
-                           prof ? P->d_cells : nullptr));
-    }
+    TickArgs ta = P->targs;
+    if (!prof) ta.cells = nullptr;
+    for (int t = 0; t < k; ++t)
+      CUDA_TRY(launch_tick(P->fp64, P->paper, ta, P->grid, st, prof ? &P->evs[4 * t] : nullptr, false));
   }
   P->ticks += k;
   P->launches += 3 * k;
@@ -535,6 +552,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   }
   CUDA_TRY(launch_init(P->fp64, P->d_solves, P->d_items, P->n_items, dev ? P->d_src : nullptr, P->grid, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_sc, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_final, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, 4 * sizeof(unsigned long long), st));
   CUDA_TRY(cudaMemcpyAsync(P->d_active, &n, sizeof(int), cudaMemcpyHostToDevice, st));
   {
@@ -550,8 +568,10 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   P->launches = 0;
   P->ticks = 0;
 
-  // host guard: every solve ends within max_iter + 2 (max_refine + 1) ticks
-  const int64_t max_ticks = (int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2) + 2 * P->opts.check_every;
+  // host guard: every solve ends within a bounded number of ticks
+  // (an inner pass's convergence is seen one tick late: two ticks per pass
+  // boundary)
+  const int64_t max_ticks = 2 * ((int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2)) + 2 * P->opts.check_every;
   int64_t ticks = 0;
   ats_status s;
   // Keep one poll interval queued ahead of the one being polled, so the GPU
@@ -598,7 +618,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
                                cudaMemcpyDeviceToHost, st));
   }
   std::vector<SolveScalars> sc(n);
-  CUDA_TRY(cudaMemcpyAsync(sc.data(), P->d_sc, sizeof(SolveScalars) * n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(sc.data(), P->d_final, sizeof(SolveScalars) * n, cudaMemcpyDeviceToHost, st));
   unsigned long long cells[4] = {0, 0, 0, 0};
   if (P->profiling) CUDA_TRY(cudaMemcpyAsync(cells, P->d_cells, sizeof(cells), cudaMemcpyDeviceToHost, st));
   std::vector<int> flags(n, 0);
