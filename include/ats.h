@@ -233,6 +233,21 @@ ats_status ats_hierarchy_destroy(ats_hierarchy *h);
 ats_status ats_hierarchy_level(ats_hierarchy *h, int level, ats_level **out);
 /* Set E and K ([N] of that level, host or device per mem); E is E^n. */
 ats_status ats_hierarchy_set_state(ats_hierarchy *h, int level, const double *E, const double *K, int mem);
+/* Radiation-matter mode (Sect. 2.1, flux-limited diffusion): per level the gas
+ * density rho and temperature T ([N], host or device per mem) and the opacity
+ * constant k0.  Once every level has them, each level solve first computes,
+ * on its leaf cells from rho, T and E^n: rho kappa_R = k0 rho^2 / T (kappa_R
+ * = kappa_P = k0 rho / T per unit mass), R = |grad E| / (rho kappa_R E) with
+ * central (one-sided at a missing neighbour) differences over same-level
+ * cells, the Levermore-Pomraning limiter lambda = (2 + R) / (6 + 3R + R^2),
+ * K = c lambda / (rho kappa_R); and the linearised gas coupling sigma = dt
+ * kappa_P rho c, mu = 4 a_R T^3 / (rho c_v), diagonal shift s = sigma / (1 +
+ * sigma mu), source s a_R T^4; after the solve T = T + sigma (E - a_R T^4) /
+ * (rho c_v (1 + sigma mu)).  Units c = a_R = c_v = 1.  K of the level is set
+ * from the current E immediately. */
+ats_status ats_hierarchy_set_fld(ats_hierarchy *h, int level, const double *rho, const double *T, double k0,
+                                 int mem);
+ats_status ats_hierarchy_get_temperature(ats_hierarchy *h, int level, double *T, int mem);
 /* Copy E of a level out; refined cells carry the restriction of their children. */
 ats_status ats_hierarchy_get_state(ats_hierarchy *h, int level, double *E, int mem);
 /* Advance `level` by dt: with ATS_ORDER_FINE_FIRST the finer levels first take

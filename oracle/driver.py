@@ -21,6 +21,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import DIRICHLET, REL_COARSER, REL_FINER, STOP_CERTIFIED, assemble, pcg
+from . import fld as fldmod
 
 AX = (0, 0, 1, 1, 2, 2)
 SG = (-1, 1, -1, 1, -1, 1)
@@ -41,10 +42,21 @@ class _Level:
 
 
 class Hierarchy:
-    def __init__(self, levels, states, order="fine_first"):
+    def __init__(self, levels, states, order="fine_first", fld=None):
+        """states: per level (E, K).  fld: None, or (per-level rho, per-level T,
+        k0) for the radiation-matter mode (K, s, src from the gas state before
+        every level solve, T updated after it)."""
         self.L = [_Level(d) for d in levels]
         self.E = [np.array(e, dtype=np.float64) for e, _ in states]
         self.K = [np.array(k, dtype=np.float64) for _, k in states]
+        self.fld = None
+        if fld is not None:
+            rho, T, k0 = fld
+            self.fld = ([np.array(r, dtype=np.float64) for r in rho], [np.array(t, dtype=np.float64) for t in T], k0)
+            for l, d in enumerate(levels):
+                leaf = d.leaf_cells()
+                K0, _, _ = fldmod.coefficients(d, self.fld[0][l], self.fld[1][l], self.E[l], 1.0, k0)
+                self.K[l][leaf] = K0[leaf]
         self.E_prev = [e.copy() for e in self.E]
         self.order = order
         self.faces = [self._faces(l) for l in range(len(levels))]
@@ -89,23 +101,30 @@ class Hierarchy:
     def solve_level(self, l, dt, theta, tol):
         self.restrict(l)
         desc = self.L[l].desc
+        s_shift = src = None
+        if self.fld is not None:
+            leaf = desc.leaf_cells()
+            Kf, s_shift, src = fldmod.coefficients(desc, self.fld[0][l], self.fld[1][l], self.E[l], dt, self.fld[2])
+            self.K[l][leaf] = Kf[leaf]
+            s_shift = np.where(leaf, s_shift, 0.0)
+            src = np.where(leaf, src, 0.0)
         f = self.faces[l]
         fcell = np.array([a for a, _, _, _ in f], dtype=np.int32)
         fdir = np.array([b for _, b, _, _ in f], dtype=np.int8)
         frel = np.array([c for _, _, c, _ in f], dtype=np.int8)
         fE = np.zeros(len(f))
         fK = np.zeros(len(f))
-        for k, (_, _, rel, src) in enumerate(f):
+        for k, (_, _, rel, j) in enumerate(f):
             if rel == REL_FINER:
-                fE[k] = self.E[l][src]
-                fK[k] = self.K[l][src]
+                fE[k] = self.E[l][j]
+                fK[k] = self.K[l][j]
             else:
                 if self.order == "fine_first":
-                    fE[k] = self.E[l - 1][src]       # coarse held at E^n
+                    fE[k] = self.E[l - 1][j]       # coarse held at E^n
                 else:
-                    e0, e1 = self.E_prev[l - 1][src], self.E[l - 1][src]
+                    e0, e1 = self.E_prev[l - 1][j], self.E[l - 1][j]
                     fE[k] = e0 + theta * (e1 - e0)
-                fK[k] = self.K[l - 1][src]
+                fK[k] = self.K[l - 1][j]
 
         class D:
             pass
@@ -116,11 +135,15 @@ class Hierarchy:
         lv.face_kind = np.full(len(f), DIRICHLET, dtype=np.int8)
         lv.face_alpha = np.ones(len(f))
         self.E_prev[l] = self.E[l].copy()
-        S = assemble(lv, dt, self.K[l], self.E[l], face_K=fK, face_E=fE)
+        S = assemble(lv, dt, self.K[l], self.E[l], s=s_shift, src=src, face_K=fK, face_E=fE)
         x, info = pcg(S, self.E[l], tol=tol, stop_rule=STOP_CERTIFIED)
         assert info["status"] == 0, info
         self.iterations += info["iterations"]
         self.E[l] = x
+        if self.fld is not None:
+            leaf = desc.leaf_cells()
+            Tn = fldmod.update_temperature(self.fld[0][l], self.fld[1][l], x, dt, self.fld[2])
+            self.fld[1][l] = np.where(leaf, Tn, self.fld[1][l])
 
     def advance(self, l, dt, tol=5e-11, theta=1.0):
         fine = l + 1 < len(self.L)

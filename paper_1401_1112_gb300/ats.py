@@ -123,6 +123,8 @@ _SIGS = [
     ("ats_hierarchy_get_state", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
     ("ats_level_advance", ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ats_solve_opts),
                                          ctypes.POINTER(ats_solve_stats)]),
+    ("ats_hierarchy_set_fld", ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int]),
+    ("ats_hierarchy_get_temperature", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
     ("ats_hierarchy_plan_faces", ctypes.c_int, [ctypes.POINTER(ats_hierarchy_desc), ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_int64), P, P, P, P]),
     ("ats_solve_noalloc", ctypes.c_int, [ctypes.c_int, P, ctypes.c_int64, P, P, P, ctypes.c_double, P, P,
@@ -451,6 +453,18 @@ def ats_hierarchy_get_state(h, level, out):
     return _check(lib().ats_hierarchy_get_state(h, level, _ptr(out), mem), "ats_hierarchy_get_state")
 
 
+def ats_hierarchy_set_fld(h, level, rho, T, k0):
+    keep = []
+    mem = _mem_of(rho, T)
+    return _check(lib().ats_hierarchy_set_fld(h, level, _ptr(rho, keep=keep), _ptr(T, keep=keep), float(k0), mem),
+                  "ats_hierarchy_set_fld")
+
+
+def ats_hierarchy_get_temperature(h, level, out):
+    mem = _mem_of(out)
+    return _check(lib().ats_hierarchy_get_temperature(h, level, _ptr(out), mem), "ats_hierarchy_get_temperature")
+
+
 def ats_level_advance(h, level, dt, opts: Optional[ats_solve_opts] = None):
     o = opts if opts is not None else make_opts()
     st = ats_solve_stats()
@@ -546,6 +560,14 @@ class Hierarchy:
     def state(self, level):
         out = np.empty(self.levels[level].n_cell)
         ats_hierarchy_get_state(self.handle, level, out)
+        return out
+
+    def set_fld(self, level, rho, T, k0):
+        ats_hierarchy_set_fld(self.handle, level, rho, T, k0)
+
+    def temperature(self, level):
+        out = np.empty(self.levels[level].n_cell)
+        ats_hierarchy_get_temperature(self.handle, level, out)
         return out
 
     def advance(self, level, dt, **opts):

@@ -158,6 +158,17 @@ cudaError_t launch_apply64(const SolveDev *solve_host_copy, const double *x, dou
 
 int tick_blocks_per_sm(bool fp64, bool paper);
 
+// Flux-limited diffusion coefficients (K, s, src from rho, T, E^n) and the
+// gas temperature update after a solve (kernels.cu).
+cudaError_t launch_fld_coef(int64_t n_oct, const int32_t *nbr, const uint8_t *leaf, const double *E, const double *rho,
+                            const double *T, double dx, double dt, double k0, double *K, double *s, double *src,
+                            cudaStream_t st);
+cudaError_t launch_fld_temperature(int64_t N, const uint8_t *leaf, const double *E, const double *rho, double *T,
+                                   double dt, double k0, cudaStream_t st);
+// Device topology of a level (runtime.cpp): neighbour table and leaf masks.
+const int32_t *level_nbr(const ats_level *L);
+const uint8_t *level_leaf(const ats_level *L);
+
 // AMR coupling kernels (restriction of children, ghost gather of interface faces).
 cudaError_t launch_restrict(int n, const int32_t *cell, const int32_t *child, const double *Ef, const double *Kf,
                             double *Ec, double *Kc, cudaStream_t st);

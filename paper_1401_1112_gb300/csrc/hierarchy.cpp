@@ -128,6 +128,8 @@ std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, 
 
 struct HLevel {
   ats_level *lvl = nullptr;
+  double dx = 0.0;
+  double *rho = nullptr, *T = nullptr, *s = nullptr, *src = nullptr;  // flux-limited diffusion state
   int64_t N = 0, n_face = 0, n_restrict = 0;
   double *E = nullptr, *E_prev = nullptr, *K = nullptr, *fE = nullptr, *fK = nullptr;
   int8_t *src_rel = nullptr;  // 0 same level (FINER), 1 coarser
@@ -137,6 +139,8 @@ struct HLevel {
 struct ats_hierarchy {
   ats_context *ctx = nullptr;
   int order = ATS_ORDER_FINE_FIRST;
+  bool fld = false;  // K, s and src from the gas state before every level solve
+  double k0 = 0.0;
   std::vector<HLevel> lv;
 };
 
@@ -153,7 +157,7 @@ namespace {
 
 void hierarchy_free(ats_hierarchy *H) {
   for (HLevel &h : H->lv) {
-    void *ptrs[] = {h.E, h.E_prev, h.K, h.fE, h.fK, h.src_rel, h.src_cell, h.r_cell, h.r_child};
+    void *ptrs[] = {h.E, h.E_prev, h.K, h.fE, h.fK, h.src_rel, h.src_cell, h.r_cell, h.r_child, h.rho, h.T, h.s, h.src};
     for (void *p : ptrs) ctx_free(H->ctx, p);
     if (h.lvl) ats_level_destroy(h.lvl);
   }
@@ -176,6 +180,12 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   cudaStream_t st = ctx_stream(H->ctx);
   ats_status s = restrict_into(H, l);
   if (s != ATS_OK) return s;
+  if (H->fld) {
+    // coefficients frozen at E^n of this level (leaf cells; refined cells keep
+    // the restriction of their children's K)
+    H_TRY(launch_fld_coef(h.N / 8, level_nbr(h.lvl), level_leaf(h.lvl), h.E, h.rho, h.T, h.dx, dt, H->k0, h.K, h.s,
+                          h.src, st));
+  }
   const HLevel *coarse = l > 0 ? &H->lv[l - 1] : nullptr;
   // fine first: the coarser level has not moved, its current E is E^n;
   // coarse first: interpolate between its E^n (E_prev) and E^{n+1} (E)
@@ -192,6 +202,10 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   c.E_old = h.E_prev;
   c.face_K = h.n_face ? h.fK : nullptr;
   c.face_E = h.n_face ? h.fE : nullptr;
+  if (H->fld) {
+    c.s = h.s;
+    c.src = h.src;
+  }
   if ((s = ats_level_build_operator(h.lvl, &c)) != ATS_OK) return s;
   ats_solve_opts o;
   if (opts) o = *opts;
@@ -200,6 +214,7 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   ats_solve_stats st1;
   std::memset(&st1, 0, sizeof(st1));
   s = ats_solve(h.lvl, nullptr, h.E, &o, &st1);
+  if (s == ATS_OK && H->fld) H_TRY(launch_fld_temperature(h.N, level_leaf(h.lvl), h.E, h.rho, h.T, dt, H->k0, st));
   if (acc) {
     acc->iterations += st1.iterations;
     acc->refinements += st1.refinements;
@@ -309,6 +324,7 @@ ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc
       return s;
     }
     h.N = 8 * d.n_oct;
+    h.dx = d.dx;
     h.n_face = nf;
     h.n_restrict = (int64_t)lf.restrict_cell.size();
     void *p;
@@ -373,6 +389,50 @@ ats_status ats_hierarchy_set_state(ats_hierarchy *H, int level, const double *E,
   H_TRY(cudaMemcpyAsync(h.E, E, sizeof(double) * h.N, k, st));
   H_TRY(cudaMemcpyAsync(h.E_prev, E, sizeof(double) * h.N, k, st));
   H_TRY(cudaMemcpyAsync(h.K, K, sizeof(double) * h.N, k, st));
+  H_TRY(cudaStreamSynchronize(st));
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_set_fld(ats_hierarchy *H, int level, const double *rho, const double *T, double k0, int mem) {
+  if (!H || level < 0 || level >= (int)H->lv.size() || !rho || !T || !(k0 > 0.0)) {
+    set_error("ats_hierarchy_set_fld: bad argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  HLevel &h = H->lv[level];
+  cudaStream_t st = ctx_stream(H->ctx);
+  ats_status s;
+  void *p;
+  if (!h.rho) {
+    const size_t b = sizeof(double) * h.N;
+    if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
+    h.rho = (double *)p;
+    if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
+    h.T = (double *)p;
+    if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
+    h.s = (double *)p;
+    if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
+    h.src = (double *)p;
+  }
+  const cudaMemcpyKind k = mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  H_TRY(cudaMemcpyAsync(h.rho, rho, sizeof(double) * h.N, k, st));
+  H_TRY(cudaMemcpyAsync(h.T, T, sizeof(double) * h.N, k, st));
+  H->k0 = k0;
+  // initial K from the current E (dt does not enter K)
+  H_TRY(launch_fld_coef(h.N / 8, level_nbr(h.lvl), level_leaf(h.lvl), h.E, h.rho, h.T, h.dx, 1.0, k0, h.K, h.s,
+                        h.src, st));
+  H_TRY(cudaStreamSynchronize(st));
+  bool all = true;
+  for (const HLevel &x : H->lv) all = all && x.rho != nullptr;
+  H->fld = all;
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_get_temperature(ats_hierarchy *H, int level, double *T, int mem) {
+  if (!H || level < 0 || level >= (int)H->lv.size() || !T || !H->lv[level].T) return ATS_ERR_INVALID_ARG;
+  HLevel &h = H->lv[level];
+  cudaStream_t st = ctx_stream(H->ctx);
+  H_TRY(cudaMemcpyAsync(T, h.T, sizeof(double) * h.N,
+                        mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   H_TRY(cudaStreamSynchronize(st));
   return ATS_OK;
 }

@@ -1052,6 +1052,84 @@ __global__ void k_gather_faces(int n_face, const int8_t *__restrict__ src_rel, c
   }
 }
 
+// Flux-limited diffusion coefficients and linearised coupling of one level
+// (Sect. 2.1; the limiter and linearisation readings are stated with the
+// entry point): for every leaf cell, from rho, T and E^n,
+//   rho kappa_R = k0 rho^2 / T,  R = |grad E| / (rho kappa_R E),
+//   lambda = (2 + R) / (6 + 3 R + R^2),  K = c lambda / (rho kappa_R),
+//   sigma = dt kappa_P rho c (kappa_P = kappa_R),  mu = 4 a_R T^3 / (rho c_v),
+//   s = sigma / (1 + sigma mu),  src = s a_R T^4;
+// grad E by central differences over same-level cells, one-sided where a
+// neighbour is missing.  Non-leaf cells keep K (restricted) and get s = src = 0.
+__global__ void k_fld_coef(int64_t n_oct, const int32_t *__restrict__ nbr, const uint8_t *__restrict__ leaf,
+                           const double *__restrict__ E, const double *__restrict__ rho,
+                           const double *__restrict__ T, double dx, double dt, double k0, double *__restrict__ K,
+                           double *__restrict__ s_out, double *__restrict__ src_out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 8 * n_oct) return;
+  const int64_t o = i >> 3;
+  const int c = (int)(i & 7);
+  if (!((leaf[o] >> c) & 1)) {
+    s_out[i] = 0.0;
+    src_out[i] = 0.0;
+    return;
+  }
+  const double e = E[i];
+  double g2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const int m = 1 << a;
+    const int b = (c >> a) & 1;
+    const double e_in = E[o * 8 + (c ^ m)];  // the other cell of the oct along a
+    const int nb = nbr[o * 6 + 2 * a + b];    // the oct on this cell's outer side
+    double g;
+    if (nb >= 0) {
+      const double e_out = E[(int64_t)nb * 8 + (c ^ m)];
+      // b = 0: in-oct neighbour is at +a, outer at -a; b = 1: the reverse
+      g = b == 0 ? (e_in - e_out) / (2.0 * dx) : (e_out - e_in) / (2.0 * dx);
+    } else {
+      g = b == 0 ? (e_in - e) / dx : (e - e_in) / dx;
+    }
+    g2 += g * g;
+  }
+  const double r = rho[i], t = T[i];
+  const double kr = k0 * r * r / t;
+  const double R = sqrt(g2) / (kr * e);
+  const double lam = (2.0 + R) / (6.0 + 3.0 * R + R * R);
+  K[i] = lam / kr;  // c = 1
+  const double sigma = dt * kr;
+  const double mu = 4.0 * t * t * t / r;  // a_R = c_v = 1
+  const double sv = sigma / (1.0 + sigma * mu);
+  s_out[i] = sv;
+  src_out[i] = sv * t * t * t * t;
+}
+
+// Gas temperature after the radiation solve: T = T_n + sigma (E - a_R T_n^4) /
+// (rho c_v (1 + sigma mu)) on leaf cells.
+__global__ void k_fld_temperature(int64_t N, const uint8_t *__restrict__ leaf, const double *__restrict__ E,
+                                  const double *__restrict__ rho, double *__restrict__ T, double dt, double k0) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N || !((leaf[i >> 3] >> (i & 7)) & 1)) return;
+  const double r = rho[i], t = T[i];
+  const double kr = k0 * r * r / t;
+  const double sigma = dt * kr;
+  const double mu = 4.0 * t * t * t / r;
+  T[i] = t + sigma * (E[i] - t * t * t * t) / (r * (1.0 + sigma * mu));
+}
+
+cudaError_t launch_fld_coef(int64_t n_oct, const int32_t *nbr, const uint8_t *leaf, const double *E, const double *rho,
+                            const double *T, double dx, double dt, double k0, double *K, double *s, double *src,
+                            cudaStream_t st) {
+  const int64_t N = 8 * n_oct;
+  k_fld_coef<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(n_oct, nbr, leaf, E, rho, T, dx, dt, k0, K, s, src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fld_temperature(int64_t N, const uint8_t *leaf, const double *E, const double *rho, double *T,
+                                   double dt, double k0, cudaStream_t st) {
+  k_fld_temperature<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, leaf, E, rho, T, dt, k0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_restrict(int n, const int32_t *cell, const int32_t *child, const double *Ef, const double *Kf,
                             double *Ec, double *Kc, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;

@@ -132,6 +132,8 @@ namespace ats {
 ats_status ctx_alloc(ats_context *ctx, size_t bytes, void **out) { return dev_alloc(ctx, bytes, out); }
 void ctx_free(ats_context *ctx, void *p) { dev_free(ctx, p); }
 cudaStream_t ctx_stream(const ats_context *ctx) { return ctx->stream; }
+const int32_t *level_nbr(const ats_level *L) { return L->nbr; }
+const uint8_t *level_leaf(const ats_level *L) { return L->leaf; }
 int ctx_device(const ats_context *ctx) { return ctx->device; }
 }  // namespace ats
 

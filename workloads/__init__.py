@@ -433,3 +433,72 @@ def random_hierarchy(seed: int, n0: int = 8, n_levels: int = 3, frac: float = 0.
     for lv in levels:
         states.append((rng.uniform(0.5, 1.5, lv.n_cell), np.exp(rng.standard_normal(lv.n_cell))))
     return levels, states, float(rng.uniform(2.0, 20.0)) * dx0 * dx0 / 2.0
+
+
+def _trilinear(field: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Trilinear interpolation of a cell-centred field on [-1/2, 1/2]^3
+    (n^3 cells) at points pts [m, 3], clamped at the walls."""
+    n = field.shape[0]
+    u = (pts + 0.5) * n - 0.5
+    i0 = np.clip(np.floor(u).astype(np.int64), 0, n - 1)
+    i1 = np.clip(i0 + 1, 0, n - 1)
+    f = np.clip(u - i0, 0.0, 1.0)
+    out = np.zeros(len(pts))
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                ix = i1[:, 0] if dx else i0[:, 0]
+                iy = i1[:, 1] if dy else i0[:, 1]
+                iz = i1[:, 2] if dz else i0[:, 2]
+                w = (f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1]) * (f[:, 2] if dz else 1 - f[:, 2])
+                out += w * field[ix, iy, iz]
+    return out
+
+
+def config3(n0: int = 128, n_levels: int = 4, sigma_ln: float = 1.5, r0: float = 0.05, seed: int = 1403,
+            cfl: float = 30.0):
+    """FLD radiation-matter workload on an AMR grid: base n0^3 on
+    [-1/2, 1/2]^3; density = trilinear interpolation of a seeded log-normal
+    base field (sigma_ln, mean 1) times a central core 1/(1+(r/r0)^2); a cell
+    of level l < n_levels-1 is refined where density > 4^(l+1) x the base
+    mean, then eroded to keep 2:1 balance.  T0 = 1; E0 = a_R T0^4 (1 + 10
+    exp(-r^2/(2 0.05^2))); k0 makes the median base-cell optical depth
+    rho kappa_R dx0 = 1.  Returns (levels, per-level (E, rho, T), k0, cfl) -- the
+    time step is set from the base-level K by the caller (cfl x explicit)."""
+    rng = np.random.default_rng(seed)
+    dx0 = 1.0 / n0
+    lnrho = sigma_ln * rng.standard_normal((n0, n0, n0))
+    base_field = np.exp(lnrho)
+    base_field /= base_field.mean()
+    base = box_octs(n0 // 2, n0 // 2, n0 // 2)
+
+    def density(lv_cells, dx):
+        xyz = -0.5 + (lv_cells + 0.5) * dx
+        r2 = (xyz ** 2).sum(1)
+        return _trilinear(base_field, xyz) / (1.0 + r2 / (r0 * r0))
+
+    base_cells = _cells_of_octs(base)
+    rho_mean = density(base_cells, dx0).mean()
+    refined = []
+    octs = base.astype(np.int64)
+    for l in range(n_levels - 1):
+        cells = _cells_of_octs(octs)
+        dx = dx0 / 2 ** l
+        rho = density(cells, dx)
+        want = cells[rho > 4.0 ** (l + 1) * rho_mean]
+        ref = balance_refinement(cells, want, n0 * 2 ** l)
+        if len(ref) == 0:
+            break
+        refined.append(ref)
+        octs = ref
+    levels = hierarchy_from_refined(base, refined, dx0)
+    states = []
+    for lv in levels:
+        cells = lv.cell_xyz()
+        rho = density(cells, lv.dx)
+        xyz = cell_centres(lv, (-0.5, -0.5, -0.5))
+        E = 1.0 + 10.0 * np.exp(-(xyz ** 2).sum(1) / (2 * 0.05 ** 2))
+        states.append((E, rho, np.ones(lv.n_cell)))
+    rho0 = states[0][1]
+    k0 = 1.0 / (np.median(rho0 * rho0) * dx0)
+    return levels, states, k0, cfl
