@@ -266,6 +266,50 @@ ats_status ats_hierarchy_plan_faces(const ats_hierarchy_desc *desc, int level, i
                                     int32_t *face_cell, int8_t *face_dir, int8_t *face_rel,
                                     int32_t *src_cell);
 
+/* ---- serving: continuous batching of level solves ---------------------------- */
+/* A server owns a private context on `device` and a scheduler thread.  Any
+ * thread submits level solves; the scheduler admits queued requests in arrival
+ * order whenever a slot, enough work items and the device-memory budget allow
+ * (an estimate of the request's resident bytes), builds them on the device and
+ * joins them to the solves already in flight; every device tick advances all
+ * resident solves one step (one CUDA graph of `check_every` ticks); finished
+ * solves are copied back and their memory released.  A solve's arithmetic
+ * involves no other solve: its result is the same alone and in any mix.
+ * Requests whose estimate exceeds the whole budget fail with
+ * ATS_ERR_OVER_BUDGET.  All ats_server_* calls are thread-safe. */
+typedef struct ats_server ats_server;
+typedef struct {
+  ats_solve_opts solve; /* precision, max_iter, inner_rtol, check_every, tile (tol/stop per request) */
+  int max_slots;        /* resident solves at most (0 = 1024)                                   */
+  int max_items;        /* work-item pool (0 = 65536)                                          */
+} ats_server_opts;
+typedef struct {
+  const ats_level_desc *level; /* host topology, copied at submit                          */
+  const ats_coef_desc *coef;   /* host per-step values (mem = ATS_MEM_HOST), copied at submit */
+  const double *x0;            /* host [N] initial guess or NULL (= E_old)                   */
+  double tol;                  /* stopping tolerance of this request (0 = 1e-10)             */
+  int stop_rule;               /* ATS_STOP_RESIDUAL or ATS_STOP_CERTIFIED                     */
+} ats_request;
+typedef struct {
+  ats_status status;
+  ats_solve_stats stats;
+  double latency_us; /* submit to result ready                      */
+  double queue_us;   /* submit to admission                          */
+} ats_result;
+typedef struct {
+  uint64_t completed, queued;
+  int64_t ticks;
+  int peak_resident;
+  size_t resident_bytes;
+} ats_server_counters;
+ats_status ats_server_create(int device, size_t mem_budget_bytes, const ats_server_opts *opts, ats_server **out);
+/* Stops after the queued and resident solves are done, then frees everything. */
+ats_status ats_server_destroy(ats_server *server);
+ats_status ats_server_submit(ats_server *server, const ats_request *req, uint64_t *ticket);
+/* Wait for a ticket (timeout_us < 0: forever); x_out: host [N] or NULL. */
+ats_status ats_server_wait(ats_server *server, uint64_t ticket, int64_t timeout_us, double *x_out, ats_result *res);
+ats_status ats_server_stats(ats_server *server, ats_server_counters *out);
+
 /* ---- allocation-free solve ------------------------------------------------- */
 /* The paper has no counterpart to this entry point: it is a service for
  * callers that cannot allocate device memory (code inside a CUDA stream

@@ -92,6 +92,25 @@ class ats_solve_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ats_server_opts(ctypes.Structure):
+    _fields_ = [("solve", ats_solve_opts), ("max_slots", ctypes.c_int), ("max_items", ctypes.c_int)]
+
+
+class ats_request(ctypes.Structure):
+    _fields_ = [("level", ctypes.POINTER(ats_level_desc)), ("coef", ctypes.POINTER(ats_coef_desc)), ("x0", P),
+                ("tol", ctypes.c_double), ("stop_rule", ctypes.c_int)]
+
+
+class ats_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("stats", ats_solve_stats), ("latency_us", ctypes.c_double),
+                ("queue_us", ctypes.c_double)]
+
+
+class ats_server_counters(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("ticks", ctypes.c_int64),
+                ("peak_resident", ctypes.c_int), ("resident_bytes", ctypes.c_size_t)]
+
+
 # (name, restype, argtypes) of every exported entry point
 _SIGS = [
     ("ats_context_create", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(P)]),
@@ -127,6 +146,12 @@ _SIGS = [
     ("ats_hierarchy_get_temperature", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
     ("ats_hierarchy_plan_faces", ctypes.c_int, [ctypes.POINTER(ats_hierarchy_desc), ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_int64), P, P, P, P]),
+    ("ats_server_create", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(ats_server_opts),
+                                         ctypes.POINTER(P)]),
+    ("ats_server_destroy", ctypes.c_int, [P]),
+    ("ats_server_submit", ctypes.c_int, [P, ctypes.POINTER(ats_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("ats_server_wait", ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_int64, P, ctypes.POINTER(ats_result)]),
+    ("ats_server_stats", ctypes.c_int, [P, ctypes.POINTER(ats_server_counters)]),
     ("ats_solve_noalloc", ctypes.c_int, [ctypes.c_int, P, ctypes.c_int64, P, P, P, ctypes.c_double, P, P,
                                          ctypes.c_double, ctypes.c_int, ctypes.POINTER(ats_solve_stats)]),
 ]
@@ -490,6 +515,57 @@ def ats_hierarchy_plan_faces(levels, level, order=ATS_ORDER_FINE_FIRST):
     return cell, dr, rel, src
 
 
+def ats_server_create(device=0, mem_budget_bytes=0, opts: Optional[ats_solve_opts] = None, max_slots=0,
+                      max_items=0):
+    so = ats_server_opts()
+    so.solve = opts if opts is not None else make_opts()
+    so.max_slots = max_slots
+    so.max_items = max_items
+    h = P()
+    _check(lib().ats_server_create(device, mem_budget_bytes, ctypes.byref(so), ctypes.byref(h)), "ats_server_create")
+    return h
+
+
+def ats_server_destroy(server):
+    return _check(lib().ats_server_destroy(server), "ats_server_destroy")
+
+
+def ats_server_submit(server, level, dt, K, E_old, tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, x0=None, s=None,
+                      src=None, face_K=None, face_E=None, face_F=None):
+    """Submit one level solve (host arrays, copied by the call); returns the ticket."""
+    keep = []
+    d = _level_desc(level, keep)
+    c = coef_desc(dt, K, E_old, s=s, src=src, face_K=face_K, face_E=face_E, face_F=face_F, keep=keep)
+    if c.mem != ATS_MEM_HOST:
+        raise ValueError("server requests take host arrays")
+    r = ats_request()
+    r.level = ctypes.pointer(d)
+    r.coef = ctypes.pointer(c)
+    r.x0 = _ptr(x0, keep=keep)
+    r.tol = float(tol)
+    r.stop_rule = int(stop_rule)
+    t = ctypes.c_uint64()
+    _check(lib().ats_server_submit(server, ctypes.byref(r), ctypes.byref(t)), "ats_server_submit")
+    return t.value
+
+
+def ats_server_wait(server, ticket, n_cell, timeout_us=-1):
+    """Returns (status, x, result dict with stats, latency_us, queue_us)."""
+    x = np.empty(n_cell)
+    res = ats_result()
+    code = lib().ats_server_wait(server, ctypes.c_uint64(ticket), int(timeout_us), x.ctypes.data_as(P),
+                                 ctypes.byref(res))
+    out = {"status": res.status, "stats": res.stats.as_dict(), "latency_us": res.latency_us,
+           "queue_us": res.queue_us}
+    return code, x, out
+
+
+def ats_server_stats(server):
+    c = ats_server_counters()
+    _check(lib().ats_server_stats(server, ctypes.byref(c)), "ats_server_stats")
+    return {k: getattr(c, k) for k, _ in c._fields_}
+
+
 # ---------------------------------------------------------------------------
 # handle owners
 # ---------------------------------------------------------------------------
@@ -576,6 +652,27 @@ class Hierarchy:
     def close(self):
         if self.handle:
             ats_hierarchy_destroy(self.handle)
+            self.handle = None
+
+
+class Server:
+    def __init__(self, device=0, mem_budget_bytes=0, max_slots=0, max_items=0, **opts):
+        self.handle = ats_server_create(device, mem_budget_bytes, make_opts(**opts), max_slots, max_items)
+
+    def submit(self, level, step, tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, x0=None):
+        return ats_server_submit(self.handle, level, step.dt, step.K, step.E, tol=tol, stop_rule=stop_rule, x0=x0,
+                                 s=step.s, src=step.src, face_K=step.face_K, face_E=step.face_E,
+                                 face_F=step.face_F)
+
+    def wait(self, ticket, n_cell, timeout_us=-1):
+        return ats_server_wait(self.handle, ticket, n_cell, timeout_us)
+
+    def stats(self):
+        return ats_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ats_server_destroy(self.handle)
             self.handle = None
 
 

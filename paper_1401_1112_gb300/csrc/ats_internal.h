@@ -165,6 +165,19 @@ cudaError_t launch_fld_coef(int64_t n_oct, const int32_t *nbr, const uint8_t *le
                             cudaStream_t st);
 cudaError_t launch_fld_temperature(int64_t N, const uint8_t *leaf, const double *E, const double *rho, double *T,
                                    double dt, double k0, cudaStream_t st);
+// Serving support (runtime.cpp): the device descriptor of one solve of a
+// built level with the given options and work-item range (allocates the
+// level's CG vectors of that precision if needed), the work-item tiling, and
+// level accessors.
+ats_status solve_dev_for(ats_level *L, const ats_solve_opts &o, bool fp64, int item_begin, int n_items,
+                         SolveDev *out);
+int tile_for(int64_t n_oct, int requested);
+ats_solve_opts normalized_opts(const ats_solve_opts *in);
+double *level_x64(ats_level *L);
+int64_t level_cells(const ats_level *L);
+// Admission of new solves between ticks: append each new solve's items to the
+// current tick's refinement list and count it active (kernels.cu).
+cudaError_t launch_admit(const TickArgs &a, const int32_t *slots, int n_new, cudaStream_t st);
 // Device topology of a level (runtime.cpp): neighbour table and leaf masks.
 const int32_t *level_nbr(const ats_level *L);
 const uint8_t *level_leaf(const ats_level *L);

@@ -1224,6 +1224,30 @@ cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cuda
 }
 
 // ---------------------------------------------------------------------------
+// admission of new solves between ticks (continuous batching)
+// ---------------------------------------------------------------------------
+
+__global__ void k_admit(TickArgs a, const int32_t *__restrict__ slots, int n_new) {
+  __shared__ int base;
+  const int s = slots[blockIdx.x];
+  const SolveDev &sd = a.solves[s];
+  const int cur = a.ctl->parity;
+  if (threadIdx.x == 0) {
+    base = atomicAdd(&a.ctl->count[cur][kRefine], sd.n_items);
+    atomicAdd(a.n_active, 1);
+  }
+  __syncthreads();
+  int32_t *l = a.lists + (size_t)(cur * 2 + kRefine) * a.n_items;
+  for (int k = threadIdx.x; k < sd.n_items; k += blockDim.x) l[base + k] = sd.item_begin + k;
+}
+
+cudaError_t launch_admit(const TickArgs &a, const int32_t *slots, int n_new, cudaStream_t st) {
+  if (n_new <= 0) return cudaSuccess;
+  k_admit<<<n_new, 128, 0, st>>>(a, slots, n_new);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // solve start / end over the work list
 // ---------------------------------------------------------------------------
 

@@ -133,6 +133,8 @@ ats_status ctx_alloc(ats_context *ctx, size_t bytes, void **out) { return dev_al
 void ctx_free(ats_context *ctx, void *p) { dev_free(ctx, p); }
 cudaStream_t ctx_stream(const ats_context *ctx) { return ctx->stream; }
 const int32_t *level_nbr(const ats_level *L) { return L->nbr; }
+double *level_x64(ats_level *L) { return L->x64; }
+int64_t level_cells(const ats_level *L) { return L->N; }
 const uint8_t *level_leaf(const ats_level *L) { return L->leaf; }
 int ctx_device(const ats_context *ctx) { return ctx->device; }
 }  // namespace ats
@@ -651,6 +653,43 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
 }
 
 }  // namespace
+
+namespace ats {
+int tile_for(int64_t n_oct, int requested) { return choose_tile(n_oct, requested); }
+ats_solve_opts normalized_opts(const ats_solve_opts *in) { return normalize(in); }
+ats_status solve_dev_for(ats_level *L, const ats_solve_opts &o, bool fp64, int item_begin, int n_items,
+                         SolveDev *out) {
+  ats_status s = ensure_vectors(L, fp64);
+  if (s != ATS_OK) return s;
+  SolveDev &sd = *out;
+  std::memset(&sd, 0, sizeof(sd));
+  sd.nbr = L->nbr;
+  sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
+  sd.K64 = L->K64;
+  sd.KT = fp64 ? (const void *)L->K64 : (const void *)L->K32;
+  sd.xd64 = L->xd64;
+  sd.xdT = fp64 ? (const void *)L->xd64 : (const void *)L->xd32;
+  sd.b64 = L->b64;
+  sd.x64 = L->x64;
+  const int vk = fp64 ? 0 : 1;
+  sd.e = L->e[vk];
+  sd.z = L->z[vk];
+  sd.p0 = L->p0[vk];
+  sd.p1 = L->p1[vk];
+  sd.h = 0.5 * L->dt / (L->dx * L->dx);
+  sd.tol = o.tol;
+  sd.inner_rtol = fp64 ? 0.0 : o.inner_rtol;
+  sd.final_safety = fp64 ? 1.0 : 0.5;
+  sd.n_oct = (int32_t)L->n_oct;
+  sd.item_begin = item_begin;
+  sd.n_items = n_items;
+  sd.stop_rule = o.stop_rule;
+  sd.max_iter = o.max_iter;
+  sd.max_refine = o.max_refine;
+  sd.inner_max = fp64 ? o.max_iter : 4000;
+  return ATS_OK;
+}
+}  // namespace ats
 
 // ---------------------------------------------------------------------------
 // C ABI
