@@ -328,6 +328,10 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(solves, budget_s=args.cpu_seconds)
 
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = run_serve(args, ats, local)
+
     batch.close()
     for L in levels:
         L.close()
@@ -351,9 +355,86 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "fp64_per_solve": fp64,
+        "serve": serve,
         "solve_stats": {"iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
                         "refinements_mean": float(np.mean(refs)),
                         "max_rel_residual": float(np.max(bounds)), "layout_s": round(layout_s, 3)},
+    }
+
+
+def run_serve(args, ats, device):
+    """Served request stream: Poisson arrivals of level solves (sizes
+    log-uniform 16^3 .. serve_max_cells, Dirichlet / Neumann / Robin walls,
+    tol 1e-6 or 1e-10), arrival rate 0.8 x the plain per-solve FP64 GPU
+    capacity measured on the same requests; continuous-batching server in
+    mixed precision.  Reports p50 / p99 latency and throughput of the server,
+    and of the plain FP64 path serving the same arrivals one at a time
+    (measured service times, FIFO queue)."""
+    import threading
+
+    reqs = W.config5_requests(n_req=args.serve_requests, seed=1405, hi_cells=args.serve_max_cells)
+    built = [W.build_request(r) for r in reqs]
+    # plain per-solve FP64: service time of every request (build + solve)
+    svc = []
+    with ats.Context(device) as ctx:
+        for (lv, st), r in zip(built, reqs):
+            L = ats.Level(ctx, lv)
+            x = st.E.copy()
+            t0 = time.perf_counter()
+            L.build(st.dt, st.K, st.E, face_E=st.face_E, face_F=st.face_F)
+            code, _ = L.solve(x, tol=r["tol"], precision=ats.ATS_PREC_FP64)
+            svc.append(time.perf_counter() - t0)
+            L.close()
+            if code != 0:
+                raise RuntimeError("fp64 serve baseline failed")
+    svc = np.array(svc)
+    cap = len(svc) / svc.sum()
+    lam = 0.8 * cap
+    arrivals = np.array([r["t"] for r in reqs]) * (reqs[-1]["id"] + 1) / reqs[-1]["t"] / lam
+    # FIFO single server with the measured FP64 service times (Lindley recursion)
+    fin = np.zeros(len(svc))
+    free = 0.0
+    for i, (a, sv) in enumerate(zip(arrivals, svc)):
+        start = max(a, free)
+        free = start + sv
+        fin[i] = free
+    lat64 = (fin - arrivals) * 1e3
+    # the continuous-batching server on the same arrivals
+    srv = ats.Server(device, mem_budget_bytes=int(args.serve_budget_gb * (1 << 30)), precision=ats.ATS_PREC_MIXED,
+                     check_every=4)
+    tickets = [None] * len(reqs)
+    t_start = time.perf_counter()
+
+    def submitter():
+        for k, ((lv, st), r) in enumerate(zip(built, reqs)):
+            delay = arrivals[k] - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(lv, st, tol=r["tol"])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = []
+    errs = 0
+    for k, ((lv, st), r) in enumerate(zip(built, reqs)):
+        while tickets[k] is None:
+            time.sleep(0.0002)
+        code, x, res = srv.wait(tickets[k], lv.n_cell)
+        errs += code != 0
+        lat.append(res["latency_us"] / 1e3)
+    t_end = time.perf_counter()
+    th.join()
+    st_srv = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {
+        "requests": len(reqs), "max_cells": int(args.serve_max_cells), "arrival_rate_per_s": round(lam, 2),
+        "throughput": round(len(reqs) / (t_end - t_start), 2), "unit": UNIT,
+        "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+        "errors": int(errs), "peak_resident": st_srv["peak_resident"],
+        "fp64_per_solve": {"capacity": round(cap, 2), "p50_ms": round(float(np.percentile(lat64, 50)), 3),
+                           "p99_ms": round(float(np.percentile(lat64, 99)), 3),
+                           "note": "plain FP64 solves one at a time, FIFO on the same arrivals (measured service times)"},
     }
 
 
@@ -437,6 +518,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-max-cells", type=int, default=128 ** 3)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     rank, world, local = _dist()
     if world > 1 and args.impl == "ours":

@@ -199,6 +199,8 @@ struct Layout {
 };
 // Returns "" on success or an error message.
 std::string build_layout(const ats_level_desc &d, Layout &out);
+// ats_level_create with a layout already built on the host (runtime.cpp).
+ats_status level_create_with_layout(ats_context *ctx, const ats_level_desc *desc, const Layout &lay, ats_level **out);
 
 void set_error(const std::string &msg);
 

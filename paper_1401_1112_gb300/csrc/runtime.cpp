@@ -802,6 +802,14 @@ ats_status ats_level_create(ats_context *ctx, const ats_level_desc *desc, ats_le
     set_error(msg);
     return ATS_ERR_INVALID_ARG;
   }
+  return ats::level_create_with_layout(ctx, desc, lay, out);
+}
+
+}  // extern "C"
+
+ats_status ats::level_create_with_layout(ats_context *ctx, const ats_level_desc *desc, const Layout &lay,
+                                         ats_level **out) {
+  *out = nullptr;
   CUDA_TRY(cudaSetDevice(ctx->device));
   ats_level *L = new (std::nothrow) ats_level();
   if (!L) return ATS_ERR_OOM;
@@ -853,6 +861,8 @@ ats_status ats_level_create(ats_context *ctx, const ats_level_desc *desc, ats_le
   *out = L;
   return ATS_OK;
 }
+
+extern "C" {
 
 ats_status ats_level_destroy(ats_level *L) {
   if (!L) return ATS_ERR_INVALID_ARG;

@@ -50,6 +50,7 @@ struct Pending {
   int stop_rule = ATS_STOP_RESIDUAL;
   Clock::time_point submitted;
   size_t bytes = 0;  // device-memory estimate
+  Layout layout;     // built by the submitting thread, off the device loop
 };
 
 struct Slot {
@@ -195,7 +196,7 @@ ats_status admit_one_impl(ats_server *S, Pending &p, int slot, std::vector<int32
   d.face_kind = p.face_kind.data();
   d.face_rel = p.face_rel.data();
   d.face_alpha = p.face_alpha.empty() ? nullptr : p.face_alpha.data();
-  ats_status s = ats_level_create(S->ctx, &d, &sl.lvl);
+  ats_status s = level_create_with_layout(S->ctx, &d, p.layout, &sl.lvl);
   if (s != ATS_OK) return s;
   ats_coef_desc c;
   std::memset(&c, 0, sizeof(c));
@@ -542,6 +543,23 @@ ats_status ats_server_submit(ats_server *S, const ats_request *r, uint64_t *tick
   p->stop_rule = r->stop_rule;
   p->submitted = Clock::now();
   p->bytes = estimate_bytes(*p, S->fp64);
+  {
+    // the host part of level creation (neighbour table, interface records) runs
+    // in the submitting thread, so the scheduler only uploads
+    ats_level_desc dd = d;
+    dd.oct_xyz = p->oct_xyz.data();
+    dd.leaf_mask = p->has_leaf ? p->leaf.data() : nullptr;
+    dd.face_cell = p->face_cell.data();
+    dd.face_dir = p->face_dir.data();
+    dd.face_kind = p->face_kind.data();
+    dd.face_rel = p->face_rel.data();
+    dd.face_alpha = p->face_alpha.empty() ? nullptr : p->face_alpha.data();
+    std::string msg = build_layout(dd, p->layout);
+    if (!msg.empty()) {
+      set_error("ats_server_submit: " + msg);
+      return ATS_ERR_INVALID_ARG;
+    }
+  }
   std::lock_guard<std::mutex> lk(S->mu);
   if (!S->fatal.empty()) {
     set_error("server failed: " + S->fatal);
