@@ -50,6 +50,24 @@ def _dist():
     return rank, world, local
 
 
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own batch of independent solves (weak scaling):
+    the workload seed of rank r."""
+    return 1404 + 1000 * rank
+
+
+def reduce_max(value: float, device=None) -> float:
+    """Max over ranks of a per-rank time (no-op without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -119,25 +137,26 @@ class ClockSampler:
         }
 
 
-def _traffic_for(kernel: str):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, if the
-    summary was taken on the current kernel source (else None)."""
+def _traffic_for(kernel: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch of a kernel, from the committed ncu capture
+    (profiles/ncu_traffic.json) when it was taken on the current kernel
+    source: the captured launch's DRAM / algorithmic byte ratio applied to
+    this run's average launch.  None otherwise."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     try:
-        d = json.load(open(p))
         import hashlib
 
+        d = json.load(open(p))
         src = open(os.path.join(ROOT, "paper_1401_1112_gb300", "csrc", "kernels.cu"), "rb").read()
         if d.get("kernels_cu_sha256") != hashlib.sha256(src).hexdigest():
             return None
         k = d["kernels"].get(kernel)
         if not k:
             return None
-        # scale the captured launch's DRAM bytes to this run's average launch
-        return k
-    except Exception:
+        return round(k["dram_bytes"] / k["algorithmic_bytes"] * alg_bytes_per_launch)
+    except (OSError, ValueError, KeyError):
         return None
 
 
@@ -155,7 +174,7 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    solves = W.config4(n_solves=args.solves, seed=1404 + 1000 * rank)
+    solves = W.config4(n_solves=args.solves, seed=replica_seed(rank))
     n = len(solves)
     sizes = [lv.n_cell for lv, _ in solves]
     total_cells = int(sum(sizes))
@@ -228,7 +247,8 @@ def run_ours(args, rank, world, local):
     sampler.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    acc = {"op_ms": 0.0, "op_bytes": 0.0, "ref_ms": 0.0, "ref_bytes": 0.0, "upd_ms": 0.0, "upd_bytes": 0.0}
+    acc = {"op_ms": 0.0, "op_bytes": 0.0, "ref_ms": 0.0, "ref_bytes": 0.0, "upd_ms": 0.0, "upd_bytes": 0.0,
+           "ticks": 0}
     launches = 0
     ev0.record(stream)
     for _ in range(args.steps):
@@ -240,11 +260,7 @@ def run_ours(args, rank, world, local):
     ev1.record(stream)
     barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ev0.elapsed_time(ev1), dev)
     batch.set_profiling(False)
     value = n * args.steps * world / (ms / 1e3)
     iters = [s["iterations"] for s in stats]
@@ -261,7 +277,8 @@ def run_ours(args, rank, world, local):
     roofline = {
         "bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
         "frac": round(achieved / peak, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-        "traffic": _traffic_for(dom),
+        "traffic": _traffic_for(dom, dbytes / max(1, acc["ticks"])),
+        "launches": int(acc["ticks"]), "bytes_per_launch": round(dbytes / max(1, acc["ticks"])),
         "per_kernel": {k: {"ms": round(acc[a], 3),
                            "GBps": round(acc[b] / (acc[a] / 1e3) / 1e9, 1) if acc[a] else None}
                        for k, (a, b) in kern.items()},
@@ -298,11 +315,7 @@ def run_ours(args, rank, world, local):
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        e_s = time.perf_counter() - t1
-        if dist is not None:
-            t = torch.tensor([e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
+        e_s = reduce_max(time.perf_counter() - t1, dev)
         h2d = int(K_h.nbytes + E_h.nbytes + (fE_h.nbytes + fF_h.nbytes if foffs[-1] else 0) + E_h.nbytes)
         e2e = {"value": round(n * args.steps * world / e_s, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(E_h.nbytes)}

@@ -1,0 +1,52 @@
+"""Multi-GPU path of bench.py on CPU: level solves are independent, so N
+GPUs are N replicas with different seeds (weak scaling) and the only
+collective is the max over ranks of the timed region.  Checked here with two
+gloo ranks on 127.0.0.1 (no GPU)."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import workloads as W
+
+    seed = bench.replica_seed(rank)
+    solves = W.config4(n_solves=3, seed=seed)
+    m = bench.reduce_max(1.0 + rank, torch.device("cpu"))
+    out[rank] = (seed, int(solves[0][0].n_oct), m)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.timeout(120)
+def test_two_replicas_distinct_work_and_max_time():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+    seeds = {out[r][0] for r in range(world)}
+    assert len(seeds) == world                      # each rank has its own problems
+    assert all(out[r][2] == float(world) for r in range(world))   # max over ranks seen by all
+
+
+def test_reduce_max_without_process_group():
+    import bench
+
+    assert bench.reduce_max(3.5) == 3.5
