@@ -321,7 +321,8 @@ ats_status ats_server_stats(ats_server *server, ats_server_counters *out);
  * held by every GPU that loads the library until the process exits).
  *
  * Arguments (all arrays are DEVICE pointers, FP64, read in stream order on
- * `stream`, a cudaStream_t or NULL for the default stream):
+ * `stream`, a cudaStream_t or NULL for the default stream; K, xd, b and x
+ * start on a 32-byte boundary, as every cudaMalloc block does):
  *   n_oct     octs of the level, 1 <= 8 n_oct <= ATS_NOALLOC_MAX_CELLS;
  *   nbr       [6 n_oct] oct neighbour table (ats_layout_neighbors gives it);
  *   K         [8 n_oct] cell K on leaf cells, a negative value on cells that
@@ -332,7 +333,8 @@ ats_status ats_server_stats(ats_server *server, ats_server_counters *out);
  *   b         [8 n_oct] right-hand side;
  *   x         [8 n_oct] initial guess in, solution out;
  *   tol       ||r_j|| <= tol ||r_0||; max_iter: CG cap (<= 0: 20000).
- * Returns ATS_ERR_INVALID_ARG for sizes above ATS_NOALLOC_MAX_CELLS.  The
+ * Returns ATS_ERR_INVALID_ARG for sizes above ATS_NOALLOC_MAX_CELLS or a
+ * misaligned array.  The
  * first call on each device looks up the array's device address with that
  * device current: make it outside any stream capture.  Every call reuses the
  * same array (its contents are the last call's; what must start at zero is

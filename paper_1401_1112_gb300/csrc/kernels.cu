@@ -122,40 +122,46 @@ __device__ __forceinline__ void warp_reduce_acc(Acc<double> &a) {
 // oct-wise vector I/O (one thread owns the eight cells of one oct)
 // ---------------------------------------------------------------------------
 
+// 256-bit global accesses (sm_100 and later): the 32 bytes of an FP32 oct are
+// one request (one L1 sector access instead of two 16-byte halves), an FP64
+// oct is two.  Every oct base is 32-byte aligned: vectors are whole octs in
+// device allocations aligned to 256 bytes (user pointers are checked on the
+// host).  Read-only loads use the non-coherent path and may be scheduled
+// freely; loads of data this kernel also writes are volatile so that they
+// stay ordered with the stores.
 __device__ __forceinline__ void ld8_ro(const float *__restrict__ p, float (&v)[8]) {
-  const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-  const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void ld4_ro(const double *__restrict__ p, double &a, double &b, double &c, double &d) {
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(a), "=d"(b), "=d"(c), "=d"(d) : "l"(p));
 }
 __device__ __forceinline__ void ld8_ro(const double *__restrict__ p, double (&v)[8]) {
-  const double2 *q = reinterpret_cast<const double2 *>(p);
-  const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-  v[4] = c.x; v[5] = c.y; v[6] = d.x; v[7] = d.y;
+  ld4_ro(p, v[0], v[1], v[2], v[3]);
+  ld4_ro(p + 4, v[4], v[5], v[6], v[7]);
 }
 __device__ __forceinline__ void ld8_rw(const float *p, float (&v)[8]) {
-  const float4 a = reinterpret_cast<const float4 *>(p)[0];
-  const float4 b = reinterpret_cast<const float4 *>(p)[1];
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
 }
 __device__ __forceinline__ void ld8_rw(const double *p, double (&v)[8]) {
-  const double2 *q = reinterpret_cast<const double2 *>(p);
-  const double2 a = q[0], b = q[1], c = q[2], d = q[3];
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-  v[4] = c.x; v[5] = c.y; v[6] = d.x; v[7] = d.y;
+  asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
+  asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];"
+               : "=d"(v[4]), "=d"(v[5]), "=d"(v[6]), "=d"(v[7])
+               : "l"(p + 4));
 }
 __device__ __forceinline__ void st8(float *p, const float (&v)[8]) {
-  reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
-  reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
 }
 __device__ __forceinline__ void st8(double *p, const double (&v)[8]) {
-  double2 *q = reinterpret_cast<double2 *>(p);
-  q[0] = make_double2(v[0], v[1]);
-  q[1] = make_double2(v[2], v[3]);
-  q[2] = make_double2(v[4], v[5]);
-  q[3] = make_double2(v[6], v[7]);
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3])
+               : "memory");
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p + 4), "d"(v[4]), "d"(v[5]), "d"(v[6]), "d"(v[7])
+               : "memory");
 }
 
 // Load the four cells of a neighbour oct that face this oct: the cells whose
@@ -163,12 +169,8 @@ __device__ __forceinline__ void st8(double *p, const double (&v)[8]) {
 // for exactly those cells c.
 template <int A, int NB>
 __device__ __forceinline__ void ld_face(const float *__restrict__ p, float (&v)[8]) {
-  if (A == 0) {
-    ld8_ro(p, v);
-  } else if (A == 1) {
-    const float2 a = __ldg(reinterpret_cast<const float2 *>(p + 2 * NB));
-    const float2 b = __ldg(reinterpret_cast<const float2 *>(p + 4 + 2 * NB));
-    v[2 * NB] = a.x; v[2 * NB + 1] = a.y; v[4 + 2 * NB] = b.x; v[5 + 2 * NB] = b.y;
+  if (A != 2) {
+    ld8_ro(p, v);  // x and y faces: the whole oct in one 32-byte access
   } else {
     const float4 a = __ldg(reinterpret_cast<const float4 *>(p + 4 * NB));
     v[4 * NB] = a.x; v[4 * NB + 1] = a.y; v[4 * NB + 2] = a.z; v[4 * NB + 3] = a.w;
@@ -183,9 +185,7 @@ __device__ __forceinline__ void ld_face(const double *__restrict__ p, double (&v
     const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 4 + 2 * NB));
     v[2 * NB] = a.x; v[2 * NB + 1] = a.y; v[4 + 2 * NB] = b.x; v[5 + 2 * NB] = b.y;
   } else {
-    const double2 a = __ldg(reinterpret_cast<const double2 *>(p + 4 * NB));
-    const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 4 * NB + 2));
-    v[4 * NB] = a.x; v[4 * NB + 1] = a.y; v[4 * NB + 2] = b.x; v[4 * NB + 3] = b.y;
+    ld4_ro(p + 4 * NB, v[4 * NB], v[4 * NB + 1], v[4 * NB + 2], v[4 * NB + 3]);
   }
 }
 

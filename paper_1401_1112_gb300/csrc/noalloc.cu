@@ -88,6 +88,11 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
     set_error("ats_solve_noalloc: h and tol must be > 0, device in range");
     return ATS_ERR_INVALID_ARG;
   }
+  // the kernels move an oct's eight FP64 values as two 32-byte accesses
+  if (((uintptr_t)K | (uintptr_t)xd | (uintptr_t)b | (uintptr_t)x) & 31u) {
+    set_error("ats_solve_noalloc: K, xd, b and x must be 32-byte aligned device pointers");
+    return ATS_ERR_INVALID_ARG;
+  }
   if (max_iter <= 0) max_iter = 20000;
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) {

@@ -109,3 +109,17 @@ def test_no_device_is_reported_not_faked(built):
     with pytest.raises(built.AtsError) as e:
         built.ats_context_create(0, 0)
     assert e.value.code == built.ATS_ERR_NO_DEVICE
+
+
+def test_noalloc_rejects_misaligned_arrays(built):
+    """The allocation-free entry point checks the 32-byte alignment of its
+    FP64 arrays before any CUDA call (the kernels move an oct as two 32-byte
+    accesses)."""
+    import ctypes
+
+    st = built.ats_solve_stats()
+    V = ctypes.c_void_p
+    code = built.lib().ats_solve_noalloc(0, None, 8, V(0x1000), V(0x2008), None, 0.5, V(0x3000), V(0x4000),
+                                         1e-10, 0, ctypes.byref(st))
+    assert code == built.ATS_ERR_INVALID_ARG
+    assert "32-byte" in built.ats_last_error()
