@@ -267,11 +267,14 @@ def run_ours(args, rank, world, local):
     refs = [s["refinements"] for s in stats]
     bounds = [s["res_norm"] / s["r0_norm"] if s["r0_norm"] > 0 else 0.0 for s in stats]
 
-    # dominant kernel roofline (algorithmic bytes / event-timed duration)
+    # dominant kernel roofline (algorithmic bytes / event-timed duration).
+    # k_ref (the FP64 residual, bound by the FP64 ALU) runs on a second stream
+    # concurrently with k_op, so its event span includes time shared with k_op:
+    # the roofline kernel is the longer of the two HBM-bound CG kernels.
     peak, peak_kind = _peaks()
     kern = {"k_op<float>": ("op_ms", "op_bytes"), "k_ref<float>": ("ref_ms", "ref_bytes"),
             "k_upd<float>": ("upd_ms", "upd_bytes")}
-    dom = max(kern, key=lambda k: acc[kern[k][0]])
+    dom = max(("k_op<float>", "k_upd<float>"), key=lambda k: acc[kern[k][0]])
     dms, dbytes = acc[kern[dom][0]], acc[kern[dom][1]]
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
     roofline = {
@@ -280,7 +283,8 @@ def run_ours(args, rank, world, local):
         "traffic": _traffic_for(dom, dbytes / max(1, acc["ticks"])),
         "launches": int(acc["ticks"]), "bytes_per_launch": round(dbytes / max(1, acc["ticks"])),
         "per_kernel": {k: {"ms": round(acc[a], 3),
-                           "GBps": round(acc[b] / (acc[a] / 1e3) / 1e9, 1) if acc[a] else None}
+                           "GBps": round(acc[b] / (acc[a] / 1e3) / 1e9, 1) if acc[a] else None,
+                           "bound": "fp64 alu, concurrent with k_op" if k.startswith("k_ref") else "hbm"}
                        for k, (a, b) in kern.items()},
     }
 

@@ -138,12 +138,20 @@ struct TickArgs {
   unsigned long long *cells;  // [4] cells processed per kernel/phase, or null
 };
 
-// One tick = k_op (CG items, and x += e for refinement items) + k_ref
-// (refinement residual) + k_upd (all).  ev (null, or 4 events) is recorded
-// before k_op, between the kernels and after k_upd; `capture` says whether
-// the stream is being captured.
-cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cudaStream_t st, cudaEvent_t *ev,
-                        bool capture);
+// One tick = k_op (CG items) and k_ref (refinement residual of the solves in
+// their refinement phase), which touch disjoint solves, then k_upd (all items;
+// a solve that leaves its inner solve folds x += e there).  With fj->aux set,
+// k_ref is launched first on fj->aux, forked from st, then k_op on st, and
+// both join before k_upd, so the two overlap; otherwise all three run on st.  ev (null, or 6 events):
+// [0] / [1] around k_op, [2] / [3] around k_ref, [4] / [5] around k_upd;
+// `capture` says whether the stream is being captured.
+struct TickStreams {
+  cudaStream_t aux;
+  cudaEvent_t fork, join;  // created with cudaEventDisableTiming
+};
+constexpr int kTickEvents = 6;
+cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cudaStream_t st, const TickStreams *fj,
+                        cudaEvent_t *ev, bool capture);
 
 // Start of a solve: e = 0 on every cell of every item, and x64 = src[solve]
 // where src (device array of device pointers) is non-null for that solve.

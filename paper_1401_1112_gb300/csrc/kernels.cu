@@ -643,8 +643,9 @@ __device__ __forceinline__ int32_t *phase_list(int32_t *lists, int n_items, int 
   return lists + (size_t)(parity * 2 + phase) * n_items;
 }
 
-// CG items: p = z + beta p, q = (I + dt A) p, partial p.q.  Refinement items:
-// x += e, e = 0 (the finished inner solve's correction), before k_ref.
+// CG items: p = z + beta p, q = (I + dt A) p, partial p.q.  k_op and k_ref
+// touch disjoint solves (CG-phase and refinement-phase lists) and may run
+// concurrently.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a) {
   __shared__ Acc<T> red[kThreads / 32][3];
@@ -652,7 +653,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a
   __shared__ double bcast[kNumPartials];
   const int cur = __ldcg(&a.ctl->parity);
   const int n_in = __ldcg(&a.ctl->count[cur][kInner]);
-  const int n_rf = __ldcg(&a.ctl->count[cur][kRefine]);
   const int32_t *list = phase_list(a.lists, a.n_items, cur, kInner);
   const SolveScalars *S = a.sbuf + (size_t)cur * a.n_solves;
   const double *Pprev = a.p_upd + (size_t)(cur ^ 1) * a.n_items * kNumPartials;
@@ -693,14 +693,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a
     }
     store_item_partials<T>(a.p_op + (size_t)it * kNumPartials, pq, none, none, 0.f, red, redmx);
     if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 0, (unsigned long long)item.n_oct * 8);
-  }
-  const int32_t *rlist = phase_list(a.lists, a.n_items, cur, kRefine);
-  for (int li = blockIdx.x; li < n_rf; li += gridDim.x) {
-    const WorkItem item = a.items[__ldcg(rlist + li)];
-    const SolveDev &sd = a.solves[item.solve];
-    const int oct_end = item.oct_begin + item.n_oct;
-    for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads) upd_refine_oct<T>(sd, o);
-    if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 3, (unsigned long long)item.n_oct * 8);
   }
 }
 
@@ -817,6 +809,15 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs 
           upd_load_own(sd, o, p, w);
           upd_compute<T, kPaper>(sd, o, w, h, alpha, p, rz, rr, maxchg);
         }
+      }
+      // the inner solve ends here (converged, or an iteration cap sends the
+      // solve to a true-residual pass): x += e, e = 0 on this item, so the
+      // next tick's k_ref reads the corrected x
+      const bool to_ref =
+          conv || (!brk && (sc.iters + 1 >= sd.max_iter || sc.inner_iters + 1 >= sd.inner_max));
+      if (to_ref) {
+        for (int o = o0; o < oct_end; o += kThreads) upd_refine_oct<T>(sd, o);
+        if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 3, (unsigned long long)item.n_oct * 8);
       }
       store_item_partials<T>(Pcur + (size_t)it * kNumPartials, rz, rr, none, maxchg, red, redmx);
       if (a.cells && threadIdx.x == 0 && !conv && !brk) atomicAdd(a.cells + 2, (unsigned long long)item.n_oct * 8);
@@ -1203,24 +1204,36 @@ static cudaError_t record(cudaEvent_t ev, cudaStream_t st, bool capture) {
 }
 
 template <typename T, bool kPaper>
-static cudaError_t tick_impl(const TickArgs &a, int grid, cudaStream_t st, cudaEvent_t *ev, bool capture) {
+static cudaError_t tick_impl(const TickArgs &a, int grid, cudaStream_t st, const TickStreams *fj, cudaEvent_t *ev,
+                             bool capture) {
   cudaError_t err;
+  const bool fork = fj && fj->aux;
+  cudaStream_t sr = fork ? fj->aux : st;
+  if (fork && (err = cudaEventRecord(fj->fork, st)) != cudaSuccess) return err;
+  // k_ref first: its FP64-bound items start before k_op's CTAs take the SMs
+  if (fork && (err = cudaStreamWaitEvent(sr, fj->fork, 0)) != cudaSuccess) return err;
+  if ((err = record(ev ? ev[2] : nullptr, sr, capture)) != cudaSuccess) return err;
+  k_ref<T><<<grid, kThreads, 0, sr>>>(a);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if ((err = record(ev ? ev[3] : nullptr, sr, capture)) != cudaSuccess) return err;
   if ((err = record(ev ? ev[0] : nullptr, st, capture)) != cudaSuccess) return err;
   k_op<T><<<grid, kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if ((err = record(ev ? ev[1] : nullptr, st, capture)) != cudaSuccess) return err;
-  k_ref<T><<<grid, kThreads, 0, st>>>(a);
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  if ((err = record(ev ? ev[2] : nullptr, st, capture)) != cudaSuccess) return err;
+  if (fork) {
+    if ((err = cudaEventRecord(fj->join, sr)) != cudaSuccess) return err;
+    if ((err = cudaStreamWaitEvent(st, fj->join, 0)) != cudaSuccess) return err;
+  }
+  if ((err = record(ev ? ev[4] : nullptr, st, capture)) != cudaSuccess) return err;
   k_upd<T, kPaper><<<grid, kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  return record(ev ? ev[3] : nullptr, st, capture);
+  return record(ev ? ev[5] : nullptr, st, capture);
 }
 
-cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cudaStream_t st, cudaEvent_t *ev,
-                        bool capture) {
-  if (fp64) return paper ? tick_impl<double, true>(a, grid, st, ev, capture) : tick_impl<double, false>(a, grid, st, ev, capture);
-  return paper ? tick_impl<float, true>(a, grid, st, ev, capture) : tick_impl<float, false>(a, grid, st, ev, capture);
+cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cudaStream_t st, const TickStreams *fj,
+                        cudaEvent_t *ev, bool capture) {
+  if (fp64) return paper ? tick_impl<double, true>(a, grid, st, fj, ev, capture) : tick_impl<double, false>(a, grid, st, fj, ev, capture);
+  return paper ? tick_impl<float, true>(a, grid, st, fj, ev, capture) : tick_impl<float, false>(a, grid, st, fj, ev, capture);
 }
 
 // ---------------------------------------------------------------------------

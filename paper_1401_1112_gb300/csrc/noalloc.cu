@@ -217,7 +217,7 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
   int active = 1;
   while (active > 0 && ticks < max_ticks) {
     for (int t = 0; t < 8; ++t)
-      NA_TRY(launch_tick(true, false, ta, grid, st, nullptr, false));
+      NA_TRY(launch_tick(true, false, ta, grid, st, nullptr, nullptr, false));
     ticks += 8;
     NA_TRY(cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     NA_TRY(cudaStreamSynchronize(st));

@@ -171,8 +171,9 @@ struct Plan {
   int graph_ticks = 0;
   bool graph_profiled = false;
   bool profiling = false;
-  std::vector<cudaEvent_t> evs;  // 4 per tick of a chunk
+  std::vector<cudaEvent_t> evs;  // kTickEvents per tick of a chunk
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+  TickStreams fj{nullptr, nullptr, nullptr};  // k_ref's stream, fork / join events
   int slot = 0;
   double op_ms = 0.0, ref_ms = 0.0, upd_ms = 0.0, op_bytes = 0.0, ref_bytes = 0.0, upd_bytes = 0.0;
   int launches = 0;
@@ -246,6 +247,9 @@ void plan_free(Plan *P) {
   for (auto e : P->evs) cudaEventDestroy(e);
   for (auto e : P->poll_ev)
     if (e) cudaEventDestroy(e);
+  if (P->fj.fork) cudaEventDestroy(P->fj.fork);
+  if (P->fj.join) cudaEventDestroy(P->fj.join);
+  if (P->fj.aux) cudaStreamDestroy(P->fj.aux);
   dev_free(ctx, P->d_solves);
   dev_free(ctx, P->d_sc);
   dev_free(ctx, P->d_final);
@@ -407,13 +411,16 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   }
   CUDA_TRY(cudaEventCreateWithFlags(&P->poll_ev[0], cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&P->poll_ev[1], cudaEventDisableTiming));
+  CUDA_TRY(cudaStreamCreateWithFlags(&P->fj.aux, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&P->fj.fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&P->fj.join, cudaEventDisableTiming));
   CUDA_TRY(cudaStreamSynchronize(st));
   *out = P;
   return ATS_OK;
 }
 
 ats_status plan_ensure_events(Plan *P) {
-  const size_t need = 4 * (size_t)P->opts.check_every;
+  const size_t need = kTickEvents * (size_t)P->opts.check_every;
   while (P->evs.size() < need) {
     cudaEvent_t e;
     CUDA_TRY(cudaEventCreate(&e));
@@ -443,7 +450,7 @@ ats_status plan_enqueue_chunk(Plan *P) {
       TickArgs ta = P->targs;
       if (!prof) ta.cells = nullptr;
       for (int t = 0; t < k && err == cudaSuccess; ++t)
-        err = launch_tick(P->fp64, P->paper, ta, P->grid, st, prof ? &P->evs[4 * t] : nullptr, true);
+        err = launch_tick(P->fp64, P->paper, ta, P->grid, st, &P->fj, prof ? &P->evs[kTickEvents * t] : nullptr, true);
       cudaError_t err2 = cudaStreamEndCapture(st, &g);
       if (err != cudaSuccess || err2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -470,7 +477,7 @@ ats_status plan_enqueue_chunk(Plan *P) {
     TickArgs ta = P->targs;
     if (!prof) ta.cells = nullptr;
     for (int t = 0; t < k; ++t)
-      CUDA_TRY(launch_tick(P->fp64, P->paper, ta, P->grid, st, prof ? &P->evs[4 * t] : nullptr, false));
+      CUDA_TRY(launch_tick(P->fp64, P->paper, ta, P->grid, st, &P->fj, prof ? &P->evs[kTickEvents * t] : nullptr, false));
   }
   P->ticks += k;
   P->launches += 3 * k;
@@ -484,9 +491,10 @@ ats_status plan_collect_events(Plan *P) {
   const int k = P->opts.check_every;
   for (int t = 0; t < k; ++t) {
     float a = 0.f, b = 0.f, c = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&a, P->evs[4 * t], P->evs[4 * t + 1]));
-    CUDA_TRY(cudaEventElapsedTime(&b, P->evs[4 * t + 1], P->evs[4 * t + 2]));
-    CUDA_TRY(cudaEventElapsedTime(&c, P->evs[4 * t + 2], P->evs[4 * t + 3]));
+    cudaEvent_t *e = &P->evs[kTickEvents * t];
+    CUDA_TRY(cudaEventElapsedTime(&a, e[0], e[1]));
+    CUDA_TRY(cudaEventElapsedTime(&b, e[2], e[3]));
+    CUDA_TRY(cudaEventElapsedTime(&c, e[4], e[5]));
     P->op_ms += a;
     P->ref_ms += b;
     P->upd_ms += c;
@@ -497,14 +505,14 @@ ats_status plan_collect_events(Plan *P) {
 // Algorithmic bytes per cell of each kernel and phase: the compulsory traffic
 // of the vectors and coefficients (neighbour tables and records not counted).
 //   k_op, CG:        read z, p_old, K_T; write p_new                (4 words)
-//   k_op, x += e:    read/write x (FP64) and e                        (16 B + 2 words)
 //   k_ref:           read K64, x64, b64 (+ K_T when mixed); write z   (24 B + 1-2 words)
 //   k_upd, CG:       read p, K_T, z, e; write z, e                   (6 words)
+//   k_upd, x += e:   read/write x (FP64) and e (end of an inner solve) (16 B + 2 words)
 void plan_bytes(const Plan *P, const unsigned long long cells[4], double *op_b, double *ref_b, double *upd_b) {
   const double w = P->fp64 ? 8.0 : 4.0;
-  *op_b = 4 * w * cells[0] + (16 + 2 * w) * cells[3];
+  *op_b = 4 * w * cells[0];
   *ref_b = (24 + (P->fp64 ? 0 : w) + w) * cells[1];
-  *upd_b = 6 * w * cells[2];
+  *upd_b = 6 * w * cells[2] + (16 + 2 * w) * cells[3];
 }
 
 // Run a plan to completion.  x_inout[k] (host or device per opts.mem) or the

@@ -132,6 +132,7 @@ struct ats_server {
   SolveScalars *h_final = nullptr;  // pinned
   int *h_active = nullptr;          // pinned
   cudaStream_t st = nullptr;
+  TickStreams fj{nullptr, nullptr, nullptr};  // k_ref's stream, fork / join events
   // host state
   std::vector<Slot> slots;
   std::unique_ptr<ItemPool> pool;
@@ -291,7 +292,7 @@ ats_status capture_graph(ats_server *S) {
   S_TRY(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
   for (int t = 0; t < S->opts.check_every && err == cudaSuccess; ++t)
-    err = launch_tick(S->fp64, false, S->targs, S->grid, S->st, nullptr, true);
+    err = launch_tick(S->fp64, false, S->targs, S->grid, S->st, &S->fj, nullptr, true);
   cudaError_t err2 = cudaStreamEndCapture(S->st, &g);
   if (err != cudaSuccess || err2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -447,6 +448,13 @@ ats_status ats_server_create(int device, size_t mem_budget_bytes, const ats_serv
     ats_server_destroy(S);
     return code;
   };
+  if (cudaStreamCreateWithFlags(&S->fj.aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->fj.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->fj.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("server: stream or event creation failed");
+    return fail(ATS_ERR_CUDA);
+  }
   void *p;
   const size_t ms = S->max_slots, mi = S->max_items;
   if ((s = ctx_alloc(S->ctx, sizeof(SolveDev) * ms, &p)) != ATS_OK) return fail(s);
@@ -620,6 +628,9 @@ ats_status ats_server_destroy(ats_server *S) {
       if (sl.lvl) ats_level_destroy(sl.lvl);
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->h_final) cudaFreeHost(S->h_final);
+    if (S->fj.fork) cudaEventDestroy(S->fj.fork);
+    if (S->fj.join) cudaEventDestroy(S->fj.join);
+    if (S->fj.aux) cudaStreamDestroy(S->fj.aux);
     ats_context_destroy(S->ctx);  // frees every device buffer of the server
   }
   delete S;
