@@ -64,7 +64,7 @@ struct SolveScalars {
   int32_t status;
   int32_t final_pass;   // the next refinement pass ends the solve
   int32_t ticks;
-  int32_t pad;
+  float inner_t2;        // inner_target^2 in FP32 (the FP32 convergence test)
   double rz;            // r.z of the newest residual that is not yet a direction
   double r0;
   double inner_target;

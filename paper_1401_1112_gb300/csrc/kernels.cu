@@ -66,6 +66,7 @@ struct Acc<double> {
   __device__ __forceinline__ void add_value(double v) { s += v; }
   __device__ __forceinline__ void merge(const Acc<double> &o) { s += o.s; }
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ double val() const { return s; }
 };
 template <>
 struct Acc<float> {
@@ -95,6 +96,8 @@ struct Acc<float> {
     c = __fadd_rn(c, __fadd_rn(o.c, e));
   }
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+  // the sum rounded to FP32 (no FP64 instruction)
+  __device__ __forceinline__ float val() const { return __fadd_rn(s, c); }
 };
 
 // Warp reduction of a compensated FP32 accumulator: the (hi, lo) pairs are
@@ -464,47 +467,54 @@ __device__ __forceinline__ void store_item_partials(double *slots, Acc<T> a0, Ac
   __syncthreads();
 }
 
-// Totals of the first `ns` slots over the items [begin, begin + n) of a solve
-// (and the max of slot 3 when want_max), evaluated to FP64; every thread of
-// the CTA receives them.
+// Totals over the items [begin, begin + n) of a solve, in one pass over the
+// partials: sum 0 from slot k0 of P0, sums 1 and 2 from slots k1 and k2 of P1
+// (a null array or a negative slot leaves the sum at zero) and, with
+// want_max, the max of slot 3 of P1.  After one barrier every thread merges
+// the warps' results itself, in the same order, so every thread holds
+// bitwise the same totals.  red / redmx are not the buffers of
+// store_item_partials (a warp may store its item sums while another thread
+// still reads these).
 template <typename T>
-__device__ __forceinline__ void solve_totals(const double *P, int begin, int n, int ns, bool want_max,
-                                             double (&tot)[kNumPartials], Acc<T> (*red)[3], float *redmx,
-                                             double *bcast) {
+struct Totals {
+  Acc<T> s[3];
+  float mx;
+};
+template <typename T>
+__device__ __forceinline__ void gather_totals(const double *P0, int k0, const double *P1, int k1, int k2,
+                                              bool want_max, int begin, int n, Totals<T> &out, Acc<T> (*red)[3],
+                                              float *redmx) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Acc<T> a[3];
+  Acc<T> acc[3];
   float mx = 0.f;
   for (int it = begin + (int)threadIdx.x; it < begin + n; it += kThreads) {
-    const double *p = P + (size_t)it * kNumPartials;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      if (k < ns) Slot<T>::load_add(p + k, a[k]);
-    if (want_max) mx = fmaxf(mx, (float)__ldcg(p + 3));
+    const size_t base = (size_t)it * kNumPartials;
+    if (P0) Slot<T>::load_add(P0 + base + k0, acc[0]);
+    if (P1) {
+      if (k1 >= 0) Slot<T>::load_add(P1 + base + k1, acc[1]);
+      if (k2 >= 0) Slot<T>::load_add(P1 + base + k2, acc[2]);
+      if (want_max) mx = fmaxf(mx, (float)__ldcg(P1 + base + 3));
+    }
   }
 #pragma unroll
-  for (int k = 0; k < 3; ++k) warp_reduce_acc(a[k]);
+  for (int k = 0; k < 3; ++k) warp_reduce_acc(acc[k]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(kFull, mx, off));
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) red[warp][k] = a[k];
+    for (int k = 0; k < 3; ++k) red[warp][k] = acc[k];
     redmx[warp] = mx;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < kThreads / 32; ++w) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) red[0][k].merge(red[w][k]);
-      redmx[0] = fmaxf(redmx[0], redmx[w]);
-    }
+  for (int k = 0; k < 3; ++k) out.s[k] = red[0][k];
+  out.mx = redmx[0];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) bcast[k] = red[0][k].get();
-    bcast[3] = (double)redmx[0];
+  for (int w = 1; w < kThreads / 32; ++w) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out.s[k].merge(red[w][k]);
+    out.mx = fmaxf(out.mx, redmx[w]);
   }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < kNumPartials; ++k) tot[k] = bcast[k];
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -648,9 +658,8 @@ __device__ __forceinline__ int32_t *phase_list(int32_t *lists, int n_items, int 
 // concurrently.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a) {
-  __shared__ Acc<T> red[kThreads / 32][3];
-  __shared__ float redmx[kThreads / 32];
-  __shared__ double bcast[kNumPartials];
+  __shared__ Acc<T> red[kThreads / 32][3], red2[kThreads / 32][3];
+  __shared__ float redmx[kThreads / 32], redmx2[kThreads / 32];
   const int cur = __ldcg(&a.ctl->parity);
   const int n_in = __ldcg(&a.ctl->count[cur][kInner]);
   const int32_t *list = phase_list(a.lists, a.n_items, cur, kInner);
@@ -675,14 +684,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a
     OpOwn<T> w;
     if (o0 < oct_end) op_load_own(sd, o0, first, pold, w);
     // beta = (r_j . z_j) / (r_{j-1} . z_{j-1}) from the previous update's partials
+    // (every thread, in the bulk precision)
     T beta = T(0);
     if (!first) {
-      double tot[kNumPartials];
-      solve_totals<T>(Pprev, sd.item_begin, sd.n_items, 1, false, tot, red, redmx, bcast);
-      if (threadIdx.x == 0) bcast[0] = tot[0] / rz_prev;  // one FP64 divide per CTA
-      __syncthreads();
-      beta = (T)bcast[0];
-      __syncthreads();
+      Totals<T> tt;
+      gather_totals<T>(nullptr, 0, Pprev, 0, -1, false, sd.item_begin, sd.n_items, tt, red2, redmx2);
+      beta = tt.s[1].val() / (T)rz_prev;
     }
     const T h = (T)sd.h;
     Acc<T> pq, none;
@@ -749,9 +756,8 @@ __device__ __forceinline__ void commit_solve(const TickArgs &a, int cur, int s, 
 // solve's next state and list entries.
 template <typename T, bool kPaper>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs a) {
-  __shared__ Acc<T> red[kThreads / 32][3];
-  __shared__ float redmx[kThreads / 32];
-  __shared__ double bcast[kNumPartials];
+  __shared__ Acc<T> red[kThreads / 32][3], red2[kThreads / 32][3];
+  __shared__ float redmx[kThreads / 32], redmx2[kThreads / 32];
   __shared__ int s_base;
   const int cur = __ldcg(&a.ctl->parity);
   const int n_in = __ldcg(&a.ctl->count[cur][kInner]);
@@ -775,35 +781,25 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs 
       const int o0 = item.oct_begin + (int)threadIdx.x;
       UpdOwn<T> w;
       if (o0 < oct_end) upd_load_own(sd, o0, p, w);
-      double tq[kNumPartials];
-      solve_totals<T>(a.p_op, sd.item_begin, sd.n_items, 1, false, tq, red, redmx, bcast);
-      double rz_j = sc.rz, rr_j = 0.0, mx = 0.0;
-      if (!first) {
-        double tp[kNumPartials];
-        solve_totals<T>(Pprev, sd.item_begin, sd.n_items, 2, kPaper, tp, red, redmx, bcast);
-        rz_j = tp[0];
-        rr_j = tp[1];
-        mx = tp[3];
-      }
-      // the scalar decisions once per CTA (FP64 divide and square root are
-      // slow here), then broadcast
-      if (threadIdx.x == 0) {
-        const bool cv = !first && ((sqrt(rr_j) <= sc.inner_target && (!kPaper || mx < sd.tol)) || rz_j == 0.0);
-        const bool bk = !cv && (!(rz_j >= 0.0) || !isfinite(rz_j) || !(tq[0] > 0.0) || !isfinite(tq[0]));
-        bcast[0] = cv ? 1.0 : 0.0;
-        bcast[1] = bk ? 1.0 : 0.0;
-        bcast[2] = (cv || bk) ? 0.0 : rz_j / tq[0];
-      }
-      __syncthreads();
-      const bool conv = bcast[0] != 0.0;
-      const bool brk = bcast[1] != 0.0;
-      const double alpha64 = bcast[2];
-      __syncthreads();
+      // p.q of this tick and, after the first iteration, r.z and r.r of the
+      // previous update: one pass over the solve's partials
+      Totals<T> tt;
+      gather_totals<T>(a.p_op, 0, first ? nullptr : Pprev, 0, 1, kPaper && !first, sd.item_begin, sd.n_items, tt,
+                       red2, redmx2);
+      const T pq = tt.s[0].val();
+      const T rz_j = first ? (T)sc.rz : tt.s[1].val();
+      const T rr_j = first ? T(0) : tt.s[2].val();
+      const float mx = tt.mx;
+      // the scalar decisions, taken by every thread from the same totals in
+      // the bulk precision (sqrt(r.r) <= target as r.r <= target^2)
+      const T target2 = sizeof(T) == 4 ? (T)sc.inner_t2 : (T)(sc.inner_target * sc.inner_target);
+      const bool conv = !first && ((rr_j <= target2 && (!kPaper || mx < (float)sd.tol)) || rz_j == T(0));
+      const bool brk = !conv && (!(rz_j >= T(0)) || !isfinite(rz_j) || !(pq > T(0)) || !isfinite(pq));
+      const T alpha = (conv || brk) ? T(0) : rz_j / pq;
       Acc<T> rz, rr, none;
       float maxchg = 0.f;
       if (!conv && !brk) {
         const T h = (T)sd.h;
-        const T alpha = (T)alpha64;
         if (o0 < oct_end) upd_compute<T, kPaper>(sd, o0, w, h, alpha, p, rz, rr, maxchg);
         for (int o = o0 + kThreads; o < oct_end; o += kThreads) {
           upd_load_own(sd, o, p, w);
@@ -834,7 +830,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs 
           nx.inner_iters += 1;
           nx.first = 0;
           nx.pcur ^= 1;
-          nx.rz = rz_j;
+          nx.rz = first ? sc.rz : tt.s[1].get();
           nx.maxchg = mx;
           if (nx.iters >= sd.max_iter) {
             nx.status = ATS_ERR_NOT_CONVERGED;
@@ -847,9 +843,11 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs 
         commit_solve(a, cur, s, sd, nx, &s_base);
       }
     } else {
-      double t[kNumPartials];
-      solve_totals<T>(a.p_op, sd.item_begin, sd.n_items, 3, false, t, red, redmx, bcast);
+      // only the owner CTA decides after a true-residual pass
       if (owner) {
+        Totals<T> tt;
+        gather_totals<T>(a.p_op, 0, a.p_op, 1, 2, false, sd.item_begin, sd.n_items, tt, red2, redmx2);
+        const double t[3] = {tt.s[0].get(), tt.s[1].get(), tt.s[2].get()};
         SolveScalars nx = sc;
         nx.ticks += 1;
         const double rnorm = sqrt(t[0]);
@@ -879,6 +877,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs 
           nx.first = 1;
           nx.inner_iters = 0;
           nx.inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
+          nx.inner_t2 = (float)(nx.inner_target * nx.inner_target);
         }
         commit_solve(a, cur, s, sd, nx, &s_base);
       }
