@@ -437,6 +437,9 @@ struct Slot<double> {
 
 // Block sums of three accumulators (and a max) of this CTA's item, reduced
 // across warps in the accumulator precision; thread 0 writes the slots.
+// There is no barrier after thread 0's merge: callers alternate between two
+// red / redmx buffers by item, so a buffer is written again only after the
+// next item's barrier, which thread 0 reaches after its merge.
 template <typename T>
 __device__ __forceinline__ void store_item_partials(double *slots, Acc<T> a0, Acc<T> a1, Acc<T> a2, float mx,
                                                     Acc<T> (*red)[3], float *redmx) {
@@ -464,7 +467,6 @@ __device__ __forceinline__ void store_item_partials(double *slots, Acc<T> a0, Ac
     Slot<T>::store(slots + 2, red[0][2]);
     slots[3] = (double)redmx[0];
   }
-  __syncthreads();
 }
 
 // Totals over the items [begin, begin + n) of a solve, in one pass over the
@@ -653,13 +655,60 @@ __device__ __forceinline__ int32_t *phase_list(int32_t *lists, int n_items, int 
   return lists + (size_t)(parity * 2 + phase) * n_items;
 }
 
+// Descriptors of a batch of this CTA's work items, staged in shared memory:
+// list positions li0, li0 + G, ... (G = gridDim.x; positions below n0 are in
+// list0, the others in list1 at li - n0), each with its item, its solve's
+// descriptor and scalars.  The three dependent global reads (list entry,
+// item, solve) are paid once per batch instead of once per item.
+constexpr int kBatch = 32;
+struct ItemSlot {
+  SolveDev sd;
+  SolveScalars sc;
+  WorkItem item;
+  int32_t it;
+  int32_t inner;  // from list0
+  int32_t pad[2];
+};
+static_assert(sizeof(SolveDev) % 8 == 0 && sizeof(SolveScalars) % 8 == 0, "descriptors are copied as 8-byte words");
+
+__device__ __forceinline__ int stage_items(const TickArgs &a, const int32_t *list0, int n0, const int32_t *list1,
+                                           int n, int li0, const SolveScalars *S, ItemSlot *slots) {
+  const int G = (int)gridDim.x;
+  const int left = (n - li0 + G - 1) / G;
+  const int m = left < kBatch ? left : kBatch;
+  if ((int)threadIdx.x < m) {
+    const int li = li0 + (int)threadIdx.x * G;
+    const bool in0 = li < n0;
+    const int it = in0 ? __ldcg(list0 + li) : __ldcg(list1 + (li - n0));
+    slots[threadIdx.x].it = it;
+    slots[threadIdx.x].inner = in0 ? 1 : 0;
+    slots[threadIdx.x].item = a.items[it];
+  }
+  __syncthreads();
+  constexpr int wd = (int)(sizeof(SolveDev) / 8), ws = (int)(sizeof(SolveScalars) / 8);
+  for (int w = threadIdx.x; w < m * (wd + ws); w += kThreads) {
+    const int k = w / (wd + ws), j = w - k * (wd + ws);
+    const int sv = slots[k].item.solve;
+    if (j < wd) {
+      reinterpret_cast<unsigned long long *>(&slots[k].sd)[j] =
+          reinterpret_cast<const unsigned long long *>(a.solves + sv)[j];
+    } else {
+      reinterpret_cast<unsigned long long *>(&slots[k].sc)[j - wd] =
+          __ldcg(reinterpret_cast<const unsigned long long *>(S + sv) + (j - wd));
+    }
+  }
+  __syncthreads();
+  return m;
+}
+
 // CG items: p = z + beta p, q = (I + dt A) p, partial p.q.  k_op and k_ref
 // touch disjoint solves (CG-phase and refinement-phase lists) and may run
 // concurrently.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a) {
-  __shared__ Acc<T> red[kThreads / 32][3], red2[kThreads / 32][3];
-  __shared__ float redmx[kThreads / 32], redmx2[kThreads / 32];
+  __shared__ Acc<T> red[2][kThreads / 32][3], red2[kThreads / 32][3];
+  __shared__ float redmx[2][kThreads / 32], redmx2[kThreads / 32];
+  int buf = 0;
   const int cur = __ldcg(&a.ctl->parity);
   const int n_in = __ldcg(&a.ctl->count[cur][kInner]);
   const int32_t *list = phase_list(a.lists, a.n_items, cur, kInner);
@@ -669,11 +718,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a
     a.ctl->count[cur ^ 1][0] = 0;
     a.ctl->count[cur ^ 1][1] = 0;
   }
-  for (int li = blockIdx.x; li < n_in; li += gridDim.x) {
-    const int it = __ldcg(list + li);
-    const WorkItem item = a.items[it];
-    const SolveDev &sd = a.solves[item.solve];
-    const SolveScalars &sc = S[item.solve];
+  __shared__ ItemSlot slots[kBatch];
+  for (int li0 = blockIdx.x; li0 < n_in; li0 += kBatch * gridDim.x) {
+  const int m = stage_items(a, list, n_in, nullptr, n_in, li0, S, slots);
+  for (int bi = 0; bi < m; ++bi) {
+    const int it = slots[bi].it;
+    const WorkItem item = slots[bi].item;
+    const SolveDev &sd = slots[bi].sd;
+    const SolveScalars &sc = slots[bi].sc;
     const bool first = sc.first != 0;
     const int pcur = sc.pcur;
     const double rz_prev = sc.rz;
@@ -698,30 +750,41 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a
       op_load_own(sd, o, first, pold, w);
       op_compute(sd, o, w, h, beta, first, pold, pnew, pq);
     }
-    store_item_partials<T>(a.p_op + (size_t)it * kNumPartials, pq, none, none, 0.f, red, redmx);
+    store_item_partials<T>(a.p_op + (size_t)it * kNumPartials, pq, none, none, 0.f, red[buf], redmx[buf]);
+    buf ^= 1;
     if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 0, (unsigned long long)item.n_oct * 8);
+  }
+  __syncthreads();  // the slots are restaged
   }
 }
 
 // Refinement items: FP64 true residual, z = D^-1 r, partials r.r, x.x, r.z.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) k_ref(TickArgs a) {
-  __shared__ Acc<T> red[kThreads / 32][3];
-  __shared__ float redmx[kThreads / 32];
+  __shared__ Acc<T> red[2][kThreads / 32][3];
+  __shared__ float redmx[2][kThreads / 32];
+  int buf = 0;
   const int cur = __ldcg(&a.ctl->parity);
   const int n_rf = __ldcg(&a.ctl->count[cur][kRefine]);
   const int32_t *list = phase_list(a.lists, a.n_items, cur, kRefine);
-  for (int li = blockIdx.x; li < n_rf; li += gridDim.x) {
-    const int it = __ldcg(list + li);
-    const WorkItem item = a.items[it];
-    const SolveDev &sd = a.solves[item.solve];
+  const SolveScalars *S = a.sbuf + (size_t)cur * a.n_solves;
+  __shared__ ItemSlot slots[kBatch];
+  for (int li0 = blockIdx.x; li0 < n_rf; li0 += kBatch * gridDim.x) {
+  const int m = stage_items(a, list, n_rf, nullptr, n_rf, li0, S, slots);
+  for (int bi = 0; bi < m; ++bi) {
+    const int it = slots[bi].it;
+    const WorkItem item = slots[bi].item;
+    const SolveDev &sd = slots[bi].sd;
     const int oct_end = item.oct_begin + item.n_oct;
     Acc<T> rr, xx, rz;
     const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
     for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
       op_refine_oct<T>(sd, o, want_x, rr, xx, rz);
-    store_item_partials<T>(a.p_op + (size_t)it * kNumPartials, rr, xx, rz, 0.f, red, redmx);
+    store_item_partials<T>(a.p_op + (size_t)it * kNumPartials, rr, xx, rz, 0.f, red[buf], redmx[buf]);
+    buf ^= 1;
     if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 1, (unsigned long long)item.n_oct * 8);
+  }
+  __syncthreads();  // the slots are restaged
   }
 }
 
@@ -756,23 +819,27 @@ __device__ __forceinline__ void commit_solve(const TickArgs &a, int cur, int s, 
 // solve's next state and list entries.
 template <typename T, bool kPaper>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs a) {
-  __shared__ Acc<T> red[kThreads / 32][3], red2[kThreads / 32][3];
-  __shared__ float redmx[kThreads / 32], redmx2[kThreads / 32];
+  __shared__ Acc<T> red[2][kThreads / 32][3], red2[kThreads / 32][3];
+  __shared__ float redmx[2][kThreads / 32], redmx2[kThreads / 32];
   __shared__ int s_base;
+  int buf = 0;
   const int cur = __ldcg(&a.ctl->parity);
   const int n_in = __ldcg(&a.ctl->count[cur][kInner]);
   const int n_list = n_in + __ldcg(&a.ctl->count[cur][kRefine]);
   const SolveScalars *S = a.sbuf + (size_t)cur * a.n_solves;
   const double *Pprev = a.p_upd + (size_t)(cur ^ 1) * a.n_items * kNumPartials;
   double *Pcur = a.p_upd + (size_t)cur * a.n_items * kNumPartials;
-  for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
-    const bool inner = li < n_in;
-    const int it = inner ? __ldcg(phase_list(a.lists, a.n_items, cur, kInner) + li)
-                         : __ldcg(phase_list(a.lists, a.n_items, cur, kRefine) + (li - n_in));
-    const WorkItem item = a.items[it];
+  __shared__ ItemSlot slots[kBatch];
+  for (int li0 = blockIdx.x; li0 < n_list; li0 += kBatch * gridDim.x) {
+  const int m = stage_items(a, phase_list(a.lists, a.n_items, cur, kInner), n_in,
+                            phase_list(a.lists, a.n_items, cur, kRefine), n_list, li0, S, slots);
+  for (int bi = 0; bi < m; ++bi) {
+    const bool inner = slots[bi].inner != 0;
+    const int it = slots[bi].it;
+    const WorkItem item = slots[bi].item;
     const int s = item.solve;
-    const SolveDev &sd = a.solves[s];
-    const SolveScalars sc = S[s];
+    const SolveDev &sd = slots[bi].sd;
+    const SolveScalars &sc = slots[bi].sc;
     const bool owner = (it == sd.item_begin);
     if (inner) {
       const bool first = sc.first != 0;
@@ -815,7 +882,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs 
         for (int o = o0; o < oct_end; o += kThreads) upd_refine_oct<T>(sd, o);
         if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 3, (unsigned long long)item.n_oct * 8);
       }
-      store_item_partials<T>(Pcur + (size_t)it * kNumPartials, rz, rr, none, maxchg, red, redmx);
+      store_item_partials<T>(Pcur + (size_t)it * kNumPartials, rz, rr, none, maxchg, red[buf], redmx[buf]);
+      buf ^= 1;
       if (a.cells && threadIdx.x == 0 && !conv && !brk) atomicAdd(a.cells + 2, (unsigned long long)item.n_oct * 8);
       if (owner) {
         SolveScalars nx = sc;
@@ -882,6 +950,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs 
         commit_solve(a, cur, s, sd, nx, &s_base);
       }
     }
+  }
+  __syncthreads();  // the slots are restaged
   }
   // the last CTA of the grid flips the list parity for the next tick
   __syncthreads();
