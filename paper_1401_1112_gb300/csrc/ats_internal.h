@@ -36,6 +36,8 @@ struct SolveDev {
   void *z;              // [N]  preconditioned residual (bulk precision)
   void *p0;             // [N]  search direction, ping
   void *p1;             // [N]  search direction, pong
+  void *q;              // [N]  (I + dt A) p of the current direction (k_op)
+  void *dg;             // [N]  diagonal D = 1 + xd + sum C (k_ref; 1 off the leaves)
   double h;             // dt / dx^2 / 2, so an interior C = h (K_i + K_j)
   double tol;
   double inner_rtol;

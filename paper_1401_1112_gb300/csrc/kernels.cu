@@ -245,26 +245,6 @@ __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T
   }
 }
 
-// k_upd, CG phase, out-of-oct face DIR: neighbour p and K.
-template <int DIR, typename T>
-__device__ __forceinline__ void upd_face(int n, const T *__restrict__ KT, const T *__restrict__ p, T h,
-                                         const T (&K)[8], T (&dsum)[8], T (&off)[8]) {
-  constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
-  if (n < 0) return;
-  T Kn[8], Pn[8];
-  ld_face<A, NB>(KT + 8 * n, Kn);
-  ld_face<A, NB>(p + 8 * n, Pn);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    if (((c >> A) & 1) != S) continue;
-    const int j = c ^ (1 << A);
-    const T C = (Kn[j] >= T(0)) ? h * (K[c] + Kn[j]) : T(0);
-    dsum[c] += C;
-    off[c] += C * Pn[j];
-  }
-}
-
-
 // k_ref, out-of-oct face DIR: FP64 flux sums (K_i + K_j)(x_i - x_j) and the
 // bulk-precision diagonal for the preconditioner.
 template <int DIR, typename T>
@@ -287,7 +267,7 @@ __device__ __forceinline__ void ref_face(int n, const SolveDev &sd, const T *__r
       const double Ks = K[c] + Kn[j];
       acc[c] = fma(Ks, xv[c] - Xn[j], acc[c]);
       if (mixed) dsT[c] += hT * (KTo[c] + KTn[j]);
-      else dsT[c] += (T)Ks;
+      else dsT[c] += (T)(sd.h * Ks);
     }
   }
 }
@@ -332,7 +312,7 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
         const double df = xv[c] - xv[d];
         acc[c] = fma(Ks, df, acc[c]);
         acc[d] = fma(-Ks, df, acc[d]);
-        const T Ct = mixed ? hT * (KTo[c] + KTo[d]) : (T)Ks;
+        const T Ct = mixed ? hT * (KTo[c] + KTo[d]) : (T)(h * Ks);
         dsT[c] += Ct;
         dsT[d] += Ct;
       }
@@ -350,23 +330,19 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
     ld8_ro(sd.xd64 + 8 * rec, xd);
     if (mixed) ld8_ro((const T *)sd.xdT + 8 * rec, xdT);
   }
-  T zo[8];
+  T zo[8], dv[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const bool leaf = K[c] >= 0.0;
     const double base = rec >= 0 ? fma(-(1.0 + xd[c]), xv[c], b[c]) : b[c] - xv[c];
     const double r = fma(-h, acc[c], base);
     const T rT = (T)r;
-    T zc;
-    if (mixed) {
-      const T dT = T(1) + (rec >= 0 ? xdT[c] : T(0)) + dsT[c];
-      zc = rT / dT;
-    } else {
-      // FP64 bulk: dsT holds the plain K sums; D = 1 + xd + h sum
-      const double d = 1.0 + (rec >= 0 ? xd[c] : 0.0) + h * (double)dsT[c];
-      zc = (T)(r / d);
-    }
+    // D in the bulk precision, formed as the CG kernels form it; kept for
+    // the update kernel of the following inner solve
+    const T dT = T(1) + (rec >= 0 ? (mixed ? xdT[c] : (T)xd[c]) : T(0)) + dsT[c];
+    const T zc = rT / dT;
     zo[c] = leaf ? zc : T(0);
+    dv[c] = leaf ? dT : T(1);
     if (leaf) {
       rr.add(rT, rT);
       rz.add(rT, zc);
@@ -377,6 +353,7 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
     }
   }
   st8(z + 8 * o, zo);
+  st8((T *)sd.dg + 8 * o, dv);
 }
 
 // k_upd, refinement phase: x += e, e = 0.
@@ -568,75 +545,56 @@ __device__ __forceinline__ void op_compute(const SolveDev &sd, int o, const OpOw
 #pragma unroll
     for (int c = 0; c < 8; ++c) xd[c] = T(0);
   }
-  T local = T(0);
+  T local = T(0), qv[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const T d = T(1) + xd[c] + dsum[c];
     const T q = d * pv[c] - off[c];
-    if (w.K[c] >= T(0)) local = fma(pv[c], q, local);
+    const bool leaf = w.K[c] >= T(0);
+    if (leaf) local = fma(pv[c], q, local);
+    qv[c] = leaf ? q : T(0);
   }
   pq.add_value(local);
   st8(pnew + 8 * o, pv);  // non-leaf cells carry z = p = 0
+  st8((T *)sd.q + 8 * o, qv);
 }
 
+// k_upd, CG phase: nothing but the oct's own values.  q = (I + dt A) p was
+// stored by k_op and D by the refinement pass, so no neighbour is read.
 template <typename T>
 struct UpdOwn {
-  int nb[6];
-  int rec;
-  T K[8], p[8], z[8], e[8];
+  T p[8], q[8], d[8], z[8], e[8];
 };
 
 template <typename T>
 __device__ __forceinline__ void upd_load_own(const SolveDev &sd, int o, const T *__restrict__ p, UpdOwn<T> &w) {
-  load_nbr6(sd.nbr, o, w.nb);
-  w.rec = __ldg(sd.xrec + o);
-  ld8_ro((const T *)sd.KT + 8 * o, w.K);
+  // p, q (this tick's k_op) and D (a refinement pass) are read-only here
   ld8_ro(p + 8 * o, w.p);
+  ld8_ro((const T *)sd.q + 8 * o, w.q);
+  ld8_ro((const T *)sd.dg + 8 * o, w.d);
   ld8_rw((const T *)sd.z + 8 * o, w.z);
   ld8_rw((const T *)sd.e + 8 * o, w.e);
 }
 
-// k_upd, CG phase: q = (I + dt A) p, r = D z - alpha q, z = r / D, e += alpha p,
-// partials r.z, r.r (and the max relative change for the paper rule).
+// r = D z - alpha q, z = r / D, e += alpha p; partials r.z, r.r (and the max
+// relative change for the paper rule).  Off the leaves p = q = z = 0 and
+// D = 1, so those cells stay zero.
 template <typename T, bool kPaper>
-__device__ __forceinline__ void upd_compute(const SolveDev &sd, int o, UpdOwn<T> &w, T h, T alpha,
-                                            const T *__restrict__ p, Acc<T> &rz, Acc<T> &rr, float &maxchg) {
-  const T *__restrict__ KT = (const T *)sd.KT;
-  T dsum[8], off[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) dsum[c] = off[c] = T(0);
-  in_oct_faces(w.K, w.p, h, dsum, off);
-  upd_face<0>(w.nb[0], KT, p, h, w.K, dsum, off);
-  upd_face<1>(w.nb[1], KT, p, h, w.K, dsum, off);
-  upd_face<2>(w.nb[2], KT, p, h, w.K, dsum, off);
-  upd_face<3>(w.nb[3], KT, p, h, w.K, dsum, off);
-  upd_face<4>(w.nb[4], KT, p, h, w.K, dsum, off);
-  upd_face<5>(w.nb[5], KT, p, h, w.K, dsum, off);
-  T xd[8];
-  if (w.rec >= 0) {
-    ld8_ro((const T *)sd.xdT + 8 * w.rec, xd);
-  } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) xd[c] = T(0);
-  }
+__device__ __forceinline__ void upd_compute(const SolveDev &sd, int o, UpdOwn<T> &w, T alpha, Acc<T> &rz,
+                                            Acc<T> &rr, float &maxchg) {
   double xo[8];
   if (kPaper) ld8_rw(sd.x64 + 8 * o, xo);
   T lrz = T(0), lrr = T(0);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const bool leaf = w.K[c] >= T(0);
-    const T d = T(1) + xd[c] + dsum[c];
-    const T q = d * w.p[c] - off[c];
-    const T r = d * w.z[c] - alpha * q;
-    const T zn = r / d;
+    const T r = w.d[c] * w.z[c] - alpha * w.q[c];
+    const T zn = r / w.d[c];
     const T step = alpha * w.p[c];
-    if (leaf) {
-      lrz = fma(r, zn, lrz);
-      lrr = fma(r, r, lrr);
-      if (kPaper) maxchg = fmaxf(maxchg, (float)(fabs((double)step) / fabs(xo[c] + (double)w.e[c])));
-    }
-    w.z[c] = leaf ? zn : T(0);
-    w.e[c] = leaf ? w.e[c] + step : T(0);
+    lrz = fma(r, zn, lrz);
+    lrr = fma(r, r, lrr);
+    if (kPaper && step != T(0)) maxchg = fmaxf(maxchg, (float)(fabs((double)step) / fabs(xo[c] + (double)w.e[c])));
+    w.z[c] = zn;
+    w.e[c] += step;
   }
   rz.add_value(lrz);
   rr.add_value(lrr);
@@ -866,11 +824,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs 
       Acc<T> rz, rr, none;
       float maxchg = 0.f;
       if (!conv && !brk) {
-        const T h = (T)sd.h;
-        if (o0 < oct_end) upd_compute<T, kPaper>(sd, o0, w, h, alpha, p, rz, rr, maxchg);
+        if (o0 < oct_end) upd_compute<T, kPaper>(sd, o0, w, alpha, rz, rr, maxchg);
         for (int o = o0 + kThreads; o < oct_end; o += kThreads) {
           upd_load_own(sd, o, p, w);
-          upd_compute<T, kPaper>(sd, o, w, h, alpha, p, rz, rr, maxchg);
+          upd_compute<T, kPaper>(sd, o, w, alpha, rz, rr, maxchg);
         }
       }
       // the inner solve ends here (converged, or an iteration cap sends the

@@ -50,11 +50,11 @@ constexpr size_t kOffPart = align256(kOffLists + sizeof(int32_t) * 4 * kNoAllocM
 constexpr size_t kOffXrec = align256(kOffPart + 3 * sizeof(double) * kNumPartials * kNoAllocMaxItems);
 constexpr size_t kOffVec = align256(kOffXrec + sizeof(int32_t) * (kNoAllocMaxCells / 8));
 constexpr size_t kVecBytes = align256(sizeof(double) * kNoAllocMaxCells);
-constexpr size_t kScratchBytes = kOffVec + 4 * kVecBytes;  // e, z, p0, p1
+constexpr size_t kScratchBytes = kOffVec + 6 * kVecBytes;  // e, z, p0, p1, q, D
 
 }  // namespace
 
-// The scratch array (about 8.5 MB for the default maximum of 2^18 cells).
+// The scratch array (about 12.7 MB for the default maximum of 2^18 cells).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
@@ -152,6 +152,8 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
   sd.z = vec + vstride;
   sd.p0 = vec + 2 * vstride;
   sd.p1 = vec + 3 * vstride;
+  sd.q = vec + 4 * vstride;
+  sd.dg = vec + 5 * vstride;
   sd.h = h;
   sd.tol = tol;
   sd.inner_rtol = 0.0;

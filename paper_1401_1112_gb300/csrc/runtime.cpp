@@ -64,6 +64,7 @@ struct ats_level {
   double *x64 = nullptr;
   void *e[2] = {nullptr, nullptr}, *z[2] = {nullptr, nullptr};
   void *p0[2] = {nullptr, nullptr}, *p1[2] = {nullptr, nullptr};
+  void *q[2] = {nullptr, nullptr}, *dg[2] = {nullptr, nullptr};
   double *rhs_save = nullptr;  // b when a solve overrides it
   Plan *solo = nullptr;        // cached single-solve plan
 };
@@ -237,6 +238,8 @@ ats_status ensure_vectors(ats_level *L, bool fp64) {
   if (!L->z[k] && (s = dev_alloc(ctx, es * L->N, &L->z[k])) != ATS_OK) return s;
   if (!L->p0[k] && (s = dev_alloc(ctx, es * L->N, &L->p0[k])) != ATS_OK) return s;
   if (!L->p1[k] && (s = dev_alloc(ctx, es * L->N, &L->p1[k])) != ATS_OK) return s;
+  if (!L->q[k] && (s = dev_alloc(ctx, es * L->N, &L->q[k])) != ATS_OK) return s;
+  if (!L->dg[k] && (s = dev_alloc(ctx, es * L->N, &L->dg[k])) != ATS_OK) return s;
   return ATS_OK;
 }
 
@@ -328,6 +331,8 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     sd.z = L->z[vk];
     sd.p0 = L->p0[vk];
     sd.p1 = L->p1[vk];
+    sd.q = L->q[vk];
+    sd.dg = L->dg[vk];
     sd.h = 0.5 * L->dt / (L->dx * L->dx);
     sd.tol = o.tol;
     sd.inner_rtol = P->fp64 ? 0.0 : o.inner_rtol;
@@ -504,15 +509,15 @@ ats_status plan_collect_events(Plan *P) {
 
 // Algorithmic bytes per cell of each kernel and phase: the compulsory traffic
 // of the vectors and coefficients (neighbour tables and records not counted).
-//   k_op, CG:        read z, p_old, K_T; write p_new                (4 words)
-//   k_ref:           read K64, x64, b64 (+ K_T when mixed); write z   (24 B + 1-2 words)
-//   k_upd, CG:       read p, K_T, z, e; write z, e                   (6 words)
+//   k_op, CG:        read z, p_old, K_T; write p_new, q               (5 words)
+//   k_ref:           read K64, x64, b64 (+ K_T when mixed); write z, D (24 B + 2-3 words)
+//   k_upd, CG:       read p, q, D, z, e; write z, e                   (7 words)
 //   k_upd, x += e:   read/write x (FP64) and e (end of an inner solve) (16 B + 2 words)
 void plan_bytes(const Plan *P, const unsigned long long cells[4], double *op_b, double *ref_b, double *upd_b) {
   const double w = P->fp64 ? 8.0 : 4.0;
-  *op_b = 4 * w * cells[0];
-  *ref_b = (24 + (P->fp64 ? 0 : w) + w) * cells[1];
-  *upd_b = 6 * w * cells[2] + (16 + 2 * w) * cells[3];
+  *op_b = 5 * w * cells[0];
+  *ref_b = (24 + (P->fp64 ? 0 : w) + 2 * w) * cells[1];
+  *upd_b = 7 * w * cells[2] + (16 + 2 * w) * cells[3];
 }
 
 // Run a plan to completion.  x_inout[k] (host or device per opts.mem) or the
@@ -684,6 +689,8 @@ ats_status solve_dev_for(ats_level *L, const ats_solve_opts &o, bool fp64, int i
   sd.z = L->z[vk];
   sd.p0 = L->p0[vk];
   sd.p1 = L->p1[vk];
+  sd.q = L->q[vk];
+  sd.dg = L->dg[vk];
   sd.h = 0.5 * L->dt / (L->dx * L->dx);
   sd.tol = o.tol;
   sd.inner_rtol = fp64 ? 0.0 : o.inner_rtol;
@@ -881,7 +888,8 @@ ats_status ats_level_destroy(ats_level *L) {
   void *ptrs[] = {L->nbr, L->frec, L->rec_face, L->xrec_dense, L->leaf, L->fkind, L->frel,
                   L->falpha, L->K64, L->xd64, L->b64, L->K32, L->xd32, L->err_flag,
                   L->stage_cell, L->stage_face, L->x64, L->rhs_save,
-                  L->e[0], L->z[0], L->p0[0], L->p1[0], L->e[1], L->z[1], L->p0[1], L->p1[1]};
+                  L->e[0], L->z[0], L->p0[0], L->p1[0], L->e[1], L->z[1], L->p0[1], L->p1[1],
+                  L->q[0], L->dg[0], L->q[1], L->dg[1]};
   for (void *p : ptrs) dev_free(ctx, p);
   delete L;
   return ATS_OK;
