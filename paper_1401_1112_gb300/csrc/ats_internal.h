@@ -152,8 +152,12 @@ struct TickStreams {
   cudaEvent_t fork, join;  // created with cudaEventDisableTiming
 };
 constexpr int kTickEvents = 6;
-cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cudaStream_t st, const TickStreams *fj,
-                        cudaEvent_t *ev, bool capture);
+// grids: [0] k_op, [1] k_ref, [2] k_upd (each kernel strides over its list).
+cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, const int grids[3], cudaStream_t st,
+                        const TickStreams *fj, cudaEvent_t *ev, bool capture);
+// Resident grid of each tick kernel on `device` (its CTAs per SM under its
+// register and shared-memory use, times the SM count), in launch_tick order.
+void tick_grids(bool fp64, bool paper, int device, int grids[3]);
 
 // Start of a solve: e = 0 on every cell of every item, and x64 = src[solve]
 // where src (device array of device pointers) is non-null for that solve.

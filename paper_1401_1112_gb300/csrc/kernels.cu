@@ -42,15 +42,21 @@ namespace ats {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-// resident CTAs per SM the tick kernels are compiled for (caps registers):
-// the FP32 CG path keeps its loads in flight with 5 CTAs of 128 threads; the
-// FP64 bulk path needs twice the registers per value.
-#ifndef ATS_MINB_F32
-#define ATS_MINB_F32 4
+// resident CTAs per SM the CG tick kernels are compiled for (caps
+// registers); the FP64 bulk path needs twice the registers per value.
+#ifndef ATS_MINB_OP
+#define ATS_MINB_OP 4
+#endif
+#ifndef ATS_MINB_UPD
+#define ATS_MINB_UPD 4
 #endif
 template <typename T>
-struct MinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? ATS_MINB_F32 : 3;
+struct MinBlocks {  // k_op
+  static constexpr int value = sizeof(T) == 4 ? ATS_MINB_OP : 3;
+};
+template <typename T>
+struct MinBlocksUpd {
+  static constexpr int value = sizeof(T) == 4 ? ATS_MINB_UPD : 3;
 };
 
 // FP64-quality dot-product accumulation.  FP32 bulk: each product is split
@@ -776,7 +782,7 @@ __device__ __forceinline__ void commit_solve(const TickArgs &a, int cur, int s, 
 // after a true-residual pass.  The CTA owning a solve's first item writes the
 // solve's next state and list entries.
 template <typename T, bool kPaper>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_upd(TickArgs a) {
+__global__ void __launch_bounds__(kThreads, MinBlocksUpd<T>::value) k_upd(TickArgs a) {
   __shared__ Acc<T> red[2][kThreads / 32][3], red2[kThreads / 32][3];
   __shared__ float redmx[2][kThreads / 32], redmx2[kThreads / 32];
   __shared__ int s_base;
@@ -1230,8 +1236,8 @@ static cudaError_t record(cudaEvent_t ev, cudaStream_t st, bool capture) {
 }
 
 template <typename T, bool kPaper>
-static cudaError_t tick_impl(const TickArgs &a, int grid, cudaStream_t st, const TickStreams *fj, cudaEvent_t *ev,
-                             bool capture) {
+static cudaError_t tick_impl(const TickArgs &a, const int grids[3], cudaStream_t st, const TickStreams *fj,
+                             cudaEvent_t *ev, bool capture) {
   cudaError_t err;
   const bool fork = fj && fj->aux;
   cudaStream_t sr = fork ? fj->aux : st;
@@ -1239,11 +1245,11 @@ static cudaError_t tick_impl(const TickArgs &a, int grid, cudaStream_t st, const
   // k_ref first: its FP64-bound items start before k_op's CTAs take the SMs
   if (fork && (err = cudaStreamWaitEvent(sr, fj->fork, 0)) != cudaSuccess) return err;
   if ((err = record(ev ? ev[2] : nullptr, sr, capture)) != cudaSuccess) return err;
-  k_ref<T><<<grid, kThreads, 0, sr>>>(a);
+  k_ref<T><<<grids[1], kThreads, 0, sr>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if ((err = record(ev ? ev[3] : nullptr, sr, capture)) != cudaSuccess) return err;
   if ((err = record(ev ? ev[0] : nullptr, st, capture)) != cudaSuccess) return err;
-  k_op<T><<<grid, kThreads, 0, st>>>(a);
+  k_op<T><<<grids[0], kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if ((err = record(ev ? ev[1] : nullptr, st, capture)) != cudaSuccess) return err;
   if (fork) {
@@ -1251,15 +1257,35 @@ static cudaError_t tick_impl(const TickArgs &a, int grid, cudaStream_t st, const
     if ((err = cudaStreamWaitEvent(st, fj->join, 0)) != cudaSuccess) return err;
   }
   if ((err = record(ev ? ev[4] : nullptr, st, capture)) != cudaSuccess) return err;
-  k_upd<T, kPaper><<<grid, kThreads, 0, st>>>(a);
+  k_upd<T, kPaper><<<grids[2], kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   return record(ev ? ev[5] : nullptr, st, capture);
 }
 
-cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, int grid, cudaStream_t st, const TickStreams *fj,
-                        cudaEvent_t *ev, bool capture) {
-  if (fp64) return paper ? tick_impl<double, true>(a, grid, st, fj, ev, capture) : tick_impl<double, false>(a, grid, st, fj, ev, capture);
-  return paper ? tick_impl<float, true>(a, grid, st, fj, ev, capture) : tick_impl<float, false>(a, grid, st, fj, ev, capture);
+cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, const int grids[3], cudaStream_t st,
+                        const TickStreams *fj, cudaEvent_t *ev, bool capture) {
+  if (fp64) return paper ? tick_impl<double, true>(a, grids, st, fj, ev, capture) : tick_impl<double, false>(a, grids, st, fj, ev, capture);
+  return paper ? tick_impl<float, true>(a, grids, st, fj, ev, capture) : tick_impl<float, false>(a, grids, st, fj, ev, capture);
+}
+
+template <typename T, bool kPaper>
+static void grids_impl(int sms, int grids[3]) {
+  int b[3] = {0, 0, 0};
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_op<T>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_ref<T>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_upd<T, kPaper>, kThreads, 0);
+#ifdef ATS_REF_PER_SM
+  if (b[1] > ATS_REF_PER_SM) b[1] = ATS_REF_PER_SM;
+#endif
+  for (int k = 0; k < 3; ++k) grids[k] = (b[k] > 0 ? b[k] : 1) * sms;
+}
+
+void tick_grids(bool fp64, bool paper, int device, int grids[3]) {
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (sms <= 0) sms = 1;
+  if (fp64) paper ? grids_impl<double, true>(sms, grids) : grids_impl<double, false>(sms, grids);
+  else paper ? grids_impl<float, true>(sms, grids) : grids_impl<float, false>(sms, grids);
 }
 
 // ---------------------------------------------------------------------------
@@ -1335,7 +1361,7 @@ int tick_blocks_per_sm(bool fp64, bool paper) {
   int a = 0, b = 0;
   if (fp64) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_op<double>, kThreads, 0);
-    if (paper) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_upd<double, true>, kThreads, 0);
+    if (paper) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_upd<double, true>, kThreads, 0);  // init / final grid
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_upd<double, false>, kThreads, 0);
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_op<float>, kThreads, 0);

@@ -196,6 +196,9 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
   int sms = 1, bps = tick_blocks_per_sm(true, false);
   NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   const int grid = n_items < bps * sms ? n_items : bps * sms;
+  int grids[3];
+  tick_grids(true, false, device, grids);
+  for (int k = 0; k < 3; ++k) grids[k] = n_items < grids[k] ? n_items : grids[k];
   NA_TRY(launch_init(true, d_solve, d_items, n_items, nullptr, grid, st));
   // the host copies above read stack memory: finish them before it goes away
   NA_TRY(cudaStreamSynchronize(st));
@@ -219,7 +222,7 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
   int active = 1;
   while (active > 0 && ticks < max_ticks) {
     for (int t = 0; t < 8; ++t)
-      NA_TRY(launch_tick(true, false, ta, grid, st, nullptr, nullptr, false));
+      NA_TRY(launch_tick(true, false, ta, grids, st, nullptr, nullptr, false));
     ticks += 8;
     NA_TRY(cudaMemcpyAsync(&active, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     NA_TRY(cudaStreamSynchronize(st));

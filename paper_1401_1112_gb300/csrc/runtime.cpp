@@ -150,6 +150,7 @@ struct Plan {
   ats_solve_opts opts{};
   bool fp64 = true, paper = false;
   int n = 0, n_items = 0, grid = 1;
+  int grids[3] = {1, 1, 1};  // tick kernels: k_op, k_ref, k_upd
   SolveDev *d_solves = nullptr;
   SolveScalars *d_sc = nullptr;     // [2][n] double-buffered scalars
   SolveScalars *d_final = nullptr;  // [n] state of finished solves
@@ -361,6 +362,8 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   P->n_items = (int)items.size();
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
   P->grid = std::max(1, std::min(P->n_items, bps * ctx->num_sms));
+  tick_grids(P->fp64, P->paper, ctx->device, P->grids);
+  for (int k = 0; k < 3; ++k) P->grids[k] = std::max(1, std::min(P->n_items, P->grids[k]));
   if ((s = dev_alloc_t(ctx, n, &P->d_solves)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 2 * (size_t)n, &P->d_sc)) != ATS_OK ||
       (s = dev_alloc_t(ctx, n, &P->d_final)) != ATS_OK ||
@@ -455,7 +458,7 @@ ats_status plan_enqueue_chunk(Plan *P) {
       TickArgs ta = P->targs;
       if (!prof) ta.cells = nullptr;
       for (int t = 0; t < k && err == cudaSuccess; ++t)
-        err = launch_tick(P->fp64, P->paper, ta, P->grid, st, &P->fj, prof ? &P->evs[kTickEvents * t] : nullptr, true);
+        err = launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, prof ? &P->evs[kTickEvents * t] : nullptr, true);
       cudaError_t err2 = cudaStreamEndCapture(st, &g);
       if (err != cudaSuccess || err2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -482,7 +485,7 @@ ats_status plan_enqueue_chunk(Plan *P) {
     TickArgs ta = P->targs;
     if (!prof) ta.cells = nullptr;
     for (int t = 0; t < k; ++t)
-      CUDA_TRY(launch_tick(P->fp64, P->paper, ta, P->grid, st, &P->fj, prof ? &P->evs[kTickEvents * t] : nullptr, false));
+      CUDA_TRY(launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, prof ? &P->evs[kTickEvents * t] : nullptr, false));
   }
   P->ticks += k;
   P->launches += 3 * k;

@@ -117,7 +117,8 @@ struct ats_server {
   ats_context *ctx = nullptr;
   ats_solve_opts opts{};
   bool fp64 = false;
-  int max_slots = 0, max_items = 0, grid = 1;
+  int max_slots = 0, max_items = 0;
+  int grids[3] = {1, 1, 1};  // tick kernels: k_op, k_ref, k_upd
   size_t budget = 0, resident = 0;
   // device plan
   SolveDev *d_solves = nullptr;
@@ -292,7 +293,7 @@ ats_status capture_graph(ats_server *S) {
   S_TRY(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
   for (int t = 0; t < S->opts.check_every && err == cudaSuccess; ++t)
-    err = launch_tick(S->fp64, false, S->targs, S->grid, S->st, &S->fj, nullptr, true);
+    err = launch_tick(S->fp64, false, S->targs, S->grids, S->st, &S->fj, nullptr, true);
   cudaError_t err2 = cudaStreamEndCapture(S->st, &g);
   if (err != cudaSuccess || err2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -503,9 +504,7 @@ ats_status ats_server_create(int device, size_t mem_budget_bytes, const ats_serv
   t.p_upd = S->d_part + (size_t)kNumPartials * mi;
   t.n_active = S->d_active;
   t.cells = nullptr;
-  int sms = 1;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  S->grid = tick_blocks_per_sm(S->fp64, false) * sms;
+  tick_grids(S->fp64, false, device, S->grids);
   S->worker = std::thread(worker_loop, S);
   *out = S;
   return ATS_OK;
