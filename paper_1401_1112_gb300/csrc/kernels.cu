@@ -1274,9 +1274,6 @@ static void grids_impl(int sms, int grids[3]) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_op<T>, kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_ref<T>, kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_upd<T, kPaper>, kThreads, 0);
-#ifdef ATS_REF_PER_SM
-  if (b[1] > ATS_REF_PER_SM) b[1] = ATS_REF_PER_SM;
-#endif
   for (int k = 0; k < 3; ++k) grids[k] = (b[k] > 0 ? b[k] : 1) * sms;
 }
 
