@@ -125,6 +125,11 @@ cudaError_t launch_coef_build_batch(const CoefArgs *args, const int64_t *cell_of
 cudaError_t launch_gather_flags(const int *const *flags, int n, int *out, cudaStream_t st);
 
 // Device state of a planned batch, passed by value to the tick kernels.
+// Cells processed, counted when profiling: [0] k_op CG items after the first
+// iteration of an inner solve, [1] k_ref, [2] k_upd CG items, [3] x += e at
+// the end of an inner solve, [4] k_op CG items in a first iteration.
+constexpr int kCellCounters = 5;
+
 struct TickArgs {
   const SolveDev *solves;
   SolveScalars *sbuf;       // [2][n_solves]
@@ -137,7 +142,7 @@ struct TickArgs {
   double *p_op;             // [n_items][kNumPartials] partials of k_op / k_ref
   double *p_upd;            // [2][n_items][kNumPartials] partials of k_upd by parity
   int *n_active;
-  unsigned long long *cells;  // [4] cells processed per kernel/phase, or null
+  unsigned long long *cells;  // [kCellCounters] cells per kernel / phase, or null
 };
 
 // One tick = k_op (CG items) and k_ref (refinement residual of the solves in

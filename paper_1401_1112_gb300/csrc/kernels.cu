@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a
     }
     store_item_partials<T>(a.p_op + (size_t)it * kNumPartials, pq, none, none, 0.f, red[buf], redmx[buf]);
     buf ^= 1;
-    if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + 0, (unsigned long long)item.n_oct * 8);
+    if (a.cells && threadIdx.x == 0) atomicAdd(a.cells + (first ? 4 : 0), (unsigned long long)item.n_oct * 8);
   }
   __syncthreads();  // the slots are restaged
   }

@@ -370,7 +370,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, P->n_items, &P->d_items)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 3 * (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, 4, &P->d_cells)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, kCellCounters, &P->d_cells)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 4 * (size_t)P->n_items, &P->d_lists)) != ATS_OK ||
       (s = dev_alloc_t(ctx, (size_t)P->n_items, &P->d_ident)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_ctl)) != ATS_OK ||
@@ -512,13 +512,15 @@ ats_status plan_collect_events(Plan *P) {
 
 // Algorithmic bytes per cell of each kernel and phase: the compulsory traffic
 // of the vectors and coefficients (neighbour tables and records not counted).
-//   k_op, CG:        read z, p_old, K_T; write p_new, q               (5 words)
+//   k_op, CG:        read z, p_old, K_T; write p_new, q               (5 words;
+//                    4 in the first iteration of an inner solve: p = z)
 //   k_ref:           read K64, x64, b64 (+ K_T when mixed); write z, D (24 B + 2-3 words)
 //   k_upd, CG:       read p, q, D, z, e; write z, e                   (7 words)
 //   k_upd, x += e:   read/write x (FP64) and e (end of an inner solve) (16 B + 2 words)
-void plan_bytes(const Plan *P, const unsigned long long cells[4], double *op_b, double *ref_b, double *upd_b) {
+void plan_bytes(const Plan *P, const unsigned long long cells[kCellCounters], double *op_b, double *ref_b,
+                double *upd_b) {
   const double w = P->fp64 ? 8.0 : 4.0;
-  *op_b = 5 * w * cells[0];
+  *op_b = 5 * w * cells[0] + 4 * w * cells[4];  // first iteration of an inner solve: no p_old
   *ref_b = (24 + (P->fp64 ? 0 : w) + 2 * w) * cells[1];
   *upd_b = 7 * w * cells[2] + (16 + 2 * w) * cells[3];
 }
@@ -573,7 +575,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   CUDA_TRY(launch_init(P->fp64, P->d_solves, P->d_items, P->n_items, dev ? P->d_src : nullptr, P->grid, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_sc, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_final, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, 4 * sizeof(unsigned long long), st));
+  CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, kCellCounters * sizeof(unsigned long long), st));
   CUDA_TRY(cudaMemcpyAsync(P->d_active, &n, sizeof(int), cudaMemcpyHostToDevice, st));
   {
     // every item of every solve starts in the refinement phase (r0 = b - A x0)
@@ -639,7 +641,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   }
   std::vector<SolveScalars> sc(n);
   CUDA_TRY(cudaMemcpyAsync(sc.data(), P->d_final, sizeof(SolveScalars) * n, cudaMemcpyDeviceToHost, st));
-  unsigned long long cells[4] = {0, 0, 0, 0};
+  unsigned long long cells[kCellCounters] = {0, 0, 0, 0, 0};
   if (P->profiling) CUDA_TRY(cudaMemcpyAsync(cells, P->d_cells, sizeof(cells), cudaMemcpyDeviceToHost, st));
   std::vector<int> flags(n, 0);
   CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, n, P->d_flags, st));
