@@ -205,10 +205,9 @@ __device__ __forceinline__ void load_nbr6(const int32_t *__restrict__ nbr, int o
 }
 
 // The three in-oct faces of every cell, each cell pair once:
-// dsum += C, off += C * v(neighbour), with C = h (K_i + K_j) between leaves.
+// off += C * v(neighbour), with C = h (K_i + K_j) between leaves.
 template <typename T>
-__device__ __forceinline__ void in_oct_faces(const T (&K)[8], const T (&v)[8], T h, T (&dsum)[8],
-                                             T (&off)[8]) {
+__device__ __forceinline__ void in_oct_faces(const T (&K)[8], const T (&v)[8], T h, T (&off)[8]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -216,8 +215,6 @@ __device__ __forceinline__ void in_oct_faces(const T (&K)[8], const T (&v)[8], T
       if (c & (1 << a)) continue;
       const int d = c | (1 << a);
       const T C = (K[c] >= T(0) && K[d] >= T(0)) ? h * (K[c] + K[d]) : T(0);
-      dsum[c] += C;
-      dsum[d] += C;
       off[c] += C * v[d];
       off[d] += C * v[c];
     }
@@ -233,7 +230,7 @@ __device__ __forceinline__ void in_oct_faces(const T (&K)[8], const T (&v)[8], T
 template <int DIR, typename T>
 __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T *__restrict__ z,
                                         const T *__restrict__ pold, bool first, T beta, T h,
-                                        const T (&K)[8], T (&dsum)[8], T (&off)[8]) {
+                                        const T (&K)[8], T (&off)[8]) {
   constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
   if (n < 0) return;
   T Kn[8], Zn[8], Pn[8];
@@ -246,7 +243,6 @@ __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T
     const int j = c ^ (1 << A);
     const T pj = first ? Zn[j] : fma(beta, Pn[j], Zn[j]);
     const T C = (Kn[j] >= T(0)) ? h * (K[c] + Kn[j]) : T(0);
-    dsum[c] += C;
     off[c] += C * pj;
   }
 }
@@ -507,20 +503,21 @@ __device__ __forceinline__ void gather_totals(const double *P0, int k0, const do
 // reduces the solve totals it needs
 // ---------------------------------------------------------------------------
 
+// The diagonal D = 1 + xd + sum C of an inner solve is the one its
+// refinement pass stored, so k_op forms only the off-diagonal sums.
 template <typename T>
 struct OpOwn {
   int nb[6];
-  int rec;
-  T K[8], z[8], pp[8];
+  T K[8], z[8], pp[8], d[8];
 };
 
 template <typename T>
 __device__ __forceinline__ void op_load_own(const SolveDev &sd, int o, bool first, const T *__restrict__ pold,
                                             OpOwn<T> &w) {
   load_nbr6(sd.nbr, o, w.nb);
-  w.rec = __ldg(sd.xrec + o);
   ld8_ro((const T *)sd.KT + 8 * o, w.K);
   ld8_ro((const T *)sd.z + 8 * o, w.z);
+  ld8_ro((const T *)sd.dg + 8 * o, w.d);
   if (!first) ld8_ro(pold + 8 * o, w.pp);
 }
 
@@ -534,28 +531,20 @@ __device__ __forceinline__ void op_compute(const SolveDev &sd, int o, const OpOw
   T pv[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) pv[c] = first ? w.z[c] : fma(beta, w.pp[c], w.z[c]);
-  T dsum[8], off[8];
+  T off[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) dsum[c] = off[c] = T(0);
-  in_oct_faces(w.K, pv, h, dsum, off);
-  op_face<0>(w.nb[0], KT, z, pold, first, beta, h, w.K, dsum, off);
-  op_face<1>(w.nb[1], KT, z, pold, first, beta, h, w.K, dsum, off);
-  op_face<2>(w.nb[2], KT, z, pold, first, beta, h, w.K, dsum, off);
-  op_face<3>(w.nb[3], KT, z, pold, first, beta, h, w.K, dsum, off);
-  op_face<4>(w.nb[4], KT, z, pold, first, beta, h, w.K, dsum, off);
-  op_face<5>(w.nb[5], KT, z, pold, first, beta, h, w.K, dsum, off);
-  T xd[8];
-  if (w.rec >= 0) {
-    ld8_ro((const T *)sd.xdT + 8 * w.rec, xd);
-  } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) xd[c] = T(0);
-  }
+  for (int c = 0; c < 8; ++c) off[c] = T(0);
+  in_oct_faces(w.K, pv, h, off);
+  op_face<0>(w.nb[0], KT, z, pold, first, beta, h, w.K, off);
+  op_face<1>(w.nb[1], KT, z, pold, first, beta, h, w.K, off);
+  op_face<2>(w.nb[2], KT, z, pold, first, beta, h, w.K, off);
+  op_face<3>(w.nb[3], KT, z, pold, first, beta, h, w.K, off);
+  op_face<4>(w.nb[4], KT, z, pold, first, beta, h, w.K, off);
+  op_face<5>(w.nb[5], KT, z, pold, first, beta, h, w.K, off);
   T local = T(0), qv[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const T d = T(1) + xd[c] + dsum[c];
-    const T q = d * pv[c] - off[c];
+    const T q = w.d[c] * pv[c] - off[c];
     const bool leaf = w.K[c] >= T(0);
     if (leaf) local = fma(pv[c], q, local);
     qv[c] = leaf ? q : T(0);

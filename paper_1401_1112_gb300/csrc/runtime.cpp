@@ -512,15 +512,15 @@ ats_status plan_collect_events(Plan *P) {
 
 // Algorithmic bytes per cell of each kernel and phase: the compulsory traffic
 // of the vectors and coefficients (neighbour tables and records not counted).
-//   k_op, CG:        read z, p_old, K_T; write p_new, q               (5 words;
-//                    4 in the first iteration of an inner solve: p = z)
+//   k_op, CG:        read z, p_old, K_T, D; write p_new, q            (6 words;
+//                    5 in the first iteration of an inner solve: p = z)
 //   k_ref:           read K64, x64, b64 (+ K_T when mixed); write z, D (24 B + 2-3 words)
 //   k_upd, CG:       read p, q, D, z, e; write z, e                   (7 words)
 //   k_upd, x += e:   read/write x (FP64) and e (end of an inner solve) (16 B + 2 words)
 void plan_bytes(const Plan *P, const unsigned long long cells[kCellCounters], double *op_b, double *ref_b,
                 double *upd_b) {
   const double w = P->fp64 ? 8.0 : 4.0;
-  *op_b = 5 * w * cells[0] + 4 * w * cells[4];  // first iteration of an inner solve: no p_old
+  *op_b = 6 * w * cells[0] + 5 * w * cells[4];  // first iteration of an inner solve: no p_old
   *ref_b = (24 + (P->fp64 ? 0 : w) + 2 * w) * cells[1];
   *upd_b = 7 * w * cells[2] + (16 + 2 * w) * cells[3];
 }
