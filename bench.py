@@ -172,7 +172,10 @@ def run_ours(args, rank, world, local):
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # one non-default stream for torch's work and the library's, so that the
+    # per-step copies and the solves are ordered (and graphs can be captured)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
 
     solves = W.config4(n_solves=args.solves, seed=replica_seed(rank))
     n = len(solves)

@@ -276,6 +276,15 @@ def ats_context_destroy(ctx):
 
 
 def ats_context_set_stream(ctx, stream_handle: Optional[int]):
+    """``stream_handle``: a cudaStream_t (e.g. ``torch.cuda.Stream().cuda_stream``),
+    or None for the context's own stream.  0 (the legacy default stream, which
+    is what ``torch.cuda.current_stream()`` returns unless a stream was made
+    current) is rejected: the C call would take it as "own stream" and run
+    unordered with the caller's work, and the library's CUDA graphs cannot be
+    captured on the legacy stream."""
+    if stream_handle is not None and int(stream_handle) == 0:
+        raise ValueError("stream handle 0 is the legacy default stream: pass a non-default stream "
+                         "(torch.cuda.Stream) or None for the context's own stream")
     return _check(lib().ats_context_set_stream(ctx, ctypes.c_void_p(stream_handle) if stream_handle else None),
                   "ats_context_set_stream")
 
@@ -573,7 +582,7 @@ def ats_server_stats(server):
 class Context:
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: Optional[int] = None):
         self.handle = ats_context_create(device, mem_budget_bytes)
-        if stream:
+        if stream is not None:
             ats_context_set_stream(self.handle, stream)
 
     def set_stream(self, stream_handle):

@@ -149,17 +149,27 @@ struct TickArgs {
 // their refinement phase), which touch disjoint solves, then k_upd (all items;
 // a solve that leaves its inner solve folds x += e there).  With fj->aux set,
 // k_ref is launched first on fj->aux, forked from st, then k_op on st, and
-// both join before k_upd, so the two overlap; otherwise all three run on st.  ev (null, or 6 events):
-// [0] / [1] around k_op, [2] / [3] around k_ref, [4] / [5] around k_upd;
-// `capture` says whether the stream is being captured.
+// both join before k_upd, so the two overlap; otherwise all three run on st.
+// tt (null, or timing): after each kernel an event is recorded on a side
+// stream that waits for that kernel and that nothing else waits for, so the
+// timestamps stay off the kernels' dependency chain; ev[0] after k_op, ev[1]
+// after k_ref, ev[2] after k_upd.  `capture` says whether st is being
+// captured.
 struct TickStreams {
   cudaStream_t aux;
   cudaEvent_t fork, join;  // created with cudaEventDisableTiming
 };
-constexpr int kTickEvents = 6;
+struct TickTiming {
+  cudaStream_t side;
+  cudaEvent_t mark;  // ordering marker, cudaEventDisableTiming
+  cudaEvent_t *ev;   // [kTickEvents] timing events of this tick
+};
+constexpr int kTickEvents = 3;
+// Record `ev` on tt->side once the work queued so far on `from` is done.
+cudaError_t record_after(const TickTiming &tt, cudaEvent_t ev, cudaStream_t from, bool capture);
 // grids: [0] k_op, [1] k_ref, [2] k_upd (each kernel strides over its list).
 cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, const int grids[3], cudaStream_t st,
-                        const TickStreams *fj, cudaEvent_t *ev, bool capture);
+                        const TickStreams *fj, const TickTiming *tt, bool capture);
 // Resident grid of each tick kernel on `device` (its CTAs per SM under its
 // register and shared-memory use, times the SM count), in launch_tick order.
 void tick_grids(bool fp64, bool paper, int device, int grids[3]);

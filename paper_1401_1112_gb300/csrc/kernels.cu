@@ -1219,42 +1219,42 @@ cudaError_t launch_apply64(const SolveDev *sd, const double *x, double *y, cudaS
 // tick launcher
 // ---------------------------------------------------------------------------
 
-static cudaError_t record(cudaEvent_t ev, cudaStream_t st, bool capture) {
-  if (!ev) return cudaSuccess;
-  return capture ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
+cudaError_t record_after(const TickTiming &tt, cudaEvent_t ev, cudaStream_t from, bool capture) {
+  cudaError_t err;
+  if ((err = cudaEventRecord(tt.mark, from)) != cudaSuccess) return err;
+  if ((err = cudaStreamWaitEvent(tt.side, tt.mark, 0)) != cudaSuccess) return err;
+  return capture ? cudaEventRecordWithFlags(ev, tt.side, cudaEventRecordExternal) : cudaEventRecord(ev, tt.side);
 }
 
 template <typename T, bool kPaper>
 static cudaError_t tick_impl(const TickArgs &a, const int grids[3], cudaStream_t st, const TickStreams *fj,
-                             cudaEvent_t *ev, bool capture) {
+                             const TickTiming *tt, bool capture) {
   cudaError_t err;
   const bool fork = fj && fj->aux;
   cudaStream_t sr = fork ? fj->aux : st;
   if (fork && (err = cudaEventRecord(fj->fork, st)) != cudaSuccess) return err;
   // k_ref first: its FP64-bound items start before k_op's CTAs take the SMs
   if (fork && (err = cudaStreamWaitEvent(sr, fj->fork, 0)) != cudaSuccess) return err;
-  if ((err = record(ev ? ev[2] : nullptr, sr, capture)) != cudaSuccess) return err;
   k_ref<T><<<grids[1], kThreads, 0, sr>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  if ((err = record(ev ? ev[3] : nullptr, sr, capture)) != cudaSuccess) return err;
-  if ((err = record(ev ? ev[0] : nullptr, st, capture)) != cudaSuccess) return err;
+  if (tt && (err = record_after(*tt, tt->ev[1], sr, capture)) != cudaSuccess) return err;
   k_op<T><<<grids[0], kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  if ((err = record(ev ? ev[1] : nullptr, st, capture)) != cudaSuccess) return err;
+  if (tt && (err = record_after(*tt, tt->ev[0], st, capture)) != cudaSuccess) return err;
   if (fork) {
     if ((err = cudaEventRecord(fj->join, sr)) != cudaSuccess) return err;
     if ((err = cudaStreamWaitEvent(st, fj->join, 0)) != cudaSuccess) return err;
   }
-  if ((err = record(ev ? ev[4] : nullptr, st, capture)) != cudaSuccess) return err;
   k_upd<T, kPaper><<<grids[2], kThreads, 0, st>>>(a);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  return record(ev ? ev[5] : nullptr, st, capture);
+  if (tt && (err = record_after(*tt, tt->ev[2], st, capture)) != cudaSuccess) return err;
+  return cudaSuccess;
 }
 
 cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, const int grids[3], cudaStream_t st,
-                        const TickStreams *fj, cudaEvent_t *ev, bool capture) {
-  if (fp64) return paper ? tick_impl<double, true>(a, grids, st, fj, ev, capture) : tick_impl<double, false>(a, grids, st, fj, ev, capture);
-  return paper ? tick_impl<float, true>(a, grids, st, fj, ev, capture) : tick_impl<float, false>(a, grids, st, fj, ev, capture);
+                        const TickStreams *fj, const TickTiming *tt, bool capture) {
+  if (fp64) return paper ? tick_impl<double, true>(a, grids, st, fj, tt, capture) : tick_impl<double, false>(a, grids, st, fj, tt, capture);
+  return paper ? tick_impl<float, true>(a, grids, st, fj, tt, capture) : tick_impl<float, false>(a, grids, st, fj, tt, capture);
 }
 
 template <typename T, bool kPaper>

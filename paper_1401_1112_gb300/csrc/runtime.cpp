@@ -173,9 +173,11 @@ struct Plan {
   int graph_ticks = 0;
   bool graph_profiled = false;
   bool profiling = false;
-  std::vector<cudaEvent_t> evs;  // kTickEvents per tick of a chunk
+  std::vector<cudaEvent_t> evs;  // chunk start, then kTickEvents per tick of a chunk
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   TickStreams fj{nullptr, nullptr, nullptr};  // k_ref's stream, fork / join events
+  cudaStream_t side = nullptr;                // timing events (profiling)
+  cudaEvent_t mark = nullptr;
   int slot = 0;
   double op_ms = 0.0, ref_ms = 0.0, upd_ms = 0.0, op_bytes = 0.0, ref_bytes = 0.0, upd_bytes = 0.0;
   int launches = 0;
@@ -254,6 +256,8 @@ void plan_free(Plan *P) {
   if (P->fj.fork) cudaEventDestroy(P->fj.fork);
   if (P->fj.join) cudaEventDestroy(P->fj.join);
   if (P->fj.aux) cudaStreamDestroy(P->fj.aux);
+  if (P->mark) cudaEventDestroy(P->mark);
+  if (P->side) cudaStreamDestroy(P->side);
   dev_free(ctx, P->d_solves);
   dev_free(ctx, P->d_sc);
   dev_free(ctx, P->d_final);
@@ -422,19 +426,41 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   CUDA_TRY(cudaStreamCreateWithFlags(&P->fj.aux, cudaStreamNonBlocking));
   CUDA_TRY(cudaEventCreateWithFlags(&P->fj.fork, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&P->fj.join, cudaEventDisableTiming));
+  CUDA_TRY(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&P->mark, cudaEventDisableTiming));
   CUDA_TRY(cudaStreamSynchronize(st));
   *out = P;
   return ATS_OK;
 }
 
 ats_status plan_ensure_events(Plan *P) {
-  const size_t need = kTickEvents * (size_t)P->opts.check_every;
+  const size_t need = 1 + kTickEvents * (size_t)P->opts.check_every;
   while (P->evs.size() < need) {
     cudaEvent_t e;
     CUDA_TRY(cudaEventCreate(&e));
     P->evs.push_back(e);
   }
   return ATS_OK;
+}
+
+// `k` ticks on st; when profiling, with timing events on the side stream
+// (chunk start, then per tick), the side stream rejoining st at the end.
+cudaError_t timed_ticks(Plan *P, const TickArgs &ta, cudaStream_t st, int k, bool capture) {
+  cudaError_t err = cudaSuccess;
+  if (!P->profiling) {
+    for (int t = 0; t < k && err == cudaSuccess; ++t)
+      err = launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, nullptr, capture);
+    return err;
+  }
+  TickTiming tt{P->side, P->mark, nullptr};
+  if ((err = record_after(tt, P->evs[0], st, capture)) != cudaSuccess) return err;
+  for (int t = 0; t < k && err == cudaSuccess; ++t) {
+    tt.ev = &P->evs[1 + kTickEvents * t];
+    err = launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, &tt, capture);
+  }
+  if (err != cudaSuccess) return err;
+  if ((err = cudaEventRecord(P->mark, P->side)) != cudaSuccess) return err;
+  return cudaStreamWaitEvent(st, P->mark, 0);
 }
 
 // Enqueue one poll interval (check_every ticks) on the stream.
@@ -457,8 +483,7 @@ ats_status plan_enqueue_chunk(Plan *P) {
       cudaError_t err = cudaSuccess;
       TickArgs ta = P->targs;
       if (!prof) ta.cells = nullptr;
-      for (int t = 0; t < k && err == cudaSuccess; ++t)
-        err = launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, prof ? &P->evs[kTickEvents * t] : nullptr, true);
+      err = timed_ticks(P, ta, st, k, true);
       cudaError_t err2 = cudaStreamEndCapture(st, &g);
       if (err != cudaSuccess || err2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -484,8 +509,7 @@ ats_status plan_enqueue_chunk(Plan *P) {
     }
     TickArgs ta = P->targs;
     if (!prof) ta.cells = nullptr;
-    for (int t = 0; t < k; ++t)
-      CUDA_TRY(launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, prof ? &P->evs[kTickEvents * t] : nullptr, false));
+    CUDA_TRY(timed_ticks(P, ta, st, k, false));
   }
   P->ticks += k;
   P->launches += 3 * k;
@@ -495,17 +519,22 @@ ats_status plan_enqueue_chunk(Plan *P) {
   return ATS_OK;
 }
 
+// Per tick: k_op and k_ref both start when the previous k_upd (or the chunk)
+// ends; k_upd starts when the later of the two ends.
 ats_status plan_collect_events(Plan *P) {
   const int k = P->opts.check_every;
+  cudaEvent_t prev = P->evs[0];
   for (int t = 0; t < k; ++t) {
-    float a = 0.f, b = 0.f, c = 0.f;
-    cudaEvent_t *e = &P->evs[kTickEvents * t];
-    CUDA_TRY(cudaEventElapsedTime(&a, e[0], e[1]));
-    CUDA_TRY(cudaEventElapsedTime(&b, e[2], e[3]));
-    CUDA_TRY(cudaEventElapsedTime(&c, e[4], e[5]));
+    float a = 0.f, b = 0.f, c = 0.f, order = 0.f;
+    cudaEvent_t *e = &P->evs[1 + kTickEvents * t];
+    CUDA_TRY(cudaEventElapsedTime(&a, prev, e[0]));
+    CUDA_TRY(cudaEventElapsedTime(&b, prev, e[1]));
+    CUDA_TRY(cudaEventElapsedTime(&order, e[0], e[1]));
+    CUDA_TRY(cudaEventElapsedTime(&c, order >= 0.f ? e[1] : e[0], e[2]));
     P->op_ms += a;
     P->ref_ms += b;
     P->upd_ms += c;
+    prev = e[2];
   }
   return ATS_OK;
 }

@@ -123,3 +123,11 @@ def test_noalloc_rejects_misaligned_arrays(built):
                                          1e-10, 0, ctypes.byref(st))
     assert code == built.ATS_ERR_INVALID_ARG
     assert "32-byte" in built.ats_last_error()
+
+
+def test_legacy_default_stream_is_rejected(built):
+    """Stream handle 0 (the legacy default stream) would be taken as "the
+    context's own stream" and run unordered with the caller's work; the
+    binding rejects it before any CUDA call."""
+    with pytest.raises(ValueError, match="legacy default stream"):
+        built.ats_context_set_stream(None, 0)
