@@ -317,7 +317,7 @@ ats_status ats_server_stats(ats_server *server, ats_server_counters *out);
  * processes whose allocator belongs to another runtime).  It solves one level
  * like ats_solve with ATS_PREC_FP64 and ATS_STOP_RESIDUAL, but calls no
  * cudaMalloc or cudaFree: its CG vectors, partial sums, work list and
- * scalars live in one fixed device array inside the library (about 12.7 MB,
+ * scalars live in one fixed device array inside the library (about 19 MB,
  * held by every GPU that loads the library until the process exits).
  *
  * Arguments (all arrays are DEVICE pointers, FP64, read in stream order on

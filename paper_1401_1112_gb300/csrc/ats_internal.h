@@ -36,6 +36,7 @@ struct SolveDev {
   void *z;              // [N]  preconditioned residual (bulk precision)
   void *p0;             // [N]  search direction, ping
   void *p1;             // [N]  search direction, pong
+  const double *C64;    // [n_oct][3][8] h (K_i + K_j) of each cell's +x, +y, +z face (0 off the leaves)
   void *q;              // [N]  (I + dt A) p of the current direction (k_op)
   void *dg;             // [N]  diagonal D = 1 + xd + sum C (k_ref; 1 off the leaves)
   double h;             // dt / dx^2 / 2, so an interior C = h (K_i + K_j)
@@ -116,12 +117,20 @@ struct CoefArgs {
   float *xd32;
   double *b64;
   int *err_flag;
+  const int32_t *nbr;   // for the face coefficients
+  double *C64;          // [n_oct][3][8] written by the face-coefficient pass
 };
+// K, diagonal extras and b, then the FP64 face coefficients C64 (a second
+// pass, once K64 is complete).
 cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st);
 // One launch for many levels (args, cell_off: device arrays, n levels) after
 // zeroing the levels' error flags (flags: device array of device pointers).
 cudaError_t launch_coef_build_batch(const CoefArgs *args, const int64_t *cell_off, int n, int64_t total_cells,
                                     int *const *flags, cudaStream_t st);
+// FP64 face coefficients C64[(3 o + a) 8 + c] = h (K_i + K_j) between cell i =
+// 8 o + c and its +a neighbour j when both are leaves (K >= 0), else 0.
+cudaError_t launch_face_coef(int64_t n_oct, const int32_t *nbr, const double *K64, double h, double *C64,
+                             cudaStream_t st);
 cudaError_t launch_gather_flags(const int *const *flags, int n, int *out, cudaStream_t st);
 
 // Device state of a planned batch, passed by value to the tick kernels.

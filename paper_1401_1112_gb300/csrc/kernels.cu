@@ -247,55 +247,80 @@ __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T
   }
 }
 
-// k_ref, out-of-oct face DIR: FP64 flux sums (K_i + K_j)(x_i - x_j) and the
-// bulk-precision diagonal for the preconditioner.
-template <int DIR, typename T>
-__device__ __forceinline__ void ref_face(int n, const SolveDev &sd, const T *__restrict__ KT, T hT,
-                                         const double (&K)[8], const T (&KTo)[8],
-                                         const double (&xv)[8], double (&acc)[8], T (&dsT)[8]) {
-  constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
-  constexpr bool mixed = sizeof(T) != sizeof(double);
-  if (n < 0) return;
-  double Kn[8], Xn[8];
-  T KTn[8];
-  ld_face<A, NB>(sd.K64 + 8 * n, Kn);
-  ld_face<A, NB>(sd.x64 + 8 * n, Xn);
-  if (mixed) ld_face<A, NB>(KT + 8 * n, KTn);
+// k_ref, axis A of an oct: FP64 flux sums C (x_i - x_j) with the stored FP64
+// face coefficients C = h (K_i + K_j) (row A of this oct for the in-oct pairs
+// and the +A face, row A of the -A neighbour for the -A face), and the FP32
+// diagonal sums of the bulk precision.
+template <int A, typename T>
+__device__ __forceinline__ void ref_axis(const SolveDev &sd, int o, const int (&nb)[6], const T *__restrict__ KT,
+                                         T hT, const T (&KTo)[8], const double (&xv)[8], double (&acc)[8],
+                                         T (&dsT)[8]) {
+  constexpr int bit = 1 << A;
+  double Cu[8];
+  ld8_ro(sd.C64 + (3 * (size_t)o + A) * 8, Cu);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    if (((c >> A) & 1) != S) continue;
-    const int j = c ^ (1 << A);
-    if (Kn[j] >= 0.0) {
-      const double Ks = K[c] + Kn[j];
-      acc[c] = fma(Ks, xv[c] - Xn[j], acc[c]);
-      if (mixed) dsT[c] += hT * (KTo[c] + KTn[j]);
-      else dsT[c] += (T)(sd.h * Ks);
+    if (c & bit) continue;
+    const int d = c | bit;
+    const double df = xv[c] - xv[d];
+    acc[c] = fma(Cu[c], df, acc[c]);
+    acc[d] = fma(-Cu[c], df, acc[d]);
+    if (KTo[c] >= T(0) && KTo[d] >= T(0)) {
+      const T Ct = hT * (KTo[c] + KTo[d]);
+      dsT[c] += Ct;
+      dsT[d] += Ct;
+    }
+  }
+  int n = nb[2 * A + 1];  // +A face: this oct's cells with bit A set, C from row A of this oct
+  if (n >= 0) {
+    double Xn[8];
+    T KTn[8];
+    ld_face<A, 0>(sd.x64 + 8 * n, Xn);
+    ld_face<A, 0>(KT + 8 * n, KTn);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (!(c & bit)) continue;
+      const int j = c ^ bit;
+      acc[c] = fma(Cu[c], xv[c] - Xn[j], acc[c]);
+      if (KTn[j] >= T(0)) dsT[c] += hT * (KTo[c] + KTn[j]);
+    }
+  }
+  n = nb[2 * A];  // -A face: cells with bit A clear, C from row A of the -A neighbour
+  if (n >= 0) {
+    double Xn[8], Cn[8];
+    T KTn[8];
+    ld_face<A, 1>(sd.x64 + 8 * n, Xn);
+    ld_face<A, 1>(sd.C64 + (3 * (size_t)n + A) * 8, Cn);
+    ld_face<A, 1>(KT + 8 * n, KTn);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c & bit) continue;
+      const int j = c | bit;
+      acc[c] = fma(Cn[j], xv[c] - Xn[j], acc[c]);
+      if (KTn[j] >= T(0)) dsT[c] += hT * (KTo[c] + KTn[j]);
     }
   }
 }
 
-// k_ref: true residual r = b - (I + dt A) x in FP64 with the FP64 K, xd and b,
-// written as r = b - (1 + xd) x - h sum_f (K_i + K_j)(x_i - x_j) (every
-// product a DFMA); z = r / D_T in the bulk precision.  The correction e was
-// added to x by k_op in this tick.  Norms for the stopping test (r.r, x.x)
-// and r.z are accumulated with compensated bulk-precision dots.
+// k_ref: true residual r = b - (I + dt A) x in FP64 with the FP64 xd, b and
+// face coefficients, written as r = b - (1 + xd) x - sum_f C_f (x_i - x_j)
+// (every product a DFMA); z = r / D_T in the bulk precision, D_T stored for the
+// CG kernels of the following inner solve.  Norms for the stopping test (r.r,
+// x.x) and r.z are accumulated with compensated bulk-precision dots.
 template <typename T>
 __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool want_x, Acc<T> &rr,
                                               Acc<T> &xx, Acc<T> &rz) {
   const T *__restrict__ KT = (const T *)sd.KT;
   T *z = (T *)sd.z;
   constexpr bool mixed = sizeof(T) != sizeof(double);
-  const double h = sd.h;
   const T hT = (T)sd.h;
   int nb[6];
   load_nbr6(sd.nbr, o, nb);
   const int rec = __ldg(sd.xrec + o);
-  double K[8], xv[8], b[8];
+  double xv[8];
   T KTo[8];
-  ld8_ro(sd.K64 + 8 * o, K);
   ld8_ro(sd.x64 + 8 * o, xv);
-  ld8_ro(sd.b64 + 8 * o, b);
-  if (mixed) ld8_ro(KT + 8 * o, KTo);
+  ld8_ro(KT + 8 * o, KTo);
   double acc[8];
   T dsT[8];
 #pragma unroll
@@ -303,44 +328,25 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
     acc[c] = 0.0;
     dsT[c] = T(0);
   }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      if (c & (1 << a)) continue;
-      const int d = c | (1 << a);
-      if (K[c] >= 0.0 && K[d] >= 0.0) {
-        const double Ks = K[c] + K[d];
-        const double df = xv[c] - xv[d];
-        acc[c] = fma(Ks, df, acc[c]);
-        acc[d] = fma(-Ks, df, acc[d]);
-        const T Ct = mixed ? hT * (KTo[c] + KTo[d]) : (T)(h * Ks);
-        dsT[c] += Ct;
-        dsT[d] += Ct;
-      }
-    }
-  }
-  ref_face<0>(nb[0], sd, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<1>(nb[1], sd, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<2>(nb[2], sd, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<3>(nb[3], sd, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<4>(nb[4], sd, KT, hT, K, KTo, xv, acc, dsT);
-  ref_face<5>(nb[5], sd, KT, hT, K, KTo, xv, acc, dsT);
-  double xd[8];
+  ref_axis<0>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
+  ref_axis<1>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
+  ref_axis<2>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
+  double xd[8], b[8];
   T xdT[8];
   if (rec >= 0) {
     ld8_ro(sd.xd64 + 8 * rec, xd);
     if (mixed) ld8_ro((const T *)sd.xdT + 8 * rec, xdT);
   }
+  ld8_ro(sd.b64 + 8 * o, b);
   T zo[8], dv[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const bool leaf = K[c] >= 0.0;
+    const bool leaf = KTo[c] >= T(0);
     const double base = rec >= 0 ? fma(-(1.0 + xd[c]), xv[c], b[c]) : b[c] - xv[c];
-    const double r = fma(-h, acc[c], base);
+    const double r = base - acc[c];
     const T rT = (T)r;
-    // D in the bulk precision, formed as the CG kernels form it; kept for
-    // the update kernel of the following inner solve
+    // D in the bulk precision, kept for the CG kernels of the following
+    // inner solve
     const T dT = T(1) + (rec >= 0 ? (mixed ? xdT[c] : (T)xd[c]) : T(0)) + dsT[c];
     const T zc = rT / dT;
     zo[c] = leaf ? zc : T(0);
@@ -998,6 +1004,52 @@ __global__ void k_coef_build_batch(const CoefArgs *__restrict__ args, const int6
   coef_cell(args[lo], g - cell_off[lo]);
 }
 
+// The FP64 face coefficients of cell i = 8 o + c: for each axis a, the face
+// towards +a (the in-oct partner when bit a of c is 0, else the facing cell of
+// the +a neighbour oct).
+__device__ __forceinline__ void face_coef_cell(const int32_t *__restrict__ nbr, const double *__restrict__ K64,
+                                               double h, double *__restrict__ C64, int64_t i) {
+  const int64_t o = i >> 3;
+  const int c = (int)(i & 7);
+  const double Ki = K64[i];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int bit = 1 << ax;
+    int64_t j = -1;
+    if (!(c & bit)) {
+      j = 8 * o + (c | bit);
+    } else {
+      const int n = nbr[6 * o + 2 * ax + 1];
+      if (n >= 0) j = 8 * (int64_t)n + (c ^ bit);
+    }
+    double C = 0.0;
+    if (j >= 0) {
+      const double Kj = K64[j];
+      if (Ki >= 0.0 && Kj >= 0.0) C = h * (Ki + Kj);
+    }
+    C64[(3 * o + ax) * 8 + c] = C;
+  }
+}
+
+__global__ void k_face_coef(int64_t n_oct, const int32_t *__restrict__ nbr, const double *__restrict__ K64,
+                            double h, double *__restrict__ C64) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 8 * n_oct) face_coef_cell(nbr, K64, h, C64, i);
+}
+
+__global__ void k_face_coef_batch(const CoefArgs *__restrict__ args, const int64_t *__restrict__ cell_off, int n) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cell_off[n]) return;
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cell_off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  const CoefArgs &a = args[lo];
+  face_coef_cell(a.nbr, a.K64, a.h, a.C64, g - cell_off[lo]);
+}
+
 __global__ void k_zero_flags(int *const *__restrict__ flags, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) *flags[k] = 0;
@@ -1014,6 +1066,16 @@ cudaError_t launch_coef_build_batch(const CoefArgs *args, const int64_t *cell_of
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || total_cells == 0) return e;
   k_coef_build_batch<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(args, cell_off, n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_face_coef_batch<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(args, cell_off, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_coef(int64_t n_oct, const int32_t *nbr, const double *K64, double h, double *C64,
+                             cudaStream_t st) {
+  if (n_oct <= 0) return cudaSuccess;
+  const int64_t N = 8 * n_oct;
+  k_face_coef<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(n_oct, nbr, K64, h, C64);
   return cudaGetLastError();
 }
 
@@ -1027,7 +1089,9 @@ cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st) {
   const int threads = 256;
   const int64_t blocks = (N + threads - 1) / threads;
   k_coef_build<<<(unsigned)blocks, threads, 0, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_face_coef(a.n_oct, a.nbr, a.K64, a.h, a.C64, st);
 }
 
 // ---------------------------------------------------------------------------

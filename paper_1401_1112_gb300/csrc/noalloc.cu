@@ -50,11 +50,11 @@ constexpr size_t kOffPart = align256(kOffLists + sizeof(int32_t) * 4 * kNoAllocM
 constexpr size_t kOffXrec = align256(kOffPart + 3 * sizeof(double) * kNumPartials * kNoAllocMaxItems);
 constexpr size_t kOffVec = align256(kOffXrec + sizeof(int32_t) * (kNoAllocMaxCells / 8));
 constexpr size_t kVecBytes = align256(sizeof(double) * kNoAllocMaxCells);
-constexpr size_t kScratchBytes = kOffVec + 6 * kVecBytes;  // e, z, p0, p1, q, D
+constexpr size_t kScratchBytes = kOffVec + 9 * kVecBytes;  // e, z, p0, p1, q, D, then C64 (3 vectors)
 
 }  // namespace
 
-// The scratch array (about 12.7 MB for the default maximum of 2^18 cells).
+// The scratch array (about 19 MB for the default maximum of 2^18 cells).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
@@ -154,6 +154,7 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
   sd.p1 = vec + 3 * vstride;
   sd.q = vec + 4 * vstride;
   sd.dg = vec + 5 * vstride;
+  sd.C64 = vec + 6 * vstride;
   sd.h = h;
   sd.tol = tol;
   sd.inner_rtol = 0.0;
@@ -192,6 +193,8 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
   NA_TRY(cudaMemcpyAsync(d_lists + (size_t)kRefine * n_items, first_list, sizeof(int32_t) * n_items,
                          cudaMemcpyHostToDevice, st));
   k_fill_xrec<<<(unsigned)((n_oct + 255) / 256), 256, 0, st>>>(d_xrec, (int)n_oct, xd != nullptr);
+  NA_TRY(cudaGetLastError());
+  NA_TRY(launch_face_coef(n_oct, nbr, K, h, vec + 6 * vstride, st));
   NA_TRY(cudaGetLastError());
   int sms = 1, bps = tick_blocks_per_sm(true, false);
   NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));

@@ -53,6 +53,7 @@ struct ats_level {
   bool dense_xd = false;
   double dt = 0.0;
   double *K64 = nullptr, *xd64 = nullptr, *b64 = nullptr;
+  double *C64 = nullptr;  // [n_oct][3][8] FP64 face coefficients (+x, +y, +z faces)
   float *K32 = nullptr, *xd32 = nullptr;
   int64_t xd_cap = 0;  // records allocated in xd64/xd32
   int *err_flag = nullptr;
@@ -326,6 +327,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     sd.nbr = L->nbr;
     sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
     sd.K64 = L->K64;
+    sd.C64 = L->C64;
     sd.KT = P->fp64 ? (const void *)L->K64 : (const void *)L->K32;
     sd.xd64 = L->xd64;
     sd.xdT = P->fp64 ? (const void *)L->xd64 : (const void *)L->xd32;
@@ -543,14 +545,15 @@ ats_status plan_collect_events(Plan *P) {
 // of the vectors and coefficients (neighbour tables and records not counted).
 //   k_op, CG:        read z, p_old, K_T, D; write p_new, q            (6 words;
 //                    5 in the first iteration of an inner solve: p = z)
-//   k_ref:           read K64, x64, b64 (+ K_T when mixed); write z, D (24 B + 2-3 words)
+//   k_ref:           read x64, b64, the three FP64 face coefficients, K_T;
+//                    write z, D                                        (40 B + 3 words)
 //   k_upd, CG:       read p, q, D, z, e; write z, e                   (7 words)
 //   k_upd, x += e:   read/write x (FP64) and e (end of an inner solve) (16 B + 2 words)
 void plan_bytes(const Plan *P, const unsigned long long cells[kCellCounters], double *op_b, double *ref_b,
                 double *upd_b) {
   const double w = P->fp64 ? 8.0 : 4.0;
   *op_b = 6 * w * cells[0] + 5 * w * cells[4];  // first iteration of an inner solve: no p_old
-  *ref_b = (24 + (P->fp64 ? 0 : w) + 2 * w) * cells[1];
+  *ref_b = (40 + 3 * w) * cells[1];
   *upd_b = 7 * w * cells[2] + (16 + 2 * w) * cells[3];
 }
 
@@ -713,6 +716,7 @@ ats_status solve_dev_for(ats_level *L, const ats_solve_opts &o, bool fp64, int i
   sd.nbr = L->nbr;
   sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
   sd.K64 = L->K64;
+  sd.C64 = L->C64;
   sd.KT = fp64 ? (const void *)L->K64 : (const void *)L->K32;
   sd.xd64 = L->xd64;
   sd.xdT = fp64 ? (const void *)L->xd64 : (const void *)L->xd32;
@@ -920,7 +924,7 @@ ats_status ats_level_destroy(ats_level *L) {
   cudaStreamSynchronize(ctx->stream);
   if (L->solo) plan_free(L->solo);
   void *ptrs[] = {L->nbr, L->frec, L->rec_face, L->xrec_dense, L->leaf, L->fkind, L->frel,
-                  L->falpha, L->K64, L->xd64, L->b64, L->K32, L->xd32, L->err_flag,
+                  L->falpha, L->K64, L->xd64, L->b64, L->C64, L->K32, L->xd32, L->err_flag,
                   L->stage_cell, L->stage_face, L->x64, L->rhs_save,
                   L->e[0], L->z[0], L->p0[0], L->p1[0], L->e[1], L->z[1], L->p0[1], L->p1[1],
                   L->q[0], L->dg[0], L->q[1], L->dg[1]};
@@ -970,6 +974,7 @@ ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out)
     if ((s = dev_alloc_t(ctx, N, &L->K64)) != ATS_OK) return s;
     if ((s = dev_alloc_t(ctx, N, &L->K32)) != ATS_OK) return s;
     if ((s = dev_alloc_t(ctx, N, &L->b64)) != ATS_OK) return s;
+    if ((s = dev_alloc_t(ctx, 3 * N, &L->C64)) != ATS_OK) return s;
   }
   // diagonal extras: sparse records, or dense when a shift s is given
   const bool dense = (c->s != nullptr);
@@ -1053,6 +1058,8 @@ ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out)
   a.xd32 = L->xd32;
   a.b64 = L->b64;
   a.err_flag = L->err_flag;
+  a.nbr = L->nbr;
+  a.C64 = L->C64;
   L->dt = c->dt;
   L->built = true;
   return ATS_OK;
