@@ -126,7 +126,16 @@ typedef struct {
   int check_every;   /* ticks between host convergence polls (0 = 16)       */
   int use_graph;     /* 1 = capture the poll interval as a CUDA graph        */
   int mem;           /* ATS_MEM_HOST / ATS_MEM_DEVICE for x (and rhs)        */
+  int x0;            /* ATS_X0_*: where the initial guess comes from          */
 } ats_solve_opts;
+
+/* initial guess of a solve (ats_solve_opts.x0) */
+#define ATS_X0_GIVEN 0 /* x_inout holds the initial guess on entry (default) */
+#define ATS_X0_E_OLD 1 /* start from E^n given to the level's last operator  */
+                       /* build (the paper's initial guess, Sect. 3.3.4):     */
+                       /* x_inout is output only.  Device E^n arrays must be  */
+                       /* unchanged from the build to the end of the solve;   */
+                       /* host E^n is kept in the library's staging copy.     */
 
 typedef struct {
   int status;          /* ATS_OK or ATS_ERR_NOT_CONVERGED / _BREAKDOWN      */

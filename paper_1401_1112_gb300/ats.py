@@ -38,6 +38,7 @@ ATS_REL_SAME, ATS_REL_COARSER, ATS_REL_FINER = 0, 1, 2
 ATS_MEM_HOST, ATS_MEM_DEVICE = 0, 1
 ATS_STOP_RESIDUAL, ATS_STOP_CERTIFIED, ATS_STOP_PAPER = 0, 1, 2
 ATS_PREC_FP64, ATS_PREC_MIXED = 0, 1
+ATS_X0_GIVEN, ATS_X0_E_OLD = 0, 1
 
 P = ctypes.c_void_p
 
@@ -62,7 +63,7 @@ class ats_solve_opts(ctypes.Structure):
         ("tol", ctypes.c_double), ("stop_rule", ctypes.c_int), ("precision", ctypes.c_int),
         ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
         ("tile_octs", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
-        ("mem", ctypes.c_int),
+        ("mem", ctypes.c_int), ("x0", ctypes.c_int),
     ]
 
 
@@ -241,7 +242,8 @@ def _level_desc(level, keep):
 
 
 def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, max_iter=0, max_refine=0,
-              inner_rtol=0.0, tile_octs=0, check_every=0, use_graph=0, mem=ATS_MEM_HOST) -> ats_solve_opts:
+              inner_rtol=0.0, tile_octs=0, check_every=0, use_graph=0, mem=ATS_MEM_HOST,
+              x0=ATS_X0_GIVEN) -> ats_solve_opts:
     o = ats_solve_opts()
     lib().ats_default_opts(ctypes.byref(o))
     o.tol = tol
@@ -258,6 +260,7 @@ def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, m
         o.check_every = check_every
     o.use_graph = use_graph
     o.mem = mem
+    o.x0 = x0
     return o
 
 

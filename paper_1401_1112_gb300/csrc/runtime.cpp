@@ -67,6 +67,7 @@ struct ats_level {
   void *p0[2] = {nullptr, nullptr}, *p1[2] = {nullptr, nullptr};
   void *q[2] = {nullptr, nullptr}, *dg[2] = {nullptr, nullptr};
   double *rhs_save = nullptr;  // b when a solve overrides it
+  const double *E_dev = nullptr;  // device E^n of the last operator build (x0 = E^n)
   Plan *solo = nullptr;        // cached single-solve plan
 };
 
@@ -167,6 +168,7 @@ struct Plan {
   int *d_flags = nullptr;          // [n] gathered flags
   const double **d_src = nullptr;  // [n] device pointers for x copy-in (or null)
   double **d_dst = nullptr;        // [n] device pointers for x copy-out (or null)
+  double *d_xstage = nullptr;      // [sum N] host x staged on the device (host-memory solves)
   int *h_active = nullptr;         // pinned [2]: one per poll slot
   std::vector<SolveDev> h_solves;
   std::vector<SolveScalars> h_sc;
@@ -187,6 +189,11 @@ struct Plan {
 
 struct ats_batch {
   Plan *plan = nullptr;
+  // host inputs of the batched build, staged in one device buffer per kind
+  // (cell arrays K, E_old, s, src; face arrays K, E, F) so that runs of levels
+  // whose host arrays are contiguous cost one copy
+  double *stage_cell[4] = {nullptr, nullptr, nullptr, nullptr};
+  double *stage_face[3] = {nullptr, nullptr, nullptr};
   // batched operator build
   CoefArgs *d_args = nullptr;
   int64_t *d_cell_off = nullptr;
@@ -232,6 +239,29 @@ int choose_tile(int64_t n_oct, int requested) {
   return 8 * kThreads;
 }
 
+// Copy per-level host arrays into (h2d) or out of one device buffer at the
+// levels' offsets off[k]: levels whose host arrays follow each other in
+// memory form one run and cost one copy.  Levels with a null host pointer are
+// skipped.
+ats_status copy_runs(cudaStream_t st, bool h2d, double *dev, const int64_t *off, int n, double *const *host) {
+  int k = 0;
+  while (k < n) {
+    if (!host[k]) {
+      ++k;
+      continue;
+    }
+    int e = k + 1;
+    while (e < n && host[e] && host[e] == host[e - 1] + (off[e] - off[e - 1])) ++e;
+    const size_t bytes = sizeof(double) * (size_t)(off[e] - off[k]);
+    if (bytes) {
+      CUDA_TRY(h2d ? cudaMemcpyAsync(dev + off[k], host[k], bytes, cudaMemcpyHostToDevice, st)
+                   : cudaMemcpyAsync(host[k], dev + off[k], bytes, cudaMemcpyDeviceToHost, st));
+    }
+    k = e;
+  }
+  return ATS_OK;
+}
+
 ats_status ensure_vectors(ats_level *L, bool fp64) {
   const int k = fp64 ? 0 : 1;
   ats_context *ctx = L->ctx;
@@ -273,6 +303,7 @@ void plan_free(Plan *P) {
   dev_free(ctx, P->d_flags);
   dev_free(ctx, P->d_src);
   dev_free(ctx, P->d_dst);
+  dev_free(ctx, P->d_xstage);
   if (P->h_active) cudaFreeHost(P->h_active);
   delete P;
 }
@@ -291,6 +322,10 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   }
   if (o.stop_rule < 0 || o.stop_rule > 2) {
     set_error("bad stop_rule");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (o.x0 != ATS_X0_GIVEN && o.x0 != ATS_X0_E_OLD) {
+    set_error("bad x0");
     return ATS_ERR_INVALID_ARG;
   }
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -584,27 +619,40 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   }
   if (stale)
     CUDA_TRY(cudaMemcpyAsync(P->d_solves, P->h_solves.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice, st));
-  // copy-in of x
+  // copy-in of x: device x is read in place; host x goes through one staging
+  // buffer, one copy per run of levels whose host arrays are contiguous
   std::vector<const double *> src(n, nullptr);
   std::vector<double *> dst(n, nullptr);
+  std::vector<int64_t> off(n + 1, 0);
+  const bool x0_e = P->opts.x0 == ATS_X0_E_OLD;
   for (int k = 0; k < n; ++k) {
     if (!x_inout || !x_inout[k]) {
       set_error("x_inout[k] is NULL");
       return ATS_ERR_INVALID_ARG;
     }
-    if (dev) {
-      src[k] = x_inout[k];
-      dst[k] = x_inout[k];
-    } else {
-      CUDA_TRY(cudaMemcpyAsync(P->levels[k]->x64, x_inout[k], sizeof(double) * P->levels[k]->N,
-                               cudaMemcpyHostToDevice, st));
+    if (x0_e && !P->levels[k]->E_dev) {
+      set_error("x0 = E_old: the level has no operator build");
+      return ATS_ERR_INVALID_ARG;
+    }
+    off[k + 1] = off[k] + P->levels[k]->N;
+  }
+  if (!dev) {
+    if (!P->d_xstage) {
+      ats_status s2 = dev_alloc_t(ctx, std::max<int64_t>(1, off[n]), &P->d_xstage);
+      if (s2 != ATS_OK) return s2;
+    }
+    if (!x0_e) {
+      ats_status s2 = copy_runs(st, true, P->d_xstage, off.data(), n, x_inout);
+      if (s2 != ATS_OK) return s2;
     }
   }
-  if (dev) {
-    CUDA_TRY(cudaMemcpyAsync(P->d_src, src.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(P->d_dst, dst.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+  for (int k = 0; k < n; ++k) {
+    dst[k] = dev ? x_inout[k] : P->d_xstage + off[k];
+    src[k] = x0_e ? P->levels[k]->E_dev : dst[k];
   }
-  CUDA_TRY(launch_init(P->fp64, P->d_solves, P->d_items, P->n_items, dev ? P->d_src : nullptr, P->grid, st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_src, src.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_dst, dst.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(launch_init(P->fp64, P->d_solves, P->d_items, P->n_items, P->d_src, P->grid, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_sc, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_final, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, kCellCounters * sizeof(unsigned long long), st));
@@ -664,12 +712,10 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   }
   (void)pending;
   // copy-out
-  if (dev) {
-    CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->grid, st));
-  } else {
-    for (int k = 0; k < n; ++k)
-      CUDA_TRY(cudaMemcpyAsync(x_inout[k], P->levels[k]->x64, sizeof(double) * P->levels[k]->N,
-                               cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->grid, st));
+  if (!dev) {
+    ats_status s2 = copy_runs(st, false, P->d_xstage, off.data(), n, x_inout);
+    if (s2 != ATS_OK) return s2;
   }
   std::vector<SolveScalars> sc(n);
   CUDA_TRY(cudaMemcpyAsync(sc.data(), P->d_final, sizeof(SolveScalars) * n, cudaMemcpyDeviceToHost, st));
@@ -1060,6 +1106,7 @@ ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out)
   a.err_flag = L->err_flag;
   a.nbr = L->nbr;
   a.C64 = L->C64;
+  L->E_dev = E;
   L->dt = c->dt;
   L->built = true;
   return ATS_OK;
@@ -1200,6 +1247,8 @@ ats_status ats_batch_destroy(ats_batch *B) {
     cudaStreamSynchronize(ctx->stream);
     dev_free(ctx, B->d_args);
     dev_free(ctx, B->d_cell_off);
+    for (double *p : B->stage_cell) dev_free(ctx, p);
+    for (double *p : B->stage_face) dev_free(ctx, p);
     plan_free(B->plan);
   }
   delete B;
@@ -1224,15 +1273,48 @@ ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
   Plan *P = B->plan;
   ats_context *ctx = P->ctx;
   const int n = P->n;
-  std::vector<CoefArgs> args(n);
-  bool any_host = false;
-  for (int k = 0; k < n; ++k) {
-    ats_status s = prepare_operator(P->levels[k], &coefs[k], &args[k]);
-    if (s != ATS_OK) return s;
-    any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
-  }
   cudaStream_t st = ctx->stream;
   ats_status s;
+  std::vector<CoefArgs> args(n);
+  std::vector<ats_coef_desc> dc(coefs, coefs + n);
+  bool any_host = false;
+  for (int k = 0; k < n; ++k) any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
+  if (any_host) {
+    // host inputs: one staging buffer per array kind for the whole batch
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    std::vector<int64_t> oc(n + 1, 0), of(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+      oc[k + 1] = oc[k] + P->levels[k]->N;
+      of[k + 1] = of[k] + P->levels[k]->n_face;
+    }
+    const double *ats_coef_desc::*cell_kind[4] = {&ats_coef_desc::K, &ats_coef_desc::E_old, &ats_coef_desc::s,
+                                                  &ats_coef_desc::src};
+    const double *ats_coef_desc::*face_kind[3] = {&ats_coef_desc::face_K, &ats_coef_desc::face_E,
+                                                  &ats_coef_desc::face_F};
+    std::vector<double *> hp(n);
+    for (int q = 0; q < 7; ++q) {
+      const bool cell = q < 4;
+      const double *ats_coef_desc::*m = cell ? cell_kind[q] : face_kind[q - 4];
+      const std::vector<int64_t> &o = cell ? oc : of;
+      bool any = false;
+      for (int k = 0; k < n; ++k) {
+        const bool h = coefs[k].mem == ATS_MEM_HOST && coefs[k].*m && o[k + 1] > o[k];
+        hp[k] = h ? const_cast<double *>(coefs[k].*m) : nullptr;
+        any = any || h;
+      }
+      if (!any) continue;
+      double *&stage = cell ? B->stage_cell[q] : B->stage_face[q - 4];
+      if (!stage && (s = dev_alloc_t(ctx, std::max<int64_t>(1, o[n]), &stage)) != ATS_OK) return s;
+      if ((s = copy_runs(st, true, stage, o.data(), n, hp.data())) != ATS_OK) return s;
+      for (int k = 0; k < n; ++k)
+        if (hp[k]) dc[k].*m = stage + o[k];
+    }
+    for (int k = 0; k < n; ++k) dc[k].mem = ATS_MEM_DEVICE;
+  }
+  for (int k = 0; k < n; ++k) {
+    s = prepare_operator(P->levels[k], &dc[k], &args[k]);
+    if (s != ATS_OK) return s;
+  }
   if (!B->d_args) {
     if ((s = dev_alloc_t(ctx, n, &B->d_args)) != ATS_OK) return s;
     if ((s = dev_alloc_t(ctx, n + 1, &B->d_cell_off)) != ATS_OK) return s;

@@ -278,3 +278,82 @@ def test_batched_operator_build_matches_per_level(ats, ctx):
     B.close()
     for L in levels:
         L.close()
+
+
+def test_batched_host_inputs_from_one_buffer(ats, ctx):
+    """Host inputs given as views of one contiguous buffer per array kind, and
+    x as views of one buffer, are staged with one copy per contiguous run;
+    the batch results equal the per-level builds and solves bitwise."""
+    rng = np.random.default_rng(93)
+    solves = [W.random_box_solve(rng, o, robin=True) for o in (3, 50, 200, 8)]
+    n = len(solves)
+    off = np.concatenate([[0], np.cumsum([lv.n_cell for lv, _ in solves])])
+    foff = np.concatenate([[0], np.cumsum([lv.n_face for lv, _ in solves])])
+    def cat(key):
+        parts = [getattr(st, key) for _, st in solves]
+        return None if any(p is None for p in parts) else np.concatenate(parts)
+
+    Kb, Eb = cat("K"), cat("E")
+    fKb, fEb, fFb = cat("face_K"), cat("face_E"), cat("face_F")
+
+    def fview(a, k):
+        return a[foff[k]:foff[k + 1]] if a is not None and foff[k + 1] > foff[k] else None
+
+    levels = [ats.Level(ctx, lv) for lv, _ in solves]
+    for L, (lv, st) in zip(levels, solves):  # plan needs built operators
+        L.build(st.dt, st.K, st.E, **_faces(st))
+    B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                  mem=ats.ATS_MEM_HOST, use_graph=1)
+    coefs = B.prepare_coefs([dict(dt=solves[k][1].dt, K=Kb[off[k]:off[k + 1]], E_old=Eb[off[k]:off[k + 1]],
+                                  face_K=fview(fKb, k), face_E=fview(fEb, k), face_F=fview(fFb, k))
+                             for k in range(n)])
+    B.build_operators(coefs)
+    xb = Eb.copy()
+    code, stats = B.solve([xb[off[k]:off[k + 1]] for k in range(n)])
+    assert code == 0, stats
+    for k, ((lv, st), L) in enumerate(zip(solves, levels)):
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        x = st.E.copy()
+        code, _ = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED)
+        assert code == 0
+        np.testing.assert_array_equal(x, xb[off[k]:off[k + 1]])
+        _, xr = _oracle_solution(lv, st)
+        assert _rel(x, xr) <= PAR
+    B.close()
+    for L in levels:
+        L.close()
+
+
+@pytest.mark.parametrize("mem", ["host", "device"])
+def test_initial_guess_from_build(ats, ctx, mem):
+    """x0 = E^n of the last operator build (ATS_X0_E_OLD) gives bitwise the
+    result of passing x = E^n as the initial guess."""
+    import torch
+
+    rng = np.random.default_rng(95)
+    solves = [W.random_box_solve(rng, o, robin=True) for o in (4, 70, 9)]
+    levels = [ats.Level(ctx, lv) for lv, _ in solves]
+    dev = torch.device("cuda:0")
+    conv = (lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)) if mem == "device" \
+        else (lambda a: a)
+    M = ats.ATS_MEM_DEVICE if mem == "device" else ats.ATS_MEM_HOST
+    coefs = [dict(dt=st.dt, K=conv(st.K), E_old=conv(st.E), face_K=conv(st.face_K), face_E=conv(st.face_E),
+                  face_F=conv(st.face_F)) for _, st in solves]
+    for L, c in zip(levels, coefs):
+        L.build(**c)
+    torch.cuda.synchronize()
+    outs = []
+    for x0 in (ats.ATS_X0_GIVEN, ats.ATS_X0_E_OLD):
+        B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                      mem=M, use_graph=1, x0=x0)
+        prepared = B.prepare_coefs(coefs)
+        B.build_operators(prepared)
+        xs = [conv(st.E.copy()) if x0 == ats.ATS_X0_GIVEN else conv(np.full(lv.n_cell, np.nan)) for lv, st in solves]
+        code, stats = B.solve(xs)
+        assert code == 0, stats
+        outs.append([x.cpu().numpy() if mem == "device" else x for x in xs])
+        B.close()
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+    for L in levels:
+        L.close()
