@@ -120,13 +120,14 @@ struct CoefArgs {
   const int32_t *nbr;   // for the face coefficients
   double *C64;          // [n_oct][3][8] written by the face-coefficient pass
 };
-// K, diagonal extras and b, then the FP64 face coefficients C64 (a second
-// pass, once K64 is complete).
+// K, diagonal extras, b and the FP64 face coefficients C64, one thread per cell.
 cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st);
-// One launch for many levels (args, cell_off: device arrays, n levels) after
-// zeroing the levels' error flags (flags: device array of device pointers).
-cudaError_t launch_coef_build_batch(const CoefArgs *args, const int64_t *cell_off, int n, int64_t total_cells,
-                                    int *const *flags, cudaStream_t st);
+// One launch for many levels after zeroing the levels' error flags (flags:
+// device array of device pointers): block b of kCoefThreads threads builds
+// cells of level blk_level[b], starting at (b - blk_first[level]) * kCoefThreads.
+constexpr int kCoefThreads = 256;
+cudaError_t launch_coef_build_batch(const CoefArgs *args, const int32_t *blk_level, const int32_t *blk_first,
+                                    int n_blocks, int n, int *const *flags, cudaStream_t st);
 // FP64 face coefficients C64[(3 o + a) 8 + c] = h (K_i + K_j) between cell i =
 // 8 o + c and its +a neighbour j when both are leaves (K >= 0), else 0.
 cudaError_t launch_face_coef(int64_t n_oct, const int32_t *nbr, const double *K64, double h, double *C64,

@@ -928,6 +928,28 @@ __global__ void __launch_bounds__(kThreads, MinBlocksUpd<T>::value) k_upd(TickAr
 // coefficient build (one thread per cell)
 // ---------------------------------------------------------------------------
 
+// FP64 coefficients of the +x, +y, +z faces of leaf cell i = 8 o + c from the
+// input K (the same values the face-coefficient pass derives from K64):
+// h (K_i + K_j) when the +a neighbour j (in-oct partner, or the facing cell
+// of the +a neighbour oct) is a leaf, else 0.
+__device__ __forceinline__ void coef_faces(const CoefArgs &a, int64_t o, int c, bool leaf, double K) {
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int bit = 1 << ax;
+    int64_t oj = -1;
+    int cj = c ^ bit;
+    if (!(c & bit)) {
+      oj = o;
+    } else {
+      const int n = a.nbr[6 * o + 2 * ax + 1];
+      if (n >= 0) oj = n;
+    }
+    double C = 0.0;
+    if (leaf && oj >= 0 && (!a.leaf || ((a.leaf[oj] >> cj) & 1))) C = a.h * (K + a.K[8 * oj + cj]);
+    a.C64[(3 * o + ax) * 8 + c] = C;
+  }
+}
+
 __device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
   const int64_t o = i >> 3;
   const int c = (int)(i & 7);
@@ -937,6 +959,7 @@ __device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
     a.K64[i] = -1.0;
     a.K32[i] = -1.0f;
     a.b64[i] = 0.0;
+    coef_faces(a, o, c, false, 0.0);
     if (xr >= 0) {
       a.xd64[(int64_t)xr * 8 + c] = 0.0;
       a.xd32[(int64_t)xr * 8 + c] = 0.0f;
@@ -944,6 +967,7 @@ __device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
     return;
   }
   const double K = a.K[i];
+  coef_faces(a, o, c, true, K);
   const double E = a.E_old[i];
   bool ok = (K > 0.0) && isfinite(K) && isfinite(E);
   double xd = a.s ? a.s[i] : 0.0;
@@ -989,19 +1013,14 @@ __global__ void k_coef_build(CoefArgs a) {
   coef_cell(a, i);
 }
 
-// All levels of a batch in one launch: cell g belongs to the level k with
-// cell_off[k] <= g < cell_off[k + 1].
-__global__ void k_coef_build_batch(const CoefArgs *__restrict__ args, const int64_t *__restrict__ cell_off,
-                                   int n) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= cell_off[n]) return;
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (cell_off[mid] <= g) lo = mid;
-    else hi = mid - 1;
-  }
-  coef_cell(args[lo], g - cell_off[lo]);
+// All levels of a batch in one launch: block b belongs to level
+// blk_level[b] and covers its cells from (b - blk_first[level]) * blockDim.
+__global__ void k_coef_build_batch(const CoefArgs *__restrict__ args, const int32_t *__restrict__ blk_level,
+                                   const int32_t *__restrict__ blk_first) {
+  const int k = blk_level[blockIdx.x];
+  const CoefArgs &a = args[k];
+  const int64_t i = (int64_t)(blockIdx.x - blk_first[k]) * blockDim.x + threadIdx.x;
+  if (i < 8 * a.n_oct) coef_cell(a, i);
 }
 
 // The FP64 face coefficients of cell i = 8 o + c: for each axis a, the face
@@ -1037,19 +1056,6 @@ __global__ void k_face_coef(int64_t n_oct, const int32_t *__restrict__ nbr, cons
   if (i < 8 * n_oct) face_coef_cell(nbr, K64, h, C64, i);
 }
 
-__global__ void k_face_coef_batch(const CoefArgs *__restrict__ args, const int64_t *__restrict__ cell_off, int n) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= cell_off[n]) return;
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (cell_off[mid] <= g) lo = mid;
-    else hi = mid - 1;
-  }
-  const CoefArgs &a = args[lo];
-  face_coef_cell(a.nbr, a.K64, a.h, a.C64, g - cell_off[lo]);
-}
-
 __global__ void k_zero_flags(int *const *__restrict__ flags, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) *flags[k] = 0;
@@ -1060,14 +1066,12 @@ __global__ void k_gather_flags(const int *const *__restrict__ flags, int n, int 
   if (k < n) out[k] = *flags[k];
 }
 
-cudaError_t launch_coef_build_batch(const CoefArgs *args, const int64_t *cell_off, int n, int64_t total_cells,
-                                    int *const *flags, cudaStream_t st) {
+cudaError_t launch_coef_build_batch(const CoefArgs *args, const int32_t *blk_level, const int32_t *blk_first,
+                                    int n_blocks, int n, int *const *flags, cudaStream_t st) {
   k_zero_flags<<<(n + 255) / 256, 256, 0, st>>>(flags, n);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || total_cells == 0) return e;
-  k_coef_build_batch<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(args, cell_off, n);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_face_coef_batch<<<(unsigned)((total_cells + 255) / 256), 256, 0, st>>>(args, cell_off, n);
+  if (e != cudaSuccess || n_blocks == 0) return e;
+  k_coef_build_batch<<<(unsigned)n_blocks, kCoefThreads, 0, st>>>(args, blk_level, blk_first);
   return cudaGetLastError();
 }
 
@@ -1089,9 +1093,7 @@ cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st) {
   const int threads = 256;
   const int64_t blocks = (N + threads - 1) / threads;
   k_coef_build<<<(unsigned)blocks, threads, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_face_coef(a.n_oct, a.nbr, a.K64, a.h, a.C64, st);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

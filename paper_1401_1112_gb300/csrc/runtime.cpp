@@ -196,9 +196,10 @@ struct ats_batch {
   double *stage_face[3] = {nullptr, nullptr, nullptr};
   // batched operator build
   CoefArgs *d_args = nullptr;
-  int64_t *d_cell_off = nullptr;
+  int32_t *d_blk_level = nullptr;  // batched build: level of each block
+  int32_t *d_blk_first = nullptr;  // [n + 1] first block of each level
+  int n_blocks = 0;
   std::vector<CoefArgs> h_args;  // last uploaded arguments
-  int64_t total_cells = 0;
 };
 
 namespace {
@@ -1246,7 +1247,8 @@ ats_status ats_batch_destroy(ats_batch *B) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     dev_free(ctx, B->d_args);
-    dev_free(ctx, B->d_cell_off);
+    dev_free(ctx, B->d_blk_level);
+    dev_free(ctx, B->d_blk_first);
     for (double *p : B->stage_cell) dev_free(ctx, p);
     for (double *p : B->stage_face) dev_free(ctx, p);
     plan_free(B->plan);
@@ -1317,11 +1319,19 @@ ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
   }
   if (!B->d_args) {
     if ((s = dev_alloc_t(ctx, n, &B->d_args)) != ATS_OK) return s;
-    if ((s = dev_alloc_t(ctx, n + 1, &B->d_cell_off)) != ATS_OK) return s;
-    std::vector<int64_t> off(n + 1, 0);
-    for (int k = 0; k < n; ++k) off[k + 1] = off[k] + P->levels[k]->N;
-    B->total_cells = off[n];
-    CUDA_TRY(cudaMemcpyAsync(B->d_cell_off, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> first(n + 1, 0), level;
+    for (int k = 0; k < n; ++k) {
+      const int64_t nb = (P->levels[k]->N + kCoefThreads - 1) / kCoefThreads;
+      first[k + 1] = first[k] + (int32_t)nb;
+      for (int64_t b = 0; b < nb; ++b) level.push_back(k);
+    }
+    B->n_blocks = first[n];
+    if ((s = dev_alloc_t(ctx, n + 1, &B->d_blk_first)) != ATS_OK) return s;
+    if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, B->n_blocks), &B->d_blk_level)) != ATS_OK) return s;
+    CUDA_TRY(cudaMemcpyAsync(B->d_blk_first, first.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    if (B->n_blocks)
+      CUDA_TRY(cudaMemcpyAsync(B->d_blk_level, level.data(), sizeof(int32_t) * B->n_blocks, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));  // the host tables go out of scope
   }
   // upload the per-level arguments only when they changed (same buffers and
   // dt from step to step is the common case)
@@ -1329,7 +1339,7 @@ ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
     B->h_args = args;
     CUDA_TRY(cudaMemcpyAsync(B->d_args, B->h_args.data(), sizeof(CoefArgs) * n, cudaMemcpyHostToDevice, st));
   }
-  CUDA_TRY(launch_coef_build_batch(B->d_args, B->d_cell_off, n, B->total_cells, P->d_flag_ptrs, st));
+  CUDA_TRY(launch_coef_build_batch(B->d_args, B->d_blk_level, B->d_blk_first, B->n_blocks, n, P->d_flag_ptrs, st));
   if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
   return ATS_OK;
 }
