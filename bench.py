@@ -267,6 +267,7 @@ def run_ours(args, rank, world, local):
     batch.set_profiling(False)
     value = n * args.steps * world / (ms / 1e3)
     iters = [s["iterations"] for s in stats]
+    cell_its = int(sum(int(s["iterations"]) * int(sz) for s, sz in zip(stats, sizes)))  # per step
     refs = [s["refinements"] for s in stats]
     bounds = [s["res_norm"] / s["r0_norm"] if s["r0_norm"] > 0 else 0.0 for s in stats]
 
@@ -285,6 +286,11 @@ def run_ours(args, rank, world, local):
         "frac": round(achieved / peak, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
         "traffic": _traffic_for(dom, dbytes / max(1, acc["ticks"])),
         "launches": int(acc["ticks"]), "bytes_per_launch": round(dbytes / max(1, acc["ticks"])),
+        # the whole step on the minimal Jacobi-PCG traffic: 10 words per cell
+        # and CG iteration (read p, K, x, r, q, D^-1; write q, x, r, p)
+        "cg_step": {"cell_iterations": cell_its, "bytes_per_cell_iteration": 10 * 4,
+                    "achieved": round(cell_its * 40.0 / (ms / args.steps / 1e3) / 1e9, 1),
+                    "frac": round(cell_its * 40.0 / (ms / args.steps / 1e3) / 1e9 / peak, 4)},
         "per_kernel": {k: {"ms": round(acc[a], 3),
                            "GBps": round(acc[b] / (acc[a] / 1e3) / 1e9, 1) if acc[a] else None,
                            "bound": "fp64 alu, concurrent with k_op" if k.startswith("k_ref") else "hbm"}
