@@ -15,12 +15,24 @@ coordinates with Python dictionaries; it shares nothing with the library.
 The "coarse first" order (the two-level workload's reading) solves the
 coarse level first and gives the fine substeps the coarse value linear in
 time, E_c^n + (k/2)(E_c^{n+1} - E_c^n) at the end of fine substep k.
+
+Energy-conserving interfaces (Sect. 3.3.1 - 3.3.2, fine first only): at the
+end of every fine update the energy that crossed each fine-to-coarse face is
+stored (its time integral over the fine steps, which is the Delta t-weighted
+mean flux of Eq. mean_flux times the coarse step).  The coarse level's
+coarse-to-fine faces then take either the Dirichlet row (the restriction,
+as above), the Neumann row with that stored energy as the imposed flux F
+(energy conserved exactly), or the Robin row with weight alpha between the
+two.  In the units of the level system (energy per unit cell volume over the
+step, the reading of the Neumann sign), a fine face f next to coarse cell c
+moves C_f (E_f^{k} - E_c) V_f / V_c = C_f (E_f^k - E_c) / 8 into c during
+fine step k, with C_f = (2/3) dt_f/(2 dx_f^2) (K_f + K_c).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import DIRICHLET, REL_COARSER, REL_FINER, STOP_CERTIFIED, assemble, pcg
+from . import DIRICHLET, NEUMANN, REL_COARSER, REL_FINER, ROBIN, STOP_CERTIFIED, assemble, pcg
 from . import fld as fldmod
 
 AX = (0, 0, 1, 1, 2, 2)
@@ -42,10 +54,18 @@ class _Level:
 
 
 class Hierarchy:
-    def __init__(self, levels, states, order="fine_first", fld=None):
+    def __init__(self, levels, states, order="fine_first", fld=None, interface="dirichlet", alpha=1.0):
         """states: per level (E, K).  fld: None, or (per-level rho, per-level T,
         k0) for the radiation-matter mode (K, s, src from the gas state before
-        every level solve, T updated after it)."""
+        every level solve, T updated after it).  interface: the row of the
+        coarse-to-fine faces, "dirichlet", "neumann" (stored flux) or "robin"
+        (weight alpha on the Dirichlet part)."""
+        if interface not in ("dirichlet", "neumann", "robin"):
+            raise ValueError(interface)
+        if interface != "dirichlet" and order != "fine_first":
+            raise ValueError("stored interface fluxes need the fine-first order")
+        self.interface = interface
+        self.alpha = {"dirichlet": 1.0, "neumann": 0.0, "robin": float(alpha)}[interface]
         self.L = [_Level(d) for d in levels]
         self.E = [np.array(e, dtype=np.float64) for e, _ in states]
         self.K = [np.array(k, dtype=np.float64) for _, k in states]
@@ -61,6 +81,21 @@ class Hierarchy:
         self.order = order
         self.faces = [self._faces(l) for l in range(len(levels))]
         self.iterations = 0
+        # stored interface energy per coarse-to-fine face of each level (energy
+        # per unit volume of the coarse cell), and where each fine-to-coarse
+        # face of the level below sends its energy
+        self.store = [np.zeros(len(f)) for f in self.faces]
+        self.send = []
+        for l in range(len(levels)):
+            if l == 0:
+                self.send.append({})
+                continue
+            index = {(cell, d): k for k, (cell, d, rel, _) in enumerate(self.faces[l - 1]) if rel == REL_FINER}
+            self.send.append({k: index[(jc, d ^ 1)] for k, (_, d, rel, jc) in enumerate(self.faces[l])
+                              if rel == REL_COARSER})
+        # per level solve: (level, energy its leaves gained through their
+        # coarse-to-fine faces, stored fine-side energy the solve consumed)
+        self.audit = []
 
     def _faces(self, l):
         """(cell, dir, rel, src) of every interface face of level l."""
@@ -134,12 +169,36 @@ class Hierarchy:
         lv.face_cell, lv.face_dir, lv.face_rel = fcell, fdir, frel
         lv.face_kind = np.full(len(f), DIRICHLET, dtype=np.int8)
         lv.face_alpha = np.ones(len(f))
+        fF = np.zeros(len(f))
+        if self.interface != "dirichlet":
+            fine_side = frel == REL_FINER
+            lv.face_kind[fine_side] = NEUMANN if self.interface == "neumann" else ROBIN
+            lv.face_alpha[fine_side] = self.alpha
+            fF[fine_side] = self.store[l][fine_side]
         self.E_prev[l] = self.E[l].copy()
-        S = assemble(lv, dt, self.K[l], self.E[l], s=s_shift, src=src, face_K=fK, face_E=fE)
+        S = assemble(lv, dt, self.K[l], self.E[l], s=s_shift, src=src, face_K=fK, face_E=fE, face_F=fF)
         x, info = pcg(S, self.E[l], tol=tol, stop_rule=STOP_CERTIFIED)
         assert info["status"] == 0, info
         self.iterations += info["iterations"]
         self.E[l] = x
+        # energy (per unit coarse volume) this level's coarse-to-fine faces gave
+        # its leaves, by the face rows of Sect. 3.2: Dirichlet alpha C (E_nb - x),
+        # Neumann / Robin (1 - alpha) F on top
+        h = dt / (2.0 * desc.dx * desc.dx)
+        gained = 0.0
+        for k, (cell, _, rel, _) in enumerate(f):
+            if rel != REL_FINER:
+                continue
+            C = h * (self.K[l][cell] + fK[k])
+            gained += self.alpha * C * (fE[k] - x[cell]) + (1.0 - self.alpha) * fF[k]
+        consumed = float(np.sum(self.store[l])) * desc.dx ** 3
+        self.audit.append((l, gained * desc.dx ** 3, consumed))
+        self.store[l][:] = 0.0
+        # energy this level's fine-to-coarse faces took from the coarser cells
+        for k, kc in self.send[l].items():
+            cell = f[k][0]
+            C = (2.0 / 3.0) * h * (self.K[l][cell] + fK[k])
+            self.store[l - 1][kc] += C * (x[cell] - fE[k]) / 8.0
         if self.fld is not None:
             leaf = desc.leaf_cells()
             Tn = fldmod.update_temperature(self.fld[0][l], self.fld[1][l], x, dt, self.fld[2])
@@ -158,6 +217,15 @@ class Hierarchy:
                 self.advance(l + 1, dt / 2, tol, theta=0.5)
                 self.advance(l + 1, dt / 2, tol, theta=1.0)
                 self.restrict(l)
+
+    def energy(self):
+        """Total energy: E times the cell volume over the leaf cells of every
+        level."""
+        tot = 0.0
+        for lev, E in zip(self.L, self.E):
+            leaf = lev.desc.leaf_cells()
+            tot += float(np.sum(E[leaf])) * lev.desc.dx ** 3
+        return tot
 
     def state(self, l):
         for k in range(len(self.L) - 2, l - 1, -1):
