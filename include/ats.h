@@ -238,6 +238,24 @@ typedef struct {
 } ats_hierarchy_desc;
 ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc, ats_hierarchy **out);
 ats_status ats_hierarchy_destroy(ats_hierarchy *h);
+/* Row of the coarse-to-fine faces (Sect. 3.3.1 - 3.3.2).  After every solve
+ * of a level, the energy its fine-to-coarse faces moved into the coarser
+ * cells is stored per coarse-to-fine face of the coarser level (energy per
+ * unit coarse-cell volume, C (E_fine - E_coarse) / 8 with the 2/3 factor of
+ * Sect. 3.3.1, summed over the fine steps: the Delta t-weighted mean flux of
+ * Eq. mean_flux times the coarse step).  The coarser level's next solve uses
+ * it and clears it:
+ *   ATS_FACE_DIRICHLET  the restriction of the refined cell (default; the
+ *                       stored energy is not used);
+ *   ATS_FACE_NEUMANN    the stored energy as the imposed flux F: the total
+ *                       energy of a closed hierarchy is conserved;
+ *   ATS_FACE_ROBIN      alpha (Dirichlet part) + (1 - alpha) stored flux,
+ *                       alpha in [0, 1].
+ * Fine-to-coarse faces stay Dirichlet with the coarse value held at E^n.
+ * Neumann and Robin need ATS_ORDER_FINE_FIRST (the stored energy must exist
+ * before the coarse solve); ATS_ERR_INVALID_ARG otherwise or for a bad kind
+ * or alpha.  Clears the stores. */
+ats_status ats_hierarchy_set_interface(ats_hierarchy *h, int kind, double alpha);
 /* The ats_level of one hierarchy level (owned by the hierarchy). */
 ats_status ats_hierarchy_level(ats_hierarchy *h, int level, ats_level **out);
 /* Set E and K ([N] of that level, host or device per mem); E is E^n. */

@@ -138,6 +138,7 @@ _SIGS = [
     ("ats_layout_neighbors", ctypes.c_int, [ctypes.POINTER(ats_level_desc), P]),
     ("ats_hierarchy_create", ctypes.c_int, [P, ctypes.POINTER(ats_hierarchy_desc), ctypes.POINTER(P)]),
     ("ats_hierarchy_destroy", ctypes.c_int, [P]),
+    ("ats_hierarchy_set_interface", ctypes.c_int, [P, ctypes.c_int, ctypes.c_double]),
     ("ats_hierarchy_level", ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(P)]),
     ("ats_hierarchy_set_state", ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int]),
     ("ats_hierarchy_get_state", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
@@ -472,6 +473,10 @@ def ats_hierarchy_destroy(h):
     return _check(lib().ats_hierarchy_destroy(h), "ats_hierarchy_destroy")
 
 
+def ats_hierarchy_set_interface(h, kind, alpha=1.0):
+    return _check(lib().ats_hierarchy_set_interface(h, int(kind), float(alpha)), "ats_hierarchy_set_interface")
+
+
 def ats_hierarchy_level(h, level):
     out = P()
     _check(lib().ats_hierarchy_level(h, level, ctypes.byref(out)), "ats_hierarchy_level")
@@ -652,6 +657,11 @@ class Hierarchy:
 
     def set_fld(self, level, rho, T, k0):
         ats_hierarchy_set_fld(self.handle, level, rho, T, k0)
+
+    def set_interface(self, kind, alpha=1.0):
+        """Row of the coarse-to-fine faces: ATS_FACE_DIRICHLET (restriction),
+        ATS_FACE_NEUMANN (stored fine-side flux) or ATS_FACE_ROBIN (alpha)."""
+        ats_hierarchy_set_interface(self.handle, kind, alpha)
 
     def temperature(self, level):
         out = np.empty(self.levels[level].n_cell)

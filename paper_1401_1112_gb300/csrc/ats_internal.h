@@ -222,6 +222,16 @@ const int32_t *level_nbr(const ats_level *L);
 const uint8_t *level_leaf(const ats_level *L);
 
 // AMR coupling kernels (restriction of children, ghost gather of interface faces).
+// Stored interface energy (Sect. 3.3.2): for each face f of the coarse level
+// with fine faces gather4[4 f .. 4 f + 3] (fine-to-coarse faces of the finer
+// level, -1 = none), store[f] += sum_g C_g (x[fcell[g]] - fE[g]) / 8 with
+// C_g = (2/3) h_f (K[fcell[g]] + fK[g]) -- the energy per unit coarse-cell
+// volume the fine solve just moved into the coarse cell.
+cudaError_t launch_flux_store(int n_face, const int32_t *gather4, const int32_t *fcell, const double *x,
+                              const double *K, const double *fK, const double *fE, double h_f, double *store,
+                              cudaStream_t st);
+// Replace the face rows (kind, alpha: host arrays of the level's n_face).
+ats_status level_set_face_rows(ats_level *L, const int8_t *kind, const double *alpha);
 cudaError_t launch_restrict(int n, const int32_t *cell, const int32_t *child, const double *Ef, const double *Kf,
                             double *Ec, double *Kc, cudaStream_t st);
 cudaError_t launch_gather_faces(int n_face, const int8_t *src_rel, const int32_t *src_cell, const double *E_same,

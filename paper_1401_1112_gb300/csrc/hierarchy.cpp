@@ -134,6 +134,12 @@ struct HLevel {
   double *E = nullptr, *E_prev = nullptr, *K = nullptr, *fE = nullptr, *fK = nullptr;
   int8_t *src_rel = nullptr;  // 0 same level (FINER), 1 coarser
   int32_t *src_cell = nullptr, *r_cell = nullptr, *r_child = nullptr;
+  // stored interface energy (Sect. 3.3.2): per face of this level, and for
+  // each coarse-to-fine face the (up to 4) fine-to-coarse faces of the next
+  // level that feed it
+  int32_t *fcell = nullptr, *gather4 = nullptr;
+  double *fstore = nullptr;
+  std::vector<int8_t> rel;  // host copy of the face relations
 };
 
 struct ats_hierarchy {
@@ -141,6 +147,8 @@ struct ats_hierarchy {
   int order = ATS_ORDER_FINE_FIRST;
   bool fld = false;  // K, s and src from the gas state before every level solve
   double k0 = 0.0;
+  int iface_kind = ATS_FACE_DIRICHLET;  // row of the coarse-to-fine faces
+  double iface_alpha = 1.0;
   std::vector<HLevel> lv;
 };
 
@@ -157,7 +165,8 @@ namespace {
 
 void hierarchy_free(ats_hierarchy *H) {
   for (HLevel &h : H->lv) {
-    void *ptrs[] = {h.E, h.E_prev, h.K, h.fE, h.fK, h.src_rel, h.src_cell, h.r_cell, h.r_child, h.rho, h.T, h.s, h.src};
+    void *ptrs[] = {h.E,  h.E_prev, h.K,   h.fE, h.fK, h.src_rel, h.src_cell, h.r_cell, h.r_child,
+                    h.rho, h.T,     h.s,   h.src, h.fcell, h.gather4, h.fstore};
     for (void *p : ptrs) ctx_free(H->ctx, p);
     if (h.lvl) ats_level_destroy(h.lvl);
   }
@@ -202,6 +211,8 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   c.E_old = h.E_prev;
   c.face_K = h.n_face ? h.fK : nullptr;
   c.face_E = h.n_face ? h.fE : nullptr;
+  const bool stored = H->iface_kind != ATS_FACE_DIRICHLET;
+  if (stored && h.n_face) c.face_F = h.fstore;  // the fine-side energy of the finer level's steps
   if (H->fld) {
     c.s = h.s;
     c.src = h.src;
@@ -215,6 +226,12 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   std::memset(&st1, 0, sizeof(st1));
   s = ats_solve(h.lvl, nullptr, h.E, &o, &st1);
   if (s == ATS_OK && H->fld) H_TRY(launch_fld_temperature(h.N, level_leaf(h.lvl), h.E, h.rho, h.T, dt, H->k0, st));
+  if (s == ATS_OK && stored) {
+    if (h.n_face) H_TRY(cudaMemsetAsync(h.fstore, 0, sizeof(double) * h.n_face, st));
+    if (coarse && coarse->n_face)  // this step's fine-to-coarse energy, for the coarser level's next solve
+      H_TRY(launch_flux_store((int)coarse->n_face, coarse->gather4, h.fcell, h.E, h.K, h.fK, h.fE,
+                              0.5 * dt / (h.dx * h.dx), H->lv[l - 1].fstore, st));
+  }
   if (acc) {
     acc->iterations += st1.iterations;
     acc->refinements += st1.refinements;
@@ -299,14 +316,17 @@ ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc
   H->order = desc->order;
   H->lv.resize(desc->n_levels);
   cudaStream_t st = ctx_stream(ctx);
+  std::vector<LevelFaces> lfs(desc->n_levels);
   for (int l = 0; l < desc->n_levels; ++l) {
-    LevelFaces lf;
-    std::string msg = plan_level_faces(desc->levels, desc->n_levels, l, lf);
+    std::string msg = plan_level_faces(desc->levels, desc->n_levels, l, lfs[l]);
     if (!msg.empty()) {
       set_error(msg);
       hierarchy_free(H);
       return ATS_ERR_INVALID_ARG;
     }
+  }
+  for (int l = 0; l < desc->n_levels; ++l) {
+    const LevelFaces &lf = lfs[l];
     HLevel &h = H->lv[l];
     ats_level_desc d = desc->levels[l];
     const int64_t nf = (int64_t)lf.cell.size();
@@ -341,9 +361,33 @@ ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc
         (s = alloc(sizeof(int8_t) * nf, (void **)&h.src_rel)) != ATS_OK ||
         (s = alloc(sizeof(int32_t) * nf, (void **)&h.src_cell)) != ATS_OK ||
         (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_cell)) != ATS_OK ||
-        (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_child)) != ATS_OK) {
+        (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_child)) != ATS_OK ||
+        (s = alloc(sizeof(int32_t) * nf, (void **)&h.fcell)) != ATS_OK ||
+        (s = alloc(sizeof(int32_t) * 4 * nf, (void **)&h.gather4)) != ATS_OK ||
+        (s = alloc(sizeof(double) * nf, (void **)&h.fstore)) != ATS_OK) {
       hierarchy_free(H);
       return s;
+    }
+    h.rel = lf.rel;
+    // coarse-to-fine face (cell, dir) of this level <- the fine-to-coarse faces
+    // of the next level whose coarse cell and opposite direction match
+    std::vector<int32_t> g4(4 * nf, -1);
+    if (l + 1 < desc->n_levels) {
+      std::unordered_map<int64_t, int64_t> at;
+      for (int64_t f = 0; f < nf; ++f)
+        if (lf.rel[f] == ATS_REL_FINER) at[6 * (int64_t)lf.cell[f] + lf.dir[f]] = f;
+      const LevelFaces &ff = lfs[l + 1];
+      for (size_t g = 0; g < ff.cell.size(); ++g) {
+        if (ff.rel[g] != ATS_REL_COARSER) continue;
+        auto it = at.find(6 * (int64_t)ff.src_cell[g] + (ff.dir[g] ^ 1));
+        if (it == at.end()) continue;
+        int32_t *slot = &g4[4 * it->second];
+        for (int k = 0; k < 4; ++k)
+          if (slot[k] < 0) {
+            slot[k] = (int32_t)g;
+            break;
+          }
+      }
     }
     std::vector<int8_t> srel(nf);
     for (int64_t f = 0; f < nf; ++f) srel[f] = lf.rel[f] == ATS_REL_COARSER ? 1 : 0;
@@ -351,6 +395,9 @@ ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc
     if (nf) {
       e = cudaMemcpyAsync(h.src_rel, srel.data(), nf, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(h.src_cell, lf.src_cell.data(), 4 * nf, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h.fcell, lf.cell.data(), 4 * nf, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h.gather4, g4.data(), 16 * nf, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h.fstore, 0, sizeof(double) * nf, st);
     }
     if (e == cudaSuccess && h.n_restrict) {
       e = cudaMemcpyAsync(h.r_cell, lf.restrict_cell.data(), 4 * h.n_restrict, cudaMemcpyHostToDevice, st);
@@ -365,6 +412,40 @@ ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc
     }
   }
   *out = H;
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_set_interface(ats_hierarchy *H, int kind, double alpha) {
+  if (!H) return ATS_ERR_INVALID_ARG;
+  if (kind != ATS_FACE_DIRICHLET && kind != ATS_FACE_NEUMANN && kind != ATS_FACE_ROBIN) {
+    set_error("bad interface kind");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (kind == ATS_FACE_ROBIN && !(alpha >= 0.0 && alpha <= 1.0)) {
+    set_error("Robin alpha must be in [0, 1]");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (kind != ATS_FACE_DIRICHLET && H->order != ATS_ORDER_FINE_FIRST) {
+    set_error("stored interface fluxes need the fine-first order");
+    return ATS_ERR_INVALID_ARG;
+  }
+  const double a = kind == ATS_FACE_DIRICHLET ? 1.0 : (kind == ATS_FACE_NEUMANN ? 0.0 : alpha);
+  cudaStream_t st = ctx_stream(H->ctx);
+  for (HLevel &h : H->lv) {
+    std::vector<int8_t> k(h.n_face, ATS_FACE_DIRICHLET);
+    std::vector<double> al(h.n_face, 1.0);
+    for (int64_t f = 0; f < h.n_face; ++f)
+      if (h.rel[f] == ATS_REL_FINER) {
+        k[f] = (int8_t)kind;
+        al[f] = a;
+      }
+    ats_status s = level_set_face_rows(h.lvl, k.data(), al.data());
+    if (s != ATS_OK) return s;
+    if (h.n_face) H_TRY(cudaMemsetAsync(h.fstore, 0, sizeof(double) * h.n_face, st));
+  }
+  H_TRY(cudaStreamSynchronize(st));
+  H->iface_kind = kind;
+  H->iface_alpha = a;
   return ATS_OK;
 }
 

@@ -1102,6 +1102,33 @@ cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st) {
 
 // Restriction: the value of a refined cell R of level l is the mean of its
 // eight children (the child oct at level l+1), for E and for K.
+__global__ void k_flux_store(int n_face, const int32_t *__restrict__ gather4, const int32_t *__restrict__ fcell,
+                             const double *__restrict__ x, const double *__restrict__ K,
+                             const double *__restrict__ fK, const double *__restrict__ fE, double hf,
+                             double *__restrict__ store) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_face) return;
+  double acc = 0.0;
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int g = gather4[4 * f + k];
+    if (g < 0) continue;
+    const int cell = fcell[g];
+    acc += (2.0 / 3.0) * hf * (K[cell] + fK[g]) * (x[cell] - fE[g]);
+    any = true;
+  }
+  if (any) store[f] += acc / 8.0;
+}
+
+cudaError_t launch_flux_store(int n_face, const int32_t *gather4, const int32_t *fcell, const double *x,
+                              const double *K, const double *fK, const double *fE, double h_f, double *store,
+                              cudaStream_t st) {
+  if (n_face <= 0) return cudaSuccess;
+  k_flux_store<<<(n_face + 127) / 128, 128, 0, st>>>(n_face, gather4, fcell, x, K, fK, fE, h_f, store);
+  return cudaGetLastError();
+}
+
 __global__ void k_restrict(int n, const int32_t *__restrict__ cell, const int32_t *__restrict__ child,
                            const double *__restrict__ Ef, const double *__restrict__ Kf,
                            double *__restrict__ Ec, double *__restrict__ Kc) {

@@ -139,6 +139,15 @@ const int32_t *level_nbr(const ats_level *L) { return L->nbr; }
 double *level_x64(ats_level *L) { return L->x64; }
 int64_t level_cells(const ats_level *L) { return L->N; }
 const uint8_t *level_leaf(const ats_level *L) { return L->leaf; }
+ats_status level_set_face_rows(ats_level *L, const int8_t *kind, const double *alpha) {
+  if (!L) return ATS_ERR_INVALID_ARG;
+  if (L->n_face == 0) return ATS_OK;
+  cudaStream_t st = L->ctx->stream;
+  CUDA_TRY(cudaMemcpyAsync(L->fkind, kind, L->n_face, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(L->falpha, alpha, sizeof(double) * L->n_face, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return ATS_OK;
+}
 int ctx_device(const ats_context *ctx) { return ctx->device; }
 }  // namespace ats
 
