@@ -358,6 +358,10 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, ats, local)
 
+    amr = None
+    if rank == 0 and not args.no_amr:
+        amr = run_amr_interfaces(ats, ctx)
+
     batch.close()
     for L in levels:
         L.close()
@@ -382,10 +386,47 @@ def run_ours(args, rank, world, local):
         "clocks": clocks,
         "fp64_per_solve": fp64,
         "serve": serve,
+        "amr_interfaces": amr,
         "solve_stats": {"iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
                         "refinements_mean": float(np.mean(refs)),
                         "max_rel_residual": float(np.max(bounds)), "layout_s": round(layout_s, 3)},
     }
+
+
+def run_amr_interfaces(ats, ctx, coarse_steps=3):
+    """The two-level workload (base 64^3, level 1 on the central 1/8 of the
+    volume, Gaussian pulse, constant K, fine first) with each row of the
+    coarse-to-fine faces: time per coarse step (two fine solves and one
+    coarse solve, mixed precision, certified 5e-11) and the relative change
+    of the total energy per step (zero-flux walls: only the interfaces can
+    change it; the Neumann rows with the stored flux conserve it)."""
+    levels, states, dt = W.config2(n0=64)
+
+    def energy(H):
+        return sum(float(np.sum(H.state(l)[lv.leaf_cells()])) * lv.dx ** 3 for l, lv in enumerate(levels))
+
+    out = {"workload": "two-level heat: 64^3 base + 64^3 fine cells on the central 1/8, fine first",
+           "coarse_steps": coarse_steps}
+    for name, kind, alpha in (("dirichlet", ats.ATS_FACE_DIRICHLET, 1.0), ("neumann", ats.ATS_FACE_NEUMANN, 0.0),
+                              ("robin_0.5", ats.ATS_FACE_ROBIN, 0.5)):
+        H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
+        H.set_interface(kind, alpha)
+        for l, (E, K) in enumerate(states):
+            H.set_state(l, E, K)
+        opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED)
+        H.advance(0, dt, **opts)  # warm-up step (plans, graphs)
+        e0 = energy(H)
+        t0 = time.perf_counter()
+        for _ in range(coarse_steps):
+            code, _ = H.advance(0, dt, **opts)
+            if code != 0:
+                raise RuntimeError(f"amr {name} step failed: {code}")
+        t_s = time.perf_counter() - t0
+        e1 = energy(H)
+        out[name] = {"ms_per_coarse_step": round(t_s / coarse_steps * 1e3, 3),
+                     "energy_change_per_step": float((e1 - e0) / e0 / coarse_steps)}
+        H.close()
+    return out
 
 
 def run_serve(args, ats, device):
@@ -545,6 +586,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-max-cells", type=int, default=128 ** 3)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
