@@ -169,6 +169,21 @@ def pcg(system: System, x0, tol=1e-10, stop_rule=STOP_RESIDUAL, max_iter=100000,
     }
 
 
+def cn_step(level, dt, K, E_old, src=None, face_K=None, face_E=None, face_F=None, tol=1e-10,
+            stop_rule=STOP_RESIDUAL, max_iter=100000):
+    """Crank-Nicolson step (the second-order integrator Sect. 3.3.3 names as
+    the remedy for the first-order backward Euler): the same SPD matrix with
+    dt/2, M' = I + (dt/2) A, and the explicit half step on the right-hand side,
+    M' E^{n+1} = (I - (dt/2) A) E^n + the step's face and source terms:
+    b_CN = 2 b' - M' E^n with b' the right-hand side assembled for dt/2 (its
+    source terms at half weight, F and src being amounts over the full step).
+    x0 = E^n.  Returns (x, info)."""
+    half = lambda a: None if a is None else 0.5 * np.asarray(a, dtype=np.float64)
+    S = assemble(level, 0.5 * dt, K, E_old, src=half(src), face_K=face_K, face_E=face_E, face_F=half(face_F))
+    b_cn = 2.0 * S.b - S.matvec(E_old)
+    return pcg(S, E_old, tol=tol, stop_rule=stop_rule, max_iter=max_iter, b=b_cn)
+
+
 def solve_level(level, dt, K, E_old, x0=None, tol=1e-10, stop_rule=STOP_RESIDUAL, max_iter=100000,
                 **faces):
     """assemble + pcg in one call; x0 defaults to E^n (Sect. 3.3.4)."""
