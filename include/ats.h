@@ -113,7 +113,21 @@ typedef struct {
   const double *face_E; /* [n_face] neighbour value E_nb, NULL = 0              */
   const double *face_F; /* [n_face] imposed flux F (energy per unit volume into  */
                         /* the cell over the step), NULL = 0                     */
+  int integrator;       /* ATS_INTEGRATOR_* (0 = backward Euler)                 */
 } ats_coef_desc;
+
+/* time integrator of a level step (ats_coef_desc.integrator) */
+#define ATS_INTEGRATOR_BACKWARD_EULER 0 /* Eq. Er_imp1: (I + dt A) E^{n+1} = E^n + ...      */
+#define ATS_INTEGRATOR_CRANK_NICOLSON 1 /* second order (Sect. 3.3.3 names it): the      */
+        /* operator is built for dt/2 with F and src at half weight (they stay amounts  */
+        /* over the full step), and every solve of the level returns 2 x' - E^n, where */
+        /* x' solves that backward-Euler half step and E^n is the build's E_old; this  */
+        /* equals the Crank-Nicolson step (I + dt/2 A) E^{n+1} = (I - dt/2 A) E^n + .. */
+        /* An initial guess x on entry is a guess of E^{n+1}: the solve starts from   */
+        /* (x + E^n) / 2.  The solve statistics, ats_level_get_rhs and               */
+        /* ats_level_apply refer to the half-step system.  Not with a shift s         */
+        /* (ATS_ERR_INVALID_ARG); device E_old must stay unchanged until the solve.   */
+        /* Hierarchy substeps (ats_level_advance) integrate with backward Euler.    */
 
 typedef struct {
   double tol;        /* stopping tolerance (default 1e-10)                    */

@@ -39,6 +39,7 @@ ATS_MEM_HOST, ATS_MEM_DEVICE = 0, 1
 ATS_STOP_RESIDUAL, ATS_STOP_CERTIFIED, ATS_STOP_PAPER = 0, 1, 2
 ATS_PREC_FP64, ATS_PREC_MIXED = 0, 1
 ATS_X0_GIVEN, ATS_X0_E_OLD = 0, 1
+ATS_INTEGRATOR_BACKWARD_EULER, ATS_INTEGRATOR_CRANK_NICOLSON = 0, 1
 
 P = ctypes.c_void_p
 
@@ -54,7 +55,7 @@ class ats_level_desc(ctypes.Structure):
 class ats_coef_desc(ctypes.Structure):
     _fields_ = [
         ("dt", ctypes.c_double), ("mem", ctypes.c_int), ("K", P), ("E_old", P), ("s", P),
-        ("src", P), ("face_K", P), ("face_E", P), ("face_F", P),
+        ("src", P), ("face_K", P), ("face_E", P), ("face_F", P), ("integrator", ctypes.c_int),
     ]
 
 
@@ -317,12 +318,14 @@ def ats_level_size(lvl):
     return a.value, b.value, c.value
 
 
-def coef_desc(dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None, keep=None):
+def coef_desc(dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None, keep=None,
+              integrator=ATS_INTEGRATOR_BACKWARD_EULER):
     """Fill an ats_coef_desc (``keep`` collects converted host arrays that
     must outlive the call)."""
     keep = [] if keep is None else keep
     c = ats_coef_desc()
     c.dt = float(dt)
+    c.integrator = int(integrator)
     c.mem = _mem_of(K, E_old, s, src, face_K, face_E, face_F)
     c.K = _ptr(K, keep=keep)
     c.E_old = _ptr(E_old, keep=keep)
@@ -334,18 +337,11 @@ def coef_desc(dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=N
     return c
 
 
-def ats_level_build_operator(lvl, dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None):
+def ats_level_build_operator(lvl, dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None,
+                             integrator=ATS_INTEGRATOR_BACKWARD_EULER):
     keep = []
-    c = ats_coef_desc()
-    c.dt = float(dt)
-    c.mem = _mem_of(K, E_old, s, src, face_K, face_E, face_F)
-    c.K = _ptr(K, keep=keep)
-    c.E_old = _ptr(E_old, keep=keep)
-    c.s = _ptr(s, keep=keep)
-    c.src = _ptr(src, keep=keep)
-    c.face_K = _ptr(face_K, keep=keep)
-    c.face_E = _ptr(face_E, keep=keep)
-    c.face_F = _ptr(face_F, keep=keep)
+    c = coef_desc(dt, K, E_old, s=s, src=src, face_K=face_K, face_E=face_E, face_F=face_F, keep=keep,
+                  integrator=integrator)
     return _check(lib().ats_level_build_operator(lvl, ctypes.byref(c)), "ats_level_build_operator")
 
 
@@ -548,11 +544,12 @@ def ats_server_destroy(server):
 
 
 def ats_server_submit(server, level, dt, K, E_old, tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, x0=None, s=None,
-                      src=None, face_K=None, face_E=None, face_F=None):
+                      src=None, face_K=None, face_E=None, face_F=None, integrator=ATS_INTEGRATOR_BACKWARD_EULER):
     """Submit one level solve (host arrays, copied by the call); returns the ticket."""
     keep = []
     d = _level_desc(level, keep)
-    c = coef_desc(dt, K, E_old, s=s, src=src, face_K=face_K, face_E=face_E, face_F=face_F, keep=keep)
+    c = coef_desc(dt, K, E_old, s=s, src=src, face_K=face_K, face_E=face_E, face_F=face_F, keep=keep,
+                  integrator=integrator)
     if c.mem != ATS_MEM_HOST:
         raise ValueError("server requests take host arrays")
     r = ats_request()
@@ -618,9 +615,10 @@ class Level:
         self.handle = ats_level_create(ctx.handle, level_desc)
         self.n_cell = 8 * int(level_desc.oct_xyz.shape[0])
 
-    def build(self, dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None):
+    def build(self, dt, K, E_old, s=None, src=None, face_K=None, face_E=None, face_F=None,
+              integrator=ATS_INTEGRATOR_BACKWARD_EULER):
         return ats_level_build_operator(self.handle, dt, K, E_old, s=s, src=src, face_K=face_K, face_E=face_E,
-                                        face_F=face_F)
+                                        face_F=face_F, integrator=integrator)
 
     def rhs(self):
         out = np.empty(self.n_cell)
@@ -681,10 +679,11 @@ class Server:
     def __init__(self, device=0, mem_budget_bytes=0, max_slots=0, max_items=0, **opts):
         self.handle = ats_server_create(device, mem_budget_bytes, make_opts(**opts), max_slots, max_items)
 
-    def submit(self, level, step, tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, x0=None):
+    def submit(self, level, step, tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, x0=None,
+               integrator=ATS_INTEGRATOR_BACKWARD_EULER):
         return ats_server_submit(self.handle, level, step.dt, step.K, step.E, tol=tol, stop_rule=stop_rule, x0=x0,
                                  s=step.s, src=step.src, face_K=step.face_K, face_E=step.face_E,
-                                 face_F=step.face_F)
+                                 face_F=step.face_F, integrator=integrator)
 
     def wait(self, ticket, n_cell, timeout_us=-1):
         return ats_server_wait(self.handle, ticket, n_cell, timeout_us)

@@ -37,6 +37,7 @@ struct SolveDev {
   void *p0;             // [N]  search direction, ping
   void *p1;             // [N]  search direction, pong
   const double *C64;    // [n_oct][3][8] h (K_i + K_j) of each cell's +x, +y, +z face (0 off the leaves)
+  const double *cn_base;  // Crank-Nicolson: E^n; the copy-out returns 2 x - E^n (else null)
   void *q;              // [N]  (I + dt A) p of the current direction (k_op)
   void *dg;             // [N]  diagonal D = 1 + xd + sum C (k_ref; 1 off the leaves)
   double h;             // dt / dx^2 / 2, so an interior C = h (K_i + K_j)
@@ -119,6 +120,7 @@ struct CoefArgs {
   int *err_flag;
   const int32_t *nbr;   // for the face coefficients
   double *C64;          // [n_oct][3][8] written by the face-coefficient pass
+  double src_scale;     // weight of src and face F (1; 1/2 for a Crank-Nicolson half step)
 };
 // K, diagonal extras, b and the FP64 face coefficients C64, one thread per cell.
 cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st);
@@ -230,6 +232,10 @@ const uint8_t *level_leaf(const ats_level *L);
 cudaError_t launch_flux_store(int n_face, const int32_t *gather4, const int32_t *fcell, const double *x,
                               const double *K, const double *fK, const double *fE, double h_f, double *store,
                               cudaStream_t st);
+// out[i] = 2 x[i] - E[i] (the Crank-Nicolson step from its backward-Euler half step).
+cudaError_t launch_cn_extrapolate(int64_t N, const double *x, const double *E, double *out, cudaStream_t st);
+// E^n of a Crank-Nicolson operator build of L (null for backward Euler).
+const double *level_cn_base(const ats_level *L);
 // Replace the face rows (kind, alpha: host arrays of the level's n_face).
 ats_status level_set_face_rows(ats_level *L, const int8_t *kind, const double *alpha);
 cudaError_t launch_restrict(int n, const int32_t *cell, const int32_t *child, const double *Ef, const double *Kf,

@@ -972,7 +972,7 @@ __device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
   bool ok = (K > 0.0) && isfinite(K) && isfinite(E);
   double xd = a.s ? a.s[i] : 0.0;
   ok = ok && isfinite(xd) && xd >= 0.0;
-  double rhs = E + (a.src ? a.src[i] : 0.0);
+  double rhs = E + (a.src ? a.src_scale * a.src[i] : 0.0);
   const int fr = a.frec[o];
   if (fr >= 0) {
     for (int dir = 0; dir < 6; ++dir) {
@@ -980,7 +980,7 @@ __device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
       if (f < 0) continue;
       const double Kn = a.face_K ? a.face_K[f] : K;
       const double Enb = a.face_E ? a.face_E[f] : 0.0;
-      const double F = a.face_F ? a.face_F[f] : 0.0;
+      const double F = a.face_F ? a.src_scale * a.face_F[f] : 0.0;
       const double alpha = a.face_alpha ? a.face_alpha[f] : 1.0;
       ok = ok && (Kn > 0.0) && isfinite(Kn) && isfinite(Enb) && isfinite(F);
       const double factor = (a.face_rel[f] == ATS_REL_COARSER) ? (2.0 / 3.0) : 1.0;
@@ -1406,7 +1406,8 @@ __global__ void k_init(const SolveDev *__restrict__ solves, const WorkItem *__re
     const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item.n_oct * 8;
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
       e[b + k] = T(0);
-      if (xs) sd.x64[b + k] = xs[b + k];
+      // Crank-Nicolson: x is a guess of E^{n+1}, the half-step root is (x + E^n) / 2
+      if (xs) sd.x64[b + k] = sd.cn_base ? 0.5 * (xs[b + k] + sd.cn_base[b + k]) : xs[b + k];
     }
   }
 }
@@ -1419,7 +1420,11 @@ __global__ void k_final(const SolveDev *__restrict__ solves, const WorkItem *__r
     if (!xd) continue;
     const SolveDev &sd = solves[item.solve];
     const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item.n_oct * 8;
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) xd[b + k] = sd.x64[b + k];
+    if (sd.cn_base) {
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) xd[b + k] = 2.0 * sd.x64[b + k] - sd.cn_base[b + k];
+    } else {
+      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) xd[b + k] = sd.x64[b + k];
+    }
   }
 }
 
@@ -1427,6 +1432,18 @@ cudaError_t launch_init(bool fp64, const SolveDev *solves, const WorkItem *items
                         const double *const *src, int grid, cudaStream_t st) {
   if (fp64) k_init<double><<<grid, kThreads, 0, st>>>(solves, items, n_items, src);
   else k_init<float><<<grid, kThreads, 0, st>>>(solves, items, n_items, src);
+  return cudaGetLastError();
+}
+
+__global__ void k_cn_extrapolate(int64_t N, const double *__restrict__ x, const double *__restrict__ E,
+                                 double *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) out[i] = 2.0 * x[i] - E[i];
+}
+
+cudaError_t launch_cn_extrapolate(int64_t N, const double *x, const double *E, double *out, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  k_cn_extrapolate<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, x, E, out);
   return cudaGetLastError();
 }
 

@@ -68,6 +68,7 @@ struct ats_level {
   void *q[2] = {nullptr, nullptr}, *dg[2] = {nullptr, nullptr};
   double *rhs_save = nullptr;  // b when a solve overrides it
   const double *E_dev = nullptr;  // device E^n of the last operator build (x0 = E^n)
+  const double *cn_base = nullptr;  // E^n when that build was a Crank-Nicolson half step
   Plan *solo = nullptr;        // cached single-solve plan
 };
 
@@ -137,6 +138,7 @@ void ctx_free(ats_context *ctx, void *p) { dev_free(ctx, p); }
 cudaStream_t ctx_stream(const ats_context *ctx) { return ctx->stream; }
 const int32_t *level_nbr(const ats_level *L) { return L->nbr; }
 double *level_x64(ats_level *L) { return L->x64; }
+const double *level_cn_base(const ats_level *L) { return L->cn_base; }
 int64_t level_cells(const ats_level *L) { return L->N; }
 const uint8_t *level_leaf(const ats_level *L) { return L->leaf; }
 ats_status level_set_face_rows(ats_level *L, const int8_t *kind, const double *alpha) {
@@ -378,6 +380,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     sd.xdT = P->fp64 ? (const void *)L->xd64 : (const void *)L->xd32;
     sd.b64 = L->b64;
     sd.x64 = L->x64;
+    sd.cn_base = L->cn_base;
     const int vk = P->fp64 ? 0 : 1;
     sd.e = L->e[vk];
     sd.z = L->z[vk];
@@ -619,8 +622,9 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
     const double h = 0.5 * L->dt / (L->dx * L->dx);
     const int32_t *xrec = L->dense_xd ? L->xrec_dense : L->frec;
     const void *xdT = P->fp64 ? (const void *)L->xd64 : (const void *)L->xd32;
-    if (sd.h != h || sd.xrec != xrec || sd.xd64 != L->xd64 || sd.xdT != xdT) {
+    if (sd.h != h || sd.xrec != xrec || sd.xd64 != L->xd64 || sd.xdT != xdT || sd.cn_base != L->cn_base) {
       sd.h = h;
+      sd.cn_base = L->cn_base;
       sd.xrec = xrec;
       sd.xd64 = L->xd64;
       sd.xdT = xdT;
@@ -778,6 +782,7 @@ ats_status solve_dev_for(ats_level *L, const ats_solve_opts &o, bool fp64, int i
   sd.xdT = fp64 ? (const void *)L->xd64 : (const void *)L->xd32;
   sd.b64 = L->b64;
   sd.x64 = L->x64;
+  sd.cn_base = L->cn_base;
   const int vk = fp64 ? 0 : 1;
   sd.e = L->e[vk];
   sd.z = L->z[vk];
@@ -1021,6 +1026,18 @@ ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out)
     set_error("bad mem");
     return ATS_ERR_INVALID_ARG;
   }
+  const bool cn = (c->integrator == ATS_INTEGRATOR_CRANK_NICOLSON);
+  if (!cn && c->integrator != ATS_INTEGRATOR_BACKWARD_EULER) {
+    set_error("unknown integrator");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (cn && c->s) {
+    set_error("the Crank-Nicolson integrator takes no shift s");
+    return ATS_ERR_INVALID_ARG;
+  }
+  // Crank-Nicolson: the backward-Euler system of the half step (sources at
+  // half weight); the solve extrapolates E^{n+1} = 2 x - E^n from its root
+  const double dt_op = cn ? 0.5 * c->dt : c->dt;
   ats_context *ctx = L->ctx;
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -1107,7 +1124,8 @@ ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out)
   a.E_old = E;
   a.s = sh;
   a.src = src;
-  a.h = 0.5 * c->dt / (L->dx * L->dx);
+  a.h = 0.5 * dt_op / (L->dx * L->dx);
+  a.src_scale = cn ? 0.5 : 1.0;
   a.K64 = L->K64;
   a.K32 = L->K32;
   a.xd64 = L->xd64;
@@ -1117,7 +1135,8 @@ ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out)
   a.nbr = L->nbr;
   a.C64 = L->C64;
   L->E_dev = E;
-  L->dt = c->dt;
+  L->cn_base = cn ? E : nullptr;
+  L->dt = dt_op;
   L->built = true;
   return ATS_OK;
 }

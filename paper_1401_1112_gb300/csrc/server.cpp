@@ -46,6 +46,7 @@ struct Pending {
   std::vector<int32_t> face_cell;
   std::vector<int8_t> face_dir, face_kind, face_rel;
   std::vector<double> face_alpha, K, E, s, src, face_K, face_E, face_F, x0;
+  int integrator = ATS_INTEGRATOR_BACKWARD_EULER;
   double tol = 1e-10;
   int stop_rule = ATS_STOP_RESIDUAL;
   Clock::time_point submitted;
@@ -203,6 +204,7 @@ ats_status admit_one_impl(ats_server *S, Pending &p, int slot, std::vector<int32
   ats_coef_desc c;
   std::memset(&c, 0, sizeof(c));
   c.dt = p.dt;
+  c.integrator = p.integrator;
   c.mem = ATS_MEM_HOST;
   c.K = p.K.data();
   c.E_old = p.E.data();
@@ -263,6 +265,8 @@ void retire(ats_server *S, int slot, const SolveScalars &fin) {
   Done dn;
   const int64_t N = level_cells(sl.lvl);
   dn.x.resize(N);
+  if (const double *base = level_cn_base(sl.lvl))  // Crank-Nicolson: E^{n+1} = 2 x - E^n
+    launch_cn_extrapolate(N, level_x64(sl.lvl), base, level_x64(sl.lvl), S->st);
   cudaMemcpyAsync(dn.x.data(), level_x64(sl.lvl), sizeof(double) * N, cudaMemcpyDeviceToHost, S->st);
   cudaStreamSynchronize(S->st);
   dn.status = fin.status;
@@ -521,6 +525,11 @@ ats_status ats_server_submit(ats_server *S, const ats_request *r, uint64_t *tick
     set_error("ats_server_submit: request arrays must be host arrays with n_oct > 0, K, E_old and dt > 0");
     return ATS_ERR_INVALID_ARG;
   }
+  if ((c.integrator != ATS_INTEGRATOR_BACKWARD_EULER && c.integrator != ATS_INTEGRATOR_CRANK_NICOLSON) ||
+      (c.integrator == ATS_INTEGRATOR_CRANK_NICOLSON && c.s)) {
+    set_error("ats_server_submit: unknown integrator, or a shift s with Crank-Nicolson");
+    return ATS_ERR_INVALID_ARG;
+  }
   std::unique_ptr<Pending> p(new (std::nothrow) Pending());
   if (!p) return ATS_ERR_OOM;
   const size_t n = (size_t)d.n_oct, N = 8 * n, nf = (size_t)d.n_face;
@@ -546,6 +555,9 @@ ats_status ats_server_submit(ats_server *S, const ats_request *r, uint64_t *tick
   if (c.s) p->s.assign(c.s, c.s + N);
   if (c.src) p->src.assign(c.src, c.src + N);
   if (r->x0) p->x0.assign(r->x0, r->x0 + N);
+  p->integrator = c.integrator;
+  if (r->x0 && p->integrator == ATS_INTEGRATOR_CRANK_NICOLSON)
+    for (size_t i = 0; i < N; ++i) p->x0[i] = 0.5 * (p->x0[i] + p->E[i]);  // guess of the half-step root
   p->tol = r->tol > 0.0 ? r->tol : 1e-10;
   p->stop_rule = r->stop_rule;
   p->submitted = Clock::now();
