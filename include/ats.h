@@ -118,7 +118,7 @@ typedef struct {
 
 /* time integrator of a level step (ats_coef_desc.integrator) */
 #define ATS_INTEGRATOR_BACKWARD_EULER 0 /* Eq. Er_imp1: (I + dt A) E^{n+1} = E^n + ...      */
-#define ATS_INTEGRATOR_CRANK_NICOLSON 1 /* second order (Sect. 3.3.3 names it): the      */
+#define ATS_INTEGRATOR_CRANK_NICOLSON 1 /* second order (Sect. 3.3.5 names it): the      */
         /* operator is built for dt/2 with F and src at half weight (they stay amounts  */
         /* over the full step), and every solve of the level returns 2 x' - E^n, where */
         /* x' solves that backward-Euler half step and E^n is the build's E_old; this  */

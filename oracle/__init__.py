@@ -171,7 +171,7 @@ def pcg(system: System, x0, tol=1e-10, stop_rule=STOP_RESIDUAL, max_iter=100000,
 
 def cn_step(level, dt, K, E_old, src=None, face_K=None, face_E=None, face_F=None, tol=1e-10,
             stop_rule=STOP_RESIDUAL, max_iter=100000):
-    """Crank-Nicolson step (the second-order integrator Sect. 3.3.3 names as
+    """Crank-Nicolson step (the second-order integrator Sect. 3.3.5 names as
     the remedy for the first-order backward Euler): the same SPD matrix with
     dt/2, M' = I + (dt/2) A, and the explicit half step on the right-hand side,
     M' E^{n+1} = (I - (dt/2) A) E^n + the step's face and source terms:

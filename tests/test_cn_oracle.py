@@ -1,5 +1,5 @@
 """Crank-Nicolson step of the oracle (the second-order integrator named in
-Sect. 3.3.3): pins that do not depend on the implementation.
+Sect. 3.3.5): pins that do not depend on the implementation.
 
 * Constant K, zero-flux box: the step is diagonal in the DCT-II basis, each
   mode multiplied by (1 - c lambda / 2) / (1 + c lambda / 2), c = dt K / dx^2.

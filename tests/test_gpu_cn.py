@@ -1,4 +1,4 @@
-"""Crank-Nicolson steps on the GPU (the second-order integrator Sect. 3.3.3
+"""Crank-Nicolson steps on the GPU (the second-order integrator Sect. 3.3.5
 names): the library builds the backward-Euler system of the half step, solves
 it, and returns 2 x' - E^n; the oracle solves the Crank-Nicolson system
 (I + dt/2 A) E^{n+1} = (I - dt/2 A) E^n + the step's face and source terms
