@@ -362,6 +362,36 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_amr:
         amr = run_amr_interfaces(ats, ctx)
 
+    # the same batch integrated with Crank-Nicolson (half-step backward-Euler
+    # operator, E^{n+1} = 2 x' - E^n in the copy-out), device-resident inputs
+    cn = None
+    if rank == 0 and not args.no_cn:
+        cn_coefs = batch.prepare_coefs([dict(coef_kwargs(k), integrator=ats.ATS_INTEGRATOR_CRANK_NICOLSON)
+                                        for k in range(n)])
+
+        def cn_step():
+            x_d.copy_(E_d)
+            batch.build_operators(cn_coefs)
+            code, st = batch.solve(xs)
+            if code != 0:
+                raise RuntimeError(f"Crank-Nicolson batch failed: {code}")
+            return st
+
+        cn_step()
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            cst = cn_step()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / args.steps
+        cn = {"value": round(n / (cms / 1e3), 2), "unit": UNIT, "ms_per_step": round(cms, 3),
+              "iterations_mean": float(np.mean([s["iterations"] for s in cst])),
+              "iterations_max": int(np.max([s["iterations"] for s in cst])),
+              "workload": "the same batch, one Crank-Nicolson step per solve"}
+
     batch.close()
     for L in levels:
         L.close()
@@ -387,6 +417,7 @@ def run_ours(args, rank, world, local):
         "fp64_per_solve": fp64,
         "serve": serve,
         "amr_interfaces": amr,
+        "crank_nicolson": cn,
         "solve_stats": {"iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
                         "refinements_mean": float(np.mean(refs)),
                         "max_rel_residual": float(np.max(bounds)), "layout_s": round(layout_s, 3)},
@@ -587,6 +618,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--no-cn", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-max-cells", type=int, default=128 ** 3)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
