@@ -223,6 +223,18 @@ def run_ours(args, rank, world, local):
     def build_ops():
         batch.build_operators(coefs)  # all levels' coefficients and right-hand sides, one launch
 
+    # work-item size and poll interval chosen by the library's autotuner on
+    # these solves (before the warm-up; not timed)
+    tune = None
+    if not args.no_autotune and args.tile == 0:
+        build_ops()
+        x_d.copy_(E_d)
+        t_tune = time.time()
+        tune = batch.autotune(xs, reps=2)
+        tune["seconds"] = round(time.time() - t_tune, 2)
+    tile_octs = tune["tile_octs"] if tune else args.tile
+    check_every = tune["check_every"] if tune else args.check_every
+
     def step():
         x_d.copy_(E_d)          # initial guess x0 = E^n
         build_ops()             # coefficients, interface terms, right-hand side
@@ -308,7 +320,8 @@ def run_ours(args, rank, world, local):
         Kn, En, fEn, fFn, xn = Kp.numpy(), Ep.numpy(), fEp.numpy(), fFp.numpy(), xp.numpy()
         # x0 = E^n of the build (the paper's initial guess): x is output only
         hbatch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_RESIDUAL, precision=ats.ATS_PREC_MIXED,
-                           use_graph=1, check_every=args.check_every, mem=ats.ATS_MEM_HOST, x0=ats.ATS_X0_E_OLD)
+                           use_graph=1, check_every=check_every, tile_octs=tile_octs, mem=ats.ATS_MEM_HOST,
+                           x0=ats.ATS_X0_E_OLD)
         hx = [xn[offs[k]:offs[k + 1]] for k in range(n)]
 
         hcoefs = hbatch.prepare_coefs([
@@ -408,6 +421,7 @@ def run_ours(args, rank, world, local):
             "solves": n, "cells": total_cells, "tol": TOL, "seed": 1404,
             "l2": "inputs larger than L2 (working set ~%.2f GB)" % (total_cells * 64 / 1e9),
             "parallelism": f"replicas x{world}",
+            "tile_octs": tile_octs, "check_every": check_every, "autotune": tune,
         },
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -619,6 +633,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-cn", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-max-cells", type=int, default=128 ** 3)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)

@@ -232,6 +232,34 @@ typedef struct {
 ats_status ats_batch_set_profiling(ats_batch *batch, int on);
 ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out);
 
+/* Autotuner of the batched launch (not in the paper, whose solver is one CPU
+ * CG per level): times ats_batch_solve on the batch's own levels and
+ * operators for every candidate pair (work-item size tile_octs, poll
+ * interval check_every) and keeps the fastest, together with the options the
+ * batch was created with.  tiles[n_tiles]: octs per work item, 0 = the
+ * library's size rule (256, or 1024 for levels above 131 072 octs), others
+ * rounded up to a multiple of 32; NULL / 0 = {0, 128, 256, 384, 512}.
+ * checks[n_checks]: ticks per CUDA graph and host poll; NULL / 0 = {8, 16,
+ * 32}.  reps (>= 1): timed solves per candidate after one warm-up solve (the
+ * fastest counts).  x_inout as in ats_batch_solve: with x0 = ATS_X0_GIVEN
+ * every trial starts from the caller's x (kept in a scratch copy); on return
+ * it holds the solution of one more solve with the chosen configuration, whose
+ * plan the batch keeps.  Results are valid solutions for every candidate but
+ * differ between tile sizes in the last bits (a solve's reduction order
+ * follows its work items).  out: the choice, its time and the time of the
+ * batch's original options (may be NULL).  Errors: ATS_ERR_INVALID_ARG for a
+ * NULL batch or x, a negative tile or an unbuilt level; the first failing
+ * solve's status otherwise (the batch then keeps its original plan). */
+typedef struct {
+  int tile_octs;     /* chosen octs per work item (0 = the size rule)      */
+  int check_every;   /* chosen ticks per graph / poll interval             */
+  double ms;         /* fastest solve time of the chosen configuration     */
+  double ms_default; /* fastest solve time of the batch's original options */
+  int candidates;    /* configurations timed                               */
+} ats_tune_result;
+ats_status ats_batch_autotune(ats_batch *batch, double *const *x_inout, const int *tiles, int n_tiles,
+                              const int *checks, int n_checks, int reps, ats_tune_result *out);
+
 /* ---- AMR hierarchy and the level substep driver (Sect. 2.2, 3.3) ----------- */
 /* A hierarchy of levels l = 0 .. n_levels-1, dx halving per level; an oct at
  * level l+1 with oct coordinates (x, y, z) refines cell (x, y, z) of level l,

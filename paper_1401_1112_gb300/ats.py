@@ -83,6 +83,11 @@ class ats_kernel_stats(ctypes.Structure):
     ]
 
 
+class ats_tune_result(ctypes.Structure):
+    _fields_ = [("tile_octs", ctypes.c_int), ("check_every", ctypes.c_int), ("ms", ctypes.c_double),
+                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
 class ats_solve_stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("refinements", ctypes.c_int),
@@ -133,6 +138,9 @@ _SIGS = [
     ("ats_batch_build_operators", ctypes.c_int, [P, ctypes.POINTER(ats_coef_desc)]),
     ("ats_batch_set_profiling", ctypes.c_int, [P, ctypes.c_int]),
     ("ats_batch_kernel_stats", ctypes.c_int, [P, ctypes.POINTER(ats_kernel_stats)]),
+    ("ats_batch_autotune", ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ats_tune_result)]),
     ("ats_default_opts", None, [ctypes.POINTER(ats_solve_opts)]),
     ("ats_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("ats_last_error", ctypes.c_char_p, []),
@@ -409,6 +417,18 @@ def ats_batch_kernel_stats(batch):
     k = ats_kernel_stats()
     _check(lib().ats_batch_kernel_stats(batch, ctypes.byref(k)), "ats_batch_kernel_stats")
     return {name: getattr(k, name) for name, _ in k._fields_}
+
+
+def ats_batch_autotune(batch, xs: Sequence, tiles: Sequence[int] = (), checks: Sequence[int] = (), reps: int = 2):
+    """Time the batch's solve per (tile_octs, check_every) candidate and keep
+    the fastest; xs as in ``ats_batch_solve`` (holds a solution on return)."""
+    arr = (P * len(xs))(*[_ptr(x) for x in xs])
+    ta = (ctypes.c_int * max(1, len(tiles)))(*tiles)
+    ca = (ctypes.c_int * max(1, len(checks)))(*checks)
+    r = ats_tune_result()
+    _check(lib().ats_batch_autotune(batch, arr, ta, len(tiles), ca, len(checks), int(reps), ctypes.byref(r)),
+           "ats_batch_autotune")
+    return {name: getattr(r, name) for name, _ in r._fields_}
 
 
 def ats_default_opts() -> ats_solve_opts:
@@ -722,6 +742,9 @@ class Batch:
 
     def kernel_stats(self):
         return ats_batch_kernel_stats(self.handle)
+
+    def autotune(self, xs, tiles=(), checks=(), reps=2):
+        return ats_batch_autotune(self.handle, xs, tiles=tiles, checks=checks, reps=reps)
 
     def close(self):
         if self.handle:

@@ -1378,6 +1378,147 @@ ats_status ats_batch_set_profiling(ats_batch *B, int on) {
   return ATS_OK;
 }
 
+ats_status ats_batch_autotune(ats_batch *B, double *const *x_inout, const int *tiles, int n_tiles,
+                              const int *checks, int n_checks, int reps, ats_tune_result *out) {
+  if (!B || !B->plan || !x_inout || n_tiles < 0 || n_checks < 0 || (n_tiles > 0 && !tiles) ||
+      (n_checks > 0 && !checks)) {
+    set_error("ats_batch_autotune: bad arguments");
+    return ATS_ERR_INVALID_ARG;
+  }
+  Plan *P = B->plan;
+  ats_context *ctx = P->ctx;
+  cudaStream_t st = ctx->stream;
+  const int n = P->n;
+  const ats_solve_opts base = P->opts;
+  const bool dev = base.mem == ATS_MEM_DEVICE;
+  const bool restore = base.x0 == ATS_X0_GIVEN;  // every trial starts from the caller's x
+  reps = std::max(1, reps);
+  for (int k = 0; k < n; ++k) {
+    if (!x_inout[k]) {
+      set_error("x_inout[k] is NULL");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (!P->levels[k]->built) {
+      set_error("level operator not built");
+      return ATS_ERR_INVALID_ARG;
+    }
+  }
+  static const int kTiles[] = {0, 128, 256, 384, 512};
+  static const int kChecks[] = {8, 16, 32};
+  if (n_tiles == 0) {
+    tiles = kTiles;
+    n_tiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
+  }
+  if (n_checks == 0) {
+    checks = kChecks;
+    n_checks = (int)(sizeof(kChecks) / sizeof(kChecks[0]));
+  }
+  for (int i = 0; i < n_tiles; ++i)
+    if (tiles[i] < 0) {
+      set_error("ats_batch_autotune: negative tile");
+      return ATS_ERR_INVALID_ARG;
+    }
+  // the caller's x, kept for the trials to start from
+  std::vector<int64_t> off(n + 1, 0);
+  for (int k = 0; k < n; ++k) off[k + 1] = off[k] + P->levels[k]->N;
+  double *dsave = nullptr;
+  std::vector<double> hsave;
+  ats_status s;
+  if (restore) {
+    if (dev) {
+      if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, off[n]), &dsave)) != ATS_OK) return s;
+      for (int k = 0; k < n; ++k)
+        CUDA_TRY(cudaMemcpyAsync(dsave + off[k], x_inout[k], sizeof(double) * (off[k + 1] - off[k]),
+                                 cudaMemcpyDeviceToDevice, st));
+    } else {
+      hsave.resize((size_t)off[n]);
+      for (int k = 0; k < n; ++k) std::memcpy(hsave.data() + off[k], x_inout[k], sizeof(double) * (off[k + 1] - off[k]));
+    }
+  }
+  auto put_back = [&]() -> ats_status {
+    if (!restore) return ATS_OK;
+    for (int k = 0; k < n; ++k) {
+      const size_t bytes = sizeof(double) * (off[k + 1] - off[k]);
+      if (dev) CUDA_TRY(cudaMemcpyAsync(x_inout[k], dsave + off[k], bytes, cudaMemcpyDeviceToDevice, st));
+      else std::memcpy(x_inout[k], hsave.data() + off[k], bytes);
+    }
+    return ATS_OK;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  // one plan per candidate: a warm-up solve (graph capture), then the fastest of reps solves
+  auto time_plan = [&](Plan *Q, double *ms) -> ats_status {
+    ats_status r;
+    if ((r = put_back()) != ATS_OK) return r;
+    if ((r = plan_run(Q, x_inout, nullptr)) != ATS_OK) return r;
+    *ms = 1e300;
+    for (int i = 0; i < reps; ++i) {
+      if ((r = put_back()) != ATS_OK) return r;
+      CUDA_TRY(cudaEventRecord(e0, st));
+      if ((r = plan_run(Q, x_inout, nullptr)) != ATS_OK) return r;
+      CUDA_TRY(cudaEventRecord(e1, st));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+      *ms = std::min(*ms, (double)t);
+    }
+    return ATS_OK;
+  };
+  ats_tune_result res;
+  std::memset(&res, 0, sizeof(res));
+  s = ATS_OK;
+  const bool was_profiling = P->profiling;
+  P->profiling = false;
+  if ((s = time_plan(P, &res.ms_default)) == ATS_OK) {
+    res.tile_octs = base.tile_octs;
+    res.check_every = base.check_every;
+    res.ms = res.ms_default;
+    res.candidates = 1;
+    for (int i = 0; i < n_tiles && s == ATS_OK; ++i) {
+      for (int j = 0; j < n_checks && s == ATS_OK; ++j) {
+        ats_solve_opts o = base;
+        o.tile_octs = tiles[i];
+        o.check_every = checks[j];
+        if (o.tile_octs == base.tile_octs && normalize(&o).check_every == base.check_every) continue;
+        Plan *Q = nullptr;
+        if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) != ATS_OK) break;
+        double ms = 0.0;
+        s = time_plan(Q, &ms);
+        plan_free(Q);
+        if (s != ATS_OK) break;
+        ++res.candidates;
+        if (ms < res.ms) {
+          res.ms = ms;
+          res.tile_octs = o.tile_octs;
+          res.check_every = normalize(&o).check_every;
+        }
+      }
+    }
+  }
+  // the batch keeps the fastest configuration, and x_inout holds its solution
+  if (s == ATS_OK && (res.tile_octs != base.tile_octs || res.check_every != base.check_every)) {
+    ats_solve_opts o = base;
+    o.tile_octs = res.tile_octs;
+    o.check_every = res.check_every;
+    Plan *Q = nullptr;
+    if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) == ATS_OK) {
+      plan_free(P);
+      B->plan = P = Q;
+    }
+  }
+  P->profiling = was_profiling;
+  if (s == ATS_OK && (s = put_back()) == ATS_OK) s = plan_run(P, x_inout, nullptr);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (dsave) {
+    cudaStreamSynchronize(st);
+    dev_free(ctx, dsave);
+  }
+  if (s == ATS_OK && out) *out = res;
+  return s;
+}
+
 ats_status ats_batch_kernel_stats(const ats_batch *B, ats_kernel_stats *out) {
   if (!B || !B->plan || !out) return ATS_ERR_INVALID_ARG;
   const Plan *P = B->plan;

@@ -357,3 +357,55 @@ def test_initial_guess_from_build(ats, ctx, mem):
         np.testing.assert_array_equal(a, b)
     for L in levels:
         L.close()
+
+
+@pytest.mark.parametrize("mem", ["host", "device"])
+def test_autotune_keeps_a_valid_fastest_plan(ats, ctx, mem):
+    """The autotuner times every (tile, poll interval) candidate on the batch's
+    own solves, keeps the fastest plan, and leaves a solution in x: each solve
+    matches the oracle, and later solves of the batch are bitwise those of a
+    batch created with the chosen options."""
+    import torch
+
+    rng = np.random.default_rng(83)
+    solves = [W.random_box_solve(rng, o) for o in (1, 7, 64, 100, 333, 900, 2)]
+    dev = torch.device("cuda:0")
+    conv = (lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)) if mem == "device" else (lambda a: a)
+    back = (lambda t: t.cpu().numpy()) if mem == "device" else (lambda a: a)
+    M = ats.ATS_MEM_DEVICE if mem == "device" else ats.ATS_MEM_HOST
+    x0 = ats.ATS_X0_E_OLD if mem == "device" else ats.ATS_X0_GIVEN
+    levels = []
+    for lv, st in solves:
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        levels.append(L)
+    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=1, mem=M, x0=x0)
+    B = ats.Batch(ctx, levels, check_every=16, **opts)
+    xs = [conv(st.E.copy()) for _, st in solves]
+    r = B.autotune(xs, tiles=(0, 64, 256), checks=(4, 16), reps=1)
+    assert r["candidates"] == 6  # the batch's own options (0, 16) are timed once
+    assert r["tile_octs"] in (0, 64, 256) and r["check_every"] in (4, 16)
+    assert 0.0 < r["ms"] <= r["ms_default"]
+    for (lv, st), x in zip(solves, xs):
+        _, xr = _oracle_solution(lv, st)
+        assert _rel(back(x), xr) <= PAR
+    xs2 = [conv(st.E.copy()) for _, st in solves]
+    code, _ = B.solve(xs2)
+    assert code == 0
+    B.close()
+    B3 = ats.Batch(ctx, levels, check_every=r["check_every"], tile_octs=r["tile_octs"], **opts)
+    xs3 = [conv(st.E.copy()) for _, st in solves]
+    code, _ = B3.solve(xs3)
+    assert code == 0
+    for a, b in zip(xs2, xs3):
+        np.testing.assert_array_equal(back(a), back(b))
+    B3.close()
+    with pytest.raises(ats.AtsError) as e:
+        B3 = ats.Batch(ctx, levels, **opts)
+        try:
+            B3.autotune([conv(st.E.copy()) for _, st in solves], tiles=(-32,), reps=1)
+        finally:
+            B3.close()
+    assert e.value.code == ats.ATS_ERR_INVALID_ARG
+    for L in levels:
+        L.close()
