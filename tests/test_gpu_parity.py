@@ -409,3 +409,76 @@ def test_autotune_keeps_a_valid_fastest_plan(ats, ctx, mem):
     assert e.value.code == ats.ATS_ERR_INVALID_ARG
     for L in levels:
         L.close()
+
+
+def test_unrefined_fp32_error_and_refinement(ats, ctx):
+    """The mixed path without FP64 refinement (one FP32 inner solve from the
+    FP64 residual of x0, max_refine = 1) stops near the FP32 floor: its error
+    against the oracle lies between 1e-10 and 1e-4 and the final true-residual
+    pass reports it (status NOT_CONVERGED); with refinement the same solves
+    reach the 1e-10 bound."""
+    rng = np.random.default_rng(91)
+    for o in (8, 120, 700):
+        # large steps (10..100 explicit steps): the correction x - E^n is a
+        # sizeable part of x, so the FP32 floor shows in the result
+        lv, st = W.random_box_solve(rng, o, dt_lo=10.0, dt_hi=100.0, robin=True)
+        _, xr = _oracle_solution(lv, st)
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        x = st.E.copy()
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                              max_refine=1, inner_rtol=1e-6)
+        assert code == ats.ATS_ERR_NOT_CONVERGED, stats
+        assert stats["refinements"] == 2
+        e_un = _rel(x, xr)
+        assert 1e-10 < e_un < 1e-4, e_un
+        assert stats["err_bound"] > TOL
+        x = st.E.copy()
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED)
+        assert code == 0, stats
+        assert _rel(x, xr) <= PAR
+        L.close()
+
+
+def test_full_size_batch_sampled_parity(ats, ctx):
+    """The benchmark's workload at full size and in its launch configuration
+    (512 solves, 21 M cells, device arrays, mixed precision, graph-replayed
+    ticks of 16, certified 5e-11): every solve ends OK with its FP64
+    certificate <= 5e-11, and sampled solves (the smallest, the largest and
+    six drawn at random) match the oracle to 1e-10."""
+    import torch
+
+    solves = W.config4(n_solves=512, seed=1404)
+    dev = torch.device("cuda:0")
+    sizes = [lv.n_cell for lv, _ in solves]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    K_d = torch.from_numpy(np.concatenate([st.K for _, st in solves])).to(dev)
+    E_d = torch.from_numpy(np.concatenate([st.E for _, st in solves])).to(dev)
+    x_d = E_d.clone()
+    levels, coefs = [], []
+    for k, (lv, st) in enumerate(solves):
+        L = ats.Level(ctx, lv)
+        c = dict(dt=st.dt, K=K_d[offs[k]:offs[k + 1]], E_old=E_d[offs[k]:offs[k + 1]],
+                 face_E=None if st.face_E is None else torch.from_numpy(st.face_E).to(dev),
+                 face_F=None if st.face_F is None else torch.from_numpy(st.face_F).to(dev))
+        L.build(**c)
+        levels.append(L)
+        coefs.append(c)
+    torch.cuda.synchronize()
+    B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                  use_graph=1, check_every=16, mem=ats.ATS_MEM_DEVICE)
+    B.build_operators(B.prepare_coefs(coefs))
+    xs = [x_d[offs[k]:offs[k + 1]] for k in range(len(solves))]
+    code, stats = B.solve(xs)
+    assert code == 0
+    assert all(s["status"] == 0 and s["err_bound"] <= TOL for s in stats)
+    x = x_d.cpu().numpy()
+    rng = np.random.default_rng(5)
+    sample = {int(np.argmin(sizes)), int(np.argmax(sizes))} | set(int(i) for i in rng.choice(len(solves), 6, False))
+    for k in sorted(sample):
+        lv, st = solves[k]
+        _, xr = _oracle_solution(lv, st)
+        assert _rel(x[offs[k]:offs[k + 1]], xr) <= PAR, k
+    B.close()
+    for L in levels:
+        L.close()
