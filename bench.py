@@ -322,8 +322,10 @@ def run_ours(args, rank, world, local):
         xp = torch.empty_like(Ep).pin_memory()
         Kn, En, fEn, fFn, xn = Kp.numpy(), Ep.numpy(), fEp.numpy(), fFp.numpy(), xp.numpy()
         # x0 = E^n of the build (the paper's initial guess): x is output only
+        # the whole tick loop as one graph (device-side WHILE node): the host
+        # waits once per solve
         hbatch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
-                           use_graph=1, check_every=check_every, tile_octs=tile_octs, mem=ats.ATS_MEM_HOST,
+                           use_graph=2, check_every=check_every, tile_octs=tile_octs, mem=ats.ATS_MEM_HOST,
                            x0=ats.ATS_X0_E_OLD)
         hx = [xn[offs[k]:offs[k + 1]] for k in range(n)]
 
@@ -468,7 +470,7 @@ def run_ours(args, rank, world, local):
     }
 
 
-def run_amr_interfaces(ats, ctx, coarse_steps=3):
+def run_amr_interfaces(ats, ctx, coarse_steps=3, use_graph=2, check_every=16):
     """The two-level workload (base 64^3, level 1 on the central 1/8 of the
     volume, Gaussian pulse, constant K, fine first) with each row of the
     coarse-to-fine faces: time per coarse step (two fine solves and one
@@ -481,14 +483,15 @@ def run_amr_interfaces(ats, ctx, coarse_steps=3):
         return sum(float(np.sum(H.state(l)[lv.leaf_cells()])) * lv.dx ** 3 for l, lv in enumerate(levels))
 
     out = {"workload": "two-level heat: 64^3 base + 64^3 fine cells on the central 1/8, fine first",
-           "coarse_steps": coarse_steps}
+           "coarse_steps": coarse_steps, "use_graph": use_graph, "check_every": check_every}
     for name, kind, alpha in (("dirichlet", ats.ATS_FACE_DIRICHLET, 1.0), ("neumann", ats.ATS_FACE_NEUMANN, 0.0),
                               ("robin_0.5", ats.ATS_FACE_ROBIN, 0.5)):
         H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
         H.set_interface(kind, alpha)
         for l, (E, K) in enumerate(states):
             H.set_state(l, E, K)
-        opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED)
+        opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=use_graph,
+                    check_every=check_every)
         H.advance(0, dt, **opts)  # warm-up step (plans, graphs)
         e0 = energy(H)
         t0 = time.perf_counter()

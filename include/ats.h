@@ -138,7 +138,7 @@ typedef struct {
   double inner_rtol; /* mixed: residual reduction per inner FP32 solve (0 = 1e-5) */
   int tile_octs;     /* octs per work item, multiple of 32 (0 = autotuned)   */
   int check_every;   /* ticks between host convergence polls (0 = 16)       */
-  int use_graph;     /* 1 = capture the poll interval as a CUDA graph        */
+  int use_graph;     /* 1 = each poll interval of check_every ticks is one CUDA graph, the host polls between intervals; 2 = the whole tick loop is one graph (a WHILE conditional node over one interval, ended on the device when no solve is active), the host waits once (with profiling on, 2 runs as 1) */
   int mem;           /* ATS_MEM_HOST / ATS_MEM_DEVICE for x (and rhs)        */
   int x0;            /* ATS_X0_*: where the initial guess comes from          */
 } ats_solve_opts;

@@ -232,6 +232,14 @@ const uint8_t *level_leaf(const ats_level *L);
 cudaError_t launch_flux_store(int n_face, const int32_t *gather4, const int32_t *fcell, const double *x,
                               const double *K, const double *fK, const double *fE, double h_f, double *store,
                               cudaStream_t st);
+// A graph holding one WHILE conditional node (default value 1, assigned at
+// every launch); body: the node's (empty) body graph to capture into.
+cudaError_t make_while_graph(cudaGraph_t *graph, cudaGraph_t *body, cudaGraphConditionalHandle *handle);
+// Condition kernel of the device-side tick loop (a WHILE graph node): counts
+// the intervals in *chunks and sets h to continue while n_active > 0 and
+// fewer than max_chunks intervals have run.
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const int *n_active, int *chunks, int max_chunks,
+                             cudaStream_t st);
 // out[i] = 2 x[i] - E[i] (the Crank-Nicolson step from its backward-Euler half step).
 cudaError_t launch_cn_extrapolate(int64_t N, const double *x, const double *E, double *out, cudaStream_t st);
 // E^n of a Crank-Nicolson operator build of L (null for backward Euler).

@@ -185,6 +185,11 @@ struct Plan {
   std::vector<SolveScalars> h_sc;
   cudaGraphExec_t exec = nullptr;
   int graph_ticks = 0;
+  // use_graph = 2: the whole tick loop as one graph (WHILE node over one
+  // interval of ticks); d_loop counts the intervals run
+  cudaGraphExec_t loop_exec = nullptr;
+  int *d_loop = nullptr;
+  int loop_max = 0;
   bool graph_profiled = false;
   bool profiling = false;
   std::vector<cudaEvent_t> evs;  // chunk start, then kTickEvents per tick of a chunk
@@ -293,6 +298,8 @@ void plan_free(Plan *P) {
   if (!P) return;
   ats_context *ctx = P->ctx;
   if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->loop_exec) cudaGraphExecDestroy(P->loop_exec);
+  dev_free(ctx, P->d_loop);
   for (auto e : P->evs) cudaEventDestroy(e);
   for (auto e : P->poll_ev)
     if (e) cudaEventDestroy(e);
@@ -513,6 +520,51 @@ cudaError_t timed_ticks(Plan *P, const TickArgs &ta, cudaStream_t st, int k, boo
   return cudaStreamWaitEvent(st, P->mark, 0);
 }
 
+// The device-driven loop of use_graph = 2: a graph holding one WHILE node
+// whose body is one interval of ticks followed by the condition kernel.  The
+// handle's default value 1 runs the body once per launch before the first
+// test.  Built once per plan (the interval bound is fixed by the options).
+ats_status plan_ensure_loop(Plan *P, int max_chunks) {
+  if (P->loop_exec && P->loop_max == max_chunks) return ATS_OK;
+  if (P->loop_exec) {
+    cudaGraphExecDestroy(P->loop_exec);
+    P->loop_exec = nullptr;
+  }
+  ats_context *ctx = P->ctx;
+  cudaStream_t st = ctx->stream;
+  if (!P->d_loop) {
+    ats_status s = dev_alloc_t(ctx, 1, &P->d_loop);
+    if (s != ATS_OK) return s;
+    CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
+  }
+  cudaGraph_t g = nullptr, body = nullptr;
+  cudaGraphConditionalHandle h;
+  cudaError_t err = make_while_graph(&g, &body, &h);
+  if (err == cudaSuccess) {
+    err = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+      TickArgs ta = P->targs;
+      ta.cells = nullptr;
+      for (int t = 0; t < P->opts.check_every && err == cudaSuccess; ++t)
+        err = launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, nullptr, true);
+      if (err == cudaSuccess) err = launch_loop_cond(h, P->d_active, P->d_loop, max_chunks, st);
+      cudaGraph_t out = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(st, &out);
+      if (err == cudaSuccess) err = e2;
+    }
+  }
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&P->loop_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    P->loop_exec = nullptr;
+    set_error(std::string("device loop graph: ") + cudaGetErrorString(err));
+    return ATS_ERR_CUDA;
+  }
+  P->loop_max = max_chunks;
+  return ATS_OK;
+}
+
 // Enqueue one poll interval (check_every ticks) on the stream.
 ats_status plan_enqueue_chunk(Plan *P) {
   cudaStream_t st = P->ctx->stream;
@@ -690,6 +742,18 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   const int64_t max_ticks = 2 * ((int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2)) + 2 * P->opts.check_every;
   int64_t ticks = 0;
   ats_status s;
+  bool timed_out = false;
+  // use_graph = 2 (not while profiling: the timing events cannot sit in a
+  // conditional body): the whole loop is one graph launch, ended on the device
+  const bool device_loop = P->opts.use_graph == 2 && !P->profiling;
+  int chunks_run = 0;
+  if (device_loop) {
+    const int max_chunks = (int)std::min<int64_t>((max_ticks + P->opts.check_every - 1) / P->opts.check_every, 1 << 30);
+    if ((s = plan_ensure_loop(P, max_chunks)) != ATS_OK) return s;
+    CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
+    CUDA_TRY(cudaGraphLaunch(P->loop_exec, st));
+    CUDA_TRY(cudaMemcpyAsync(P->h_active, P->d_loop, sizeof(int), cudaMemcpyDeviceToHost, st));  // pinned
+  } else {
   // Keep one poll interval queued ahead of the one being polled, so the GPU
   // never idles on the host's check (not when profiling: the per-tick events
   // must be read back before they are recorded again).  Extra intervals after
@@ -706,7 +770,6 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
     ++pending;
     ticks += P->opts.check_every;
   }
-  bool timed_out = false;
   for (;;) {
     CUDA_TRY(cudaEventSynchronize(P->poll_ev[poll_slot]));
     const int active = P->h_active[poll_slot];
@@ -725,6 +788,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
     ticks += P->opts.check_every;
   }
   (void)pending;
+  }
   // copy-out
   CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->grid, st));
   if (!dev) {
@@ -739,6 +803,12 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, n, P->d_flags, st));
   CUDA_TRY(cudaMemcpyAsync(flags.data(), P->d_flags, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (device_loop) {
+    chunks_run = P->h_active[0];
+    P->ticks = chunks_run * P->opts.check_every;
+    P->launches = 3 * P->ticks + chunks_run;
+    if ((int64_t)chunks_run * P->opts.check_every >= max_ticks) timed_out = true;
+  }
   if (P->profiling) plan_bytes(P, cells, &P->op_bytes, &P->ref_bytes, &P->upd_bytes);
   ats_status first_err = ATS_OK;
   for (int k = 0; k < n; ++k) {

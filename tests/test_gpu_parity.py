@@ -482,3 +482,45 @@ def test_full_size_batch_sampled_parity(ats, ctx):
     B.close()
     for L in levels:
         L.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_device_loop_matches_host_polled(ats, ctx, prec):
+    """A ragged batch and a solo solve with the whole tick loop in one graph
+    (use_graph = 2, a WHILE conditional node) give bitwise the results and
+    statistics of host-polled graphs (use_graph = 1); an iteration cap still
+    ends the loop with NOT_CONVERGED."""
+    rng = np.random.default_rng(61)
+    solves = [W.random_box_solve(rng, o, robin=True) for o in (2, 40, 300, 1100, 9)]
+    P = ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED
+    levels = []
+    for lv, st in solves:
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        levels.append(L)
+    res = {}
+    for g in (1, 2):
+        B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, use_graph=g, check_every=4)
+        xs = [st.E.copy() for _, st in solves]
+        code, stats = B.solve(xs)
+        assert code == 0, stats
+        xs2 = [st.E.copy() for _, st in solves]
+        code, stats2 = B.solve(xs2)  # the graph is reused
+        assert code == 0
+        for a, b in zip(xs, xs2):
+            np.testing.assert_array_equal(a, b)
+        res[g] = (xs, [(s["iterations"], s["refinements"], s["ticks"]) for s in stats])
+        B.close()
+    for a, b in zip(res[1][0], res[2][0]):
+        np.testing.assert_array_equal(a, b)
+    assert res[1][1] == res[2][1]
+    for (lv, st), x in zip(solves, res[2][0]):
+        _, xr = _oracle_solution(lv, st)
+        assert _rel(x, xr) <= PAR
+    lv, st = solves[3]
+    x = st.E.copy()
+    code, s = levels[3].solve(x, tol=1e-14, precision=P, use_graph=2, check_every=4, max_iter=5)
+    assert code == ats.ATS_ERR_NOT_CONVERGED
+    assert s["iterations"] == 5
+    for L in levels:
+        L.close()
