@@ -232,6 +232,23 @@ const uint8_t *level_leaf(const ats_level *L);
 cudaError_t launch_flux_store(int n_face, const int32_t *gather4, const int32_t *fcell, const double *x,
                               const double *K, const double *fK, const double *fE, double h_f, double *store,
                               cudaStream_t st);
+// Result record of a solve enqueued without a host wait (device memory):
+// its final state, its error flag (bad input) and the tick intervals its
+// device-driven loop ran.
+struct DeferredRec {
+  SolveScalars sc;
+  int flag;
+  int chunks;
+};
+// Enqueue one solve of L on the context stream with the whole tick loop as
+// one graph (use_graph = 2 is forced): x_dev is the device initial guess and
+// solution, d_rec (device) receives the result.  Nothing waits on the host.
+// check_every / max_ticks: the loop's interval and tick bound, for
+// deferred_result.
+ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opts *opts, DeferredRec *d_rec,
+                                int *check_every, int64_t *max_ticks);
+// Status and statistics of a deferred solve from a host copy of its record.
+ats_status deferred_result(const DeferredRec &r, int check_every, int64_t max_ticks, ats_solve_stats *out);
 // A graph holding one WHILE conditional node (default value 1, assigned at
 // every launch); body: the node's (empty) body graph to capture into.
 cudaError_t make_while_graph(cudaGraph_t *graph, cudaGraph_t *body, cudaGraphConditionalHandle *handle);

@@ -150,6 +150,13 @@ struct ats_hierarchy {
   int iface_kind = ATS_FACE_DIRICHLET;  // row of the coarse-to-fine faces
   double iface_alpha = 1.0;
   std::vector<HLevel> lv;
+  // use_graph = 2: the level solves of one ats_level_advance are enqueued
+  // without host waits; their result records are read once at the end
+  DeferredRec *d_recs = nullptr;
+  DeferredRec *h_recs = nullptr;  // pinned
+  int rec_cap = 0, n_recs = 0;
+  std::vector<std::pair<int, int64_t>> rec_meta;  // interval, tick bound per record
+  bool deferred = false;
 };
 
 namespace {
@@ -164,6 +171,8 @@ namespace {
   } while (0)
 
 void hierarchy_free(ats_hierarchy *H) {
+  ctx_free(H->ctx, H->d_recs);
+  if (H->h_recs) cudaFreeHost(H->h_recs);
   for (HLevel &h : H->lv) {
     void *ptrs[] = {h.E,  h.E_prev, h.K,   h.fE, h.fK, h.src_rel, h.src_cell, h.r_cell, h.r_child,
                     h.rho, h.T,     h.s,   h.src, h.fcell, h.gather4, h.fstore};
@@ -224,7 +233,19 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   o.mem = ATS_MEM_DEVICE;
   ats_solve_stats st1;
   std::memset(&st1, 0, sizeof(st1));
-  s = ats_solve(h.lvl, nullptr, h.E, &o, &st1);
+  if (H->deferred) {
+    if (H->n_recs >= H->rec_cap) {
+      set_error("ats_level_advance: more solves than planned");
+      return ATS_ERR_INVALID_ARG;
+    }
+    int ce = 0;
+    int64_t mt = 0;
+    s = level_solve_deferred(h.lvl, h.E, &o, H->d_recs + H->n_recs, &ce, &mt);
+    if (s != ATS_OK) return s;
+    H->rec_meta[H->n_recs++] = {ce, mt};
+  } else {
+    s = ats_solve(h.lvl, nullptr, h.E, &o, &st1);
+  }
   if (s == ATS_OK && H->fld) H_TRY(launch_fld_temperature(h.N, level_leaf(h.lvl), h.E, h.rho, h.T, dt, H->k0, st));
   if (s == ATS_OK && stored) {
     if (h.n_face) H_TRY(cudaMemsetAsync(h.fstore, 0, sizeof(double) * h.n_face, st));
@@ -232,7 +253,7 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
       H_TRY(launch_flux_store((int)coarse->n_face, coarse->gather4, h.fcell, h.E, h.K, h.fK, h.fE,
                               0.5 * dt / (h.dx * h.dx), H->lv[l - 1].fstore, st));
   }
-  if (acc) {
+  if (acc && !H->deferred) {
     acc->iterations += st1.iterations;
     acc->refinements += st1.refinements;
     acc->ticks += st1.ticks;
@@ -543,7 +564,54 @@ ats_status ats_level_advance(ats_hierarchy *H, int level, double dt, const ats_s
   std::memset(&acc, 0, sizeof(acc));
   acc.status = ATS_OK;
   cudaSetDevice(ctx_device(H->ctx));
+  // use_graph = 2: every level solve is one graph launch (device-driven tick
+  // loop) and none is waited for; the step's records are read once at the
+  // end, so a failing solve is reported after the whole step has run
+  H->deferred = opts && opts->use_graph == 2;
+  if (H->deferred) {
+    const int n_lv = (int)H->lv.size();
+    const int need = (1 << std::min(30, n_lv - level)) + 1;  // at most 2^(levels below) solves
+    if (need > H->rec_cap) {
+      ctx_free(H->ctx, H->d_recs);
+      H->d_recs = nullptr;
+      if (H->h_recs) cudaFreeHost(H->h_recs);
+      H->h_recs = nullptr;
+      H->rec_cap = 0;
+      void *p = nullptr;
+      ats_status s0 = ctx_alloc(H->ctx, sizeof(DeferredRec) * need, &p);
+      if (s0 != ATS_OK) return s0;
+      H->d_recs = (DeferredRec *)p;
+      if (cudaMallocHost(&H->h_recs, sizeof(DeferredRec) * need) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("ats_level_advance: pinned allocation failed");
+        return ATS_ERR_OOM;
+      }
+      H->rec_cap = need;
+    }
+    H->rec_meta.assign(H->rec_cap, {0, 0});
+    H->n_recs = 0;
+  }
   ats_status s = advance(H, level, dt, 1.0, opts, &acc);
+  if (H->deferred) {
+    cudaStream_t st = ctx_stream(H->ctx);
+    if (H->n_recs > 0)
+      H_TRY(cudaMemcpyAsync(H->h_recs, H->d_recs, sizeof(DeferredRec) * H->n_recs, cudaMemcpyDeviceToHost, st));
+    H_TRY(cudaStreamSynchronize(st));
+    for (int k = 0; k < H->n_recs; ++k) {
+      ats_solve_stats st1;
+      const ats_status r = deferred_result(H->h_recs[k], H->rec_meta[k].first, H->rec_meta[k].second, &st1);
+      acc.iterations += st1.iterations;
+      acc.refinements += st1.refinements;
+      acc.ticks += st1.ticks;
+      acc.r0_norm = std::max(acc.r0_norm, st1.r0_norm);
+      acc.res_norm = std::max(acc.res_norm, st1.res_norm);
+      acc.x_norm = std::max(acc.x_norm, st1.x_norm);
+      acc.err_bound = std::max(acc.err_bound, st1.err_bound);
+      if (acc.status == ATS_OK) acc.status = r;
+      if (s == ATS_OK && r != ATS_OK) s = r;
+    }
+    H->deferred = false;
+  }
   if (stats) *stats = acc;
   return s;
 }

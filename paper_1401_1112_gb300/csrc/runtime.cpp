@@ -659,7 +659,12 @@ void plan_bytes(const Plan *P, const unsigned long long cells[kCellCounters], do
 
 // Run a plan to completion.  x_inout[k] (host or device per opts.mem) or the
 // level's current rhs override is handled by the caller.
-ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
+// Enqueue the start of a run: refresh the solve descriptors of levels
+// rebuilt since the plan was made, copy x in (device x is read in place,
+// host x goes through one staging buffer, one copy per run of levels whose
+// host arrays are contiguous), reset every solve's state and the work lists.
+// off: [n + 1] offsets of the levels in the staging buffer.
+ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off) {
   ats_context *ctx = P->ctx;
   cudaStream_t st = ctx->stream;
   const int n = P->n;
@@ -689,7 +694,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   // buffer, one copy per run of levels whose host arrays are contiguous
   std::vector<const double *> src(n, nullptr);
   std::vector<double *> dst(n, nullptr);
-  std::vector<int64_t> off(n + 1, 0);
+  off.assign(n + 1, 0);
   const bool x0_e = P->opts.x0 == ATS_X0_E_OLD;
   for (int k = 0; k < n; ++k) {
     if (!x_inout || !x_inout[k]) {
@@ -735,11 +740,28 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   P->op_ms = P->ref_ms = P->upd_ms = 0.0;
   P->launches = 0;
   P->ticks = 0;
+  return ATS_OK;
+}
+
+// The tick bound of a run: every solve ends within it (an inner pass's
+// convergence is seen one tick late: two ticks per pass boundary).
+int64_t plan_max_ticks(const Plan *P) {
+  return 2 * ((int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2)) + 2 * P->opts.check_every;
+}
+
+ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
+  ats_context *ctx = P->ctx;
+  cudaStream_t st = ctx->stream;
+  const int n = P->n;
+  const bool dev = (P->opts.mem == ATS_MEM_DEVICE);
+  std::vector<int64_t> off;
+  {
+    ats_status s0 = plan_begin(P, x_inout, off);
+    if (s0 != ATS_OK) return s0;
+  }
 
   // host guard: every solve ends within a bounded number of ticks
-  // (an inner pass's convergence is seen one tick late: two ticks per pass
-  // boundary)
-  const int64_t max_ticks = 2 * ((int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2)) + 2 * P->opts.check_every;
+  const int64_t max_ticks = plan_max_ticks(P);
   int64_t ticks = 0;
   ats_status s;
   bool timed_out = false;
@@ -1270,6 +1292,77 @@ ats_status ats_level_apply(ats_level *L, const double *x, double *y, int mem) {
   }
   return ATS_OK;
 }
+
+ats_status ats_solve(ats_level *L, const double *rhs, double *x_inout, const ats_solve_opts *opts,
+                     ats_solve_stats *stats);
+}  // extern "C"
+
+namespace ats {
+
+ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opts *opts, DeferredRec *d_rec,
+                                int *check_every, int64_t *max_ticks) {
+  if (!L || !x_dev || !d_rec || !L->built) {
+    set_error("deferred solve: bad argument or level operator not built");
+    return ATS_ERR_INVALID_ARG;
+  }
+  ats_solve_opts o = normalize(opts);
+  o.use_graph = 2;
+  o.mem = ATS_MEM_DEVICE;
+  ats_context *ctx = L->ctx;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  ats_status s;
+  if (L->solo && (std::memcmp(&L->solo->opts, &o, sizeof(o)) != 0 ||
+                  L->solo->fp64 != (o.precision == ATS_PREC_FP64))) {
+    plan_free(L->solo);
+    L->solo = nullptr;
+  }
+  if (!L->solo) {
+    ats_level *arr[1] = {L};
+    if ((s = plan_create(ctx, arr, 1, &o, &L->solo)) != ATS_OK) return s;
+  }
+  Plan *P = L->solo;
+  const bool prof = P->profiling;
+  P->profiling = false;
+  std::vector<int64_t> off;
+  double *xs[1] = {x_dev};
+  s = plan_begin(P, xs, off);
+  const int64_t mt = plan_max_ticks(P);
+  const int max_chunks = (int)std::min<int64_t>((mt + o.check_every - 1) / o.check_every, 1 << 30);
+  if (s == ATS_OK) s = plan_ensure_loop(P, max_chunks);
+  P->profiling = prof;
+  if (s != ATS_OK) return s;
+  CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
+  CUDA_TRY(cudaGraphLaunch(P->loop_exec, st));
+  CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->grid, st));
+  CUDA_TRY(cudaMemcpyAsync(&d_rec->sc, P->d_final, sizeof(SolveScalars), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, 1, &d_rec->flag, st));
+  CUDA_TRY(cudaMemcpyAsync(&d_rec->chunks, P->d_loop, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  *check_every = o.check_every;
+  *max_ticks = mt;
+  return ATS_OK;
+}
+
+ats_status deferred_result(const DeferredRec &r, int check_every, int64_t max_ticks, ats_solve_stats *out) {
+  int status = r.sc.status;
+  if (r.flag) status = ATS_ERR_BAD_INPUT;
+  else if ((int64_t)r.chunks * check_every >= max_ticks && r.sc.phase != kDone) status = ATS_ERR_TIMEOUT;
+  if (out) {
+    out->status = status;
+    out->iterations = r.sc.iters;
+    out->refinements = r.sc.refines;
+    out->ticks = r.sc.ticks;
+    out->r0_norm = r.sc.r0;
+    out->res_norm = r.sc.rnorm;
+    out->x_norm = r.sc.xnorm;
+    out->err_bound = r.sc.xnorm > 0.0 ? r.sc.rnorm / r.sc.xnorm : 0.0;
+  }
+  return status;
+}
+
+}  // namespace ats
+
+extern "C" {
 
 ats_status ats_solve(ats_level *L, const double *rhs, double *x_inout, const ats_solve_opts *opts,
                      ats_solve_stats *stats) {

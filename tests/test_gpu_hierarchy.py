@@ -92,21 +92,35 @@ def test_two_level_heat_full_size(ats, ctx):
 
 def test_device_loop_steps_are_bitwise_the_host_polled_ones(ats, ctx):
     """use_graph = 2 runs every level solve's tick loop as one graph (a WHILE
-    conditional node ended on the device); the ticks are the same as with
-    host polling (0: direct launches, 1: one graph per interval), so the
-    hierarchy states are bitwise equal after two coarse steps."""
+    conditional node ended on the device) and enqueues the step's solves
+    without host waits; the ticks are the same as with host polling (0:
+    direct launches, 1: one graph per interval), so the hierarchy states and
+    the step statistics are bitwise equal after two coarse steps, in both
+    orders.  A failing solve is still reported (after the whole step)."""
     levels, states, dt = W.random_hierarchy(4, n0=8, n_levels=3)
-    out = []
-    for use_graph, check in ((0, 16), (1, 16), (2, 16), (2, 3)):
-        H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
-        for l, (E, K) in enumerate(states):
-            H.set_state(l, E, K)
-        for _ in range(2):
-            code, st = H.advance(0, dt, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
-                                 use_graph=use_graph, check_every=check)
-            assert code == 0, st
-        out.append([H.state(l).copy() for l in range(len(levels))])
-        H.close()
-    for other in out[1:]:
-        for a, b in zip(out[0], other):
-            np.testing.assert_array_equal(a, b)
+    for order in (ats.ATS_ORDER_FINE_FIRST, ats.ATS_ORDER_COARSE_FIRST):
+        out, its = [], []
+        for use_graph, check in ((0, 16), (1, 16), (2, 16), (2, 3)):
+            H = ats.Hierarchy(ctx, levels, order)
+            for l, (E, K) in enumerate(states):
+                H.set_state(l, E, K)
+            step_its = []
+            for _ in range(2):
+                code, st = H.advance(0, dt, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED,
+                                     precision=ats.ATS_PREC_MIXED, use_graph=use_graph, check_every=check)
+                assert code == 0, st
+                step_its.append((st["iterations"], st["refinements"], st["ticks"]))
+            out.append([H.state(l).copy() for l in range(len(levels))])
+            its.append(step_its)
+            H.close()
+        for other, other_its in zip(out[1:], its[1:]):
+            assert other_its == its[0]
+            for a, b in zip(out[0], other):
+                np.testing.assert_array_equal(a, b)
+    H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
+    for l, (E, K) in enumerate(states):
+        H.set_state(l, E, K)
+    code, st = H.advance(0, dt, tol=1e-14, precision=ats.ATS_PREC_FP64, use_graph=2, max_iter=2)
+    assert code == ats.ATS_ERR_NOT_CONVERGED
+    assert st["status"] == ats.ATS_ERR_NOT_CONVERGED
+    H.close()
