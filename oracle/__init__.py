@@ -13,7 +13,11 @@ Contents
   * ``spectral`` -- DCT-II closed-form solve for constant K with zero-flux
     walls (the exact discrete solution, independent of CG).
   * ``fld``      -- flux-limited-diffusion coefficients and the linearised
-    gas-radiation coupling (Sect. 2.1 with the readings listed in the design doc).
+    gas-radiation coupling (Sect. 2.1; the paper leaves the limiter and the
+    coupling to its Paper I, and the module docstring states the forms taken).
+  * ``equilibrium`` -- the equilibrium test with a nonlinear diffusion
+    coefficient (Sect. 4.2) on uniform grids: closed form, lagged steps to
+    the steady state, the paper's L2 norm.
   * ``driver``   -- the two-level / multi-level adaptive time-stepping driver
     (Sect. 2.2 and Sect. 3.3), level by level, on top of assemble + pcg.
 """

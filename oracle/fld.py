@@ -4,7 +4,7 @@ coupling (TEST INFRASTRUCTURE ONLY).
 Sect. 2.1: the radiative energy diffuses with K = c lambda / (rho kappa_R)
 and exchanges energy with the gas through kappa_P rho c (a_R T^4 - E_r).  The
 limiter lambda and the linearisation are in the paper's Paper I, not in this
-paper; the readings used (stated in the design doc) are:
+paper; the readings used are:
   * Levermore-Pomraning limiter lambda(R) = (2 + R) / (6 + 3R + R^2),
     R = |grad E| / (rho kappa_R E), lambda -> 1/3 for R -> 0;
   * kappa_R = kappa_P = k0 rho / T (per unit mass), so rho kappa_R = k0 rho^2 / T;

@@ -194,8 +194,24 @@ def gaussian(xyz: np.ndarray, sigma: float = 0.05, floor: float = 1e-3) -> np.nd
 
 
 # ---------------------------------------------------------------------------
-# The five workload configurations (sizes and recipes as stated in the design doc)
+# The five workload configurations: sizes and recipes
 # ---------------------------------------------------------------------------
+
+def equilibrium_column(n: int, E_left: float = 4.0, E_right: float = 0.5):
+    """The equilibrium test's set-up (Sect. 4.2) on a uniform grid of n cells
+    in x over [0, 1] (n even): a column of n/2 octs, one oct thick in y and z
+    with zero-flux walls there (the problem stays one-dimensional);
+    Dirichlet walls at x = 0 and x = 1 holding E_left / E_right in the ghost
+    cells (relation REL_SAME: ghost centre one cell width away); the initial
+    state is the step E_left for x < 0.5, E_right above.  Returns (level,
+    E_init, face_E per wall descriptor, x of every cell centre)."""
+    assert n % 2 == 0 and n >= 2
+    lv = box_level(n // 2, 1, 1, 1.0 / n, walls=[(DIRICHLET, 1.0), (DIRICHLET, 1.0), None, None, None, None])
+    x = (lv.cell_xyz()[:, 0] + 0.5) / n
+    E = np.where(x < 0.5, E_left, E_right).astype(np.float64)
+    face_E = np.where(lv.face_dir == 0, E_left, E_right).astype(np.float64)
+    return lv, E, face_E, x
+
 
 def config1(n: int = 32, K: float = 1.0, cfl: float = 10.0):
     """Single-level uniform n^3 box on [-1/2, 1/2]^3, constant K, one backward-
