@@ -406,6 +406,10 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_amr:
         amr = run_amr_interfaces(ats, ctx)
 
+    equilibrium = None
+    if rank == 0 and not args.no_equilibrium:
+        equilibrium = run_equilibrium(ats, ctx)
+
     # the same batch integrated with Crank-Nicolson (half-step backward-Euler
     # operator, E^{n+1} = 2 x' - E^n in the copy-out), device-resident inputs
     cn = None
@@ -464,6 +468,7 @@ def run_ours(args, rank, world, local):
         "serve": serve,
         "amr_interfaces": amr,
         "crank_nicolson": cn,
+        "equilibrium_1d": equilibrium,
         "solve_stats": {"iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
                         "refinements_mean": float(np.mean(refs)),
                         "max_err_bound": float(np.max(bounds)), "layout_s": round(layout_s, 3)},
@@ -505,6 +510,25 @@ def run_amr_interfaces(ats, ctx, coarse_steps=3, use_graph=2, check_every=16):
                      "energy_change_per_step": float((e1 - e0) / e0 / coarse_steps)}
         H.close()
     return out
+
+
+def run_equilibrium(ats, ctx):
+    """The equilibrium test with a nonlinear diffusion coefficient (Sect.
+    4.2) on uniform grids of 8..128 cells: steps to the steady state (lagged
+    K = E^1.5 evaluated on the device, mixed precision, certified 5e-11 per
+    step, one graph per solve), the paper's L2 norm against the closed form,
+    and its ratio per halving of dx (the paper: close to second order)."""
+    from paper_1401_1112_gb300 import equilibrium as G
+
+    rows = []
+    for n in (8, 16, 32, 64, 128):
+        lv, E, fE, _ = W.equilibrium_column(n)
+        Es, steps, ok, s_step = G.relax(ctx, lv, E, fE)
+        rows.append({"cells_x": n, "steps": steps, "converged": bool(ok), "ms_per_step": round(s_step * 1e3, 3),
+                     "l2": G.l2_error(lv, Es)})
+    ratios = [round(rows[i]["l2"] / rows[i + 1]["l2"], 3) for i in range(len(rows) - 1)]
+    return {"workload": "1D column, E = 4 / 0.5 Dirichlet walls, K = E^1.5 lagged, dt = 0.1, to a step change "
+                        "< 1e-10", "grids": rows, "l2_ratio_per_halving": ratios}
 
 
 def run_serve(args, ats, device):
@@ -720,6 +744,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-cn", action="store_true")
+    ap.add_argument("--no-equilibrium", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-max-cells", type=int, default=128 ** 3)

@@ -192,6 +192,14 @@ ats_status ats_level_get_rhs(ats_level *lvl, double *b, int mem);
 /* y = (I + dt A) x in FP64 for a built level (x, y: [N], mem = host/device). */
 ats_status ats_level_apply(ats_level *lvl, const double *x, double *y, int mem);
 
+/* Cell coefficient model of the nonlinear equilibrium test (Sect. 4.2):
+ * K[i] = K0 * E[i]^p for i < n, on the context's stream (not waited for).
+ * E, K: device arrays of n FP64 values (may alias).  The lagged-coefficient
+ * step builds the level operator from K(E^n).  E[i] <= 0 with a non-integer
+ * p gives NaN, which the next operator build reports as ATS_ERR_BAD_INPUT.
+ * Errors: ATS_ERR_INVALID_ARG (NULL context or arrays, n < 0), ATS_ERR_CUDA. */
+ats_status ats_power_law_K(ats_context *ctx, int64_t n, const double *E, double K0, double p, double *K);
+
 /* ---- solve (Sect. 3.3.4: diagonal-preconditioned CG) ---------------------- */
 /* Solve (I + dt A) x = b for one built level.  rhs_or_null: NULL = the b of
  * ats_level_build_operator, else [N] replaces it for this call.  x_inout:

@@ -138,6 +138,7 @@ _SIGS = [
     ("ats_batch_build_operators", ctypes.c_int, [P, ctypes.POINTER(ats_coef_desc)]),
     ("ats_batch_set_profiling", ctypes.c_int, [P, ctypes.c_int]),
     ("ats_batch_kernel_stats", ctypes.c_int, [P, ctypes.POINTER(ats_kernel_stats)]),
+    ("ats_power_law_K", ctypes.c_int, [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_double, P]),
     ("ats_batch_autotune", ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ats_tune_result)]),
@@ -431,6 +432,17 @@ def ats_batch_autotune(batch, xs: Sequence, tiles: Sequence[int] = (), checks: S
     return {name: getattr(r, name) for name, _ in r._fields_}
 
 
+def ats_power_law_K(ctx, E, K0, p, K):
+    """K = K0 E^p on the device (E, K: CUDA tensors of float64)."""
+    for t in (E, K):
+        if _mem_of(t) != ATS_MEM_DEVICE:
+            raise ValueError("ats_power_law_K takes device arrays")
+    n = int(E.numel())
+    if int(K.numel()) != n:
+        raise ValueError("E and K differ in size")
+    return _check(lib().ats_power_law_K(ctx, n, _ptr(E), float(K0), float(p), _ptr(K)), "ats_power_law_K")
+
+
 def ats_default_opts() -> ats_solve_opts:
     o = ats_solve_opts()
     lib().ats_default_opts(ctypes.byref(o))
@@ -606,6 +618,7 @@ def ats_server_stats(server):
 
 class Context:
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream: Optional[int] = None):
+        self.device = device
         self.handle = ats_context_create(device, mem_budget_bytes)
         if stream is not None:
             ats_context_set_stream(self.handle, stream)

@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libats.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["kernels.cu", "runtime.cpp", "layout.cpp", "hierarchy.cpp", "server.cpp", "noalloc.cu", "loop.cu"]
+SOURCES = ["kernels.cu", "runtime.cpp", "layout.cpp", "hierarchy.cpp", "server.cpp", "noalloc.cu", "loop.cu",
+           "coef_models.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
