@@ -276,8 +276,12 @@ ats_status ats_batch_autotune(ats_batch *batch, double *const *x_inout, const in
  * with the restriction (mean of the 8 children) of that cell (coarse-to-fine,
  * Sect. 3.3.2, factor 1); a leaf next to a coarser leaf gets a Dirichlet face
  * with the coarse value (fine-to-coarse, Sect. 3.3.1, factor 2/3); faces on
- * the base level's outer boundary are zero-flux walls.  2:1 balance is
- * required (ATS_ERR_INVALID_ARG otherwise). */
+ * the domain's outer boundary (no cell beyond them at any level) are
+ * zero-flux walls unless wall_kind makes a side Dirichlet: then every leaf of
+ * every level on that side gets a Dirichlet face holding wall_E in a ghost
+ * cell one cell width of its level away (relation ATS_REL_SAME), with ghost
+ * coefficient wall_K.  2:1 balance is required (ATS_ERR_INVALID_ARG
+ * otherwise). */
 typedef struct ats_hierarchy ats_hierarchy;
 #define ATS_ORDER_FINE_FIRST 0   /* the paper: finer levels first, coarse value held at E^n   */
 #define ATS_ORDER_COARSE_FIRST 1 /* coarse step first, fine ghosts linear in time over it   */
@@ -285,6 +289,10 @@ typedef struct {
   int n_levels;
   const ats_level_desc *levels; /* per level: n_oct, oct_xyz, leaf_mask, dx; face fields ignored */
   int order;                    /* ATS_ORDER_*                                                   */
+  const int8_t *wall_kind;      /* [6] or NULL (all zero flux): per side -x,+x,-y,+y,-z,+z,     */
+                                /* -1 zero flux or ATS_FACE_DIRICHLET                            */
+  const double *wall_E;         /* [6] ghost value of each Dirichlet side (host)                 */
+  const double *wall_K;         /* [6] ghost diffusion coefficient of each Dirichlet side, > 0   */
 } ats_hierarchy_desc;
 ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc, ats_hierarchy **out);
 ats_status ats_hierarchy_destroy(ats_hierarchy *h);
@@ -322,6 +330,12 @@ ats_status ats_hierarchy_set_state(ats_hierarchy *h, int level, const double *E,
  * sigma mu), source s a_R T^4; after the solve T = T + sigma (E - a_R T^4) /
  * (rho c_v (1 + sigma mu)).  Units c = a_R = c_v = 1.  K of the level is set
  * from the current E immediately. */
+/* Power-law coefficient mode (the nonlinear equilibrium test, Sect. 4.2):
+ * before every level solve, K = K0 E^a on the level's leaf cells from its
+ * E^n (refined cells keep the mean of their children's K), held over the
+ * step.  K0 > 0; a = 0 gives the constant K0.  Not with the radiation-matter
+ * mode (ATS_ERR_INVALID_ARG). */
+ats_status ats_hierarchy_set_power_law(ats_hierarchy *h, double K0, double a);
 ats_status ats_hierarchy_set_fld(ats_hierarchy *h, int level, const double *rho, const double *T, double k0,
                                  int mem);
 ats_status ats_hierarchy_get_temperature(ats_hierarchy *h, int level, double *T, int mem);
@@ -337,8 +351,9 @@ ats_status ats_level_advance(ats_hierarchy *h, int level, double dt, const ats_s
                              ats_solve_stats *stats);
 /* Host-only (no device): the interface faces the hierarchy derives for one
  * level.  Call with NULL arrays to get n_face first.  rel is ATS_REL_FINER
- * (src_cell = refined cell of the same level) or ATS_REL_COARSER (src_cell =
- * leaf of level - 1). */
+ * (src_cell = refined cell of the same level), ATS_REL_COARSER (src_cell =
+ * leaf of level - 1) or, on a Dirichlet side of the domain, ATS_REL_SAME
+ * (src_cell = the side, 0..5). */
 ats_status ats_hierarchy_plan_faces(const ats_hierarchy_desc *desc, int level, int64_t *n_face,
                                     int32_t *face_cell, int8_t *face_dir, int8_t *face_rel,
                                     int32_t *src_cell);

@@ -27,12 +27,17 @@ two.  In the units of the level system (energy per unit cell volume over the
 step, the reading of the Neumann sign), a fine face f next to coarse cell c
 moves C_f (E_f^{k} - E_c) V_f / V_c = C_f (E_f^k - E_c) / 8 into c during
 fine step k, with C_f = (2/3) dt_f/(2 dx_f^2) (K_f + K_c).
+
+Domain sides: zero flux, or Dirichlet with a ghost value E_w and ghost
+coefficient K_w one cell width of the level away (the leaves of every level
+on that side).  Power-law coefficient (the equilibrium test of Sect. 4.2):
+K = K0 E^a on the leaves from E^n before every level solve.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import DIRICHLET, NEUMANN, REL_COARSER, REL_FINER, ROBIN, STOP_CERTIFIED, assemble, pcg
+from . import DIRICHLET, NEUMANN, REL_COARSER, REL_FINER, REL_SAME, ROBIN, STOP_CERTIFIED, assemble, pcg
 from . import fld as fldmod
 
 AX = (0, 0, 1, 1, 2, 2)
@@ -54,17 +59,22 @@ class _Level:
 
 
 class Hierarchy:
-    def __init__(self, levels, states, order="fine_first", fld=None, interface="dirichlet", alpha=1.0):
+    def __init__(self, levels, states, order="fine_first", fld=None, interface="dirichlet", alpha=1.0, walls=None,
+                 power_law=None):
         """states: per level (E, K).  fld: None, or (per-level rho, per-level T,
         k0) for the radiation-matter mode (K, s, src from the gas state before
         every level solve, T updated after it).  interface: the row of the
         coarse-to-fine faces, "dirichlet", "neumann" (stored flux) or "robin"
-        (weight alpha on the Dirichlet part)."""
+        (weight alpha on the Dirichlet part).  walls: None (zero-flux domain)
+        or {side: (E_w, K_w)} for the Dirichlet sides (0..5 = -x, +x, -y, +y,
+        -z, +z).  power_law: None or (K0, a)."""
         if interface not in ("dirichlet", "neumann", "robin"):
             raise ValueError(interface)
         if interface != "dirichlet" and order != "fine_first":
             raise ValueError("stored interface fluxes need the fine-first order")
         self.interface = interface
+        self.walls = dict(walls or {})
+        self.power_law = power_law
         self.alpha = {"dirichlet": 1.0, "neumann": 0.0, "robin": float(alpha)}[interface]
         self.L = [_Level(d) for d in levels]
         self.E = [np.array(e, dtype=np.float64) for e, _ in states]
@@ -115,12 +125,23 @@ class Hierarchy:
                         out.append((cell, d, REL_FINER, j))
                     continue
                 if l == 0:
+                    if d in self.walls:
+                        out.append((cell, d, REL_SAME, d))
                     continue
                 qc = tuple(v // 2 for v in q)   # Python floor division
                 jc = self.L[l - 1].cell_of.get(qc)
                 if jc is not None:
                     assert self.L[l - 1].is_leaf[jc]
                     out.append((cell, d, REL_COARSER, jc))
+                    continue
+                # no cell beyond the face at any coarser level: the domain side
+                r, inside = qc, False
+                for k in range(l - 2, -1, -1):
+                    r = tuple(v // 2 for v in r)
+                    inside = inside or r in self.L[k].cell_of
+                assert not inside, "2:1 balance violated"
+                if d in self.walls:
+                    out.append((cell, d, REL_SAME, d))
         return out
 
     def restrict(self, l):
@@ -143,6 +164,10 @@ class Hierarchy:
             self.K[l][leaf] = Kf[leaf]
             s_shift = np.where(leaf, s_shift, 0.0)
             src = np.where(leaf, src, 0.0)
+        if self.power_law is not None:
+            leaf = desc.leaf_cells()
+            K0, a = self.power_law
+            self.K[l][leaf] = K0 * self.E[l][leaf] ** a
         f = self.faces[l]
         fcell = np.array([a for a, _, _, _ in f], dtype=np.int32)
         fdir = np.array([b for _, b, _, _ in f], dtype=np.int8)
@@ -153,6 +178,8 @@ class Hierarchy:
             if rel == REL_FINER:
                 fE[k] = self.E[l][j]
                 fK[k] = self.K[l][j]
+            elif rel == REL_SAME:
+                fE[k], fK[k] = self.walls[j]
             else:
                 if self.order == "fine_first":
                     fE[k] = self.E[l - 1][j]       # coarse held at E^n

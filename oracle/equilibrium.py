@@ -19,6 +19,11 @@ Readings:
     over the cells of the one-dimensional profile, N_eff the number of cells
     at the finest resolution.
 
+On an AMR hierarchy (the paper's adaptive-time-step runs) the same steps go
+through the level driver (``oracle.driver``): fine levels first, each level
+with the power-law coefficient from its own E^n, Dirichlet sides on every
+level that touches them.
+
 The oracle takes time steps until the steady state is reached: each step
 assembles the level matrix with the lagged K and solves it with the oracle's
 PCG.  The fixed point of the lagged steps is the discrete nonlinear steady
@@ -81,3 +86,39 @@ def l2_error(level, E, n_eff=None):
     x = (ix + 0.5) * dx
     n_eff = len(ix) if n_eff is None else n_eff
     return float(np.sqrt(np.sum(((e - analytic(x)) * dx) ** 2) / n_eff))
+
+
+def relax_amr(levels, E_init, walls, K0=1.0, a=A_EXP, dt=0.1, tol_step=1e-10, max_steps=2000, tol=5e-11):
+    """Coarse steps of dt (the finer levels take their substeps, fine first)
+    until the largest relative change of the leaf values over a coarse step
+    is below tol_step.  walls: {side: E_wall}.  Returns (per-level E, steps,
+    converged)."""
+    from .driver import Hierarchy
+
+    states = [(np.array(e, dtype=np.float64), power_law_K(e, K0, a)) for e in E_init]
+    H = Hierarchy(levels, states, order="fine_first",
+                  walls={side: (e, float(power_law_K(e, K0, a))) for side, e in walls.items()}, power_law=(K0, a))
+    leaves = [lv.leaf_cells() for lv in levels]
+    prev = [H.state(l)[leaves[l]] for l in range(len(levels))]
+    for step in range(1, max_steps + 1):
+        H.advance(0, dt, tol=tol)
+        cur = [H.state(l)[leaves[l]] for l in range(len(levels))]
+        scale = max(float(np.max(np.abs(c))) for c in cur)
+        change = max(float(np.max(np.abs(c - p))) for c, p in zip(cur, prev)) / scale
+        prev = cur
+        if change < tol_step:
+            return [H.state(l) for l in range(len(levels))], step, True
+    return [H.state(l) for l in range(len(levels))], max_steps, False
+
+
+def l2_error_amr(levels, E_levels, n_eff):
+    """The paper's L2 norm over the leaf cells of the y = z = 0 row of every
+    level, dx_i the cell's own width, N_eff the cells at the finest
+    resolution."""
+    tot = 0.0
+    for lv, E in zip(levels, E_levels):
+        xyz = lv.cell_xyz()
+        row = (xyz[:, 1] == 0) & (xyz[:, 2] == 0) & lv.leaf_cells()
+        x = (xyz[row, 0] + 0.5) * lv.dx
+        tot += float(np.sum(((np.asarray(E)[row] - analytic(x)) * lv.dx) ** 2))
+    return float(np.sqrt(tot / n_eff))

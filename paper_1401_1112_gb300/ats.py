@@ -69,7 +69,8 @@ class ats_solve_opts(ctypes.Structure):
 
 
 class ats_hierarchy_desc(ctypes.Structure):
-    _fields_ = [("n_levels", ctypes.c_int), ("levels", ctypes.POINTER(ats_level_desc)), ("order", ctypes.c_int)]
+    _fields_ = [("n_levels", ctypes.c_int), ("levels", ctypes.POINTER(ats_level_desc)), ("order", ctypes.c_int),
+                ("wall_kind", P), ("wall_E", P), ("wall_K", P)]
 
 
 ATS_ORDER_FINE_FIRST, ATS_ORDER_COARSE_FIRST = 0, 1
@@ -156,6 +157,7 @@ _SIGS = [
                                          ctypes.POINTER(ats_solve_stats)]),
     ("ats_hierarchy_set_fld", ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int]),
     ("ats_hierarchy_get_temperature", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
+    ("ats_hierarchy_set_power_law", ctypes.c_int, [P, ctypes.c_double, ctypes.c_double]),
     ("ats_hierarchy_plan_faces", ctypes.c_int, [ctypes.POINTER(ats_hierarchy_desc), ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_int64), P, P, P, P]),
     ("ats_server_create", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(ats_server_opts),
@@ -479,19 +481,33 @@ def ats_solve_noalloc(device, stream, n_oct, nbr, K, xd, h, b, x, tol=1e-10, max
     return code, st.as_dict()
 
 
-def _hierarchy_desc(levels, order, keep):
+def _hierarchy_desc(levels, order, keep, walls=None):
+    """walls: None (zero-flux domain) or {side: (E_ghost, K_ghost)} for the
+    Dirichlet sides (0..5 = -x, +x, -y, +y, -z, +z)."""
     arr = (ats_level_desc * len(levels))(*[_level_desc(l, keep) for l in levels])
     keep.append(arr)
     d = ats_hierarchy_desc()
     d.n_levels = len(levels)
     d.levels = ctypes.cast(arr, ctypes.POINTER(ats_level_desc))
     d.order = order
+    if walls:
+        kind = np.full(6, -1, dtype=np.int8)
+        wE = np.zeros(6)
+        wK = np.ones(6)
+        for side, (e, k) in walls.items():
+            kind[side] = ATS_FACE_DIRICHLET
+            wE[side] = e
+            wK[side] = k
+        keep += [kind, wE, wK]
+        d.wall_kind = kind.ctypes.data_as(P)
+        d.wall_E = wE.ctypes.data_as(P)
+        d.wall_K = wK.ctypes.data_as(P)
     return d
 
 
-def ats_hierarchy_create(ctx, levels, order=ATS_ORDER_FINE_FIRST):
+def ats_hierarchy_create(ctx, levels, order=ATS_ORDER_FINE_FIRST, walls=None):
     keep = []
-    d = _hierarchy_desc(levels, order, keep)
+    d = _hierarchy_desc(levels, order, keep, walls)
     h = P()
     _check(lib().ats_hierarchy_create(ctx, ctypes.byref(d), ctypes.byref(h)), "ats_hierarchy_create")
     return h
@@ -499,6 +515,10 @@ def ats_hierarchy_create(ctx, levels, order=ATS_ORDER_FINE_FIRST):
 
 def ats_hierarchy_destroy(h):
     return _check(lib().ats_hierarchy_destroy(h), "ats_hierarchy_destroy")
+
+
+def ats_hierarchy_set_power_law(h, K0, a):
+    return _check(lib().ats_hierarchy_set_power_law(h, float(K0), float(a)), "ats_hierarchy_set_power_law")
 
 
 def ats_hierarchy_set_interface(h, kind, alpha=1.0):
@@ -542,11 +562,11 @@ def ats_level_advance(h, level, dt, opts: Optional[ats_solve_opts] = None):
     return code, st.as_dict()
 
 
-def ats_hierarchy_plan_faces(levels, level, order=ATS_ORDER_FINE_FIRST):
+def ats_hierarchy_plan_faces(levels, level, order=ATS_ORDER_FINE_FIRST, walls=None):
     """Host-only: (cell, dir, rel, src_cell) arrays of the interface faces the
     library derives for one level."""
     keep = []
-    d = _hierarchy_desc(levels, order, keep)
+    d = _hierarchy_desc(levels, order, keep, walls)
     n = ctypes.c_int64()
     _check(lib().ats_hierarchy_plan_faces(ctypes.byref(d), level, ctypes.byref(n), None, None, None, None),
            "ats_hierarchy_plan_faces")
@@ -673,10 +693,13 @@ class Level:
 
 
 class Hierarchy:
-    def __init__(self, ctx: Context, levels, order=ATS_ORDER_FINE_FIRST):
+    def __init__(self, ctx: Context, levels, order=ATS_ORDER_FINE_FIRST, walls=None):
         self.ctx = ctx
         self.levels = levels
-        self.handle = ats_hierarchy_create(ctx.handle, levels, order)
+        self.handle = ats_hierarchy_create(ctx.handle, levels, order, walls)
+
+    def set_power_law(self, K0, a):
+        ats_hierarchy_set_power_law(self.handle, K0, a)
 
     def set_state(self, level, E, K):
         ats_hierarchy_set_state(self.handle, level, E, K)

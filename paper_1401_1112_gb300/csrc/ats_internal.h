@@ -267,7 +267,7 @@ cudaError_t launch_restrict(int n, const int32_t *cell, const int32_t *child, co
                             double *Ec, double *Kc, cudaStream_t st);
 cudaError_t launch_gather_faces(int n_face, const int8_t *src_rel, const int32_t *src_cell, const double *E_same,
                                 const double *K_same, const double *Ec_old, const double *Ec_new,
-                                const double *K_coarse, double theta, double *fE, double *fK, cudaStream_t st);
+                                const double *K_coarse, double theta, double *fE, double *fK, const double *wall, cudaStream_t st);
 
 // ---- layout (layout.cpp) ----
 struct Layout {
@@ -302,6 +302,12 @@ struct LevelFaces {
   std::vector<int32_t> restrict_cell;   // refined cells of this level ...
   std::vector<int32_t> restrict_child;  // ... and their child oct at level l + 1
 };
-std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, LevelFaces &out);
+// wall_kind: [6] or NULL (see ats_hierarchy_desc).
+std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, LevelFaces &out,
+                             const int8_t *wall_kind);
+// K = K0 E^a on the leaf cells of a level (all cells when leaf is NULL; bit c
+// of leaf[o] marks cell 8 o + c); the other cells keep K.
+cudaError_t launch_power_law_K(int64_t n_cell, const uint8_t *leaf, const double *E, double K0, double a,
+                               double *K, cudaStream_t st);
 
 }  // namespace ats

@@ -15,7 +15,23 @@ __global__ void k_power_law_K(int64_t n, const double *__restrict__ E, double K0
   if (i < n) K[i] = K0 * pow(E[i], p);
 }
 
+__global__ void k_power_law_K_leaf(int64_t n, const uint8_t *__restrict__ leaf, const double *__restrict__ E, double K0,
+                                   double p, double *__restrict__ K) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (leaf && !((leaf[i >> 3] >> (i & 7)) & 1)) return;
+  K[i] = K0 * pow(E[i], p);
+}
+
 }  // namespace
+
+cudaError_t launch_power_law_K(int64_t n_cell, const uint8_t *leaf, const double *E, double K0, double a, double *K,
+                               cudaStream_t st) {
+  if (n_cell <= 0) return cudaSuccess;
+  k_power_law_K_leaf<<<(unsigned)((n_cell + 255) / 256), 256, 0, st>>>(n_cell, leaf, E, K0, a, K);
+  return cudaGetLastError();
+}
+
 }  // namespace ats
 
 extern "C" {

@@ -59,8 +59,21 @@ constexpr int kSg[6] = {-1, 1, -1, 1, -1, 1};
 
 namespace ats {
 
-std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, LevelFaces &out) {
+std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, LevelFaces &out,
+                             const int8_t *wall_kind) {
   if (l < 0 || l >= n_levels) return "level out of range";
+  if (wall_kind)
+    for (int k = 0; k < 6; ++k)
+      if (wall_kind[k] != -1 && wall_kind[k] != ATS_FACE_DIRICHLET) return "wall_kind: -1 or ATS_FACE_DIRICHLET";
+  // a face on the domain boundary: a Dirichlet side gets a face with the
+  // side's ghost (src_cell = side), a zero-flux side nothing
+  auto wall = [&](int64_t cell, int dir) {
+    if (!wall_kind || wall_kind[dir] != ATS_FACE_DIRICHLET) return;
+    out.cell.push_back((int32_t)cell);
+    out.dir.push_back((int8_t)dir);
+    out.rel.push_back((int8_t)ATS_REL_SAME);
+    out.src_cell.push_back((int32_t)dir);
+  };
   std::vector<LevelIndex> idx;
   idx.reserve(n_levels);
   for (int k = 0; k < n_levels; ++k) {
@@ -87,7 +100,10 @@ std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, 
           out.src_cell.push_back((int32_t)j);
           continue;
         }
-        if (l == 0) continue;  // outside the base level: domain wall (zero flux)
+        if (l == 0) {  // outside the base level: the domain boundary
+          wall(cell, dir);
+          continue;
+        }
         const int64_t m[3] = {floor_div2(q[0]), floor_div2(q[1]), floor_div2(q[2])};
         const int64_t jc = idx[l - 1].cell(m[0], m[1], m[2]);
         if (jc >= 0) {
@@ -106,6 +122,7 @@ std::string plan_level_faces(const ats_level_desc *levels, int n_levels, int l, 
             return "level " + std::to_string(l) + ": 2:1 balance violated (neighbour found at level " +
                    std::to_string(k) + ")";
         }
+        wall(cell, dir);
       }
     }
   }
@@ -149,6 +166,9 @@ struct ats_hierarchy {
   double k0 = 0.0;
   int iface_kind = ATS_FACE_DIRICHLET;  // row of the coarse-to-fine faces
   double iface_alpha = 1.0;
+  double *d_wall = nullptr;  // [12] ghost E and K of the six domain sides
+  bool power_law = false;    // K = pl_K0 E^pl_a on the leaves before every solve
+  double pl_K0 = 1.0, pl_a = 0.0;
   std::vector<HLevel> lv;
   // use_graph = 2: the level solves of one ats_level_advance are enqueued
   // without host waits; their result records are read once at the end
@@ -171,6 +191,7 @@ namespace {
   } while (0)
 
 void hierarchy_free(ats_hierarchy *H) {
+  ctx_free(H->ctx, H->d_wall);
   ctx_free(H->ctx, H->d_recs);
   if (H->h_recs) cudaFreeHost(H->h_recs);
   for (HLevel &h : H->lv) {
@@ -198,6 +219,8 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   cudaStream_t st = ctx_stream(H->ctx);
   ats_status s = restrict_into(H, l);
   if (s != ATS_OK) return s;
+  if (H->power_law)  // frozen at E^n of this level, leaf cells (refined cells keep the restriction)
+    H_TRY(launch_power_law_K(h.N, level_leaf(h.lvl), h.E, H->pl_K0, H->pl_a, h.K, st));
   if (H->fld) {
     // coefficients frozen at E^n of this level (leaf cells; refined cells keep
     // the restriction of their children's K)
@@ -210,7 +233,7 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   const double *ec_old = !coarse ? nullptr : (H->order == ATS_ORDER_FINE_FIRST ? coarse->E : coarse->E_prev);
   H_TRY(launch_gather_faces((int)h.n_face, h.src_rel, h.src_cell, h.E, h.K, ec_old, coarse ? coarse->E : nullptr,
                             coarse ? coarse->K : nullptr, H->order == ATS_ORDER_FINE_FIRST ? 0.0 : theta, h.fE,
-                            h.fK, st));
+                            h.fK, H->d_wall, st));
   H_TRY(cudaMemcpyAsync(h.E_prev, h.E, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, st));
   ats_coef_desc c;
   std::memset(&c, 0, sizeof(c));
@@ -302,7 +325,7 @@ ats_status ats_hierarchy_plan_faces(const ats_hierarchy_desc *desc, int level, i
     return ATS_ERR_INVALID_ARG;
   }
   LevelFaces lf;
-  std::string msg = plan_level_faces(desc->levels, desc->n_levels, level, lf);
+  std::string msg = plan_level_faces(desc->levels, desc->n_levels, level, lf, desc->wall_kind);
   if (!msg.empty()) {
     set_error(msg);
     return ATS_ERR_INVALID_ARG;
@@ -337,9 +360,40 @@ ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc
   H->order = desc->order;
   H->lv.resize(desc->n_levels);
   cudaStream_t st = ctx_stream(ctx);
+  {
+    // ghost values of the domain sides (used by Dirichlet sides only)
+    double wall[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1};
+    if (desc->wall_kind) {
+      for (int k = 0; k < 6; ++k) {
+        if (desc->wall_kind[k] != ATS_FACE_DIRICHLET) continue;
+        if (!desc->wall_E || !desc->wall_K || !std::isfinite(desc->wall_E[k]) || !(desc->wall_K[k] > 0.0) ||
+            !std::isfinite(desc->wall_K[k])) {
+          set_error("a Dirichlet side needs a finite wall_E and a wall_K > 0");
+          hierarchy_free(H);
+          return ATS_ERR_INVALID_ARG;
+        }
+        wall[k] = desc->wall_E[k];
+        wall[6 + k] = desc->wall_K[k];
+      }
+    }
+    void *p = nullptr;
+    ats_status s0 = ctx_alloc(ctx, sizeof(wall), &p);
+    if (s0 != ATS_OK) {
+      hierarchy_free(H);
+      return s0;
+    }
+    H->d_wall = (double *)p;
+    cudaError_t e0 = cudaMemcpyAsync(H->d_wall, wall, sizeof(wall), cudaMemcpyHostToDevice, st);
+    if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(st);
+    if (e0 != cudaSuccess) {
+      set_error(cudaGetErrorString(e0));
+      hierarchy_free(H);
+      return ATS_ERR_CUDA;
+    }
+  }
   std::vector<LevelFaces> lfs(desc->n_levels);
   for (int l = 0; l < desc->n_levels; ++l) {
-    std::string msg = plan_level_faces(desc->levels, desc->n_levels, l, lfs[l]);
+    std::string msg = plan_level_faces(desc->levels, desc->n_levels, l, lfs[l], desc->wall_kind);
     if (!msg.empty()) {
       set_error(msg);
       hierarchy_free(H);
@@ -411,7 +465,8 @@ ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc
       }
     }
     std::vector<int8_t> srel(nf);
-    for (int64_t f = 0; f < nf; ++f) srel[f] = lf.rel[f] == ATS_REL_COARSER ? 1 : 0;
+    for (int64_t f = 0; f < nf; ++f)
+      srel[f] = lf.rel[f] == ATS_REL_COARSER ? 1 : (lf.rel[f] == ATS_REL_SAME ? 2 : 0);
     cudaError_t e = cudaSuccess;
     if (nf) {
       e = cudaMemcpyAsync(h.src_rel, srel.data(), nf, cudaMemcpyHostToDevice, st);
@@ -433,6 +488,21 @@ ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc
     }
   }
   *out = H;
+  return ATS_OK;
+}
+
+ats_status ats_hierarchy_set_power_law(ats_hierarchy *H, double K0, double a) {
+  if (!H || !(K0 > 0.0) || !std::isfinite(K0) || !std::isfinite(a)) {
+    set_error("ats_hierarchy_set_power_law: K0 > 0 and a finite a are required");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (H->fld) {
+    set_error("ats_hierarchy_set_power_law: the hierarchy is in the radiation-matter mode");
+    return ATS_ERR_INVALID_ARG;
+  }
+  H->power_law = true;
+  H->pl_K0 = K0;
+  H->pl_a = a;
   return ATS_OK;
 }
 
@@ -498,6 +568,10 @@ ats_status ats_hierarchy_set_state(ats_hierarchy *H, int level, const double *E,
 ats_status ats_hierarchy_set_fld(ats_hierarchy *H, int level, const double *rho, const double *T, double k0, int mem) {
   if (!H || level < 0 || level >= (int)H->lv.size() || !rho || !T || !(k0 > 0.0)) {
     set_error("ats_hierarchy_set_fld: bad argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (H->power_law) {
+    set_error("ats_hierarchy_set_fld: the hierarchy is in the power-law coefficient mode");
     return ATS_ERR_INVALID_ARG;
   }
   HLevel &h = H->lv[level];

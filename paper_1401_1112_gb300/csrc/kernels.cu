@@ -1153,13 +1153,16 @@ __global__ void k_gather_faces(int n_face, const int8_t *__restrict__ src_rel, c
                                const double *__restrict__ E_same, const double *__restrict__ K_same,
                                const double *__restrict__ Ec_old, const double *__restrict__ Ec_new,
                                const double *__restrict__ K_coarse, double theta, double *__restrict__ fE,
-                               double *__restrict__ fK) {
+                               double *__restrict__ fK, const double *__restrict__ wall) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= n_face) return;
   const int64_t j = src_cell[f];
   if (src_rel[f] == 0) {
     fE[f] = E_same[j];
     fK[f] = K_same[j];
+  } else if (src_rel[f] == 2) {  // Dirichlet side of the domain: the side's ghost value and coefficient
+    fE[f] = wall[j];
+    fK[f] = wall[6 + j];
   } else {
     const double e0 = Ec_old[j];
     fE[f] = theta == 0.0 ? e0 : e0 + theta * (Ec_new[j] - e0);
@@ -1254,10 +1257,11 @@ cudaError_t launch_restrict(int n, const int32_t *cell, const int32_t *child, co
 
 cudaError_t launch_gather_faces(int n_face, const int8_t *src_rel, const int32_t *src_cell, const double *E_same,
                                 const double *K_same, const double *Ec_old, const double *Ec_new,
-                                const double *K_coarse, double theta, double *fE, double *fK, cudaStream_t st) {
+                                const double *K_coarse, double theta, double *fE, double *fK, const double *wall,
+                                cudaStream_t st) {
   if (n_face <= 0) return cudaSuccess;
   k_gather_faces<<<(n_face + 255) / 256, 256, 0, st>>>(n_face, src_rel, src_cell, E_same, K_same, Ec_old, Ec_new,
-                                                        K_coarse, theta, fE, fK);
+                                                        K_coarse, theta, fE, fK, wall);
   return cudaGetLastError();
 }
 

@@ -73,3 +73,46 @@ def test_uniform_grids_converge_at_close_to_second_order(relaxed):
     ratios = [l2[i] / l2[i + 1] for i in range(len(l2) - 1)]
     assert all(3.0 <= r <= 4.5 for r in ratios), ratios
     assert ratios[-1] >= 3.5, ratios
+
+
+def test_walled_hierarchy_holds_the_exact_linear_steady_state():
+    """Constant K (a = 0), Dirichlet sides on a three-level column refined in
+    its interior: the linear profile through the two ghost values (at
+    x = -dx0/2 and 1 + dx0/2) is reproduced exactly by every level's rows
+    (fine-to-coarse ghosts, restrictions and walls are all exact for a
+    linear function), so the relaxed state equals it on every leaf."""
+    levels = W.column_hierarchy(8, [[3, 4], [7, 8]])
+    E0, E1 = 3.0, 1.0
+    E_init = [np.full(lv.n_cell, 2.0) for lv in levels]
+    Es, steps, ok = Q.relax_amr(levels, E_init, {0: E0, 1: E1}, K0=1.0, a=0.0)
+    assert ok, steps
+    dx0 = levels[0].dx
+    for lv, E in zip(levels, Es):
+        x = (lv.cell_xyz()[:, 0] + 0.5) * lv.dx
+        lin = E0 + (E1 - E0) * (x + 0.5 * dx0) / (1.0 + dx0)
+        leaf = lv.leaf_cells()
+        assert np.max(np.abs(E[leaf] - lin[leaf])) <= 1e-9
+
+
+def test_single_level_hierarchy_matches_the_uniform_relaxation(relaxed):
+    levels, E_init, walls = W.equilibrium_amr(0)
+    Es, _, ok = Q.relax_amr(levels, E_init, walls)
+    assert ok
+    lv, E, _ = relaxed[8]
+    assert np.max(np.abs(Es[0] - E)) <= 1e-9 * np.max(E)
+
+
+def test_adaptive_levels_lower_the_error():
+    """The paper's adaptive-time-step runs of this test (static mesh refined
+    toward the steep end): each added level lowers the L2 norm; the error of
+    the coarse region, which the refinement does not touch, keeps it from
+    falling as fast as on uniform grids (the paper: first order at best with
+    more than two levels)."""
+    l2 = []
+    for l_max in range(4):
+        levels, E_init, walls = W.equilibrium_amr(l_max)
+        Es, steps, ok = Q.relax_amr(levels, E_init, walls)
+        assert ok, (l_max, steps)
+        l2.append(Q.l2_error_amr(levels, Es, 8 * 2 ** l_max))
+    ratios = [l2[i] / l2[i + 1] for i in range(len(l2) - 1)]
+    assert all(1.2 <= r <= 4.0 for r in ratios), ratios

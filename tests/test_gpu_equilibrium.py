@@ -64,3 +64,42 @@ def test_relaxed_states_match_the_oracle(ats, ctx, prec):
         assert l2[-1] == pytest.approx(Q.l2_error(lv, Eo), rel=1e-6)
     ratios = [l2[i] / l2[i + 1] for i in range(len(l2) - 1)]
     assert all(3.0 <= r <= 4.5 for r in ratios), ratios
+
+
+@pytest.mark.parametrize("l_max", [0, 1, 2, 3])
+def test_adaptive_runs_match_the_oracle(ats, ctx, l_max):
+    """The adaptive-time-step runs (static mesh refined toward the steep end,
+    Dirichlet sides on every level touching them, K = E^1.5 from each
+    level's own E^n, fine levels first): relaxed leaf values within 1e-8 of
+    the oracle's driver, the same L2 norm."""
+    from paper_1401_1112_gb300 import equilibrium as G
+
+    levels, E_init, walls = W.equilibrium_amr(l_max)
+    Eg, steps, ok, _ = G.relax_amr(ctx, levels, E_init, walls)
+    assert ok, steps
+    Eo, steps_o, ok_o = Q.relax_amr(levels, E_init, walls)
+    assert ok_o
+    scale = max(float(np.max(e)) for e in Eo)
+    for lv, a, b in zip(levels, Eg, Eo):
+        leaf = lv.leaf_cells()
+        assert np.max(np.abs(a[leaf] - b[leaf])) <= 1e-8 * scale
+    n_eff = 8 * 2 ** l_max
+    assert G.l2_error_amr(levels, Eg, n_eff) == pytest.approx(Q.l2_error_amr(levels, Eo, n_eff), rel=1e-6)
+
+
+def test_walled_hierarchy_linear_steady_state(ats, ctx):
+    """Constant K, Dirichlet sides, interior refinement: the exact linear
+    profile through the ghost values on every leaf (as the oracle's pin)."""
+    from paper_1401_1112_gb300 import equilibrium as G
+
+    levels = W.column_hierarchy(8, [[3, 4], [7, 8]])
+    E0, E1 = 3.0, 1.0
+    Es, steps, ok, _ = G.relax_amr(ctx, levels, [np.full(lv.n_cell, 2.0) for lv in levels], {0: E0, 1: E1},
+                                   K0=1.0, a=0.0, precision=ats.ATS_PREC_FP64)
+    assert ok, steps
+    dx0 = levels[0].dx
+    for lv, E in zip(levels, Es):
+        x = (lv.cell_xyz()[:, 0] + 0.5) * lv.dx
+        lin = E0 + (E1 - E0) * (x + 0.5 * dx0) / (1.0 + dx0)
+        leaf = lv.leaf_cells()
+        assert np.max(np.abs(E[leaf] - lin[leaf])) <= 1e-8

@@ -213,6 +213,41 @@ def equilibrium_column(n: int, E_left: float = 4.0, E_right: float = 0.5):
     return lv, E, face_E, x
 
 
+def column_hierarchy(n0: int, refined_x):
+    """A one-dimensional AMR column over [0, 1]: the base level has n0 cells
+    in x (n0 even) and one oct in y and z; refined_x[l] lists the level-l x
+    cells to refine (every cell of those x slices, so the column stays
+    uniform in y and z; level l has 2^(l+1) cells across y and z).  Returns
+    the LevelDesc list (no face descriptors)."""
+    assert n0 % 2 == 0
+    base = np.stack(np.meshgrid(np.arange(n0 // 2), [0], [0], indexing="ij"), -1).reshape(-1, 3)
+    refined = []
+    for l, xs in enumerate(refined_x):
+        m = 2 ** (l + 1)
+        yz = np.stack(np.meshgrid(np.arange(m), np.arange(m), indexing="ij"), -1).reshape(-1, 2)
+        cells = [np.column_stack([np.full(len(yz), int(ix)), yz]) for ix in sorted(set(int(v) for v in xs))]
+        refined.append(np.concatenate(cells).astype(np.int64) if cells else np.zeros((0, 3), np.int64))
+    return hierarchy_from_refined(base.astype(np.int32), refined, 1.0 / n0)
+
+
+def equilibrium_amr(l_max: int, n0: int = 8):
+    """The equilibrium test's AMR set-up on a static mesh: base n0 cells over
+    [0, 1]; level l + 1 refines the right half of level l's x range
+    ([1 - 2^-(l+1), 1]: the steep end of the steady profile), up to l_max.
+    Dirichlet sides -x (E = 4) and +x (E = 0.5); step initial state.
+    Returns (levels, per-level E_init, walls {side: E})."""
+    refined_x = []
+    for l in range(l_max):
+        n_l = n0 * 2 ** l                    # level-l cells across the whole domain
+        refined_x.append(list(range(n_l - n0 // 2, n_l)))
+    levels = column_hierarchy(n0, refined_x)
+    E = []
+    for lv in levels:
+        x = (lv.cell_xyz()[:, 0] + 0.5) * lv.dx
+        E.append(np.where(x < 0.5, 4.0, 0.5).astype(np.float64))
+    return levels, E, {0: 4.0, 1: 0.5}
+
+
 def config1(n: int = 32, K: float = 1.0, cfl: float = 10.0):
     """Single-level uniform n^3 box on [-1/2, 1/2]^3, constant K, one backward-
     Euler step of dt = cfl * dx^2 / (2K), Gaussian (sigma 0.05) + 1e-3 floor,
