@@ -527,8 +527,17 @@ def run_equilibrium(ats, ctx):
         rows.append({"cells_x": n, "steps": steps, "converged": bool(ok), "ms_per_step": round(s_step * 1e3, 3),
                      "l2": G.l2_error(lv, Es)})
     ratios = [round(rows[i]["l2"] / rows[i + 1]["l2"], 3) for i in range(len(rows) - 1)]
+    # the adaptive-time-step runs: base 8 cells, up to four levels refining
+    # toward the steep end, fine levels first
+    amr = []
+    for l_max in range(5):
+        levels, E_init, walls = W.equilibrium_amr(l_max)
+        Es, steps, ok, s_step = G.relax_amr(ctx, levels, E_init, walls)
+        amr.append({"l_max": l_max, "effective_cells_x": 8 * 2 ** l_max, "coarse_steps": steps, "converged": bool(ok),
+                    "ms_per_coarse_step": round(s_step * 1e3, 3),
+                    "l2": G.l2_error_amr(levels, Es, 8 * 2 ** l_max)})
     return {"workload": "1D column, E = 4 / 0.5 Dirichlet walls, K = E^1.5 lagged, dt = 0.1, to a step change "
-                        "< 1e-10", "grids": rows, "l2_ratio_per_halving": ratios}
+                        "< 1e-10", "grids": rows, "l2_ratio_per_halving": ratios, "adaptive": amr}
 
 
 def run_serve(args, ats, device):

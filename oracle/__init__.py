@@ -18,6 +18,9 @@ Contents
   * ``equilibrium`` -- the equilibrium test with a nonlinear diffusion
     coefficient (Sect. 4.2) on uniform grids: closed form, lagged steps to
     the steady state, the paper's L2 norm.
+  * ``dirac``    -- the linear diffusion test (Sect. 4.1): a pulse on a 1D
+    column whose mesh follows the 25 % gradient criterion before every
+    coarse step, with each interface row.
   * ``driver``   -- the two-level / multi-level adaptive time-stepping driver
     (Sect. 2.2 and Sect. 3.3), level by level, on top of assemble + pcg.
 """

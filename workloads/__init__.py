@@ -248,6 +248,27 @@ def equilibrium_amr(l_max: int, n0: int = 8):
     return levels, E, {0: 4.0, 1: 0.5}
 
 
+def dirac_column(E0: float = 1e5, K: float = 1e10):
+    """The linear diffusion test's set-up (Sect. 4.1) on a static mesh: a
+    column over [0, 1] with a base of 32 cells and three levels of refinement
+    nested around the centre (level 1 on [0.25, 0.75], level 2 on
+    [0.3125, 0.6875], level 3 on [0.375, 0.625]: effective resolution 256);
+    E = 1 everywhere except the finest cells of the slice starting at
+    x = 0.5, which hold E0 / dx (a Dirac of weight E0); K = c / (3 rho
+    kappa_R) with rho kappa_R = 1 and c = 3e10 (cgs); coarse step 3.125e-15,
+    64 coarse steps to t = 2e-13.  Returns (levels, per-level (E, K), dt0,
+    n_steps, x0 = centre of the Dirac cell)."""
+    levels = column_hierarchy(32, [list(range(8, 24)), list(range(20, 44)), list(range(48, 80))])
+    states = []
+    dx3 = levels[-1].dx
+    for l, lv in enumerate(levels):
+        E = np.ones(lv.n_cell)
+        if l == len(levels) - 1:
+            E[lv.cell_xyz()[:, 0] == 128] = E0 / dx3
+        states.append((E, np.full(lv.n_cell, K)))
+    return levels, states, 3.125e-15, 64, 0.5 + 0.5 * dx3
+
+
 def config1(n: int = 32, K: float = 1.0, cfl: float = 10.0):
     """Single-level uniform n^3 box on [-1/2, 1/2]^3, constant K, one backward-
     Euler step of dt = cfl * dx^2 / (2K), Gaussian (sigma 0.05) + 1e-3 floor,
