@@ -788,7 +788,7 @@ def main():
     ap.add_argument("--no-dirac", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=96)
-    ap.add_argument("--serve-max-cells", type=int, default=128 ** 3)
+    ap.add_argument("--serve-max-cells", type=int, default=256 ** 3)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     rank, world, local = _dist()
