@@ -242,7 +242,7 @@ def run_ours(args, rank, world, local):
         x_d.copy_(E_d)          # initial guess x0 = E^n
         build_ops()             # coefficients, interface terms, right-hand side
         code, stats = batch.solve(xs)
-        if code != 0:
+        if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
             raise RuntimeError(f"batch solve failed: {code} {ats.ats_last_error()}")
         return stats
 
@@ -337,7 +337,7 @@ def run_ours(args, rank, world, local):
         def e2e_step():
             hbatch.build_operators(hcoefs)  # K, E^n and face values from pinned host memory
             code, _ = hbatch.solve(hx)      # solution back to pinned host memory
-            if code != 0:
+            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
                 raise RuntimeError("e2e solve failed")
 
         e2e_step()
@@ -369,7 +369,7 @@ def run_ours(args, rank, world, local):
             code, _ = ats.ats_solve(levels[k].handle, xs[k], opts=ats.make_opts(
                 tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_FP64,
                 check_every=args.check_every, mem=ats.ATS_MEM_DEVICE))
-            if code != 0:
+            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
                 raise RuntimeError("fp64 solve failed")
         torch.cuda.synchronize()
         f_s = time.perf_counter() - t1
@@ -388,7 +388,7 @@ def run_ours(args, rank, world, local):
         build_ops()
         x_d.copy_(E_d)
         code, _ = ubatch.solve(xs)
-        if code not in (0, ats.ATS_ERR_NOT_CONVERGED):
+        if code < 0 and code != ats.ATS_ERR_NOT_CONVERGED:
             raise RuntimeError(f"unrefined batch failed: {code}")
         ubatch.close()
         xh = x_d.cpu().numpy()
@@ -424,7 +424,7 @@ def run_ours(args, rank, world, local):
             x_d.copy_(E_d)
             batch.build_operators(cn_coefs)
             code, st = batch.solve(xs)
-            if code != 0:
+            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
                 raise RuntimeError(f"Crank-Nicolson batch failed: {code}")
             return st
 
@@ -506,7 +506,7 @@ def run_amr_interfaces(ats, ctx, coarse_steps=3, use_graph=2, check_every=16):
         t0 = time.perf_counter()
         for _ in range(coarse_steps):
             code, _ = H.advance(0, dt, **opts)
-            if code != 0:
+            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
                 raise RuntimeError(f"amr {name} step failed: {code}")
         t_s = time.perf_counter() - t0
         e1 = energy(H)
@@ -594,7 +594,7 @@ def run_serve(args, ats, device):
             code, _ = L.solve(x, tol=r["tol"], precision=ats.ATS_PREC_FP64)
             svc.append(time.perf_counter() - t0)
             L.close()
-            if code != 0:
+            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
                 raise RuntimeError("fp64 serve baseline failed")
     svc = np.array(svc)
     cap = len(svc) / svc.sum()
@@ -629,7 +629,7 @@ def run_serve(args, ats, device):
         while tickets[k] is None:
             time.sleep(0.0002)
         code, x, res = srv.wait(tickets[k], lv.n_cell)
-        errs += code != 0
+        errs += code < 0
         lat.append(res["latency_us"] / 1e3)
     t_end = time.perf_counter()
     th.join()

@@ -57,7 +57,10 @@ typedef int ats_status;
 #define ATS_ERR_CUDA (-7)          /* a CUDA runtime call failed              */
 #define ATS_ERR_NO_DEVICE (-8)     /* no usable CUDA device                   */
 #define ATS_ERR_BAD_INPUT (-9)     /* non-finite value or K <= 0 on a leaf    */
-#define ATS_WARN_NEGATIVE 1        /* solution has a negative energy          */
+#define ATS_WARN_NEGATIVE 1        /* the solve succeeded but its result has a  */
+                                   /* negative energy (the failure mode Sect. 4.2 */
+                                   /* reports with Neumann interfaces); checked  */
+                                   /* at the copy-out (not by ats_solve_noalloc) */
 
 /* face kinds (Sect. 3.2) */
 #define ATS_FACE_DIRICHLET 0
@@ -215,7 +218,8 @@ ats_status ats_batch_create(ats_context *ctx, ats_level *const *levels, int n,
                             const ats_solve_opts *opts, ats_batch **out);
 /* Solve all levels of the batch; x_inout[k] is solve k's [N_k] vector
  * (initial guess in, solution out), host or device per opts->mem. stats: [n]
- * or NULL.  Returns the first error status of any solve, else ATS_OK. */
+ * or NULL.  Returns the first error status of any solve, else the first
+ * warning (ATS_WARN_NEGATIVE), else ATS_OK. */
 ats_status ats_batch_solve(ats_batch *batch, double *const *x_inout, ats_solve_stats *stats);
 ats_status ats_batch_destroy(ats_batch *batch);
 /* Build the operators of every level of the batch in one kernel launch

@@ -190,9 +190,11 @@ void tick_grids(bool fp64, bool paper, int device, int grids[3]);
 // where src (device array of device pointers) is non-null for that solve.
 cudaError_t launch_init(bool fp64, const SolveDev *solves, const WorkItem *items, int n_items,
                         const double *const *src, int grid, cudaStream_t st);
-// End of a solve: dst[solve] = x64 where dst[solve] is non-null.
+// End of a solve: dst[solve] = x64 (2 x64 - E^n for Crank-Nicolson) where
+// dst[solve] is non-null; neg[solve] |= 1 (neg may be null) when a value of
+// the result is negative.
 cudaError_t launch_final(const SolveDev *solves, const WorkItem *items, int n_items,
-                         double *const *dst, int grid, cudaStream_t st);
+                         double *const *dst, int *neg, int grid, cudaStream_t st);
 
 cudaError_t launch_apply64(const SolveDev *solve_host_copy, const double *x, double *y,
                            cudaStream_t st);
@@ -239,6 +241,8 @@ struct DeferredRec {
   SolveScalars sc;
   int flag;
   int chunks;
+  int neg;  // a negative energy in the result
+  int pad;
 };
 // Enqueue one solve of L on the context stream with the whole tick loop as
 // one graph (use_graph = 2 is forced): x_dev is the device initial guess and

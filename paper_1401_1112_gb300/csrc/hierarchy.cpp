@@ -269,8 +269,10 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
   } else {
     s = ats_solve(h.lvl, nullptr, h.E, &o, &st1);
   }
-  if (s == ATS_OK && H->fld) H_TRY(launch_fld_temperature(h.N, level_leaf(h.lvl), h.E, h.rho, h.T, dt, H->k0, st));
-  if (s == ATS_OK && stored) {
+  // a warning (a negative energy in the result) is reported, not fatal
+  const bool ok = s >= 0;
+  if (ok && H->fld) H_TRY(launch_fld_temperature(h.N, level_leaf(h.lvl), h.E, h.rho, h.T, dt, H->k0, st));
+  if (ok && stored) {
     if (h.n_face) H_TRY(cudaMemsetAsync(h.fstore, 0, sizeof(double) * h.n_face, st));
     if (coarse && coarse->n_face)  // this step's fine-to-coarse energy, for the coarser level's next solve
       H_TRY(launch_flux_store((int)coarse->n_face, coarse->gather4, h.fcell, h.E, h.K, h.fK, h.fE,
@@ -284,9 +286,9 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
     acc->res_norm = std::max(acc->res_norm, st1.res_norm);
     acc->x_norm = std::max(acc->x_norm, st1.x_norm);
     acc->err_bound = std::max(acc->err_bound, st1.err_bound);
-    if (acc->status == ATS_OK) acc->status = st1.status;
+    if (st1.status < 0 ? acc->status >= 0 : acc->status == ATS_OK) acc->status = st1.status;
   }
-  return s;
+  return ok ? ATS_OK : s;
 }
 
 // advance level l (and, recursively, the finer ones) by dt; theta0/theta1:
@@ -681,11 +683,13 @@ ats_status ats_level_advance(ats_hierarchy *H, int level, double dt, const ats_s
       acc.res_norm = std::max(acc.res_norm, st1.res_norm);
       acc.x_norm = std::max(acc.x_norm, st1.x_norm);
       acc.err_bound = std::max(acc.err_bound, st1.err_bound);
-      if (acc.status == ATS_OK) acc.status = r;
-      if (s == ATS_OK && r != ATS_OK) s = r;
+      if (r < 0 ? acc.status >= 0 : acc.status == ATS_OK) acc.status = r;
+      if (r < 0 && s >= 0) s = r;
     }
     H->deferred = false;
   }
+  // errors first; else the first warning of the step's solves
+  if (s == ATS_OK && acc.status > 0) s = acc.status;
   if (stats) *stats = acc;
   return s;
 }

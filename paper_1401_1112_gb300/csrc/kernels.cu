@@ -1417,18 +1417,20 @@ __global__ void k_init(const SolveDev *__restrict__ solves, const WorkItem *__re
 }
 
 __global__ void k_final(const SolveDev *__restrict__ solves, const WorkItem *__restrict__ items,
-                        int n_items, double *const *__restrict__ dst) {
+                        int n_items, double *const *__restrict__ dst, int *__restrict__ neg) {
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const WorkItem item = items[it];
     double *xd = dst[item.solve];
     if (!xd) continue;
     const SolveDev &sd = solves[item.solve];
     const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item.n_oct * 8;
-    if (sd.cn_base) {
-      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) xd[b + k] = 2.0 * sd.x64[b + k] - sd.cn_base[b + k];
-    } else {
-      for (int64_t k = threadIdx.x; k < n; k += blockDim.x) xd[b + k] = sd.x64[b + k];
+    bool below = false;  // a negative energy in the result (the warning of the solve)
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+      const double v = sd.cn_base ? 2.0 * sd.x64[b + k] - sd.cn_base[b + k] : sd.x64[b + k];
+      xd[b + k] = v;
+      below = below || v < 0.0;
     }
+    if (__syncthreads_or(below) && neg && threadIdx.x == 0) atomicOr(neg + item.solve, 1);
   }
 }
 
@@ -1452,8 +1454,8 @@ cudaError_t launch_cn_extrapolate(int64_t N, const double *x, const double *E, d
 }
 
 cudaError_t launch_final(const SolveDev *solves, const WorkItem *items, int n_items,
-                         double *const *dst, int grid, cudaStream_t st) {
-  k_final<<<grid, kThreads, 0, st>>>(solves, items, n_items, dst);
+                         double *const *dst, int *neg, int grid, cudaStream_t st) {
+  k_final<<<grid, kThreads, 0, st>>>(solves, items, n_items, dst, neg);
   return cudaGetLastError();
 }
 

@@ -176,7 +176,7 @@ struct Plan {
   int32_t *d_ident = nullptr;      // [n_items] 0..n_items-1 (the full list)
   TickCtl *d_ctl = nullptr;
   int **d_flag_ptrs = nullptr;     // [n] the levels' error flags
-  int *d_flags = nullptr;          // [n] gathered flags
+  int *d_flags = nullptr;          // [n] gathered flags, then [n] negative-result flags
   const double **d_src = nullptr;  // [n] device pointers for x copy-in (or null)
   double **d_dst = nullptr;        // [n] device pointers for x copy-out (or null)
   double *d_xstage = nullptr;      // [sum N] host x staged on the device (host-memory solves)
@@ -436,7 +436,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, (size_t)P->n_items, &P->d_ident)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_ctl)) != ATS_OK ||
       (s = dev_alloc_t(ctx, n, &P->d_flag_ptrs)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, n, &P->d_flags)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 2 * (size_t)n, &P->d_flags)) != ATS_OK ||
       (s = dev_alloc_t(ctx, n, &P->d_src)) != ATS_OK ||
       (s = dev_alloc_t(ctx, n, &P->d_dst)) != ATS_OK) {
     plan_free(P);
@@ -812,7 +812,8 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   (void)pending;
   }
   // copy-out
-  CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->grid, st));
+  CUDA_TRY(cudaMemsetAsync(P->d_flags + n, 0, sizeof(int) * n, st));
+  CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->d_flags + n, P->grid, st));
   if (!dev) {
     ats_status s2 = copy_runs(st, false, P->d_xstage, off.data(), n, x_inout);
     if (s2 != ATS_OK) return s2;
@@ -821,9 +822,9 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   CUDA_TRY(cudaMemcpyAsync(sc.data(), P->d_final, sizeof(SolveScalars) * n, cudaMemcpyDeviceToHost, st));
   unsigned long long cells[kCellCounters] = {0, 0, 0, 0, 0};
   if (P->profiling) CUDA_TRY(cudaMemcpyAsync(cells, P->d_cells, sizeof(cells), cudaMemcpyDeviceToHost, st));
-  std::vector<int> flags(n, 0);
+  std::vector<int> flags(2 * n, 0);
   CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, n, P->d_flags, st));
-  CUDA_TRY(cudaMemcpyAsync(flags.data(), P->d_flags, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(flags.data(), P->d_flags, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   if (device_loop) {
     chunks_run = P->h_active[0];
@@ -832,11 +833,12 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
     if ((int64_t)chunks_run * P->opts.check_every >= max_ticks) timed_out = true;
   }
   if (P->profiling) plan_bytes(P, cells, &P->op_bytes, &P->ref_bytes, &P->upd_bytes);
-  ats_status first_err = ATS_OK;
+  ats_status first_err = ATS_OK, first_warn = ATS_OK;
   for (int k = 0; k < n; ++k) {
     int status = sc[k].status;
     if (flags[k]) status = ATS_ERR_BAD_INPUT;
     if (timed_out && sc[k].phase != kDone) status = ATS_ERR_TIMEOUT;
+    if (status == ATS_OK && flags[n + k]) status = ATS_WARN_NEGATIVE;
     if (stats) {
       ats_solve_stats &o = stats[k];
       o.status = status;
@@ -848,10 +850,14 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
       o.x_norm = sc[k].xnorm;
       o.err_bound = sc[k].xnorm > 0.0 ? sc[k].rnorm / sc[k].xnorm : 0.0;
     }
-    if (status != ATS_OK && first_err == ATS_OK) first_err = status;
+    if (status < 0 && first_err == ATS_OK) first_err = status;
+    if (status > 0 && first_warn == ATS_OK) first_warn = status;
   }
-  if (first_err != ATS_OK) set_error(std::string("solve failed: ") + ats_status_string(first_err));
-  return first_err;
+  if (first_err != ATS_OK) {
+    set_error(std::string("solve failed: ") + ats_status_string(first_err));
+    return first_err;
+  }
+  return first_warn;
 }
 
 }  // namespace
@@ -1334,7 +1340,8 @@ ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opt
   if (s != ATS_OK) return s;
   CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
   CUDA_TRY(cudaGraphLaunch(P->loop_exec, st));
-  CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->grid, st));
+  CUDA_TRY(cudaMemsetAsync(&d_rec->neg, 0, sizeof(int), st));
+  CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, &d_rec->neg, P->grid, st));
   CUDA_TRY(cudaMemcpyAsync(&d_rec->sc, P->d_final, sizeof(SolveScalars), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, 1, &d_rec->flag, st));
   CUDA_TRY(cudaMemcpyAsync(&d_rec->chunks, P->d_loop, sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -1347,6 +1354,7 @@ ats_status deferred_result(const DeferredRec &r, int check_every, int64_t max_ti
   int status = r.sc.status;
   if (r.flag) status = ATS_ERR_BAD_INPUT;
   else if ((int64_t)r.chunks * check_every >= max_ticks && r.sc.phase != kDone) status = ATS_ERR_TIMEOUT;
+  if (status == ATS_OK && r.neg) status = ATS_WARN_NEGATIVE;
   if (out) {
     out->status = status;
     out->iterations = r.sc.iters;

@@ -269,8 +269,15 @@ void retire(ats_server *S, int slot, const SolveScalars &fin) {
     launch_cn_extrapolate(N, level_x64(sl.lvl), base, level_x64(sl.lvl), S->st);
   cudaMemcpyAsync(dn.x.data(), level_x64(sl.lvl), sizeof(double) * N, cudaMemcpyDeviceToHost, S->st);
   cudaStreamSynchronize(S->st);
-  dn.status = fin.status;
-  dn.stats.status = fin.status;
+  int status = fin.status;
+  if (status == ATS_OK)  // a negative energy in the result: the warning of the solve
+    for (int64_t i = 0; i < N; ++i)
+      if (dn.x[i] < 0.0) {
+        status = ATS_WARN_NEGATIVE;
+        break;
+      }
+  dn.status = status;
+  dn.stats.status = status;
   dn.stats.iterations = fin.iters;
   dn.stats.refinements = fin.refines;
   dn.stats.ticks = fin.ticks;

@@ -52,7 +52,7 @@ def relax(ctx, level_desc, E_init, face_E, K0=1.0, a=A_EXP, dt=0.1, tol_step=1e-
             torch.cuda.synchronize(dev)
             code, st = L.solve(x, tol=tol, stop_rule=A.ATS_STOP_CERTIFIED, precision=precision,
                                mem=A.ATS_MEM_DEVICE, use_graph=use_graph)
-            if code != 0:
+            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
                 raise RuntimeError(f"equilibrium step {steps} failed: {code} {st}")
             change = float((x - E).abs().max() / E.abs().max())  # the solve has returned: x is final
             E.copy_(x)
@@ -103,7 +103,7 @@ def relax_amr(ctx, levels, E_init, walls, K0=1.0, a=A_EXP, dt=0.1, tol_step=1e-1
         for steps in range(1, max_steps + 1):
             code, st = H.advance(0, dt, tol=tol, stop_rule=A.ATS_STOP_CERTIFIED, precision=precision,
                                  use_graph=use_graph)
-            if code != 0:
+            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
                 raise RuntimeError(f"equilibrium coarse step {steps} failed: {code} {st}")
             cur = [H.state(l)[leaves[l]] for l in range(len(levels))]
             scale = max(float(np.max(np.abs(c))) for c in cur)

@@ -10,6 +10,10 @@ library's half-step root is within tol ||x'|| of the exact one (doubled by the
 extrapolation) and the oracle's E^{n+1} within tol ||E^{n+1}||:
 ||E_gpu - E_oracle|| <= 2 tol ||x'|| + tol ||E^{n+1}||.  With tol = 2.5e-11
 that bound stays below 1e-10 ||E^{n+1}|| on these inputs (checked).
+
+Crank-Nicolson does not keep positivity (its factor tends to -1 on stiff
+modes), so a solve may end with the warning ATS_WARN_NEGATIVE: success is
+a status >= 0.
 """
 import numpy as np
 import pytest
@@ -84,7 +88,7 @@ def test_cn_level_matches_oracle(ats, ctx, prec, seed):
     x = st.E.copy()
     code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED,
                           precision=ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED)
-    assert code == 0, stats
+    assert code >= 0, stats
     _check_cn(x, xr, st.E)
     nl = ~lv.leaf_cells()
     np.testing.assert_array_equal(x[nl], st.E[nl])  # 2 E - E on cells the solve leaves alone
@@ -92,7 +96,7 @@ def test_cn_level_matches_oracle(ats, ctx, prec, seed):
     L.build(st.dt, st.K, st.E, src=st.src, **_faces(st))
     x = st.E.copy()
     code, _ = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED)
-    assert code == 0
+    assert code >= 0
     xb = _be_oracle(lv, st)
     assert np.linalg.norm(x - xb) <= PAR * np.linalg.norm(xb)
     L.close()
@@ -107,10 +111,10 @@ def test_cn_initial_guess_is_a_guess_of_the_new_state(ats, ctx):
     L.build(st.dt, st.K, st.E, integrator=ats.ATS_INTEGRATOR_CRANK_NICOLSON, **_faces(st))
     x = st.E.copy()
     code, cold = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_FP64)
-    assert code == 0
+    assert code >= 0
     x = xr.copy()
     code, warm = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_FP64)
-    assert code == 0
+    assert code >= 0
     assert warm["iterations"] < cold["iterations"]
     assert warm["r0_norm"] < 1e-6 * cold["r0_norm"]
     _check_cn(x, xr, st.E)
@@ -143,7 +147,7 @@ def test_cn_batch_mixed_integrators(ats, ctx, mem):
     B.build_operators(B.prepare_coefs(coefs))
     xs = [conv(np.full(lv.n_cell, np.nan)) for lv, _ in solves]
     code, stats = B.solve(xs)
-    assert code == 0, stats
+    assert code >= 0, stats
     got = [x.cpu().numpy() if mem == "device" else x for x in xs]
     B.close()
     for (lv, st), ig, x, L in zip(solves, integ, got, levels):
@@ -155,7 +159,7 @@ def test_cn_batch_mixed_integrators(ats, ctx, mem):
         L.build(st.dt, st.K, st.E, integrator=ig, **_faces(st))
         xo = st.E.copy()
         code, _ = L.solve(xo, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED)
-        assert code == 0
+        assert code >= 0
         np.testing.assert_array_equal(xo, x)
     for L in levels:
         L.close()
@@ -174,7 +178,7 @@ def test_cn_server_requests(ats):
         tickets.append((srv.submit(lv, st, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, x0=x0, integrator=ig), ig))
     for (lv, st), (t, ig) in zip(reqs, tickets):
         code, x, res = srv.wait(t, lv.n_cell)
-        assert code == 0, res
+        assert code >= 0, res
         if ig == ats.ATS_INTEGRATOR_CRANK_NICOLSON:
             _check_cn(x, _cn_oracle(lv, st), st.E)
         else:

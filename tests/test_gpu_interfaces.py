@@ -54,8 +54,11 @@ def test_interfaces_match_oracle(ats, ctx, seed, interface, alpha):
     steps = 2
     for _ in range(steps):
         code, st = H.advance(0, dt, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED)
-        assert code == 0, st
         ref.advance(0, dt, tol=TOL)
+        # negative energies, the failure Sect. 4.2 reports for Neumann
+        # interfaces, come with the warning
+        negative = any(float(np.min(ref.E[l][lv.leaf_cells()])) < 0.0 for l, lv in enumerate(levels))
+        assert code == (ats.ATS_WARN_NEGATIVE if negative else 0), st
     bound = steps * 7 * 1e-10
     for l in range(len(levels)):
         assert _rel(H.state(l), ref.state(l)) <= bound, l
@@ -71,7 +74,7 @@ def test_neumann_interfaces_conserve_energy_on_gpu(ats, ctx):
     e0 = _energy(levels, [E for E, _ in states])
     for _ in range(3):
         code, st = H.advance(0, dt, tol=1e-12, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_FP64)
-        assert code == 0, st
+        assert code >= 0, st  # Neumann interfaces may leave negative energies (ATS_WARN_NEGATIVE)
     e1 = _energy(levels, [H.state(l) for l in range(len(levels))])
     assert abs(e1 - e0) <= 1e-10 * e0, (e0, e1)
 

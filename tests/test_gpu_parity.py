@@ -524,3 +524,34 @@ def test_device_loop_matches_host_polled(ats, ctx, prec):
     assert s["iterations"] == 5
     for L in levels:
         L.close()
+
+
+def test_negative_energy_warning(ats, ctx):
+    """A result with a negative value (here from a strong sink) is still the
+    solution (matches the oracle) and carries the warning ATS_WARN_NEGATIVE,
+    alone and in a batch beside solves without it (the batch returns the
+    warning, each solve its own status)."""
+    rng = np.random.default_rng(17)
+    solves = [W.random_box_solve(rng, o) for o in (30, 200)]
+    (lv, st), (lv2, st2) = solves
+    src = np.full(lv.n_cell, -50.0)
+    S = oracle.assemble(lv, st.dt, st.K, st.E, src=src, **_faces(st))
+    xr, info = oracle.pcg(S, st.E, tol=TOL, stop_rule=oracle.STOP_CERTIFIED)
+    assert info["status"] == 0 and np.min(xr) < 0.0
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, src=src, **_faces(st))
+    x = st.E.copy()
+    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED)
+    assert code == ats.ATS_WARN_NEGATIVE and stats["status"] == ats.ATS_WARN_NEGATIVE
+    assert _rel(x, xr) <= PAR
+    L2 = ats.Level(ctx, lv2)
+    L2.build(st2.dt, st2.K, st2.E, **_faces(st2))
+    B = ats.Batch(ctx, [L2, L], tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=1)
+    xs = [st2.E.copy(), st.E.copy()]
+    code, bstats = B.solve(xs)
+    assert code == ats.ATS_WARN_NEGATIVE
+    assert [s["status"] for s in bstats] == [0, ats.ATS_WARN_NEGATIVE]
+    np.testing.assert_array_equal(xs[1], x)
+    B.close()
+    L.close()
+    L2.close()
