@@ -334,12 +334,17 @@ def run_ours(args, rank, world, local):
                  face_E=fEn[foffs[k]:foffs[k + 1]] if foffs[k + 1] > foffs[k] else None,
                  face_F=fFn[foffs[k]:foffs[k + 1]] if foffs[k + 1] > foffs[k] else None) for k in range(n)])
 
+        # each step: its inputs from pinned host memory (copied on the batch's
+        # copy stream while the previous step's solve runs, then built), the
+        # solve, the solution back to pinned host memory
         def e2e_step():
-            hbatch.build_operators(hcoefs)  # K, E^n and face values from pinned host memory
-            code, _ = hbatch.solve(hx)      # solution back to pinned host memory
+            hbatch.build_operators(hcoefs)   # this step's operators, from the prefetched copies
+            hbatch.prefetch_operators(hcoefs)  # the next step's inputs, overlapping this solve
+            code, _ = hbatch.solve(hx)
             if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
                 raise RuntimeError("e2e solve failed")
 
+        hbatch.prefetch_operators(hcoefs)
         e2e_step()
         barrier()
         t1 = time.perf_counter()

@@ -227,6 +227,17 @@ ats_status ats_batch_destroy(ats_batch *batch);
  * describes level k.  Errors as ats_level_build_operator; ATS_ERR_BAD_INPUT
  * is reported per solve by the next ats_batch_solve. */
 ats_status ats_batch_build_operators(ats_batch *batch, const ats_coef_desc *coefs);
+/* Pipelining of host inputs: copy the host arrays of coefs (the next step's
+ * operators) on a copy stream of the batch into its second staging set, and
+ * return without waiting, so that the copies overlap a solve the caller runs
+ * meanwhile (host<->device links carry both directions at once; use pinned
+ * host memory, pageable copies do not overlap).  The next
+ * ats_batch_build_operators with the same host arrays (same pointers) builds
+ * from the copies instead of copying again; with other arrays the prefetch
+ * is dropped.  The host arrays must not change until that build returns.
+ * Device arrays are not copied (nothing to prefetch).  Errors: as
+ * ats_batch_build_operators. */
+ats_status ats_batch_prefetch_operators(ats_batch *batch, const ats_coef_desc *coefs);
 /* One-shot form: create, solve and destroy. */
 ats_status ats_batch_run(ats_context *ctx, ats_level *const *levels, int n, double *const *x_inout,
                          const ats_solve_opts *opts, ats_solve_stats *stats);

@@ -140,6 +140,7 @@ _SIGS = [
     ("ats_batch_set_profiling", ctypes.c_int, [P, ctypes.c_int]),
     ("ats_batch_kernel_stats", ctypes.c_int, [P, ctypes.POINTER(ats_kernel_stats)]),
     ("ats_power_law_K", ctypes.c_int, [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_double, P]),
+    ("ats_batch_prefetch_operators", ctypes.c_int, [P, ctypes.POINTER(ats_coef_desc)]),
     ("ats_batch_autotune", ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ats_tune_result)]),
@@ -410,6 +411,12 @@ def ats_batch_run(ctx, levels: Sequence, xs: Sequence, opts: Optional[ats_solve_
 def ats_batch_build_operators(batch, coefs):
     """coefs: a ctypes array of ats_coef_desc (see ``coef_desc``), one per level."""
     return _check(lib().ats_batch_build_operators(batch, coefs), "ats_batch_build_operators")
+
+
+def ats_batch_prefetch_operators(batch, coefs):
+    """coefs: a ctypes array of ats_coef_desc; their host arrays are copied
+    to the device without waiting (see the C header)."""
+    return _check(lib().ats_batch_prefetch_operators(batch, coefs), "ats_batch_prefetch_operators")
 
 
 def ats_batch_set_profiling(batch, on: bool):
@@ -772,6 +779,9 @@ class Batch:
 
     def build_operators(self, prepared):
         return ats_batch_build_operators(self.handle, prepared[0])
+
+    def prefetch_operators(self, prepared):
+        return ats_batch_prefetch_operators(self.handle, prepared[0])
 
     def set_profiling(self, on=True):
         ats_batch_set_profiling(self.handle, on)

@@ -207,9 +207,16 @@ struct ats_batch {
   Plan *plan = nullptr;
   // host inputs of the batched build, staged in one device buffer per kind
   // (cell arrays K, E_old, s, src; face arrays K, E, F) so that runs of levels
-  // whose host arrays are contiguous cost one copy
-  double *stage_cell[4] = {nullptr, nullptr, nullptr, nullptr};
-  double *stage_face[3] = {nullptr, nullptr, nullptr};
+  // whose host arrays are contiguous cost one copy; two sets, used in turn,
+  // so that the next step's inputs can be copied while a solve runs
+  double *stage_cell[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+  double *stage_face[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int cur_set = 0;  // the set the operators were last built from
+  // ats_batch_prefetch_operators: copies on their own stream into the other set
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copied = nullptr, released = nullptr;
+  bool prefetched = false;
+  std::vector<const double *> pf_ptrs;  // the prefetched host arrays, 7 per level
   // batched operator build
   CoefArgs *d_args = nullptr;
   int32_t *d_blk_level = nullptr;  // batched build: level of each block
@@ -1448,8 +1455,14 @@ ats_status ats_batch_destroy(ats_batch *B) {
     dev_free(ctx, B->d_args);
     dev_free(ctx, B->d_blk_level);
     dev_free(ctx, B->d_blk_first);
-    for (double *p : B->stage_cell) dev_free(ctx, p);
-    for (double *p : B->stage_face) dev_free(ctx, p);
+    if (B->copy_st) cudaStreamSynchronize(B->copy_st);
+    for (auto &set : B->stage_cell)
+      for (double *p : set) dev_free(ctx, p);
+    for (auto &set : B->stage_face)
+      for (double *p : set) dev_free(ctx, p);
+    if (B->copied) cudaEventDestroy(B->copied);
+    if (B->released) cudaEventDestroy(B->released);
+    if (B->copy_st) cudaStreamDestroy(B->copy_st);
     plan_free(B->plan);
   }
   delete B;
@@ -1466,6 +1479,68 @@ ats_status ats_batch_run(ats_context *ctx, ats_level *const *levels, int n, doub
   return s;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The host arrays of a batch's coefficient descriptors (7 per level; null for
+// device arrays or absent ones), to recognise the arrays of a prefetch.
+std::vector<const double *> batch_host_ptrs(const ats_coef_desc *coefs, int n) {
+  std::vector<const double *> out;
+  out.reserve(7 * (size_t)n);
+  for (int k = 0; k < n; ++k) {
+    const ats_coef_desc &c = coefs[k];
+    const bool h = c.mem == ATS_MEM_HOST;
+    for (const double *p : {c.K, c.E_old, c.s, c.src, c.face_K, c.face_E, c.face_F}) out.push_back(h ? p : nullptr);
+  }
+  return out;
+}
+
+// Stage the host arrays of coefs in staging set `set` (allocated on first
+// use), one copy per run of levels whose host arrays are contiguous, on
+// stream st (copy = false: the arrays are already there); dc[k] gets the
+// device pointers.
+ats_status batch_stage(ats_batch *B, const ats_coef_desc *coefs, int set, cudaStream_t st, bool copy,
+                       ats_coef_desc *dc) {
+  Plan *P = B->plan;
+  ats_context *ctx = P->ctx;
+  const int n = P->n;
+  ats_status s;
+  std::vector<int64_t> oc(n + 1, 0), of(n + 1, 0);
+  for (int k = 0; k < n; ++k) {
+    oc[k + 1] = oc[k] + P->levels[k]->N;
+    of[k + 1] = of[k] + P->levels[k]->n_face;
+  }
+  const double *ats_coef_desc::*cell_kind[4] = {&ats_coef_desc::K, &ats_coef_desc::E_old, &ats_coef_desc::s,
+                                                &ats_coef_desc::src};
+  const double *ats_coef_desc::*face_kind[3] = {&ats_coef_desc::face_K, &ats_coef_desc::face_E,
+                                                &ats_coef_desc::face_F};
+  std::vector<double *> hp(n);
+  for (int q = 0; q < 7; ++q) {
+    const bool cell = q < 4;
+    const double *ats_coef_desc::*m = cell ? cell_kind[q] : face_kind[q - 4];
+    const std::vector<int64_t> &o = cell ? oc : of;
+    bool any = false;
+    for (int k = 0; k < n; ++k) {
+      const bool h = coefs[k].mem == ATS_MEM_HOST && coefs[k].*m && o[k + 1] > o[k];
+      hp[k] = h ? const_cast<double *>(coefs[k].*m) : nullptr;
+      any = any || h;
+    }
+    if (!any) continue;
+    double *&stage = cell ? B->stage_cell[set][q] : B->stage_face[set][q - 4];
+    if (!stage && (s = dev_alloc_t(ctx, std::max<int64_t>(1, o[n]), &stage)) != ATS_OK) return s;
+    if (copy && (s = copy_runs(st, true, stage, o.data(), n, hp.data())) != ATS_OK) return s;
+    for (int k = 0; k < n; ++k)
+      if (hp[k]) dc[k].*m = stage + o[k];
+  }
+  for (int k = 0; k < n; ++k) dc[k].mem = ATS_MEM_DEVICE;
+  return ATS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
   if (!B || !B->plan || !coefs) {
     set_error("null argument");
@@ -1480,38 +1555,19 @@ ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
   std::vector<ats_coef_desc> dc(coefs, coefs + n);
   bool any_host = false;
   for (int k = 0; k < n; ++k) any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
+  bool from_prefetch = false;
   if (any_host) {
-    // host inputs: one staging buffer per array kind for the whole batch
+    // host inputs go to the set not used by the last build (the last solve may
+    // still read that one's E_old); a matching prefetch has copied them already
     CUDA_TRY(cudaSetDevice(ctx->device));
-    std::vector<int64_t> oc(n + 1, 0), of(n + 1, 0);
-    for (int k = 0; k < n; ++k) {
-      oc[k + 1] = oc[k] + P->levels[k]->N;
-      of[k + 1] = of[k] + P->levels[k]->n_face;
-    }
-    const double *ats_coef_desc::*cell_kind[4] = {&ats_coef_desc::K, &ats_coef_desc::E_old, &ats_coef_desc::s,
-                                                  &ats_coef_desc::src};
-    const double *ats_coef_desc::*face_kind[3] = {&ats_coef_desc::face_K, &ats_coef_desc::face_E,
-                                                  &ats_coef_desc::face_F};
-    std::vector<double *> hp(n);
-    for (int q = 0; q < 7; ++q) {
-      const bool cell = q < 4;
-      const double *ats_coef_desc::*m = cell ? cell_kind[q] : face_kind[q - 4];
-      const std::vector<int64_t> &o = cell ? oc : of;
-      bool any = false;
-      for (int k = 0; k < n; ++k) {
-        const bool h = coefs[k].mem == ATS_MEM_HOST && coefs[k].*m && o[k + 1] > o[k];
-        hp[k] = h ? const_cast<double *>(coefs[k].*m) : nullptr;
-        any = any || h;
-      }
-      if (!any) continue;
-      double *&stage = cell ? B->stage_cell[q] : B->stage_face[q - 4];
-      if (!stage && (s = dev_alloc_t(ctx, std::max<int64_t>(1, o[n]), &stage)) != ATS_OK) return s;
-      if ((s = copy_runs(st, true, stage, o.data(), n, hp.data())) != ATS_OK) return s;
-      for (int k = 0; k < n; ++k)
-        if (hp[k]) dc[k].*m = stage + o[k];
-    }
-    for (int k = 0; k < n; ++k) dc[k].mem = ATS_MEM_DEVICE;
+    const int set = B->cur_set ^ 1;
+    from_prefetch = B->prefetched && batch_host_ptrs(coefs, n) == B->pf_ptrs;
+    if (from_prefetch) CUDA_TRY(cudaStreamWaitEvent(st, B->copied, 0));
+    else if (B->prefetched && B->copy_st) CUDA_TRY(cudaStreamSynchronize(B->copy_st));  // a stale prefetch
+    if ((s = batch_stage(B, coefs, set, st, !from_prefetch, dc.data())) != ATS_OK) return s;
+    B->cur_set = set;
   }
+  B->prefetched = false;
   for (int k = 0; k < n; ++k) {
     s = prepare_operator(P->levels[k], &dc[k], &args[k]);
     if (s != ATS_OK) return s;
@@ -1539,7 +1595,40 @@ ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
     CUDA_TRY(cudaMemcpyAsync(B->d_args, B->h_args.data(), sizeof(CoefArgs) * n, cudaMemcpyHostToDevice, st));
   }
   CUDA_TRY(launch_coef_build_batch(B->d_args, B->d_blk_level, B->d_blk_first, B->n_blocks, n, P->d_flag_ptrs, st));
-  if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
+  // host arrays: the caller may reuse them once the call returns
+  if (from_prefetch) CUDA_TRY(cudaEventSynchronize(B->copied));
+  else if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
+  return ATS_OK;
+}
+
+ats_status ats_batch_prefetch_operators(ats_batch *B, const ats_coef_desc *coefs) {
+  if (!B || !B->plan || !coefs) {
+    set_error("null argument");
+    return ATS_ERR_INVALID_ARG;
+  }
+  Plan *P = B->plan;
+  ats_context *ctx = P->ctx;
+  const int n = P->n;
+  bool any_host = false;
+  for (int k = 0; k < n; ++k) any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
+  B->prefetched = false;
+  if (!any_host) return ATS_OK;  // nothing to copy
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  if (!B->copy_st) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&B->copy_st, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&B->copied, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&B->released, cudaEventDisableTiming));
+  }
+  // the other set is free once the work queued so far on the context stream
+  // (which read it two builds ago) has run
+  CUDA_TRY(cudaEventRecord(B->released, ctx->stream));
+  CUDA_TRY(cudaStreamWaitEvent(B->copy_st, B->released, 0));
+  std::vector<ats_coef_desc> dc(coefs, coefs + n);
+  ats_status s = batch_stage(B, coefs, B->cur_set ^ 1, B->copy_st, true, dc.data());
+  if (s != ATS_OK) return s;
+  CUDA_TRY(cudaEventRecord(B->copied, B->copy_st));
+  B->pf_ptrs = batch_host_ptrs(coefs, n);
+  B->prefetched = true;
   return ATS_OK;
 }
 

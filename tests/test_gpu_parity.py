@@ -555,3 +555,56 @@ def test_negative_energy_warning(ats, ctx):
     B.close()
     L.close()
     L2.close()
+
+
+def test_prefetched_inputs_give_the_same_results(ats, ctx):
+    """Host inputs copied ahead on the batch's copy stream (while a solve
+    runs) give bitwise the results of plain builds; a prefetch of other
+    arrays than the next build's is dropped."""
+    rng = np.random.default_rng(29)
+    solves = [W.random_box_solve(rng, o, robin=True) for o in (5, 80, 300)]
+    levels = []
+    for lv, st in solves:
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        levels.append(L)
+
+    def coefs(scale):
+        return [dict(dt=st.dt, K=st.K.copy(), E_old=st.E * scale, face_K=st.face_K, face_E=st.face_E,
+                     face_F=st.face_F) for _, st in solves]
+
+    B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                  mem=ats.ATS_MEM_HOST, x0=ats.ATS_X0_E_OLD, use_graph=2)
+    A, Bc = B.prepare_coefs(coefs(1.0)), B.prepare_coefs(coefs(1.1))
+
+    def solve():
+        xs = [np.empty(lv.n_cell) for lv, _ in solves]
+        code, _ = B.solve(xs)
+        assert code == 0
+        return xs
+
+    B.build_operators(A)
+    xa = solve()
+    B.build_operators(Bc)
+    xb = solve()
+    B.build_operators(A)
+    B.prefetch_operators(Bc)   # copies overlap the next solve
+    xa2 = solve()
+    B.build_operators(Bc)      # from the prefetched copies
+    xb2 = solve()
+    B.prefetch_operators(Bc)
+    B.build_operators(A)       # other arrays: the prefetch is dropped
+    xa3 = solve()
+    for u, v in zip(xa, xa2):
+        np.testing.assert_array_equal(u, v)
+    for u, v in zip(xb, xb2):
+        np.testing.assert_array_equal(u, v)
+    for u, v in zip(xa, xa3):
+        np.testing.assert_array_equal(u, v)
+    for (lv, st), x in zip(solves, xb):
+        S = oracle.assemble(lv, st.dt, st.K, st.E * 1.1, **_faces(st))
+        xr, info = oracle.pcg(S, st.E * 1.1, tol=TOL, stop_rule=oracle.STOP_CERTIFIED)
+        assert _rel(x, xr) <= PAR
+    B.close()
+    for L in levels:
+        L.close()
