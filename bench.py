@@ -14,7 +14,15 @@ Default workload (one "step" = every row of the hot path over one batch):
 
 Metric: level-solves/s (whole job), with the dominant kernel's achieved HBM
 bandwidth against the measured peak, the plain per-solve FP64 GPU path on the
-same mix, and the FP64 CPU oracle on a bounded sample.
+same mix, and the FP64 CPU oracle on a bounded sample (one thread and every
+host core), with the error of each GPU path against it.
+
+Other legs on the same line (each can be switched off): the end-to-end
+number through pinned host buffers (inputs of the next step copied during
+the solve); the same batch with Crank-Nicolson steps; the served request
+stream (p50 / p99 latency against plain FP64 one at a time); the two-level
+AMR step with each interface row; the paper's equilibrium test (uniform and
+adaptive) and its Dirac test with a mesh that follows the gradient criterion.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
 
