@@ -52,3 +52,24 @@ def test_unbalanced_rejected(ats):
         [tuple(c) for c in levels[1].oct_xyz.tolist()], dtype=np.int64), ref], levels[0].dx)
     with pytest.raises(ats.AtsError, match="2:1"):
         ats.ats_hierarchy_plan_faces(lv, 2)
+
+
+@pytest.mark.parametrize("sides", [{0: 1.0, 1: 2.0}, {2: 1.0, 5: 3.0}, {0: 1.0, 1: 1.0, 2: 1.0, 3: 1.0, 4: 1.0, 5: 1.0}])
+def test_domain_side_faces_match_oracle_driver(ats, sides):
+    """Dirichlet domain sides: every leaf of every level on such a side gets a
+    face (relation REL_SAME, src = the side), as the oracle's driver derives
+    them independently; the zero-flux sides get none."""
+    levels = W.column_hierarchy(8, [[5, 6, 7], [12, 13, 14, 15]])   # refinement reaching the +x side
+    states = [(np.ones(lv.n_cell), np.ones(lv.n_cell)) for lv in levels]
+    walls = {s: (e, 1.0) for s, e in sides.items()}
+    H = driver.Hierarchy(levels, states, walls=walls)
+    for l in range(len(levels)):
+        cell, dr, rel, src = ats.ats_hierarchy_plan_faces(levels, l, walls=walls)
+        mine = sorted(zip(cell.tolist(), dr.tolist(), rel.tolist(), src.tolist()))
+        assert mine == sorted(H.faces[l]), l
+        wall = rel == ats.ATS_REL_SAME
+        assert set(dr[wall].tolist()) <= set(sides)
+        assert np.all(src[wall] == dr[wall])
+    # a +x side face on the finest level (the refinement reaches it)
+    cell, dr, rel, _ = ats.ats_hierarchy_plan_faces(levels, 2, walls=walls)
+    assert (1 in sides) == bool(np.any((rel == ats.ATS_REL_SAME) & (dr == 1)))
