@@ -269,15 +269,8 @@ void retire(ats_server *S, int slot, const SolveScalars &fin) {
     launch_cn_extrapolate(N, level_x64(sl.lvl), base, level_x64(sl.lvl), S->st);
   cudaMemcpyAsync(dn.x.data(), level_x64(sl.lvl), sizeof(double) * N, cudaMemcpyDeviceToHost, S->st);
   cudaStreamSynchronize(S->st);
-  int status = fin.status;
-  if (status == ATS_OK)  // a negative energy in the result: the warning of the solve
-    for (int64_t i = 0; i < N; ++i)
-      if (dn.x[i] < 0.0) {
-        status = ATS_WARN_NEGATIVE;
-        break;
-      }
-  dn.status = status;
-  dn.stats.status = status;
+  dn.status = fin.status;  // the negative-energy warning is found by the waiting thread
+  dn.stats.status = fin.status;
   dn.stats.iterations = fin.iters;
   dn.stats.refinements = fin.refines;
   dn.stats.ticks = fin.ticks;
@@ -611,6 +604,13 @@ ats_status ats_server_wait(ats_server *S, uint64_t ticket, int64_t timeout_us, d
   Done dn = std::move(S->done[ticket]);
   S->done.erase(ticket);
   lk.unlock();
+  if (dn.status == ATS_OK)  // a negative energy in the result: the warning of the solve (here, off the scheduler)
+    for (double v : dn.x)
+      if (v < 0.0) {
+        dn.status = ATS_WARN_NEGATIVE;
+        dn.stats.status = ATS_WARN_NEGATIVE;
+        break;
+      }
   if (x_out && !dn.x.empty()) std::memcpy(x_out, dn.x.data(), sizeof(double) * dn.x.size());
   if (res) {
     res->status = dn.status;
