@@ -287,6 +287,9 @@ std::string build_layout(const ats_level_desc &d, Layout &out);
 ats_status level_create_with_layout(ats_context *ctx, const ats_level_desc *desc, const Layout &lay, ats_level **out);
 
 void set_error(const std::string &msg);
+// The status of the exception being handled (call only in a catch handler):
+// ATS_ERR_OOM for std::bad_alloc, else ATS_ERR_INVALID_ARG; sets the message.
+ats_status abi_exception() noexcept;
 
 // Context services for other translation units (runtime.cpp).
 ats_status ctx_alloc(ats_context *ctx, size_t bytes, void **out);

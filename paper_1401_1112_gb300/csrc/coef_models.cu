@@ -37,22 +37,26 @@ cudaError_t launch_power_law_K(int64_t n_cell, const uint8_t *leaf, const double
 extern "C" {
 
 ats_status ats_power_law_K(ats_context *ctx, int64_t n, const double *E, double K0, double p, double *K) {
-  if (!ctx || n < 0 || (n > 0 && (!E || !K))) {
-    ats::set_error("ats_power_law_K: bad argument");
-    return ATS_ERR_INVALID_ARG;
+  try {  // no C++ exception leaves the library
+    if (!ctx || n < 0 || (n > 0 && (!E || !K))) {
+      ats::set_error("ats_power_law_K: bad argument");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (n == 0) return ATS_OK;
+    cudaError_t e = cudaSetDevice(ats::ctx_device(ctx));
+    if (e == cudaSuccess) {
+      const unsigned blocks = (unsigned)((n + 255) / 256);
+      ats::k_power_law_K<<<blocks, 256, 0, ats::ctx_stream(ctx)>>>(n, E, K0, p, K);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      ats::set_error(std::string("ats_power_law_K: ") + cudaGetErrorString(e));
+      return ATS_ERR_CUDA;
+    }
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  if (n == 0) return ATS_OK;
-  cudaError_t e = cudaSetDevice(ats::ctx_device(ctx));
-  if (e == cudaSuccess) {
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    ats::k_power_law_K<<<blocks, 256, 0, ats::ctx_stream(ctx)>>>(n, E, K0, p, K);
-    e = cudaGetLastError();
-  }
-  if (e != cudaSuccess) {
-    ats::set_error(std::string("ats_power_law_K: ") + cudaGetErrorString(e));
-    return ATS_ERR_CUDA;
-  }
-  return ATS_OK;
 }
 
 }  // extern "C"

@@ -322,376 +322,420 @@ extern "C" {
 
 ats_status ats_hierarchy_plan_faces(const ats_hierarchy_desc *desc, int level, int64_t *n_face, int32_t *face_cell,
                                     int8_t *face_dir, int8_t *face_rel, int32_t *src_cell) {
-  if (!desc || !n_face || desc->n_levels <= 0 || !desc->levels) {
-    set_error("null argument");
-    return ATS_ERR_INVALID_ARG;
+  try {  // no C++ exception leaves the library
+    if (!desc || !n_face || desc->n_levels <= 0 || !desc->levels) {
+      set_error("null argument");
+      return ATS_ERR_INVALID_ARG;
+    }
+    LevelFaces lf;
+    std::string msg = plan_level_faces(desc->levels, desc->n_levels, level, lf, desc->wall_kind);
+    if (!msg.empty()) {
+      set_error(msg);
+      return ATS_ERR_INVALID_ARG;
+    }
+    *n_face = (int64_t)lf.cell.size();
+    if (face_cell) std::copy(lf.cell.begin(), lf.cell.end(), face_cell);
+    if (face_dir) std::copy(lf.dir.begin(), lf.dir.end(), face_dir);
+    if (face_rel) std::copy(lf.rel.begin(), lf.rel.end(), face_rel);
+    if (src_cell) std::copy(lf.src_cell.begin(), lf.src_cell.end(), src_cell);
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  LevelFaces lf;
-  std::string msg = plan_level_faces(desc->levels, desc->n_levels, level, lf, desc->wall_kind);
-  if (!msg.empty()) {
-    set_error(msg);
-    return ATS_ERR_INVALID_ARG;
-  }
-  *n_face = (int64_t)lf.cell.size();
-  if (face_cell) std::copy(lf.cell.begin(), lf.cell.end(), face_cell);
-  if (face_dir) std::copy(lf.dir.begin(), lf.dir.end(), face_dir);
-  if (face_rel) std::copy(lf.rel.begin(), lf.rel.end(), face_rel);
-  if (src_cell) std::copy(lf.src_cell.begin(), lf.src_cell.end(), src_cell);
-  return ATS_OK;
 }
 
 ats_status ats_hierarchy_create(ats_context *ctx, const ats_hierarchy_desc *desc, ats_hierarchy **out) {
-  if (!ctx || !desc || !out || desc->n_levels <= 0 || !desc->levels) {
-    set_error("null argument");
-    return ATS_ERR_INVALID_ARG;
-  }
-  if (desc->order != ATS_ORDER_FINE_FIRST && desc->order != ATS_ORDER_COARSE_FIRST) {
-    set_error("bad order");
-    return ATS_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
-  for (int l = 1; l < desc->n_levels; ++l) {
-    if (std::fabs(desc->levels[l].dx * 2.0 - desc->levels[l - 1].dx) > 1e-12 * desc->levels[l - 1].dx) {
-      set_error("each level must halve dx");
+  try {  // no C++ exception leaves the library
+    if (!ctx || !desc || !out || desc->n_levels <= 0 || !desc->levels) {
+      set_error("null argument");
       return ATS_ERR_INVALID_ARG;
     }
-  }
-  ats_hierarchy *H = new (std::nothrow) ats_hierarchy();
-  if (!H) return ATS_ERR_OOM;
-  H->ctx = ctx;
-  H->order = desc->order;
-  H->lv.resize(desc->n_levels);
-  cudaStream_t st = ctx_stream(ctx);
-  {
-    // ghost values of the domain sides (used by Dirichlet sides only)
-    double wall[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1};
-    if (desc->wall_kind) {
-      for (int k = 0; k < 6; ++k) {
-        if (desc->wall_kind[k] != ATS_FACE_DIRICHLET) continue;
-        if (!desc->wall_E || !desc->wall_K || !std::isfinite(desc->wall_E[k]) || !(desc->wall_K[k] > 0.0) ||
-            !std::isfinite(desc->wall_K[k])) {
-          set_error("a Dirichlet side needs a finite wall_E and a wall_K > 0");
-          hierarchy_free(H);
-          return ATS_ERR_INVALID_ARG;
-        }
-        wall[k] = desc->wall_E[k];
-        wall[6 + k] = desc->wall_K[k];
+    if (desc->order != ATS_ORDER_FINE_FIRST && desc->order != ATS_ORDER_COARSE_FIRST) {
+      set_error("bad order");
+      return ATS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    for (int l = 1; l < desc->n_levels; ++l) {
+      if (std::fabs(desc->levels[l].dx * 2.0 - desc->levels[l - 1].dx) > 1e-12 * desc->levels[l - 1].dx) {
+        set_error("each level must halve dx");
+        return ATS_ERR_INVALID_ARG;
       }
     }
-    void *p = nullptr;
-    ats_status s0 = ctx_alloc(ctx, sizeof(wall), &p);
-    if (s0 != ATS_OK) {
-      hierarchy_free(H);
-      return s0;
-    }
-    H->d_wall = (double *)p;
-    cudaError_t e0 = cudaMemcpyAsync(H->d_wall, wall, sizeof(wall), cudaMemcpyHostToDevice, st);
-    if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(st);
-    if (e0 != cudaSuccess) {
-      set_error(cudaGetErrorString(e0));
-      hierarchy_free(H);
-      return ATS_ERR_CUDA;
-    }
-  }
-  std::vector<LevelFaces> lfs(desc->n_levels);
-  for (int l = 0; l < desc->n_levels; ++l) {
-    std::string msg = plan_level_faces(desc->levels, desc->n_levels, l, lfs[l], desc->wall_kind);
-    if (!msg.empty()) {
-      set_error(msg);
-      hierarchy_free(H);
-      return ATS_ERR_INVALID_ARG;
-    }
-  }
-  for (int l = 0; l < desc->n_levels; ++l) {
-    const LevelFaces &lf = lfs[l];
-    HLevel &h = H->lv[l];
-    ats_level_desc d = desc->levels[l];
-    const int64_t nf = (int64_t)lf.cell.size();
-    std::vector<int8_t> kind(nf, ATS_FACE_DIRICHLET);
-    std::vector<double> alpha(nf, 1.0);
-    d.n_face = nf;
-    d.face_cell = lf.cell.data();
-    d.face_dir = lf.dir.data();
-    d.face_kind = kind.data();
-    d.face_rel = lf.rel.data();
-    d.face_alpha = alpha.data();
-    ats_status s = ats_level_create(ctx, &d, &h.lvl);
-    if (s != ATS_OK) {
-      hierarchy_free(H);
-      return s;
-    }
-    h.N = 8 * d.n_oct;
-    h.dx = d.dx;
-    h.n_face = nf;
-    h.n_restrict = (int64_t)lf.restrict_cell.size();
-    void *p;
-    auto alloc = [&](size_t bytes, void **dst) {
-      ats_status r = ctx_alloc(ctx, bytes ? bytes : 16, &p);
-      *dst = p;
-      return r;
-    };
-    if ((s = alloc(sizeof(double) * h.N, (void **)&h.E)) != ATS_OK ||
-        (s = alloc(sizeof(double) * h.N, (void **)&h.E_prev)) != ATS_OK ||
-        (s = alloc(sizeof(double) * h.N, (void **)&h.K)) != ATS_OK ||
-        (s = alloc(sizeof(double) * nf, (void **)&h.fE)) != ATS_OK ||
-        (s = alloc(sizeof(double) * nf, (void **)&h.fK)) != ATS_OK ||
-        (s = alloc(sizeof(int8_t) * nf, (void **)&h.src_rel)) != ATS_OK ||
-        (s = alloc(sizeof(int32_t) * nf, (void **)&h.src_cell)) != ATS_OK ||
-        (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_cell)) != ATS_OK ||
-        (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_child)) != ATS_OK ||
-        (s = alloc(sizeof(int32_t) * nf, (void **)&h.fcell)) != ATS_OK ||
-        (s = alloc(sizeof(int32_t) * 4 * nf, (void **)&h.gather4)) != ATS_OK ||
-        (s = alloc(sizeof(double) * nf, (void **)&h.fstore)) != ATS_OK) {
-      hierarchy_free(H);
-      return s;
-    }
-    h.rel = lf.rel;
-    // coarse-to-fine face (cell, dir) of this level <- the fine-to-coarse faces
-    // of the next level whose coarse cell and opposite direction match
-    std::vector<int32_t> g4(4 * nf, -1);
-    if (l + 1 < desc->n_levels) {
-      std::unordered_map<int64_t, int64_t> at;
-      for (int64_t f = 0; f < nf; ++f)
-        if (lf.rel[f] == ATS_REL_FINER) at[6 * (int64_t)lf.cell[f] + lf.dir[f]] = f;
-      const LevelFaces &ff = lfs[l + 1];
-      for (size_t g = 0; g < ff.cell.size(); ++g) {
-        if (ff.rel[g] != ATS_REL_COARSER) continue;
-        auto it = at.find(6 * (int64_t)ff.src_cell[g] + (ff.dir[g] ^ 1));
-        if (it == at.end()) continue;
-        int32_t *slot = &g4[4 * it->second];
-        for (int k = 0; k < 4; ++k)
-          if (slot[k] < 0) {
-            slot[k] = (int32_t)g;
-            break;
+    ats_hierarchy *H = new (std::nothrow) ats_hierarchy();
+    if (!H) return ATS_ERR_OOM;
+    H->ctx = ctx;
+    H->order = desc->order;
+    H->lv.resize(desc->n_levels);
+    cudaStream_t st = ctx_stream(ctx);
+    {
+      // ghost values of the domain sides (used by Dirichlet sides only)
+      double wall[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1};
+      if (desc->wall_kind) {
+        for (int k = 0; k < 6; ++k) {
+          if (desc->wall_kind[k] != ATS_FACE_DIRICHLET) continue;
+          if (!desc->wall_E || !desc->wall_K || !std::isfinite(desc->wall_E[k]) || !(desc->wall_K[k] > 0.0) ||
+              !std::isfinite(desc->wall_K[k])) {
+            set_error("a Dirichlet side needs a finite wall_E and a wall_K > 0");
+            hierarchy_free(H);
+            return ATS_ERR_INVALID_ARG;
           }
+          wall[k] = desc->wall_E[k];
+          wall[6 + k] = desc->wall_K[k];
+        }
+      }
+      void *p = nullptr;
+      ats_status s0 = ctx_alloc(ctx, sizeof(wall), &p);
+      if (s0 != ATS_OK) {
+        hierarchy_free(H);
+        return s0;
+      }
+      H->d_wall = (double *)p;
+      cudaError_t e0 = cudaMemcpyAsync(H->d_wall, wall, sizeof(wall), cudaMemcpyHostToDevice, st);
+      if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(st);
+      if (e0 != cudaSuccess) {
+        set_error(cudaGetErrorString(e0));
+        hierarchy_free(H);
+        return ATS_ERR_CUDA;
       }
     }
-    std::vector<int8_t> srel(nf);
-    for (int64_t f = 0; f < nf; ++f)
-      srel[f] = lf.rel[f] == ATS_REL_COARSER ? 1 : (lf.rel[f] == ATS_REL_SAME ? 2 : 0);
-    cudaError_t e = cudaSuccess;
-    if (nf) {
-      e = cudaMemcpyAsync(h.src_rel, srel.data(), nf, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h.src_cell, lf.src_cell.data(), 4 * nf, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h.fcell, lf.cell.data(), 4 * nf, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h.gather4, g4.data(), 16 * nf, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(h.fstore, 0, sizeof(double) * nf, st);
+    std::vector<LevelFaces> lfs(desc->n_levels);
+    for (int l = 0; l < desc->n_levels; ++l) {
+      std::string msg = plan_level_faces(desc->levels, desc->n_levels, l, lfs[l], desc->wall_kind);
+      if (!msg.empty()) {
+        set_error(msg);
+        hierarchy_free(H);
+        return ATS_ERR_INVALID_ARG;
+      }
     }
-    if (e == cudaSuccess && h.n_restrict) {
-      e = cudaMemcpyAsync(h.r_cell, lf.restrict_cell.data(), 4 * h.n_restrict, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h.r_child, lf.restrict_child.data(), 4 * h.n_restrict, cudaMemcpyHostToDevice, st);
+    for (int l = 0; l < desc->n_levels; ++l) {
+      const LevelFaces &lf = lfs[l];
+      HLevel &h = H->lv[l];
+      ats_level_desc d = desc->levels[l];
+      const int64_t nf = (int64_t)lf.cell.size();
+      std::vector<int8_t> kind(nf, ATS_FACE_DIRICHLET);
+      std::vector<double> alpha(nf, 1.0);
+      d.n_face = nf;
+      d.face_cell = lf.cell.data();
+      d.face_dir = lf.dir.data();
+      d.face_kind = kind.data();
+      d.face_rel = lf.rel.data();
+      d.face_alpha = alpha.data();
+      ats_status s = ats_level_create(ctx, &d, &h.lvl);
+      if (s != ATS_OK) {
+        hierarchy_free(H);
+        return s;
+      }
+      h.N = 8 * d.n_oct;
+      h.dx = d.dx;
+      h.n_face = nf;
+      h.n_restrict = (int64_t)lf.restrict_cell.size();
+      void *p;
+      auto alloc = [&](size_t bytes, void **dst) {
+        ats_status r = ctx_alloc(ctx, bytes ? bytes : 16, &p);
+        *dst = p;
+        return r;
+      };
+      if ((s = alloc(sizeof(double) * h.N, (void **)&h.E)) != ATS_OK ||
+          (s = alloc(sizeof(double) * h.N, (void **)&h.E_prev)) != ATS_OK ||
+          (s = alloc(sizeof(double) * h.N, (void **)&h.K)) != ATS_OK ||
+          (s = alloc(sizeof(double) * nf, (void **)&h.fE)) != ATS_OK ||
+          (s = alloc(sizeof(double) * nf, (void **)&h.fK)) != ATS_OK ||
+          (s = alloc(sizeof(int8_t) * nf, (void **)&h.src_rel)) != ATS_OK ||
+          (s = alloc(sizeof(int32_t) * nf, (void **)&h.src_cell)) != ATS_OK ||
+          (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_cell)) != ATS_OK ||
+          (s = alloc(sizeof(int32_t) * h.n_restrict, (void **)&h.r_child)) != ATS_OK ||
+          (s = alloc(sizeof(int32_t) * nf, (void **)&h.fcell)) != ATS_OK ||
+          (s = alloc(sizeof(int32_t) * 4 * nf, (void **)&h.gather4)) != ATS_OK ||
+          (s = alloc(sizeof(double) * nf, (void **)&h.fstore)) != ATS_OK) {
+        hierarchy_free(H);
+        return s;
+      }
+      h.rel = lf.rel;
+      // coarse-to-fine face (cell, dir) of this level <- the fine-to-coarse faces
+      // of the next level whose coarse cell and opposite direction match
+      std::vector<int32_t> g4(4 * nf, -1);
+      if (l + 1 < desc->n_levels) {
+        std::unordered_map<int64_t, int64_t> at;
+        for (int64_t f = 0; f < nf; ++f)
+          if (lf.rel[f] == ATS_REL_FINER) at[6 * (int64_t)lf.cell[f] + lf.dir[f]] = f;
+        const LevelFaces &ff = lfs[l + 1];
+        for (size_t g = 0; g < ff.cell.size(); ++g) {
+          if (ff.rel[g] != ATS_REL_COARSER) continue;
+          auto it = at.find(6 * (int64_t)ff.src_cell[g] + (ff.dir[g] ^ 1));
+          if (it == at.end()) continue;
+          int32_t *slot = &g4[4 * it->second];
+          for (int k = 0; k < 4; ++k)
+            if (slot[k] < 0) {
+              slot[k] = (int32_t)g;
+              break;
+            }
+        }
+      }
+      std::vector<int8_t> srel(nf);
+      for (int64_t f = 0; f < nf; ++f)
+        srel[f] = lf.rel[f] == ATS_REL_COARSER ? 1 : (lf.rel[f] == ATS_REL_SAME ? 2 : 0);
+      cudaError_t e = cudaSuccess;
+      if (nf) {
+        e = cudaMemcpyAsync(h.src_rel, srel.data(), nf, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.src_cell, lf.src_cell.data(), 4 * nf, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.fcell, lf.cell.data(), 4 * nf, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.gather4, g4.data(), 16 * nf, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h.fstore, 0, sizeof(double) * nf, st);
+      }
+      if (e == cudaSuccess && h.n_restrict) {
+        e = cudaMemcpyAsync(h.r_cell, lf.restrict_cell.data(), 4 * h.n_restrict, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(h.r_child, lf.restrict_child.data(), 4 * h.n_restrict, cudaMemcpyHostToDevice, st);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        set_error(cudaGetErrorString(e));
+        hierarchy_free(H);
+        return ATS_ERR_CUDA;
+      }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-      set_error(cudaGetErrorString(e));
-      hierarchy_free(H);
-      return ATS_ERR_CUDA;
-    }
+    *out = H;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  *out = H;
-  return ATS_OK;
 }
 
 ats_status ats_hierarchy_set_power_law(ats_hierarchy *H, double K0, double a) {
-  if (!H || !(K0 > 0.0) || !std::isfinite(K0) || !std::isfinite(a)) {
-    set_error("ats_hierarchy_set_power_law: K0 > 0 and a finite a are required");
-    return ATS_ERR_INVALID_ARG;
+  try {  // no C++ exception leaves the library
+    if (!H || !(K0 > 0.0) || !std::isfinite(K0) || !std::isfinite(a)) {
+      set_error("ats_hierarchy_set_power_law: K0 > 0 and a finite a are required");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (H->fld) {
+      set_error("ats_hierarchy_set_power_law: the hierarchy is in the radiation-matter mode");
+      return ATS_ERR_INVALID_ARG;
+    }
+    H->power_law = true;
+    H->pl_K0 = K0;
+    H->pl_a = a;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  if (H->fld) {
-    set_error("ats_hierarchy_set_power_law: the hierarchy is in the radiation-matter mode");
-    return ATS_ERR_INVALID_ARG;
-  }
-  H->power_law = true;
-  H->pl_K0 = K0;
-  H->pl_a = a;
-  return ATS_OK;
 }
 
 ats_status ats_hierarchy_set_interface(ats_hierarchy *H, int kind, double alpha) {
-  if (!H) return ATS_ERR_INVALID_ARG;
-  if (kind != ATS_FACE_DIRICHLET && kind != ATS_FACE_NEUMANN && kind != ATS_FACE_ROBIN) {
-    set_error("bad interface kind");
-    return ATS_ERR_INVALID_ARG;
+  try {  // no C++ exception leaves the library
+    if (!H) return ATS_ERR_INVALID_ARG;
+    if (kind != ATS_FACE_DIRICHLET && kind != ATS_FACE_NEUMANN && kind != ATS_FACE_ROBIN) {
+      set_error("bad interface kind");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (kind == ATS_FACE_ROBIN && !(alpha >= 0.0 && alpha <= 1.0)) {
+      set_error("Robin alpha must be in [0, 1]");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (kind != ATS_FACE_DIRICHLET && H->order != ATS_ORDER_FINE_FIRST) {
+      set_error("stored interface fluxes need the fine-first order");
+      return ATS_ERR_INVALID_ARG;
+    }
+    const double a = kind == ATS_FACE_DIRICHLET ? 1.0 : (kind == ATS_FACE_NEUMANN ? 0.0 : alpha);
+    cudaStream_t st = ctx_stream(H->ctx);
+    for (HLevel &h : H->lv) {
+      std::vector<int8_t> k(h.n_face, ATS_FACE_DIRICHLET);
+      std::vector<double> al(h.n_face, 1.0);
+      for (int64_t f = 0; f < h.n_face; ++f)
+        if (h.rel[f] == ATS_REL_FINER) {
+          k[f] = (int8_t)kind;
+          al[f] = a;
+        }
+      ats_status s = level_set_face_rows(h.lvl, k.data(), al.data());
+      if (s != ATS_OK) return s;
+      if (h.n_face) H_TRY(cudaMemsetAsync(h.fstore, 0, sizeof(double) * h.n_face, st));
+    }
+    H_TRY(cudaStreamSynchronize(st));
+    H->iface_kind = kind;
+    H->iface_alpha = a;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  if (kind == ATS_FACE_ROBIN && !(alpha >= 0.0 && alpha <= 1.0)) {
-    set_error("Robin alpha must be in [0, 1]");
-    return ATS_ERR_INVALID_ARG;
-  }
-  if (kind != ATS_FACE_DIRICHLET && H->order != ATS_ORDER_FINE_FIRST) {
-    set_error("stored interface fluxes need the fine-first order");
-    return ATS_ERR_INVALID_ARG;
-  }
-  const double a = kind == ATS_FACE_DIRICHLET ? 1.0 : (kind == ATS_FACE_NEUMANN ? 0.0 : alpha);
-  cudaStream_t st = ctx_stream(H->ctx);
-  for (HLevel &h : H->lv) {
-    std::vector<int8_t> k(h.n_face, ATS_FACE_DIRICHLET);
-    std::vector<double> al(h.n_face, 1.0);
-    for (int64_t f = 0; f < h.n_face; ++f)
-      if (h.rel[f] == ATS_REL_FINER) {
-        k[f] = (int8_t)kind;
-        al[f] = a;
-      }
-    ats_status s = level_set_face_rows(h.lvl, k.data(), al.data());
-    if (s != ATS_OK) return s;
-    if (h.n_face) H_TRY(cudaMemsetAsync(h.fstore, 0, sizeof(double) * h.n_face, st));
-  }
-  H_TRY(cudaStreamSynchronize(st));
-  H->iface_kind = kind;
-  H->iface_alpha = a;
-  return ATS_OK;
 }
 
 ats_status ats_hierarchy_destroy(ats_hierarchy *H) {
-  if (!H) return ATS_ERR_INVALID_ARG;
-  cudaStreamSynchronize(ctx_stream(H->ctx));
-  hierarchy_free(H);
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!H) return ATS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(ctx_stream(H->ctx));
+    hierarchy_free(H);
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_hierarchy_level(ats_hierarchy *H, int level, ats_level **out) {
-  if (!H || !out || level < 0 || level >= (int)H->lv.size()) return ATS_ERR_INVALID_ARG;
-  *out = H->lv[level].lvl;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!H || !out || level < 0 || level >= (int)H->lv.size()) return ATS_ERR_INVALID_ARG;
+    *out = H->lv[level].lvl;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_hierarchy_set_state(ats_hierarchy *H, int level, const double *E, const double *K, int mem) {
-  if (!H || level < 0 || level >= (int)H->lv.size() || !E || !K) return ATS_ERR_INVALID_ARG;
-  HLevel &h = H->lv[level];
-  cudaStream_t st = ctx_stream(H->ctx);
-  const cudaMemcpyKind k = mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  H_TRY(cudaMemcpyAsync(h.E, E, sizeof(double) * h.N, k, st));
-  H_TRY(cudaMemcpyAsync(h.E_prev, E, sizeof(double) * h.N, k, st));
-  H_TRY(cudaMemcpyAsync(h.K, K, sizeof(double) * h.N, k, st));
-  H_TRY(cudaStreamSynchronize(st));
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!H || level < 0 || level >= (int)H->lv.size() || !E || !K) return ATS_ERR_INVALID_ARG;
+    HLevel &h = H->lv[level];
+    cudaStream_t st = ctx_stream(H->ctx);
+    const cudaMemcpyKind k = mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    H_TRY(cudaMemcpyAsync(h.E, E, sizeof(double) * h.N, k, st));
+    H_TRY(cudaMemcpyAsync(h.E_prev, E, sizeof(double) * h.N, k, st));
+    H_TRY(cudaMemcpyAsync(h.K, K, sizeof(double) * h.N, k, st));
+    H_TRY(cudaStreamSynchronize(st));
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_hierarchy_set_fld(ats_hierarchy *H, int level, const double *rho, const double *T, double k0, int mem) {
-  if (!H || level < 0 || level >= (int)H->lv.size() || !rho || !T || !(k0 > 0.0)) {
-    set_error("ats_hierarchy_set_fld: bad argument");
-    return ATS_ERR_INVALID_ARG;
+  try {  // no C++ exception leaves the library
+    if (!H || level < 0 || level >= (int)H->lv.size() || !rho || !T || !(k0 > 0.0)) {
+      set_error("ats_hierarchy_set_fld: bad argument");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (H->power_law) {
+      set_error("ats_hierarchy_set_fld: the hierarchy is in the power-law coefficient mode");
+      return ATS_ERR_INVALID_ARG;
+    }
+    HLevel &h = H->lv[level];
+    cudaStream_t st = ctx_stream(H->ctx);
+    ats_status s;
+    void *p;
+    if (!h.rho) {
+      const size_t b = sizeof(double) * h.N;
+      if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
+      h.rho = (double *)p;
+      if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
+      h.T = (double *)p;
+      if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
+      h.s = (double *)p;
+      if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
+      h.src = (double *)p;
+    }
+    const cudaMemcpyKind k = mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    H_TRY(cudaMemcpyAsync(h.rho, rho, sizeof(double) * h.N, k, st));
+    H_TRY(cudaMemcpyAsync(h.T, T, sizeof(double) * h.N, k, st));
+    H->k0 = k0;
+    // initial K from the current E (dt does not enter K)
+    H_TRY(launch_fld_coef(h.N / 8, level_nbr(h.lvl), level_leaf(h.lvl), h.E, h.rho, h.T, h.dx, 1.0, k0, h.K, h.s,
+                          h.src, st));
+    H_TRY(cudaStreamSynchronize(st));
+    bool all = true;
+    for (const HLevel &x : H->lv) all = all && x.rho != nullptr;
+    H->fld = all;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  if (H->power_law) {
-    set_error("ats_hierarchy_set_fld: the hierarchy is in the power-law coefficient mode");
-    return ATS_ERR_INVALID_ARG;
-  }
-  HLevel &h = H->lv[level];
-  cudaStream_t st = ctx_stream(H->ctx);
-  ats_status s;
-  void *p;
-  if (!h.rho) {
-    const size_t b = sizeof(double) * h.N;
-    if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
-    h.rho = (double *)p;
-    if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
-    h.T = (double *)p;
-    if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
-    h.s = (double *)p;
-    if ((s = ctx_alloc(H->ctx, b, &p)) != ATS_OK) return s;
-    h.src = (double *)p;
-  }
-  const cudaMemcpyKind k = mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  H_TRY(cudaMemcpyAsync(h.rho, rho, sizeof(double) * h.N, k, st));
-  H_TRY(cudaMemcpyAsync(h.T, T, sizeof(double) * h.N, k, st));
-  H->k0 = k0;
-  // initial K from the current E (dt does not enter K)
-  H_TRY(launch_fld_coef(h.N / 8, level_nbr(h.lvl), level_leaf(h.lvl), h.E, h.rho, h.T, h.dx, 1.0, k0, h.K, h.s,
-                        h.src, st));
-  H_TRY(cudaStreamSynchronize(st));
-  bool all = true;
-  for (const HLevel &x : H->lv) all = all && x.rho != nullptr;
-  H->fld = all;
-  return ATS_OK;
 }
 
 ats_status ats_hierarchy_get_temperature(ats_hierarchy *H, int level, double *T, int mem) {
-  if (!H || level < 0 || level >= (int)H->lv.size() || !T || !H->lv[level].T) return ATS_ERR_INVALID_ARG;
-  HLevel &h = H->lv[level];
-  cudaStream_t st = ctx_stream(H->ctx);
-  H_TRY(cudaMemcpyAsync(T, h.T, sizeof(double) * h.N,
-                        mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  H_TRY(cudaStreamSynchronize(st));
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!H || level < 0 || level >= (int)H->lv.size() || !T || !H->lv[level].T) return ATS_ERR_INVALID_ARG;
+    HLevel &h = H->lv[level];
+    cudaStream_t st = ctx_stream(H->ctx);
+    H_TRY(cudaMemcpyAsync(T, h.T, sizeof(double) * h.N,
+                          mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    H_TRY(cudaStreamSynchronize(st));
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_hierarchy_get_state(ats_hierarchy *H, int level, double *E, int mem) {
-  if (!H || level < 0 || level >= (int)H->lv.size() || !E) return ATS_ERR_INVALID_ARG;
-  // refined cells report the restriction of their children
-  for (int l = (int)H->lv.size() - 2; l >= level; --l) {
-    ats_status s = restrict_into(H, l);
-    if (s != ATS_OK) return s;
+  try {  // no C++ exception leaves the library
+    if (!H || level < 0 || level >= (int)H->lv.size() || !E) return ATS_ERR_INVALID_ARG;
+    // refined cells report the restriction of their children
+    for (int l = (int)H->lv.size() - 2; l >= level; --l) {
+      ats_status s = restrict_into(H, l);
+      if (s != ATS_OK) return s;
+    }
+    HLevel &h = H->lv[level];
+    cudaStream_t st = ctx_stream(H->ctx);
+    H_TRY(cudaMemcpyAsync(E, h.E, sizeof(double) * h.N,
+                          mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    H_TRY(cudaStreamSynchronize(st));
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  HLevel &h = H->lv[level];
-  cudaStream_t st = ctx_stream(H->ctx);
-  H_TRY(cudaMemcpyAsync(E, h.E, sizeof(double) * h.N,
-                        mem == ATS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  H_TRY(cudaStreamSynchronize(st));
-  return ATS_OK;
 }
 
 ats_status ats_level_advance(ats_hierarchy *H, int level, double dt, const ats_solve_opts *opts,
                              ats_solve_stats *stats) {
-  if (!H || level < 0 || level >= (int)H->lv.size() || !(dt > 0.0)) {
-    set_error("ats_level_advance: bad argument");
-    return ATS_ERR_INVALID_ARG;
-  }
-  ats_solve_stats acc;
-  std::memset(&acc, 0, sizeof(acc));
-  acc.status = ATS_OK;
-  cudaSetDevice(ctx_device(H->ctx));
-  // use_graph = 2: every level solve is one graph launch (device-driven tick
-  // loop) and none is waited for; the step's records are read once at the
-  // end, so a failing solve is reported after the whole step has run
-  H->deferred = opts && opts->use_graph == 2;
-  if (H->deferred) {
-    const int n_lv = (int)H->lv.size();
-    const int need = (1 << std::min(30, n_lv - level)) + 1;  // at most 2^(levels below) solves
-    if (need > H->rec_cap) {
-      ctx_free(H->ctx, H->d_recs);
-      H->d_recs = nullptr;
-      if (H->h_recs) cudaFreeHost(H->h_recs);
-      H->h_recs = nullptr;
-      H->rec_cap = 0;
-      void *p = nullptr;
-      ats_status s0 = ctx_alloc(H->ctx, sizeof(DeferredRec) * need, &p);
-      if (s0 != ATS_OK) return s0;
-      H->d_recs = (DeferredRec *)p;
-      if (cudaMallocHost(&H->h_recs, sizeof(DeferredRec) * need) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("ats_level_advance: pinned allocation failed");
-        return ATS_ERR_OOM;
+  try {  // no C++ exception leaves the library
+    if (!H || level < 0 || level >= (int)H->lv.size() || !(dt > 0.0)) {
+      set_error("ats_level_advance: bad argument");
+      return ATS_ERR_INVALID_ARG;
+    }
+    ats_solve_stats acc;
+    std::memset(&acc, 0, sizeof(acc));
+    acc.status = ATS_OK;
+    cudaSetDevice(ctx_device(H->ctx));
+    // use_graph = 2: every level solve is one graph launch (device-driven tick
+    // loop) and none is waited for; the step's records are read once at the
+    // end, so a failing solve is reported after the whole step has run
+    H->deferred = opts && opts->use_graph == 2;
+    if (H->deferred) {
+      const int n_lv = (int)H->lv.size();
+      const int need = (1 << std::min(30, n_lv - level)) + 1;  // at most 2^(levels below) solves
+      if (need > H->rec_cap) {
+        ctx_free(H->ctx, H->d_recs);
+        H->d_recs = nullptr;
+        if (H->h_recs) cudaFreeHost(H->h_recs);
+        H->h_recs = nullptr;
+        H->rec_cap = 0;
+        void *p = nullptr;
+        ats_status s0 = ctx_alloc(H->ctx, sizeof(DeferredRec) * need, &p);
+        if (s0 != ATS_OK) return s0;
+        H->d_recs = (DeferredRec *)p;
+        if (cudaMallocHost(&H->h_recs, sizeof(DeferredRec) * need) != cudaSuccess) {
+          cudaGetLastError();
+          set_error("ats_level_advance: pinned allocation failed");
+          return ATS_ERR_OOM;
+        }
+        H->rec_cap = need;
       }
-      H->rec_cap = need;
+      H->rec_meta.assign(H->rec_cap, {0, 0});
+      H->n_recs = 0;
     }
-    H->rec_meta.assign(H->rec_cap, {0, 0});
-    H->n_recs = 0;
-  }
-  ats_status s = advance(H, level, dt, 1.0, opts, &acc);
-  if (H->deferred) {
-    cudaStream_t st = ctx_stream(H->ctx);
-    if (H->n_recs > 0)
-      H_TRY(cudaMemcpyAsync(H->h_recs, H->d_recs, sizeof(DeferredRec) * H->n_recs, cudaMemcpyDeviceToHost, st));
-    H_TRY(cudaStreamSynchronize(st));
-    for (int k = 0; k < H->n_recs; ++k) {
-      ats_solve_stats st1;
-      const ats_status r = deferred_result(H->h_recs[k], H->rec_meta[k].first, H->rec_meta[k].second, &st1);
-      acc.iterations += st1.iterations;
-      acc.refinements += st1.refinements;
-      acc.ticks += st1.ticks;
-      acc.r0_norm = std::max(acc.r0_norm, st1.r0_norm);
-      acc.res_norm = std::max(acc.res_norm, st1.res_norm);
-      acc.x_norm = std::max(acc.x_norm, st1.x_norm);
-      acc.err_bound = std::max(acc.err_bound, st1.err_bound);
-      if (r < 0 ? acc.status >= 0 : acc.status == ATS_OK) acc.status = r;
-      if (r < 0 && s >= 0) s = r;
+    ats_status s = advance(H, level, dt, 1.0, opts, &acc);
+    if (H->deferred) {
+      cudaStream_t st = ctx_stream(H->ctx);
+      if (H->n_recs > 0)
+        H_TRY(cudaMemcpyAsync(H->h_recs, H->d_recs, sizeof(DeferredRec) * H->n_recs, cudaMemcpyDeviceToHost, st));
+      H_TRY(cudaStreamSynchronize(st));
+      for (int k = 0; k < H->n_recs; ++k) {
+        ats_solve_stats st1;
+        const ats_status r = deferred_result(H->h_recs[k], H->rec_meta[k].first, H->rec_meta[k].second, &st1);
+        acc.iterations += st1.iterations;
+        acc.refinements += st1.refinements;
+        acc.ticks += st1.ticks;
+        acc.r0_norm = std::max(acc.r0_norm, st1.r0_norm);
+        acc.res_norm = std::max(acc.res_norm, st1.res_norm);
+        acc.x_norm = std::max(acc.x_norm, st1.x_norm);
+        acc.err_bound = std::max(acc.err_bound, st1.err_bound);
+        if (r < 0 ? acc.status >= 0 : acc.status == ATS_OK) acc.status = r;
+        if (r < 0 && s >= 0) s = r;
+      }
+      H->deferred = false;
     }
-    H->deferred = false;
+    // errors first; else the first warning of the step's solves
+    if (s == ATS_OK && acc.status > 0) s = acc.status;
+    if (stats) *stats = acc;
+    return s;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  // errors first; else the first warning of the step's solves
-  if (s == ATS_OK && acc.status > 0) s = acc.status;
-  if (stats) *stats = acc;
-  return s;
 }
 
 }  // extern "C"

@@ -19,6 +19,26 @@ namespace ats {
 static thread_local std::string g_last_error;
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+// Called in the catch handler of an entry point: the status of the exception
+// being handled (no C++ exception leaves the library).
+ats_status abi_exception() noexcept {
+  auto note = [](const char *m) noexcept {
+    try {
+      g_last_error = m;
+    } catch (...) {
+    }
+  };
+  try {
+    throw;
+  } catch (const std::bad_alloc &) {
+    note("out of host memory");
+    return ATS_ERR_OOM;
+  } catch (...) {
+    note("internal error");
+    return ATS_ERR_INVALID_ARG;
+  }
+}
+
 }  // namespace ats
 
 using namespace ats;
@@ -940,88 +960,112 @@ const char *ats_status_string(ats_status s) {
 const char *ats_last_error(void) { return g_last_error.c_str(); }
 
 ats_status ats_layout_neighbors(const ats_level_desc *desc, int32_t *nbr) {
-  if (!desc || !nbr) {
-    set_error("null argument");
-    return ATS_ERR_INVALID_ARG;
+  try {  // no C++ exception leaves the library
+    if (!desc || !nbr) {
+      set_error("null argument");
+      return ATS_ERR_INVALID_ARG;
+    }
+    Layout lay;
+    std::string msg = build_layout(*desc, lay);
+    if (!msg.empty()) {
+      set_error(msg);
+      return ATS_ERR_INVALID_ARG;
+    }
+    std::memcpy(nbr, lay.nbr.data(), sizeof(int32_t) * lay.nbr.size());
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  Layout lay;
-  std::string msg = build_layout(*desc, lay);
-  if (!msg.empty()) {
-    set_error(msg);
-    return ATS_ERR_INVALID_ARG;
-  }
-  std::memcpy(nbr, lay.nbr.data(), sizeof(int32_t) * lay.nbr.size());
-  return ATS_OK;
 }
 
 ats_status ats_context_create(int device, size_t budget, ats_context **out) {
-  if (!out) return ATS_ERR_INVALID_ARG;
-  *out = nullptr;
-  int count = 0;
-  if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) {
-    cudaGetLastError();
-    set_error("no CUDA device");
-    return ATS_ERR_NO_DEVICE;
+  try {  // no C++ exception leaves the library
+    if (!out) return ATS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) {
+      cudaGetLastError();
+      set_error("no CUDA device");
+      return ATS_ERR_NO_DEVICE;
+    }
+    if (device < 0 || device >= count) {
+      set_error("device index out of range");
+      return ATS_ERR_INVALID_ARG;
+    }
+    CUDA_TRY(cudaSetDevice(device));
+    ats_context *ctx = new (std::nothrow) ats_context();
+    if (!ctx) return ATS_ERR_OOM;
+    ctx->device = device;
+    ctx->budget = budget;
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete ctx;
+      set_error(cudaGetErrorString(e));
+      return ATS_ERR_CUDA;
+    }
+    ctx->stream = ctx->own_stream;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (ctx->num_sms <= 0) ctx->num_sms = 1;
+    *out = ctx;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  if (device < 0 || device >= count) {
-    set_error("device index out of range");
-    return ATS_ERR_INVALID_ARG;
-  }
-  CUDA_TRY(cudaSetDevice(device));
-  ats_context *ctx = new (std::nothrow) ats_context();
-  if (!ctx) return ATS_ERR_OOM;
-  ctx->device = device;
-  ctx->budget = budget;
-  cudaError_t e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
-  if (e != cudaSuccess) {
-    delete ctx;
-    set_error(cudaGetErrorString(e));
-    return ATS_ERR_CUDA;
-  }
-  ctx->stream = ctx->own_stream;
-  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (ctx->num_sms <= 0) ctx->num_sms = 1;
-  *out = ctx;
-  return ATS_OK;
 }
 
 ats_status ats_context_destroy(ats_context *ctx) {
-  if (!ctx) return ATS_ERR_INVALID_ARG;
-  cudaSetDevice(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
-  for (auto &kv : ctx->allocs) cudaFree(kv.first);
-  ctx->allocs.clear();
-  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
-  delete ctx;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!ctx) return ATS_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->allocs) cudaFree(kv.first);
+    ctx->allocs.clear();
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_context_set_stream(ats_context *ctx, void *stream) {
-  if (!ctx) return ATS_ERR_INVALID_ARG;
-  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!ctx) return ATS_ERR_INVALID_ARG;
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_context_memory(const ats_context *ctx, size_t *used, size_t *budget) {
-  if (!ctx) return ATS_ERR_INVALID_ARG;
-  if (used) *used = ctx->used;
-  if (budget) *budget = ctx->budget;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!ctx) return ATS_ERR_INVALID_ARG;
+    if (used) *used = ctx->used;
+    if (budget) *budget = ctx->budget;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_level_create(ats_context *ctx, const ats_level_desc *desc, ats_level **out) {
-  if (!ctx || !desc || !out) {
-    set_error("null argument");
-    return ATS_ERR_INVALID_ARG;
+  try {  // no C++ exception leaves the library
+    if (!ctx || !desc || !out) {
+      set_error("null argument");
+      return ATS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    Layout lay;
+    std::string msg = build_layout(*desc, lay);
+    if (!msg.empty()) {
+      set_error(msg);
+      return ATS_ERR_INVALID_ARG;
+    }
+    return ats::level_create_with_layout(ctx, desc, lay, out);
+  } catch (...) {
+    return ats::abi_exception();
   }
-  *out = nullptr;
-  Layout lay;
-  std::string msg = build_layout(*desc, lay);
-  if (!msg.empty()) {
-    set_error(msg);
-    return ATS_ERR_INVALID_ARG;
-  }
-  return ats::level_create_with_layout(ctx, desc, lay, out);
 }
 
 }  // extern "C"
@@ -1084,27 +1128,35 @@ ats_status ats::level_create_with_layout(ats_context *ctx, const ats_level_desc 
 extern "C" {
 
 ats_status ats_level_destroy(ats_level *L) {
-  if (!L) return ATS_ERR_INVALID_ARG;
-  ats_context *ctx = L->ctx;
-  cudaSetDevice(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
-  if (L->solo) plan_free(L->solo);
-  void *ptrs[] = {L->nbr, L->frec, L->rec_face, L->xrec_dense, L->leaf, L->fkind, L->frel,
-                  L->falpha, L->K64, L->xd64, L->b64, L->C64, L->K32, L->xd32, L->err_flag,
-                  L->stage_cell, L->stage_face, L->x64, L->rhs_save,
-                  L->e[0], L->z[0], L->p0[0], L->p1[0], L->e[1], L->z[1], L->p0[1], L->p1[1],
-                  L->q[0], L->dg[0], L->q[1], L->dg[1]};
-  for (void *p : ptrs) dev_free(ctx, p);
-  delete L;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!L) return ATS_ERR_INVALID_ARG;
+    ats_context *ctx = L->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (L->solo) plan_free(L->solo);
+    void *ptrs[] = {L->nbr, L->frec, L->rec_face, L->xrec_dense, L->leaf, L->fkind, L->frel,
+                    L->falpha, L->K64, L->xd64, L->b64, L->C64, L->K32, L->xd32, L->err_flag,
+                    L->stage_cell, L->stage_face, L->x64, L->rhs_save,
+                    L->e[0], L->z[0], L->p0[0], L->p1[0], L->e[1], L->z[1], L->p0[1], L->p1[1],
+                    L->q[0], L->dg[0], L->q[1], L->dg[1]};
+    for (void *p : ptrs) dev_free(ctx, p);
+    delete L;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_level_size(const ats_level *L, int64_t *n_oct, int64_t *n_cell, int64_t *n_face) {
-  if (!L) return ATS_ERR_INVALID_ARG;
-  if (n_oct) *n_oct = L->n_oct;
-  if (n_cell) *n_cell = L->N;
-  if (n_face) *n_face = L->n_face;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!L) return ATS_ERR_INVALID_ARG;
+    if (n_oct) *n_oct = L->n_oct;
+    if (n_cell) *n_cell = L->N;
+    if (n_face) *n_face = L->n_face;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 }  // extern "C"
@@ -1251,59 +1303,71 @@ ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out)
 extern "C" {
 
 ats_status ats_level_build_operator(ats_level *L, const ats_coef_desc *c) {
-  CoefArgs a;
-  ats_status s = prepare_operator(L, c, &a);
-  if (s != ATS_OK) return s;
-  cudaStream_t st = L->ctx->stream;
-  CUDA_TRY(cudaMemsetAsync(L->err_flag, 0, sizeof(int), st));
-  CUDA_TRY(launch_coef_build(a, st));
-  // host arrays: the caller may reuse them once the call returns
-  if (c->mem == ATS_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    CoefArgs a;
+    ats_status s = prepare_operator(L, c, &a);
+    if (s != ATS_OK) return s;
+    cudaStream_t st = L->ctx->stream;
+    CUDA_TRY(cudaMemsetAsync(L->err_flag, 0, sizeof(int), st));
+    CUDA_TRY(launch_coef_build(a, st));
+    // host arrays: the caller may reuse them once the call returns
+    if (c->mem == ATS_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_level_get_rhs(ats_level *L, double *b, int mem) {
-  if (!L || !b || !L->built) return ATS_ERR_INVALID_ARG;
-  CUDA_TRY(cudaSetDevice(L->ctx->device));
-  CUDA_TRY(cudaMemcpyAsync(b, L->b64, sizeof(double) * L->N, kind_of(mem, false), L->ctx->stream));
-  CUDA_TRY(cudaStreamSynchronize(L->ctx->stream));
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!L || !b || !L->built) return ATS_ERR_INVALID_ARG;
+    CUDA_TRY(cudaSetDevice(L->ctx->device));
+    CUDA_TRY(cudaMemcpyAsync(b, L->b64, sizeof(double) * L->N, kind_of(mem, false), L->ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->ctx->stream));
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_level_apply(ats_level *L, const double *x, double *y, int mem) {
-  if (!L || !x || !y || !L->built) return ATS_ERR_INVALID_ARG;
-  ats_context *ctx = L->ctx;
-  CUDA_TRY(cudaSetDevice(ctx->device));
-  cudaStream_t st = ctx->stream;
-  double *dx = nullptr, *dy = nullptr;
-  ats_status s;
-  if (mem == ATS_MEM_HOST) {
-    if ((s = dev_alloc_t(ctx, L->N, &dx)) != ATS_OK) return s;
-    if ((s = dev_alloc_t(ctx, L->N, &dy)) != ATS_OK) {
-      dev_free(ctx, dx);
-      return s;
+  try {  // no C++ exception leaves the library
+    if (!L || !x || !y || !L->built) return ATS_ERR_INVALID_ARG;
+    ats_context *ctx = L->ctx;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    double *dx = nullptr, *dy = nullptr;
+    ats_status s;
+    if (mem == ATS_MEM_HOST) {
+      if ((s = dev_alloc_t(ctx, L->N, &dx)) != ATS_OK) return s;
+      if ((s = dev_alloc_t(ctx, L->N, &dy)) != ATS_OK) {
+        dev_free(ctx, dx);
+        return s;
+      }
+      cudaMemcpyAsync(dx, x, sizeof(double) * L->N, cudaMemcpyHostToDevice, st);
     }
-    cudaMemcpyAsync(dx, x, sizeof(double) * L->N, cudaMemcpyHostToDevice, st);
+    SolveDev sd;
+    std::memset(&sd, 0, sizeof(sd));
+    sd.nbr = L->nbr;
+    sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
+    sd.K64 = L->K64;
+    sd.xd64 = L->xd64;
+    sd.h = 0.5 * L->dt / (L->dx * L->dx);
+    sd.n_oct = (int32_t)L->n_oct;
+    cudaError_t e = launch_apply64(&sd, mem == ATS_MEM_HOST ? dx : x, mem == ATS_MEM_HOST ? dy : y, st);
+    if (e == cudaSuccess && mem == ATS_MEM_HOST)
+      e = cudaMemcpyAsync(y, dy, sizeof(double) * L->N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(ctx, dx);
+    dev_free(ctx, dy);
+    if (e != cudaSuccess) {
+      set_error(cudaGetErrorString(e));
+      return ATS_ERR_CUDA;
+    }
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  SolveDev sd;
-  std::memset(&sd, 0, sizeof(sd));
-  sd.nbr = L->nbr;
-  sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
-  sd.K64 = L->K64;
-  sd.xd64 = L->xd64;
-  sd.h = 0.5 * L->dt / (L->dx * L->dx);
-  sd.n_oct = (int32_t)L->n_oct;
-  cudaError_t e = launch_apply64(&sd, mem == ATS_MEM_HOST ? dx : x, mem == ATS_MEM_HOST ? dy : y, st);
-  if (e == cudaSuccess && mem == ATS_MEM_HOST)
-    e = cudaMemcpyAsync(y, dy, sizeof(double) * L->N, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  dev_free(ctx, dx);
-  dev_free(ctx, dy);
-  if (e != cudaSuccess) {
-    set_error(cudaGetErrorString(e));
-    return ATS_ERR_CUDA;
-  }
-  return ATS_OK;
 }
 
 ats_status ats_solve(ats_level *L, const double *rhs, double *x_inout, const ats_solve_opts *opts,
@@ -1381,102 +1445,122 @@ extern "C" {
 
 ats_status ats_solve(ats_level *L, const double *rhs, double *x_inout, const ats_solve_opts *opts,
                      ats_solve_stats *stats) {
-  if (!L || !x_inout) {
-    set_error("null argument");
-    return ATS_ERR_INVALID_ARG;
-  }
-  if (!L->built) {
-    set_error("level operator not built");
-    return ATS_ERR_INVALID_ARG;
-  }
-  ats_solve_opts o = normalize(opts);
-  ats_context *ctx = L->ctx;
-  CUDA_TRY(cudaSetDevice(ctx->device));
-  cudaStream_t st = ctx->stream;
-  ats_status s;
-  // (re)use the cached single-solve plan when its options match
-  if (L->solo && (std::memcmp(&L->solo->opts, &o, sizeof(o)) != 0 ||
-                  L->solo->fp64 != (o.precision == ATS_PREC_FP64))) {
-    plan_free(L->solo);
-    L->solo = nullptr;
-  }
-  if (!L->solo) {
-    ats_level *arr[1] = {L};
-    if ((s = plan_create(ctx, arr, 1, &o, &L->solo)) != ATS_OK) return s;
-  }
-  if (rhs) {
-    if (!L->rhs_save && (s = dev_alloc_t(ctx, L->N, &L->rhs_save)) != ATS_OK) return s;
-    CUDA_TRY(cudaMemcpyAsync(L->rhs_save, L->b64, sizeof(double) * L->N, cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(L->b64, rhs, sizeof(double) * L->N, kind_of(o.mem, true), st));
-  }
-  double *xs[1] = {x_inout};
-  s = plan_run(L->solo, xs, stats);
-  if (rhs) {
-    cudaMemcpyAsync(L->b64, L->rhs_save, sizeof(double) * L->N, cudaMemcpyDeviceToDevice, st);
-    cudaStreamSynchronize(st);
-  }
-  return s;
-}
-
-ats_status ats_batch_create(ats_context *ctx, ats_level *const *levels, int n, const ats_solve_opts *opts,
-                            ats_batch **out) {
-  if (!out) return ATS_ERR_INVALID_ARG;
-  *out = nullptr;
-  Plan *P = nullptr;
-  ats_status s = plan_create(ctx, levels, n, opts, &P);
-  if (s != ATS_OK) return s;
-  ats_batch *B = new (std::nothrow) ats_batch();
-  if (!B) {
-    plan_free(P);
-    return ATS_ERR_OOM;
-  }
-  B->plan = P;
-  *out = B;
-  return ATS_OK;
-}
-
-ats_status ats_batch_solve(ats_batch *B, double *const *x_inout, ats_solve_stats *stats) {
-  if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
-  for (ats_level *L : B->plan->levels) {
+  try {  // no C++ exception leaves the library
+    if (!L || !x_inout) {
+      set_error("null argument");
+      return ATS_ERR_INVALID_ARG;
+    }
     if (!L->built) {
       set_error("level operator not built");
       return ATS_ERR_INVALID_ARG;
     }
+    ats_solve_opts o = normalize(opts);
+    ats_context *ctx = L->ctx;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    ats_status s;
+    // (re)use the cached single-solve plan when its options match
+    if (L->solo && (std::memcmp(&L->solo->opts, &o, sizeof(o)) != 0 ||
+                    L->solo->fp64 != (o.precision == ATS_PREC_FP64))) {
+      plan_free(L->solo);
+      L->solo = nullptr;
+    }
+    if (!L->solo) {
+      ats_level *arr[1] = {L};
+      if ((s = plan_create(ctx, arr, 1, &o, &L->solo)) != ATS_OK) return s;
+    }
+    if (rhs) {
+      if (!L->rhs_save && (s = dev_alloc_t(ctx, L->N, &L->rhs_save)) != ATS_OK) return s;
+      CUDA_TRY(cudaMemcpyAsync(L->rhs_save, L->b64, sizeof(double) * L->N, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(cudaMemcpyAsync(L->b64, rhs, sizeof(double) * L->N, kind_of(o.mem, true), st));
+    }
+    double *xs[1] = {x_inout};
+    s = plan_run(L->solo, xs, stats);
+    if (rhs) {
+      cudaMemcpyAsync(L->b64, L->rhs_save, sizeof(double) * L->N, cudaMemcpyDeviceToDevice, st);
+      cudaStreamSynchronize(st);
+    }
+    return s;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  return plan_run(B->plan, x_inout, stats);
+}
+
+ats_status ats_batch_create(ats_context *ctx, ats_level *const *levels, int n, const ats_solve_opts *opts,
+                            ats_batch **out) {
+  try {  // no C++ exception leaves the library
+    if (!out) return ATS_ERR_INVALID_ARG;
+    *out = nullptr;
+    Plan *P = nullptr;
+    ats_status s = plan_create(ctx, levels, n, opts, &P);
+    if (s != ATS_OK) return s;
+    ats_batch *B = new (std::nothrow) ats_batch();
+    if (!B) {
+      plan_free(P);
+      return ATS_ERR_OOM;
+    }
+    B->plan = P;
+    *out = B;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
+}
+
+ats_status ats_batch_solve(ats_batch *B, double *const *x_inout, ats_solve_stats *stats) {
+  try {  // no C++ exception leaves the library
+    if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
+    for (ats_level *L : B->plan->levels) {
+      if (!L->built) {
+        set_error("level operator not built");
+        return ATS_ERR_INVALID_ARG;
+      }
+    }
+    return plan_run(B->plan, x_inout, stats);
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_batch_destroy(ats_batch *B) {
-  if (!B) return ATS_ERR_INVALID_ARG;
-  if (B->plan) {
-    ats_context *ctx = B->plan->ctx;
-    cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
-    dev_free(ctx, B->d_args);
-    dev_free(ctx, B->d_blk_level);
-    dev_free(ctx, B->d_blk_first);
-    if (B->copy_st) cudaStreamSynchronize(B->copy_st);
-    for (auto &set : B->stage_cell)
-      for (double *p : set) dev_free(ctx, p);
-    for (auto &set : B->stage_face)
-      for (double *p : set) dev_free(ctx, p);
-    if (B->copied) cudaEventDestroy(B->copied);
-    if (B->released) cudaEventDestroy(B->released);
-    if (B->copy_st) cudaStreamDestroy(B->copy_st);
-    plan_free(B->plan);
+  try {  // no C++ exception leaves the library
+    if (!B) return ATS_ERR_INVALID_ARG;
+    if (B->plan) {
+      ats_context *ctx = B->plan->ctx;
+      cudaSetDevice(ctx->device);
+      cudaStreamSynchronize(ctx->stream);
+      dev_free(ctx, B->d_args);
+      dev_free(ctx, B->d_blk_level);
+      dev_free(ctx, B->d_blk_first);
+      if (B->copy_st) cudaStreamSynchronize(B->copy_st);
+      for (auto &set : B->stage_cell)
+        for (double *p : set) dev_free(ctx, p);
+      for (auto &set : B->stage_face)
+        for (double *p : set) dev_free(ctx, p);
+      if (B->copied) cudaEventDestroy(B->copied);
+      if (B->released) cudaEventDestroy(B->released);
+      if (B->copy_st) cudaStreamDestroy(B->copy_st);
+      plan_free(B->plan);
+    }
+    delete B;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  delete B;
-  return ATS_OK;
 }
 
 ats_status ats_batch_run(ats_context *ctx, ats_level *const *levels, int n, double *const *x_inout,
                          const ats_solve_opts *opts, ats_solve_stats *stats) {
-  ats_batch *B = nullptr;
-  ats_status s = ats_batch_create(ctx, levels, n, opts, &B);
-  if (s != ATS_OK) return s;
-  s = ats_batch_solve(B, x_inout, stats);
-  ats_batch_destroy(B);
-  return s;
+  try {  // no C++ exception leaves the library
+    ats_batch *B = nullptr;
+    ats_status s = ats_batch_create(ctx, levels, n, opts, &B);
+    if (s != ATS_OK) return s;
+    s = ats_batch_solve(B, x_inout, stats);
+    ats_batch_destroy(B);
+    return s;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 }  // extern "C"
@@ -1542,255 +1626,275 @@ ats_status batch_stage(ats_batch *B, const ats_coef_desc *coefs, int set, cudaSt
 extern "C" {
 
 ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
-  if (!B || !B->plan || !coefs) {
-    set_error("null argument");
-    return ATS_ERR_INVALID_ARG;
-  }
-  Plan *P = B->plan;
-  ats_context *ctx = P->ctx;
-  const int n = P->n;
-  cudaStream_t st = ctx->stream;
-  ats_status s;
-  std::vector<CoefArgs> args(n);
-  std::vector<ats_coef_desc> dc(coefs, coefs + n);
-  bool any_host = false;
-  for (int k = 0; k < n; ++k) any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
-  bool from_prefetch = false;
-  if (any_host) {
-    // host inputs go to the set not used by the last build (the last solve may
-    // still read that one's E_old); a matching prefetch has copied them already
-    CUDA_TRY(cudaSetDevice(ctx->device));
-    const int set = B->cur_set ^ 1;
-    from_prefetch = B->prefetched && batch_host_ptrs(coefs, n) == B->pf_ptrs;
-    if (from_prefetch) CUDA_TRY(cudaStreamWaitEvent(st, B->copied, 0));
-    else if (B->prefetched && B->copy_st) CUDA_TRY(cudaStreamSynchronize(B->copy_st));  // a stale prefetch
-    if ((s = batch_stage(B, coefs, set, st, !from_prefetch, dc.data())) != ATS_OK) return s;
-    B->cur_set = set;
-  }
-  B->prefetched = false;
-  for (int k = 0; k < n; ++k) {
-    s = prepare_operator(P->levels[k], &dc[k], &args[k]);
-    if (s != ATS_OK) return s;
-  }
-  if (!B->d_args) {
-    if ((s = dev_alloc_t(ctx, n, &B->d_args)) != ATS_OK) return s;
-    std::vector<int32_t> first(n + 1, 0), level;
-    for (int k = 0; k < n; ++k) {
-      const int64_t nb = (P->levels[k]->N + kCoefThreads - 1) / kCoefThreads;
-      first[k + 1] = first[k] + (int32_t)nb;
-      for (int64_t b = 0; b < nb; ++b) level.push_back(k);
+  try {  // no C++ exception leaves the library
+    if (!B || !B->plan || !coefs) {
+      set_error("null argument");
+      return ATS_ERR_INVALID_ARG;
     }
-    B->n_blocks = first[n];
-    if ((s = dev_alloc_t(ctx, n + 1, &B->d_blk_first)) != ATS_OK) return s;
-    if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, B->n_blocks), &B->d_blk_level)) != ATS_OK) return s;
-    CUDA_TRY(cudaMemcpyAsync(B->d_blk_first, first.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
-    if (B->n_blocks)
-      CUDA_TRY(cudaMemcpyAsync(B->d_blk_level, level.data(), sizeof(int32_t) * B->n_blocks, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaStreamSynchronize(st));  // the host tables go out of scope
+    Plan *P = B->plan;
+    ats_context *ctx = P->ctx;
+    const int n = P->n;
+    cudaStream_t st = ctx->stream;
+    ats_status s;
+    std::vector<CoefArgs> args(n);
+    std::vector<ats_coef_desc> dc(coefs, coefs + n);
+    bool any_host = false;
+    for (int k = 0; k < n; ++k) any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
+    bool from_prefetch = false;
+    if (any_host) {
+      // host inputs go to the set not used by the last build (the last solve may
+      // still read that one's E_old); a matching prefetch has copied them already
+      CUDA_TRY(cudaSetDevice(ctx->device));
+      const int set = B->cur_set ^ 1;
+      from_prefetch = B->prefetched && batch_host_ptrs(coefs, n) == B->pf_ptrs;
+      if (from_prefetch) CUDA_TRY(cudaStreamWaitEvent(st, B->copied, 0));
+      else if (B->prefetched && B->copy_st) CUDA_TRY(cudaStreamSynchronize(B->copy_st));  // a stale prefetch
+      if ((s = batch_stage(B, coefs, set, st, !from_prefetch, dc.data())) != ATS_OK) return s;
+      B->cur_set = set;
+    }
+    B->prefetched = false;
+    for (int k = 0; k < n; ++k) {
+      s = prepare_operator(P->levels[k], &dc[k], &args[k]);
+      if (s != ATS_OK) return s;
+    }
+    if (!B->d_args) {
+      if ((s = dev_alloc_t(ctx, n, &B->d_args)) != ATS_OK) return s;
+      std::vector<int32_t> first(n + 1, 0), level;
+      for (int k = 0; k < n; ++k) {
+        const int64_t nb = (P->levels[k]->N + kCoefThreads - 1) / kCoefThreads;
+        first[k + 1] = first[k] + (int32_t)nb;
+        for (int64_t b = 0; b < nb; ++b) level.push_back(k);
+      }
+      B->n_blocks = first[n];
+      if ((s = dev_alloc_t(ctx, n + 1, &B->d_blk_first)) != ATS_OK) return s;
+      if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, B->n_blocks), &B->d_blk_level)) != ATS_OK) return s;
+      CUDA_TRY(cudaMemcpyAsync(B->d_blk_first, first.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
+      if (B->n_blocks)
+        CUDA_TRY(cudaMemcpyAsync(B->d_blk_level, level.data(), sizeof(int32_t) * B->n_blocks, cudaMemcpyHostToDevice, st));
+      CUDA_TRY(cudaStreamSynchronize(st));  // the host tables go out of scope
+    }
+    // upload the per-level arguments only when they changed (same buffers and
+    // dt from step to step is the common case)
+    if (B->h_args.size() != (size_t)n || std::memcmp(B->h_args.data(), args.data(), sizeof(CoefArgs) * n) != 0) {
+      B->h_args = args;
+      CUDA_TRY(cudaMemcpyAsync(B->d_args, B->h_args.data(), sizeof(CoefArgs) * n, cudaMemcpyHostToDevice, st));
+    }
+    CUDA_TRY(launch_coef_build_batch(B->d_args, B->d_blk_level, B->d_blk_first, B->n_blocks, n, P->d_flag_ptrs, st));
+    // host arrays: the caller may reuse them once the call returns
+    if (from_prefetch) CUDA_TRY(cudaEventSynchronize(B->copied));
+    else if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  // upload the per-level arguments only when they changed (same buffers and
-  // dt from step to step is the common case)
-  if (B->h_args.size() != (size_t)n || std::memcmp(B->h_args.data(), args.data(), sizeof(CoefArgs) * n) != 0) {
-    B->h_args = args;
-    CUDA_TRY(cudaMemcpyAsync(B->d_args, B->h_args.data(), sizeof(CoefArgs) * n, cudaMemcpyHostToDevice, st));
-  }
-  CUDA_TRY(launch_coef_build_batch(B->d_args, B->d_blk_level, B->d_blk_first, B->n_blocks, n, P->d_flag_ptrs, st));
-  // host arrays: the caller may reuse them once the call returns
-  if (from_prefetch) CUDA_TRY(cudaEventSynchronize(B->copied));
-  else if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
-  return ATS_OK;
 }
 
 ats_status ats_batch_prefetch_operators(ats_batch *B, const ats_coef_desc *coefs) {
-  if (!B || !B->plan || !coefs) {
-    set_error("null argument");
-    return ATS_ERR_INVALID_ARG;
+  try {  // no C++ exception leaves the library
+    if (!B || !B->plan || !coefs) {
+      set_error("null argument");
+      return ATS_ERR_INVALID_ARG;
+    }
+    Plan *P = B->plan;
+    ats_context *ctx = P->ctx;
+    const int n = P->n;
+    bool any_host = false;
+    for (int k = 0; k < n; ++k) any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
+    B->prefetched = false;
+    if (!any_host) return ATS_OK;  // nothing to copy
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    if (!B->copy_st) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&B->copy_st, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&B->copied, cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&B->released, cudaEventDisableTiming));
+    }
+    // the other set is free once the work queued so far on the context stream
+    // (which read it two builds ago) has run
+    CUDA_TRY(cudaEventRecord(B->released, ctx->stream));
+    CUDA_TRY(cudaStreamWaitEvent(B->copy_st, B->released, 0));
+    std::vector<ats_coef_desc> dc(coefs, coefs + n);
+    ats_status s = batch_stage(B, coefs, B->cur_set ^ 1, B->copy_st, true, dc.data());
+    if (s != ATS_OK) return s;
+    CUDA_TRY(cudaEventRecord(B->copied, B->copy_st));
+    B->pf_ptrs = batch_host_ptrs(coefs, n);
+    B->prefetched = true;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  Plan *P = B->plan;
-  ats_context *ctx = P->ctx;
-  const int n = P->n;
-  bool any_host = false;
-  for (int k = 0; k < n; ++k) any_host = any_host || coefs[k].mem == ATS_MEM_HOST;
-  B->prefetched = false;
-  if (!any_host) return ATS_OK;  // nothing to copy
-  CUDA_TRY(cudaSetDevice(ctx->device));
-  if (!B->copy_st) {
-    CUDA_TRY(cudaStreamCreateWithFlags(&B->copy_st, cudaStreamNonBlocking));
-    CUDA_TRY(cudaEventCreateWithFlags(&B->copied, cudaEventDisableTiming));
-    CUDA_TRY(cudaEventCreateWithFlags(&B->released, cudaEventDisableTiming));
-  }
-  // the other set is free once the work queued so far on the context stream
-  // (which read it two builds ago) has run
-  CUDA_TRY(cudaEventRecord(B->released, ctx->stream));
-  CUDA_TRY(cudaStreamWaitEvent(B->copy_st, B->released, 0));
-  std::vector<ats_coef_desc> dc(coefs, coefs + n);
-  ats_status s = batch_stage(B, coefs, B->cur_set ^ 1, B->copy_st, true, dc.data());
-  if (s != ATS_OK) return s;
-  CUDA_TRY(cudaEventRecord(B->copied, B->copy_st));
-  B->pf_ptrs = batch_host_ptrs(coefs, n);
-  B->prefetched = true;
-  return ATS_OK;
 }
 
 ats_status ats_batch_set_profiling(ats_batch *B, int on) {
-  if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
-  B->plan->profiling = on != 0;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!B || !B->plan) return ATS_ERR_INVALID_ARG;
+    B->plan->profiling = on != 0;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_batch_autotune(ats_batch *B, double *const *x_inout, const int *tiles, int n_tiles,
                               const int *checks, int n_checks, int reps, ats_tune_result *out) {
-  if (!B || !B->plan || !x_inout || n_tiles < 0 || n_checks < 0 || (n_tiles > 0 && !tiles) ||
-      (n_checks > 0 && !checks)) {
-    set_error("ats_batch_autotune: bad arguments");
-    return ATS_ERR_INVALID_ARG;
-  }
-  Plan *P = B->plan;
-  ats_context *ctx = P->ctx;
-  cudaStream_t st = ctx->stream;
-  const int n = P->n;
-  const ats_solve_opts base = P->opts;
-  const bool dev = base.mem == ATS_MEM_DEVICE;
-  const bool restore = base.x0 == ATS_X0_GIVEN;  // every trial starts from the caller's x
-  reps = std::max(1, reps);
-  for (int k = 0; k < n; ++k) {
-    if (!x_inout[k]) {
-      set_error("x_inout[k] is NULL");
+  try {  // no C++ exception leaves the library
+    if (!B || !B->plan || !x_inout || n_tiles < 0 || n_checks < 0 || (n_tiles > 0 && !tiles) ||
+        (n_checks > 0 && !checks)) {
+      set_error("ats_batch_autotune: bad arguments");
       return ATS_ERR_INVALID_ARG;
     }
-    if (!P->levels[k]->built) {
-      set_error("level operator not built");
-      return ATS_ERR_INVALID_ARG;
-    }
-  }
-  static const int kTiles[] = {0, 128, 256, 384, 512};
-  static const int kChecks[] = {8, 16, 32};
-  if (n_tiles == 0) {
-    tiles = kTiles;
-    n_tiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
-  }
-  if (n_checks == 0) {
-    checks = kChecks;
-    n_checks = (int)(sizeof(kChecks) / sizeof(kChecks[0]));
-  }
-  for (int i = 0; i < n_tiles; ++i)
-    if (tiles[i] < 0) {
-      set_error("ats_batch_autotune: negative tile");
-      return ATS_ERR_INVALID_ARG;
-    }
-  // the caller's x, kept for the trials to start from
-  std::vector<int64_t> off(n + 1, 0);
-  for (int k = 0; k < n; ++k) off[k + 1] = off[k] + P->levels[k]->N;
-  double *dsave = nullptr;
-  std::vector<double> hsave;
-  ats_status s;
-  if (restore) {
-    if (dev) {
-      if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, off[n]), &dsave)) != ATS_OK) return s;
-      for (int k = 0; k < n; ++k)
-        CUDA_TRY(cudaMemcpyAsync(dsave + off[k], x_inout[k], sizeof(double) * (off[k + 1] - off[k]),
-                                 cudaMemcpyDeviceToDevice, st));
-    } else {
-      hsave.resize((size_t)off[n]);
-      for (int k = 0; k < n; ++k) std::memcpy(hsave.data() + off[k], x_inout[k], sizeof(double) * (off[k + 1] - off[k]));
-    }
-  }
-  auto put_back = [&]() -> ats_status {
-    if (!restore) return ATS_OK;
+    Plan *P = B->plan;
+    ats_context *ctx = P->ctx;
+    cudaStream_t st = ctx->stream;
+    const int n = P->n;
+    const ats_solve_opts base = P->opts;
+    const bool dev = base.mem == ATS_MEM_DEVICE;
+    const bool restore = base.x0 == ATS_X0_GIVEN;  // every trial starts from the caller's x
+    reps = std::max(1, reps);
     for (int k = 0; k < n; ++k) {
-      const size_t bytes = sizeof(double) * (off[k + 1] - off[k]);
-      if (dev) CUDA_TRY(cudaMemcpyAsync(x_inout[k], dsave + off[k], bytes, cudaMemcpyDeviceToDevice, st));
-      else std::memcpy(x_inout[k], hsave.data() + off[k], bytes);
+      if (!x_inout[k]) {
+        set_error("x_inout[k] is NULL");
+        return ATS_ERR_INVALID_ARG;
+      }
+      if (!P->levels[k]->built) {
+        set_error("level operator not built");
+        return ATS_ERR_INVALID_ARG;
+      }
     }
-    return ATS_OK;
-  };
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  CUDA_TRY(cudaEventCreate(&e0));
-  CUDA_TRY(cudaEventCreate(&e1));
-  // one plan per candidate: a warm-up solve (graph capture), then the fastest of reps solves
-  auto time_plan = [&](Plan *Q, double *ms) -> ats_status {
-    ats_status r;
-    if ((r = put_back()) != ATS_OK) return r;
-    if ((r = plan_run(Q, x_inout, nullptr)) != ATS_OK) return r;
-    *ms = 1e300;
-    for (int i = 0; i < reps; ++i) {
+    static const int kTiles[] = {0, 128, 256, 384, 512};
+    static const int kChecks[] = {8, 16, 32};
+    if (n_tiles == 0) {
+      tiles = kTiles;
+      n_tiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
+    }
+    if (n_checks == 0) {
+      checks = kChecks;
+      n_checks = (int)(sizeof(kChecks) / sizeof(kChecks[0]));
+    }
+    for (int i = 0; i < n_tiles; ++i)
+      if (tiles[i] < 0) {
+        set_error("ats_batch_autotune: negative tile");
+        return ATS_ERR_INVALID_ARG;
+      }
+    // the caller's x, kept for the trials to start from
+    std::vector<int64_t> off(n + 1, 0);
+    for (int k = 0; k < n; ++k) off[k + 1] = off[k] + P->levels[k]->N;
+    double *dsave = nullptr;
+    std::vector<double> hsave;
+    ats_status s;
+    if (restore) {
+      if (dev) {
+        if ((s = dev_alloc_t(ctx, std::max<int64_t>(1, off[n]), &dsave)) != ATS_OK) return s;
+        for (int k = 0; k < n; ++k)
+          CUDA_TRY(cudaMemcpyAsync(dsave + off[k], x_inout[k], sizeof(double) * (off[k + 1] - off[k]),
+                                   cudaMemcpyDeviceToDevice, st));
+      } else {
+        hsave.resize((size_t)off[n]);
+        for (int k = 0; k < n; ++k) std::memcpy(hsave.data() + off[k], x_inout[k], sizeof(double) * (off[k + 1] - off[k]));
+      }
+    }
+    auto put_back = [&]() -> ats_status {
+      if (!restore) return ATS_OK;
+      for (int k = 0; k < n; ++k) {
+        const size_t bytes = sizeof(double) * (off[k + 1] - off[k]);
+        if (dev) CUDA_TRY(cudaMemcpyAsync(x_inout[k], dsave + off[k], bytes, cudaMemcpyDeviceToDevice, st));
+        else std::memcpy(x_inout[k], hsave.data() + off[k], bytes);
+      }
+      return ATS_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    // one plan per candidate: a warm-up solve (graph capture), then the fastest of reps solves
+    auto time_plan = [&](Plan *Q, double *ms) -> ats_status {
+      ats_status r;
       if ((r = put_back()) != ATS_OK) return r;
-      CUDA_TRY(cudaEventRecord(e0, st));
       if ((r = plan_run(Q, x_inout, nullptr)) != ATS_OK) return r;
-      CUDA_TRY(cudaEventRecord(e1, st));
-      CUDA_TRY(cudaEventSynchronize(e1));
-      float t = 0.f;
-      CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-      *ms = std::min(*ms, (double)t);
-    }
-    return ATS_OK;
-  };
-  ats_tune_result res;
-  std::memset(&res, 0, sizeof(res));
-  s = ATS_OK;
-  const bool was_profiling = P->profiling;
-  P->profiling = false;
-  if ((s = time_plan(P, &res.ms_default)) == ATS_OK) {
-    res.tile_octs = base.tile_octs;
-    res.check_every = base.check_every;
-    res.ms = res.ms_default;
-    res.candidates = 1;
-    for (int i = 0; i < n_tiles && s == ATS_OK; ++i) {
-      for (int j = 0; j < n_checks && s == ATS_OK; ++j) {
-        ats_solve_opts o = base;
-        o.tile_octs = tiles[i];
-        o.check_every = checks[j];
-        if (o.tile_octs == base.tile_octs && normalize(&o).check_every == base.check_every) continue;
-        Plan *Q = nullptr;
-        if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) != ATS_OK) break;
-        double ms = 0.0;
-        s = time_plan(Q, &ms);
-        plan_free(Q);
-        if (s != ATS_OK) break;
-        ++res.candidates;
-        if (ms < res.ms) {
-          res.ms = ms;
-          res.tile_octs = o.tile_octs;
-          res.check_every = normalize(&o).check_every;
+      *ms = 1e300;
+      for (int i = 0; i < reps; ++i) {
+        if ((r = put_back()) != ATS_OK) return r;
+        CUDA_TRY(cudaEventRecord(e0, st));
+        if ((r = plan_run(Q, x_inout, nullptr)) != ATS_OK) return r;
+        CUDA_TRY(cudaEventRecord(e1, st));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        *ms = std::min(*ms, (double)t);
+      }
+      return ATS_OK;
+    };
+    ats_tune_result res;
+    std::memset(&res, 0, sizeof(res));
+    s = ATS_OK;
+    const bool was_profiling = P->profiling;
+    P->profiling = false;
+    if ((s = time_plan(P, &res.ms_default)) == ATS_OK) {
+      res.tile_octs = base.tile_octs;
+      res.check_every = base.check_every;
+      res.ms = res.ms_default;
+      res.candidates = 1;
+      for (int i = 0; i < n_tiles && s == ATS_OK; ++i) {
+        for (int j = 0; j < n_checks && s == ATS_OK; ++j) {
+          ats_solve_opts o = base;
+          o.tile_octs = tiles[i];
+          o.check_every = checks[j];
+          if (o.tile_octs == base.tile_octs && normalize(&o).check_every == base.check_every) continue;
+          Plan *Q = nullptr;
+          if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) != ATS_OK) break;
+          double ms = 0.0;
+          s = time_plan(Q, &ms);
+          plan_free(Q);
+          if (s != ATS_OK) break;
+          ++res.candidates;
+          if (ms < res.ms) {
+            res.ms = ms;
+            res.tile_octs = o.tile_octs;
+            res.check_every = normalize(&o).check_every;
+          }
         }
       }
     }
-  }
-  // the batch keeps the fastest configuration, and x_inout holds its solution
-  if (s == ATS_OK && (res.tile_octs != base.tile_octs || res.check_every != base.check_every)) {
-    ats_solve_opts o = base;
-    o.tile_octs = res.tile_octs;
-    o.check_every = res.check_every;
-    Plan *Q = nullptr;
-    if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) == ATS_OK) {
-      plan_free(P);
-      B->plan = P = Q;
+    // the batch keeps the fastest configuration, and x_inout holds its solution
+    if (s == ATS_OK && (res.tile_octs != base.tile_octs || res.check_every != base.check_every)) {
+      ats_solve_opts o = base;
+      o.tile_octs = res.tile_octs;
+      o.check_every = res.check_every;
+      Plan *Q = nullptr;
+      if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) == ATS_OK) {
+        plan_free(P);
+        B->plan = P = Q;
+      }
     }
+    P->profiling = was_profiling;
+    if (s == ATS_OK && (s = put_back()) == ATS_OK) s = plan_run(P, x_inout, nullptr);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (dsave) {
+      cudaStreamSynchronize(st);
+      dev_free(ctx, dsave);
+    }
+    if (s == ATS_OK && out) *out = res;
+    return s;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  P->profiling = was_profiling;
-  if (s == ATS_OK && (s = put_back()) == ATS_OK) s = plan_run(P, x_inout, nullptr);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (dsave) {
-    cudaStreamSynchronize(st);
-    dev_free(ctx, dsave);
-  }
-  if (s == ATS_OK && out) *out = res;
-  return s;
 }
 
 ats_status ats_batch_kernel_stats(const ats_batch *B, ats_kernel_stats *out) {
-  if (!B || !B->plan || !out) return ATS_ERR_INVALID_ARG;
-  const Plan *P = B->plan;
-  out->op_ms = P->op_ms;
-  out->op_bytes = P->op_bytes;
-  out->ref_ms = P->ref_ms;
-  out->ref_bytes = P->ref_bytes;
-  out->upd_ms = P->upd_ms;
-  out->upd_bytes = P->upd_bytes;
-  out->launches = P->launches;
-  out->ticks = P->ticks;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!B || !B->plan || !out) return ATS_ERR_INVALID_ARG;
+    const Plan *P = B->plan;
+    out->op_ms = P->op_ms;
+    out->op_bytes = P->op_bytes;
+    out->ref_ms = P->ref_ms;
+    out->ref_bytes = P->ref_bytes;
+    out->upd_ms = P->upd_ms;
+    out->upd_bytes = P->upd_bytes;
+    out->launches = P->launches;
+    out->ticks = P->ticks;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 }  // extern "C"

@@ -429,230 +429,250 @@ void worker_loop(ats_server *S) {
 extern "C" {
 
 ats_status ats_server_create(int device, size_t mem_budget_bytes, const ats_server_opts *so, ats_server **out) {
-  if (!out) return ATS_ERR_INVALID_ARG;
-  *out = nullptr;
-  ats_server_opts defaults;
-  std::memset(&defaults, 0, sizeof(defaults));
-  const ats_server_opts &o = so ? *so : defaults;
-  ats_server *S = new (std::nothrow) ats_server();
-  if (!S) return ATS_ERR_OOM;
-  ats_status s = ats_context_create(device, 0, &S->ctx);
-  if (s != ATS_OK) {
-    delete S;
-    return s;
+  try {  // no C++ exception leaves the library
+    if (!out) return ATS_ERR_INVALID_ARG;
+    *out = nullptr;
+    ats_server_opts defaults;
+    std::memset(&defaults, 0, sizeof(defaults));
+    const ats_server_opts &o = so ? *so : defaults;
+    ats_server *S = new (std::nothrow) ats_server();
+    if (!S) return ATS_ERR_OOM;
+    ats_status s = ats_context_create(device, 0, &S->ctx);
+    if (s != ATS_OK) {
+      delete S;
+      return s;
+    }
+    S->opts = normalized_opts(&o.solve);
+    S->fp64 = S->opts.precision == ATS_PREC_FP64;
+    S->max_slots = o.max_slots > 0 ? o.max_slots : 1024;
+    S->max_items = o.max_items > 0 ? o.max_items : 1 << 16;
+    S->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)1 << 40;
+    S->slots.resize(S->max_slots);
+    S->pool.reset(new ItemPool(S->max_items));
+    S->st = ctx_stream(S->ctx);
+    auto fail = [&](ats_status code) {
+      ats_server_destroy(S);
+      return code;
+    };
+    if (cudaStreamCreateWithFlags(&S->fj.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->fj.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->fj.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("server: stream or event creation failed");
+      return fail(ATS_ERR_CUDA);
+    }
+    void *p;
+    const size_t ms = S->max_slots, mi = S->max_items;
+    if ((s = ctx_alloc(S->ctx, sizeof(SolveDev) * ms, &p)) != ATS_OK) return fail(s);
+    S->d_solves = (SolveDev *)p;
+    if ((s = ctx_alloc(S->ctx, sizeof(SolveScalars) * 2 * ms, &p)) != ATS_OK) return fail(s);
+    S->d_sc = (SolveScalars *)p;
+    if ((s = ctx_alloc(S->ctx, sizeof(SolveScalars) * ms, &p)) != ATS_OK) return fail(s);
+    S->d_final = (SolveScalars *)p;
+    if ((s = ctx_alloc(S->ctx, sizeof(WorkItem) * mi, &p)) != ATS_OK) return fail(s);
+    S->d_items = (WorkItem *)p;
+    if ((s = ctx_alloc(S->ctx, sizeof(int32_t) * 4 * mi, &p)) != ATS_OK) return fail(s);
+    S->d_lists = (int32_t *)p;
+    if ((s = ctx_alloc(S->ctx, sizeof(int32_t) * ms, &p)) != ATS_OK) return fail(s);
+    S->d_admit = (int32_t *)p;
+    if ((s = ctx_alloc(S->ctx, sizeof(double) * kNumPartials * 3 * mi, &p)) != ATS_OK) return fail(s);
+    S->d_part = (double *)p;
+    if ((s = ctx_alloc(S->ctx, sizeof(TickCtl), &p)) != ATS_OK) return fail(s);
+    S->d_ctl = (TickCtl *)p;
+    if ((s = ctx_alloc(S->ctx, sizeof(int), &p)) != ATS_OK) return fail(s);
+    S->d_active = (int *)p;
+    if (cudaMallocHost(&S->h_final, sizeof(SolveScalars) * ms) != cudaSuccess) return fail(ATS_ERR_OOM);
+    TickCtl c0;
+    std::memset(&c0, 0, sizeof(c0));
+    std::vector<SolveScalars> done_init(ms);
+    for (auto &x : done_init) {
+      std::memset(&x, 0, sizeof(x));
+      x.phase = kDone;
+    }
+    const int zero = 0;
+    if (cudaMemcpyAsync(S->d_ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, S->st) != cudaSuccess ||
+        cudaMemcpyAsync(S->d_active, &zero, sizeof(int), cudaMemcpyHostToDevice, S->st) != cudaSuccess ||
+        cudaMemcpyAsync(S->d_final, done_init.data(), sizeof(SolveScalars) * ms, cudaMemcpyHostToDevice, S->st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(S->st) != cudaSuccess)
+      return fail(ATS_ERR_CUDA);
+    TickArgs &t = S->targs;
+    t.solves = S->d_solves;
+    t.sbuf = S->d_sc;
+    t.final_sc = S->d_final;
+    t.items = S->d_items;
+    t.lists = S->d_lists;
+    t.n_items = S->max_items;
+    t.n_solves = S->max_slots;
+    t.ctl = S->d_ctl;
+    t.p_op = S->d_part;
+    t.p_upd = S->d_part + (size_t)kNumPartials * mi;
+    t.n_active = S->d_active;
+    t.cells = nullptr;
+    tick_grids(S->fp64, false, device, S->grids);
+    S->worker = std::thread(worker_loop, S);
+    *out = S;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  S->opts = normalized_opts(&o.solve);
-  S->fp64 = S->opts.precision == ATS_PREC_FP64;
-  S->max_slots = o.max_slots > 0 ? o.max_slots : 1024;
-  S->max_items = o.max_items > 0 ? o.max_items : 1 << 16;
-  S->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)1 << 40;
-  S->slots.resize(S->max_slots);
-  S->pool.reset(new ItemPool(S->max_items));
-  S->st = ctx_stream(S->ctx);
-  auto fail = [&](ats_status code) {
-    ats_server_destroy(S);
-    return code;
-  };
-  if (cudaStreamCreateWithFlags(&S->fj.aux, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&S->fj.fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&S->fj.join, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("server: stream or event creation failed");
-    return fail(ATS_ERR_CUDA);
-  }
-  void *p;
-  const size_t ms = S->max_slots, mi = S->max_items;
-  if ((s = ctx_alloc(S->ctx, sizeof(SolveDev) * ms, &p)) != ATS_OK) return fail(s);
-  S->d_solves = (SolveDev *)p;
-  if ((s = ctx_alloc(S->ctx, sizeof(SolveScalars) * 2 * ms, &p)) != ATS_OK) return fail(s);
-  S->d_sc = (SolveScalars *)p;
-  if ((s = ctx_alloc(S->ctx, sizeof(SolveScalars) * ms, &p)) != ATS_OK) return fail(s);
-  S->d_final = (SolveScalars *)p;
-  if ((s = ctx_alloc(S->ctx, sizeof(WorkItem) * mi, &p)) != ATS_OK) return fail(s);
-  S->d_items = (WorkItem *)p;
-  if ((s = ctx_alloc(S->ctx, sizeof(int32_t) * 4 * mi, &p)) != ATS_OK) return fail(s);
-  S->d_lists = (int32_t *)p;
-  if ((s = ctx_alloc(S->ctx, sizeof(int32_t) * ms, &p)) != ATS_OK) return fail(s);
-  S->d_admit = (int32_t *)p;
-  if ((s = ctx_alloc(S->ctx, sizeof(double) * kNumPartials * 3 * mi, &p)) != ATS_OK) return fail(s);
-  S->d_part = (double *)p;
-  if ((s = ctx_alloc(S->ctx, sizeof(TickCtl), &p)) != ATS_OK) return fail(s);
-  S->d_ctl = (TickCtl *)p;
-  if ((s = ctx_alloc(S->ctx, sizeof(int), &p)) != ATS_OK) return fail(s);
-  S->d_active = (int *)p;
-  if (cudaMallocHost(&S->h_final, sizeof(SolveScalars) * ms) != cudaSuccess) return fail(ATS_ERR_OOM);
-  TickCtl c0;
-  std::memset(&c0, 0, sizeof(c0));
-  std::vector<SolveScalars> done_init(ms);
-  for (auto &x : done_init) {
-    std::memset(&x, 0, sizeof(x));
-    x.phase = kDone;
-  }
-  const int zero = 0;
-  if (cudaMemcpyAsync(S->d_ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, S->st) != cudaSuccess ||
-      cudaMemcpyAsync(S->d_active, &zero, sizeof(int), cudaMemcpyHostToDevice, S->st) != cudaSuccess ||
-      cudaMemcpyAsync(S->d_final, done_init.data(), sizeof(SolveScalars) * ms, cudaMemcpyHostToDevice, S->st) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(S->st) != cudaSuccess)
-    return fail(ATS_ERR_CUDA);
-  TickArgs &t = S->targs;
-  t.solves = S->d_solves;
-  t.sbuf = S->d_sc;
-  t.final_sc = S->d_final;
-  t.items = S->d_items;
-  t.lists = S->d_lists;
-  t.n_items = S->max_items;
-  t.n_solves = S->max_slots;
-  t.ctl = S->d_ctl;
-  t.p_op = S->d_part;
-  t.p_upd = S->d_part + (size_t)kNumPartials * mi;
-  t.n_active = S->d_active;
-  t.cells = nullptr;
-  tick_grids(S->fp64, false, device, S->grids);
-  S->worker = std::thread(worker_loop, S);
-  *out = S;
-  return ATS_OK;
 }
 
 ats_status ats_server_submit(ats_server *S, const ats_request *r, uint64_t *ticket) {
-  if (!S || !r || !r->level || !r->coef || !ticket) {
-    set_error("ats_server_submit: null argument");
-    return ATS_ERR_INVALID_ARG;
-  }
-  const ats_level_desc &d = *r->level;
-  const ats_coef_desc &c = *r->coef;
-  if (c.mem != ATS_MEM_HOST || d.n_oct <= 0 || !d.oct_xyz || !c.K || !c.E_old || !(c.dt > 0.0)) {
-    set_error("ats_server_submit: request arrays must be host arrays with n_oct > 0, K, E_old and dt > 0");
-    return ATS_ERR_INVALID_ARG;
-  }
-  if ((c.integrator != ATS_INTEGRATOR_BACKWARD_EULER && c.integrator != ATS_INTEGRATOR_CRANK_NICOLSON) ||
-      (c.integrator == ATS_INTEGRATOR_CRANK_NICOLSON && c.s)) {
-    set_error("ats_server_submit: unknown integrator, or a shift s with Crank-Nicolson");
-    return ATS_ERR_INVALID_ARG;
-  }
-  std::unique_ptr<Pending> p(new (std::nothrow) Pending());
-  if (!p) return ATS_ERR_OOM;
-  const size_t n = (size_t)d.n_oct, N = 8 * n, nf = (size_t)d.n_face;
-  p->oct_xyz.assign(d.oct_xyz, d.oct_xyz + 3 * n);
-  if (d.leaf_mask) {
-    p->leaf.assign(d.leaf_mask, d.leaf_mask + n);
-    p->has_leaf = true;
-  }
-  p->dx = d.dx;
-  p->dt = c.dt;
-  if (nf) {
-    p->face_cell.assign(d.face_cell, d.face_cell + nf);
-    p->face_dir.assign(d.face_dir, d.face_dir + nf);
-    p->face_kind.assign(d.face_kind, d.face_kind + nf);
-    p->face_rel.assign(d.face_rel, d.face_rel + nf);
-    if (d.face_alpha) p->face_alpha.assign(d.face_alpha, d.face_alpha + nf);
-    if (c.face_K) p->face_K.assign(c.face_K, c.face_K + nf);
-    if (c.face_E) p->face_E.assign(c.face_E, c.face_E + nf);
-    if (c.face_F) p->face_F.assign(c.face_F, c.face_F + nf);
-  }
-  p->K.assign(c.K, c.K + N);
-  p->E.assign(c.E_old, c.E_old + N);
-  if (c.s) p->s.assign(c.s, c.s + N);
-  if (c.src) p->src.assign(c.src, c.src + N);
-  if (r->x0) p->x0.assign(r->x0, r->x0 + N);
-  p->integrator = c.integrator;
-  if (r->x0 && p->integrator == ATS_INTEGRATOR_CRANK_NICOLSON)
-    for (size_t i = 0; i < N; ++i) p->x0[i] = 0.5 * (p->x0[i] + p->E[i]);  // guess of the half-step root
-  p->tol = r->tol > 0.0 ? r->tol : 1e-10;
-  p->stop_rule = r->stop_rule;
-  p->submitted = Clock::now();
-  p->bytes = estimate_bytes(*p, S->fp64);
-  {
-    // the host part of level creation (neighbour table, interface records) runs
-    // in the submitting thread, so the scheduler only uploads
-    ats_level_desc dd = d;
-    dd.oct_xyz = p->oct_xyz.data();
-    dd.leaf_mask = p->has_leaf ? p->leaf.data() : nullptr;
-    dd.face_cell = p->face_cell.data();
-    dd.face_dir = p->face_dir.data();
-    dd.face_kind = p->face_kind.data();
-    dd.face_rel = p->face_rel.data();
-    dd.face_alpha = p->face_alpha.empty() ? nullptr : p->face_alpha.data();
-    std::string msg = build_layout(dd, p->layout);
-    if (!msg.empty()) {
-      set_error("ats_server_submit: " + msg);
+  try {  // no C++ exception leaves the library
+    if (!S || !r || !r->level || !r->coef || !ticket) {
+      set_error("ats_server_submit: null argument");
       return ATS_ERR_INVALID_ARG;
     }
+    const ats_level_desc &d = *r->level;
+    const ats_coef_desc &c = *r->coef;
+    if (c.mem != ATS_MEM_HOST || d.n_oct <= 0 || !d.oct_xyz || !c.K || !c.E_old || !(c.dt > 0.0)) {
+      set_error("ats_server_submit: request arrays must be host arrays with n_oct > 0, K, E_old and dt > 0");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if ((c.integrator != ATS_INTEGRATOR_BACKWARD_EULER && c.integrator != ATS_INTEGRATOR_CRANK_NICOLSON) ||
+        (c.integrator == ATS_INTEGRATOR_CRANK_NICOLSON && c.s)) {
+      set_error("ats_server_submit: unknown integrator, or a shift s with Crank-Nicolson");
+      return ATS_ERR_INVALID_ARG;
+    }
+    std::unique_ptr<Pending> p(new (std::nothrow) Pending());
+    if (!p) return ATS_ERR_OOM;
+    const size_t n = (size_t)d.n_oct, N = 8 * n, nf = (size_t)d.n_face;
+    p->oct_xyz.assign(d.oct_xyz, d.oct_xyz + 3 * n);
+    if (d.leaf_mask) {
+      p->leaf.assign(d.leaf_mask, d.leaf_mask + n);
+      p->has_leaf = true;
+    }
+    p->dx = d.dx;
+    p->dt = c.dt;
+    if (nf) {
+      p->face_cell.assign(d.face_cell, d.face_cell + nf);
+      p->face_dir.assign(d.face_dir, d.face_dir + nf);
+      p->face_kind.assign(d.face_kind, d.face_kind + nf);
+      p->face_rel.assign(d.face_rel, d.face_rel + nf);
+      if (d.face_alpha) p->face_alpha.assign(d.face_alpha, d.face_alpha + nf);
+      if (c.face_K) p->face_K.assign(c.face_K, c.face_K + nf);
+      if (c.face_E) p->face_E.assign(c.face_E, c.face_E + nf);
+      if (c.face_F) p->face_F.assign(c.face_F, c.face_F + nf);
+    }
+    p->K.assign(c.K, c.K + N);
+    p->E.assign(c.E_old, c.E_old + N);
+    if (c.s) p->s.assign(c.s, c.s + N);
+    if (c.src) p->src.assign(c.src, c.src + N);
+    if (r->x0) p->x0.assign(r->x0, r->x0 + N);
+    p->integrator = c.integrator;
+    if (r->x0 && p->integrator == ATS_INTEGRATOR_CRANK_NICOLSON)
+      for (size_t i = 0; i < N; ++i) p->x0[i] = 0.5 * (p->x0[i] + p->E[i]);  // guess of the half-step root
+    p->tol = r->tol > 0.0 ? r->tol : 1e-10;
+    p->stop_rule = r->stop_rule;
+    p->submitted = Clock::now();
+    p->bytes = estimate_bytes(*p, S->fp64);
+    {
+      // the host part of level creation (neighbour table, interface records) runs
+      // in the submitting thread, so the scheduler only uploads
+      ats_level_desc dd = d;
+      dd.oct_xyz = p->oct_xyz.data();
+      dd.leaf_mask = p->has_leaf ? p->leaf.data() : nullptr;
+      dd.face_cell = p->face_cell.data();
+      dd.face_dir = p->face_dir.data();
+      dd.face_kind = p->face_kind.data();
+      dd.face_rel = p->face_rel.data();
+      dd.face_alpha = p->face_alpha.empty() ? nullptr : p->face_alpha.data();
+      std::string msg = build_layout(dd, p->layout);
+      if (!msg.empty()) {
+        set_error("ats_server_submit: " + msg);
+        return ATS_ERR_INVALID_ARG;
+      }
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->fatal.empty()) {
+      set_error("server failed: " + S->fatal);
+      return ATS_ERR_CUDA;
+    }
+    p->ticket = S->next_ticket++;
+    *ticket = p->ticket;
+    S->queue.push_back(std::move(p));
+    S->cv_work.notify_one();
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  std::lock_guard<std::mutex> lk(S->mu);
-  if (!S->fatal.empty()) {
-    set_error("server failed: " + S->fatal);
-    return ATS_ERR_CUDA;
-  }
-  p->ticket = S->next_ticket++;
-  *ticket = p->ticket;
-  S->queue.push_back(std::move(p));
-  S->cv_work.notify_one();
-  return ATS_OK;
 }
 
 ats_status ats_server_wait(ats_server *S, uint64_t ticket, int64_t timeout_us, double *x_out, ats_result *res) {
-  if (!S) return ATS_ERR_INVALID_ARG;
-  std::unique_lock<std::mutex> lk(S->mu);
-  auto ready = [&] { return S->done.count(ticket) > 0; };
-  if (timeout_us < 0) {
-    S->cv_done.wait(lk, ready);
-  } else if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
-    set_error("ats_server_wait: timed out");
-    return ATS_ERR_TIMEOUT;
+  try {  // no C++ exception leaves the library
+    if (!S) return ATS_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto ready = [&] { return S->done.count(ticket) > 0; };
+    if (timeout_us < 0) {
+      S->cv_done.wait(lk, ready);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+      set_error("ats_server_wait: timed out");
+      return ATS_ERR_TIMEOUT;
+    }
+    Done dn = std::move(S->done[ticket]);
+    S->done.erase(ticket);
+    lk.unlock();
+    if (dn.status == ATS_OK)  // a negative energy in the result: the warning of the solve (here, off the scheduler)
+      for (double v : dn.x)
+        if (v < 0.0) {
+          dn.status = ATS_WARN_NEGATIVE;
+          dn.stats.status = ATS_WARN_NEGATIVE;
+          break;
+        }
+    if (x_out && !dn.x.empty()) std::memcpy(x_out, dn.x.data(), sizeof(double) * dn.x.size());
+    if (res) {
+      res->status = dn.status;
+      res->stats = dn.stats;
+      res->latency_us = dn.latency_us;
+      res->queue_us = dn.queue_us;
+    }
+    return dn.status;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  Done dn = std::move(S->done[ticket]);
-  S->done.erase(ticket);
-  lk.unlock();
-  if (dn.status == ATS_OK)  // a negative energy in the result: the warning of the solve (here, off the scheduler)
-    for (double v : dn.x)
-      if (v < 0.0) {
-        dn.status = ATS_WARN_NEGATIVE;
-        dn.stats.status = ATS_WARN_NEGATIVE;
-        break;
-      }
-  if (x_out && !dn.x.empty()) std::memcpy(x_out, dn.x.data(), sizeof(double) * dn.x.size());
-  if (res) {
-    res->status = dn.status;
-    res->stats = dn.stats;
-    res->latency_us = dn.latency_us;
-    res->queue_us = dn.queue_us;
-  }
-  return dn.status;
 }
 
 ats_status ats_server_stats(ats_server *S, ats_server_counters *out) {
-  if (!S || !out) return ATS_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lk(S->mu);
-  out->completed = S->completed;
-  out->queued = (uint64_t)S->queue.size();
-  out->ticks = S->ticks;
-  out->peak_resident = S->peak_resident;
-  out->resident_bytes = S->resident;
-  return ATS_OK;
+  try {  // no C++ exception leaves the library
+    if (!S || !out) return ATS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->completed = S->completed;
+    out->queued = (uint64_t)S->queue.size();
+    out->ticks = S->ticks;
+    out->peak_resident = S->peak_resident;
+    out->resident_bytes = S->resident;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
+  }
 }
 
 ats_status ats_server_destroy(ats_server *S) {
-  if (!S) return ATS_ERR_INVALID_ARG;
-  {
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->stop = true;
-    S->cv_work.notify_all();
+  try {  // no C++ exception leaves the library
+    if (!S) return ATS_ERR_INVALID_ARG;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->stop = true;
+      S->cv_work.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    if (S->ctx) {
+      cudaStreamSynchronize(S->st);
+      for (auto &sl : S->slots)
+        if (sl.lvl) ats_level_destroy(sl.lvl);
+      if (S->exec) cudaGraphExecDestroy(S->exec);
+      if (S->h_final) cudaFreeHost(S->h_final);
+      if (S->fj.fork) cudaEventDestroy(S->fj.fork);
+      if (S->fj.join) cudaEventDestroy(S->fj.join);
+      if (S->fj.aux) cudaStreamDestroy(S->fj.aux);
+      ats_context_destroy(S->ctx);  // frees every device buffer of the server
+    }
+    delete S;
+    return ATS_OK;
+  } catch (...) {
+    return ats::abi_exception();
   }
-  if (S->worker.joinable()) S->worker.join();
-  if (S->ctx) {
-    cudaStreamSynchronize(S->st);
-    for (auto &sl : S->slots)
-      if (sl.lvl) ats_level_destroy(sl.lvl);
-    if (S->exec) cudaGraphExecDestroy(S->exec);
-    if (S->h_final) cudaFreeHost(S->h_final);
-    if (S->fj.fork) cudaEventDestroy(S->fj.fork);
-    if (S->fj.join) cudaEventDestroy(S->fj.join);
-    if (S->fj.aux) cudaStreamDestroy(S->fj.aux);
-    ats_context_destroy(S->ctx);  // frees every device buffer of the server
-  }
-  delete S;
-  return ATS_OK;
 }
 
 }  // extern "C"
