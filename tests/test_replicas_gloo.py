@@ -50,3 +50,41 @@ def test_reduce_max_without_process_group():
     import bench
 
     assert bench.reduce_max(3.5) == 3.5
+
+
+def _failing_worker(rank, world, port, out):
+    import datetime
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    import bench
+
+    if rank == 1:
+        out[rank] = "left"  # fails between steps: never joins the step's max-over-ranks
+        os._exit(0)
+    try:
+        bench.reduce_max(1.0, torch.device("cpu"))
+        out[rank] = "completed"
+    except Exception as e:  # the collective ends with an error instead of waiting forever
+        out[rank] = "error: " + type(e).__name__
+
+
+@pytest.mark.timeout(120)
+def test_a_rank_that_leaves_is_seen_by_the_others():
+    """A replica that fails between steps: the remaining rank's timing
+    collective (the only one of the replicas path) ends with an error after
+    the process group's short timeout instead of hanging."""
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    ctx = mp.start_processes(_failing_worker, args=(world, port, out), nprocs=world, join=False,
+                             start_method="spawn")
+    try:
+        while not ctx.join(timeout=60):
+            pass
+    except Exception:
+        pass  # a rank's exit is reported by join; the outcome is in `out`
+    assert out.get(1) == "left"
+    assert str(out.get(0, "")).startswith("error"), dict(out)
