@@ -746,7 +746,7 @@ def run_reference(args, rank, world):
 
     oracle.build()
     cores = os.cpu_count() or 1
-    per_step = args.ref_solves_per_step or 4 * cores
+    per_step = args.ref_solves_per_step or 12 * cores
     rng = np.random.default_rng(11)
     with mp.get_context("spawn").Pool(cores) as pool:
         pool.map(_oracle_warm, range(cores), chunksize=1)
@@ -790,7 +790,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="octs per work item (0 = library default)")
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="mixed inner reduction (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-solves-per-step", type=int, default=0, help="0 = four per host core")
+    ap.add_argument("--ref-solves-per-step", type=int, default=0, help="0 = twelve per host core")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
