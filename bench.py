@@ -419,6 +419,9 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_amr:
         amr = run_amr_interfaces(ats, ctx)
 
+    fld_amr = None
+    if rank == 0 and not args.no_fld:
+        fld_amr = run_fld_amr(ats, ctx)
     equilibrium = None
     if rank == 0 and not args.no_equilibrium:
         equilibrium = run_equilibrium(ats, ctx)
@@ -485,6 +488,7 @@ def run_ours(args, rank, world, local):
         "amr_interfaces": amr,
         "crank_nicolson": cn,
         "equilibrium_1d": equilibrium,
+        "fld_amr": fld_amr,
         "dirac_1d": dirac,
         "solve_stats": {"iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
                         "refinements_mean": float(np.mean(refs)),
@@ -527,6 +531,43 @@ def run_amr_interfaces(ats, ctx, coarse_steps=3, use_graph=2, check_every=16):
                      "energy_change_per_step": float((e1 - e0) / e0 / coarse_steps)}
         H.close()
     return out
+
+
+def run_fld_amr(ats, ctx, coarse_steps=3):
+    """The radiation-matter workload: base 128^3 and three refined levels
+    (density above 4^(l+1) x the mean), flux-limited coefficients from each
+    level's E^n, linearised gas coupling, fine levels first, mixed precision
+    certified to 5e-11 per level solve, the device-driven coarse step: time
+    per coarse step (15 level solves) and the solve statistics."""
+    levels, states, k0, cfl = W.config3(n0=128)
+    rho = [s[1] for s in states]
+    H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
+    try:
+        for l, (E, r, t) in enumerate(states):
+            H.set_state(l, E, np.ones_like(E))
+        for l, (E, r, t) in enumerate(states):
+            H.set_fld(l, r, t, k0)
+        kmed = np.median((1.0 / 3.0) / (k0 * rho[0] ** 2))
+        dt = cfl * levels[0].dx ** 2 / (2.0 * kmed)
+        opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=2)
+        code, st = H.advance(0, dt, **opts)  # warm-up (plans, graphs)
+        if code < 0:
+            raise RuntimeError(f"fld warm-up step failed: {code}")
+        its = 0
+        t0 = time.perf_counter()
+        for _ in range(coarse_steps):
+            code, st = H.advance(0, dt, **opts)
+            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
+                raise RuntimeError(f"fld coarse step failed: {code}")
+            its += st["iterations"]
+        el = time.perf_counter() - t0
+    finally:
+        H.close()
+    return {"workload": "4-level AMR radiation-matter: base 128^3 + %s cells, 15 level solves per coarse step, "
+                        "fine first" % "/".join(str(lv.n_cell) for lv in levels[1:]),
+            "coarse_steps": coarse_steps, "ms_per_coarse_step": round(el / coarse_steps * 1e3, 3),
+            "cg_iterations_per_coarse_step": its / coarse_steps,
+            "cells_per_coarse_step": int(sum(lv.n_cell * 2 ** l for l, lv in enumerate(levels)))}
 
 
 def run_equilibrium(ats, ctx):
@@ -799,6 +840,7 @@ def main():
     ap.add_argument("--no-cn", action="store_true")
     ap.add_argument("--no-equilibrium", action="store_true")
     ap.add_argument("--no-dirac", action="store_true")
+    ap.add_argument("--no-fld", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-max-cells", type=int, default=256 ** 3)
