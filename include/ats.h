@@ -139,7 +139,9 @@ typedef struct {
   int max_iter;      /* cap on CG iterations per solve (0 = 20000)            */
   int max_refine;    /* cap on FP64 residual passes (0 = 40)                 */
   double inner_rtol; /* mixed: residual reduction per inner FP32 solve (0 = 1e-5) */
-  int tile_octs;     /* octs per work item, multiple of 32 (0 = autotuned)   */
+  int tile_octs;     /* octs per work item, multiple of 32 (0 = the size rule: */
+                     /* about one item per CTA of the stencil kernel's grid, */
+                     /* 256..1024; ats_batch_autotune tunes it per batch)    */
   int check_every;   /* ticks between host convergence polls (0 = 16)       */
   int use_graph;     /* 1 = each poll interval of check_every ticks is one CUDA graph, the host polls between intervals; 2 = the whole tick loop is one graph (a WHILE conditional node over one interval, ended on the device when no solve is active), the host waits once (with profiling on, 2 runs as 1) */
   int mem;           /* ATS_MEM_HOST / ATS_MEM_DEVICE for x (and rhs)        */
@@ -260,7 +262,7 @@ ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out)
  * operators for every candidate pair (work-item size tile_octs, poll
  * interval check_every) and keeps the fastest, together with the options the
  * batch was created with.  tiles[n_tiles]: octs per work item, 0 = the
- * library's size rule (256, or 1024 for levels above 131 072 octs), others
+ * library's size rule (see ats_solve_opts.tile_octs), others
  * rounded up to a multiple of 32; NULL / 0 = {0, 128, 256, 384, 512}.
  * checks[n_checks]: ticks per CUDA graph and host poll; NULL / 0 = {8, 16,
  * 32}.  reps (>= 1): timed solves per candidate after one warm-up solve (the

@@ -214,7 +214,7 @@ cudaError_t launch_fld_temperature(int64_t N, const uint8_t *leaf, const double 
 // level accessors.
 ats_status solve_dev_for(ats_level *L, const ats_solve_opts &o, bool fp64, int item_begin, int n_items,
                          SolveDev *out);
-int tile_for(int64_t n_oct, int requested);
+int tile_for(int64_t n_oct, int requested, int grid);
 ats_solve_opts normalized_opts(const ats_solve_opts *in);
 double *level_x64(ats_level *L);
 int64_t level_cells(const ats_level *L);

@@ -275,12 +275,17 @@ ats_solve_opts normalize(const ats_solve_opts *in) {
 }
 
 // Octs per work item (one CTA of kThreads threads, one oct per thread and
-// pass).  Items of one pass keep every CTA's loads independent; very large
-// solves take longer items so their last-CTA reduction stays short.
-int choose_tile(int64_t n_oct, int requested) {
+// pass).  A level gets about one item per CTA of the stencil kernel's
+// resident grid `grid` -- a large solve keeps every SM busy with as few
+// per-item reductions as possible -- rounded up to a multiple of 128 octs and
+// kept within 256..1024: smaller levels take 256, and their items spread over
+// the CTAs beside the other solves of a batch.
+int choose_tile(int64_t n_oct, int requested, int grid) {
   if (requested > 0) return std::max(32, (requested + 31) / 32 * 32);
-  if (n_oct <= 131072) return 2 * kThreads;
-  return 8 * kThreads;
+  const int64_t g = std::max(1, grid);
+  const int64_t per_cta = (n_oct + g - 1) / g;
+  const int64_t t = (per_cta + 127) / 128 * 128;
+  return (int)std::min<int64_t>(8 * kThreads, std::max<int64_t>(2 * kThreads, t));
 }
 
 // Copy per-level host arrays into (h2d) or out of one device buffer at the
@@ -383,6 +388,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   P->paper = (o.stop_rule == ATS_STOP_PAPER);
   P->n = n;
   std::vector<WorkItem> items;
+  tick_grids(P->fp64, P->paper, ctx->device, P->grids);  // the item size follows the stencil kernel's grid
   P->h_solves.resize(n);
   P->h_sc.resize(n);
   ats_status s;
@@ -431,7 +437,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     sd.max_iter = o.max_iter;
     sd.max_refine = o.max_refine;
     sd.inner_max = P->fp64 ? o.max_iter : 4000;
-    const int tile = choose_tile(L->n_oct, o.tile_octs);
+    const int tile = choose_tile(L->n_oct, o.tile_octs, P->grids[0]);
     sd.item_begin = (int32_t)items.size();
     for (int64_t b = 0; b < L->n_oct; b += tile) {
       WorkItem w;
@@ -450,7 +456,6 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   P->n_items = (int)items.size();
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
   P->grid = std::max(1, std::min(P->n_items, bps * ctx->num_sms));
-  tick_grids(P->fp64, P->paper, ctx->device, P->grids);
   for (int k = 0; k < 3; ++k) P->grids[k] = std::max(1, std::min(P->n_items, P->grids[k]));
   if ((s = dev_alloc_t(ctx, n, &P->d_solves)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 2 * (size_t)n, &P->d_sc)) != ATS_OK ||
@@ -890,7 +895,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
 }  // namespace
 
 namespace ats {
-int tile_for(int64_t n_oct, int requested) { return choose_tile(n_oct, requested); }
+int tile_for(int64_t n_oct, int requested, int grid) { return choose_tile(n_oct, requested, grid); }
 ats_solve_opts normalized_opts(const ats_solve_opts *in) { return normalize(in); }
 ats_status solve_dev_for(ats_level *L, const ats_solve_opts &o, bool fp64, int item_begin, int n_items,
                          SolveDev *out) {

@@ -214,7 +214,7 @@ ats_status admit_one_impl(ats_server *S, Pending &p, int slot, std::vector<int32
   c.face_E = p.face_E.empty() ? nullptr : p.face_E.data();
   c.face_F = p.face_F.empty() ? nullptr : p.face_F.data();
   if ((s = ats_level_build_operator(sl.lvl, &c)) != ATS_OK) return s;
-  const int tile = tile_for(d.n_oct, S->opts.tile_octs);
+  const int tile = tile_for(d.n_oct, S->opts.tile_octs, S->grids[0]);
   const int n_items = (int)((d.n_oct + tile - 1) / tile);
   if (n_items > S->max_items) {
     set_error("request needs more work items than the server holds");
