@@ -777,6 +777,100 @@ def cpu_baseline(solves, budget_s=15.0, seed=7, gpu_results=None, all_cores=True
     return out
 
 
+def run_configs(ats, ctx):
+    """Every workload configuration timed the same way on the oracle (one
+    host thread, the cpu_baseline of that configuration) and on the GPU (FP64
+    and mixed, after a warm-up), each solve certified to 5e-11, with the GPU
+    result's relative L2 difference to the oracle's:
+      c1 one level, 32^3 Gaussian, one step;
+      c2 two levels, 64^3 + 64^3 central, one coarse step (coarse first, fine
+         ghosts linear in time);
+      c3 four levels, radiation-matter, base 128^3, one coarse step (fine
+         first).
+    (The batched and served configurations are the main line and its serve
+    leg.)"""
+    import oracle
+    from oracle import driver, fld
+
+    out = {}
+    opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, use_graph=2)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    # c1
+    lv, st = W.config1(32)
+    t0 = time.perf_counter()
+    S = oracle.assemble(lv, st.dt, st.K, st.E)
+    xr, info = oracle.pcg(S, st.E, tol=5e-11, stop_rule=oracle.STOP_CERTIFIED)
+    t_or = time.perf_counter() - t0
+    L = ats.Level(ctx, lv)
+    row = {"cells": lv.n_cell, "oracle_ms": round(t_or * 1e3, 3), "iterations": info["iterations"]}
+    for name, prec in (("fp64", ats.ATS_PREC_FP64), ("mixed", ats.ATS_PREC_MIXED)):
+        L.build(st.dt, st.K, st.E)
+        x = st.E.copy()
+        L.solve(x, precision=prec, **opts)
+        t0 = time.perf_counter()
+        reps = 20
+        for _ in range(reps):
+            L.build(st.dt, st.K, st.E)
+            x = st.E.copy()
+            code, _ = L.solve(x, precision=prec, **opts)
+        row[name + "_ms"] = round((time.perf_counter() - t0) / reps * 1e3, 3)
+        row[name + "_rel_l2_vs_oracle"] = rel(x, xr)
+    L.close()
+    out["c1"] = row
+
+    # c2 (coarse first, the configuration's reading)
+    levels, states, dt = W.config2(64)
+    ref = driver.Hierarchy(levels, states, order="coarse_first")
+    t0 = time.perf_counter()
+    ref.advance(0, dt, tol=5e-11)
+    t_or = time.perf_counter() - t0
+    row = {"cells": int(sum(lv.n_cell for lv in levels)), "oracle_ms": round(t_or * 1e3, 1)}
+    for name, prec in (("fp64", ats.ATS_PREC_FP64), ("mixed", ats.ATS_PREC_MIXED)):
+        H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_COARSE_FIRST)
+        for l, (E, K) in enumerate(states):
+            H.set_state(l, E, K)
+        H.advance(0, dt, precision=prec, **opts)  # plans and graphs; the timed step is the same step again
+        for l, (E, K) in enumerate(states):
+            H.set_state(l, E, K)
+        t0 = time.perf_counter()
+        H.advance(0, dt, precision=prec, **opts)
+        row[name + "_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+        row[name + "_rel_l2_vs_oracle"] = max(rel(H.state(l), ref.state(l)) for l in range(len(levels)))
+        H.close()
+    out["c2"] = row
+
+    # c3
+    levels, states, k0, cfl = W.config3(n0=128)
+    rho = [s_[1] for s_ in states]
+    T = [s_[2] for s_ in states]
+    kmed = np.median((1.0 / 3.0) / (k0 * rho[0] ** 2))
+    dt = cfl * levels[0].dx ** 2 / (2.0 * kmed)
+    ref = driver.Hierarchy(levels, [(E, np.ones_like(E)) for E, _, _ in states], order="fine_first",
+                           fld=([r.copy() for r in rho], [t_.copy() for t_ in T], k0))
+    t0 = time.perf_counter()
+    ref.advance(0, dt, tol=5e-11)
+    t_or = time.perf_counter() - t0
+    row = {"cells": int(sum(lv.n_cell for lv in levels)), "oracle_ms": round(t_or * 1e3, 1)}
+    for name, prec in (("fp64", ats.ATS_PREC_FP64), ("mixed", ats.ATS_PREC_MIXED)):
+        H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
+        for timed in (False, True):  # a warm-up step (plans, graphs), then the same step again
+            for l, (E, r, t) in enumerate(states):
+                H.set_state(l, E, np.ones_like(E))
+            for l, (E, r, t) in enumerate(states):
+                H.set_fld(l, r, t, k0)
+            t0 = time.perf_counter()
+            H.advance(0, dt, precision=prec, **opts)
+            el = time.perf_counter() - t0
+        row[name + "_ms"] = round(el * 1e3, 3)
+        row[name + "_rel_l2_vs_oracle"] = max(rel(H.state(l), ref.state(l)) for l in range(len(levels)))
+        H.close()
+    out["c3"] = row
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -841,6 +935,8 @@ def main():
     ap.add_argument("--no-equilibrium", action="store_true")
     ap.add_argument("--no-dirac", action="store_true")
     ap.add_argument("--no-fld", action="store_true")
+    ap.add_argument("--configs", action="store_true",
+                    help="time each workload configuration on the oracle and the GPU (one JSON line) instead")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-max-cells", type=int, default=256 ** 3)
@@ -851,6 +947,20 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group(backend="nccl")
+    if args.configs:
+        if rank != 0:
+            return
+        import torch
+
+        from paper_1401_1112_gb300 import ats, build
+
+        build.build()
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        with ats.Context(0) as ctx:
+            ctx.set_stream(stream.cuda_stream)
+            print(json.dumps({"configs": run_configs(ats, ctx)}), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
