@@ -689,8 +689,6 @@ void plan_bytes(const Plan *P, const unsigned long long cells[kCellCounters], do
   *upd_b = 7 * w * cells[2] + (16 + 2 * w) * cells[3];
 }
 
-// Run a plan to completion.  x_inout[k] (host or device per opts.mem) or the
-// level's current rhs override is handled by the caller.
 // Enqueue the start of a run: refresh the solve descriptors of levels
 // rebuilt since the plan was made, copy x in (device x is read in place,
 // host x goes through one staging buffer, one copy per run of levels whose
@@ -781,6 +779,9 @@ int64_t plan_max_ticks(const Plan *P) {
   return 2 * ((int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2)) + 2 * P->opts.check_every;
 }
 
+// Run a plan to completion: x_inout[k] (host or device per opts.mem) is the
+// initial guess and receives the result.  A right-hand-side override is the
+// caller's: ats_solve writes it into the level's b before and restores b after.
 ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   ats_context *ctx = P->ctx;
   cudaStream_t st = ctx->stream;

@@ -89,6 +89,11 @@ def test_layout_rejects_bad_descriptions(built):
     walls.face_alpha[0] = 1.5
     with pytest.raises(built.AtsError, match="alpha"):
         built.ats_layout_neighbors(walls)
+    # a level without octs
+    empty = W.LevelDesc(np.zeros((0, 3), np.int32), None, 0.1,
+                        *(np.zeros(0, t) for t in (np.int32, np.int8, np.int8, np.int8, np.float64)))
+    with pytest.raises(built.AtsError, match="no octs"):
+        built.ats_layout_neighbors(empty)
     # descriptor on a non-leaf cell
     lv2 = W.box_level(1, 1, 1, 0.1, [(W.DIRICHLET, 1.0)] * 6)
     lv2.leaf = np.array([0xFE], np.uint8)

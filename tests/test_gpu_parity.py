@@ -217,6 +217,42 @@ def test_batch_matches_oracle_and_is_invariant(ats, ctx, prec):
         L.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_state_already_converged(ats, ctx, prec):
+    """Degenerate case: a constant state between zero-flux walls is its own
+    backward-Euler step (every face flux C (x_i - x_j) is exactly zero), so
+    the first FP64 residual is zero and every stopping rule ends the solve
+    there: no CG iteration, x = E^n bitwise.  Beside a solve that does
+    iterate, in one batch, neither result changes."""
+    rng = np.random.default_rng(91)
+    P = ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED
+    lv = W.box_level(5, 3, 4, 0.05)
+    K = np.exp(rng.standard_normal(lv.n_cell))
+    E = np.full(lv.n_cell, 0.7)
+    L = ats.Level(ctx, lv)
+    L.build(10.0 * 0.05 ** 2, K, E)
+    for rule in (ats.ATS_STOP_CERTIFIED, ats.ATS_STOP_RESIDUAL, ats.ATS_STOP_PAPER):
+        x = E.copy()
+        code, stats = L.solve(x, tol=TOL, stop_rule=rule, precision=P)
+        assert code == 0, stats
+        assert stats["iterations"] == 0 and stats["res_norm"] == 0.0
+        np.testing.assert_array_equal(x, E)
+    lv2, st2 = W.random_box_solve(rng, 50)
+    L2 = ats.Level(ctx, lv2)
+    L2.build(st2.dt, st2.K, st2.E, **_faces(st2))
+    _, xr2 = _oracle_solution(lv2, st2)
+    B = ats.Batch(ctx, [L, L2], tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, use_graph=1, check_every=8)
+    xs = [E.copy(), st2.E.copy()]
+    code, stats = B.solve(xs)
+    assert code == 0, stats
+    assert stats[0]["iterations"] == 0 and stats[1]["iterations"] > 0
+    np.testing.assert_array_equal(xs[0], E)
+    assert _rel(xs[1], xr2) <= PAR
+    B.close()
+    L2.close()
+    L.close()
+
+
 def test_bad_input_and_caps(ats, ctx):
     lv, st = W.random_amr_level(81)
     L = ats.Level(ctx, lv)
