@@ -461,6 +461,16 @@ const char *ats_last_error(void);
 /* Host-only layout helper (no device needed): the oct neighbour table of a
  * level, nbr[6 o + dir] = neighbour oct index or -1. */
 ats_status ats_layout_neighbors(const ats_level_desc *desc, int32_t *nbr);
+/* Bounds-checked build (the library compiled with ATS_BOUNDS_CHECK=1): every
+ * index a kernel gathers through (neighbour oct, interface record, face
+ * descriptor, work item, work-list entry) is tested against the length of
+ * the array it indexes; an index out of range is counted on the device and
+ * its access skipped, so a corrupt table gives wrong results and a count,
+ * never an access outside a buffer.  *count (host) receives the number of
+ * such indices met on `device` since the previous call, which resets it;
+ * the call synchronises the device.  The default build has no checks and
+ * sets *count = -1.  Errors: ATS_ERR_INVALID_ARG (null count), ATS_ERR_CUDA. */
+ats_status ats_bounds_violations(int device, long long *count);
 
 #ifdef __cplusplus
 }

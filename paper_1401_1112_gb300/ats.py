@@ -19,7 +19,10 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libats.so")
+# ATS_BOUNDS_CHECK=1 selects the bounds-checked build of the same library
+# (paper_1401_1112_gb300.build.build(checked=True)).
+LIB_PATH = os.path.join(_HERE, "_build_checked" if os.environ.get("ATS_BOUNDS_CHECK") == "1" else "_build",
+                        "libats.so")
 
 ATS_OK = 0
 ATS_ERR_INVALID_ARG = -1
@@ -169,6 +172,7 @@ _SIGS = [
     ("ats_server_stats", ctypes.c_int, [P, ctypes.POINTER(ats_server_counters)]),
     ("ats_solve_noalloc", ctypes.c_int, [ctypes.c_int, P, ctypes.c_int64, P, P, P, ctypes.c_double, P, P,
                                          ctypes.c_double, ctypes.c_int, ctypes.POINTER(ats_solve_stats)]),
+    ("ats_bounds_violations", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
 ]
 
 ATS_NOALLOC_MAX_CELLS = 262144
@@ -464,6 +468,14 @@ def ats_status_string(code: int) -> str:
 
 def ats_last_error() -> str:
     return lib().ats_last_error().decode(errors="replace")
+
+
+def ats_bounds_violations(device: int = 0) -> int:
+    """Out-of-range gathered indices counted since the last call by a
+    bounds-checked build (the count restarts); -1 from the default build."""
+    n = ctypes.c_longlong(0)
+    _check(lib().ats_bounds_violations(device, ctypes.byref(n)), "ats_bounds_violations")
+    return int(n.value)
 
 
 def ats_layout_neighbors(level) -> np.ndarray:

@@ -17,6 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libats.so")
+# the bounds-checked build (ATS_BOUNDS_CHECK=1): same sources, every gathered
+# index range-checked on the device; made on request, not by default
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libats.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["kernels.cu", "runtime.cpp", "layout.cpp", "hierarchy.cpp", "server.cpp", "noalloc.cu", "loop.cu",
@@ -31,37 +35,42 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _flags(extra=()):
-    # ATS_NVCC_DEFINES: optional extra -D definitions (e.g. the register cap
-    # ATS_MINB_F32 of the FP32 tick kernels) for tuning sweeps
-    defines = os.environ.get("ATS_NVCC_DEFINES", "").split()
+def _defines(checked=False):
+    # ATS_NVCC_DEFINES: optional extra -D definitions (e.g. the register caps
+    # ATS_MINB_OP / ATS_MINB_UPD of the FP32 tick kernels) for tuning sweeps
+    return os.environ.get("ATS_NVCC_DEFINES", "").split() + (["-DATS_BOUNDS_CHECK=1"] if checked else [])
+
+
+def _flags(extra=(), checked=False):
+    defines = _defines(checked)
     return [
         "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
         "-I", INCLUDE, "-I", CSRC, *defines, *extra,
     ]
 
 
-def _needs_build() -> bool:
-    if not os.path.exists(LIB):
+def _needs_build(lib=LIB, checked=False) -> bool:
+    if not os.path.exists(lib):
         return True
-    stamp = LIB + ".defines"
-    if (open(stamp).read() if os.path.exists(stamp) else "") != os.environ.get("ATS_NVCC_DEFINES", ""):
+    stamp = lib + ".defines"
+    if (open(stamp).read() if os.path.exists(stamp) else "") != " ".join(_defines(checked)):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    if not force and not _needs_build():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, checked: bool = False) -> str:
+    out_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if not force and not _needs_build(lib, checked):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
+        cmd = [cc, *_flags(extra, checked), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -74,16 +83,17 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if err:
                 sys.stderr.write(err)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    with open(LIB + ".defines", "w") as f:
-        f.write(os.environ.get("ATS_NVCC_DEFINES", ""))
-    return LIB
+    os.replace(tmp, lib)
+    with open(lib + ".defines", "w") as f:
+        f.write(" ".join(_defines(checked)))
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

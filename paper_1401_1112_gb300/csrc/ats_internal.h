@@ -51,7 +51,7 @@ struct SolveDev {
   int32_t max_iter;
   int32_t max_refine;
   int32_t inner_max;    // iterations per inner pass before a restart
-  int32_t pad;
+  int32_t n_xd;         // records in xd64 / xdT (bounds of xrec)
 };
 
 // Per-solve scalars (device).  Double-buffered by tick parity: the kernels of
@@ -121,6 +121,9 @@ struct CoefArgs {
   const int32_t *nbr;   // for the face coefficients
   double *C64;          // [n_oct][3][8] written by the face-coefficient pass
   double src_scale;     // weight of src and face F (1; 1/2 for a Crank-Nicolson half step)
+  int64_t n_rec;        // face records (bounds of frec)
+  int64_t n_xd;         // diagonal-extra records (bounds of xrec)
+  int64_t n_face;       // interface descriptors (bounds of rec_face entries)
 };
 // K, diagonal extras, b and the FP64 face coefficients C64, one thread per cell.
 cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st);

@@ -2,16 +2,18 @@
 //
 //  k_coef_build  cell diffusion coefficients, interface diagonal extras and the
 //                right-hand side b (Sect. 3.1, Eq. Er_imp1; Sect. 3.2 rows).
-//  k_op / k_upd  one device "tick" of every solve in a work list: either one
-//                iteration of the diagonal-preconditioned CG of Sect. 3.3.4
-//                (k_op: p = z + beta p, q = (I + dt A) p, p.q; k_upd:
-//                e += alpha p, r = D z - alpha q, z = D^-1 r, r.z, r.r) or one
-//                FP64 true-residual pass r = b - (I + dt A)(x + e) of the
-//                iterative refinement (k_op) followed by x += e (k_upd).
+//  k_op / k_ref / k_upd  one device "tick" of every solve in a work list.  A
+//                solve in its CG phase does one iteration of the diagonal-
+//                preconditioned CG of Sect. 3.3.4 (k_op: p = z + beta p,
+//                q = (I + dt A) p, p.q; k_upd: e += alpha p, r = D z - alpha q,
+//                z = D^-1 r, r.z, r.r); a solve in its refinement phase does
+//                one FP64 true-residual pass r = b - (I + dt A) x (k_ref, on a
+//                second stream beside k_op), the k_upd of its last inner
+//                iteration having added x += e.
 //
 // Layout: a level is an array of octs; cell c = ix + 2 iy + 4 iz of oct o is
 // element 8 o + c.  One thread owns one oct: its eight cells of every vector
-// come in as two float4 (four double2) loads, the twelve in-oct faces are
+// come in as one 32-byte load (two in FP64), the twelve in-oct faces are
 // computed in registers, and the three out-of-oct faces of each cell come
 // from the six face-neighbour octs (index table), of which only the four
 // facing cells are loaded.  K < 0 marks a cell that is not an unknown of the
@@ -37,9 +39,51 @@
 
 #include "ats_internal.h"
 
+#ifndef ATS_BOUNDS_CHECK
+#define ATS_BOUNDS_CHECK 0
+#endif
+
 namespace ats {
 
+#if ATS_BOUNDS_CHECK
+__device__ unsigned long long g_bound_violations;
+#endif
+
 namespace {
+
+// Bounds-checked build (ATS_BOUNDS_CHECK=1): a gathered index (neighbour oct,
+// record, face, work item, list entry) is tested against the length of the
+// array it indexes before use; an index out of range is counted and the
+// caller skips the access (a neighbour becomes "no neighbour", a work item
+// becomes empty), so no kernel reads or writes outside its buffers.  In the
+// default build the test is constant true and compiles away.
+__device__ __forceinline__ bool idx_ok(long long i, long long n) {
+#if ATS_BOUNDS_CHECK
+  if (i >= 0 && i < n) return true;
+  atomicAdd(&g_bound_violations, 1ull);
+  return false;
+#else
+  (void)i;
+  (void)n;
+  return true;
+#endif
+}
+
+// Neighbour octs: -1 (none) or an oct of the level.
+__device__ __forceinline__ void check_nbr6(int (&nb)[6], int64_t n_oct) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+    if (nb[k] >= 0 && !idx_ok(nb[k], n_oct)) nb[k] = -1;
+}
+
+// Octs of a work item that lie inside its solve's level (all of them unless
+// the bounds-checked build finds the item out of range).
+__device__ __forceinline__ int item_octs(const WorkItem &item, const SolveDev &sd) {
+  if (!idx_ok(item.oct_begin, (long long)sd.n_oct + 1) || !idx_ok(item.n_oct, (long long)sd.n_oct + 1) ||
+      !idx_ok((long long)item.oct_begin + item.n_oct, (long long)sd.n_oct + 1))
+    return 0;
+  return item.n_oct;
+}
 
 constexpr unsigned kFull = 0xffffffffu;
 // resident CTAs per SM the CG tick kernels are compiled for (caps
@@ -316,7 +360,9 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
   const T hT = (T)sd.h;
   int nb[6];
   load_nbr6(sd.nbr, o, nb);
-  const int rec = __ldg(sd.xrec + o);
+  check_nbr6(nb, sd.n_oct);
+  int rec = __ldg(sd.xrec + o);
+  if (rec >= 0 && !idx_ok(rec, sd.n_xd)) rec = -1;
   double xv[8];
   T KTo[8];
   ld8_ro(sd.x64 + 8 * o, xv);
@@ -521,6 +567,7 @@ template <typename T>
 __device__ __forceinline__ void op_load_own(const SolveDev &sd, int o, bool first, const T *__restrict__ pold,
                                             OpOwn<T> &w) {
   load_nbr6(sd.nbr, o, w.nb);
+  check_nbr6(w.nb, sd.n_oct);
   ld8_ro((const T *)sd.KT + 8 * o, w.K);
   ld8_ro((const T *)sd.z + 8 * o, w.z);
   ld8_ro((const T *)sd.dg + 8 * o, w.d);
@@ -638,10 +685,16 @@ __device__ __forceinline__ int stage_items(const TickArgs &a, const int32_t *lis
   if ((int)threadIdx.x < m) {
     const int li = li0 + (int)threadIdx.x * G;
     const bool in0 = li < n0;
-    const int it = in0 ? __ldcg(list0 + li) : __ldcg(list1 + (li - n0));
+    int it = in0 ? __ldcg(list0 + li) : __ldcg(list1 + (li - n0));
+    if (!idx_ok(it, a.n_items)) it = 0;
     slots[threadIdx.x].it = it;
     slots[threadIdx.x].inner = in0 ? 1 : 0;
-    slots[threadIdx.x].item = a.items[it];
+    WorkItem item = a.items[it];
+    if (!idx_ok(item.solve, a.n_solves)) {
+      item.solve = 0;
+      item.n_oct = 0;
+    }
+    slots[threadIdx.x].item = item;
   }
   __syncthreads();
   constexpr int wd = (int)(sizeof(SolveDev) / 8), ws = (int)(sizeof(SolveScalars) / 8);
@@ -690,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_op(TickArgs a
     const double rz_prev = sc.rz;
     const T *pold = (const T *)(pcur ? sd.p1 : sd.p0);
     T *pnew = (T *)(pcur ? sd.p0 : sd.p1);
-    const int oct_end = item.oct_begin + item.n_oct;
+    const int oct_end = item.oct_begin + item_octs(item, sd);
     const int o0 = item.oct_begin + (int)threadIdx.x;
     OpOwn<T> w;
     if (o0 < oct_end) op_load_own(sd, o0, first, pold, w);
@@ -734,7 +787,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ref(TickArgs a) {
     const int it = slots[bi].it;
     const WorkItem item = slots[bi].item;
     const SolveDev &sd = slots[bi].sd;
-    const int oct_end = item.oct_begin + item.n_oct;
+    const int oct_end = item.oct_begin + item_octs(item, sd);
     Acc<T> rr, xx, rz;
     const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
     for (int o = item.oct_begin + (int)threadIdx.x; o < oct_end; o += kThreads)
@@ -762,7 +815,8 @@ __device__ __forceinline__ void commit_solve(const TickArgs &a, int cur, int s, 
     }
   }
   __syncthreads();
-  const int base = *s_base;
+  int base = *s_base;
+  if (base >= 0 && !idx_ok((long long)base + sd.n_items - 1, a.n_items)) base = -1;
   if (base >= 0) {
     int32_t *nl = phase_list(a.lists, a.n_items, cur ^ 1, next.phase);
     for (int k = threadIdx.x; k < sd.n_items; k += kThreads) nl[base + k] = sd.item_begin + k;
@@ -803,7 +857,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocksUpd<T>::value) k_upd(TickAr
     if (inner) {
       const bool first = sc.first != 0;
       const T *p = (const T *)(sc.pcur ? sd.p0 : sd.p1);  // written by k_op this tick
-      const int oct_end = item.oct_begin + item.n_oct;
+      const int oct_end = item.oct_begin + item_octs(item, sd);
       const int o0 = item.oct_begin + (int)threadIdx.x;
       UpdOwn<T> w;
       if (o0 < oct_end) upd_load_own(sd, o0, p, w);
@@ -942,7 +996,7 @@ __device__ __forceinline__ void coef_faces(const CoefArgs &a, int64_t o, int c, 
       oj = o;
     } else {
       const int n = a.nbr[6 * o + 2 * ax + 1];
-      if (n >= 0) oj = n;
+      if (n >= 0 && idx_ok(n, a.n_oct)) oj = n;
     }
     double C = 0.0;
     if (leaf && oj >= 0 && (!a.leaf || ((a.leaf[oj] >> cj) & 1))) C = a.h * (K + a.K[8 * oj + cj]);
@@ -954,7 +1008,8 @@ __device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
   const int64_t o = i >> 3;
   const int c = (int)(i & 7);
   const bool leaf = a.leaf ? ((a.leaf[o] >> c) & 1) : true;
-  const int xr = a.xrec[o];
+  int xr = a.xrec[o];
+  if (xr >= 0 && !idx_ok(xr, a.n_xd)) xr = -1;
   if (!leaf) {
     a.K64[i] = -1.0;
     a.K32[i] = -1.0f;
@@ -973,11 +1028,12 @@ __device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
   double xd = a.s ? a.s[i] : 0.0;
   ok = ok && isfinite(xd) && xd >= 0.0;
   double rhs = E + (a.src ? a.src_scale * a.src[i] : 0.0);
-  const int fr = a.frec[o];
+  int fr = a.frec[o];
+  if (fr >= 0 && !idx_ok(fr, a.n_rec)) fr = -1;
   if (fr >= 0) {
     for (int dir = 0; dir < 6; ++dir) {
       const int f = a.rec_face[(int64_t)fr * 48 + c * 6 + dir];
-      if (f < 0) continue;
+      if (f < 0 || !idx_ok(f, a.n_face)) continue;
       const double Kn = a.face_K ? a.face_K[f] : K;
       const double Enb = a.face_E ? a.face_E[f] : 0.0;
       const double F = a.face_F ? a.src_scale * a.face_F[f] : 0.0;
@@ -1027,7 +1083,7 @@ __global__ void k_coef_build_batch(const CoefArgs *__restrict__ args, const int3
 // towards +a (the in-oct partner when bit a of c is 0, else the facing cell of
 // the +a neighbour oct).
 __device__ __forceinline__ void face_coef_cell(const int32_t *__restrict__ nbr, const double *__restrict__ K64,
-                                               double h, double *__restrict__ C64, int64_t i) {
+                                               double h, double *__restrict__ C64, int64_t i, int64_t n_oct) {
   const int64_t o = i >> 3;
   const int c = (int)(i & 7);
   const double Ki = K64[i];
@@ -1039,7 +1095,7 @@ __device__ __forceinline__ void face_coef_cell(const int32_t *__restrict__ nbr, 
       j = 8 * o + (c | bit);
     } else {
       const int n = nbr[6 * o + 2 * ax + 1];
-      if (n >= 0) j = 8 * (int64_t)n + (c ^ bit);
+      if (n >= 0 && idx_ok(n, n_oct)) j = 8 * (int64_t)n + (c ^ bit);
     }
     double C = 0.0;
     if (j >= 0) {
@@ -1053,7 +1109,7 @@ __device__ __forceinline__ void face_coef_cell(const int32_t *__restrict__ nbr, 
 __global__ void k_face_coef(int64_t n_oct, const int32_t *__restrict__ nbr, const double *__restrict__ K64,
                             double h, double *__restrict__ C64) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 8 * n_oct) face_coef_cell(nbr, K64, h, C64, i);
+  if (i < 8 * n_oct) face_coef_cell(nbr, K64, h, C64, i, n_oct);
 }
 
 __global__ void k_zero_flags(int *const *__restrict__ flags, int n) {
@@ -1200,7 +1256,7 @@ __global__ void k_fld_coef(int64_t n_oct, const int32_t *__restrict__ nbr, const
     const double e_in = E[o * 8 + (c ^ m)];  // the other cell of the oct along a
     const int nb = nbr[o * 6 + 2 * a + b];    // the oct on this cell's outer side
     double g;
-    if (nb >= 0) {
+    if (nb >= 0 && idx_ok(nb, n_oct)) {
       const double e_out = E[(int64_t)nb * 8 + (c ^ m)];
       // b = 0: in-oct neighbour is at +a, outer at -a; b = 1: the reverse
       g = b == 0 ? (e_in - e_out) / (2.0 * dx) : (e_out - e_in) / (2.0 * dx);
@@ -1290,7 +1346,7 @@ __global__ void k_apply64(SolveDev sd, const double *__restrict__ x, double *__r
       off += C * x[jin];
     }
     const int nbo = sd.nbr[(int64_t)o * 6 + 2 * a + ((c >> a) & 1)];
-    if (nbo >= 0) {
+    if (nbo >= 0 && idx_ok(nbo, sd.n_oct)) {
       const int64_t j = (int64_t)nbo * 8 + (c ^ m);
       const double kj = sd.K64[j];
       if (kj >= 0.0) {
@@ -1385,6 +1441,7 @@ __global__ void k_admit(TickArgs a, const int32_t *__restrict__ slots, int n_new
     atomicAdd(a.n_active, 1);
   }
   __syncthreads();
+  if (!idx_ok((long long)base + sd.n_items - 1, a.n_items)) return;
   int32_t *l = a.lists + (size_t)(cur * 2 + kRefine) * a.n_items;
   for (int k = threadIdx.x; k < sd.n_items; k += blockDim.x) l[base + k] = sd.item_begin + k;
 }
@@ -1407,7 +1464,7 @@ __global__ void k_init(const SolveDev *__restrict__ solves, const WorkItem *__re
     const SolveDev &sd = solves[item.solve];
     const double *xs = src ? src[item.solve] : nullptr;
     T *e = (T *)sd.e;
-    const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item.n_oct * 8;
+    const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item_octs(item, sd) * 8;
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
       e[b + k] = T(0);
       // Crank-Nicolson: x is a guess of E^{n+1}, the half-step root is (x + E^n) / 2
@@ -1423,7 +1480,7 @@ __global__ void k_final(const SolveDev *__restrict__ solves, const WorkItem *__r
     double *xd = dst[item.solve];
     if (!xd) continue;
     const SolveDev &sd = solves[item.solve];
-    const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item.n_oct * 8;
+    const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item_octs(item, sd) * 8;
     bool below = false;  // a negative energy in the result (the warning of the solve)
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
       const double v = sd.cn_base ? 2.0 * sd.x64[b + k] - sd.cn_base[b + k] : sd.x64[b + k];
@@ -1475,3 +1532,28 @@ int tick_blocks_per_sm(bool fp64, bool paper) {
 }
 
 }  // namespace ats
+
+// Out-of-range gathered indices counted by a bounds-checked build since the
+// last call (the count restarts at zero); -1 from the default build.
+extern "C" ats_status ats_bounds_violations(int device, long long *count) {
+  if (!count) return ATS_ERR_INVALID_ARG;
+#if ATS_BOUNDS_CHECK
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return ATS_ERR_CUDA;
+  }
+  unsigned long long v = 0;
+  const unsigned long long zero = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpyFromSymbol(&v, ats::g_bound_violations, sizeof(v)) != cudaSuccess ||
+      cudaMemcpyToSymbol(ats::g_bound_violations, &zero, sizeof(zero)) != cudaSuccess) {
+    cudaGetLastError();
+    return ATS_ERR_CUDA;
+  }
+  *count = (long long)v;
+#else
+  (void)device;
+  *count = -1;
+#endif
+  return ATS_OK;
+}

@@ -143,6 +143,7 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
     std::memset(&sd, 0, sizeof(sd));
     sd.nbr = nbr;
     sd.xrec = d_xrec;
+    sd.n_xd = xd ? (int32_t)n_oct : 0;
     sd.K64 = K;
     sd.KT = K;
     sd.xd64 = xd;

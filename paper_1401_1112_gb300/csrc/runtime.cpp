@@ -413,6 +413,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     std::memset(&sd, 0, sizeof(sd));
     sd.nbr = L->nbr;
     sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
+    sd.n_xd = (int32_t)(L->dense_xd ? L->n_oct : L->n_rec);
     sd.K64 = L->K64;
     sd.C64 = L->C64;
     sd.KT = P->fp64 ? (const void *)L->K64 : (const void *)L->K32;
@@ -713,6 +714,7 @@ ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off
       sd.h = h;
       sd.cn_base = L->cn_base;
       sd.xrec = xrec;
+      sd.n_xd = (int32_t)(L->dense_xd ? L->n_oct : L->n_rec);
       sd.xd64 = L->xd64;
       sd.xdT = xdT;
       stale = true;
@@ -906,6 +908,7 @@ ats_status solve_dev_for(ats_level *L, const ats_solve_opts &o, bool fp64, int i
   std::memset(&sd, 0, sizeof(sd));
   sd.nbr = L->nbr;
   sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
+  sd.n_xd = (int32_t)(L->dense_xd ? L->n_oct : L->n_rec);
   sd.K64 = L->K64;
   sd.C64 = L->C64;
   sd.KT = fp64 ? (const void *)L->K64 : (const void *)L->K32;
@@ -1297,6 +1300,9 @@ ats_status prepare_operator(ats_level *L, const ats_coef_desc *c, CoefArgs *out)
   a.err_flag = L->err_flag;
   a.nbr = L->nbr;
   a.C64 = L->C64;
+  a.n_rec = L->n_rec;
+  a.n_xd = dense ? L->n_oct : L->n_rec;
+  a.n_face = L->n_face;
   L->E_dev = E;
   L->cn_base = cn ? E : nullptr;
   L->dt = dt_op;
@@ -1356,6 +1362,7 @@ ats_status ats_level_apply(ats_level *L, const double *x, double *y, int mem) {
     std::memset(&sd, 0, sizeof(sd));
     sd.nbr = L->nbr;
     sd.xrec = L->dense_xd ? L->xrec_dense : L->frec;
+    sd.n_xd = (int32_t)(L->dense_xd ? L->n_oct : L->n_rec);
     sd.K64 = L->K64;
     sd.xd64 = L->xd64;
     sd.h = 0.5 * L->dt / (L->dx * L->dx);

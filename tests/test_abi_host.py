@@ -101,6 +101,20 @@ def test_layout_rejects_bad_descriptions(built):
         built.ats_layout_neighbors(lv2)
 
 
+def test_bounds_checked_build_exports_the_same_entry_points(built):
+    """The bounds-checked build compiles from the same sources and exports
+    every declared entry point; the default build reports that it has no
+    checks (-1) without touching a device."""
+    import ctypes
+
+    from paper_1401_1112_gb300 import build
+
+    checked = ctypes.CDLL(build.build(checked=True))
+    for n in _declared_functions():
+        assert hasattr(checked, n), f"checked build lacks {n}"
+    assert built.ats_bounds_violations(0) == -1
+
+
 def test_status_strings(built):
     for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9, 1):
         assert built.ats_status_string(code) != "unknown status"
