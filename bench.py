@@ -188,7 +188,7 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
 
-    solves = W.config4(n_solves=args.solves, seed=replica_seed(rank))
+    solves = W.ragged_batch(n_solves=args.solves, seed=replica_seed(rank))
     n = len(solves)
     sizes = [lv.n_cell for lv, _ in solves]
     total_cells = int(sum(sizes))
@@ -503,7 +503,7 @@ def run_amr_interfaces(ats, ctx, coarse_steps=3, use_graph=2, check_every=16):
     coarse solve, mixed precision, certified 5e-11) and the relative change
     of the total energy per step (zero-flux walls: only the interfaces can
     change it; the Neumann rows with the stored flux conserve it)."""
-    levels, states, dt = W.config2(n0=64)
+    levels, states, dt = W.two_level_gaussian_64cube(n0=64)
 
     def energy(H):
         return sum(float(np.sum(H.state(l)[lv.leaf_cells()])) * lv.dx ** 3 for l, lv in enumerate(levels))
@@ -539,7 +539,7 @@ def run_fld_amr(ats, ctx, coarse_steps=3):
     level's E^n, linearised gas coupling, fine levels first, mixed precision
     certified to 5e-11 per level solve, the device-driven coarse step: time
     per coarse step (15 level solves) and the solve statistics."""
-    levels, states, k0, cfl = W.config3(n0=128)
+    levels, states, k0, cfl = W.radiation_matter_amr(n0=128)
     rho = [s[1] for s in states]
     H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
     try:
@@ -635,7 +635,7 @@ def run_serve(args, ats, device):
     (measured service times, FIFO queue)."""
     import threading
 
-    reqs = W.config5_requests(n_req=args.serve_requests, seed=1405, hi_cells=args.serve_max_cells)
+    reqs = W.served_requests(n_req=args.serve_requests, seed=1405, hi_cells=args.serve_max_cells)
     built = [W.build_request(r) for r in reqs]
     # plain per-solve FP64: service time of every request (build + solve)
     svc = []
@@ -782,10 +782,10 @@ def run_configs(ats, ctx):
     host thread, the cpu_baseline of that configuration) and on the GPU (FP64
     and mixed, after a warm-up), each solve certified to 5e-11, with the GPU
     result's relative L2 difference to the oracle's:
-      c1 one level, 32^3 Gaussian, one step;
-      c2 two levels, 64^3 + 64^3 central, one coarse step (coarse first, fine
+      gaussian_32cube: one level, 32^3 Gaussian, one step;
+      two_level_64cube: two levels, 64^3 + 64^3 central, one coarse step (coarse first, fine
          ghosts linear in time);
-      c3 four levels, radiation-matter, base 128^3, one coarse step (fine
+      radiation_matter_128cube: four levels, radiation-matter, base 128^3, one coarse step (fine
          first).
     (The batched and served configurations are the main line and its serve
     leg.)"""
@@ -798,8 +798,8 @@ def run_configs(ats, ctx):
     def rel(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
-    # c1
-    lv, st = W.config1(32)
+    # one level, 32^3 Gaussian
+    lv, st = W.gaussian_32cube(32)
     t0 = time.perf_counter()
     S = oracle.assemble(lv, st.dt, st.K, st.E)
     xr, info = oracle.pcg(S, st.E, tol=5e-11, stop_rule=oracle.STOP_CERTIFIED)
@@ -819,10 +819,10 @@ def run_configs(ats, ctx):
         row[name + "_ms"] = round((time.perf_counter() - t0) / reps * 1e3, 3)
         row[name + "_rel_l2_vs_oracle"] = rel(x, xr)
     L.close()
-    out["c1"] = row
+    out["gaussian_32cube"] = row
 
-    # c2 (coarse first, the configuration's reading)
-    levels, states, dt = W.config2(64)
+    # two levels, 64^3 + 64^3, coarse first (the reading of the linear-in-time ghost)
+    levels, states, dt = W.two_level_gaussian_64cube(64)
     ref = driver.Hierarchy(levels, states, order="coarse_first")
     t0 = time.perf_counter()
     ref.advance(0, dt, tol=5e-11)
@@ -840,10 +840,10 @@ def run_configs(ats, ctx):
         row[name + "_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
         row[name + "_rel_l2_vs_oracle"] = max(rel(H.state(l), ref.state(l)) for l in range(len(levels)))
         H.close()
-    out["c2"] = row
+    out["two_level_64cube"] = row
 
-    # c3
-    levels, states, k0, cfl = W.config3(n0=128)
+    # four levels, radiation-matter, base 128^3
+    levels, states, k0, cfl = W.radiation_matter_amr(n0=128)
     rho = [s_[1] for s_ in states]
     T = [s_[2] for s_ in states]
     kmed = np.median((1.0 / 3.0) / (k0 * rho[0] ** 2))
@@ -867,14 +867,14 @@ def run_configs(ats, ctx):
         row[name + "_ms"] = round(el * 1e3, 3)
         row[name + "_rel_l2_vs_oracle"] = max(rel(H.state(l), ref.state(l)) for l in range(len(levels)))
         H.close()
-    out["c3"] = row
+    out["radiation_matter_128cube"] = row
     return out
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    solves = W.config4(n_solves=args.solves, seed=1404)
+    solves = W.ragged_batch(n_solves=args.solves, seed=1404)
     import multiprocessing as mp
 
     import oracle

@@ -60,7 +60,7 @@ def run(ats):
     out["served_code"] = np.array(code)
     out["served"] = x
     srv.close()
-    levels, states, k0, cfl = W.config3(n0=32)
+    levels, states, k0, cfl = W.radiation_matter_amr(n0=32)
     H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
     for l, (E, r, T) in enumerate(states):
         H.set_state(l, E, np.ones_like(E))

@@ -27,7 +27,7 @@ def _rel(a, b):
 
 
 def _setup(ats, ctx, n0):
-    levels, states, k0, cfl = W.config3(n0=n0)
+    levels, states, k0, cfl = W.radiation_matter_amr(n0=n0)
     rho = [s[1] for s in states]
     T = [s[2] for s in states]
     K0, _, _ = fld.coefficients(levels[0], rho[0], T[0], states[0][0], 1.0, k0)
@@ -62,7 +62,7 @@ def test_fld_full_size_converges(ats):
     """The full workload (base 128^3, 4 levels): every level solve of one
     coarse step reaches the certified FP64 residual bound."""
     with ats.Context(0) as ctx:
-        levels, states, k0, cfl = W.config3(n0=128)
+        levels, states, k0, cfl = W.radiation_matter_amr(n0=128)
         rho = [s[1] for s in states]
         H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
         for l, (E, r, t) in enumerate(states):

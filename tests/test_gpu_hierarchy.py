@@ -67,7 +67,7 @@ def test_two_level_heat_full_size(ats, ctx):
     time, 4 coarse steps; GPU against the oracle, and the fine level against
     the analytic Gaussian (a loose pin: the oracle itself is 8.6% off at this
     resolution and time step, falling from 17% at half the resolution)."""
-    levels, states, dt = W.config2(n0=64)
+    levels, states, dt = W.two_level_gaussian_64cube(n0=64)
     H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_COARSE_FIRST)
     for l, (E, K) in enumerate(states):
         H.set_state(l, E, K)

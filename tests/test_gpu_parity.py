@@ -6,7 +6,7 @@ Tolerances (stated per test):
   * solves: both sides stop on the certified rule ||b - A x|| <= tol ||x||
     with tol = 5e-11; the level matrix has lambda_min >= 1, so each solution is
     within 5e-11 (relative) of the exact one and the two differ by <= 1e-10
-    relative L2 -- the benchmark spec's bound, for the FP64 and the refined mixed
+    relative L2 -- the parity bound, for the FP64 and the refined mixed
     path alike.
 """
 import numpy as np
@@ -88,9 +88,9 @@ def test_random_amr_levels_all_face_types(ats, ctx, prec, seed):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_config1_32cube_gaussian(ats, ctx, prec):
+def test_gaussian_32cube(ats, ctx, prec):
     """32^3 unit box, K = 1, dt = 10 dx^2 / 2K, Gaussian + floor, zero-flux walls."""
-    lv, st = W.config1()
+    lv, st = W.gaussian_32cube()
     _, xr = _oracle_solution(lv, st)
     L = ats.Level(ctx, lv)
     L.build(st.dt, st.K, st.E)
@@ -104,9 +104,9 @@ def test_config1_32cube_gaussian(ats, ctx, prec):
     L.close()
 
 
-def test_config1_paper_stopping_rule(ats, ctx):
+def test_gaussian_32cube_paper_stopping_rule(ats, ctx):
     """The paper's rule (L2 relative to r0 and L-inf relative change) at 1e-10."""
-    lv, st = W.config1()
+    lv, st = W.gaussian_32cube()
     S, xr = _oracle_solution(lv, st)
     L = ats.Level(ctx, lv)
     L.build(st.dt, st.K, st.E)
@@ -272,7 +272,7 @@ def test_bad_input_and_caps(ats, ctx):
 
 def test_memory_budget(ats):
     c = ats.Context(0, mem_budget_bytes=64 * 1024)
-    lv, st = W.config1()
+    lv, st = W.gaussian_32cube()
     with pytest.raises(ats.AtsError) as e:
         ats.Level(c, lv)
     assert e.value.code == ats.ATS_ERR_OVER_BUDGET
@@ -484,7 +484,7 @@ def test_full_size_batch_sampled_parity(ats, ctx):
     six drawn at random) match the oracle to 1e-10."""
     import torch
 
-    solves = W.config4(n_solves=512, seed=1404)
+    solves = W.ragged_batch(n_solves=512, seed=1404)
     dev = torch.device("cuda:0")
     sizes = [lv.n_cell for lv, _ in solves]
     offs = np.concatenate([[0], np.cumsum(sizes)])

@@ -20,7 +20,7 @@ def test_batch_is_ordered_after_caller_stream_work():
     build.build()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
-    solves = W.config4(n_solves=192, seed=77, lo_oct=64, hi_oct=1024)
+    solves = W.ragged_batch(n_solves=192, seed=77, lo_oct=64, hi_oct=1024)
     n = len(solves)
     with torch.cuda.stream(stream), ats.Context(0) as ctx:
         ctx.set_stream(stream.cuda_stream)

@@ -29,7 +29,7 @@ def test_faces_match_oracle_driver(ats, seed):
 
 
 def test_two_level_faces(ats):
-    levels, states, _ = W.config2(n0=16)
+    levels, states, _ = W.two_level_gaussian_64cube(n0=16)
     H = driver.Hierarchy(levels, states)
     for l in range(2):
         cell, dr, rel, src = ats.ats_hierarchy_plan_faces(levels, l)
@@ -43,7 +43,7 @@ def test_two_level_faces(ats):
 
 
 def test_unbalanced_rejected(ats):
-    levels, _, _ = W.config2(n0=16)
+    levels, _, _ = W.two_level_gaussian_64cube(n0=16)
     # refine one more level at a corner of level 1 that touches level 0 directly
     fine = levels[1]
     corner = fine.oct_xyz.min(axis=0).astype(np.int64) * 2

@@ -138,7 +138,7 @@ def test_second_moment_identity():
     """Backward Euler on the discrete heat operator grows the second moment by
     exactly 2 K dt M0 per dimension (summation by parts), the continuum
     result; with a pulse far from the walls the identity holds to ~1e-10."""
-    lv, st = W.config1(n=32, cfl=0.25)
+    lv, st = W.gaussian_32cube(n=32, cfl=0.25)
     xyz = W.cell_centres(lv, (-0.5, -0.5, -0.5))
     r2 = (xyz ** 2).sum(1)
     c = 1e-3

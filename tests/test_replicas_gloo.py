@@ -27,7 +27,7 @@ def _worker(rank, world, port, out):
     import workloads as W
 
     seed = bench.replica_seed(rank)
-    solves = W.config4(n_solves=3, seed=seed)
+    solves = W.ragged_batch(n_solves=3, seed=seed)
     m = bench.reduce_max(1.0 + rank, torch.device("cpu"))
     out[rank] = (seed, int(solves[0][0].n_oct), m)
     dist.barrier()

@@ -269,7 +269,7 @@ def dirac_column(E0: float = 1e5, K: float = 1e10):
     return levels, states, 3.125e-15, 64, 0.5 + 0.5 * dx3
 
 
-def config1(n: int = 32, K: float = 1.0, cfl: float = 10.0):
+def gaussian_32cube(n: int = 32, K: float = 1.0, cfl: float = 10.0):
     """Single-level uniform n^3 box on [-1/2, 1/2]^3, constant K, one backward-
     Euler step of dt = cfl * dx^2 / (2K), Gaussian (sigma 0.05) + 1e-3 floor,
     zero-flux walls."""
@@ -320,7 +320,7 @@ def random_box_solve(rng: np.random.Generator, n_oct_target: float, dt_lo=1e-3, 
     return lv, Step(dt=dt, K=K, E=E, face_E=face_E, face_F=face_F)
 
 
-def config4(n_solves: int = 512, seed: int = 1404, lo_oct: int = 64, hi_oct: int = 32768):
+def ragged_batch(n_solves: int = 512, seed: int = 1404, lo_oct: int = 64, hi_oct: int = 32768):
     """Batched level solves: oct counts log-uniform in [lo_oct, hi_oct]
     (8^3 .. 64^3 cells), ragged near-cubic boxes, per-solve dt log-uniform in
     1e-3..1e2 x explicit CFL, K log-normal (sigma 1)."""
@@ -332,7 +332,7 @@ def config4(n_solves: int = 512, seed: int = 1404, lo_oct: int = 64, hi_oct: int
     return out
 
 
-def config5_requests(n_req: int = 2000, seed: int = 1405, lo_cells: int = 16 ** 3, hi_cells: int = 256 ** 3,
+def served_requests(n_req: int = 2000, seed: int = 1405, lo_cells: int = 16 ** 3, hi_cells: int = 256 ** 3,
                      rate: float = 1.0):
     """Served request stream: Poisson arrival times (rate per second), cells
     log-uniform in [lo_cells, hi_cells], Dirichlet / Neumann / Robin walls,
@@ -463,7 +463,7 @@ def balance_refinement(existing_cells: np.ndarray, want: np.ndarray, domain_cell
     return np.array(keep, dtype=np.int64).reshape(-1, 3)
 
 
-def config2(n0: int = 64, K: float = 1.0, cfl: float = 10.0, sigma: float = 0.05):
+def two_level_gaussian_64cube(n0: int = 64, K: float = 1.0, cfl: float = 10.0, sigma: float = 0.05):
     """Two-level heat test: base n0^3 on [-1/2, 1/2]^3, level 1 (2x) covering
     the central 1/8 of the volume ([-1/4, 1/4]^3), constant K, Gaussian pulse
     at the origin; dt_coarse = cfl dx0^2 / (2K), fine substeps dt/2.  Returns
@@ -527,8 +527,8 @@ def _trilinear(field: np.ndarray, pts: np.ndarray) -> np.ndarray:
     return out
 
 
-def config3(n0: int = 128, n_levels: int = 4, sigma_ln: float = 1.5, r0: float = 0.05, seed: int = 1403,
-            cfl: float = 30.0):
+def radiation_matter_amr(n0: int = 128, n_levels: int = 4, sigma_ln: float = 1.5, r0: float = 0.05,
+                         seed: int = 1403, cfl: float = 30.0):
     """FLD radiation-matter workload on an AMR grid: base n0^3 on
     [-1/2, 1/2]^3; density = trilinear interpolation of a seeded log-normal
     base field (sigma_ln, mean 1) times a central core 1/(1+(r/r0)^2); a cell
