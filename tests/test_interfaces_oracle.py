@@ -9,6 +9,11 @@ do not depend on the implementation.
   the energy their coarse-to-fine faces delivered minus the fine-side energy
   stored for them; Robin rows change it by alpha times that Dirichlet-type
   mismatch ((1 - alpha) of the energy is conserved).
+* Sect. 3.3.5: the flux-conserving (Neumann) rows can drive a level's energy
+  negative; the Dirichlet rows cannot.  With Dirichlet rows and no source
+  every level matrix is an M-matrix whose rows sum to 1 plus the Dirichlet
+  weights, so the solution obeys the discrete maximum principle: it stays
+  between the least and the greatest of E^n and the ghost values.
 * In a 1D column with constant K the change equals the paper's two-level
   mismatch expression (Sect. 3.3.2, with the fine-to-coarse flux
   (E_1 - E_c) + (E_2 - E_c), and the oct mean of the fine cells where the
@@ -113,3 +118,25 @@ def test_column_matches_the_papers_mismatch_expression():
     de = H.energy() - e0
     assert abs(de) > 1e-8 * e0
     assert abs(de - expected) <= 1e-11 * abs(e0), (de, expected)
+
+
+@pytest.mark.parametrize("seed", [1, 5])
+def test_dirichlet_rows_keep_the_maximum_principle_neumann_rows_do_not(seed):
+    levels, states, dt = W.random_hierarchy(seed, n0=8, n_levels=3)
+    lo = min(float(e.min()) for e, _ in states)
+    hi = max(float(e.max()) for e, _ in states)
+    mins = {}
+    for interface in ("dirichlet", "neumann"):
+        H = driver.Hierarchy(levels, [(e.copy(), k.copy()) for e, k in states], order="fine_first",
+                             interface=interface)
+        mn, mx = np.inf, -np.inf
+        for _ in range(2):
+            H.advance(0, dt, tol=TOL)
+            for l, lv in enumerate(levels):
+                leaf = H.state(l)[lv.leaf_cells()]
+                mn, mx = min(mn, float(leaf.min())), max(mx, float(leaf.max()))
+        mins[interface] = mn
+        if interface == "dirichlet":
+            assert lo - 1e-10 <= mn and mx <= hi + 1e-10, (lo, hi, mn, mx)
+    assert mins["neumann"] < 0.0, mins
+
