@@ -203,16 +203,17 @@ struct Plan {
   int *h_active = nullptr;         // pinned [2]: one per poll slot
   std::vector<SolveDev> h_solves;
   std::vector<SolveScalars> h_sc;
-  cudaGraphExec_t exec = nullptr;
-  int graph_ticks = 0;
+  cudaGraphExec_t exec = nullptr;          // one interval of ticks
+  cudaGraphExec_t exec_prof[2] = {nullptr, nullptr};  // the same with the timing events of set 0 / 1
   // use_graph = 2: the whole tick loop as one graph (WHILE node over one
   // interval of ticks); d_loop counts the intervals run
   cudaGraphExec_t loop_exec = nullptr;
   int *d_loop = nullptr;
   int loop_max = 0;
-  bool graph_profiled = false;
   bool profiling = false;
-  std::vector<cudaEvent_t> evs;  // chunk start, then kTickEvents per tick of a chunk
+  // two sets (by poll slot) of: chunk start, then kTickEvents per tick of a
+  // chunk, so that one interval runs while the other's events are read
+  std::vector<cudaEvent_t> evs;
   cudaEvent_t poll_ev[2] = {nullptr, nullptr};
   TickStreams fj{nullptr, nullptr, nullptr};  // k_ref's stream, fork / join events
   cudaStream_t side = nullptr;                // timing events (profiling)
@@ -330,6 +331,8 @@ void plan_free(Plan *P) {
   if (!P) return;
   ats_context *ctx = P->ctx;
   if (P->exec) cudaGraphExecDestroy(P->exec);
+  for (auto g : P->exec_prof)
+    if (g) cudaGraphExecDestroy(g);
   if (P->loop_exec) cudaGraphExecDestroy(P->loop_exec);
   dev_free(ctx, P->d_loop);
   for (auto e : P->evs) cudaEventDestroy(e);
@@ -523,8 +526,10 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   return ATS_OK;
 }
 
+size_t events_per_set(const Plan *P) { return 1 + kTickEvents * (size_t)P->opts.check_every; }
+
 ats_status plan_ensure_events(Plan *P) {
-  const size_t need = 1 + kTickEvents * (size_t)P->opts.check_every;
+  const size_t need = 2 * events_per_set(P);
   while (P->evs.size() < need) {
     cudaEvent_t e;
     CUDA_TRY(cudaEventCreate(&e));
@@ -533,19 +538,21 @@ ats_status plan_ensure_events(Plan *P) {
   return ATS_OK;
 }
 
-// `k` ticks on st; when profiling, with timing events on the side stream
-// (chunk start, then per tick), the side stream rejoining st at the end.
-cudaError_t timed_ticks(Plan *P, const TickArgs &ta, cudaStream_t st, int k, bool capture) {
+// `k` ticks on st; when profiling, with the timing events of event set `set`
+// on the side stream (chunk start, then per tick), the side stream rejoining
+// st at the end.
+cudaError_t timed_ticks(Plan *P, const TickArgs &ta, cudaStream_t st, int k, bool capture, int set) {
   cudaError_t err = cudaSuccess;
   if (!P->profiling) {
     for (int t = 0; t < k && err == cudaSuccess; ++t)
       err = launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, nullptr, capture);
     return err;
   }
+  cudaEvent_t *evs = &P->evs[set * events_per_set(P)];
   TickTiming tt{P->side, P->mark, nullptr};
-  if ((err = record_after(tt, P->evs[0], st, capture)) != cudaSuccess) return err;
+  if ((err = record_after(tt, evs[0], st, capture)) != cudaSuccess) return err;
   for (int t = 0; t < k && err == cudaSuccess; ++t) {
-    tt.ev = &P->evs[1 + kTickEvents * t];
+    tt.ev = &evs[1 + kTickEvents * t];
     err = launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, &tt, capture);
   }
   if (err != cudaSuccess) return err;
@@ -598,17 +605,16 @@ ats_status plan_ensure_loop(Plan *P, int max_chunks) {
   return ATS_OK;
 }
 
-// Enqueue one poll interval (check_every ticks) on the stream.
+// Enqueue one poll interval (check_every ticks) on the stream; when
+// profiling, its timing events are the set of this poll slot.
 ats_status plan_enqueue_chunk(Plan *P) {
   cudaStream_t st = P->ctx->stream;
   const int k = P->opts.check_every;
   const bool prof = P->profiling;
+  const int set = P->slot;
   if (P->opts.use_graph) {
-    if (P->exec && P->graph_profiled != prof) {
-      cudaGraphExecDestroy(P->exec);
-      P->exec = nullptr;
-    }
-    if (!P->exec) {
+    cudaGraphExec_t &exec = prof ? P->exec_prof[set] : P->exec;
+    if (!exec) {
       if (prof) {
         ats_status s = plan_ensure_events(P);
         if (s != ATS_OK) return s;
@@ -618,7 +624,7 @@ ats_status plan_enqueue_chunk(Plan *P) {
       cudaError_t err = cudaSuccess;
       TickArgs ta = P->targs;
       if (!prof) ta.cells = nullptr;
-      err = timed_ticks(P, ta, st, k, true);
+      err = timed_ticks(P, ta, st, k, true, set);
       cudaError_t err2 = cudaStreamEndCapture(st, &g);
       if (err != cudaSuccess || err2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -626,17 +632,15 @@ ats_status plan_enqueue_chunk(Plan *P) {
         set_error(std::string("graph capture failed: ") + cudaGetErrorString(err != cudaSuccess ? err : err2));
         return ATS_ERR_CUDA;
       }
-      err = cudaGraphInstantiate(&P->exec, g, 0);
+      err = cudaGraphInstantiate(&exec, g, 0);
       cudaGraphDestroy(g);
       if (err != cudaSuccess) {
-        P->exec = nullptr;
+        exec = nullptr;
         set_error(std::string("graph instantiate failed: ") + cudaGetErrorString(err));
         return ATS_ERR_CUDA;
       }
-      P->graph_profiled = prof;
-      P->graph_ticks = k;
     }
-    CUDA_TRY(cudaGraphLaunch(P->exec, st));
+    CUDA_TRY(cudaGraphLaunch(exec, st));
   } else {
     if (prof) {
       ats_status s = plan_ensure_events(P);
@@ -644,7 +648,7 @@ ats_status plan_enqueue_chunk(Plan *P) {
     }
     TickArgs ta = P->targs;
     if (!prof) ta.cells = nullptr;
-    CUDA_TRY(timed_ticks(P, ta, st, k, false));
+    CUDA_TRY(timed_ticks(P, ta, st, k, false, set));
   }
   P->ticks += k;
   P->launches += 3 * k;
@@ -655,13 +659,15 @@ ats_status plan_enqueue_chunk(Plan *P) {
 }
 
 // Per tick: k_op and k_ref both start when the previous k_upd (or the chunk)
-// ends; k_upd starts when the later of the two ends.
-ats_status plan_collect_events(Plan *P) {
+// ends; k_upd starts when the later of the two ends.  `set`: the event set of
+// the interval (its poll slot).
+ats_status plan_collect_events(Plan *P, int set) {
   const int k = P->opts.check_every;
-  cudaEvent_t prev = P->evs[0];
+  cudaEvent_t *evs = &P->evs[set * events_per_set(P)];
+  cudaEvent_t prev = evs[0];
   for (int t = 0; t < k; ++t) {
     float a = 0.f, b = 0.f, c = 0.f, order = 0.f;
-    cudaEvent_t *e = &P->evs[1 + kTickEvents * t];
+    cudaEvent_t *e = &evs[1 + kTickEvents * t];
     CUDA_TRY(cudaEventElapsedTime(&a, prev, e[0]));
     CUDA_TRY(cudaEventElapsedTime(&b, prev, e[1]));
     CUDA_TRY(cudaEventElapsedTime(&order, e[0], e[1]));
@@ -804,6 +810,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   // conditional body): the whole loop is one graph launch, ended on the device
   const bool device_loop = P->opts.use_graph == 2 && !P->profiling;
   int chunks_run = 0;
+  int drain_slot = 0, drain_n = 0;  // intervals still queued when the host loop ended
   if (device_loop) {
     const int max_chunks = (int)std::min<int64_t>((max_ticks + P->opts.check_every - 1) / P->opts.check_every, 1 << 30);
     if ((s = plan_ensure_loop(P, max_chunks)) != ATS_OK) return s;
@@ -812,17 +819,16 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
     CUDA_TRY(cudaMemcpyAsync(P->h_active, P->d_loop, sizeof(int), cudaMemcpyDeviceToHost, st));  // pinned
   } else {
   // Keep one poll interval queued ahead of the one being polled, so the GPU
-  // never idles on the host's check (not when profiling: the per-tick events
-  // must be read back before they are recorded again).  Extra intervals after
-  // convergence are no-ops: every work item of a finished solve is skipped.
-  const bool pipelined = !P->profiling;
+  // never idles on the host's check.  Extra intervals after convergence are
+  // no-ops: every work item of a finished solve is skipped.  When profiling,
+  // the two queued intervals record into the two event sets (one per poll
+  // slot), and an interval's events are read before its slot is reused; the
+  // interval still queued at the end is read too, so the kernel times cover
+  // every tick that ran.
   P->slot = 0;
   int pending = 0;  // intervals enqueued but not yet polled
   int poll_slot = 0;
-  if ((s = plan_enqueue_chunk(P)) != ATS_OK) return s;
-  ++pending;
-  ticks += P->opts.check_every;
-  if (pipelined) {
+  for (int k = 0; k < 2; ++k) {
     if ((s = plan_enqueue_chunk(P)) != ATS_OK) return s;
     ++pending;
     ticks += P->opts.check_every;
@@ -830,11 +836,11 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   for (;;) {
     CUDA_TRY(cudaEventSynchronize(P->poll_ev[poll_slot]));
     const int active = P->h_active[poll_slot];
+    if (P->profiling) {
+      if ((s = plan_collect_events(P, poll_slot)) != ATS_OK) return s;
+    }
     poll_slot ^= 1;
     --pending;
-    if (P->profiling) {
-      if ((s = plan_collect_events(P)) != ATS_OK) return s;
-    }
     if (active <= 0) break;
     if (ticks >= max_ticks) {
       timed_out = true;
@@ -844,7 +850,8 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
     ++pending;
     ticks += P->opts.check_every;
   }
-  (void)pending;
+  drain_slot = poll_slot;
+  drain_n = pending;
   }
   // copy-out
   CUDA_TRY(cudaMemsetAsync(P->d_flags + n, 0, sizeof(int) * n, st));
@@ -861,6 +868,12 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, n, P->d_flags, st));
   CUDA_TRY(cudaMemcpyAsync(flags.data(), P->d_flags, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (P->profiling) {
+    for (int k = 0; k < drain_n; ++k, drain_slot ^= 1) {
+      ats_status s3 = plan_collect_events(P, drain_slot);
+      if (s3 != ATS_OK) return s3;
+    }
+  }
   if (device_loop) {
     chunks_run = P->h_active[0];
     P->ticks = chunks_run * P->opts.check_every;
