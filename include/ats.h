@@ -246,7 +246,12 @@ ats_status ats_batch_run(ats_context *ctx, ats_level *const *levels, int n, doub
 /* Kernel timing of the last ats_batch_solve, when profiling is on: CUDA
  * events around every tick kernel (also inside the replayed graphs), summed
  * per kernel, with the algorithmic bytes each moved (compulsory traffic of
- * the vectors and coefficients the kernel must read and write once). */
+ * the vectors and coefficients the kernel must read and write once).  A
+ * profiled solve is scheduled like an unprofiled one (one poll interval
+ * queued ahead, the events in two alternating sets; with use_graph = 2 it
+ * runs as use_graph = 1, a conditional graph body holding no events), and
+ * the times include every interval enqueued, the no-op one still queued when
+ * the last solve finished included. */
 typedef struct {
   double op_ms, op_bytes;    /* CG op kernel: p = z + beta p, q = A p, p.q        */
   double ref_ms, ref_bytes;  /* FP64 refinement residual kernel                  */
