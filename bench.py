@@ -34,7 +34,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -790,7 +789,7 @@ def run_configs(ats, ctx):
     (The batched and served configurations are the main line and its serve
     leg.)"""
     import oracle
-    from oracle import driver, fld
+    from oracle import driver
 
     out = {}
     opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, use_graph=2)

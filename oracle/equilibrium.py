@@ -33,7 +33,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import DIRICHLET, STOP_CERTIFIED, assemble, pcg  # noqa: F401
+from . import STOP_CERTIFIED, assemble, pcg
 
 A_EXP = 1.5          # a in kappa_R = 1e10 E^a (Sect. 4.2)
 E_LEFT, E_RIGHT = 4.0, 0.5
