@@ -87,37 +87,47 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms during the
+    timed region: sampling starts (and its first sample is awaited) before
+    the region, each line is stamped on arrival, and only the lines that
+    arrived inside the region are summarised (all lines if none did, which
+    "samples_in_region": 0 then says)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
         self._t = None
+        self._first = threading.Event()
 
-    def start(self):
+    def start(self, wait_s: float = 3.0):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self._t = threading.Thread(target=self._read, daemon=True)
         self._t.start()
+        self._first.wait(wait_s)  # sampling is live before the caller's region starts
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+            self._first.set()
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples that arrived in [t0, t1 + one period]
+        (perf_counter times; None: every sample)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(2.0 * self.PERIOD_MS / 1e3)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -125,9 +135,19 @@ class ClockSampler:
             self.proc.kill()
         if self._t:
             self._t.join(timeout=2)
+        lines = list(self.lines)
+        inside = lines
+        if t0 is not None and t1 is not None:
+            inside = [(t, ln) for t, ln in lines if t0 <= t <= t1 + self.PERIOD_MS / 1e3]
+        summary = self._summarise(inside if inside else lines)
+        summary["samples_in_region"] = len(inside) if (t0 is not None and t1 is not None) else summary["samples"]
+        return summary
+
+    @staticmethod
+    def _summarise(lines):
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -268,8 +288,9 @@ def run_ours(args, rank, world, local):
 
     batch.set_profiling(True)
     sampler = ClockSampler(local)
-    barrier()
     sampler.start()
+    barrier()
+    t_region = time.perf_counter()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     acc = {"op_ms": 0.0, "op_bytes": 0.0, "ref_ms": 0.0, "ref_bytes": 0.0, "upd_ms": 0.0, "upd_bytes": 0.0,
@@ -284,7 +305,7 @@ def run_ours(args, rank, world, local):
         launches += ks["launches"] + 5  # tick kernels + operator build (2) + init, final, flag gather
     ev1.record(stream)
     barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop(t_region, time.perf_counter())
     ms = reduce_max(ev0.elapsed_time(ev1), dev)
     batch.set_profiling(False)
     value = n * args.steps * world / (ms / 1e3)
