@@ -426,13 +426,14 @@ ats_status ats_server_stats(ats_server *server, ats_server_counters *out);
 
 /* ---- allocation-free solve ------------------------------------------------- */
 /* The paper has no counterpart to this entry point: it is a service for
- * callers that cannot allocate device memory (code inside a CUDA stream
- * capture, plug-ins confined to a memory pool owned by their host program,
- * processes whose allocator belongs to another runtime).  It solves one level
- * like ats_solve with ATS_PREC_FP64 and ATS_STOP_RESIDUAL, but calls no
- * cudaMalloc or cudaFree: its CG vectors, partial sums, work list and
- * scalars live in one fixed device array inside the library (about 19 MB,
- * held by every GPU that loads the library until the process exits).
+ * callers that cannot allocate device memory -- plug-ins confined to a memory
+ * pool owned by their host program, and processes whose device memory belongs
+ * to another runtime's allocator (a framework's caching allocator) that must
+ * not be bypassed.  It solves one level like ats_solve with ATS_PREC_FP64 and
+ * ATS_STOP_RESIDUAL, but calls no cudaMalloc or cudaFree: its CG vectors,
+ * partial sums, work list and scalars live in one fixed device array inside
+ * the library (about 19 MB, held by every GPU that loads the library until
+ * the process exits).
  *
  * Arguments (all arrays are DEVICE pointers, FP64, read in stream order on
  * `stream`, a cudaStream_t or NULL for the default stream; K, xd, b and x
@@ -440,20 +441,22 @@ ats_status ats_server_stats(ats_server *server, ats_server_counters *out);
  *   n_oct     octs of the level, 1 <= 8 n_oct <= ATS_NOALLOC_MAX_CELLS;
  *   nbr       [6 n_oct] oct neighbour table (ats_layout_neighbors gives it);
  *   K         [8 n_oct] cell K on leaf cells, a negative value on cells that
- *             are not unknowns of the level;
- *   xd        [8 n_oct] extra diagonal per cell (coupling shift plus the
- *             interface terms w C of Sect. 3.2), or NULL for none;
+ *             are not unknowns of the level (their x is left as it is);
+ *   xd        [8 n_oct] extra diagonal per cell (a coupling shift plus the
+ *             diagonal terms of interface faces), or NULL for none;
  *   h         dt / dx^2 / 2, so an interior face has C = h (K_i + K_j);
  *   b         [8 n_oct] right-hand side;
  *   x         [8 n_oct] initial guess in, solution out;
  *   tol       ||r_j|| <= tol ||r_0||; max_iter: CG cap (<= 0: 20000).
- * Returns ATS_ERR_INVALID_ARG for sizes above ATS_NOALLOC_MAX_CELLS or a
- * misaligned array.  The
- * first call on each device looks up the array's device address with that
- * device current: make it outside any stream capture.  Every call reuses the
- * same array (its contents are the last call's; what must start at zero is
- * cleared by each call), so calls that overlap on the GPU race: serialise
- * them. */
+ * The call is synchronous: it synchronises `stream` and polls the solve from
+ * the host, so `stream` must not be under stream capture (a capturing stream
+ * is rejected with ATS_ERR_INVALID_ARG before anything is enqueued).
+ * Returns ATS_ERR_INVALID_ARG for sizes above ATS_NOALLOC_MAX_CELLS, a
+ * misaligned array or a capturing stream.  The first call on each device
+ * looks up the array's device address with that device current.  Every call
+ * reuses the same array (its contents are the last call's; what must start
+ * at zero is cleared by each call), so calls that overlap on the GPU race:
+ * serialise them. */
 #define ATS_NOALLOC_MAX_CELLS 262144
 ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct, const int32_t *nbr,
                              const double *K, const double *xd, double h, const double *b,

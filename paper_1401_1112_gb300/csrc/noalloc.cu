@@ -1,14 +1,20 @@
 // ats_solve_noalloc: the single-level FP64 Jacobi-PCG solve without any
 // device allocation.
 //
-// Who needs it: callers that cannot call cudaMalloc -- code running inside a
-// stream capture that must not allocate, plug-ins handed a fixed memory pool
-// by a host application that owns all allocation, or processes whose CUDA
-// allocator is another runtime's (a framework caching allocator) and may not
-// be bypassed.  They pass device pointers for every input and output; the
-// CG vectors, reduction partials, work list and per-solve scalars live in one
+// Who needs it: callers that cannot call cudaMalloc -- plug-ins handed a fixed
+// memory pool by a host application that owns every device allocation, and
+// processes whose device memory belongs to another runtime's allocator (a
+// framework's caching allocator) that must not be bypassed or made to give
+// memory back.  They pass device pointers for every input and output; the CG
+// vectors, reduction partials, work list and per-solve scalars live in one
 // file-scope device array defined below, which every GPU that loads this
 // library keeps until the process exits.
+//
+// The call is synchronous: it copies its descriptors from host memory, polls
+// the solve's progress from the host and synchronises the caller's stream
+// before it returns.  So it cannot run inside a CUDA stream capture; a stream
+// that is being captured is rejected with ATS_ERR_INVALID_ARG before any work
+// is enqueued on it.
 //
 // Limits and sharing: at most kNoAllocMaxCells cells per call (larger
 // requests are rejected).  All calls share the one array and it keeps the
@@ -18,8 +24,7 @@
 // two streams) race on the array: serialise them.
 //
 // Set-up: the first call on each device looks up the device address of the
-// array (cudaGetSymbolAddress) with that device current; make that first call
-// outside any stream capture.
+// array (cudaGetSymbolAddress) with that device current.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,6 +120,22 @@ extern "C" ats_status ats_solve_noalloc(int device, void *stream, int64_t n_oct,
       base = (unsigned char *)g_scratch_ptr[device];
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // the call synchronises st and reads the solve state back to the host,
+    // which a stream capture does not allow: refuse before enqueuing anything
+    {
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      e = cudaStreamIsCapturing(st, &cap);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("ats_solve_noalloc: cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+        return ATS_ERR_INVALID_ARG;
+      }
+      if (cap != cudaStreamCaptureStatusNone) {
+        set_error("ats_solve_noalloc: the stream is being captured; the call synchronises its stream and cannot "
+                  "be captured into a CUDA graph");
+        return ATS_ERR_INVALID_ARG;
+      }
+    }
   
     SolveDev *d_solve = (SolveDev *)(base + kOffSolve);
     SolveScalars *d_sc = (SolveScalars *)(base + kOffScal);
