@@ -98,8 +98,11 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     PERIOD_MS = 20
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu_id: str):
+        # nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES,
+        # so the sampler is given a stable identifier of the GPU in use (its
+        # UUID, else its PCI bus id; see smi_gpu_id), never a CUDA ordinal
+        self.gpu = str(gpu_id)
         self.proc = None
         self.lines = []  # (arrival time, line)
         self._t = None
@@ -126,7 +129,7 @@ class ClockSampler:
         """Summary of the samples that arrived in [t0, t1 + one period]
         (perf_counter times; None: every sample)."""
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "gpu": self.gpu}
         time.sleep(2.0 * self.PERIOD_MS / 1e3)
         self.proc.terminate()
         try:
@@ -140,6 +143,7 @@ class ClockSampler:
         if t0 is not None and t1 is not None:
             inside = [(t, ln) for t, ln in lines if t0 <= t <= t1 + self.PERIOD_MS / 1e3]
         summary = self._summarise(inside if inside else lines)
+        summary["gpu"] = self.gpu
         summary["samples_in_region"] = len(inside) if (t0 is not None and t1 is not None) else summary["samples"]
         return summary
 
@@ -165,6 +169,27 @@ class ClockSampler:
             "reasons": sorted(reasons),
             "samples": len(sm),
         }
+
+
+def smi_gpu_id(local: int) -> str:
+    """nvidia-smi's identifier of CUDA device `local` of this process: its
+    UUID ("GPU-..."), else its PCI bus id, else (neither known) the ordinal
+    itself, which is only right when no CUDA_VISIBLE_DEVICES remapping is in
+    force."""
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    try:
+        p = torch.cuda.get_device_properties(local)
+        return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        pass
+    return str(local)
 
 
 def _traffic_for(kernel: str, alg_bytes_per_launch: float):
@@ -287,7 +312,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
 
     batch.set_profiling(True)
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(smi_gpu_id(local))
     sampler.start()
     barrier()
     t_region = time.perf_counter()

@@ -11,6 +11,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FAKE = """#!{py}
 import sys, time
+# the sampler must name the GPU by a stable identifier, not a CUDA ordinal
+ids = [a for a in sys.argv[1:] if a.startswith("--id=")]
+with open({log!r}, "w") as f:
+    f.write(ids[0][5:] if ids else "")
 # one CSV line every 20 ms: SM clock 1000 MHz for 0.3 s, then 2000 MHz with
 # the power cap active, as the real query prints them (noheader, nounits)
 t0 = time.time()
@@ -31,11 +35,13 @@ def _bench():
 
 def test_sampler_keeps_the_region_only(tmp_path, monkeypatch):
     exe = tmp_path / "nvidia-smi"
-    exe.write_text(FAKE.format(py=sys.executable))
+    log = tmp_path / "id.txt"
+    exe.write_text(FAKE.format(py=sys.executable, log=str(log)))
     exe.chmod(exe.stat().st_mode | stat.S_IEXEC)
     monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
     bench = _bench()
-    s = bench.ClockSampler(0)
+    uuid = "GPU-6f1e2d3c-0000-1111-2222-333344445555"
+    s = bench.ClockSampler(uuid)
     s.start()
     assert s.lines, "the first sample is awaited before the region"
     time.sleep(0.45)  # past the switch to 2000 MHz
@@ -45,11 +51,13 @@ def test_sampler_keeps_the_region_only(tmp_path, monkeypatch):
     assert out["samples_in_region"] >= 5
     assert out["sm_mhz"] == 2000.0 and out["sm_max_mhz"] == 2070.0
     assert out["reasons"] == ["sw_power_cap"]
+    assert out["gpu"] == uuid
+    assert log.read_text() == uuid
 
 
 def test_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     monkeypatch.setenv("PATH", str(tmp_path))
     bench = _bench()
-    s = bench.ClockSampler(0)
+    s = bench.ClockSampler("GPU-x")
     s.start()
     assert s.stop(0.0, 1.0)["reasons"] == ["nvidia-smi unavailable"]
