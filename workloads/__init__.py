@@ -357,16 +357,17 @@ def build_request(req):
 
 
 def random_amr_level(seed: int, n_box: int = 3, refine_frac: float = 0.2, dx: float = 0.1,
-                     kinds=(DIRICHLET, NEUMANN, ROBIN)):
-    """A small irregular level for parity tests: a union of random oct boxes,
-    some leaf cells refined (non-leaf), and a descriptor of random kind /
-    relation / alpha on every face without a same-level leaf neighbour, except
-    a random subset left as zero-flux walls.  Per-step values are random."""
+                     kinds=(DIRICHLET, NEUMANN, ROBIN), box_hi: int = 4):
+    """A small irregular level for parity tests: a union of random oct boxes
+    (corners in [0, box_hi)^3, extents in [1, box_hi) octs per axis), some
+    leaf cells refined (non-leaf), and a descriptor of random kind / relation /
+    alpha on every face without a same-level leaf neighbour, except a random
+    subset left as zero-flux walls.  Per-step values are random."""
     rng = np.random.default_rng(seed)
     pts = []
     for _ in range(n_box):
-        lo = rng.integers(0, 4, 3)
-        ext = rng.integers(1, 4, 3)
+        lo = rng.integers(0, box_hi, 3)
+        ext = rng.integers(1, box_hi, 3)
         g = np.stack(np.meshgrid(*[np.arange(lo[k], lo[k] + ext[k]) for k in range(3)], indexing="ij"), -1)
         pts.append(g.reshape(-1, 3))
     xyz = np.unique(np.concatenate(pts), axis=0).astype(np.int32)
