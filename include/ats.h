@@ -146,7 +146,37 @@ typedef struct {
   int use_graph;     /* 1 = each poll interval of check_every ticks is one CUDA graph, the host polls between intervals; 2 = the whole tick loop is one graph (a WHILE conditional node over one interval, ended on the device when no solve is active), the host waits once (with profiling on, 2 runs as 1) */
   int mem;           /* ATS_MEM_HOST / ATS_MEM_DEVICE for x (and rhs)        */
   int x0;            /* ATS_X0_*: where the initial guess comes from          */
+  int sched;         /* ATS_SCHED_*: tick path or resident solver (0 = AUTO)  */
+  int res_threads;   /* resident solver: threads per CTA, 256 or 512          */
+                     /* (0 = 512 for ATS_PREC_MIXED, 256 for ATS_PREC_FP64)   */
+  int res_cluster;   /* resident solver: CTAs per thread-block cluster, 1..16 */
+                     /* (0 = 8)                                              */
+  int res_cta_octs;  /* resident solver: a level of at most this many octs is */
+                     /* solved by one CTA alone (0 = 2048, < 0 = never)      */
+  int res_max_octs;  /* ATS_SCHED_AUTO: levels above this many octs take the  */
+                     /* tick path (0 = 4096)                                 */
+  int fp32_scalars;  /* resident solver, mixed precision: 1 = CG alpha, beta  */
+                     /* from the dot totals rounded to FP32 (the tick path's  */
+                     /* form); 0 = from the FP64 totals (default)            */
 } ats_solve_opts;
+
+/* scheduling of a solve (ats_solve_opts.sched).  Which path a level takes
+ * depends on that level and the options alone, so a level gives bitwise the
+ * same result solved alone and in any batch with the same options.
+ *   Tick path: every solve still running advances one CG step per "tick" (a
+ *   stencil kernel, a refinement kernel and an update kernel over the active
+ *   work items of all solves), ticks replayed as CUDA graphs, host or device
+ *   polling between intervals; one solve spreads over the whole GPU.
+ *   Resident solver: a solve runs from its first residual pass to its
+ *   certificate inside one persistent launch, on one thread-block cluster of
+ *   res_cluster CTAs (per-step sums exchanged through distributed shared
+ *   memory, steps ordered by the hardware cluster barrier), or on one CTA when
+ *   the level has at most res_cta_octs octs; clusters and CTAs take solves
+ *   from work queues ordered by estimated work (largest first).  Not for the
+ *   paper stopping rule (ATS_STOP_PAPER takes the tick path). */
+#define ATS_SCHED_AUTO 0     /* resident solver for levels up to res_max_octs octs */
+#define ATS_SCHED_TICK 1     /* the tick path for every level                    */
+#define ATS_SCHED_RESIDENT 2 /* the resident solver for every level              */
 
 /* initial guess of a solve (ats_solve_opts.x0) */
 #define ATS_X0_GIVEN 0 /* x_inout holds the initial guess on entry (default) */
@@ -258,6 +288,16 @@ typedef struct {
   double upd_ms, upd_bytes;  /* update kernel: e, z, dots; x += e after refinement */
   int launches;              /* tick-kernel launches                              */
   int ticks;                 /* ticks enqueued                                    */
+  double res_ms, res_bytes;  /* resident solver launch (all its steps) and the    */
+                             /* algorithmic bytes of its steps, counted per step  */
+                             /* kind as for the tick kernels                      */
+  int res_launches;          /* resident-solver launches                          */
+  int res_solves;            /* solves taken by the resident solver               */
+  double res_span_ms;        /* first resident solve's start to the last one's end */
+  double res_longest_ms;     /* the longest resident solve                         */
+  double res_occupancy;      /* CTA-time inside solves / (span x the launch's CTAs) */
+  int res_longest;           /* index of the longest resident solve (-1: none)     */
+  int res_grid;              /* CTAs of the resident launch                        */
 } ats_kernel_stats;
 ats_status ats_batch_set_profiling(ats_batch *batch, int on);
 ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out);

@@ -67,7 +67,9 @@ class ats_solve_opts(ctypes.Structure):
         ("tol", ctypes.c_double), ("stop_rule", ctypes.c_int), ("precision", ctypes.c_int),
         ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
         ("tile_octs", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
-        ("mem", ctypes.c_int), ("x0", ctypes.c_int),
+        ("mem", ctypes.c_int), ("x0", ctypes.c_int), ("sched", ctypes.c_int), ("res_threads", ctypes.c_int),
+        ("res_cluster", ctypes.c_int), ("res_cta_octs", ctypes.c_int), ("res_max_octs", ctypes.c_int),
+        ("fp32_scalars", ctypes.c_int),
     ]
 
 
@@ -77,13 +79,17 @@ class ats_hierarchy_desc(ctypes.Structure):
 
 
 ATS_ORDER_FINE_FIRST, ATS_ORDER_COARSE_FIRST = 0, 1
+ATS_SCHED_AUTO, ATS_SCHED_TICK, ATS_SCHED_RESIDENT = 0, 1, 2
 
 
 class ats_kernel_stats(ctypes.Structure):
     _fields_ = [
         ("op_ms", ctypes.c_double), ("op_bytes", ctypes.c_double), ("ref_ms", ctypes.c_double),
         ("ref_bytes", ctypes.c_double), ("upd_ms", ctypes.c_double), ("upd_bytes", ctypes.c_double),
-        ("launches", ctypes.c_int), ("ticks", ctypes.c_int),
+        ("launches", ctypes.c_int), ("ticks", ctypes.c_int), ("res_ms", ctypes.c_double),
+        ("res_bytes", ctypes.c_double), ("res_launches", ctypes.c_int), ("res_solves", ctypes.c_int),
+        ("res_span_ms", ctypes.c_double), ("res_longest_ms", ctypes.c_double), ("res_occupancy", ctypes.c_double),
+        ("res_longest", ctypes.c_int), ("res_grid", ctypes.c_int),
     ]
 
 
@@ -261,7 +267,8 @@ def _level_desc(level, keep):
 
 def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, max_iter=0, max_refine=0,
               inner_rtol=0.0, tile_octs=0, check_every=0, use_graph=0, mem=ATS_MEM_HOST,
-              x0=ATS_X0_GIVEN) -> ats_solve_opts:
+              x0=ATS_X0_GIVEN, sched=ATS_SCHED_AUTO, res_threads=0, res_cluster=0, res_cta_octs=0,
+              res_max_octs=0, fp32_scalars=0) -> ats_solve_opts:
     o = ats_solve_opts()
     lib().ats_default_opts(ctypes.byref(o))
     o.tol = tol
@@ -279,6 +286,12 @@ def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, m
     o.use_graph = use_graph
     o.mem = mem
     o.x0 = x0
+    o.sched = sched
+    o.res_threads = res_threads
+    o.res_cluster = res_cluster
+    o.res_cta_octs = res_cta_octs
+    o.res_max_octs = res_max_octs
+    o.fp32_scalars = fp32_scalars
     return o
 
 

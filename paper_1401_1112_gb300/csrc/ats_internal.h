@@ -189,6 +189,31 @@ cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, const int grid
 // register and shared-memory use, times the SM count), in launch_tick order.
 void tick_grids(bool fp64, bool paper, int device, int grids[3]);
 
+// Resident solver (kernels.cu): whole solves inside one launch.  Solves in
+// queue[0, n_cq) are taken by thread-block clusters, solves in
+// queue[n_cq, n_cq + n_tq) by single CTAs; heads[0] / heads[1] are the next
+// positions of the two queues (zero before the launch).  A finished solve
+// writes its state to final_sc.  With cells set, the cells processed per step
+// kind are added as the tick kernels count them (kCellCounters).
+struct ResArgs {
+  const SolveDev *solves;
+  SolveScalars *final_sc;
+  const int32_t *queue;
+  int n_cq, n_tq, n_solves;
+  int fp32_scalars;  // 1: alpha and beta from the totals rounded to FP32 (mixed precision)
+  int *heads;
+  unsigned long long *cells;
+  unsigned long long *t_solve;  // [n_solves][2] %globaltimer at a solve's start and end (profiling), or null
+};
+// One resident launch on st: clusters of `cluster` CTAs of `threads` threads
+// (256 or 512), `grid` CTAs in all (a multiple of `cluster`) when the cluster
+// queue is not empty, else `grid` single CTAs.
+cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st);
+// Clusters of that shape resident at once on the current device (0: none).
+int resident_max_clusters(bool fp64, int threads, int cluster);
+// CTAs of the single-CTA kernel resident per SM.
+int resident_cta_blocks(bool fp64, int threads);
+
 // Start of a solve: e = 0 on every cell of every item, and x64 = src[solve]
 // where src (device array of device pointers) is non-null for that solve.
 cudaError_t launch_init(bool fp64, const SolveDev *solves, const WorkItem *items, int n_items,

@@ -242,6 +242,61 @@ __device__ __forceinline__ void ld_face(const double *__restrict__ p, double (&v
   }
 }
 
+// Coherent loads for the resident solver (one launch runs every iteration of
+// a solve): vectors that another CTA of the cluster wrote earlier in the same
+// launch are read from L2 (ld.global.cg) after the step's cluster barrier,
+// never through the non-coherent read-only path.  asm volatile keeps them
+// after that barrier.
+#ifndef ATS_RES_LD
+#define ATS_RES_LD ".cg"
+#endif
+__device__ __forceinline__ void ldc8(const float *p, float (&v)[8]) {
+  asm volatile("ld.global" ATS_RES_LD ".v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void ldc4(const double *p, double &a, double &b, double &c, double &d) {
+  asm volatile("ld.global" ATS_RES_LD ".v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(a), "=d"(b), "=d"(c), "=d"(d) : "l"(p));
+}
+__device__ __forceinline__ void ldc8(const double *p, double (&v)[8]) {
+  ldc4(p, v[0], v[1], v[2], v[3]);
+  ldc4(p + 4, v[4], v[5], v[6], v[7]);
+}
+template <int A, int NB>
+__device__ __forceinline__ void ldc_face(const float *p, float (&v)[8]) {
+  if (A != 2) {
+    ldc8(p, v);
+  } else {
+    asm volatile("ld.global" ATS_RES_LD ".v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v[4 * NB]), "=f"(v[4 * NB + 1]), "=f"(v[4 * NB + 2]), "=f"(v[4 * NB + 3])
+                 : "l"(p + 4 * NB));
+  }
+}
+template <int A, int NB>
+__device__ __forceinline__ void ldc_face(const double *p, double (&v)[8]) {
+  if (A == 0) {
+    ldc8(p, v);
+  } else if (A == 1) {
+    asm volatile("ld.global" ATS_RES_LD ".v2.f64 {%0, %1}, [%2];" : "=d"(v[2 * NB]), "=d"(v[2 * NB + 1]) : "l"(p + 2 * NB));
+    asm volatile("ld.global" ATS_RES_LD ".v2.f64 {%0, %1}, [%2];"
+                 : "=d"(v[4 + 2 * NB]), "=d"(v[5 + 2 * NB])
+                 : "l"(p + 4 + 2 * NB));
+  } else {
+    ldc4(p + 4 * NB, v[4 * NB], v[4 * NB + 1], v[4 * NB + 2], v[4 * NB + 3]);
+  }
+}
+// kCoh: the vector may have been written by another CTA in this launch.
+template <bool kCoh, typename T>
+__device__ __forceinline__ void ldv8(const T *p, T (&v)[8]) {
+  if (kCoh) ldc8(p, v);
+  else ld8_ro(p, v);
+}
+template <int A, int NB, bool kCoh, typename T>
+__device__ __forceinline__ void ldvf(const T *p, T (&v)[8]) {
+  if (kCoh) ldc_face<A, NB>(p, v);
+  else ld_face<A, NB>(p, v);
+}
+
 __device__ __forceinline__ void load_nbr6(const int32_t *__restrict__ nbr, int o, int (&nb)[6]) {
   const int2 *q = reinterpret_cast<const int2 *>(nbr + 6 * o);
   const int2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
@@ -271,7 +326,7 @@ __device__ __forceinline__ void in_oct_faces(const T (&K)[8], const T (&v)[8], T
 
 // k_op, CG phase, out-of-oct face DIR: p_new of the neighbour's facing cells
 // is formed on the fly from its z and p_old.
-template <int DIR, typename T>
+template <int DIR, typename T, bool kCoh = false>
 __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T *__restrict__ z,
                                         const T *__restrict__ pold, bool first, T beta, T h,
                                         const T (&K)[8], T (&off)[8]) {
@@ -279,8 +334,8 @@ __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T
   if (n < 0) return;
   T Kn[8], Zn[8], Pn[8];
   ld_face<A, NB>(KT + 8 * n, Kn);
-  ld_face<A, NB>(z + 8 * n, Zn);
-  if (!first) ld_face<A, NB>(pold + 8 * n, Pn);
+  ldvf<A, NB, kCoh>(z + 8 * n, Zn);
+  if (!first) ldvf<A, NB, kCoh>(pold + 8 * n, Pn);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (((c >> A) & 1) != S) continue;
@@ -295,7 +350,7 @@ __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T
 // face coefficients C = h (K_i + K_j) (row A of this oct for the in-oct pairs
 // and the +A face, row A of the -A neighbour for the -A face), and the FP32
 // diagonal sums of the bulk precision.
-template <int A, typename T>
+template <int A, typename T, bool kCoh = false>
 __device__ __forceinline__ void ref_axis(const SolveDev &sd, int o, const int (&nb)[6], const T *__restrict__ KT,
                                          T hT, const T (&KTo)[8], const double (&xv)[8], double (&acc)[8],
                                          T (&dsT)[8]) {
@@ -319,7 +374,7 @@ __device__ __forceinline__ void ref_axis(const SolveDev &sd, int o, const int (&
   if (n >= 0) {
     double Xn[8];
     T KTn[8];
-    ld_face<A, 0>(sd.x64 + 8 * n, Xn);
+    ldvf<A, 0, kCoh>(sd.x64 + 8 * n, Xn);
     ld_face<A, 0>(KT + 8 * n, KTn);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -333,7 +388,7 @@ __device__ __forceinline__ void ref_axis(const SolveDev &sd, int o, const int (&
   if (n >= 0) {
     double Xn[8], Cn[8];
     T KTn[8];
-    ld_face<A, 1>(sd.x64 + 8 * n, Xn);
+    ldvf<A, 1, kCoh>(sd.x64 + 8 * n, Xn);
     ld_face<A, 1>(sd.C64 + (3 * (size_t)n + A) * 8, Cn);
     ld_face<A, 1>(KT + 8 * n, KTn);
 #pragma unroll
@@ -351,7 +406,7 @@ __device__ __forceinline__ void ref_axis(const SolveDev &sd, int o, const int (&
 // (every product a DFMA); z = r / D_T in the bulk precision, D_T stored for the
 // CG kernels of the following inner solve.  Norms for the stopping test (r.r,
 // x.x) and r.z are accumulated with compensated bulk-precision dots.
-template <typename T>
+template <typename T, bool kCoh = false>
 __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool want_x, Acc<T> &rr,
                                               Acc<T> &xx, Acc<T> &rz) {
   const T *__restrict__ KT = (const T *)sd.KT;
@@ -365,7 +420,7 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
   if (rec >= 0 && !idx_ok(rec, sd.n_xd)) rec = -1;
   double xv[8];
   T KTo[8];
-  ld8_ro(sd.x64 + 8 * o, xv);
+  ldv8<kCoh>(sd.x64 + 8 * o, xv);
   ld8_ro(KT + 8 * o, KTo);
   double acc[8];
   T dsT[8];
@@ -374,9 +429,9 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
     acc[c] = 0.0;
     dsT[c] = T(0);
   }
-  ref_axis<0>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
-  ref_axis<1>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
-  ref_axis<2>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
+  ref_axis<0, T, kCoh>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
+  ref_axis<1, T, kCoh>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
+  ref_axis<2, T, kCoh>(sd, o, nb, KT, hT, KTo, xv, acc, dsT);
   double xd[8], b[8];
   T xdT[8];
   if (rec >= 0) {
@@ -563,20 +618,20 @@ struct OpOwn {
   T K[8], z[8], pp[8], d[8];
 };
 
-template <typename T>
+template <typename T, bool kCoh = false>
 __device__ __forceinline__ void op_load_own(const SolveDev &sd, int o, bool first, const T *__restrict__ pold,
                                             OpOwn<T> &w) {
   load_nbr6(sd.nbr, o, w.nb);
   check_nbr6(w.nb, sd.n_oct);
   ld8_ro((const T *)sd.KT + 8 * o, w.K);
-  ld8_ro((const T *)sd.z + 8 * o, w.z);
-  ld8_ro((const T *)sd.dg + 8 * o, w.d);
-  if (!first) ld8_ro(pold + 8 * o, w.pp);
+  ldv8<kCoh>((const T *)sd.z + 8 * o, w.z);
+  ldv8<kCoh>((const T *)sd.dg + 8 * o, w.d);
+  if (!first) ldv8<kCoh>(pold + 8 * o, w.pp);
 }
 
 // k_op, CG phase: p_new = z + beta p_old (first: z), q = (I + dt A) p_new,
 // partial p_new . q (per-oct FP32 sum, carried error-free across octs).
-template <typename T>
+template <typename T, bool kCoh = false>
 __device__ __forceinline__ void op_compute(const SolveDev &sd, int o, const OpOwn<T> &w, T h, T beta, bool first,
                                            const T *__restrict__ pold, T *__restrict__ pnew, Acc<T> &pq) {
   const T *__restrict__ KT = (const T *)sd.KT;
@@ -588,12 +643,12 @@ __device__ __forceinline__ void op_compute(const SolveDev &sd, int o, const OpOw
 #pragma unroll
   for (int c = 0; c < 8; ++c) off[c] = T(0);
   in_oct_faces(w.K, pv, h, off);
-  op_face<0>(w.nb[0], KT, z, pold, first, beta, h, w.K, off);
-  op_face<1>(w.nb[1], KT, z, pold, first, beta, h, w.K, off);
-  op_face<2>(w.nb[2], KT, z, pold, first, beta, h, w.K, off);
-  op_face<3>(w.nb[3], KT, z, pold, first, beta, h, w.K, off);
-  op_face<4>(w.nb[4], KT, z, pold, first, beta, h, w.K, off);
-  op_face<5>(w.nb[5], KT, z, pold, first, beta, h, w.K, off);
+  op_face<0, T, kCoh>(w.nb[0], KT, z, pold, first, beta, h, w.K, off);
+  op_face<1, T, kCoh>(w.nb[1], KT, z, pold, first, beta, h, w.K, off);
+  op_face<2, T, kCoh>(w.nb[2], KT, z, pold, first, beta, h, w.K, off);
+  op_face<3, T, kCoh>(w.nb[3], KT, z, pold, first, beta, h, w.K, off);
+  op_face<4, T, kCoh>(w.nb[4], KT, z, pold, first, beta, h, w.K, off);
+  op_face<5, T, kCoh>(w.nb[5], KT, z, pold, first, beta, h, w.K, off);
   T local = T(0), qv[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -614,8 +669,16 @@ struct UpdOwn {
   T p[8], q[8], d[8], z[8], e[8];
 };
 
-template <typename T>
+template <typename T, bool kCoh = false>
 __device__ __forceinline__ void upd_load_own(const SolveDev &sd, int o, const T *__restrict__ p, UpdOwn<T> &w) {
+  if (kCoh) {  // every vector is rewritten within a resident launch
+    ldc8(p + 8 * o, w.p);
+    ldc8((const T *)sd.q + 8 * o, w.q);
+    ldc8((const T *)sd.dg + 8 * o, w.d);
+    ldc8((const T *)sd.z + 8 * o, w.z);
+    ldc8((const T *)sd.e + 8 * o, w.e);
+    return;
+  }
   // p, q (this tick's k_op) and D (a refinement pass) are read-only here
   ld8_ro(p + 8 * o, w.p);
   ld8_ro((const T *)sd.q + 8 * o, w.q);
@@ -1529,6 +1592,470 @@ int tick_blocks_per_sm(bool fp64, bool paper) {
   }
   const int m = a < b ? a : b;
   return m > 0 ? m : 1;
+}
+
+// ===========================================================================
+// Resident solver: every iteration of a solve inside one launch
+// ===========================================================================
+//
+// A solve runs from its first FP64 residual pass to its final certificate
+// inside one persistent kernel.  A thread-block cluster takes a large solve:
+// its CTAs split the level's octs into contiguous ranges, and the sums of
+// each CG step (p.q; r.z and r.r; the residual norms) travel through
+// distributed shared memory, ordered by barrier.cluster (a hardware barrier:
+// no CTA spins on memory).  A CTA takes a small solve alone, ordered by
+// __syncthreads.  A solve then pays no kernel launch per iteration, and
+// solves of any mix of sizes and iteration counts keep the SMs busy until the
+// work runs out, instead of advancing in lockstep ticks.
+//
+// The arithmetic of a solve depends only on its level and on the plan's
+// resident shape (threads per CTA, CTAs per cluster, the size that selects a
+// CTA or a cluster), never on which cluster or CTA takes it or on what runs
+// beside it: sums merge in a fixed order (lanes by a shuffle tree, warps by
+// index, CTAs by cluster rank) and every CTA of a cluster merges the CTAs'
+// partials itself, so all hold bitwise the same totals and take the same
+// decisions.  The CG scalars alpha and beta are formed in FP64 from the
+// error-free (Dot2) totals and rounded to the bulk precision for the vector
+// updates.
+//
+// Memory ordering: a vector written in one step and read by another CTA in a
+// later one (z, p, D, x) is read with ld.global.cg after the step's cluster
+// barrier (release / acquire at cluster scope); arrays no step writes (K, the
+// neighbour table, face coefficients, b, diagonal extras) take the read-only
+// path.
+
+namespace {
+
+constexpr int kMaxCluster = 16;
+constexpr int kResMaxWarps = 512 / 32;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster arrives (release) and waits
+// (acquire): the hardware cluster barrier (the non-.aligned form, which
+// asks no warp convergence of its callers)
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// shared::cluster address of a variable of this CTA's shared memory in the
+// CTA of cluster rank `rank`
+__device__ __forceinline__ uint32_t cl_map(const void *p, unsigned rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_st(uint32_t a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_st(uint32_t a, const Acc<float> &v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.s), "f"(v.c) : "memory");
+}
+__device__ __forceinline__ void cl_st(uint32_t a, const Acc<double> &v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v.s) : "memory");
+}
+
+// State of the solve a group (a CTA or a cluster) works on; thread 0 of each
+// CTA updates its copy from the group's totals, so all copies agree.
+struct ResState {
+  int32_t phase, first, pcur, iters, inner_iters, refines, status, final_pass;
+  int32_t n_op, n_first, n_xpe, pad;
+  double rz, r0, rnorm, xnorm, inner_target, alpha, beta;
+};
+
+template <typename T>
+struct ResShared {
+  SolveDev sd;
+  ResState st;
+  Acc<T> red[kResMaxWarps][3];
+  __align__(16) Acc<T> inbox[2][kMaxCluster][3];  // [buffer][sender rank][sum]
+  int task;
+};
+
+// Sums of NA accumulators over the group: this CTA alone, or every CTA of the
+// cluster.  Thread 0 of each CTA ends with the group totals in `out`.  In a
+// cluster, threads r < cluster size send this CTA's partials to CTA r's inbox
+// (buffer `buf`, slot of this CTA's rank); after the cluster barrier each
+// CTA's thread 0 merges the inbox in rank order.  The inbox alternates
+// between two buffers: a buffer is written again only two sums later, after a
+// barrier that every reader of its previous contents has passed.
+template <typename T, int NA, bool kCluster>
+__device__ __forceinline__ void group_sum(Acc<T> (&a)[NA], ResShared<T> &sh, int &buf, Acc<T> (&out)[NA]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NA; ++k) warp_reduce_acc(a[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NA; ++k) sh.red[warp][k] = a[k];
+  }
+  __syncthreads();
+  if (!kCluster) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        out[k] = sh.red[0][k];
+        for (int w = 1; w < nw; ++w) out[k].merge(sh.red[w][k]);
+      }
+    }
+    return;
+  }
+  const unsigned cs = cl_size(), cr = cl_rank();
+  if (threadIdx.x < cs) {
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      Acc<T> m = sh.red[0][k];
+      for (int w = 1; w < nw; ++w) m.merge(sh.red[w][k]);
+      cl_st(cl_map(&sh.inbox[buf][cr][k], threadIdx.x), m);
+    }
+  }
+  cl_sync();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      out[k] = sh.inbox[buf][0][k];
+      for (unsigned r = 1; r < cs; ++r) out[k].merge(sh.inbox[buf][r][k]);
+    }
+  }
+  buf ^= 1;
+}
+
+template <bool kCluster>
+__device__ __forceinline__ void group_barrier() {
+  if (kCluster) cl_sync();
+  else __syncthreads();
+}
+
+// x += e, e = 0 on one oct at the end of an inner solve (resident launch).
+template <typename T>
+__device__ __forceinline__ void res_xpe_oct(const SolveDev &sd, int o) {
+  T *e = (T *)sd.e;
+  T ev[8];
+  double xv[8];
+  ldc8(e + 8 * o, ev);
+  ldc8(sd.x64 + 8 * o, xv);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    xv[c] += (double)ev[c];
+    ev[c] = T(0);
+  }
+  st8(sd.x64 + 8 * o, xv);
+  st8(e + 8 * o, ev);
+}
+
+// The rounding of a CG scalar to the bulk precision: FP64 quotient of the
+// FP64 totals (default), or, with fp32_scalars, the quotient of the totals
+// rounded to FP32 first (the tick kernels' form).
+__device__ __forceinline__ double cg_ratio(double num, double den, bool fp32) {
+  return fp32 ? (double)__fdiv_rn((float)num, (float)den) : num / den;
+}
+
+// One solve by one group: the refinement / inner-CG state machine of the tick
+// kernels (k_ref, k_op, k_upd), with its decisions taken right after each sum.
+template <typename T, bool kCluster>
+__device__ void res_solve(const ResArgs &a, int s, ResShared<T> &sh, int &buf) {
+  constexpr int wd = (int)(sizeof(SolveDev) / 8);
+  for (int w = threadIdx.x; w < wd; w += blockDim.x)
+    reinterpret_cast<unsigned long long *>(&sh.sd)[w] = reinterpret_cast<const unsigned long long *>(a.solves + s)[w];
+  const unsigned cs = kCluster ? cl_size() : 1u, cr = kCluster ? cl_rank() : 0u;
+  if (threadIdx.x == 0) {
+    ResState z;
+    memset(&z, 0, sizeof(z));
+    z.phase = kRefine;
+    z.status = ATS_OK;
+    sh.st = z;
+    if (a.t_solve && cr == 0) a.t_solve[2 * s] = globaltimer_ns();
+  }
+  __syncthreads();
+  const SolveDev &sd = sh.sd;
+  const int n = sd.n_oct;
+  const int chunk = (int)((n + (int)cs - 1) / (int)cs);
+  const int lo = min(n, (int)cr * chunk), hi = min(n, lo + chunk);
+  const int o0 = lo + (int)threadIdx.x, stride = (int)blockDim.x;
+  const T h = (T)sd.h;
+  const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
+  const bool fp32s = a.fp32_scalars != 0;
+  for (;;) {
+    const int phase = sh.st.phase;
+    if (phase == kDone) break;
+    if (phase == kRefine) {
+      // FP64 true residual of x, z = D^-1 r and D; sums r.r, x.x, r.z
+      Acc<T> acc[3], tot[3];
+      for (int o = o0; o < hi; o += stride) op_refine_oct<T, true>(sd, o, want_x, acc[0], acc[1], acc[2]);
+      group_sum<T, 3, kCluster>(acc, sh, buf, tot);
+      if (threadIdx.x == 0) {
+        ResState &st = sh.st;
+        const double rnorm = sqrt(tot[0].get()), xnorm = sqrt(tot[1].get()), rz = tot[2].get();
+        if (st.refines == 0) st.r0 = rnorm;
+        st.refines += 1;
+        st.rnorm = rnorm;
+        st.xnorm = xnorm;
+        const double target = sd.tol * (sd.stop_rule == ATS_STOP_CERTIFIED ? xnorm : st.r0);
+        if (st.final_pass) {
+          st.phase = kDone;
+        } else if (!isfinite(rnorm)) {
+          st.status = ATS_ERR_BREAKDOWN;
+          st.phase = kDone;
+        } else if (rnorm <= target) {
+          st.phase = kDone;
+        } else if (st.refines > sd.max_refine) {
+          st.status = ATS_ERR_NOT_CONVERGED;
+          st.phase = kDone;
+        } else if (!(rz > 0.0)) {
+          st.status = ATS_ERR_BREAKDOWN;
+          st.phase = kDone;
+        } else {
+          st.phase = kInner;
+          st.rz = rz;
+          st.first = 1;
+          st.inner_iters = 0;
+          st.inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    // inner CG iteration, step 1: p = z + beta p, q = (I + dt A) p, sum p.q
+    const bool first = sh.st.first != 0;
+    const T beta = (T)sh.st.beta;
+    const int pcur = sh.st.pcur;
+    const T *pold = (const T *)(pcur ? sd.p1 : sd.p0);
+    T *pnew = (T *)(pcur ? sd.p0 : sd.p1);
+    {
+      Acc<T> acc[1], tot[1];
+      OpOwn<T> w;
+      for (int o = o0; o < hi; o += stride) {
+        op_load_own<T, true>(sd, o, first, pold, w);
+        op_compute<T, true>(sd, o, w, h, beta, first, pold, pnew, acc[0]);
+      }
+      group_sum<T, 1, kCluster>(acc, sh, buf, tot);
+      if (threadIdx.x == 0) {
+        ResState &st = sh.st;
+        const double pq = tot[0].get();
+        st.n_op += 1;
+        st.n_first += first ? 1 : 0;
+        if (!(st.rz >= 0.0) || !isfinite(st.rz) || !(pq > 0.0) || !isfinite(pq)) {
+          st.status = ATS_ERR_BREAKDOWN;
+          st.phase = kDone;
+        } else {
+          st.alpha = cg_ratio(st.rz, pq, fp32s && sizeof(T) == 4);
+        }
+      }
+      __syncthreads();
+    }
+    if (sh.st.phase == kDone) break;
+    // step 2: e += alpha p, r = D z - alpha q, z = D^-1 r; sums r.z, r.r
+    {
+      const T alpha = (T)sh.st.alpha;
+      Acc<T> acc[2], tot[2];
+      UpdOwn<T> w;
+      float none = 0.f;
+      for (int o = o0; o < hi; o += stride) {
+        upd_load_own<T, true>(sd, o, pnew, w);
+        upd_compute<T, false>(sd, o, w, alpha, acc[0], acc[1], none);
+      }
+      group_sum<T, 2, kCluster>(acc, sh, buf, tot);
+      if (threadIdx.x == 0) {
+        ResState &st = sh.st;
+        const double rz_new = tot[0].get(), rr = tot[1].get();
+        st.iters += 1;
+        st.inner_iters += 1;
+        st.first = 0;
+        st.pcur ^= 1;
+        st.beta = cg_ratio(rz_new, st.rz, fp32s && sizeof(T) == 4);
+        st.rz = rz_new;
+        const bool conv = rr <= st.inner_target * st.inner_target || rz_new == 0.0;
+        if (conv) {
+          st.phase = kRefine;
+        } else if (st.iters >= sd.max_iter) {
+          st.status = ATS_ERR_NOT_CONVERGED;
+          st.final_pass = 1;
+          st.phase = kRefine;
+        } else if (st.inner_iters >= sd.inner_max) {
+          st.phase = kRefine;  // restart from the true residual
+        }
+        if (st.phase == kRefine) st.n_xpe += 1;
+      }
+      __syncthreads();
+    }
+    if (sh.st.phase == kRefine) {
+      // the inner solve ends: x += e, e = 0; the next residual pass reads the
+      // neighbours' x, so the whole group passes a barrier first
+      for (int o = o0; o < hi; o += stride) res_xpe_oct<T>(sd, o);
+      group_barrier<kCluster>();
+    }
+  }
+  if (threadIdx.x == 0 && cr == 0) {
+    const ResState &st = sh.st;
+    SolveScalars f;
+    memset(&f, 0, sizeof(f));
+    f.phase = kDone;
+    f.iters = st.iters;
+    f.inner_iters = st.inner_iters;
+    f.refines = st.refines;
+    f.status = st.status;
+    f.final_pass = st.final_pass;
+    f.ticks = st.n_op + st.iters + st.refines;  // group steps taken
+    f.rz = st.rz;
+    f.r0 = st.r0;
+    f.inner_target = st.inner_target;
+    f.rnorm = st.rnorm;
+    f.xnorm = st.xnorm;
+    a.final_sc[s] = f;
+    if (a.t_solve) a.t_solve[2 * s + 1] = globaltimer_ns();
+    if (a.cells) {
+      const unsigned long long N = 8ull * (unsigned long long)n;
+      atomicAdd(a.cells + 0, N * (unsigned long long)(st.n_op - st.n_first));
+      atomicAdd(a.cells + 4, N * (unsigned long long)st.n_first);
+      atomicAdd(a.cells + 1, N * (unsigned long long)st.refines);
+      atomicAdd(a.cells + 2, N * (unsigned long long)st.iters);
+      atomicAdd(a.cells + 3, N * (unsigned long long)st.n_xpe);
+    }
+  }
+}
+
+// Small solves, one CTA each, taken from the CTA queue until it is empty.
+template <typename T>
+__device__ void res_cta_loop(const ResArgs &a, ResShared<T> &sh, int &buf) {
+  for (;;) {
+    __syncthreads();  // every thread has read the previous task
+    if (threadIdx.x == 0) sh.task = atomicAdd(a.heads + 1, 1);
+    __syncthreads();
+    const int t = sh.task;
+    if (t >= a.n_tq) break;
+    int s = a.queue[a.n_cq + t];
+    if (!idx_ok(s, a.n_solves)) continue;
+    res_solve<T, false>(a, s, sh, buf);
+  }
+}
+
+template <typename T, int NT>
+struct ResMinBlocks {
+  static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1;
+};
+
+}  // namespace
+
+// The cluster kernel: each cluster takes the large solves of the cluster
+// queue one after the other (rank 0 draws the next position and writes it
+// into every CTA's shared memory before a cluster barrier); once that queue
+// is empty its CTAs take small solves from the CTA queue independently (no
+// cluster barrier or distributed shared memory access follows).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, ResMinBlocks<T, NT>::value) k_res_cluster(ResArgs a) {
+  __shared__ ResShared<T> sh;
+  int buf = 0;
+  const unsigned cr = cl_rank(), cs = cl_size();
+  for (;;) {
+    if (cr == 0 && threadIdx.x == 0) {
+      const int t = atomicAdd(a.heads, 1);
+      for (unsigned r = 0; r < cs; ++r) cl_st(cl_map(&sh.task, r), t);
+    }
+    cl_sync();
+    const int t = sh.task;
+    if (t >= a.n_cq) break;
+    const int s = a.queue[t];
+    if (idx_ok(s, a.n_solves)) res_solve<T, true>(a, s, sh, buf);
+  }
+  res_cta_loop<T>(a, sh, buf);
+}
+
+// The CTA kernel: small solves only (a plan without cluster solves).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, ResMinBlocks<T, NT>::value) k_res_cta(ResArgs a) {
+  __shared__ ResShared<T> sh;
+  int buf = 0;
+  res_cta_loop<T>(a, sh, buf);
+}
+
+template <typename T, int NT>
+static cudaError_t res_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st) {
+  if (a.n_cq > 0) {
+    if (cluster > 8) {
+      cudaError_t e = cudaFuncSetAttribute(k_res_cluster<T, NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_res_cluster<T, NT>, a);
+  }
+  k_res_cta<T, NT><<<grid, NT, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int NT>
+static int res_clusters_t(int cluster) {
+  if (cluster > 8 &&
+      cudaFuncSetAttribute(k_res_cluster<T, NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(cluster * 64));
+  cfg.blockDim = dim3(NT);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_res_cluster<T, NT>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <typename T, int NT>
+static int res_cta_blocks_t() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_res_cta<T, NT>, NT, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b;
+}
+
+cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st) {
+  if (a.n_cq + a.n_tq <= 0) return cudaSuccess;
+  if (cluster < 1 || cluster > kMaxCluster || grid <= 0) return cudaErrorInvalidValue;
+  if (fp64) return threads >= 512 ? res_launch_t<double, 512>(cluster, grid, a, st) : res_launch_t<double, 256>(cluster, grid, a, st);
+  return threads >= 512 ? res_launch_t<float, 512>(cluster, grid, a, st) : res_launch_t<float, 256>(cluster, grid, a, st);
+}
+
+int resident_max_clusters(bool fp64, int threads, int cluster) {
+  if (cluster < 1 || cluster > kMaxCluster) return 0;
+  if (fp64) return threads >= 512 ? res_clusters_t<double, 512>(cluster) : res_clusters_t<double, 256>(cluster);
+  return threads >= 512 ? res_clusters_t<float, 512>(cluster) : res_clusters_t<float, 256>(cluster);
+}
+
+int resident_cta_blocks(bool fp64, int threads) {
+  if (fp64) return threads >= 512 ? res_cta_blocks_t<double, 512>() : res_cta_blocks_t<double, 256>();
+  return threads >= 512 ? res_cta_blocks_t<float, 512>() : res_cta_blocks_t<float, 256>();
 }
 
 }  // namespace ats

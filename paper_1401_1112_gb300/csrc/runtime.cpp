@@ -222,6 +222,20 @@ struct Plan {
   double op_ms = 0.0, ref_ms = 0.0, upd_ms = 0.0, op_bytes = 0.0, ref_bytes = 0.0, upd_bytes = 0.0;
   int launches = 0;
   int ticks = 0;
+  // resident solver (whole solves in one launch): per solve 0 = tick path,
+  // 1 = a cluster, 2 = one CTA; the queues hold the cluster solves, then the
+  // CTA solves, each by estimated work, largest first
+  std::vector<int8_t> mode;
+  int n_cq = 0, n_tq = 0, n_tick = 0, n_tick_items = 0;
+  int res_threads = 512, res_cluster = 8, res_grid = 0;
+  int32_t *d_queue = nullptr;   // [n_cq + n_tq]
+  int *d_heads = nullptr;       // [2] next position of each queue
+  cudaEvent_t res_ev[2] = {nullptr, nullptr};
+  double res_ms = 0.0, res_bytes = 0.0;
+  int res_launches = 0;
+  unsigned long long *d_tsolve = nullptr;  // [n][2] per-solve start / end (profiling)
+  double res_span_ms = 0.0, res_longest_ms = 0.0, res_occupancy = 0.0;
+  int res_longest = -1;
 };
 
 struct ats_batch {
@@ -260,6 +274,12 @@ void fill_defaults(ats_solve_opts *o) {
   o->check_every = 16;
   o->use_graph = 0;
   o->mem = ATS_MEM_HOST;
+  o->sched = ATS_SCHED_AUTO;
+  o->res_threads = 0;
+  o->res_cluster = 0;
+  o->res_cta_octs = 0;
+  o->res_max_octs = 0;
+  o->fp32_scalars = 0;
 }
 
 ats_solve_opts normalize(const ats_solve_opts *in) {
@@ -358,8 +378,44 @@ void plan_free(Plan *P) {
   dev_free(ctx, P->d_src);
   dev_free(ctx, P->d_dst);
   dev_free(ctx, P->d_xstage);
+  dev_free(ctx, P->d_queue);
+  dev_free(ctx, P->d_heads);
+  dev_free(ctx, P->d_tsolve);
+  for (auto e : P->res_ev)
+    if (e) cudaEventDestroy(e);
   if (P->h_active) cudaFreeHost(P->h_active);
   delete P;
+}
+
+// Estimated work of a level solve, to order the resident queues (largest
+// first): octs times an iteration estimate, the square root of the stiffness
+// 1 + 8 h (h = dt / (2 dx^2), K ~ 1) capped by four times the oct count's
+// cube root (about twice the level's width in cells).
+double est_work(const ats_level *L) {
+  const double h = 0.5 * L->dt / (L->dx * L->dx);
+  const double o = (double)L->n_oct;
+  return o * std::min(std::sqrt(1.0 + 8.0 * h), 4.0 * std::cbrt(o));
+}
+
+// Upload the resident queues of P in work order.
+ats_status plan_upload_queues(Plan *P) {
+  std::vector<int32_t> cq, tq;
+  for (int k = 0; k < P->n; ++k) {
+    if (P->mode[k] == 1) cq.push_back(k);
+    if (P->mode[k] == 2) tq.push_back(k);
+  }
+  auto by_work = [&](std::vector<int32_t> &q) {
+    std::vector<double> w(P->n, 0.0);
+    for (int32_t k : q) w[k] = est_work(P->levels[k]);
+    std::stable_sort(q.begin(), q.end(), [&](int32_t a, int32_t b) { return w[a] > w[b]; });
+  };
+  by_work(cq);
+  by_work(tq);
+  cq.insert(cq.end(), tq.begin(), tq.end());
+  if (!cq.empty())
+    CUDA_TRY(cudaMemcpyAsync(P->d_queue, cq.data(), sizeof(int32_t) * cq.size(), cudaMemcpyHostToDevice,
+                             P->ctx->stream));
+  return ATS_OK;
 }
 
 ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const ats_solve_opts *opts_in,
@@ -380,6 +436,11 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   }
   if (o.x0 != ATS_X0_GIVEN && o.x0 != ATS_X0_E_OLD) {
     set_error("bad x0");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (o.sched < ATS_SCHED_AUTO || o.sched > ATS_SCHED_RESIDENT || (o.res_threads != 0 && o.res_threads != 256 &&
+      o.res_threads != 512) || o.res_cluster < 0 || o.res_cluster > 16 || o.res_max_octs < 0) {
+    set_error("bad resident-solver options (sched 0..2, res_threads 0/256/512, res_cluster 0..16)");
     return ATS_ERR_INVALID_ARG;
   }
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -458,6 +519,37 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     sc.status = ATS_OK;
   }
   P->n_items = (int)items.size();
+  // resident or tick path per solve, by a rule on the level and the options
+  // alone (a level then runs the same arithmetic alone and in any batch)
+  P->res_threads = o.res_threads > 0 ? o.res_threads : (P->fp64 ? 256 : 512);
+  P->res_cluster = o.res_cluster > 0 ? o.res_cluster : 8;
+  {
+    const bool res_ok = o.sched != ATS_SCHED_TICK && o.stop_rule != ATS_STOP_PAPER;
+    const int64_t cta_octs = o.res_cta_octs == 0 ? 2048 : o.res_cta_octs;
+    const int64_t max_octs = o.sched == ATS_SCHED_RESIDENT ? INT64_MAX : (o.res_max_octs > 0 ? o.res_max_octs : 4096);
+    int clusters = 0;
+    P->mode.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+      const int64_t no = P->levels[k]->n_oct;
+      if (!res_ok || no > max_octs) continue;
+      P->mode[k] = no <= cta_octs ? 2 : 1;
+    }
+    for (int k = 0; k < n; ++k) P->n_cq += P->mode[k] == 1;
+    if (P->n_cq > 0) {
+      clusters = resident_max_clusters(P->fp64, P->res_threads, P->res_cluster);
+      if (clusters <= 0) {  // no cluster of that shape fits this device: those levels take the tick path
+        for (int k = 0; k < n; ++k)
+          if (P->mode[k] == 1) P->mode[k] = 0;
+        P->n_cq = 0;
+      }
+    }
+    for (int k = 0; k < n; ++k) {
+      P->n_tq += P->mode[k] == 2;
+      P->n_tick += P->mode[k] == 0;
+    }
+    P->res_grid = P->n_cq > 0 ? clusters * P->res_cluster
+                              : std::max(1, resident_cta_blocks(P->fp64, P->res_threads)) * ctx->num_sms;
+  }
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
   P->grid = std::max(1, std::min(P->n_items, bps * ctx->num_sms));
   for (int k = 0; k < 3; ++k) P->grids[k] = std::max(1, std::min(P->n_items, P->grids[k]));
@@ -467,7 +559,9 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, P->n_items, &P->d_items)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 3 * (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, kCellCounters, &P->d_cells)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 2 * kCellCounters, &P->d_cells)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, std::max(1, P->n_cq + P->n_tq), &P->d_queue)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 2, &P->d_heads)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 4 * (size_t)P->n_items, &P->d_lists)) != ATS_OK ||
       (s = dev_alloc_t(ctx, (size_t)P->n_items, &P->d_ident)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_ctl)) != ATS_OK ||
@@ -488,9 +582,17 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   CUDA_TRY(cudaMemcpyAsync(P->d_solves, P->h_solves.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st));
   {
-    std::vector<int32_t> ident(P->n_items);
-    for (int i = 0; i < P->n_items; ++i) ident[i] = i;
-    CUDA_TRY(cudaMemcpyAsync(P->d_ident, ident.data(), sizeof(int32_t) * ident.size(), cudaMemcpyHostToDevice, st));
+    // the tick path's first list: the work items of the tick-path solves
+    std::vector<int32_t> ident;
+    for (int i = 0; i < P->n_items; ++i)
+      if (P->mode[items[i].solve] == 0) ident.push_back(i);
+    P->n_tick_items = (int)ident.size();
+    if (!ident.empty())
+      CUDA_TRY(cudaMemcpyAsync(P->d_ident, ident.data(), sizeof(int32_t) * ident.size(), cudaMemcpyHostToDevice, st));
+    if ((s = plan_upload_queues(P)) != ATS_OK) {
+      plan_free(P);
+      return s;
+    }
     CUDA_TRY(cudaStreamSynchronize(st));
   }
   {
@@ -521,8 +623,40 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   CUDA_TRY(cudaEventCreateWithFlags(&P->fj.join, cudaEventDisableTiming));
   CUDA_TRY(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
   CUDA_TRY(cudaEventCreateWithFlags(&P->mark, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreate(&P->res_ev[0]));
+  CUDA_TRY(cudaEventCreate(&P->res_ev[1]));
   CUDA_TRY(cudaStreamSynchronize(st));
   *out = P;
+  return ATS_OK;
+}
+
+// Enqueue the resident launch of P's cluster and CTA solves (after
+// plan_begin); with profiling, between the two timing events.
+ats_status plan_launch_resident(Plan *P, bool prof) {
+  if (P->n_cq + P->n_tq == 0) return ATS_OK;
+  cudaStream_t st = P->ctx->stream;
+  ResArgs ra;
+  std::memset(&ra, 0, sizeof(ra));
+  ra.solves = P->d_solves;
+  ra.final_sc = P->d_final;
+  ra.queue = P->d_queue;
+  ra.n_cq = P->n_cq;
+  ra.n_tq = P->n_tq;
+  ra.n_solves = P->n;
+  ra.fp32_scalars = P->opts.fp32_scalars ? 1 : 0;
+  ra.heads = P->d_heads;
+  ra.cells = prof ? P->d_cells + kCellCounters : nullptr;
+  if (prof && !P->d_tsolve) {
+    ats_status sa = dev_alloc_t(P->ctx, 2 * (size_t)P->n, &P->d_tsolve);
+    if (sa != ATS_OK) return sa;
+  }
+  if (prof) CUDA_TRY(cudaMemsetAsync(P->d_tsolve, 0, 2 * sizeof(unsigned long long) * P->n, st));
+  ra.t_solve = prof ? P->d_tsolve : nullptr;
+  CUDA_TRY(cudaMemsetAsync(P->d_heads, 0, 2 * sizeof(int), st));
+  if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[0], st));
+  CUDA_TRY(launch_resident(P->fp64, P->res_threads, P->res_cluster, P->res_grid, ra, st));
+  if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[1], st));
+  P->res_launches += 1;
   return ATS_OK;
 }
 
@@ -726,8 +860,11 @@ ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off
       stale = true;
     }
   }
-  if (stale)
+  if (stale) {
     CUDA_TRY(cudaMemcpyAsync(P->d_solves, P->h_solves.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice, st));
+    ats_status sq = plan_upload_queues(P);  // the work estimates follow dt
+    if (sq != ATS_OK) return sq;
+  }
   // copy-in of x: device x is read in place; host x goes through one staging
   // buffer, one copy per run of levels whose host arrays are contiguous
   std::vector<const double *> src(n, nullptr);
@@ -764,19 +901,23 @@ ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off
   CUDA_TRY(launch_init(P->fp64, P->d_solves, P->d_items, P->n_items, P->d_src, P->grid, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_sc, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(P->d_final, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, kCellCounters * sizeof(unsigned long long), st));
-  CUDA_TRY(cudaMemcpyAsync(P->d_active, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, 2 * kCellCounters * sizeof(unsigned long long), st));
+  // only the tick-path solves count as active for the tick loop
+  CUDA_TRY(cudaMemcpyAsync(P->d_active, &P->n_tick, sizeof(int), cudaMemcpyHostToDevice, st));
   {
-    // every item of every solve starts in the refinement phase (r0 = b - A x0)
+    // every item of every tick-path solve starts in the refinement phase (r0 = b - A x0)
     TickCtl c0;
     std::memset(&c0, 0, sizeof(c0));
-    c0.count[0][kRefine] = P->n_items;
-    CUDA_TRY(cudaMemcpyAsync(P->d_lists + (size_t)kRefine * P->n_items, P->d_ident,
-                             sizeof(int32_t) * P->n_items, cudaMemcpyDeviceToDevice, st));
+    c0.count[0][kRefine] = P->n_tick_items;
+    if (P->n_tick_items > 0)
+      CUDA_TRY(cudaMemcpyAsync(P->d_lists + (size_t)kRefine * P->n_items, P->d_ident,
+                               sizeof(int32_t) * P->n_tick_items, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(P->d_ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
   }
   P->op_ms = P->ref_ms = P->upd_ms = 0.0;
+  P->res_ms = P->res_bytes = 0.0;
   P->launches = 0;
+  P->res_launches = 0;
   P->ticks = 0;
   return ATS_OK;
 }
@@ -806,12 +947,16 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   int64_t ticks = 0;
   ats_status s;
   bool timed_out = false;
+  // the resident solves: one launch runs every one of them to its end
+  if ((s = plan_launch_resident(P, P->profiling)) != ATS_OK) return s;
   // use_graph = 2 (not while profiling: the timing events cannot sit in a
   // conditional body): the whole loop is one graph launch, ended on the device
-  const bool device_loop = P->opts.use_graph == 2 && !P->profiling;
+  const bool device_loop = P->opts.use_graph == 2 && !P->profiling && P->n_tick > 0;
   int chunks_run = 0;
   int drain_slot = 0, drain_n = 0;  // intervals still queued when the host loop ended
-  if (device_loop) {
+  if (P->n_tick == 0) {
+    // no tick-path solve: no tick loop
+  } else if (device_loop) {
     const int max_chunks = (int)std::min<int64_t>((max_ticks + P->opts.check_every - 1) / P->opts.check_every, 1 << 30);
     if ((s = plan_ensure_loop(P, max_chunks)) != ATS_OK) return s;
     CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
@@ -862,7 +1007,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   }
   std::vector<SolveScalars> sc(n);
   CUDA_TRY(cudaMemcpyAsync(sc.data(), P->d_final, sizeof(SolveScalars) * n, cudaMemcpyDeviceToHost, st));
-  unsigned long long cells[kCellCounters] = {0, 0, 0, 0, 0};
+  unsigned long long cells[2 * kCellCounters] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // tick kernels, resident launch
   if (P->profiling) CUDA_TRY(cudaMemcpyAsync(cells, P->d_cells, sizeof(cells), cudaMemcpyDeviceToHost, st));
   std::vector<int> flags(2 * n, 0);
   CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, n, P->d_flags, st));
@@ -880,12 +1025,45 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
     P->launches = 3 * P->ticks + chunks_run;
     if ((int64_t)chunks_run * P->opts.check_every >= max_ticks) timed_out = true;
   }
-  if (P->profiling) plan_bytes(P, cells, &P->op_bytes, &P->ref_bytes, &P->upd_bytes);
+  if (P->profiling) {
+    plan_bytes(P, cells, &P->op_bytes, &P->ref_bytes, &P->upd_bytes);
+    if (P->n_cq + P->n_tq > 0) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, P->res_ev[0], P->res_ev[1]));
+      P->res_ms = ms;
+      double ob = 0, rb = 0, ub = 0;
+      plan_bytes(P, cells + kCellCounters, &ob, &rb, &ub);
+      P->res_bytes = ob + rb + ub;
+      // the launch's timeline: span from the first solve's start to the last
+      // one's end, the longest solve, and the fraction of the launch's
+      // CTA-time spent inside solves
+      std::vector<unsigned long long> ts(2 * (size_t)n);
+      CUDA_TRY(cudaMemcpy(ts.data(), P->d_tsolve, sizeof(unsigned long long) * ts.size(), cudaMemcpyDeviceToHost));
+      unsigned long long t0 = ~0ull, t1 = 0;
+      double busy = 0.0, longest = 0.0;
+      P->res_longest = -1;
+      for (int k = 0; k < n; ++k) {
+        if (P->mode[k] == 0 || ts[2 * k + 1] < ts[2 * k]) continue;
+        t0 = std::min(t0, ts[2 * k]);
+        t1 = std::max(t1, ts[2 * k + 1]);
+        const double d = (double)(ts[2 * k + 1] - ts[2 * k]) * 1e-6;
+        busy += d * (P->mode[k] == 1 ? P->res_cluster : 1);
+        if (d > longest) {
+          longest = d;
+          P->res_longest = k;
+        }
+      }
+      P->res_span_ms = t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
+      P->res_longest_ms = longest;
+      P->res_occupancy = P->res_span_ms > 0 ? busy / (P->res_span_ms * P->res_grid) : 0.0;
+    }
+  }
   ats_status first_err = ATS_OK, first_warn = ATS_OK;
   for (int k = 0; k < n; ++k) {
     int status = sc[k].status;
     if (flags[k]) status = ATS_ERR_BAD_INPUT;
     if (timed_out && sc[k].phase != kDone) status = ATS_ERR_TIMEOUT;
+    if (P->mode[k] != 0 && sc[k].phase != kDone && status == ATS_OK) status = ATS_ERR_TIMEOUT;  // never ran
     if (status == ATS_OK && flags[n + k]) status = ATS_WARN_NEGATIVE;
     if (stats) {
       ats_solve_stats &o = stats[k];
@@ -1432,11 +1610,13 @@ ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opt
   s = plan_begin(P, xs, off);
   const int64_t mt = plan_max_ticks(P);
   const int max_chunks = (int)std::min<int64_t>((mt + o.check_every - 1) / o.check_every, 1 << 30);
-  if (s == ATS_OK) s = plan_ensure_loop(P, max_chunks);
+  if (s == ATS_OK && P->n_tick > 0) s = plan_ensure_loop(P, max_chunks);
+  if (s == ATS_OK && !P->d_loop) s = dev_alloc_t(ctx, 1, &P->d_loop);
+  if (s == ATS_OK) s = plan_launch_resident(P, false);
   P->profiling = prof;
   if (s != ATS_OK) return s;
   CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
-  CUDA_TRY(cudaGraphLaunch(P->loop_exec, st));
+  if (P->n_tick > 0) CUDA_TRY(cudaGraphLaunch(P->loop_exec, st));
   CUDA_TRY(cudaMemsetAsync(&d_rec->neg, 0, sizeof(int), st));
   CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, &d_rec->neg, P->grid, st));
   CUDA_TRY(cudaMemcpyAsync(&d_rec->sc, P->d_final, sizeof(SolveScalars), cudaMemcpyDeviceToDevice, st));
@@ -1917,6 +2097,15 @@ ats_status ats_batch_kernel_stats(const ats_batch *B, ats_kernel_stats *out) {
     out->upd_bytes = P->upd_bytes;
     out->launches = P->launches;
     out->ticks = P->ticks;
+    out->res_ms = P->res_ms;
+    out->res_bytes = P->res_bytes;
+    out->res_launches = P->res_launches;
+    out->res_solves = P->n_cq + P->n_tq;
+    out->res_span_ms = P->res_span_ms;
+    out->res_longest_ms = P->res_longest_ms;
+    out->res_occupancy = P->res_occupancy;
+    out->res_longest = P->res_longest;
+    out->res_grid = P->res_grid;
     return ATS_OK;
   } catch (...) {
     return ats::abi_exception();

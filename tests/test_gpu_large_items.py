@@ -101,7 +101,7 @@ def test_large_level_matches_oracle(ats, ctx, big_level, prec, tile):
 @pytest.mark.parametrize("tile", [384, 512, 1024])
 @pytest.mark.parametrize("seed", [11, 12, 13])
 def test_irregular_amr_levels_large_items(ats, ctx, prec, tile, seed):
-    """Unions of random oct boxes (hundreds of octs, several passes per thread
+    """The tick path on unions of random oct boxes (hundreds of octs, several passes per thread
     at these item sizes) with refined cells and every interface kind."""
     lv, st = W.random_amr_level(seed, n_box=4, box_hi=14)
     xr = _oracle_x(lv, st)
@@ -109,7 +109,8 @@ def test_irregular_amr_levels_large_items(ats, ctx, prec, tile, seed):
     L.build(st.dt, st.K, st.E, **_faces(st))
     x = st.E.copy()
     P = ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED
-    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, tile_octs=tile)
+    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, tile_octs=tile,
+                          sched=ats.ATS_SCHED_TICK)
     assert code == 0, stats
     assert _rel(x, xr) <= PAR
     nl = ~lv.leaf_cells()
@@ -119,7 +120,7 @@ def test_irregular_amr_levels_large_items(ats, ctx, prec, tile, seed):
 
 @pytest.mark.parametrize("tile", [384, 512, 1024])
 def test_ragged_batch_large_items(ats, ctx, tile):
-    """A ragged batch at large item sizes: every solve matches the oracle and
+    """The tick path on a ragged batch at large item sizes: every solve matches the oracle and
     is bitwise the same alone and in the batch."""
     rng = np.random.default_rng(4242 + tile)
     solves = [W.random_box_solve(rng, o, robin=True) for o in (1, 7, 100, 900, 2500, 5000)]
@@ -130,7 +131,7 @@ def test_ragged_batch_large_items(ats, ctx, tile):
         levels.append(L)
     xs = [st.E.copy() for _, st in solves]
     B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
-                  use_graph=1, check_every=8, tile_octs=tile)
+                  use_graph=1, check_every=8, tile_octs=tile, sched=ats.ATS_SCHED_TICK)
     code, stats = B.solve(xs)
     assert code == 0, stats
     for (lv, st), x in zip(solves, xs):
@@ -138,7 +139,7 @@ def test_ragged_batch_large_items(ats, ctx, tile):
     for k, ((lv, st), L) in enumerate(zip(solves, levels)):
         x = st.E.copy()
         code, _ = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
-                          tile_octs=tile)
+                          tile_octs=tile, sched=ats.ATS_SCHED_TICK)
         assert code == 0
         np.testing.assert_array_equal(x, xs[k])
     B.close()

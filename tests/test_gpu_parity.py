@@ -69,16 +69,18 @@ def test_operator_and_rhs_match_oracle(ats, ctx, seed):
     L.close()
 
 
+@pytest.mark.parametrize("sched", ["auto", "tick"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("seed", [11, 12, 13, 14])
-def test_random_amr_levels_all_face_types(ats, ctx, prec, seed):
+def test_random_amr_levels_all_face_types(ats, ctx, prec, seed, sched):
     lv, st = W.random_amr_level(seed)
     _, xr = _oracle_solution(lv, st)
     L = ats.Level(ctx, lv)
     L.build(st.dt, st.K, st.E, **_faces(st))
     x = st.E.copy()
     code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED,
-                          precision=ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED)
+                          precision=ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED,
+                          sched=ats.ATS_SCHED_TICK if sched == "tick" else ats.ATS_SCHED_AUTO)
     assert code == 0, stats
     assert stats["err_bound"] <= TOL
     assert _rel(x, xr) <= PAR
@@ -132,9 +134,11 @@ def test_ragged_shapes_and_tails(ats, ctx, dims):
     _, xr = _oracle_solution(lv, st)
     L = ats.Level(ctx, lv)
     L.build(st.dt, st.K, st.E, **_faces(st))
-    for prec, tile in ((ats.ATS_PREC_FP64, 0), (ats.ATS_PREC_MIXED, 32), (ats.ATS_PREC_MIXED, 64)):
+    for prec, tile, sched in ((ats.ATS_PREC_FP64, 0, ats.ATS_SCHED_AUTO), (ats.ATS_PREC_FP64, 0, ats.ATS_SCHED_TICK),
+                              (ats.ATS_PREC_MIXED, 32, ats.ATS_SCHED_TICK), (ats.ATS_PREC_MIXED, 64, ats.ATS_SCHED_TICK)):
         x = st.E.copy()
-        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=prec, tile_octs=tile)
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=prec, tile_octs=tile,
+                              sched=sched)
         assert code == 0, stats
         assert _rel(x, xr) <= PAR
     L.close()
@@ -182,8 +186,9 @@ def test_device_pointers_and_rhs_override(ats, ctx):
     L.close()
 
 
+@pytest.mark.parametrize("sched", ["auto", "tick"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batch_matches_oracle_and_is_invariant(ats, ctx, prec):
+def test_batch_matches_oracle_and_is_invariant(ats, ctx, prec, sched):
     """A ragged batch: every solve matches the oracle, and each result is
     bitwise the same alone and inside the batch (same work-item tiling,
     fixed-order reductions)."""
@@ -196,7 +201,9 @@ def test_batch_matches_oracle_and_is_invariant(ats, ctx, prec):
         L.build(st.dt, st.K, st.E, **_faces(st))
         levels.append(L)
     xs = [st.E.copy() for _, st in solves]
-    B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, use_graph=1, check_every=8)
+    SC = ats.ATS_SCHED_TICK if sched == "tick" else ats.ATS_SCHED_AUTO
+    B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, use_graph=1, check_every=8,
+                  sched=SC)
     code, stats = B.solve(xs)
     assert code == 0, stats
     for (lv, st), x, s in zip(solves, xs, stats):
@@ -204,7 +211,7 @@ def test_batch_matches_oracle_and_is_invariant(ats, ctx, prec):
         assert _rel(x, xr) <= PAR, s
     for k, ((lv, st), L) in enumerate(zip(solves, levels)):
         x = st.E.copy()
-        code, _ = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P)
+        code, _ = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, sched=SC)
         assert code == 0
         np.testing.assert_array_equal(x, xs[k])
     # run the batch a second time: identical results (deterministic)
@@ -415,7 +422,8 @@ def test_autotune_keeps_a_valid_fastest_plan(ats, ctx, mem):
         L = ats.Level(ctx, lv)
         L.build(st.dt, st.K, st.E, **_faces(st))
         levels.append(L)
-    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=1, mem=M, x0=x0)
+    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=1, mem=M, x0=x0,
+                sched=ats.ATS_SCHED_TICK)
     B = ats.Batch(ctx, levels, check_every=16, **opts)
     xs = [conv(st.E.copy()) for _, st in solves]
     r = B.autotune(xs, tiles=(0, 64, 256), checks=(4, 16), reps=1)
@@ -522,7 +530,7 @@ def test_full_size_batch_sampled_parity(ats, ctx):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_device_loop_matches_host_polled(ats, ctx, prec):
-    """A ragged batch and a solo solve with the whole tick loop in one graph
+    """The tick path: a ragged batch and a solo solve with the whole tick loop in one graph
     (use_graph = 2, a WHILE conditional node) give bitwise the results and
     statistics of host-polled graphs (use_graph = 1); an iteration cap still
     ends the loop with NOT_CONVERGED."""
@@ -536,7 +544,8 @@ def test_device_loop_matches_host_polled(ats, ctx, prec):
         levels.append(L)
     res = {}
     for g in (1, 2):
-        B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, use_graph=g, check_every=4)
+        B = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, use_graph=g, check_every=4,
+                      sched=ats.ATS_SCHED_TICK)
         xs = [st.E.copy() for _, st in solves]
         code, stats = B.solve(xs)
         assert code == 0, stats
@@ -555,7 +564,8 @@ def test_device_loop_matches_host_polled(ats, ctx, prec):
         assert _rel(x, xr) <= PAR
     lv, st = solves[3]
     x = st.E.copy()
-    code, s = levels[3].solve(x, tol=1e-14, precision=P, use_graph=2, check_every=4, max_iter=5)
+    code, s = levels[3].solve(x, tol=1e-14, precision=P, use_graph=2, check_every=4, max_iter=5,
+                              sched=ats.ATS_SCHED_TICK)
     assert code == ats.ATS_ERR_NOT_CONVERGED
     assert s["iterations"] == 5
     for L in levels:

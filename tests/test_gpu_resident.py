@@ -1,0 +1,251 @@
+"""GPU parity of the resident solver against the FP64 oracle.
+
+The resident solver runs a whole level solve inside one launch: a thread-block
+cluster (per-step sums through distributed shared memory, steps ordered by
+the hardware cluster barrier) or, for a small level, one CTA.  The method is
+the same as on the tick path -- the level matrix of Eq. Er_imp1 with the
+interface rows of Sect. 3.2, Jacobi-PCG (Sect. 3.3.4) in FP64 or in FP32 with
+FP64 refinement -- so the same parity bound holds: both sides stop on the
+certified rule ||b - A x|| <= 5e-11 ||x||, lambda_min >= 1 bounds each
+solution's error by its residual, and they differ by at most 1e-10 relative.
+
+Covered: every interface kind and non-leaf cells, every resident shape (one
+CTA; clusters of 1, 2, 4, 8 and 16 CTAs; 256 and 512 threads), levels with
+many octs per thread, ragged batches (bitwise alone vs in the batch, and run
+to run), the FP32-scalar variant, degenerate and capped solves.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 5e-11
+PAR = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ats():
+    from paper_1401_1112_gb300 import ats as A
+    from paper_1401_1112_gb300 import build
+
+    build.build()
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(ats):
+    c = ats.Context(0)
+    yield c
+    c.close()
+
+
+def _faces(st):
+    return dict(face_K=st.face_K, face_E=st.face_E, face_F=st.face_F)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _oracle_x(lv, st):
+    S = oracle.assemble(lv, st.dt, st.K, st.E, s=st.s, src=st.src, **_faces(st))
+    x, info = oracle.pcg(S, st.E, tol=TOL, stop_rule=oracle.STOP_CERTIFIED)
+    assert info["status"] == 0, info
+    return x
+
+
+def _prec(ats, name):
+    return ats.ATS_PREC_FP64 if name == "fp64" else ats.ATS_PREC_MIXED
+
+
+# (res_cta_octs, res_cluster, res_threads): one CTA per level, or clusters
+SHAPES = [(1 << 30, 1, 512), (-1, 1, 256), (-1, 2, 512), (-1, 4, 256), (-1, 8, 512), (-1, 16, 256),
+          (-1, 16, 512)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"cta{s[0] > 0}-c{s[1]}-t{s[2]}")
+@pytest.mark.parametrize("seed", [11, 12])
+def test_irregular_levels_every_shape(ats, ctx, prec, shape, seed):
+    """Unions of oct boxes with refined cells and Dirichlet / Neumann / Robin
+    interface faces of every relation, a coupling shift and a source."""
+    lv, st = W.random_amr_level(seed, n_box=4, box_hi=10)
+    rng = np.random.default_rng(seed)
+    st.s = rng.uniform(0, 2, lv.n_cell)
+    st.src = rng.uniform(0, 0.5, lv.n_cell)
+    xr = _oracle_x(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, s=st.s, src=st.src, **_faces(st))
+    cta, cl, th = shape
+    x = st.E.copy()
+    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=_prec(ats, prec),
+                          sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=cta, res_cluster=cl, res_threads=th)
+    assert code == 0, stats
+    assert stats["err_bound"] <= TOL
+    assert _rel(x, xr) <= PAR
+    nl = ~lv.leaf_cells()
+    np.testing.assert_array_equal(x[nl], st.E[nl])
+    L.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 37), (33, 1, 1), (3, 5, 7), (17, 9, 5)])
+def test_ragged_shapes_one_cta_and_cluster(ats, ctx, prec, dims):
+    """One oct, strips, and oct counts that leave CTAs of a cluster empty or
+    split unevenly."""
+    rng = np.random.default_rng(sum(dims))
+    lv = W.box_level(*dims, 0.05, [(W.DIRICHLET, 1.0), None, (W.ROBIN, 0.3), (W.NEUMANN, 0.0), None,
+                                   (W.DIRICHLET, 1.0)])
+    N, nf = lv.n_cell, lv.n_face
+    st = W.Step(dt=3.0 * 0.05 ** 2, K=np.exp(rng.standard_normal(N)), E=rng.uniform(0.5, 1.5, N),
+                face_K=np.exp(rng.standard_normal(nf)), face_E=rng.uniform(0, 2, nf),
+                face_F=rng.uniform(-0.1, 0.1, nf))
+    xr = _oracle_x(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, **_faces(st))
+    for cta, cl in ((1 << 30, 8), (-1, 8), (-1, 16)):
+        x = st.E.copy()
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=_prec(ats, prec),
+                              sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=cta, res_cluster=cl)
+        assert code == 0, stats
+        assert _rel(x, xr) <= PAR
+    L.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_many_octs_per_thread(ats, ctx, prec):
+    """A 32 x 32 x 24-oct level (24 576 octs): 6 to 12 octs per thread on one
+    cluster, 48 to 96 on one CTA."""
+    rng = np.random.default_rng(321)
+    lv = W.box_level(32, 32, 24, 1.0 / 64, [(W.DIRICHLET, 1.0), (W.NEUMANN, 0.0), (W.ROBIN, 0.5),
+                                            (W.DIRICHLET, 1.0), None, (W.ROBIN, 0.9)])
+    N, nf = lv.n_cell, lv.n_face
+    st = W.Step(dt=20.0 / 64 ** 2 / 2.0, K=np.exp(rng.standard_normal(N)), E=rng.uniform(0.5, 1.5, N),
+                face_K=np.exp(rng.standard_normal(nf)), face_E=rng.uniform(0, 2, nf),
+                face_F=rng.uniform(-0.05, 0.05, nf))
+    xr = _oracle_x(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, **_faces(st))
+    for cta, cl, th in ((-1, 8, 512), (-1, 4, 256), (1 << 30, 1, 512)):
+        x = st.E.copy()
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=_prec(ats, prec),
+                              sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=cta, res_cluster=cl, res_threads=th)
+        assert code == 0, stats
+        assert _rel(x, xr) <= PAR
+    L.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_alone_and_in_batch_bitwise(ats, ctx, prec):
+    """A ragged batch spanning one-CTA and cluster solves: every solve matches
+    the oracle; each result is bitwise the same alone and in the batch, and
+    run to run (the queue order and which cluster takes a solve do not
+    enter its arithmetic)."""
+    rng = np.random.default_rng(2077)
+    solves = [W.random_box_solve(rng, o, robin=True) for o in (1, 9, 130, 700, 2100, 4500, 12000, 3, 60)]
+    P = _prec(ats, prec)
+    levels = []
+    for lv, st in solves:
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        levels.append(L)
+    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P)
+    B = ats.Batch(ctx, levels, **opts)
+    assert B.kernel_stats()["res_solves"] == len(solves)
+    xs = [st.E.copy() for _, st in solves]
+    code, stats = B.solve(xs)
+    assert code == 0, stats
+    for (lv, st), x in zip(solves, xs):
+        assert _rel(x, _oracle_x(lv, st)) <= PAR
+    for k, L in enumerate(levels):
+        x = solves[k][1].E.copy()
+        code, _ = L.solve(x, **opts)
+        assert code == 0
+        np.testing.assert_array_equal(x, xs[k])
+    for _ in range(2):
+        xs2 = [st.E.copy() for _, st in solves]
+        code, stats2 = B.solve(xs2)
+        assert code == 0
+        for a, b in zip(xs, xs2):
+            np.testing.assert_array_equal(a, b)
+        assert [s["iterations"] for s in stats] == [s["iterations"] for s in stats2]
+    B.close()
+    for L in levels:
+        L.close()
+
+
+def test_fp32_scalars_variant(ats, ctx):
+    """Mixed precision with alpha and beta formed from FP32-rounded totals
+    (the tick path's form) still refines to the certificate and matches."""
+    rng = np.random.default_rng(515)
+    for o in (40, 3000):
+        lv, st = W.random_box_solve(rng, o, dt_lo=10.0, dt_hi=100.0, robin=True)
+        xr = _oracle_x(lv, st)
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        for f32 in (0, 1):
+            x = st.E.copy()
+            code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                                  sched=ats.ATS_SCHED_RESIDENT, fp32_scalars=f32)
+            assert code == 0, stats
+            assert _rel(x, xr) <= PAR
+        L.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_degenerate_and_capped(ats, ctx, prec):
+    """A constant state between zero-flux walls converges with no iteration
+    (x = E^n bitwise) beside a solve that iterates; an iteration cap ends a
+    resident solve with NOT_CONVERGED after exactly that many iterations;
+    with one refinement pass allowed the mixed path stops near the FP32
+    floor and reports it."""
+    rng = np.random.default_rng(7)
+    P = _prec(ats, prec)
+    lv = W.box_level(5, 3, 4, 0.05)
+    E = np.full(lv.n_cell, 0.7)
+    L = ats.Level(ctx, lv)
+    L.build(10.0 * 0.05 ** 2, np.exp(rng.standard_normal(lv.n_cell)), E)
+    lv2, st2 = W.random_box_solve(rng, 3000, robin=True)
+    L2 = ats.Level(ctx, lv2)
+    L2.build(st2.dt, st2.K, st2.E, **_faces(st2))
+    B = ats.Batch(ctx, [L, L2], tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P,
+                  sched=ats.ATS_SCHED_RESIDENT)
+    xs = [E.copy(), st2.E.copy()]
+    code, stats = B.solve(xs)
+    assert code == 0, stats
+    assert stats[0]["iterations"] == 0 and stats[0]["res_norm"] == 0.0
+    np.testing.assert_array_equal(xs[0], E)
+    assert _rel(xs[1], _oracle_x(lv2, st2)) <= PAR
+    B.close()
+    x = st2.E.copy()
+    code, s = L2.solve(x, tol=1e-14, precision=P, sched=ats.ATS_SCHED_RESIDENT, max_iter=5)
+    assert code == ats.ATS_ERR_NOT_CONVERGED and s["iterations"] == 5
+    if prec == "mixed":
+        x = st2.E.copy()
+        code, s = L2.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, sched=ats.ATS_SCHED_RESIDENT,
+                           max_refine=1, inner_rtol=1e-6)
+        assert code == ats.ATS_ERR_NOT_CONVERGED and s["refinements"] == 2
+        assert 1e-10 < _rel(x, _oracle_x(lv2, st2)) < 1e-4
+    L.close()
+    L2.close()
+
+
+def test_tick_and_resident_agree(ats, ctx):
+    """The same levels on both paths: each within the parity bound of the
+    oracle (their arithmetic differs, so not bitwise)."""
+    rng = np.random.default_rng(99)
+    solves = [W.random_box_solve(rng, o, robin=True) for o in (20, 800, 5000)]
+    for lv, st in solves:
+        xr = _oracle_x(lv, st)
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        for sched in (ats.ATS_SCHED_TICK, ats.ATS_SCHED_RESIDENT):
+            x = st.E.copy()
+            code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                                  sched=sched)
+            assert code == 0, stats
+            assert _rel(x, xr) <= PAR
+        L.close()
