@@ -270,9 +270,11 @@ def run_ours(args, rank, world, local):
     xs = [view(x_d, offs[k], offs[k + 1]) for k in range(n)]
     for k in range(n):  # per-level entry point once (the plan needs built operators)
         levels[k].build(**coef_kwargs(k))
+    # every level of the batch on the resident solver (levels up to
+    # --res-max-octs octs; the batch's largest has 32 768)
     batch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
                       use_graph=1, check_every=args.check_every, mem=ats.ATS_MEM_DEVICE, tile_octs=args.tile,
-                      inner_rtol=args.inner_rtol)
+                      inner_rtol=args.inner_rtol, res_max_octs=args.res_max_octs)
     coefs = batch.prepare_coefs([coef_kwargs(k) for k in range(n)])
 
     def build_ops():
@@ -289,6 +291,12 @@ def run_ours(args, rank, world, local):
         tune["seconds"] = round(time.time() - t_tune, 2)
     tile_octs = tune["tile_octs"] if tune else args.tile
     check_every = tune["check_every"] if tune else args.check_every
+    # the resident shape of the tuned plan, for the other batches of this run
+    res_shape = dict(res_max_octs=args.res_max_octs)
+    if tune:
+        res_shape.update(res_threads=tune["chosen"]["res_threads"], res_cluster=tune["chosen"]["res_cluster"],
+                         res_cta_octs=tune["chosen"]["res_cta_octs"])
+        tune.pop("chosen")
 
     def step():
         x_d.copy_(E_d)          # initial guess x0 = E^n
@@ -319,7 +327,8 @@ def run_ours(args, rank, world, local):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     acc = {"op_ms": 0.0, "op_bytes": 0.0, "ref_ms": 0.0, "ref_bytes": 0.0, "upd_ms": 0.0, "upd_bytes": 0.0,
-           "ticks": 0}
+           "ticks": 0, "res_ms": 0.0, "res_bytes": 0.0, "res_launches": 0}
+    res_timeline = []
     launches = 0
     ev0.record(stream)
     for _ in range(args.steps):
@@ -327,7 +336,10 @@ def run_ours(args, rank, world, local):
         ks = batch.kernel_stats()
         for key in acc:
             acc[key] += ks[key]
-        launches += ks["launches"] + 5  # tick kernels + operator build (2) + init, final, flag gather
+        res_timeline.append({k: ks[k] for k in ("res_span_ms", "res_longest_ms", "res_occupancy", "res_longest",
+                                                "res_grid", "res_solves")})
+        # tick kernels, resident launches, operator build (2), init, final, flag gather
+        launches += ks["launches"] + ks["res_launches"] + 5
     ev1.record(stream)
     barrier()
     clocks = sampler.stop(t_region, time.perf_counter())
@@ -344,16 +356,20 @@ def run_ours(args, rank, world, local):
     # concurrently with k_op, so its event span includes time shared with k_op:
     # the roofline kernel is the longer of the two HBM-bound CG kernels.
     peak, peak_kind = _peaks()
+    # the resident launch (a cluster kernel and, beside it, single CTAs on the
+    # SMs no cluster fits on) counts as one launch per step: its span
+    res_name = "k_res2_cluster+k_res2_cta"
     kern = {"k_op<float>": ("op_ms", "op_bytes"), "k_ref<float>": ("ref_ms", "ref_bytes"),
-            "k_upd<float>": ("upd_ms", "upd_bytes")}
-    dom = max(("k_op<float>", "k_upd<float>"), key=lambda k: acc[kern[k][0]])
+            "k_upd<float>": ("upd_ms", "upd_bytes"), res_name: ("res_ms", "res_bytes")}
+    dom = max(("k_op<float>", "k_upd<float>", res_name), key=lambda k: acc[kern[k][0]])
     dms, dbytes = acc[kern[dom][0]], acc[kern[dom][1]]
+    dl = args.steps if dom == res_name else max(1, acc["ticks"])
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else 0.0
     roofline = {
         "bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
         "frac": round(achieved / peak, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-        "traffic": _traffic_for(dom, dbytes / max(1, acc["ticks"])),
-        "launches": int(acc["ticks"]), "bytes_per_launch": round(dbytes / max(1, acc["ticks"])),
+        "traffic": _traffic_for(dom, dbytes / dl),
+        "launches": int(dl), "bytes_per_launch": round(dbytes / dl),
         # the whole step on the minimal Jacobi-PCG traffic: 10 words per cell
         # and CG iteration (read p, K, x, r, q, D^-1; write q, x, r, p)
         "cg_step": {"cell_iterations": cell_its, "bytes_per_cell_iteration": 10 * 4,
@@ -363,6 +379,7 @@ def run_ours(args, rank, world, local):
                            "GBps": round(acc[b] / (acc[a] / 1e3) / 1e9, 1) if acc[a] else None,
                            "bound": "fp64 alu, concurrent with k_op" if k.startswith("k_ref") else "hbm"}
                        for k, (a, b) in kern.items()},
+        "resident_timeline": res_timeline[-1] if res_timeline else None,
     }
 
     # end to end through the public API with host buffers (pinned)
@@ -379,7 +396,7 @@ def run_ours(args, rank, world, local):
         # waits once per solve
         hbatch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
                            use_graph=2, check_every=check_every, tile_octs=tile_octs, mem=ats.ATS_MEM_HOST,
-                           x0=ats.ATS_X0_E_OLD)
+                           x0=ats.ATS_X0_E_OLD, **res_shape)
         hx = [xn[offs[k]:offs[k + 1]] for k in range(n)]
 
         hcoefs = hbatch.prepare_coefs([
@@ -442,7 +459,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_cpu:
         ubatch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
                            use_graph=1, check_every=check_every, tile_octs=tile_octs, mem=ats.ATS_MEM_DEVICE,
-                           max_refine=1, inner_rtol=1e-6)
+                           max_refine=1, inner_rtol=1e-6, **res_shape)
         build_ops()
         x_d.copy_(E_d)
         code, _ = ubatch.solve(xs)
@@ -522,6 +539,8 @@ def run_ours(args, rank, world, local):
             "l2": "inputs larger than L2 (working set ~%.2f GB)" % (total_cells * 64 / 1e9),
             "parallelism": f"replicas x{world}",
             "tile_octs": tile_octs, "check_every": check_every, "autotune": tune,
+            "scheduler": "resident solver for levels up to %d octs (one launch runs every solve to its end: "
+                         "thread-block clusters, CG state in shared memory)" % args.res_max_octs,
         },
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -983,6 +1002,8 @@ def main():
     ap.add_argument("--configs", action="store_true",
                     help="time each workload configuration on the oracle and the GPU (one JSON line) instead")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--res-max-octs", type=int, default=32768,
+                    help="levels up to this many octs take the resident solver (0 = the library default)")
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-max-cells", type=int, default=256 ** 3)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)

@@ -154,10 +154,16 @@ typedef struct {
   int res_cta_octs;  /* resident solver: a level of at most this many octs is */
                      /* solved by one CTA alone (0 = 2048, < 0 = never)      */
   int res_max_octs;  /* ATS_SCHED_AUTO: levels above this many octs take the  */
-                     /* tick path (0 = 4096)                                 */
+                     /* tick path (0 = 16384 for ATS_PREC_MIXED, 2048 for    */
+                     /* ATS_PREC_FP64)                                       */
   int fp32_scalars;  /* resident solver, mixed precision: 1 = CG alpha, beta  */
                      /* from the dot totals rounded to FP32 (the tick path's  */
                      /* form); 0 = from the FP64 totals (default)            */
+  int res_state;     /* resident solver, mixed precision: where each CTA     */
+                     /* keeps K, z and p of its octs: 0 = shared memory      */
+                     /* (neighbours read from the owning CTA through          */
+                     /* distributed shared memory; default), 1 = global      */
+                     /* memory (L2).  The FP64 bulk always uses global.      */
 } ats_solve_opts;
 
 /* scheduling of a solve (ats_solve_opts.sched).  Which path a level takes
@@ -304,9 +310,12 @@ ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out)
 
 /* Autotuner of the batched launch (not in the paper, whose solver is one CPU
  * CG per level): times ats_batch_solve on the batch's own levels and
- * operators for every candidate pair (work-item size tile_octs, poll
- * interval check_every) and keeps the fastest, together with the options the
- * batch was created with.  tiles[n_tiles]: octs per work item, 0 = the
+ * operators for every candidate and keeps the fastest, together with the
+ * options the batch was created with.  The candidates: for a batch with
+ * tick-path solves, every pair (work-item size tile_octs, poll interval
+ * check_every); for a batch with resident solves, every resident shape
+ * (res_threads 256 / 512 x res_cluster 8 / 16 x res_cta_octs 1024 / 2048);
+ * each varies those options only.  tiles[n_tiles]: octs per work item, 0 = the
  * library's size rule (see ats_solve_opts.tile_octs), others
  * rounded up to a multiple of 32; NULL / 0 = {0, 128, 256, 384, 512}.
  * checks[n_checks]: ticks per CUDA graph and host poll; NULL / 0 = {8, 16,
@@ -316,8 +325,8 @@ ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out)
  * it holds the solution of one more solve with the chosen configuration, whose
  * plan the batch keeps.  Results are valid solutions for every candidate but
  * differ between tile sizes in the last bits (a solve's reduction order
- * follows its work items).  out: the choice, its time and the time of the
- * batch's original options (may be NULL).  Errors: ATS_ERR_INVALID_ARG for a
+ * follows its work items, a resident solve's its shape).  out: the choice,
+ * its time and the time of the batch's original options (may be NULL).  Errors: ATS_ERR_INVALID_ARG for a
  * NULL batch or x, a negative tile or an unbuilt level; the first failing
  * solve's status otherwise (the batch then keeps its original plan). */
 typedef struct {
@@ -326,6 +335,10 @@ typedef struct {
   double ms;         /* fastest solve time of the chosen configuration     */
   double ms_default; /* fastest solve time of the batch's original options */
   int candidates;    /* configurations timed                               */
+  int res_threads;   /* chosen resident shape: threads per CTA, CTAs per   */
+  int res_cluster;   /* cluster, one-CTA level limit (0 = the default)     */
+  int res_cta_octs;
+  ats_solve_opts chosen; /* the options the batch keeps                    */
 } ats_tune_result;
 ats_status ats_batch_autotune(ats_batch *batch, double *const *x_inout, const int *tiles, int n_tiles,
                               const int *checks, int n_checks, int reps, ats_tune_result *out);

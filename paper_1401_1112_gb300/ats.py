@@ -69,7 +69,7 @@ class ats_solve_opts(ctypes.Structure):
         ("tile_octs", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
         ("mem", ctypes.c_int), ("x0", ctypes.c_int), ("sched", ctypes.c_int), ("res_threads", ctypes.c_int),
         ("res_cluster", ctypes.c_int), ("res_cta_octs", ctypes.c_int), ("res_max_octs", ctypes.c_int),
-        ("fp32_scalars", ctypes.c_int),
+        ("fp32_scalars", ctypes.c_int), ("res_state", ctypes.c_int),
     ]
 
 
@@ -95,7 +95,8 @@ class ats_kernel_stats(ctypes.Structure):
 
 class ats_tune_result(ctypes.Structure):
     _fields_ = [("tile_octs", ctypes.c_int), ("check_every", ctypes.c_int), ("ms", ctypes.c_double),
-                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int)]
+                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int), ("res_threads", ctypes.c_int),
+                ("res_cluster", ctypes.c_int), ("res_cta_octs", ctypes.c_int), ("chosen", ats_solve_opts)]
 
 
 class ats_solve_stats(ctypes.Structure):
@@ -268,7 +269,7 @@ def _level_desc(level, keep):
 def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, max_iter=0, max_refine=0,
               inner_rtol=0.0, tile_octs=0, check_every=0, use_graph=0, mem=ATS_MEM_HOST,
               x0=ATS_X0_GIVEN, sched=ATS_SCHED_AUTO, res_threads=0, res_cluster=0, res_cta_octs=0,
-              res_max_octs=0, fp32_scalars=0) -> ats_solve_opts:
+              res_max_octs=0, fp32_scalars=0, res_state=0) -> ats_solve_opts:
     o = ats_solve_opts()
     lib().ats_default_opts(ctypes.byref(o))
     o.tol = tol
@@ -292,6 +293,7 @@ def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, m
     o.res_cta_octs = res_cta_octs
     o.res_max_octs = res_max_octs
     o.fp32_scalars = fp32_scalars
+    o.res_state = res_state
     return o
 
 
@@ -455,7 +457,9 @@ def ats_batch_autotune(batch, xs: Sequence, tiles: Sequence[int] = (), checks: S
     r = ats_tune_result()
     _check(lib().ats_batch_autotune(batch, arr, ta, len(tiles), ca, len(checks), int(reps), ctypes.byref(r)),
            "ats_batch_autotune")
-    return {name: getattr(r, name) for name, _ in r._fields_}
+    out = {name: getattr(r, name) for name, _ in r._fields_ if name != "chosen"}
+    out["chosen"] = {name: getattr(r.chosen, name) for name, _ in r.chosen._fields_}
+    return out
 
 
 def ats_power_law_K(ctx, E, K0, p, K):

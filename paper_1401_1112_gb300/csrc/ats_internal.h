@@ -204,6 +204,7 @@ struct ResArgs {
   int *heads;
   unsigned long long *cells;
   unsigned long long *t_solve;  // [n_solves][2] %globaltimer at a solve's start and end (profiling), or null
+  int cap;                      // shared-memory form: octs per CTA kept in shared memory
 };
 // One resident launch on st: clusters of `cluster` CTAs of `threads` threads
 // (256 or 512), `grid` CTAs in all (a multiple of `cluster`) when the cluster
@@ -213,6 +214,15 @@ cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const
 int resident_max_clusters(bool fp64, int threads, int cluster);
 // CTAs of the single-CTA kernel resident per SM.
 int resident_cta_blocks(bool fp64, int threads);
+// The resident solver with each CTA's K, z, p in shared memory (FP32 bulk):
+// a.cap octs per CTA (resident_smem_cap gives the largest that fits), one
+// CTA per SM; the same queue and grid conventions as launch_resident.
+// cta_only: the single-CTA kernel only (the CTA queue), e.g. on the SMs a
+// concurrent cluster launch leaves free.
+cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st,
+                                 bool cta_only = false);
+int resident_smem_clusters(int threads, int cluster, int cap);
+int resident_smem_cap(int threads, int device);
 
 // Start of a solve: e = 0 on every cell of every item, and x64 = src[solve]
 // where src (device array of device pointers) is non-null for that solve.

@@ -35,6 +35,8 @@
 // state (double-buffered by tick parity).  No CTA ever waits for another.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "ats_internal.h"
@@ -406,11 +408,11 @@ __device__ __forceinline__ void ref_axis(const SolveDev &sd, int o, const int (&
 // (every product a DFMA); z = r / D_T in the bulk precision, D_T stored for the
 // CG kernels of the following inner solve.  Norms for the stopping test (r.r,
 // x.x) and r.z are accumulated with compensated bulk-precision dots.
+// The values of one oct (zo = z, dv = D); op_refine_oct stores them.
 template <typename T, bool kCoh = false>
-__device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool want_x, Acc<T> &rr,
-                                              Acc<T> &xx, Acc<T> &rz) {
+__device__ __forceinline__ void ref_oct_values(const SolveDev &sd, int o, bool want_x, Acc<T> &rr, Acc<T> &xx,
+                                               Acc<T> &rz, T (&zo)[8], T (&dv)[8]) {
   const T *__restrict__ KT = (const T *)sd.KT;
-  T *z = (T *)sd.z;
   constexpr bool mixed = sizeof(T) != sizeof(double);
   const T hT = (T)sd.h;
   int nb[6];
@@ -439,7 +441,6 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
     if (mixed) ld8_ro((const T *)sd.xdT + 8 * rec, xdT);
   }
   ld8_ro(sd.b64 + 8 * o, b);
-  T zo[8], dv[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const bool leaf = KTo[c] >= T(0);
@@ -461,7 +462,14 @@ __device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool wa
       }
     }
   }
-  st8(z + 8 * o, zo);
+}
+
+template <typename T, bool kCoh = false>
+__device__ __forceinline__ void op_refine_oct(const SolveDev &sd, int o, bool want_x, Acc<T> &rr,
+                                              Acc<T> &xx, Acc<T> &rz) {
+  T zo[8], dv[8];
+  ref_oct_values<T, kCoh>(sd, o, want_x, rr, xx, rz, zo, dv);
+  st8((T *)sd.z + 8 * o, zo);
   st8((T *)sd.dg + 8 * o, dv);
 }
 
@@ -1668,6 +1676,13 @@ __device__ __forceinline__ void cl_st(uint32_t a, const Acc<double> &v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v.s) : "memory");
 }
 
+// lane 0's accumulator in every lane of the warp
+__device__ __forceinline__ void bcast_acc(const Acc<float> &a, Acc<float> &t) {
+  t.s = __shfl_sync(kFull, a.s, 0);
+  t.c = __shfl_sync(kFull, a.c, 0);
+}
+__device__ __forceinline__ void bcast_acc(const Acc<double> &a, Acc<double> &t) { t.s = __shfl_sync(kFull, a.s, 0); }
+
 // State of the solve a group (a CTA or a cluster) works on; thread 0 of each
 // CTA updates its copy from the group's totals, so all copies agree.
 struct ResState {
@@ -1686,12 +1701,15 @@ struct ResShared {
 };
 
 // Sums of NA accumulators over the group: this CTA alone, or every CTA of the
-// cluster.  Thread 0 of each CTA ends with the group totals in `out`.  In a
-// cluster, threads r < cluster size send this CTA's partials to CTA r's inbox
-// (buffer `buf`, slot of this CTA's rank); after the cluster barrier each
-// CTA's thread 0 merges the inbox in rank order.  The inbox alternates
-// between two buffers: a buffer is written again only two sums later, after a
-// barrier that every reader of its previous contents has passed.
+// cluster.  Thread 0 of each CTA ends with the group totals in `out`.  The
+// lanes of a warp, the warps of a CTA and the CTAs of a cluster are merged by
+// fixed shuffle trees (error-free TwoSum pairs in the FP32 bulk): warp 0
+// merges the warps' partials; in a cluster its lanes r < cluster size send
+// the CTA's total to CTA r's inbox (buffer `buf`, slot of this CTA's rank),
+// and after the cluster barrier warp 0 of every CTA merges its inbox, so all
+// CTAs hold bitwise the same totals.  The inbox alternates between two
+// buffers: a buffer is written again only two sums later, after a barrier
+// that every reader of its previous contents has passed.
 template <typename T, int NA, bool kCluster>
 __device__ __forceinline__ void group_sum(Acc<T> (&a)[NA], ResShared<T> &sh, int &buf, Acc<T> (&out)[NA]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1702,31 +1720,38 @@ __device__ __forceinline__ void group_sum(Acc<T> (&a)[NA], ResShared<T> &sh, int
     for (int k = 0; k < NA; ++k) sh.red[warp][k] = a[k];
   }
   __syncthreads();
+  Acc<T> m[NA];
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      if (lane < nw) m[k] = sh.red[lane][k];
+      warp_reduce_acc(m[k]);
+    }
+  }
   if (!kCluster) {
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int k = 0; k < NA; ++k) {
-        out[k] = sh.red[0][k];
-        for (int w = 1; w < nw; ++w) out[k].merge(sh.red[w][k]);
-      }
+      for (int k = 0; k < NA; ++k) out[k] = m[k];
     }
     return;
   }
   const unsigned cs = cl_size(), cr = cl_rank();
-  if (threadIdx.x < cs) {
+  if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < NA; ++k) {
-      Acc<T> m = sh.red[0][k];
-      for (int w = 1; w < nw; ++w) m.merge(sh.red[w][k]);
-      cl_st(cl_map(&sh.inbox[buf][cr][k], threadIdx.x), m);
+      Acc<T> t;
+      bcast_acc(m[k], t);
+      if ((unsigned)lane < cs) cl_st(cl_map(&sh.inbox[buf][cr][k], (unsigned)lane), t);
     }
   }
   cl_sync();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < NA; ++k) {
-      out[k] = sh.inbox[buf][0][k];
-      for (unsigned r = 1; r < cs; ++r) out[k].merge(sh.inbox[buf][r][k]);
+      Acc<T> t;
+      if ((unsigned)lane < cs) t = sh.inbox[buf][lane][k];
+      warp_reduce_acc(t);
+      if (lane == 0) out[k] = t;
     }
   }
   buf ^= 1;
@@ -1980,6 +2005,608 @@ __global__ void __launch_bounds__(NT, ResMinBlocks<T, NT>::value) k_res_cta(ResA
   res_cta_loop<T>(a, sh, buf);
 }
 
+// ---------------------------------------------------------------------------
+// Resident solver with the CG state in shared memory (FP32 bulk)
+// ---------------------------------------------------------------------------
+//
+// Each CTA of the group owns a contiguous run of the level's octs (the
+// group's octs split by cluster rank) and keeps K, z and p of the first
+// `cap` of them in shared memory for the whole solve, with each oct's six
+// neighbours coded as (owning rank, local index).  A step reads its own octs
+// from its shared memory and the neighbours' faces from the owning CTA's
+// shared memory (distributed shared memory inside the cluster): no iteration
+// reads K, z or p from L2 or HBM.  D, q and e -- read and written only by the
+// thread that owns an oct -- stay in global memory, like the FP64 arrays of
+// the refinement pass.  Octs beyond a CTA's capacity use the level's global
+// arrays.  Where an oct's values live does not change what is computed, so
+// the capacity does not enter the arithmetic.
+//
+// A CG iteration reads its neighbours' p instead of recomputing it:
+//   1. p = z + beta p on the own octs (an inner solve's first: p = z), then
+//      a group barrier;
+//   2. q = (I + dt A) p, the sum p.q;
+//   3. r = D z - alpha q, z = D^-1 r, e += alpha p, the sums r.z and r.r.
+
+extern __shared__ __align__(128) unsigned char res2_smem[];
+constexpr int kRes2OctBytes = 3 * 32 + 16;  // per oct: K, z, p rows (8 FP32 each) and six 16-bit neighbour codes
+// Shared bytes for `cap` octs: their rows, one more row of K, z and p (the
+// stand-in neighbour of a face without one: K = -1, so its coefficient is 0,
+// and p = 0), and the codes.
+__host__ __device__ constexpr size_t res2_smem_bytes(int cap) {
+  return (size_t)cap * kRes2OctBytes + 3 * 32;
+}
+
+namespace {
+
+constexpr uint16_t kCodeNone = 0xFFFF;      // no neighbour (a wall or interface face)
+constexpr uint16_t kCodeGlobal = 0xFFFE;    // a neighbour beyond its CTA's capacity: global arrays
+
+struct Res2Ctx {
+  uint32_t sK, sZ, sP, sC;  // shared-window addresses of this CTA's K, z, p rows and codes
+  int cap;                  // octs of this CTA's share kept in shared memory
+  int chunk;                // octs per CTA of the group
+  int lo;                   // first oct of this CTA
+  unsigned cr;              // this CTA's rank in the group (0 for one CTA)
+};
+
+__device__ __forceinline__ void lds4(uint32_t a, float &x, float &y, float &z, float &w) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+}
+__device__ __forceinline__ void ldsc4(uint32_t a, float &x, float &y, float &z, float &w) {
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+}
+__device__ __forceinline__ void lds8(uint32_t a, float (&v)[8]) {
+  lds4(a, v[0], v[1], v[2], v[3]);
+  lds4(a + 16, v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void ldsc8(uint32_t a, float (&v)[8]) {
+  ldsc4(a, v[0], v[1], v[2], v[3]);
+  ldsc4(a + 16, v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void sts8(uint32_t a, const float (&v)[8]) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+               : "memory");
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a + 16), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ uint32_t cl_map_s(uint32_t a, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+// Where a neighbour oct's rows are: kind 0 none, 1 this CTA's shared memory,
+// 2 another CTA's (rank r), 3 the global arrays (oct g).
+struct Nb {
+  int kind;
+  uint32_t off;  // byte offset of the oct's row in each shared array
+  unsigned r;
+  int g;
+};
+__device__ __forceinline__ Nb nb_of_global(const Res2Ctx &cx, int g) {
+  Nb n;
+  n.g = g;
+  n.r = 0;
+  n.off = 0;
+  if (g < 0) {
+    n.kind = 0;
+    return n;
+  }
+  const int r = g / cx.chunk, l = g - r * cx.chunk;
+  if (l >= cx.cap) {
+    n.kind = 3;
+    return n;
+  }
+  n.r = (unsigned)r;
+  n.off = (uint32_t)l * 32u;
+  n.kind = n.r == cx.cr ? 1 : 2;
+  return n;
+}
+__device__ __forceinline__ uint16_t code_of_global(const Res2Ctx &cx, int g) {
+  if (g < 0) return kCodeNone;
+  const int r = g / cx.chunk, l = g - r * cx.chunk;
+  return l >= cx.cap ? kCodeGlobal : (uint16_t)((r << 12) | l);
+}
+
+// The six neighbours of own oct o (local index l).
+__device__ __forceinline__ void res2_nbs(const Res2Ctx &cx, const SolveDev &sd, int o, int l, Nb (&nb)[6]) {
+  if (l < cx.cap) {
+    uint32_t c01, c23, c45, pad;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(c01), "=r"(c23), "=r"(c45), "=r"(pad)
+                 : "r"(cx.sC + (uint32_t)l * 16u));
+    const uint32_t w[3] = {c01, c23, c45};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const uint16_t c = (uint16_t)(w[d >> 1] >> (16 * (d & 1)));
+      Nb &n = nb[d];
+      n.g = -1;
+      n.r = 0;
+      n.off = 0;
+      if (c == kCodeNone) {
+        n.kind = 0;
+      } else if (c == kCodeGlobal) {
+        int g = __ldg(sd.nbr + 6 * o + d);
+        if (g >= 0 && !idx_ok(g, sd.n_oct)) g = -1;
+        n = nb_of_global(cx, g);
+      } else {
+        n.r = c >> 12;
+        n.off = (uint32_t)(c & 0xFFF) * 32u;
+        n.kind = n.r == cx.cr ? 1 : 2;
+      }
+    }
+  } else {
+    int g[6];
+    load_nbr6(sd.nbr, o, g);
+    check_nbr6(g, sd.n_oct);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = nb_of_global(cx, g[d]);
+  }
+}
+
+// The four cells of neighbour n that face this oct across axis A (NB: which
+// half), from the shared array at `arr` or the global array `garr`.
+template <int A, int NB>
+__device__ __forceinline__ void res2_face(const Nb &n, uint32_t arr, const float *garr, bool coherent,
+                                          float (&v)[8]) {
+  if (n.kind == 1) {
+    if (A != 2) lds8(arr + n.off, v);
+    else lds4(arr + n.off + 16 * NB, v[4 * NB], v[4 * NB + 1], v[4 * NB + 2], v[4 * NB + 3]);
+  } else if (n.kind == 2) {
+    const uint32_t a = cl_map_s(arr + n.off, n.r);
+    if (A != 2) ldsc8(a, v);
+    else ldsc4(a + 16 * NB, v[4 * NB], v[4 * NB + 1], v[4 * NB + 2], v[4 * NB + 3]);
+  } else {
+    if (coherent) ldc_face<A, NB>(garr + 8 * n.g, v);
+    else ld_face<A, NB>(garr + 8 * n.g, v);
+  }
+}
+
+// An own oct's row of a shared array, or of its global array beyond the capacity.
+__device__ __forceinline__ void res2_own(const Res2Ctx &cx, uint32_t arr, int l, const float *garr, int o,
+                                         bool coherent, float (&v)[8]) {
+  if (l < cx.cap) lds8(arr + (uint32_t)l * 32u, v);
+  else if (coherent) ldc8(garr + 8 * o, v);
+  else ld8_ro(garr + 8 * o, v);
+}
+__device__ __forceinline__ void res2_own_store(const Res2Ctx &cx, uint32_t arr, int l, float *garr, int o,
+                                               const float (&v)[8]) {
+  if (l < cx.cap) sts8(arr + (uint32_t)l * 32u, v);
+  else st8(garr + 8 * o, v);
+}
+
+template <int DIR>
+__device__ __forceinline__ void res2_op_face(const Res2Ctx &cx, const SolveDev &sd, const Nb &n, float h,
+                                             const float (&K)[8], float (&off)[8]) {
+  constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
+  if (n.kind == 0) return;
+  float Kn[8], Pn[8];
+  res2_face<A, NB>(n, cx.sK, (const float *)sd.KT, false, Kn);
+  res2_face<A, NB>(n, cx.sP, (const float *)sd.p0, true, Pn);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (((c >> A) & 1) != S) continue;
+    const int j = c ^ (1 << A);
+    const float C = (Kn[j] >= 0.f) ? h * (K[c] + Kn[j]) : 0.f;
+    off[c] += C * Pn[j];
+  }
+}
+
+// Step 2 on own oct o: q = D p - sum C p_nb; returns the oct's p.q.
+__device__ __forceinline__ float res2_op_oct(const Res2Ctx &cx, const SolveDev &sd, int o, float h) {
+  const int l = o - cx.lo;
+  float K[8], p[8], d[8];
+  res2_own(cx, cx.sK, l, (const float *)sd.KT, o, false, K);
+  res2_own(cx, cx.sP, l, (const float *)sd.p0, o, true, p);
+  ldc8((const float *)sd.dg + 8 * o, d);
+  Nb nb[6];
+  res2_nbs(cx, sd, o, l, nb);
+  float off[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) off[c] = 0.f;
+  in_oct_faces(K, p, h, off);
+  res2_op_face<0>(cx, sd, nb[0], h, K, off);
+  res2_op_face<1>(cx, sd, nb[1], h, K, off);
+  res2_op_face<2>(cx, sd, nb[2], h, K, off);
+  res2_op_face<3>(cx, sd, nb[3], h, K, off);
+  res2_op_face<4>(cx, sd, nb[4], h, K, off);
+  res2_op_face<5>(cx, sd, nb[5], h, K, off);
+  float local = 0.f, qv[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float q = d[c] * p[c] - off[c];
+    const bool leaf = K[c] >= 0.f;
+    if (leaf) local = fmaf(p[c], q, local);
+    qv[c] = leaf ? q : 0.f;
+  }
+  st8((float *)sd.q + 8 * o, qv);
+  return local;
+}
+
+// Step 2 on own oct o of the shared rows whose six neighbours are all in
+// shared memory (or the stand-in row): every face loads unconditionally, from
+// this CTA's rows (one CTA) or the owner's (a cluster).
+template <int DIR, bool kCluster>
+__device__ __forceinline__ void res2_fast_face(uint32_t aK, uint32_t aP, float h, const float (&K)[8], float (&off)[8]) {
+  constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
+  float Kn[8], Pn[8];
+  if (A != 2) {
+    if (kCluster) {
+      ldsc8(aK, Kn);
+      ldsc8(aP, Pn);
+    } else {
+      lds8(aK, Kn);
+      lds8(aP, Pn);
+    }
+  } else {
+    if (kCluster) {
+      ldsc4(aK + 16 * NB, Kn[4 * NB], Kn[4 * NB + 1], Kn[4 * NB + 2], Kn[4 * NB + 3]);
+      ldsc4(aP + 16 * NB, Pn[4 * NB], Pn[4 * NB + 1], Pn[4 * NB + 2], Pn[4 * NB + 3]);
+    } else {
+      lds4(aK + 16 * NB, Kn[4 * NB], Kn[4 * NB + 1], Kn[4 * NB + 2], Kn[4 * NB + 3]);
+      lds4(aP + 16 * NB, Pn[4 * NB], Pn[4 * NB + 1], Pn[4 * NB + 2], Pn[4 * NB + 3]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (((c >> A) & 1) != S) continue;
+    const int j = c ^ (1 << A);
+    const float C = (Kn[j] >= 0.f) ? h * (K[c] + Kn[j]) : 0.f;
+    off[c] += C * Pn[j];
+  }
+}
+
+template <bool kCluster>
+__device__ __forceinline__ float res2_op_oct_fast(const Res2Ctx &cx, const SolveDev &sd, int o, int l,
+                                                  const uint32_t (&w)[3], float h) {
+  float K[8], p[8], d[8];
+  lds8(cx.sK + (uint32_t)l * 32u, K);
+  lds8(cx.sP + (uint32_t)l * 32u, p);
+  ldc8((const float *)sd.dg + 8 * o, d);
+  uint32_t aK[6], aP[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
+    const uint32_t off = (c & 0xFFFu) * 32u;
+    if (kCluster) {
+      aK[k] = cl_map_s(cx.sK + off, c >> 12);
+      aP[k] = cl_map_s(cx.sP + off, c >> 12);
+    } else {
+      aK[k] = cx.sK + off;
+      aP[k] = cx.sP + off;
+    }
+  }
+  float off[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) off[c] = 0.f;
+  in_oct_faces(K, p, h, off);
+  res2_fast_face<0, kCluster>(aK[0], aP[0], h, K, off);
+  res2_fast_face<1, kCluster>(aK[1], aP[1], h, K, off);
+  res2_fast_face<2, kCluster>(aK[2], aP[2], h, K, off);
+  res2_fast_face<3, kCluster>(aK[3], aP[3], h, K, off);
+  res2_fast_face<4, kCluster>(aK[4], aP[4], h, K, off);
+  res2_fast_face<5, kCluster>(aK[5], aP[5], h, K, off);
+  float local = 0.f, qv[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float q = d[c] * p[c] - off[c];
+    const bool leaf = K[c] >= 0.f;
+    if (leaf) local = fmaf(p[c], q, local);
+    qv[c] = leaf ? q : 0.f;
+  }
+  st8((float *)sd.q + 8 * o, qv);
+  return local;
+}
+
+// Step 2 on own oct o: the branch-free form when its row and every
+// neighbour's are in shared memory, else the general one.
+template <bool kCluster>
+__device__ __forceinline__ float res2_op_any(const Res2Ctx &cx, const SolveDev &sd, int o, float h) {
+  const int l = o - cx.lo;
+  if (l < cx.cap) {
+    uint32_t w0, w1, w2, pad;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(w0), "=r"(w1), "=r"(w2), "=r"(pad)
+                 : "r"(cx.sC + (uint32_t)l * 16u));
+    const uint32_t gl = 0xFFFEu;
+    const bool any_global = ((w0 & 0xFFFFu) == gl) | ((w0 >> 16) == gl) | ((w1 & 0xFFFFu) == gl) |
+                            ((w1 >> 16) == gl) | ((w2 & 0xFFFFu) == gl) | ((w2 >> 16) == gl);
+    if (!any_global) {
+      const uint32_t w[3] = {w0, w1, w2};
+      return res2_op_oct_fast<kCluster>(cx, sd, o, l, w, h);
+    }
+  }
+  return res2_op_oct(cx, sd, o, h);
+}
+
+// Step 1 on own oct o: p = z + beta p (first: p = z).
+__device__ __forceinline__ void res2_dir_oct(const Res2Ctx &cx, const SolveDev &sd, int o, bool first, float beta) {
+  const int l = o - cx.lo;
+  float z[8], p[8];
+  res2_own(cx, cx.sZ, l, (const float *)sd.z, o, true, z);
+  if (!first) res2_own(cx, cx.sP, l, (const float *)sd.p0, o, true, p);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) p[c] = first ? z[c] : fmaf(beta, p[c], z[c]);
+  res2_own_store(cx, cx.sP, l, (float *)sd.p0, o, p);
+}
+
+// Step 3 on own oct o: r = D z - alpha q, z = r / D, e += alpha p.
+__device__ __forceinline__ void res2_upd_oct(const Res2Ctx &cx, const SolveDev &sd, int o, float alpha, float &lrz,
+                                             float &lrr) {
+  const int l = o - cx.lo;
+  float p[8], z[8], d[8], q[8], e[8];
+  res2_own(cx, cx.sP, l, (const float *)sd.p0, o, true, p);
+  res2_own(cx, cx.sZ, l, (const float *)sd.z, o, true, z);
+  ldc8((const float *)sd.dg + 8 * o, d);
+  ldc8((const float *)sd.q + 8 * o, q);
+  ldc8((const float *)sd.e + 8 * o, e);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float r = d[c] * z[c] - alpha * q[c];
+    const float zn = r / d[c];
+    lrz = fmaf(r, zn, lrz);
+    lrr = fmaf(r, r, lrr);
+    z[c] = zn;
+    e[c] += alpha * p[c];
+  }
+  res2_own_store(cx, cx.sZ, l, (float *)sd.z, o, z);
+  st8((float *)sd.e + 8 * o, e);
+}
+
+// The FP64 residual pass on own oct o (global arrays; the neighbours' x read
+// coherently), z into its shared row, D into global memory.
+__device__ __forceinline__ void res2_ref_oct(const Res2Ctx &cx, const SolveDev &sd, int o, bool want_x, Acc<float> &rr,
+                                             Acc<float> &xx, Acc<float> &rz) {
+  float zo[8], dv[8];
+  ref_oct_values<float, true>(sd, o, want_x, rr, xx, rz, zo, dv);
+  res2_own_store(cx, cx.sZ, o - cx.lo, (float *)sd.z, o, zo);
+  st8((float *)sd.dg + 8 * o, dv);
+}
+
+// One solve by one group, the CG state of its first octs in shared memory.
+template <bool kCluster>
+__device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
+  constexpr int wd = (int)(sizeof(SolveDev) / 8);
+  for (int w = threadIdx.x; w < wd; w += blockDim.x)
+    reinterpret_cast<unsigned long long *>(&sh.sd)[w] = reinterpret_cast<const unsigned long long *>(a.solves + s)[w];
+  const unsigned cs = kCluster ? cl_size() : 1u, cr = kCluster ? cl_rank() : 0u;
+  if (threadIdx.x == 0) {
+    ResState z;
+    memset(&z, 0, sizeof(z));
+    z.phase = kRefine;
+    z.status = ATS_OK;
+    sh.st = z;
+    if (a.t_solve && cr == 0) a.t_solve[2 * s] = globaltimer_ns();
+  }
+  __syncthreads();
+  const SolveDev &sd = sh.sd;
+  const int n = sd.n_oct;
+  Res2Ctx cx;
+  cx.cap = a.cap;  // octs per CTA kept in shared memory (the dynamic allocation holds that many rows)
+  cx.chunk = (int)((n + (int)cs - 1) / (int)cs);
+  cx.lo = min(n, (int)cr * cx.chunk);
+  cx.cr = cr;
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(res2_smem);
+  const uint32_t rows = (uint32_t)cx.cap + 1u;  // row `cap` of K, z and p: the stand-in neighbour
+  cx.sK = base;
+  cx.sZ = base + rows * 32u;
+  cx.sP = base + 2u * rows * 32u;
+  cx.sC = base + 3u * rows * 32u;
+  const int hi = min(n, cx.lo + cx.chunk);
+  const int o0 = cx.lo + (int)threadIdx.x, stride = (int)blockDim.x;
+  // stage in: K and the neighbour codes of the octs kept in shared memory
+  // (read by other CTAs only after the first sum's cluster barrier), and the
+  // stand-in row a face without a neighbour points to
+  if (threadIdx.x == 0) {
+    float m1[8], z0[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      m1[c] = -1.f;
+      z0[c] = 0.f;
+    }
+    sts8(cx.sK + (uint32_t)cx.cap * 32u, m1);
+    sts8(cx.sZ + (uint32_t)cx.cap * 32u, z0);
+    sts8(cx.sP + (uint32_t)cx.cap * 32u, z0);
+  }
+  const uint16_t code_none = (uint16_t)((cr << 12) | (unsigned)cx.cap);
+  for (int o = o0; o < hi && o - cx.lo < cx.cap; o += stride) {
+    const int l = o - cx.lo;
+    float K[8];
+    ld8_ro((const float *)sd.KT + 8 * o, K);
+    sts8(cx.sK + (uint32_t)l * 32u, K);
+    int g[6];
+    load_nbr6(sd.nbr, o, g);
+    check_nbr6(g, sd.n_oct);
+    uint16_t c[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      c[d] = code_of_global(cx, g[d]);
+      if (c[d] == kCodeNone) c[d] = code_none;
+    }
+    const uint32_t w0 = c[0] | ((uint32_t)c[1] << 16), w1 = c[2] | ((uint32_t)c[3] << 16),
+                   w2 = c[4] | ((uint32_t)c[5] << 16);
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(cx.sC + (uint32_t)l * 16u), "r"(w0), "r"(w1),
+                 "r"(w2), "r"(0u)
+                 : "memory");
+  }
+  const float h = (float)sd.h;
+  const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
+  const bool fp32s = a.fp32_scalars != 0;
+  for (;;) {
+    const int phase = sh.st.phase;
+    if (phase == kDone) break;
+    if (phase == kRefine) {
+      Acc<float> acc[3], tot[3];
+      for (int o = o0; o < hi; o += stride) res2_ref_oct(cx, sd, o, want_x, acc[0], acc[1], acc[2]);
+      group_sum<float, 3, kCluster>(acc, sh, buf, tot);
+      if (threadIdx.x == 0) {
+        ResState &st = sh.st;
+        const double rnorm = sqrt(tot[0].get()), xnorm = sqrt(tot[1].get()), rz = tot[2].get();
+        if (st.refines == 0) st.r0 = rnorm;
+        st.refines += 1;
+        st.rnorm = rnorm;
+        st.xnorm = xnorm;
+        const double target = sd.tol * (sd.stop_rule == ATS_STOP_CERTIFIED ? xnorm : st.r0);
+        if (st.final_pass) {
+          st.phase = kDone;
+        } else if (!isfinite(rnorm)) {
+          st.status = ATS_ERR_BREAKDOWN;
+          st.phase = kDone;
+        } else if (rnorm <= target) {
+          st.phase = kDone;
+        } else if (st.refines > sd.max_refine) {
+          st.status = ATS_ERR_NOT_CONVERGED;
+          st.phase = kDone;
+        } else if (!(rz > 0.0)) {
+          st.status = ATS_ERR_BREAKDOWN;
+          st.phase = kDone;
+        } else {
+          st.phase = kInner;
+          st.rz = rz;
+          st.first = 1;
+          st.inner_iters = 0;
+          st.inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    // step 1: the new direction on the own octs, then every CTA waits
+    {
+      const bool first = sh.st.first != 0;
+      const float beta = (float)sh.st.beta;
+      for (int o = o0; o < hi; o += stride) res2_dir_oct(cx, sd, o, first, beta);
+      group_barrier<kCluster>();
+    }
+    // step 2: q = (I + dt A) p, sum p.q
+    {
+      Acc<float> acc[1], tot[1];
+      for (int o = o0; o < hi; o += stride) acc[0].add_value(res2_op_any<kCluster>(cx, sd, o, h));
+      group_sum<float, 1, kCluster>(acc, sh, buf, tot);
+      if (threadIdx.x == 0) {
+        ResState &st = sh.st;
+        const double pq = tot[0].get();
+        st.n_op += 1;
+        st.n_first += st.first ? 1 : 0;
+        if (!(st.rz >= 0.0) || !isfinite(st.rz) || !(pq > 0.0) || !isfinite(pq)) {
+          st.status = ATS_ERR_BREAKDOWN;
+          st.phase = kDone;
+        } else {
+          st.alpha = cg_ratio(st.rz, pq, fp32s);
+        }
+      }
+      __syncthreads();
+    }
+    if (sh.st.phase == kDone) break;
+    // step 3: e += alpha p, r = D z - alpha q, z = D^-1 r; sums r.z, r.r
+    {
+      const float alpha = (float)sh.st.alpha;
+      Acc<float> acc[2], tot[2];
+      for (int o = o0; o < hi; o += stride) {
+        float lrz = 0.f, lrr = 0.f;
+        res2_upd_oct(cx, sd, o, alpha, lrz, lrr);
+        acc[0].add_value(lrz);
+        acc[1].add_value(lrr);
+      }
+      group_sum<float, 2, kCluster>(acc, sh, buf, tot);
+      if (threadIdx.x == 0) {
+        ResState &st = sh.st;
+        const double rz_new = tot[0].get(), rr = tot[1].get();
+        st.iters += 1;
+        st.inner_iters += 1;
+        st.first = 0;
+        st.beta = cg_ratio(rz_new, st.rz, fp32s);
+        st.rz = rz_new;
+        const bool conv = rr <= st.inner_target * st.inner_target || rz_new == 0.0;
+        if (conv) {
+          st.phase = kRefine;
+        } else if (st.iters >= sd.max_iter) {
+          st.status = ATS_ERR_NOT_CONVERGED;
+          st.final_pass = 1;
+          st.phase = kRefine;
+        } else if (st.inner_iters >= sd.inner_max) {
+          st.phase = kRefine;
+        }
+        if (st.phase == kRefine) st.n_xpe += 1;
+      }
+      __syncthreads();
+    }
+    if (sh.st.phase == kRefine) {
+      for (int o = o0; o < hi; o += stride) res_xpe_oct<float>(sd, o);
+      group_barrier<kCluster>();
+    }
+  }
+  if (threadIdx.x == 0 && cr == 0) {
+    const ResState &st = sh.st;
+    SolveScalars f;
+    memset(&f, 0, sizeof(f));
+    f.phase = kDone;
+    f.iters = st.iters;
+    f.inner_iters = st.inner_iters;
+    f.refines = st.refines;
+    f.status = st.status;
+    f.final_pass = st.final_pass;
+    f.ticks = st.n_op + st.iters + st.refines;
+    f.rz = st.rz;
+    f.r0 = st.r0;
+    f.inner_target = st.inner_target;
+    f.rnorm = st.rnorm;
+    f.xnorm = st.xnorm;
+    a.final_sc[s] = f;
+    if (a.t_solve) a.t_solve[2 * s + 1] = globaltimer_ns();
+    if (a.cells) {
+      const unsigned long long N = 8ull * (unsigned long long)n;
+      atomicAdd(a.cells + 0, N * (unsigned long long)(st.n_op - st.n_first));
+      atomicAdd(a.cells + 4, N * (unsigned long long)st.n_first);
+      atomicAdd(a.cells + 1, N * (unsigned long long)st.refines);
+      atomicAdd(a.cells + 2, N * (unsigned long long)st.iters);
+      atomicAdd(a.cells + 3, N * (unsigned long long)st.n_xpe);
+    }
+  }
+}
+
+__device__ void res2_cta_loop(const ResArgs &a, ResShared<float> &sh, int &buf) {
+  for (;;) {
+    __syncthreads();  // every thread has read the previous task and left the previous solve
+    if (threadIdx.x == 0) sh.task = atomicAdd(a.heads + 1, 1);
+    __syncthreads();
+    const int t = sh.task;
+    if (t >= a.n_tq) break;
+    int s = a.queue[a.n_cq + t];
+    if (!idx_ok(s, a.n_solves)) continue;
+    res2_solve<false>(a, s, sh, buf);
+  }
+}
+
+}  // namespace
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_res2_cluster(ResArgs a) {
+  __shared__ ResShared<float> sh;
+  int buf = 0;
+  const unsigned cr = cl_rank(), cs = cl_size();
+  for (;;) {
+    if (cr == 0 && threadIdx.x == 0) {
+      const int t = atomicAdd(a.heads, 1);
+      for (unsigned r = 0; r < cs; ++r) cl_st(cl_map(&sh.task, r), t);
+    }
+    cl_sync();
+    const int t = sh.task;
+    if (t >= a.n_cq) break;
+    const int s = a.queue[t];
+    if (idx_ok(s, a.n_solves)) res2_solve<true>(a, s, sh, buf);
+    cl_sync();  // every CTA is done with the shared rows before the next stage-in rewrites them
+  }
+  res2_cta_loop(a, sh, buf);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_res2_cta(ResArgs a) {
+  __shared__ ResShared<float> sh;
+  int buf = 0;
+  res2_cta_loop(a, sh, buf);
+}
+
 template <typename T, int NT>
 static cudaError_t res_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st) {
   if (a.n_cq > 0) {
@@ -2038,6 +2665,95 @@ static int res_cta_blocks_t() {
     return 0;
   }
   return b;
+}
+
+template <int NT>
+static cudaError_t res2_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
+  const size_t smem = res2_smem_bytes(a.cap);
+  if (a.n_cq > 0 && !cta_only) {
+    cudaError_t e = cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && cluster > 8)
+      e = cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_res2_cluster<NT>, a);
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_res2_cta<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_res2_cta<NT><<<grid, NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NT>
+static int res2_clusters_t(int cluster, int cap) {
+  const size_t smem = res2_smem_bytes(cap);
+  if (cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      (cluster > 8 &&
+       cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(cluster * 64));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_res2_cluster<NT>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// The largest capacity (octs per CTA, at most 4093) whose rows fit the
+// shared memory a CTA can have beside the kernels' static shared memory.
+template <int NT>
+static int res2_cap_t(int device) {
+  int optin = 0;
+  cudaFuncAttributes fa, fb;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_res2_cluster<NT>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fb, k_res2_cta<NT>) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes) + res2_smem_bytes(0);
+  if ((size_t)optin <= stat) return 0;
+  return (int)std::min<size_t>(4093, ((size_t)optin - stat) / kRes2OctBytes);
+}
+
+cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
+  if (a.n_cq + a.n_tq <= 0) return cudaSuccess;
+  if (cluster < 1 || cluster > kMaxCluster || grid <= 0 || a.cap <= 0 || a.cap > 4093) return cudaErrorInvalidValue;
+  return threads >= 512 ? res2_launch_t<512>(cluster, grid, a, st, cta_only)
+                        : res2_launch_t<256>(cluster, grid, a, st, cta_only);
+}
+
+int resident_smem_clusters(int threads, int cluster, int cap) {
+  if (cluster < 1 || cluster > kMaxCluster || cap <= 0) return 0;
+  return threads >= 512 ? res2_clusters_t<512>(cluster, cap) : res2_clusters_t<256>(cluster, cap);
+}
+
+int resident_smem_cap(int threads, int device) {
+  return threads >= 512 ? res2_cap_t<512>(device) : res2_cap_t<256>(device);
 }
 
 cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st) {

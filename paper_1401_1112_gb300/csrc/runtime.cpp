@@ -228,6 +228,9 @@ struct Plan {
   std::vector<int8_t> mode;
   int n_cq = 0, n_tq = 0, n_tick = 0, n_tick_items = 0;
   int res_threads = 512, res_cluster = 8, res_grid = 0;
+  bool res_smem = false;  // K, z, p of each CTA's octs in shared memory (FP32 bulk)
+  int res_cap = 0;        // octs per CTA kept in shared memory
+  int res_fill = 0;       // single CTAs launched beside the clusters on the SMs they leave
   int32_t *d_queue = nullptr;   // [n_cq + n_tq]
   int *d_heads = nullptr;       // [2] next position of each queue
   cudaEvent_t res_ev[2] = {nullptr, nullptr};
@@ -280,6 +283,7 @@ void fill_defaults(ats_solve_opts *o) {
   o->res_cta_octs = 0;
   o->res_max_octs = 0;
   o->fp32_scalars = 0;
+  o->res_state = 0;
 }
 
 ats_solve_opts normalize(const ats_solve_opts *in) {
@@ -439,8 +443,9 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     return ATS_ERR_INVALID_ARG;
   }
   if (o.sched < ATS_SCHED_AUTO || o.sched > ATS_SCHED_RESIDENT || (o.res_threads != 0 && o.res_threads != 256 &&
-      o.res_threads != 512) || o.res_cluster < 0 || o.res_cluster > 16 || o.res_max_octs < 0) {
-    set_error("bad resident-solver options (sched 0..2, res_threads 0/256/512, res_cluster 0..16)");
+      o.res_threads != 512) || o.res_cluster < 0 || o.res_cluster > 16 || o.res_max_octs < 0 || o.res_state < 0 ||
+      o.res_state > 1) {
+    set_error("bad resident-solver options (sched 0..2, res_threads 0/256/512, res_cluster 0..16, res_state 0/1)");
     return ATS_ERR_INVALID_ARG;
   }
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -526,8 +531,18 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   {
     const bool res_ok = o.sched != ATS_SCHED_TICK && o.stop_rule != ATS_STOP_PAPER;
     const int64_t cta_octs = o.res_cta_octs == 0 ? 2048 : o.res_cta_octs;
-    const int64_t max_octs = o.sched == ATS_SCHED_RESIDENT ? INT64_MAX : (o.res_max_octs > 0 ? o.res_max_octs : 4096);
+    // default limit: mixed precision 16384 octs (the shared-memory form
+    // beats a whole-GPU tick loop up to about there for one solve alone);
+    // FP64 (the global-memory form) 2048
+    const int64_t max_octs = o.sched == ATS_SCHED_RESIDENT
+                                 ? INT64_MAX
+                                 : (o.res_max_octs > 0 ? o.res_max_octs : (P->fp64 ? 2048 : 16384));
     int clusters = 0;
+    P->res_smem = !P->fp64 && o.res_state == 0;
+    if (P->res_smem) {
+      P->res_cap = resident_smem_cap(P->res_threads, ctx->device);
+      if (P->res_cap <= 0) P->res_smem = false;
+    }
     P->mode.assign(n, 0);
     for (int k = 0; k < n; ++k) {
       const int64_t no = P->levels[k]->n_oct;
@@ -536,7 +551,8 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     }
     for (int k = 0; k < n; ++k) P->n_cq += P->mode[k] == 1;
     if (P->n_cq > 0) {
-      clusters = resident_max_clusters(P->fp64, P->res_threads, P->res_cluster);
+      clusters = P->res_smem ? resident_smem_clusters(P->res_threads, P->res_cluster, P->res_cap)
+                             : resident_max_clusters(P->fp64, P->res_threads, P->res_cluster);
       if (clusters <= 0) {  // no cluster of that shape fits this device: those levels take the tick path
         for (int k = 0; k < n; ++k)
           if (P->mode[k] == 1) P->mode[k] = 0;
@@ -548,7 +564,11 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       P->n_tick += P->mode[k] == 0;
     }
     P->res_grid = P->n_cq > 0 ? clusters * P->res_cluster
-                              : std::max(1, resident_cta_blocks(P->fp64, P->res_threads)) * ctx->num_sms;
+                              : (P->res_smem ? 1 : std::max(1, resident_cta_blocks(P->fp64, P->res_threads))) *
+                                    ctx->num_sms;
+    // clusters pack into the GPCs with some SMs left over: single CTAs take
+    // small solves there, launched beside the clusters (one CTA per SM)
+    if (P->res_smem && P->n_cq > 0 && P->n_tq > 0) P->res_fill = std::max(0, ctx->num_sms - P->res_grid);
   }
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
   P->grid = std::max(1, std::min(P->n_items, bps * ctx->num_sms));
@@ -652,9 +672,21 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   }
   if (prof) CUDA_TRY(cudaMemsetAsync(P->d_tsolve, 0, 2 * sizeof(unsigned long long) * P->n, st));
   ra.t_solve = prof ? P->d_tsolve : nullptr;
+  ra.cap = P->res_cap;
   CUDA_TRY(cudaMemsetAsync(P->d_heads, 0, 2 * sizeof(int), st));
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[0], st));
-  CUDA_TRY(launch_resident(P->fp64, P->res_threads, P->res_cluster, P->res_grid, ra, st));
+  // the SMs no cluster fits on take small solves beside the cluster launch
+  const int fill = P->res_fill;
+  if (fill > 0) CUDA_TRY(cudaEventRecord(P->fj.fork, st));
+  if (P->res_smem) CUDA_TRY(launch_resident_smem(P->res_threads, P->res_cluster, P->res_grid, ra, st));
+  else CUDA_TRY(launch_resident(P->fp64, P->res_threads, P->res_cluster, P->res_grid, ra, st));
+  if (fill > 0) {
+    CUDA_TRY(cudaStreamWaitEvent(P->fj.aux, P->fj.fork, 0));
+    CUDA_TRY(launch_resident_smem(P->res_threads, P->res_cluster, fill, ra, P->fj.aux, true));
+    CUDA_TRY(cudaEventRecord(P->fj.join, P->fj.aux));
+    CUDA_TRY(cudaStreamWaitEvent(st, P->fj.join, 0));
+    P->res_launches += 1;
+  }
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[1], st));
   P->res_launches += 1;
   return ATS_OK;
@@ -1055,7 +1087,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
       }
       P->res_span_ms = t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
       P->res_longest_ms = longest;
-      P->res_occupancy = P->res_span_ms > 0 ? busy / (P->res_span_ms * P->res_grid) : 0.0;
+      P->res_occupancy = P->res_span_ms > 0 ? busy / (P->res_span_ms * (P->res_grid + P->res_fill)) : 0.0;
     }
   }
   ats_status first_err = ATS_OK, first_warn = ATS_OK;
@@ -2030,6 +2062,7 @@ ats_status ats_batch_autotune(ats_batch *B, double *const *x_inout, const int *t
     };
     ats_tune_result res;
     std::memset(&res, 0, sizeof(res));
+    res.chosen = base;
     s = ATS_OK;
     const bool was_profiling = P->profiling;
     P->profiling = false;
@@ -2038,32 +2071,63 @@ ats_status ats_batch_autotune(ats_batch *B, double *const *x_inout, const int *t
       res.check_every = base.check_every;
       res.ms = res.ms_default;
       res.candidates = 1;
-      for (int i = 0; i < n_tiles && s == ATS_OK; ++i) {
-        for (int j = 0; j < n_checks && s == ATS_OK; ++j) {
-          ats_solve_opts o = base;
-          o.tile_octs = tiles[i];
-          o.check_every = checks[j];
-          if (o.tile_octs == base.tile_octs && normalize(&o).check_every == base.check_every) continue;
-          Plan *Q = nullptr;
-          if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) != ATS_OK) break;
-          double ms = 0.0;
-          s = time_plan(Q, &ms);
-          plan_free(Q);
-          if (s != ATS_OK) break;
-          ++res.candidates;
-          if (ms < res.ms) {
-            res.ms = ms;
-            res.tile_octs = o.tile_octs;
-            res.check_every = normalize(&o).check_every;
+      res.res_threads = P->res_threads;
+      res.res_cluster = P->res_cluster;
+      res.res_cta_octs = base.res_cta_octs;
+      // the candidates: work-item size x poll interval for the tick-path
+      // solves, CTA threads x cluster size x one-CTA limit for the resident
+      // ones, each with the batch's other options
+      std::vector<ats_solve_opts> cands;
+      if (P->n_tick > 0) {
+        for (int i = 0; i < n_tiles; ++i)
+          for (int j = 0; j < n_checks; ++j) {
+            ats_solve_opts o = base;
+            o.tile_octs = tiles[i];
+            o.check_every = checks[j];
+            if (o.tile_octs == base.tile_octs && normalize(&o).check_every == base.check_every) continue;
+            cands.push_back(o);
           }
+      }
+      if (P->n_cq + P->n_tq > 0) {
+        static const int kThr[] = {256, 512}, kCl[] = {8, 16}, kCta[] = {1024, 2048};
+        for (int th : kThr)
+          for (int cl : kCl)
+            for (int ct : kCta) {
+              ats_solve_opts o = base;
+              o.res_threads = th;
+              o.res_cluster = cl;
+              o.res_cta_octs = ct;
+              if (th == P->res_threads && cl == P->res_cluster && ct == (base.res_cta_octs ? base.res_cta_octs : 2048))
+                continue;
+              cands.push_back(o);
+            }
+      }
+      ats_solve_opts best = base;
+      for (size_t i = 0; i < cands.size() && s == ATS_OK; ++i) {
+        const ats_solve_opts &o = cands[i];
+        Plan *Q = nullptr;
+        if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) != ATS_OK) break;
+        double ms = 0.0;
+        s = time_plan(Q, &ms);
+        const int qth = Q->res_threads, qcl = Q->res_cluster;
+        plan_free(Q);
+        if (s != ATS_OK) break;
+        ++res.candidates;
+        if (ms < res.ms) {
+          res.ms = ms;
+          best = o;
+          res.tile_octs = o.tile_octs;
+          res.check_every = normalize(&o).check_every;
+          res.res_threads = qth;
+          res.res_cluster = qcl;
+          res.res_cta_octs = o.res_cta_octs;
         }
       }
+      res.chosen = best;
     }
     // the batch keeps the fastest configuration, and x_inout holds its solution
-    if (s == ATS_OK && (res.tile_octs != base.tile_octs || res.check_every != base.check_every)) {
-      ats_solve_opts o = base;
-      o.tile_octs = res.tile_octs;
-      o.check_every = res.check_every;
+    if (s == ATS_OK && std::memcmp(&res.chosen, &base, sizeof(base)) != 0) {
+      ats_solve_opts o = res.chosen;
       Plan *Q = nullptr;
       if ((s = plan_create(ctx, P->levels.data(), n, &o, &Q)) == ATS_OK) {
         plan_free(P);
@@ -2105,7 +2169,7 @@ ats_status ats_batch_kernel_stats(const ats_batch *B, ats_kernel_stats *out) {
     out->res_longest_ms = P->res_longest_ms;
     out->res_occupancy = P->res_occupancy;
     out->res_longest = P->res_longest;
-    out->res_grid = P->res_grid;
+    out->res_grid = P->res_grid + P->res_fill;
     return ATS_OK;
   } catch (...) {
     return ats::abi_exception();

@@ -66,7 +66,17 @@ SHAPES = [(1 << 30, 1, 512), (-1, 1, 256), (-1, 2, 512), (-1, 4, 256), (-1, 8, 5
           (-1, 16, 512)]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+PRECS = ["fp64", "mixed-shared", "mixed-global"]
+
+
+def _popts(ats, name):
+    """precision and where the mixed path keeps its CG state"""
+    if name == "fp64":
+        return dict(precision=ats.ATS_PREC_FP64)
+    return dict(precision=ats.ATS_PREC_MIXED, res_state=0 if name == "mixed-shared" else 1)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"cta{s[0] > 0}-c{s[1]}-t{s[2]}")
 @pytest.mark.parametrize("seed", [11, 12])
 def test_irregular_levels_every_shape(ats, ctx, prec, shape, seed):
@@ -81,8 +91,8 @@ def test_irregular_levels_every_shape(ats, ctx, prec, shape, seed):
     L.build(st.dt, st.K, st.E, s=st.s, src=st.src, **_faces(st))
     cta, cl, th = shape
     x = st.E.copy()
-    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=_prec(ats, prec),
-                          sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=cta, res_cluster=cl, res_threads=th)
+    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, sched=ats.ATS_SCHED_RESIDENT,
+                          res_cta_octs=cta, res_cluster=cl, res_threads=th, **_popts(ats, prec))
     assert code == 0, stats
     assert stats["err_bound"] <= TOL
     assert _rel(x, xr) <= PAR
@@ -91,7 +101,7 @@ def test_irregular_levels_every_shape(ats, ctx, prec, shape, seed):
     L.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 37), (33, 1, 1), (3, 5, 7), (17, 9, 5)])
 def test_ragged_shapes_one_cta_and_cluster(ats, ctx, prec, dims):
     """One oct, strips, and oct counts that leave CTAs of a cluster empty or
@@ -108,17 +118,19 @@ def test_ragged_shapes_one_cta_and_cluster(ats, ctx, prec, dims):
     L.build(st.dt, st.K, st.E, **_faces(st))
     for cta, cl in ((1 << 30, 8), (-1, 8), (-1, 16)):
         x = st.E.copy()
-        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=_prec(ats, prec),
-                              sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=cta, res_cluster=cl)
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, sched=ats.ATS_SCHED_RESIDENT,
+                              res_cta_octs=cta, res_cluster=cl, **_popts(ats, prec))
         assert code == 0, stats
         assert _rel(x, xr) <= PAR
     L.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_many_octs_per_thread(ats, ctx, prec):
     """A 32 x 32 x 24-oct level (24 576 octs): 6 to 12 octs per thread on one
-    cluster, 48 to 96 on one CTA."""
+    cluster, 48 to 96 on one CTA; with the state in shared memory, more octs
+    per CTA than its capacity, so the octs beyond it (and the faces they
+    share) run from the global arrays."""
     rng = np.random.default_rng(321)
     lv = W.box_level(32, 32, 24, 1.0 / 64, [(W.DIRICHLET, 1.0), (W.NEUMANN, 0.0), (W.ROBIN, 0.5),
                                             (W.DIRICHLET, 1.0), None, (W.ROBIN, 0.9)])
@@ -131,14 +143,35 @@ def test_many_octs_per_thread(ats, ctx, prec):
     L.build(st.dt, st.K, st.E, **_faces(st))
     for cta, cl, th in ((-1, 8, 512), (-1, 4, 256), (1 << 30, 1, 512)):
         x = st.E.copy()
-        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=_prec(ats, prec),
-                              sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=cta, res_cluster=cl, res_threads=th)
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, sched=ats.ATS_SCHED_RESIDENT,
+                              res_cta_octs=cta, res_cluster=cl, res_threads=th, **_popts(ats, prec))
         assert code == 0, stats
         assert _rel(x, xr) <= PAR
     L.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_state_in_shared_or_global_memory_same_bits(ats, ctx):
+    """Where a CTA keeps K, z and p (shared memory, or the global arrays) does
+    not enter the arithmetic: both forms give bitwise the same result, in
+    one-CTA and cluster solves, within and beyond the shared capacity."""
+    rng = np.random.default_rng(4040)
+    for o, cta, cl in ((300, 1 << 30, 1), (5000, -1, 8), (24000, -1, 4), (24000, 1 << 30, 1)):
+        lv, st = W.random_box_solve(rng, o, robin=True)
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        res = []
+        for rs in (0, 1):
+            x = st.E.copy()
+            code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                                  sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=cta, res_cluster=cl, res_state=rs)
+            assert code == 0, stats
+            res.append((x, stats["iterations"]))
+        np.testing.assert_array_equal(res[0][0], res[1][0])
+        assert res[0][1] == res[1][1]
+        L.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_batch_alone_and_in_batch_bitwise(ats, ctx, prec):
     """A ragged batch spanning one-CTA and cluster solves: every solve matches
     the oracle; each result is bitwise the same alone and in the batch, and
@@ -146,13 +179,12 @@ def test_batch_alone_and_in_batch_bitwise(ats, ctx, prec):
     enter its arithmetic)."""
     rng = np.random.default_rng(2077)
     solves = [W.random_box_solve(rng, o, robin=True) for o in (1, 9, 130, 700, 2100, 4500, 12000, 3, 60)]
-    P = _prec(ats, prec)
     levels = []
     for lv, st in solves:
         L = ats.Level(ctx, lv)
         L.build(st.dt, st.K, st.E, **_faces(st))
         levels.append(L)
-    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P)
+    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, sched=ats.ATS_SCHED_RESIDENT, **_popts(ats, prec))
     B = ats.Batch(ctx, levels, **opts)
     assert B.kernel_stats()["res_solves"] == len(solves)
     xs = [st.E.copy() for _, st in solves]
@@ -248,4 +280,39 @@ def test_tick_and_resident_agree(ats, ctx):
                                   sched=sched)
             assert code == 0, stats
             assert _rel(x, xr) <= PAR
+        L.close()
+
+
+def test_autotune_resident_shapes(ats, ctx):
+    """The autotuner times the resident shapes (threads per CTA x cluster
+    size x one-CTA limit) on a resident batch, keeps the fastest, and leaves
+    a solution: each solve matches the oracle, and later solves are bitwise
+    those of a batch created with the chosen options."""
+    rng = np.random.default_rng(919)
+    solves = [W.random_box_solve(rng, o, robin=True) for o in (3, 90, 1500, 3000, 9000)]
+    levels = []
+    for lv, st in solves:
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        levels.append(L)
+    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, sched=ats.ATS_SCHED_RESIDENT)
+    B = ats.Batch(ctx, levels, **opts)
+    xs = [st.E.copy() for _, st in solves]
+    r = B.autotune(xs, reps=1)
+    assert r["candidates"] == 8  # the batch's own shape and the seven others
+    assert r["res_threads"] in (256, 512) and r["res_cluster"] in (8, 16) and r["res_cta_octs"] in (0, 1024, 2048)
+    assert 0.0 < r["ms"] <= r["ms_default"]
+    for (lv, st), x in zip(solves, xs):
+        assert _rel(x, _oracle_x(lv, st)) <= PAR
+    xs2 = [st.E.copy() for _, st in solves]
+    assert B.solve(xs2)[0] == 0
+    B.close()
+    B3 = ats.Batch(ctx, levels, res_threads=r["chosen"]["res_threads"], res_cluster=r["chosen"]["res_cluster"],
+                   res_cta_octs=r["chosen"]["res_cta_octs"], **opts)
+    xs3 = [st.E.copy() for _, st in solves]
+    assert B3.solve(xs3)[0] == 0
+    for a, b in zip(xs2, xs3):
+        np.testing.assert_array_equal(a, b)
+    B3.close()
+    for L in levels:
         L.close()
