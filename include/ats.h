@@ -150,7 +150,7 @@ typedef struct {
   int res_threads;   /* resident solver: threads per CTA, 256 or 512          */
                      /* (0 = 512 for ATS_PREC_MIXED, 256 for ATS_PREC_FP64)   */
   int res_cluster;   /* resident solver: CTAs per thread-block cluster, 1..16 */
-                     /* (0 = 8)                                              */
+                     /* (0 = 4)                                              */
   int res_cta_octs;  /* resident solver: a level of at most this many octs is */
                      /* solved by one CTA alone (0 = 2048, < 0 = never)      */
   int res_max_octs;  /* ATS_SCHED_AUTO: levels above this many octs take the  */
@@ -164,6 +164,13 @@ typedef struct {
                      /* (neighbours read from the owning CTA through          */
                      /* distributed shared memory; default), 1 = global      */
                      /* memory (L2).  The FP64 bulk always uses global.      */
+  int res_cluster_big; /* resident solver: CTAs per cluster for the levels    */
+                     /* whose estimated work exceeds res_big_work (0 = 16;  */
+                     /* < 0 = none: they take res_cluster)                  */
+  int res_big_work;  /* resident solver: a level of more than res_cta_octs   */
+                     /* octs takes the larger clusters when its estimated   */
+                     /* work n_oct min(sqrt(1 + 8 h), 4 n_oct^(1/3)), h =   */
+                     /* dt / (2 dx^2), exceeds this (0 = 80000)             */
 } ats_solve_opts;
 
 /* scheduling of a solve (ats_solve_opts.sched).  Which path a level takes
@@ -176,10 +183,14 @@ typedef struct {
  *   Resident solver: a solve runs from its first residual pass to its
  *   certificate inside one persistent launch, on one thread-block cluster of
  *   res_cluster CTAs (per-step sums exchanged through distributed shared
- *   memory, steps ordered by the hardware cluster barrier), or on one CTA when
- *   the level has at most res_cta_octs octs; clusters and CTAs take solves
- *   from work queues ordered by estimated work (largest first).  Not for the
- *   paper stopping rule (ATS_STOP_PAPER takes the tick path). */
+ *   memory, steps ordered by the hardware cluster barrier) of res_cluster
+ *   CTAs, or of res_cluster_big CTAs for a level whose estimated work
+ *   exceeds res_big_work, or on one CTA when the level has at most
+ *   res_cta_octs octs; clusters and CTAs take solves from work queues ordered
+ *   by estimated work (largest first); the two cluster sizes and the single
+ *   CTAs run as concurrent launches sharing the SMs in proportion to their
+ *   queues' estimated work.  Not for the paper stopping rule (ATS_STOP_PAPER
+ *   takes the tick path). */
 #define ATS_SCHED_AUTO 0     /* resident solver for levels up to res_max_octs octs */
 #define ATS_SCHED_TICK 1     /* the tick path for every level                    */
 #define ATS_SCHED_RESIDENT 2 /* the resident solver for every level              */
@@ -303,7 +314,10 @@ typedef struct {
   double res_longest_ms;     /* the longest resident solve                         */
   double res_occupancy;      /* CTA-time inside solves / (span x the launch's CTAs) */
   int res_longest;           /* index of the longest resident solve (-1: none)     */
-  int res_grid;              /* CTAs of the resident launch                        */
+  int res_grid;              /* CTAs of the resident launches                      */
+  double res_end_ms[3];      /* end of the last big-cluster / cluster / one-CTA    */
+                             /* solve, from the first resident solve's start       */
+  int res_grids[3];          /* CTAs of the big-cluster, cluster, one-CTA launches  */
 } ats_kernel_stats;
 ats_status ats_batch_set_profiling(ats_batch *batch, int on);
 ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out);
@@ -313,9 +327,11 @@ ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out)
  * operators for every candidate and keeps the fastest, together with the
  * options the batch was created with.  The candidates: for a batch with
  * tick-path solves, every pair (work-item size tile_octs, poll interval
- * check_every); for a batch with resident solves, every resident shape
- * (res_threads 256 / 512 x res_cluster 8 / 16 x res_cta_octs 1024 / 2048);
- * each varies those options only.  tiles[n_tiles]: octs per work item, 0 = the
+ * check_every); for a batch with resident solves, eight resident shapes
+ * (res_threads, res_cluster, res_cta_octs, res_cluster_big):
+ * (512, 4, 2048, 16) (512, 8, 2048, 16) (512, 8, 2048, none)
+ * (256, 4, 2048, 16) (512, 4, 1024, 16) (512, 2, 2048, 16) (512, 4, 2048, 8)
+ * (512, 16, 2048, none); each varies those options only.  tiles[n_tiles]: octs per work item, 0 = the
  * library's size rule (see ats_solve_opts.tile_octs), others
  * rounded up to a multiple of 32; NULL / 0 = {0, 128, 256, 384, 512}.
  * checks[n_checks]: ticks per CUDA graph and host poll; NULL / 0 = {8, 16,

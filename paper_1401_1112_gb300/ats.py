@@ -69,7 +69,8 @@ class ats_solve_opts(ctypes.Structure):
         ("tile_octs", ctypes.c_int), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
         ("mem", ctypes.c_int), ("x0", ctypes.c_int), ("sched", ctypes.c_int), ("res_threads", ctypes.c_int),
         ("res_cluster", ctypes.c_int), ("res_cta_octs", ctypes.c_int), ("res_max_octs", ctypes.c_int),
-        ("fp32_scalars", ctypes.c_int), ("res_state", ctypes.c_int),
+        ("fp32_scalars", ctypes.c_int), ("res_state", ctypes.c_int), ("res_cluster_big", ctypes.c_int),
+        ("res_big_work", ctypes.c_int),
     ]
 
 
@@ -89,7 +90,8 @@ class ats_kernel_stats(ctypes.Structure):
         ("launches", ctypes.c_int), ("ticks", ctypes.c_int), ("res_ms", ctypes.c_double),
         ("res_bytes", ctypes.c_double), ("res_launches", ctypes.c_int), ("res_solves", ctypes.c_int),
         ("res_span_ms", ctypes.c_double), ("res_longest_ms", ctypes.c_double), ("res_occupancy", ctypes.c_double),
-        ("res_longest", ctypes.c_int), ("res_grid", ctypes.c_int),
+        ("res_longest", ctypes.c_int), ("res_grid", ctypes.c_int), ("res_end_ms", ctypes.c_double * 3),
+        ("res_grids", ctypes.c_int * 3),
     ]
 
 
@@ -269,7 +271,7 @@ def _level_desc(level, keep):
 def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, max_iter=0, max_refine=0,
               inner_rtol=0.0, tile_octs=0, check_every=0, use_graph=0, mem=ATS_MEM_HOST,
               x0=ATS_X0_GIVEN, sched=ATS_SCHED_AUTO, res_threads=0, res_cluster=0, res_cta_octs=0,
-              res_max_octs=0, fp32_scalars=0, res_state=0) -> ats_solve_opts:
+              res_max_octs=0, fp32_scalars=0, res_state=0, res_cluster_big=0, res_big_work=0) -> ats_solve_opts:
     o = ats_solve_opts()
     lib().ats_default_opts(ctypes.byref(o))
     o.tol = tol
@@ -294,6 +296,8 @@ def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, m
     o.res_max_octs = res_max_octs
     o.fp32_scalars = fp32_scalars
     o.res_state = res_state
+    o.res_cluster_big = res_cluster_big
+    o.res_big_work = res_big_work
     return o
 
 
@@ -445,7 +449,11 @@ def ats_batch_set_profiling(batch, on: bool):
 def ats_batch_kernel_stats(batch):
     k = ats_kernel_stats()
     _check(lib().ats_batch_kernel_stats(batch, ctypes.byref(k)), "ats_batch_kernel_stats")
-    return {name: getattr(k, name) for name, _ in k._fields_}
+    out = {}
+    for name, _ in k._fields_:
+        v = getattr(k, name)
+        out[name] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 def ats_batch_autotune(batch, xs: Sequence, tiles: Sequence[int] = (), checks: Sequence[int] = (), reps: int = 2):

@@ -189,19 +189,22 @@ cudaError_t launch_tick(bool fp64, bool paper, const TickArgs &a, const int grid
 // register and shared-memory use, times the SM count), in launch_tick order.
 void tick_grids(bool fp64, bool paper, int device, int grids[3]);
 
-// Resident solver (kernels.cu): whole solves inside one launch.  Solves in
-// queue[0, n_cq) are taken by thread-block clusters, solves in
-// queue[n_cq, n_cq + n_tq) by single CTAs; heads[0] / heads[1] are the next
-// positions of the two queues (zero before the launch).  A finished solve
-// writes its state to final_sc.  With cells set, the cells processed per step
-// kind are added as the tick kernels count them (kCellCounters).
+// Resident solver (kernels.cu): whole solves inside one launch.  The
+// launch's clusters take the solves of cq[0, n_cq), then its CTAs take
+// single-CTA solves from tq[0, n_tq); *cq_head / *tq_head are the next
+// positions of the two queues (zero before the launch; several launches of a
+// plan share the CTA queue and its head).  A finished solve writes its state
+// to final_sc.  With cells set, the cells processed per step kind are added
+// as the tick kernels count them (kCellCounters).
 struct ResArgs {
   const SolveDev *solves;
   SolveScalars *final_sc;
-  const int32_t *queue;
+  const int32_t *cq;
+  const int32_t *tq;
   int n_cq, n_tq, n_solves;
   int fp32_scalars;  // 1: alpha and beta from the totals rounded to FP32 (mixed precision)
-  int *heads;
+  int *cq_head;
+  int *tq_head;
   unsigned long long *cells;
   unsigned long long *t_solve;  // [n_solves][2] %globaltimer at a solve's start and end (profiling), or null
   int cap;                      // shared-memory form: octs per CTA kept in shared memory
@@ -209,7 +212,8 @@ struct ResArgs {
 // One resident launch on st: clusters of `cluster` CTAs of `threads` threads
 // (256 or 512), `grid` CTAs in all (a multiple of `cluster`) when the cluster
 // queue is not empty, else `grid` single CTAs.
-cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st);
+cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st,
+                            bool cta_only = false);
 // Clusters of that shape resident at once on the current device (0: none).
 int resident_max_clusters(bool fp64, int threads, int cluster);
 // CTAs of the single-CTA kernel resident per SM.

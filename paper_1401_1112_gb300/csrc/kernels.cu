@@ -1956,11 +1956,11 @@ template <typename T>
 __device__ void res_cta_loop(const ResArgs &a, ResShared<T> &sh, int &buf) {
   for (;;) {
     __syncthreads();  // every thread has read the previous task
-    if (threadIdx.x == 0) sh.task = atomicAdd(a.heads + 1, 1);
+    if (threadIdx.x == 0) sh.task = atomicAdd(a.tq_head, 1);
     __syncthreads();
     const int t = sh.task;
     if (t >= a.n_tq) break;
-    int s = a.queue[a.n_cq + t];
+    int s = a.tq[t];
     if (!idx_ok(s, a.n_solves)) continue;
     res_solve<T, false>(a, s, sh, buf);
   }
@@ -1985,13 +1985,13 @@ __global__ void __launch_bounds__(NT, ResMinBlocks<T, NT>::value) k_res_cluster(
   const unsigned cr = cl_rank(), cs = cl_size();
   for (;;) {
     if (cr == 0 && threadIdx.x == 0) {
-      const int t = atomicAdd(a.heads, 1);
+      const int t = atomicAdd(a.cq_head, 1);
       for (unsigned r = 0; r < cs; ++r) cl_st(cl_map(&sh.task, r), t);
     }
     cl_sync();
     const int t = sh.task;
     if (t >= a.n_cq) break;
-    const int s = a.queue[t];
+    const int s = a.cq[t];
     if (idx_ok(s, a.n_solves)) res_solve<T, true>(a, s, sh, buf);
   }
   res_cta_loop<T>(a, sh, buf);
@@ -2568,11 +2568,11 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
 __device__ void res2_cta_loop(const ResArgs &a, ResShared<float> &sh, int &buf) {
   for (;;) {
     __syncthreads();  // every thread has read the previous task and left the previous solve
-    if (threadIdx.x == 0) sh.task = atomicAdd(a.heads + 1, 1);
+    if (threadIdx.x == 0) sh.task = atomicAdd(a.tq_head, 1);
     __syncthreads();
     const int t = sh.task;
     if (t >= a.n_tq) break;
-    int s = a.queue[a.n_cq + t];
+    int s = a.tq[t];
     if (!idx_ok(s, a.n_solves)) continue;
     res2_solve<false>(a, s, sh, buf);
   }
@@ -2587,13 +2587,13 @@ __global__ void __launch_bounds__(NT, 1) k_res2_cluster(ResArgs a) {
   const unsigned cr = cl_rank(), cs = cl_size();
   for (;;) {
     if (cr == 0 && threadIdx.x == 0) {
-      const int t = atomicAdd(a.heads, 1);
+      const int t = atomicAdd(a.cq_head, 1);
       for (unsigned r = 0; r < cs; ++r) cl_st(cl_map(&sh.task, r), t);
     }
     cl_sync();
     const int t = sh.task;
     if (t >= a.n_cq) break;
-    const int s = a.queue[t];
+    const int s = a.cq[t];
     if (idx_ok(s, a.n_solves)) res2_solve<true>(a, s, sh, buf);
     cl_sync();  // every CTA is done with the shared rows before the next stage-in rewrites them
   }
@@ -2608,8 +2608,8 @@ __global__ void __launch_bounds__(NT, 1) k_res2_cta(ResArgs a) {
 }
 
 template <typename T, int NT>
-static cudaError_t res_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st) {
-  if (a.n_cq > 0) {
+static cudaError_t res_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
+  if (a.n_cq > 0 && !cta_only) {
     if (cluster > 8) {
       cudaError_t e = cudaFuncSetAttribute(k_res_cluster<T, NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
@@ -2756,11 +2756,15 @@ int resident_smem_cap(int threads, int device) {
   return threads >= 512 ? res2_cap_t<512>(device) : res2_cap_t<256>(device);
 }
 
-cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st) {
+cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st,
+                            bool cta_only) {
   if (a.n_cq + a.n_tq <= 0) return cudaSuccess;
   if (cluster < 1 || cluster > kMaxCluster || grid <= 0) return cudaErrorInvalidValue;
-  if (fp64) return threads >= 512 ? res_launch_t<double, 512>(cluster, grid, a, st) : res_launch_t<double, 256>(cluster, grid, a, st);
-  return threads >= 512 ? res_launch_t<float, 512>(cluster, grid, a, st) : res_launch_t<float, 256>(cluster, grid, a, st);
+  if (fp64)
+    return threads >= 512 ? res_launch_t<double, 512>(cluster, grid, a, st, cta_only)
+                          : res_launch_t<double, 256>(cluster, grid, a, st, cta_only);
+  return threads >= 512 ? res_launch_t<float, 512>(cluster, grid, a, st, cta_only)
+                        : res_launch_t<float, 256>(cluster, grid, a, st, cta_only);
 }
 
 int resident_max_clusters(bool fp64, int threads, int cluster) {

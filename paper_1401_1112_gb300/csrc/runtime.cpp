@@ -223,21 +223,24 @@ struct Plan {
   int launches = 0;
   int ticks = 0;
   // resident solver (whole solves in one launch): per solve 0 = tick path,
-  // 1 = a cluster, 2 = one CTA; the queues hold the cluster solves, then the
-  // CTA solves, each by estimated work, largest first
+  // 1 = a cluster of res_cluster CTAs, 2 = one CTA, 3 = a cluster of
+  // res_cluster_big CTAs; the queues hold the big-cluster solves, the
+  // cluster solves, then the CTA solves, each by estimated work, largest first
   std::vector<int8_t> mode;
-  int n_cq = 0, n_tq = 0, n_tick = 0, n_tick_items = 0;
-  int res_threads = 512, res_cluster = 8, res_grid = 0;
+  int n_bq = 0, n_cq = 0, n_tq = 0, n_tick = 0, n_tick_items = 0;
+  int res_threads = 512, res_cluster = 8, res_cluster_big = 16, res_grid = 0, res_grid_big = 0;
   bool res_smem = false;  // K, z, p of each CTA's octs in shared memory (FP32 bulk)
   int res_cap = 0;        // octs per CTA kept in shared memory
   int res_fill = 0;       // single CTAs launched beside the clusters on the SMs they leave
-  int32_t *d_queue = nullptr;   // [n_cq + n_tq]
-  int *d_heads = nullptr;       // [2] next position of each queue
+  int32_t *d_queue = nullptr;   // [n_bq + n_cq + n_tq]
+  int *d_heads = nullptr;       // [3] next position of each queue
+  cudaStream_t aux2 = nullptr;  // the third concurrent resident launch
+  cudaEvent_t join2 = nullptr;
   cudaEvent_t res_ev[2] = {nullptr, nullptr};
   double res_ms = 0.0, res_bytes = 0.0;
   int res_launches = 0;
   unsigned long long *d_tsolve = nullptr;  // [n][2] per-solve start / end (profiling)
-  double res_span_ms = 0.0, res_longest_ms = 0.0, res_occupancy = 0.0;
+  double res_span_ms = 0.0, res_longest_ms = 0.0, res_occupancy = 0.0, res_end_ms[3] = {0.0, 0.0, 0.0};
   int res_longest = -1;
 };
 
@@ -385,6 +388,8 @@ void plan_free(Plan *P) {
   dev_free(ctx, P->d_queue);
   dev_free(ctx, P->d_heads);
   dev_free(ctx, P->d_tsolve);
+  if (P->join2) cudaEventDestroy(P->join2);
+  if (P->aux2) cudaStreamDestroy(P->aux2);
   for (auto e : P->res_ev)
     if (e) cudaEventDestroy(e);
   if (P->h_active) cudaFreeHost(P->h_active);
@@ -401,10 +406,12 @@ double est_work(const ats_level *L) {
   return o * std::min(std::sqrt(1.0 + 8.0 * h), 4.0 * std::cbrt(o));
 }
 
-// Upload the resident queues of P in work order.
+// Upload the resident queues of P in work order: big-cluster solves, cluster
+// solves, CTA solves.
 ats_status plan_upload_queues(Plan *P) {
-  std::vector<int32_t> cq, tq;
+  std::vector<int32_t> bq, cq, tq;
   for (int k = 0; k < P->n; ++k) {
+    if (P->mode[k] == 3) bq.push_back(k);
     if (P->mode[k] == 1) cq.push_back(k);
     if (P->mode[k] == 2) tq.push_back(k);
   }
@@ -413,11 +420,13 @@ ats_status plan_upload_queues(Plan *P) {
     for (int32_t k : q) w[k] = est_work(P->levels[k]);
     std::stable_sort(q.begin(), q.end(), [&](int32_t a, int32_t b) { return w[a] > w[b]; });
   };
+  by_work(bq);
   by_work(cq);
   by_work(tq);
-  cq.insert(cq.end(), tq.begin(), tq.end());
-  if (!cq.empty())
-    CUDA_TRY(cudaMemcpyAsync(P->d_queue, cq.data(), sizeof(int32_t) * cq.size(), cudaMemcpyHostToDevice,
+  bq.insert(bq.end(), cq.begin(), cq.end());
+  bq.insert(bq.end(), tq.begin(), tq.end());
+  if (!bq.empty())
+    CUDA_TRY(cudaMemcpyAsync(P->d_queue, bq.data(), sizeof(int32_t) * bq.size(), cudaMemcpyHostToDevice,
                              P->ctx->stream));
   return ATS_OK;
 }
@@ -444,8 +453,9 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   }
   if (o.sched < ATS_SCHED_AUTO || o.sched > ATS_SCHED_RESIDENT || (o.res_threads != 0 && o.res_threads != 256 &&
       o.res_threads != 512) || o.res_cluster < 0 || o.res_cluster > 16 || o.res_max_octs < 0 || o.res_state < 0 ||
-      o.res_state > 1) {
-    set_error("bad resident-solver options (sched 0..2, res_threads 0/256/512, res_cluster 0..16, res_state 0/1)");
+      o.res_state > 1 || o.res_cluster_big > 16 || o.res_big_work < 0) {
+    set_error("bad resident-solver options (sched 0..2, res_threads 0/256/512, res_cluster and res_cluster_big "
+              "up to 16, res_state 0/1)");
     return ATS_ERR_INVALID_ARG;
   }
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -527,7 +537,8 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   // resident or tick path per solve, by a rule on the level and the options
   // alone (a level then runs the same arithmetic alone and in any batch)
   P->res_threads = o.res_threads > 0 ? o.res_threads : (P->fp64 ? 256 : 512);
-  P->res_cluster = o.res_cluster > 0 ? o.res_cluster : 8;
+  P->res_cluster = o.res_cluster > 0 ? o.res_cluster : 4;
+  P->res_cluster_big = o.res_cluster_big == 0 ? 16 : (o.res_cluster_big < 0 ? 0 : o.res_cluster_big);
   {
     const bool res_ok = o.sched != ATS_SCHED_TICK && o.stop_rule != ATS_STOP_PAPER;
     const int64_t cta_octs = o.res_cta_octs == 0 ? 2048 : o.res_cta_octs;
@@ -537,38 +548,68 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     const int64_t max_octs = o.sched == ATS_SCHED_RESIDENT
                                  ? INT64_MAX
                                  : (o.res_max_octs > 0 ? o.res_max_octs : (P->fp64 ? 2048 : 16384));
-    int clusters = 0;
+    const double big_work = o.res_big_work > 0 ? (double)o.res_big_work : 80000.0;
     P->res_smem = !P->fp64 && o.res_state == 0;
     if (P->res_smem) {
       P->res_cap = resident_smem_cap(P->res_threads, ctx->device);
       if (P->res_cap <= 0) P->res_smem = false;
     }
+    auto max_clusters = [&](int cl) {
+      if (cl <= 0) return 0;
+      return P->res_smem ? resident_smem_clusters(P->res_threads, cl, P->res_cap)
+                         : resident_max_clusters(P->fp64, P->res_threads, cl);
+    };
     P->mode.assign(n, 0);
     for (int k = 0; k < n; ++k) {
       const int64_t no = P->levels[k]->n_oct;
       if (!res_ok || no > max_octs) continue;
-      P->mode[k] = no <= cta_octs ? 2 : 1;
+      P->mode[k] = no <= cta_octs ? 2 : ((P->res_cluster_big > 0 && est_work(P->levels[k]) > big_work) ? 3 : 1);
     }
-    for (int k = 0; k < n; ++k) P->n_cq += P->mode[k] == 1;
-    if (P->n_cq > 0) {
-      clusters = P->res_smem ? resident_smem_clusters(P->res_threads, P->res_cluster, P->res_cap)
-                             : resident_max_clusters(P->fp64, P->res_threads, P->res_cluster);
-      if (clusters <= 0) {  // no cluster of that shape fits this device: those levels take the tick path
-        for (int k = 0; k < n; ++k)
-          if (P->mode[k] == 1) P->mode[k] = 0;
-        P->n_cq = 0;
-      }
-    }
+    int clA = 0, clB = 0;  // clusters of each size that fit the device at once
+    bool anyA = false, anyB = false;
     for (int k = 0; k < n; ++k) {
+      anyA = anyA || P->mode[k] == 3;
+      anyB = anyB || P->mode[k] == 1;
+    }
+    if (anyA) clA = max_clusters(P->res_cluster_big);
+    if (anyB || (anyA && clA <= 0)) clB = max_clusters(P->res_cluster);
+    // a cluster shape that does not fit this device: its levels take the
+    // smaller clusters, or the tick path
+    for (int k = 0; k < n; ++k) {
+      if (P->mode[k] == 3 && clA <= 0) P->mode[k] = 1;
+      if (P->mode[k] == 1 && clB <= 0) P->mode[k] = 0;
+    }
+    double wA = 0, wB = 0, wC = 0;
+    for (int k = 0; k < n; ++k) {
+      P->n_bq += P->mode[k] == 3;
+      P->n_cq += P->mode[k] == 1;
       P->n_tq += P->mode[k] == 2;
       P->n_tick += P->mode[k] == 0;
+      const double w = P->mode[k] ? est_work(P->levels[k]) : 0.0;
+      (P->mode[k] == 3 ? wA : P->mode[k] == 1 ? wB : wC) += w;
     }
-    P->res_grid = P->n_cq > 0 ? clusters * P->res_cluster
-                              : (P->res_smem ? 1 : std::max(1, resident_cta_blocks(P->fp64, P->res_threads))) *
-                                    ctx->num_sms;
-    // clusters pack into the GPCs with some SMs left over: single CTAs take
-    // small solves there, launched beside the clusters (one CTA per SM)
-    if (P->res_smem && P->n_cq > 0 && P->n_tq > 0) P->res_fill = std::max(0, ctx->num_sms - P->res_grid);
+    // the CTA slots of the device, shared by the launches in proportion to
+    // their queues' estimated work: big clusters, clusters (whole clusters,
+    // at least one when the queue is not empty) and single CTAs (at least
+    // their share, so the largest of them start at once); a cluster that has
+    // emptied its queue goes on with single-CTA solves
+    const int cta_per_sm = P->res_smem ? 1 : std::max(1, resident_cta_blocks(P->fp64, P->res_threads));
+    const int slots = cta_per_sm * ctx->num_sms;
+    const double wsum = std::max(1e-300, wA + wB + wC);
+    int kA = 0, kB = 0;
+    if (P->n_bq > 0) kA = std::max(1, std::min(clA, (int)std::lround(slots * wA / wsum / P->res_cluster_big)));
+    if (P->n_cq > 0) kB = std::max(1, std::min(clB, (int)std::lround(slots * wB / wsum / P->res_cluster)));
+    if (P->n_bq > 0 && P->n_cq == 0) kA = std::max(kA, std::min(clA, (int)((slots * (1.0 - wC / wsum)) / P->res_cluster_big)));
+    if (P->n_cq > 0 && P->n_bq == 0) kB = std::max(kB, std::min(clB, (int)((slots * (1.0 - wC / wsum)) / P->res_cluster)));
+    const int c_min = P->n_tq > 0 ? (int)std::ceil(slots * wC / wsum) : 0;
+    while (kA * P->res_cluster_big + kB * P->res_cluster + c_min > slots && (kA > 1 || kB > 1)) {
+      if (kA * P->res_cluster_big >= kB * P->res_cluster && kA > 1) --kA;
+      else if (kB > 1) --kB;
+      else --kA;
+    }
+    P->res_grid_big = kA * P->res_cluster_big;
+    P->res_grid = P->n_bq + P->n_cq > 0 ? kB * P->res_cluster : slots;
+    if (P->n_tq > 0 && P->n_bq + P->n_cq > 0) P->res_fill = std::max(0, slots - P->res_grid - P->res_grid_big);
   }
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
   P->grid = std::max(1, std::min(P->n_items, bps * ctx->num_sms));
@@ -580,8 +621,8 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, 3 * (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 2 * kCellCounters, &P->d_cells)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, std::max(1, P->n_cq + P->n_tq), &P->d_queue)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, 2, &P->d_heads)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, std::max(1, P->n_bq + P->n_cq + P->n_tq), &P->d_queue)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 3, &P->d_heads)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 4 * (size_t)P->n_items, &P->d_lists)) != ATS_OK ||
       (s = dev_alloc_t(ctx, (size_t)P->n_items, &P->d_ident)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_ctl)) != ATS_OK ||
@@ -645,26 +686,29 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   CUDA_TRY(cudaEventCreateWithFlags(&P->mark, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreate(&P->res_ev[0]));
   CUDA_TRY(cudaEventCreate(&P->res_ev[1]));
+  CUDA_TRY(cudaStreamCreateWithFlags(&P->aux2, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&P->join2, cudaEventDisableTiming));
   CUDA_TRY(cudaStreamSynchronize(st));
   *out = P;
   return ATS_OK;
 }
 
-// Enqueue the resident launch of P's cluster and CTA solves (after
-// plan_begin); with profiling, between the two timing events.
+// Enqueue the resident launches of P's solves (after plan_begin): the big
+// clusters on the context stream, the clusters and the single CTAs on the
+// plan's two side streams, all three forked from and joined back into the
+// context stream (profiling: between the two timing events).
 ats_status plan_launch_resident(Plan *P, bool prof) {
-  if (P->n_cq + P->n_tq == 0) return ATS_OK;
+  if (P->n_bq + P->n_cq + P->n_tq == 0) return ATS_OK;
   cudaStream_t st = P->ctx->stream;
   ResArgs ra;
   std::memset(&ra, 0, sizeof(ra));
   ra.solves = P->d_solves;
   ra.final_sc = P->d_final;
-  ra.queue = P->d_queue;
-  ra.n_cq = P->n_cq;
+  ra.tq = P->d_queue + P->n_bq + P->n_cq;
   ra.n_tq = P->n_tq;
+  ra.tq_head = P->d_heads + 2;
   ra.n_solves = P->n;
   ra.fp32_scalars = P->opts.fp32_scalars ? 1 : 0;
-  ra.heads = P->d_heads;
   ra.cells = prof ? P->d_cells + kCellCounters : nullptr;
   if (prof && !P->d_tsolve) {
     ats_status sa = dev_alloc_t(P->ctx, 2 * (size_t)P->n, &P->d_tsolve);
@@ -673,22 +717,59 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   if (prof) CUDA_TRY(cudaMemsetAsync(P->d_tsolve, 0, 2 * sizeof(unsigned long long) * P->n, st));
   ra.t_solve = prof ? P->d_tsolve : nullptr;
   ra.cap = P->res_cap;
-  CUDA_TRY(cudaMemsetAsync(P->d_heads, 0, 2 * sizeof(int), st));
+  CUDA_TRY(cudaMemsetAsync(P->d_heads, 0, 3 * sizeof(int), st));
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[0], st));
-  // the SMs no cluster fits on take small solves beside the cluster launch
-  const int fill = P->res_fill;
-  if (fill > 0) CUDA_TRY(cudaEventRecord(P->fj.fork, st));
-  if (P->res_smem) CUDA_TRY(launch_resident_smem(P->res_threads, P->res_cluster, P->res_grid, ra, st));
-  else CUDA_TRY(launch_resident(P->fp64, P->res_threads, P->res_cluster, P->res_grid, ra, st));
-  if (fill > 0) {
-    CUDA_TRY(cudaStreamWaitEvent(P->fj.aux, P->fj.fork, 0));
-    CUDA_TRY(launch_resident_smem(P->res_threads, P->res_cluster, fill, ra, P->fj.aux, true));
-    CUDA_TRY(cudaEventRecord(P->fj.join, P->fj.aux));
-    CUDA_TRY(cudaStreamWaitEvent(st, P->fj.join, 0));
-    P->res_launches += 1;
+  auto launch = [&](int cluster, int grid, const ResArgs &a, cudaStream_t s2, bool cta_only) -> cudaError_t {
+    return P->res_smem ? launch_resident_smem(P->res_threads, cluster, grid, a, s2, cta_only)
+                       : launch_resident(P->fp64, P->res_threads, cluster, grid, a, s2, cta_only);
+  };
+  // the launches in order: big clusters, clusters, single CTAs (the first
+  // one on st, the others on the side streams, forked before the first)
+  struct L {
+    int cluster, grid;
+    ResArgs a;
+    bool cta_only;
+  };
+  std::vector<L> ls;
+  if (P->n_bq > 0) {
+    ResArgs a = ra;
+    a.cq = P->d_queue;
+    a.n_cq = P->n_bq;
+    a.cq_head = P->d_heads;
+    ls.push_back({P->res_cluster_big, P->res_grid_big, a, false});
   }
+  if (P->n_cq > 0) {
+    ResArgs a = ra;
+    a.cq = P->d_queue + P->n_bq;
+    a.n_cq = P->n_cq;
+    a.cq_head = P->d_heads + 1;
+    ls.push_back({P->res_cluster, P->res_grid, a, false});
+  }
+  if (ls.empty()) {
+    ResArgs a = ra;
+    a.cq = P->d_queue;
+    a.n_cq = 0;
+    a.cq_head = P->d_heads;
+    ls.push_back({1, P->res_grid, a, true});
+  } else if (P->res_fill > 0) {
+    ResArgs a = ra;
+    a.cq = P->d_queue;
+    a.n_cq = 0;
+    a.cq_head = P->d_heads;
+    ls.push_back({1, P->res_fill, a, true});
+  }
+  cudaStream_t side[2] = {P->fj.aux, P->aux2};
+  cudaEvent_t joins[2] = {P->fj.join, P->join2};
+  if (ls.size() > 1) CUDA_TRY(cudaEventRecord(P->fj.fork, st));
+  for (size_t i = 0; i < ls.size(); ++i) {
+    cudaStream_t s2 = i == 0 ? st : side[i - 1];
+    if (i > 0) CUDA_TRY(cudaStreamWaitEvent(s2, P->fj.fork, 0));
+    CUDA_TRY(launch(ls[i].cluster, ls[i].grid, ls[i].a, s2, ls[i].cta_only));
+    if (i > 0) CUDA_TRY(cudaEventRecord(joins[i - 1], s2));
+  }
+  for (size_t i = 1; i < ls.size(); ++i) CUDA_TRY(cudaStreamWaitEvent(st, joins[i - 1], 0));
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[1], st));
-  P->res_launches += 1;
+  P->res_launches += (int)ls.size();
   return ATS_OK;
 }
 
@@ -1059,7 +1140,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   }
   if (P->profiling) {
     plan_bytes(P, cells, &P->op_bytes, &P->ref_bytes, &P->upd_bytes);
-    if (P->n_cq + P->n_tq > 0) {
+    if (P->n_bq + P->n_cq + P->n_tq > 0) {
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, P->res_ev[0], P->res_ev[1]));
       P->res_ms = ms;
@@ -1079,15 +1160,23 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
         t0 = std::min(t0, ts[2 * k]);
         t1 = std::max(t1, ts[2 * k + 1]);
         const double d = (double)(ts[2 * k + 1] - ts[2 * k]) * 1e-6;
-        busy += d * (P->mode[k] == 1 ? P->res_cluster : 1);
+        busy += d * (P->mode[k] == 1 ? P->res_cluster : P->mode[k] == 3 ? P->res_cluster_big : 1);
         if (d > longest) {
           longest = d;
           P->res_longest = k;
         }
       }
       P->res_span_ms = t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
+      // when the last solve of each kind ended (big clusters, clusters, one CTA)
+      for (int q = 0; q < 3; ++q) P->res_end_ms[q] = 0.0;
+      for (int k = 0; k < n; ++k) {
+        if (P->mode[k] == 0 || ts[2 * k + 1] < ts[2 * k] || t1 <= t0) continue;
+        const int q = P->mode[k] == 3 ? 0 : P->mode[k] == 1 ? 1 : 2;
+        P->res_end_ms[q] = std::max(P->res_end_ms[q], (double)(ts[2 * k + 1] - t0) * 1e-6);
+      }
       P->res_longest_ms = longest;
-      P->res_occupancy = P->res_span_ms > 0 ? busy / (P->res_span_ms * (P->res_grid + P->res_fill)) : 0.0;
+      P->res_occupancy =
+          P->res_span_ms > 0 ? busy / (P->res_span_ms * (P->res_grid + P->res_grid_big + P->res_fill)) : 0.0;
     }
   }
   ats_status first_err = ATS_OK, first_warn = ATS_OK;
@@ -2088,19 +2177,22 @@ ats_status ats_batch_autotune(ats_batch *B, double *const *x_inout, const int *t
             cands.push_back(o);
           }
       }
-      if (P->n_cq + P->n_tq > 0) {
-        static const int kThr[] = {256, 512}, kCl[] = {8, 16}, kCta[] = {1024, 2048};
-        for (int th : kThr)
-          for (int cl : kCl)
-            for (int ct : kCta) {
-              ats_solve_opts o = base;
-              o.res_threads = th;
-              o.res_cluster = cl;
-              o.res_cta_octs = ct;
-              if (th == P->res_threads && cl == P->res_cluster && ct == (base.res_cta_octs ? base.res_cta_octs : 2048))
-                continue;
-              cands.push_back(o);
-            }
+      if (P->n_bq + P->n_cq + P->n_tq > 0) {
+        // (threads per CTA, cluster size, one-CTA limit, big-cluster size; -1 = none)
+        static const int kShapes[][4] = {{512, 4, 2048, 16}, {512, 8, 2048, 16}, {512, 8, 2048, -1},
+                                         {256, 4, 2048, 16}, {512, 4, 1024, 16}, {512, 2, 2048, 16},
+                                         {512, 4, 2048, 8}, {512, 16, 2048, -1}};
+        const int base_cta = base.res_cta_octs ? base.res_cta_octs : 2048;
+        const int base_big = P->res_cluster_big > 0 ? P->res_cluster_big : -1;
+        for (const auto &sh : kShapes) {
+          if (sh[0] == P->res_threads && sh[1] == P->res_cluster && sh[2] == base_cta && sh[3] == base_big) continue;
+          ats_solve_opts o = base;
+          o.res_threads = sh[0];
+          o.res_cluster = sh[1];
+          o.res_cta_octs = sh[2];
+          o.res_cluster_big = sh[3];
+          cands.push_back(o);
+        }
       }
       ats_solve_opts best = base;
       for (size_t i = 0; i < cands.size() && s == ATS_OK; ++i) {
@@ -2164,12 +2256,16 @@ ats_status ats_batch_kernel_stats(const ats_batch *B, ats_kernel_stats *out) {
     out->res_ms = P->res_ms;
     out->res_bytes = P->res_bytes;
     out->res_launches = P->res_launches;
-    out->res_solves = P->n_cq + P->n_tq;
+    out->res_solves = P->n_bq + P->n_cq + P->n_tq;
     out->res_span_ms = P->res_span_ms;
     out->res_longest_ms = P->res_longest_ms;
     out->res_occupancy = P->res_occupancy;
     out->res_longest = P->res_longest;
-    out->res_grid = P->res_grid + P->res_fill;
+    out->res_grid = P->res_grid + P->res_grid_big + P->res_fill;
+    for (int q = 0; q < 3; ++q) out->res_end_ms[q] = P->res_end_ms[q];
+    out->res_grids[0] = P->res_grid_big;
+    out->res_grids[1] = P->res_grid;
+    out->res_grids[2] = P->res_fill;
     return ATS_OK;
   } catch (...) {
     return ats::abi_exception();

@@ -300,7 +300,8 @@ def test_autotune_resident_shapes(ats, ctx):
     xs = [st.E.copy() for _, st in solves]
     r = B.autotune(xs, reps=1)
     assert r["candidates"] == 8  # the batch's own shape and the seven others
-    assert r["res_threads"] in (256, 512) and r["res_cluster"] in (8, 16) and r["res_cta_octs"] in (0, 1024, 2048)
+    assert r["res_threads"] in (256, 512) and r["res_cluster"] in (2, 4, 8, 16)
+    assert r["res_cta_octs"] in (0, 1024, 2048) and r["chosen"]["res_cluster_big"] in (0, 8, 16, -1)
     assert 0.0 < r["ms"] <= r["ms_default"]
     for (lv, st), x in zip(solves, xs):
         assert _rel(x, _oracle_x(lv, st)) <= PAR
@@ -308,11 +309,44 @@ def test_autotune_resident_shapes(ats, ctx):
     assert B.solve(xs2)[0] == 0
     B.close()
     B3 = ats.Batch(ctx, levels, res_threads=r["chosen"]["res_threads"], res_cluster=r["chosen"]["res_cluster"],
-                   res_cta_octs=r["chosen"]["res_cta_octs"], **opts)
+                   res_cta_octs=r["chosen"]["res_cta_octs"], res_cluster_big=r["chosen"]["res_cluster_big"], **opts)
     xs3 = [st.E.copy() for _, st in solves]
     assert B3.solve(xs3)[0] == 0
     for a, b in zip(xs2, xs3):
         np.testing.assert_array_equal(a, b)
     B3.close()
+    for L in levels:
+        L.close()
+
+
+def test_two_cluster_sizes_in_one_batch(ats, ctx):
+    """Levels of large estimated work (size x stiffness) on 16-CTA clusters,
+    the others on 8-CTA clusters or single CTAs, as three concurrent
+    launches: every solve matches the oracle and is bitwise the same alone
+    (where it runs by itself on its shape) and in the batch."""
+    rng = np.random.default_rng(5150)
+    solves = [W.random_box_solve(rng, o, robin=True, dt_lo=lo, dt_hi=lo) for o, lo in
+              ((5, 1.0), (600, 30.0), (2600, 1.0), (3100, 1.0), (5000, 80.0), (7000, 100.0), (40, 5.0), (2200, 2.0))]
+    levels = []
+    for lv, st in solves:
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        levels.append(L)
+    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, sched=ats.ATS_SCHED_RESIDENT,
+                res_cta_octs=512, res_big_work=40000, res_cluster=8, res_cluster_big=16)
+    B = ats.Batch(ctx, levels, **opts)
+    xs = [st.E.copy() for _, st in solves]
+    B.set_profiling(True)
+    code, stats = B.solve(xs)
+    assert code == 0, stats
+    g = B.kernel_stats()["res_grids"]
+    assert g[0] > 0 and g[1] > 0  # both cluster sizes ran
+    for (lv, st), x in zip(solves, xs):
+        assert _rel(x, _oracle_x(lv, st)) <= PAR
+    for k, L in enumerate(levels):
+        x = solves[k][1].E.copy()
+        assert L.solve(x, **opts)[0] == 0
+        np.testing.assert_array_equal(x, xs[k])
+    B.close()
     for L in levels:
         L.close()
