@@ -156,9 +156,10 @@ typedef struct {
   int res_max_octs;  /* ATS_SCHED_AUTO: levels above this many octs take the  */
                      /* tick path (0 = 16384 for ATS_PREC_MIXED, 2048 for    */
                      /* ATS_PREC_FP64)                                       */
-  int fp32_scalars;  /* resident solver, mixed precision: 1 = CG alpha, beta  */
-                     /* from the dot totals rounded to FP32 (the tick path's  */
-                     /* form); 0 = from the FP64 totals (default)            */
+  int cg_scalars;    /* resident solver, mixed precision: the CG step's alpha,  */
+                     /* beta and inner convergence test from the error-free   */
+                     /* dot totals, 0 = rounded to FP32 (the tick path's form, */
+                     /* default), 1 = in FP64                                 */
   int res_state;     /* resident solver, mixed precision: where each CTA     */
                      /* keeps K, z and p of its octs: 0 = shared memory      */
                      /* (neighbours read from the owning CTA through          */
@@ -170,7 +171,7 @@ typedef struct {
   int res_big_work;  /* resident solver: a level of more than res_cta_octs   */
                      /* octs takes the larger clusters when its estimated   */
                      /* work n_oct min(sqrt(1 + 8 h), 4 n_oct^(1/3)), h =   */
-                     /* dt / (2 dx^2), exceeds this (0 = 80000)             */
+                     /* dt / (2 dx^2), exceeds this (0 = 50000)             */
 } ats_solve_opts;
 
 /* scheduling of a solve (ats_solve_opts.sched).  Which path a level takes

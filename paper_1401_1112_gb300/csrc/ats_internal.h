@@ -202,7 +202,7 @@ struct ResArgs {
   const int32_t *cq;
   const int32_t *tq;
   int n_cq, n_tq, n_solves;
-  int fp32_scalars;  // 1: alpha and beta from the totals rounded to FP32 (mixed precision)
+  int cg_scalars;  // FP32 bulk: 0 = step decisions in FP32 from the rounded totals, 1 = in FP64
   int *cq_head;
   int *tq_head;
   unsigned long long *cells;

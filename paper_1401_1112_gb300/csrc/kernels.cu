@@ -1689,6 +1689,7 @@ struct ResState {
   int32_t phase, first, pcur, iters, inner_iters, refines, status, final_pass;
   int32_t n_op, n_first, n_xpe, pad;
   double rz, r0, rnorm, xnorm, inner_target, alpha, beta;
+  float rzf, t2f, alphaf, betaf;  // the same scalars in FP32 (the FP32 bulk's step decisions)
 };
 
 template <typename T>
@@ -1699,6 +1700,50 @@ struct ResShared {
   __align__(16) Acc<T> inbox[2][kMaxCluster][3];  // [buffer][sender rank][sum]
   int task;
 };
+
+// alpha = r.z / p.q, or a breakdown (p.q not positive, a non-finite value).
+template <typename T>
+__device__ __forceinline__ void cg_alpha(ResState &st, const Acc<T> &pq_tot, bool f32) {
+  if (f32) {
+    const float pq = pq_tot.val(), rz = st.rzf;
+    if (!(rz >= 0.f) || !isfinite(rz) || !(pq > 0.f) || !isfinite(pq)) {
+      st.status = ATS_ERR_BREAKDOWN;
+      st.phase = kDone;
+    } else {
+      st.alphaf = __fdiv_rn(rz, pq);
+      st.alpha = st.alphaf;
+    }
+    return;
+  }
+  const double pq = pq_tot.get();
+  if (!(st.rz >= 0.0) || !isfinite(st.rz) || !(pq > 0.0) || !isfinite(pq)) {
+    st.status = ATS_ERR_BREAKDOWN;
+    st.phase = kDone;
+  } else {
+    st.alpha = st.rz / pq;
+    st.alphaf = (float)st.alpha;
+  }
+}
+// beta = r'.z' / r.z for the next direction; returns whether the inner
+// solve has converged (r'.r' <= target^2, or r'.z' = 0).
+template <typename T>
+__device__ __forceinline__ bool cg_beta(ResState &st, const Acc<T> &rz_tot, const Acc<T> &rr_tot, bool f32) {
+  if (f32) {
+    const float rz_new = rz_tot.val(), rr = rr_tot.val();
+    st.betaf = __fdiv_rn(rz_new, st.rzf);
+    st.beta = st.betaf;
+    st.rzf = rz_new;
+    st.rz = rz_new;
+    return rr <= st.t2f || rz_new == 0.f;
+  }
+  const double rz_new = rz_tot.get(), rr = rr_tot.get();
+  st.beta = rz_new / st.rz;
+  st.betaf = (float)st.beta;
+  st.rz = rz_new;
+  st.rzf = (float)rz_new;
+  return rr <= st.inner_target * st.inner_target || rz_new == 0.0;
+}
+
 
 // Sums of NA accumulators over the group: this CTA alone, or every CTA of the
 // cluster.  Thread 0 of each CTA ends with the group totals in `out`.  The
@@ -1780,12 +1825,11 @@ __device__ __forceinline__ void res_xpe_oct(const SolveDev &sd, int o) {
   st8(e + 8 * o, ev);
 }
 
-// The rounding of a CG scalar to the bulk precision: FP64 quotient of the
-// FP64 totals (default), or, with fp32_scalars, the quotient of the totals
-// rounded to FP32 first (the tick kernels' form).
-__device__ __forceinline__ double cg_ratio(double num, double den, bool fp32) {
-  return fp32 ? (double)__fdiv_rn((float)num, (float)den) : num / den;
-}
+// The per-step CG decisions of the FP32 bulk (alpha, beta, the inner test)
+// are taken in FP32 from the error-free totals rounded once to FP32 -- the
+// tick kernels' form -- unless cg_scalars asks for FP64: one thread takes
+// them while the group waits, and the GB300's FP64 pipe makes an FP64
+// quotient the longer wait.  A refinement pass's decisions are FP64.
 
 // One solve by one group: the refinement / inner-CG state machine of the tick
 // kernels (k_ref, k_op, k_upd), with its decisions taken right after each sum.
@@ -1811,7 +1855,7 @@ __device__ void res_solve(const ResArgs &a, int s, ResShared<T> &sh, int &buf) {
   const int o0 = lo + (int)threadIdx.x, stride = (int)blockDim.x;
   const T h = (T)sd.h;
   const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
-  const bool fp32s = a.fp32_scalars != 0;
+  const bool f32 = sizeof(T) == 4 && a.cg_scalars == 0;
   for (;;) {
     const int phase = sh.st.phase;
     if (phase == kDone) break;
@@ -1844,9 +1888,11 @@ __device__ void res_solve(const ResArgs &a, int s, ResShared<T> &sh, int &buf) {
         } else {
           st.phase = kInner;
           st.rz = rz;
+          st.rzf = (float)rz;
           st.first = 1;
           st.inner_iters = 0;
           st.inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
+          st.t2f = (float)(st.inner_target * st.inner_target);
         }
       }
       __syncthreads();
@@ -1854,7 +1900,7 @@ __device__ void res_solve(const ResArgs &a, int s, ResShared<T> &sh, int &buf) {
     }
     // inner CG iteration, step 1: p = z + beta p, q = (I + dt A) p, sum p.q
     const bool first = sh.st.first != 0;
-    const T beta = (T)sh.st.beta;
+    const T beta = sizeof(T) == 4 ? (T)sh.st.betaf : (T)sh.st.beta;
     const int pcur = sh.st.pcur;
     const T *pold = (const T *)(pcur ? sd.p1 : sd.p0);
     T *pnew = (T *)(pcur ? sd.p0 : sd.p1);
@@ -1868,22 +1914,16 @@ __device__ void res_solve(const ResArgs &a, int s, ResShared<T> &sh, int &buf) {
       group_sum<T, 1, kCluster>(acc, sh, buf, tot);
       if (threadIdx.x == 0) {
         ResState &st = sh.st;
-        const double pq = tot[0].get();
         st.n_op += 1;
         st.n_first += first ? 1 : 0;
-        if (!(st.rz >= 0.0) || !isfinite(st.rz) || !(pq > 0.0) || !isfinite(pq)) {
-          st.status = ATS_ERR_BREAKDOWN;
-          st.phase = kDone;
-        } else {
-          st.alpha = cg_ratio(st.rz, pq, fp32s && sizeof(T) == 4);
-        }
+        cg_alpha(st, tot[0], f32);
       }
       __syncthreads();
     }
     if (sh.st.phase == kDone) break;
     // step 2: e += alpha p, r = D z - alpha q, z = D^-1 r; sums r.z, r.r
     {
-      const T alpha = (T)sh.st.alpha;
+      const T alpha = sizeof(T) == 4 ? (T)sh.st.alphaf : (T)sh.st.alpha;
       Acc<T> acc[2], tot[2];
       UpdOwn<T> w;
       float none = 0.f;
@@ -1894,14 +1934,11 @@ __device__ void res_solve(const ResArgs &a, int s, ResShared<T> &sh, int &buf) {
       group_sum<T, 2, kCluster>(acc, sh, buf, tot);
       if (threadIdx.x == 0) {
         ResState &st = sh.st;
-        const double rz_new = tot[0].get(), rr = tot[1].get();
         st.iters += 1;
         st.inner_iters += 1;
         st.first = 0;
         st.pcur ^= 1;
-        st.beta = cg_ratio(rz_new, st.rz, fp32s && sizeof(T) == 4);
-        st.rz = rz_new;
-        const bool conv = rr <= st.inner_target * st.inner_target || rz_new == 0.0;
+        const bool conv = cg_beta(st, tot[0], tot[1], f32);
         if (conv) {
           st.phase = kRefine;
         } else if (st.iters >= sd.max_iter) {
@@ -2011,14 +2048,17 @@ __global__ void __launch_bounds__(NT, ResMinBlocks<T, NT>::value) k_res_cta(ResA
 //
 // Each CTA of the group owns a contiguous run of the level's octs (the
 // group's octs split by cluster rank) and keeps K, z and p of the first
-// `cap` of them in shared memory for the whole solve, with each oct's six
-// neighbours coded as (owning rank, local index).  A step reads its own octs
+// kRes2Cap3 of them in shared memory for the whole solve, each array as eight
+// planes (plane c holds cell c of every oct: a warp's accesses to one cell of
+// consecutive octs are conflict-free, and a face reads exactly its four
+// cells), with each oct's six neighbours coded as (owning rank, local index).  A step reads its own octs
 // from its shared memory and the neighbours' faces from the owning CTA's
 // shared memory (distributed shared memory inside the cluster): no iteration
 // reads K, z or p from L2 or HBM.  D, q and e -- read and written only by the
-// thread that owns an oct -- stay in global memory, like the FP64 arrays of
-// the refinement pass.  Octs beyond a CTA's capacity use the level's global
-// arrays.  Where an oct's values live does not change what is computed, so
+// thread that owns an oct -- are kept there too when the CTA's share is at
+// most kRes2Cap6 octs, so a CG iteration then touches no global memory (else
+// they stay in global memory); the FP64 arrays of the refinement pass stay in
+// global memory.  Octs beyond a CTA's capacity use the level's global arrays.  Where an oct's values live does not change what is computed, so
 // the capacity does not enter the arithmetic.
 //
 // A CG iteration reads its neighbours' p instead of recomputing it:
@@ -2028,47 +2068,68 @@ __global__ void __launch_bounds__(NT, ResMinBlocks<T, NT>::value) k_res_cta(ResA
 //   3. r = D z - alpha q, z = D^-1 r, e += alpha p, the sums r.z and r.r.
 
 extern __shared__ __align__(128) unsigned char res2_smem[];
-constexpr int kRes2OctBytes = 3 * 32 + 16;  // per oct: K, z, p rows (8 FP32 each) and six 16-bit neighbour codes
-// Shared bytes for `cap` octs: their rows, one more row of K, z and p (the
-// stand-in neighbour of a face without one: K = -1, so its coefficient is 0,
-// and p = 0), and the codes.
-__host__ __device__ constexpr size_t res2_smem_bytes(int cap) {
-  return (size_t)cap * kRes2OctBytes + 3 * 32;
-}
+// Two layouts of a CTA's shared memory, chosen per solve from the size of the
+// CTA's share: all six arrays K, z, p, D, q, e for up to kRes2Cap6 octs, or
+// K, z, p only (D, q, e in global memory) for up to kRes2Cap3 octs.  Each
+// array is eight cell planes of cap + 1 floats (oct `cap`: the stand-in
+// neighbour), followed by the 16-byte neighbour codes of the octs.
+constexpr int kRes2Cap3 = 2048;
+constexpr int kRes2Cap6 = 1100;
+constexpr size_t kRes2SmemBytes = (size_t)24 * (kRes2Cap3 + 1) * 4 + (size_t)kRes2Cap3 * 16;
+static_assert((size_t)48 * (kRes2Cap6 + 1) * 4 + (size_t)kRes2Cap6 * 16 <= kRes2SmemBytes,
+              "the six-array layout fits the three-array one's allocation");
 
 namespace {
 
 constexpr uint16_t kCodeNone = 0xFFFF;      // no neighbour (a wall or interface face)
 constexpr uint16_t kCodeGlobal = 0xFFFE;    // a neighbour beyond its CTA's capacity: global arrays
 
+// The layout constants of a solve (capacities, plane stride) as compile-time
+// members, so every shared access is a register plus an immediate offset.
+template <int kCap, int kCapD>
 struct Res2Ctx {
-  uint32_t sK, sZ, sP, sC;  // shared-window addresses of this CTA's K, z, p rows and codes
-  int cap;                  // octs of this CTA's share kept in shared memory
+  static constexpr int cap = kCap;    // octs of the CTA's share whose K, z, p are in shared memory
+  static constexpr int capD = kCapD;  // ... whose D, q, e are (kCap or 0)
+  static constexpr uint32_t S = (uint32_t)(kCap + 1) * 4u;  // bytes of one cell plane
+  uint32_t sK, sZ, sP, sD, sQ, sE, sC;  // shared-window addresses of this CTA's planes and codes
   int chunk;                // octs per CTA of the group
   int lo;                   // first oct of this CTA
   unsigned cr;              // this CTA's rank in the group (0 for one CTA)
 };
+using Res2Six = Res2Ctx<kRes2Cap6, kRes2Cap6>;
+using Res2Three = Res2Ctx<kRes2Cap3, 0>;
 
-__device__ __forceinline__ void lds4(uint32_t a, float &x, float &y, float &z, float &w) {
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+// The eight cells of an oct from the planes of an array, a = the array's
+// address + 4 x the oct's local index (this CTA's shared memory, or, with the
+// _c forms, another CTA's through its shared::cluster address).
+__device__ __forceinline__ float ldsf(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
 }
-__device__ __forceinline__ void ldsc4(uint32_t a, float &x, float &y, float &z, float &w) {
-  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+__device__ __forceinline__ float ldscf(uint32_t a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
 }
-__device__ __forceinline__ void lds8(uint32_t a, float (&v)[8]) {
-  lds4(a, v[0], v[1], v[2], v[3]);
-  lds4(a + 16, v[4], v[5], v[6], v[7]);
+__device__ __forceinline__ void lds_cells(uint32_t a, uint32_t S, float (&v)[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = ldsf(a + c * S);
 }
-__device__ __forceinline__ void ldsc8(uint32_t a, float (&v)[8]) {
-  ldsc4(a, v[0], v[1], v[2], v[3]);
-  ldsc4(a + 16, v[4], v[5], v[6], v[7]);
+__device__ __forceinline__ void sts_cells(uint32_t a, uint32_t S, const float (&v)[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) asm volatile("st.shared.f32 [%0], %1;" ::"r"(a + c * S), "f"(v[c]) : "memory");
 }
-__device__ __forceinline__ void sts8(uint32_t a, const float (&v)[8]) {
-  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
-               : "memory");
-  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a + 16), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
-               : "memory");
+// The four cells facing across axis A (those with bit A equal to NB).
+template <int A, int NB, bool kRemote>
+__device__ __forceinline__ void lds_face(uint32_t a, uint32_t S, float (&v)[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (((c >> A) & 1) != NB) continue;
+    v[c] = kRemote ? ldscf(a + c * S) : ldsf(a + c * S);
+  }
 }
+
 __device__ __forceinline__ uint32_t cl_map_s(uint32_t a, unsigned rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
@@ -2079,11 +2140,12 @@ __device__ __forceinline__ uint32_t cl_map_s(uint32_t a, unsigned rank) {
 // 2 another CTA's (rank r), 3 the global arrays (oct g).
 struct Nb {
   int kind;
-  uint32_t off;  // byte offset of the oct's row in each shared array
+  uint32_t off;  // byte offset of the oct in each plane of a shared array
   unsigned r;
   int g;
 };
-__device__ __forceinline__ Nb nb_of_global(const Res2Ctx &cx, int g) {
+template <class Cx>
+__device__ __forceinline__ Nb nb_of_global(const Cx &cx, int g) {
   Nb n;
   n.g = g;
   n.r = 0;
@@ -2098,18 +2160,20 @@ __device__ __forceinline__ Nb nb_of_global(const Res2Ctx &cx, int g) {
     return n;
   }
   n.r = (unsigned)r;
-  n.off = (uint32_t)l * 32u;
+  n.off = (uint32_t)l * 4u;
   n.kind = n.r == cx.cr ? 1 : 2;
   return n;
 }
-__device__ __forceinline__ uint16_t code_of_global(const Res2Ctx &cx, int g) {
+template <class Cx>
+__device__ __forceinline__ uint16_t code_of_global(const Cx &cx, int g) {
   if (g < 0) return kCodeNone;
   const int r = g / cx.chunk, l = g - r * cx.chunk;
   return l >= cx.cap ? kCodeGlobal : (uint16_t)((r << 12) | l);
 }
 
 // The six neighbours of own oct o (local index l).
-__device__ __forceinline__ void res2_nbs(const Res2Ctx &cx, const SolveDev &sd, int o, int l, Nb (&nb)[6]) {
+template <class Cx>
+__device__ __forceinline__ void res2_nbs(const Cx &cx, const SolveDev &sd, int o, int l, Nb (&nb)[6]) {
   if (l < cx.cap) {
     uint32_t c01, c23, c45, pad;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -2131,7 +2195,7 @@ __device__ __forceinline__ void res2_nbs(const Res2Ctx &cx, const SolveDev &sd, 
         n = nb_of_global(cx, g);
       } else {
         n.r = c >> 12;
-        n.off = (uint32_t)(c & 0xFFF) * 32u;
+        n.off = (uint32_t)(c & 0xFFF) * 4u;
         n.kind = n.r == cx.cr ? 1 : 2;
       }
     }
@@ -2147,15 +2211,12 @@ __device__ __forceinline__ void res2_nbs(const Res2Ctx &cx, const SolveDev &sd, 
 // The four cells of neighbour n that face this oct across axis A (NB: which
 // half), from the shared array at `arr` or the global array `garr`.
 template <int A, int NB>
-__device__ __forceinline__ void res2_face(const Nb &n, uint32_t arr, const float *garr, bool coherent,
+__device__ __forceinline__ void res2_face(const Nb &n, uint32_t arr, uint32_t S, const float *garr, bool coherent,
                                           float (&v)[8]) {
   if (n.kind == 1) {
-    if (A != 2) lds8(arr + n.off, v);
-    else lds4(arr + n.off + 16 * NB, v[4 * NB], v[4 * NB + 1], v[4 * NB + 2], v[4 * NB + 3]);
+    lds_face<A, NB, false>(arr + n.off, S, v);
   } else if (n.kind == 2) {
-    const uint32_t a = cl_map_s(arr + n.off, n.r);
-    if (A != 2) ldsc8(a, v);
-    else ldsc4(a + 16 * NB, v[4 * NB], v[4 * NB + 1], v[4 * NB + 2], v[4 * NB + 3]);
+    lds_face<A, NB, true>(cl_map_s(arr + n.off, n.r), S, v);
   } else {
     if (coherent) ldc_face<A, NB>(garr + 8 * n.g, v);
     else ld_face<A, NB>(garr + 8 * n.g, v);
@@ -2163,26 +2224,28 @@ __device__ __forceinline__ void res2_face(const Nb &n, uint32_t arr, const float
 }
 
 // An own oct's row of a shared array, or of its global array beyond the capacity.
-__device__ __forceinline__ void res2_own(const Res2Ctx &cx, uint32_t arr, int l, const float *garr, int o,
+template <class Cx>
+__device__ __forceinline__ void res2_own(const Cx &cx, uint32_t arr, int cap, int l, const float *garr, int o,
                                          bool coherent, float (&v)[8]) {
-  if (l < cx.cap) lds8(arr + (uint32_t)l * 32u, v);
+  if (l < cap) lds_cells(arr + (uint32_t)l * 4u, cx.S, v);
   else if (coherent) ldc8(garr + 8 * o, v);
   else ld8_ro(garr + 8 * o, v);
 }
-__device__ __forceinline__ void res2_own_store(const Res2Ctx &cx, uint32_t arr, int l, float *garr, int o,
+template <class Cx>
+__device__ __forceinline__ void res2_own_store(const Cx &cx, uint32_t arr, int cap, int l, float *garr, int o,
                                                const float (&v)[8]) {
-  if (l < cx.cap) sts8(arr + (uint32_t)l * 32u, v);
+  if (l < cap) sts_cells(arr + (uint32_t)l * 4u, cx.S, v);
   else st8(garr + 8 * o, v);
 }
 
-template <int DIR>
-__device__ __forceinline__ void res2_op_face(const Res2Ctx &cx, const SolveDev &sd, const Nb &n, float h,
+template <int DIR, class Cx>
+__device__ __forceinline__ void res2_op_face(const Cx &cx, const SolveDev &sd, const Nb &n, float h,
                                              const float (&K)[8], float (&off)[8]) {
   constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
   if (n.kind == 0) return;
   float Kn[8], Pn[8];
-  res2_face<A, NB>(n, cx.sK, (const float *)sd.KT, false, Kn);
-  res2_face<A, NB>(n, cx.sP, (const float *)sd.p0, true, Pn);
+  res2_face<A, NB>(n, cx.sK, cx.S, (const float *)sd.KT, false, Kn);
+  res2_face<A, NB>(n, cx.sP, cx.S, (const float *)sd.p0, true, Pn);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (((c >> A) & 1) != S) continue;
@@ -2193,12 +2256,13 @@ __device__ __forceinline__ void res2_op_face(const Res2Ctx &cx, const SolveDev &
 }
 
 // Step 2 on own oct o: q = D p - sum C p_nb; returns the oct's p.q.
-__device__ __forceinline__ float res2_op_oct(const Res2Ctx &cx, const SolveDev &sd, int o, float h) {
+template <class Cx>
+__device__ __forceinline__ float res2_op_oct(const Cx &cx, const SolveDev &sd, int o, float h) {
   const int l = o - cx.lo;
   float K[8], p[8], d[8];
-  res2_own(cx, cx.sK, l, (const float *)sd.KT, o, false, K);
-  res2_own(cx, cx.sP, l, (const float *)sd.p0, o, true, p);
-  ldc8((const float *)sd.dg + 8 * o, d);
+  res2_own(cx, cx.sK, cx.cap, l, (const float *)sd.KT, o, false, K);
+  res2_own(cx, cx.sP, cx.cap, l, (const float *)sd.p0, o, true, p);
+  res2_own(cx, cx.sD, cx.capD, l, (const float *)sd.dg, o, true, d);
   Nb nb[6];
   res2_nbs(cx, sd, o, l, nb);
   float off[8];
@@ -2219,7 +2283,7 @@ __device__ __forceinline__ float res2_op_oct(const Res2Ctx &cx, const SolveDev &
     if (leaf) local = fmaf(p[c], q, local);
     qv[c] = leaf ? q : 0.f;
   }
-  st8((float *)sd.q + 8 * o, qv);
+  res2_own_store(cx, cx.sQ, cx.capD, l, (float *)sd.q, o, qv);
   return local;
 }
 
@@ -2227,26 +2291,12 @@ __device__ __forceinline__ float res2_op_oct(const Res2Ctx &cx, const SolveDev &
 // shared memory (or the stand-in row): every face loads unconditionally, from
 // this CTA's rows (one CTA) or the owner's (a cluster).
 template <int DIR, bool kCluster>
-__device__ __forceinline__ void res2_fast_face(uint32_t aK, uint32_t aP, float h, const float (&K)[8], float (&off)[8]) {
+__device__ __forceinline__ void res2_fast_face(uint32_t aK, uint32_t aP, uint32_t PS, float h, const float (&K)[8],
+                                               float (&off)[8]) {
   constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
   float Kn[8], Pn[8];
-  if (A != 2) {
-    if (kCluster) {
-      ldsc8(aK, Kn);
-      ldsc8(aP, Pn);
-    } else {
-      lds8(aK, Kn);
-      lds8(aP, Pn);
-    }
-  } else {
-    if (kCluster) {
-      ldsc4(aK + 16 * NB, Kn[4 * NB], Kn[4 * NB + 1], Kn[4 * NB + 2], Kn[4 * NB + 3]);
-      ldsc4(aP + 16 * NB, Pn[4 * NB], Pn[4 * NB + 1], Pn[4 * NB + 2], Pn[4 * NB + 3]);
-    } else {
-      lds4(aK + 16 * NB, Kn[4 * NB], Kn[4 * NB + 1], Kn[4 * NB + 2], Kn[4 * NB + 3]);
-      lds4(aP + 16 * NB, Pn[4 * NB], Pn[4 * NB + 1], Pn[4 * NB + 2], Pn[4 * NB + 3]);
-    }
-  }
+  lds_face<A, NB, kCluster>(aK, PS, Kn);
+  lds_face<A, NB, kCluster>(aP, PS, Pn);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (((c >> A) & 1) != S) continue;
@@ -2256,18 +2306,18 @@ __device__ __forceinline__ void res2_fast_face(uint32_t aK, uint32_t aP, float h
   }
 }
 
-template <bool kCluster>
-__device__ __forceinline__ float res2_op_oct_fast(const Res2Ctx &cx, const SolveDev &sd, int o, int l,
+template <bool kCluster, class Cx>
+__device__ __forceinline__ float res2_op_oct_fast(const Cx &cx, const SolveDev &sd, int o, int l,
                                                   const uint32_t (&w)[3], float h) {
   float K[8], p[8], d[8];
-  lds8(cx.sK + (uint32_t)l * 32u, K);
-  lds8(cx.sP + (uint32_t)l * 32u, p);
-  ldc8((const float *)sd.dg + 8 * o, d);
+  lds_cells(cx.sK + (uint32_t)l * 4u, cx.S, K);
+  lds_cells(cx.sP + (uint32_t)l * 4u, cx.S, p);
+  res2_own(cx, cx.sD, cx.capD, l, (const float *)sd.dg, o, true, d);
   uint32_t aK[6], aP[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
-    const uint32_t off = (c & 0xFFFu) * 32u;
+    const uint32_t off = (c & 0xFFFu) * 4u;
     if (kCluster) {
       aK[k] = cl_map_s(cx.sK + off, c >> 12);
       aP[k] = cl_map_s(cx.sP + off, c >> 12);
@@ -2280,12 +2330,12 @@ __device__ __forceinline__ float res2_op_oct_fast(const Res2Ctx &cx, const Solve
 #pragma unroll
   for (int c = 0; c < 8; ++c) off[c] = 0.f;
   in_oct_faces(K, p, h, off);
-  res2_fast_face<0, kCluster>(aK[0], aP[0], h, K, off);
-  res2_fast_face<1, kCluster>(aK[1], aP[1], h, K, off);
-  res2_fast_face<2, kCluster>(aK[2], aP[2], h, K, off);
-  res2_fast_face<3, kCluster>(aK[3], aP[3], h, K, off);
-  res2_fast_face<4, kCluster>(aK[4], aP[4], h, K, off);
-  res2_fast_face<5, kCluster>(aK[5], aP[5], h, K, off);
+  res2_fast_face<0, kCluster>(aK[0], aP[0], cx.S, h, K, off);
+  res2_fast_face<1, kCluster>(aK[1], aP[1], cx.S, h, K, off);
+  res2_fast_face<2, kCluster>(aK[2], aP[2], cx.S, h, K, off);
+  res2_fast_face<3, kCluster>(aK[3], aP[3], cx.S, h, K, off);
+  res2_fast_face<4, kCluster>(aK[4], aP[4], cx.S, h, K, off);
+  res2_fast_face<5, kCluster>(aK[5], aP[5], cx.S, h, K, off);
   float local = 0.f, qv[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -2294,14 +2344,14 @@ __device__ __forceinline__ float res2_op_oct_fast(const Res2Ctx &cx, const Solve
     if (leaf) local = fmaf(p[c], q, local);
     qv[c] = leaf ? q : 0.f;
   }
-  st8((float *)sd.q + 8 * o, qv);
+  res2_own_store(cx, cx.sQ, cx.capD, l, (float *)sd.q, o, qv);
   return local;
 }
 
 // Step 2 on own oct o: the branch-free form when its row and every
 // neighbour's are in shared memory, else the general one.
-template <bool kCluster>
-__device__ __forceinline__ float res2_op_any(const Res2Ctx &cx, const SolveDev &sd, int o, float h) {
+template <bool kCluster, class Cx>
+__device__ __forceinline__ float res2_op_any(const Cx &cx, const SolveDev &sd, int o, float h) {
   const int l = o - cx.lo;
   if (l < cx.cap) {
     uint32_t w0, w1, w2, pad;
@@ -2320,26 +2370,28 @@ __device__ __forceinline__ float res2_op_any(const Res2Ctx &cx, const SolveDev &
 }
 
 // Step 1 on own oct o: p = z + beta p (first: p = z).
-__device__ __forceinline__ void res2_dir_oct(const Res2Ctx &cx, const SolveDev &sd, int o, bool first, float beta) {
+template <class Cx>
+__device__ __forceinline__ void res2_dir_oct(const Cx &cx, const SolveDev &sd, int o, bool first, float beta) {
   const int l = o - cx.lo;
   float z[8], p[8];
-  res2_own(cx, cx.sZ, l, (const float *)sd.z, o, true, z);
-  if (!first) res2_own(cx, cx.sP, l, (const float *)sd.p0, o, true, p);
+  res2_own(cx, cx.sZ, cx.cap, l, (const float *)sd.z, o, true, z);
+  if (!first) res2_own(cx, cx.sP, cx.cap, l, (const float *)sd.p0, o, true, p);
 #pragma unroll
   for (int c = 0; c < 8; ++c) p[c] = first ? z[c] : fmaf(beta, p[c], z[c]);
-  res2_own_store(cx, cx.sP, l, (float *)sd.p0, o, p);
+  res2_own_store(cx, cx.sP, cx.cap, l, (float *)sd.p0, o, p);
 }
 
 // Step 3 on own oct o: r = D z - alpha q, z = r / D, e += alpha p.
-__device__ __forceinline__ void res2_upd_oct(const Res2Ctx &cx, const SolveDev &sd, int o, float alpha, float &lrz,
+template <class Cx>
+__device__ __forceinline__ void res2_upd_oct(const Cx &cx, const SolveDev &sd, int o, float alpha, float &lrz,
                                              float &lrr) {
   const int l = o - cx.lo;
   float p[8], z[8], d[8], q[8], e[8];
-  res2_own(cx, cx.sP, l, (const float *)sd.p0, o, true, p);
-  res2_own(cx, cx.sZ, l, (const float *)sd.z, o, true, z);
-  ldc8((const float *)sd.dg + 8 * o, d);
-  ldc8((const float *)sd.q + 8 * o, q);
-  ldc8((const float *)sd.e + 8 * o, e);
+  res2_own(cx, cx.sP, cx.cap, l, (const float *)sd.p0, o, true, p);
+  res2_own(cx, cx.sZ, cx.cap, l, (const float *)sd.z, o, true, z);
+  res2_own(cx, cx.sD, cx.capD, l, (const float *)sd.dg, o, true, d);
+  res2_own(cx, cx.sQ, cx.capD, l, (const float *)sd.q, o, true, q);
+  res2_own(cx, cx.sE, cx.capD, l, (const float *)sd.e, o, true, e);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const float r = d[c] * z[c] - alpha * q[c];
@@ -2349,23 +2401,47 @@ __device__ __forceinline__ void res2_upd_oct(const Res2Ctx &cx, const SolveDev &
     z[c] = zn;
     e[c] += alpha * p[c];
   }
-  res2_own_store(cx, cx.sZ, l, (float *)sd.z, o, z);
-  st8((float *)sd.e + 8 * o, e);
+  res2_own_store(cx, cx.sZ, cx.cap, l, (float *)sd.z, o, z);
+  res2_own_store(cx, cx.sE, cx.capD, l, (float *)sd.e, o, e);
 }
 
 // The FP64 residual pass on own oct o (global arrays; the neighbours' x read
 // coherently), z into its shared row, D into global memory.
-__device__ __forceinline__ void res2_ref_oct(const Res2Ctx &cx, const SolveDev &sd, int o, bool want_x, Acc<float> &rr,
+template <class Cx>
+__device__ __forceinline__ void res2_ref_oct(const Cx &cx, const SolveDev &sd, int o, bool want_x, Acc<float> &rr,
                                              Acc<float> &xx, Acc<float> &rz) {
   float zo[8], dv[8];
   ref_oct_values<float, true>(sd, o, want_x, rr, xx, rz, zo, dv);
-  res2_own_store(cx, cx.sZ, o - cx.lo, (float *)sd.z, o, zo);
-  st8((float *)sd.dg + 8 * o, dv);
+  res2_own_store(cx, cx.sZ, cx.cap, o - cx.lo, (float *)sd.z, o, zo);
+  res2_own_store(cx, cx.sD, cx.capD, o - cx.lo, (float *)sd.dg, o, dv);
 }
 
-// One solve by one group, the CG state of its first octs in shared memory.
-template <bool kCluster>
-__device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
+// x += e, e = 0 on own oct o at the end of an inner solve (e in its shared
+// planes, or global beyond the capacity).
+template <class Cx>
+__device__ __forceinline__ void res2_xpe_oct(const Cx &cx, const SolveDev &sd, int o) {
+  const int l = o - cx.lo;
+  if (l >= cx.capD) {
+    res_xpe_oct<float>(sd, o);
+    return;
+  }
+  float e[8], z0[8];
+  double xv[8];
+  lds_cells(cx.sE + (uint32_t)l * 4u, cx.S, e);
+  ldc8(sd.x64 + 8 * o, xv);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    xv[c] += (double)e[c];
+    z0[c] = 0.f;
+  }
+  st8(sd.x64 + 8 * o, xv);
+  sts_cells(cx.sE + (uint32_t)l * 4u, cx.S, z0);
+}
+
+// One solve by one group, the CG state of its first octs in shared memory in
+// the layout Cx.
+template <bool kCluster, class Cx>
+__device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
   constexpr int wd = (int)(sizeof(SolveDev) / 8);
   for (int w = threadIdx.x; w < wd; w += blockDim.x)
     reinterpret_cast<unsigned long long *>(&sh.sd)[w] = reinterpret_cast<const unsigned long long *>(a.solves + s)[w];
@@ -2381,17 +2457,19 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
   __syncthreads();
   const SolveDev &sd = sh.sd;
   const int n = sd.n_oct;
-  Res2Ctx cx;
-  cx.cap = a.cap;  // octs per CTA kept in shared memory (the dynamic allocation holds that many rows)
+  Cx cx;
   cx.chunk = (int)((n + (int)cs - 1) / (int)cs);
+  const bool six = Cx::capD > 0;
   cx.lo = min(n, (int)cr * cx.chunk);
   cx.cr = cr;
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(res2_smem);
-  const uint32_t rows = (uint32_t)cx.cap + 1u;  // row `cap` of K, z and p: the stand-in neighbour
   cx.sK = base;
-  cx.sZ = base + rows * 32u;
-  cx.sP = base + 2u * rows * 32u;
-  cx.sC = base + 3u * rows * 32u;
+  cx.sZ = base + 8u * cx.S;
+  cx.sP = base + 16u * cx.S;
+  cx.sD = base + 24u * cx.S;  // the six-array layout only
+  cx.sQ = base + 32u * cx.S;
+  cx.sE = base + 40u * cx.S;
+  cx.sC = base + (six ? 48u : 24u) * cx.S;
   const int hi = min(n, cx.lo + cx.chunk);
   const int o0 = cx.lo + (int)threadIdx.x, stride = (int)blockDim.x;
   // stage in: K and the neighbour codes of the octs kept in shared memory
@@ -2404,16 +2482,22 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
       m1[c] = -1.f;
       z0[c] = 0.f;
     }
-    sts8(cx.sK + (uint32_t)cx.cap * 32u, m1);
-    sts8(cx.sZ + (uint32_t)cx.cap * 32u, z0);
-    sts8(cx.sP + (uint32_t)cx.cap * 32u, z0);
+    sts_cells(cx.sK + (uint32_t)cx.cap * 4u, cx.S, m1);
+    sts_cells(cx.sZ + (uint32_t)cx.cap * 4u, cx.S, z0);
+    sts_cells(cx.sP + (uint32_t)cx.cap * 4u, cx.S, z0);
   }
   const uint16_t code_none = (uint16_t)((cr << 12) | (unsigned)cx.cap);
   for (int o = o0; o < hi && o - cx.lo < cx.cap; o += stride) {
     const int l = o - cx.lo;
     float K[8];
     ld8_ro((const float *)sd.KT + 8 * o, K);
-    sts8(cx.sK + (uint32_t)l * 32u, K);
+    sts_cells(cx.sK + (uint32_t)l * 4u, cx.S, K);
+    if (l < cx.capD) {  // the correction of the first inner solve starts at zero
+      float z0[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) z0[c] = 0.f;
+      sts_cells(cx.sE + (uint32_t)l * 4u, cx.S, z0);
+    }
     int g[6];
     load_nbr6(sd.nbr, o, g);
     check_nbr6(g, sd.n_oct);
@@ -2431,7 +2515,7 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
   }
   const float h = (float)sd.h;
   const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
-  const bool fp32s = a.fp32_scalars != 0;
+  const bool f32 = a.cg_scalars == 0;
   for (;;) {
     const int phase = sh.st.phase;
     if (phase == kDone) break;
@@ -2463,9 +2547,11 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
         } else {
           st.phase = kInner;
           st.rz = rz;
+          st.rzf = (float)rz;
           st.first = 1;
           st.inner_iters = 0;
           st.inner_target = fmax(sd.inner_rtol * rnorm, sd.final_safety * target);
+          st.t2f = (float)(st.inner_target * st.inner_target);
         }
       }
       __syncthreads();
@@ -2474,7 +2560,7 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
     // step 1: the new direction on the own octs, then every CTA waits
     {
       const bool first = sh.st.first != 0;
-      const float beta = (float)sh.st.beta;
+      const float beta = sh.st.betaf;
       for (int o = o0; o < hi; o += stride) res2_dir_oct(cx, sd, o, first, beta);
       group_barrier<kCluster>();
     }
@@ -2485,22 +2571,16 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
       group_sum<float, 1, kCluster>(acc, sh, buf, tot);
       if (threadIdx.x == 0) {
         ResState &st = sh.st;
-        const double pq = tot[0].get();
         st.n_op += 1;
         st.n_first += st.first ? 1 : 0;
-        if (!(st.rz >= 0.0) || !isfinite(st.rz) || !(pq > 0.0) || !isfinite(pq)) {
-          st.status = ATS_ERR_BREAKDOWN;
-          st.phase = kDone;
-        } else {
-          st.alpha = cg_ratio(st.rz, pq, fp32s);
-        }
+        cg_alpha(st, tot[0], f32);
       }
       __syncthreads();
     }
     if (sh.st.phase == kDone) break;
     // step 3: e += alpha p, r = D z - alpha q, z = D^-1 r; sums r.z, r.r
     {
-      const float alpha = (float)sh.st.alpha;
+      const float alpha = sh.st.alphaf;
       Acc<float> acc[2], tot[2];
       for (int o = o0; o < hi; o += stride) {
         float lrz = 0.f, lrr = 0.f;
@@ -2511,13 +2591,10 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
       group_sum<float, 2, kCluster>(acc, sh, buf, tot);
       if (threadIdx.x == 0) {
         ResState &st = sh.st;
-        const double rz_new = tot[0].get(), rr = tot[1].get();
         st.iters += 1;
         st.inner_iters += 1;
         st.first = 0;
-        st.beta = cg_ratio(rz_new, st.rz, fp32s);
-        st.rz = rz_new;
-        const bool conv = rr <= st.inner_target * st.inner_target || rz_new == 0.0;
+        const bool conv = cg_beta(st, tot[0], tot[1], f32);
         if (conv) {
           st.phase = kRefine;
         } else if (st.iters >= sd.max_iter) {
@@ -2532,7 +2609,7 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
       __syncthreads();
     }
     if (sh.st.phase == kRefine) {
-      for (int o = o0; o < hi; o += stride) res_xpe_oct<float>(sd, o);
+      for (int o = o0; o < hi; o += stride) res2_xpe_oct(cx, sd, o);
       group_barrier<kCluster>();
     }
   }
@@ -2563,6 +2640,18 @@ __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &b
       atomicAdd(a.cells + 3, N * (unsigned long long)st.n_xpe);
     }
   }
+}
+
+// One solve by one group: all six arrays in shared memory when the CTA's
+// share fits, else K, z and p (the share's size decides, the arithmetic is
+// the same).
+template <bool kCluster>
+__device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
+  const unsigned cs = kCluster ? cl_size() : 1u;
+  const int n = a.solves[s].n_oct;
+  const int chunk = (int)((n + (int)cs - 1) / (int)cs);
+  if (chunk <= kRes2Cap6) res2_solve_l<kCluster, Res2Six>(a, s, sh, buf);
+  else res2_solve_l<kCluster, Res2Three>(a, s, sh, buf);
 }
 
 __device__ void res2_cta_loop(const ResArgs &a, ResShared<float> &sh, int &buf) {
@@ -2669,7 +2758,7 @@ static int res_cta_blocks_t() {
 
 template <int NT>
 static cudaError_t res2_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
-  const size_t smem = res2_smem_bytes(a.cap);
+  const size_t smem = kRes2SmemBytes;
   if (a.n_cq > 0 && !cta_only) {
     cudaError_t e = cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && cluster > 8)
@@ -2697,7 +2786,8 @@ static cudaError_t res2_launch_t(int cluster, int grid, const ResArgs &a, cudaSt
 
 template <int NT>
 static int res2_clusters_t(int cluster, int cap) {
-  const size_t smem = res2_smem_bytes(cap);
+  (void)cap;
+  const size_t smem = kRes2SmemBytes;
   if (cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       (cluster > 8 &&
        cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
@@ -2723,8 +2813,8 @@ static int res2_clusters_t(int cluster, int cap) {
   return n;
 }
 
-// The largest capacity (octs per CTA, at most 4093) whose rows fit the
-// shared memory a CTA can have beside the kernels' static shared memory.
+// kRes2Cap3 when the layouts fit the shared memory a CTA can have beside the
+// kernels' static shared memory, else 0 (the shared-memory form is then off).
 template <int NT>
 static int res2_cap_t(int device) {
   int optin = 0;
@@ -2735,14 +2825,13 @@ static int res2_cap_t(int device) {
     cudaGetLastError();
     return 0;
   }
-  const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes) + res2_smem_bytes(0);
-  if ((size_t)optin <= stat) return 0;
-  return (int)std::min<size_t>(4093, ((size_t)optin - stat) / kRes2OctBytes);
+  const size_t stat = std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
+  return (size_t)optin >= stat + kRes2SmemBytes ? kRes2Cap3 : 0;
 }
 
 cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
   if (a.n_cq + a.n_tq <= 0) return cudaSuccess;
-  if (cluster < 1 || cluster > kMaxCluster || grid <= 0 || a.cap <= 0 || a.cap > 4093) return cudaErrorInvalidValue;
+  if (cluster < 1 || cluster > kMaxCluster || grid <= 0 || a.cap != kRes2Cap3) return cudaErrorInvalidValue;
   return threads >= 512 ? res2_launch_t<512>(cluster, grid, a, st, cta_only)
                         : res2_launch_t<256>(cluster, grid, a, st, cta_only);
 }

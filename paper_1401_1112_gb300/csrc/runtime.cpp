@@ -285,7 +285,7 @@ void fill_defaults(ats_solve_opts *o) {
   o->res_cluster = 0;
   o->res_cta_octs = 0;
   o->res_max_octs = 0;
-  o->fp32_scalars = 0;
+  o->cg_scalars = 0;
   o->res_state = 0;
 }
 
@@ -548,7 +548,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     const int64_t max_octs = o.sched == ATS_SCHED_RESIDENT
                                  ? INT64_MAX
                                  : (o.res_max_octs > 0 ? o.res_max_octs : (P->fp64 ? 2048 : 16384));
-    const double big_work = o.res_big_work > 0 ? (double)o.res_big_work : 80000.0;
+    const double big_work = o.res_big_work > 0 ? (double)o.res_big_work : 50000.0;
     P->res_smem = !P->fp64 && o.res_state == 0;
     if (P->res_smem) {
       P->res_cap = resident_smem_cap(P->res_threads, ctx->device);
@@ -708,7 +708,7 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   ra.n_tq = P->n_tq;
   ra.tq_head = P->d_heads + 2;
   ra.n_solves = P->n;
-  ra.fp32_scalars = P->opts.fp32_scalars ? 1 : 0;
+  ra.cg_scalars = P->opts.cg_scalars ? 1 : 0;
   ra.cells = prof ? P->d_cells + kCellCounters : nullptr;
   if (prof && !P->d_tsolve) {
     ats_status sa = dev_alloc_t(P->ctx, 2 * (size_t)P->n, &P->d_tsolve);

@@ -209,21 +209,25 @@ def test_batch_alone_and_in_batch_bitwise(ats, ctx, prec):
         L.close()
 
 
-def test_fp32_scalars_variant(ats, ctx):
-    """Mixed precision with alpha and beta formed from FP32-rounded totals
-    (the tick path's form) still refines to the certificate and matches."""
+def test_cg_scalars_in_fp32_or_fp64(ats, ctx):
+    """Mixed precision with the CG step's alpha, beta and inner test from the
+    dot totals rounded to FP32 (default) or in FP64: both refine to the
+    certificate and match the oracle, and the iteration counts stay close."""
     rng = np.random.default_rng(515)
     for o in (40, 3000):
         lv, st = W.random_box_solve(rng, o, dt_lo=10.0, dt_hi=100.0, robin=True)
         xr = _oracle_x(lv, st)
         L = ats.Level(ctx, lv)
         L.build(st.dt, st.K, st.E, **_faces(st))
-        for f32 in (0, 1):
+        its = []
+        for cs in (0, 1):
             x = st.E.copy()
             code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
-                                  sched=ats.ATS_SCHED_RESIDENT, fp32_scalars=f32)
+                                  sched=ats.ATS_SCHED_RESIDENT, cg_scalars=cs)
             assert code == 0, stats
             assert _rel(x, xr) <= PAR
+            its.append(stats["iterations"])
+        assert abs(its[0] - its[1]) <= max(3, 0.05 * its[1])
         L.close()
 
 

@@ -71,3 +71,14 @@ def test_served_requests_recipe():
     assert cells.min() >= 16 ** 3 * (1 - 1e-12) and cells.max() <= 256 ** 3 * (1 + 1e-12)
     tols = [r["tol"] for r in reqs]
     assert set(tols) == {1e-6, 1e-10} and 0.45 < tols.count(1e-6) / len(tols) < 0.55
+
+
+def test_box_wall_faces_equal_the_general_search():
+    """The analytic wall faces of a box equal the general ghost-face search
+    (same faces, same (cell, dir) order)."""
+    for dims in ((1, 1, 1), (3, 5, 7), (9, 2, 4), (8, 8, 8)):
+        xyz = W.box_octs(*dims)
+        c1, d1, _ = W.ghost_faces(xyz, None)
+        c2, d2 = W.box_wall_faces(xyz, *dims)
+        np.testing.assert_array_equal(c1, c2)
+        np.testing.assert_array_equal(d1, d2)

@@ -160,6 +160,27 @@ def box_octs(nox: int, noy: int, noz: int, origin=(0, 0, 0)) -> np.ndarray:
     return xyz[morton_sort(xyz)]
 
 
+def box_wall_faces(oct_xyz: np.ndarray, nox: int, noy: int, noz: int):
+    """The faces of a full box of octs (all cells leaves) that lie on its
+    walls, as ``ghost_faces`` lists them (cell int64[n], dir int64[n], sorted
+    by (cell, dir)), found from the cell coordinates instead of a search."""
+    ext = (2 * nox, 2 * noy, 2 * noz)
+    o = oct_xyz.astype(np.int64)
+    cells, dirs = [], []
+    for c in range(8):
+        bit = (c & 1, (c >> 1) & 1, (c >> 2) & 1)
+        for d in range(6):
+            a, side = d >> 1, d & 1
+            coord = 2 * o[:, a] + bit[a]
+            on = np.nonzero(coord == (ext[a] - 1 if side else 0))[0]
+            cells.append(8 * on + c)
+            dirs.append(np.full(on.size, d, dtype=np.int64))
+    cell = np.concatenate(cells)
+    dr = np.concatenate(dirs)
+    order = np.lexsort((dr, cell))
+    return cell[order], dr[order]
+
+
 def box_level(nox, noy, noz, dx, walls=None) -> LevelDesc:
     """A single-level box of octs.  ``walls`` is None (all zero-flux) or a list
     of 6 (kind, alpha) tuples or None per direction (None = zero-flux wall);
@@ -169,7 +190,7 @@ def box_level(nox, noy, noz, dx, walls=None) -> LevelDesc:
     lv = LevelDesc(xyz, None, float(dx), *(np.zeros(0, dtype=t) for t in (np.int32, np.int8, np.int8, np.int8, np.float64)))
     if walls is None:
         return lv
-    cell, dr, _ = ghost_faces(xyz, None)
+    cell, dr = box_wall_faces(xyz, nox, noy, noz)
     keep = np.array([walls[d] is not None for d in dr], dtype=bool)
     cell, dr = cell[keep], dr[keep]
     kind = np.array([walls[d][0] for d in dr], dtype=np.int8)
