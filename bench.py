@@ -476,6 +476,15 @@ def run_ours(args, rank, world, local):
     serve = None
     if rank == 0 and not args.no_serve:
         serve = run_serve(args, ats, local)
+        if e2e is not None:
+            # the served stream is measured end to end through the public
+            # serving calls (submit / wait, host arrays): its latencies travel
+            # with the end-to-end figure
+            e2e["served"] = {k: serve[k] for k in ("requests", "of", "throughput", "p50_ms", "p99_ms",
+                                                   "arrival_rate_per_s")}
+            e2e["served"]["fp64_per_solve"] = {k: serve["fp64_per_solve"][k]
+                                               for k in ("throughput", "p50_ms", "p99_ms")}
+            e2e["served"]["oracle_check_ok"] = all(c["within_bound"] for c in serve["oracle_check"])
 
     amr = None
     if rank == 0 and not args.no_amr:
@@ -560,40 +569,47 @@ def run_ours(args, rank, world, local):
     }
 
 
-def run_amr_interfaces(ats, ctx, coarse_steps=3, use_graph=2, check_every=16):
+def run_amr_interfaces(ats, ctx, coarse_steps=3, check_every=16):
     """The two-level workload (base 64^3, level 1 on the central 1/8 of the
     volume, Gaussian pulse, constant K, fine first) with each row of the
     coarse-to-fine faces: time per coarse step (two fine solves and one
-    coarse solve, mixed precision, certified 5e-11) and the relative change
-    of the total energy per step (zero-flux walls: only the interfaces can
-    change it; the Neumann rows with the stored flux conserve it)."""
+    coarse solve, mixed precision, certified 5e-11) as one captured graph
+    (use_graph = 3) and with deferred solves (use_graph = 2), and the
+    relative change of the total energy per step (zero-flux walls: only the
+    interfaces can change it; the Neumann rows with the stored flux conserve
+    it)."""
     levels, states, dt = W.two_level_gaussian_64cube(n0=64)
 
     def energy(H):
         return sum(float(np.sum(H.state(l)[lv.leaf_cells()])) * lv.dx ** 3 for l, lv in enumerate(levels))
 
     out = {"workload": "two-level heat: 64^3 base + 64^3 fine cells on the central 1/8, fine first",
-           "coarse_steps": coarse_steps, "use_graph": use_graph, "check_every": check_every}
+           "coarse_steps": coarse_steps, "use_graph": 3, "check_every": check_every}
     for name, kind, alpha in (("dirichlet", ats.ATS_FACE_DIRICHLET, 1.0), ("neumann", ats.ATS_FACE_NEUMANN, 0.0),
                               ("robin_0.5", ats.ATS_FACE_ROBIN, 0.5)):
-        H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
-        H.set_interface(kind, alpha)
-        for l, (E, K) in enumerate(states):
-            H.set_state(l, E, K)
-        opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=use_graph,
-                    check_every=check_every)
-        H.advance(0, dt, **opts)  # warm-up step (plans, graphs)
-        e0 = energy(H)
-        t0 = time.perf_counter()
-        for _ in range(coarse_steps):
-            code, _ = H.advance(0, dt, **opts)
-            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
-                raise RuntimeError(f"amr {name} step failed: {code}")
-        t_s = time.perf_counter() - t0
-        e1 = energy(H)
-        out[name] = {"ms_per_coarse_step": round(t_s / coarse_steps * 1e3, 3),
-                     "energy_change_per_step": float((e1 - e0) / e0 / coarse_steps)}
-        H.close()
+        row = {}
+        for ug, key in ((3, "ms_per_coarse_step"), (2, "ms_per_coarse_step_deferred")):
+            H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
+            H.set_interface(kind, alpha)
+            for l, (E, K) in enumerate(states):
+                H.set_state(l, E, K)
+            opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=ug,
+                        check_every=check_every)
+            H.advance(0, dt, **opts)  # warm-up step (plans, device loops; with 3 the step's capture)
+            e0 = energy(H)
+            t0 = time.perf_counter()
+            for _ in range(coarse_steps):
+                code, _ = H.advance(0, dt, **opts)
+                if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
+                    raise RuntimeError(f"amr {name} step failed: {code}")
+            t_s = time.perf_counter() - t0
+            e1 = energy(H)
+            row[key] = round(t_s / coarse_steps * 1e3, 3)
+            if ug == 3:
+                row["energy_change_per_step"] = float((e1 - e0) / e0 / coarse_steps)
+                row["graph"] = H.graph_stats()
+            H.close()
+        out[name] = row
     return out
 
 
@@ -601,35 +617,41 @@ def run_fld_amr(ats, ctx, coarse_steps=3):
     """The radiation-matter workload: base 128^3 and three refined levels
     (density above 4^(l+1) x the mean), flux-limited coefficients from each
     level's E^n, linearised gas coupling, fine levels first, mixed precision
-    certified to 5e-11 per level solve, the device-driven coarse step: time
-    per coarse step (15 level solves) and the solve statistics."""
+    certified to 5e-11 per level solve: time per coarse step (15 level
+    solves) as one captured graph (use_graph = 3) and with deferred solves
+    (use_graph = 2), and the solve statistics."""
     levels, states, k0, cfl = W.radiation_matter_amr(n0=128)
     rho = [s[1] for s in states]
-    H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
-    try:
-        for l, (E, r, t) in enumerate(states):
-            H.set_state(l, E, np.ones_like(E))
-        for l, (E, r, t) in enumerate(states):
-            H.set_fld(l, r, t, k0)
-        kmed = np.median((1.0 / 3.0) / (k0 * rho[0] ** 2))
-        dt = cfl * levels[0].dx ** 2 / (2.0 * kmed)
-        opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=2)
-        code, st = H.advance(0, dt, **opts)  # warm-up (plans, graphs)
-        if code < 0:
-            raise RuntimeError(f"fld warm-up step failed: {code}")
-        its = 0
-        t0 = time.perf_counter()
-        for _ in range(coarse_steps):
-            code, st = H.advance(0, dt, **opts)
-            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
-                raise RuntimeError(f"fld coarse step failed: {code}")
-            its += st["iterations"]
-        el = time.perf_counter() - t0
-    finally:
-        H.close()
+    kmed = np.median((1.0 / 3.0) / (k0 * rho[0] ** 2))
+    dt = cfl * levels[0].dx ** 2 / (2.0 * kmed)
+    res = {}
+    for ug in (3, 2):
+        H = ats.Hierarchy(ctx, levels, ats.ATS_ORDER_FINE_FIRST)
+        try:
+            for l, (E, r, t) in enumerate(states):
+                H.set_state(l, E, np.ones_like(E))
+            for l, (E, r, t) in enumerate(states):
+                H.set_fld(l, r, t, k0)
+            opts = dict(tol=5e-11, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=ug)
+            code, st = H.advance(0, dt, **opts)  # warm-up (plans, device loops; with 3 the step's capture)
+            if code < 0:
+                raise RuntimeError(f"fld warm-up step failed: {code}")
+            its = 0
+            t0 = time.perf_counter()
+            for _ in range(coarse_steps):
+                code, st = H.advance(0, dt, **opts)
+                if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
+                    raise RuntimeError(f"fld coarse step failed: {code}")
+                its += st["iterations"]
+            el = time.perf_counter() - t0
+            res[ug] = (el, its, H.graph_stats())
+        finally:
+            H.close()
+    el, its, graph = res[3]
     return {"workload": "4-level AMR radiation-matter: base 128^3 + %s cells, 15 level solves per coarse step, "
                         "fine first" % "/".join(str(lv.n_cell) for lv in levels[1:]),
-            "coarse_steps": coarse_steps, "ms_per_coarse_step": round(el / coarse_steps * 1e3, 3),
+            "coarse_steps": coarse_steps, "use_graph": 3, "ms_per_coarse_step": round(el / coarse_steps * 1e3, 3),
+            "ms_per_coarse_step_deferred": round(res[2][0] / coarse_steps * 1e3, 3), "graph": graph,
             "cg_iterations_per_coarse_step": its / coarse_steps,
             "cells_per_coarse_step": int(sum(lv.n_cell * 2 ** l for l, lv in enumerate(levels)))}
 
@@ -689,79 +711,146 @@ def run_dirac(ats, ctx, n_steps=64):
     return out
 
 
+def _serve_oracle_check(job):
+    """Oracle solution of one served request and its distance to the served
+    result: both stop on the residual rule (the served one on ||r|| <= tol
+    ||r0||, the oracle to a certified 1e-12), and lambda_min >= 1 bounds each
+    solution's distance to the exact one by its residual."""
+    (lv, st), x, res_norm = job
+    import oracle
+
+    S = oracle.assemble(lv, st.dt, st.K, st.E, face_K=st.face_K, face_E=st.face_E, face_F=st.face_F)
+    xr, info = oracle.pcg(S, st.E, tol=1e-12, stop_rule=oracle.STOP_CERTIFIED)
+    err = float(np.linalg.norm(x - xr))
+    bound = float(res_norm + info["residual"])
+    return {"cells": int(lv.n_cell), "abs_err": err, "bound": bound, "rel_err": err / float(np.linalg.norm(xr)),
+            "within_bound": bool(err <= 1.0001 * bound + 1e-14 * float(np.linalg.norm(xr)))}
+
+
 def run_serve(args, ats, device):
-    """Served request stream: Poisson arrivals of level solves (sizes
-    log-uniform 16^3 .. serve_max_cells, Dirichlet / Neumann / Robin walls,
-    tol 1e-6 or 1e-10), arrival rate 0.8 x the plain per-solve FP64 GPU
-    capacity measured on the same requests; continuous-batching server in
-    mixed precision.  Reports p50 / p99 latency and throughput of the server,
-    and of the plain FP64 path serving the same arrivals one at a time
-    (measured service times, FIFO queue)."""
+    """Served request stream (the served workload: Poisson arrivals of level
+    solves, cells log-uniform 16^3 .. serve_max_cells, Dirichlet / Neumann /
+    Robin walls, tol 1e-6 or 1e-10 on the residual rule; the first
+    serve_requests requests of its 2 000).  The requests are built on every
+    host core before anything is timed.  Then:
+      * the plain per-solve FP64 path's service time for each request (level
+        creation, operator build and solve, one at a time) gives its capacity,
+        and the arrivals are paced at 0.8 x that capacity;
+      * the continuous-batching server (mixed precision) serves the arrivals,
+        with the serve_budget_gb device budget and again with a 4 GB budget
+        (admission limited by memory);
+      * the plain per-solve FP64 path serves the same arrivals for real: one
+        request at a time in arrival order, each started when it has arrived
+        and the previous one is done;
+      * a sample of served results (the smallest request, a median one and the
+        smallest of at least 128^3 cells) is checked against the oracle.
+    Reports p50 / p99 latency (submission to result) and throughput."""
+    import multiprocessing as mp
     import threading
 
     reqs = W.served_requests(n_req=args.serve_requests, seed=1405, hi_cells=args.serve_max_cells)
-    built = [W.build_request(r) for r in reqs]
-    # plain per-solve FP64: service time of every request (build + solve)
+    t_build = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, min(len(reqs), os.cpu_count() or 1))) as pool:
+        built = pool.map(W.build_request, reqs, chunksize=1)
+    build_s = time.perf_counter() - t_build
+
+    def fp64_serve_one(ctx, k):
+        lv, st = built[k]
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, face_E=st.face_E, face_F=st.face_F)
+        x = st.E.copy()
+        code, _ = L.solve(x, tol=reqs[k]["tol"], precision=ats.ATS_PREC_FP64)
+        L.close()
+        if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
+            raise RuntimeError("fp64 served solve failed")
+
+    # plain per-solve FP64: service time of every request (level, build, solve)
     svc = []
     with ats.Context(device) as ctx:
-        for (lv, st), r in zip(built, reqs):
-            L = ats.Level(ctx, lv)
-            x = st.E.copy()
+        fp64_serve_one(ctx, 0)  # warm-up
+        for k in range(len(reqs)):
             t0 = time.perf_counter()
-            L.build(st.dt, st.K, st.E, face_E=st.face_E, face_F=st.face_F)
-            code, _ = L.solve(x, tol=r["tol"], precision=ats.ATS_PREC_FP64)
+            fp64_serve_one(ctx, k)
             svc.append(time.perf_counter() - t0)
-            L.close()
-            if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
-                raise RuntimeError("fp64 serve baseline failed")
     svc = np.array(svc)
     cap = len(svc) / svc.sum()
     lam = 0.8 * cap
     arrivals = np.array([r["t"] for r in reqs]) * (reqs[-1]["id"] + 1) / reqs[-1]["t"] / lam
-    # FIFO single server with the measured FP64 service times (Lindley recursion)
-    fin = np.zeros(len(svc))
-    free = 0.0
-    for i, (a, sv) in enumerate(zip(arrivals, svc)):
-        start = max(a, free)
-        free = start + sv
-        fin[i] = free
-    lat64 = (fin - arrivals) * 1e3
-    # the continuous-batching server on the same arrivals
-    srv = ats.Server(device, mem_budget_bytes=int(args.serve_budget_gb * (1 << 30)), precision=ats.ATS_PREC_MIXED,
-                     check_every=4)
-    tickets = [None] * len(reqs)
-    t_start = time.perf_counter()
 
-    def submitter():
+    def server_run(budget_bytes, keep_x):
+        srv = ats.Server(device, mem_budget_bytes=int(budget_bytes), precision=ats.ATS_PREC_MIXED, check_every=4)
+        tickets = [None] * len(reqs)
+        t_start = time.perf_counter()
+
+        def submitter():
+            for k, ((lv, st), r) in enumerate(zip(built, reqs)):
+                delay = arrivals[k] - (time.perf_counter() - t_start)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[k] = srv.submit(lv, st, tol=r["tol"])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, xs, rn = [], {}, {}
+        errs = 0
         for k, ((lv, st), r) in enumerate(zip(built, reqs)):
+            while tickets[k] is None:
+                time.sleep(0.0002)
+            code, x, res = srv.wait(tickets[k], lv.n_cell)
+            errs += code < 0
+            lat.append(res["latency_us"] / 1e3)
+            if k in keep_x:
+                xs[k] = x
+                rn[k] = res["stats"]["res_norm"]
+        t_end = time.perf_counter()
+        th.join()
+        st_srv = srv.stats()
+        srv.close()
+        lat = np.array(lat)
+        return {"throughput": round(len(reqs) / (t_end - t_start), 2), "unit": UNIT,
+                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "errors": int(errs), "peak_resident": st_srv["peak_resident"],
+                "budget_gb": round(budget_bytes / (1 << 30), 1)}, xs, rn
+
+    sizes = np.array([lv.n_cell for lv, _ in built])
+    order = np.argsort(sizes)
+    sample = {int(order[0]), int(order[len(order) // 2])}
+    big = [k for k in order if sizes[k] >= 128 ** 3]
+    if big:
+        sample.add(int(big[0]))
+    served, xs, rn = server_run(args.serve_budget_gb * (1 << 30), sample)
+    served_small, _, _ = server_run(4 * (1 << 30), set())
+
+    # the plain per-solve FP64 path serving the same arrivals, one at a time
+    fin = np.zeros(len(reqs))
+    with ats.Context(device) as ctx:
+        fp64_serve_one(ctx, 0)  # warm-up
+        t_start = time.perf_counter()
+        for k in range(len(reqs)):
             delay = arrivals[k] - (time.perf_counter() - t_start)
             if delay > 0:
                 time.sleep(delay)
-            tickets[k] = srv.submit(lv, st, tol=r["tol"])
+            fp64_serve_one(ctx, k)
+            fin[k] = time.perf_counter() - t_start
+        t_end = time.perf_counter()
+    lat64 = (fin - arrivals) * 1e3
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    lat = []
-    errs = 0
-    for k, ((lv, st), r) in enumerate(zip(built, reqs)):
-        while tickets[k] is None:
-            time.sleep(0.0002)
-        code, x, res = srv.wait(tickets[k], lv.n_cell)
-        errs += code < 0
-        lat.append(res["latency_us"] / 1e3)
-    t_end = time.perf_counter()
-    th.join()
-    st_srv = srv.stats()
-    srv.close()
-    lat = np.array(lat)
+    checks = []
+    if not args.no_cpu:
+        with mp.get_context("spawn").Pool(max(1, len(sample))) as pool:
+            checks = pool.map(_serve_oracle_check, [(built[k], xs[k], rn[k]) for k in sorted(sample)], chunksize=1)
+
     return {
-        "requests": len(reqs), "max_cells": int(args.serve_max_cells), "arrival_rate_per_s": round(lam, 2),
-        "throughput": round(len(reqs) / (t_end - t_start), 2), "unit": UNIT,
-        "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-        "errors": int(errs), "peak_resident": st_srv["peak_resident"],
-        "fp64_per_solve": {"capacity": round(cap, 2), "p50_ms": round(float(np.percentile(lat64, 50)), 3),
+        "requests": len(reqs), "of": 2000, "max_cells": int(args.serve_max_cells),
+        "cells_mean": round(float(sizes.mean())), "build_s": round(build_s, 1),
+        "arrival_rate_per_s": round(lam, 2), **served,
+        "budget_4gb": served_small,
+        "fp64_per_solve": {"capacity": round(cap, 2), "throughput": round(len(reqs) / (t_end - t_start), 2),
+                           "p50_ms": round(float(np.percentile(lat64, 50)), 3),
                            "p99_ms": round(float(np.percentile(lat64, 99)), 3),
-                           "note": "plain FP64 solves one at a time, FIFO on the same arrivals (measured service times)"},
+                           "path": "plain per-solve FP64 (level, build, solve), one request at a time in arrival "
+                                   "order on the same arrivals"},
+        "oracle_check": checks,
     }
 
 
@@ -1004,7 +1093,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--res-max-octs", type=int, default=32768,
                     help="levels up to this many octs take the resident solver (0 = the library default)")
-    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-requests", type=int, default=240,
+                    help="requests of the served stream's 2 000 (the first N, same arrival process)")
     ap.add_argument("--serve-max-cells", type=int, default=256 ** 3)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()

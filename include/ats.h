@@ -143,7 +143,7 @@ typedef struct {
                      /* about one item per CTA of the stencil kernel's grid, */
                      /* 256..1024; ats_batch_autotune tunes it per batch)    */
   int check_every;   /* ticks between host convergence polls (0 = 16)       */
-  int use_graph;     /* 1 = each poll interval of check_every ticks is one CUDA graph, the host polls between intervals; 2 = the whole tick loop is one graph (a WHILE conditional node over one interval, ended on the device when no solve is active), the host waits once (with profiling on, 2 runs as 1) */
+  int use_graph;     /* 1 = each poll interval of check_every ticks is one CUDA graph, the host polls between intervals; 2 = the whole tick loop is one graph (a WHILE conditional node over one interval, ended on the device when no solve is active), the host waits once (with profiling on, 2 runs as 1); 3 = as 2 for a solve, and for ats_level_advance the whole step as one graph (see there) */
   int mem;           /* ATS_MEM_HOST / ATS_MEM_DEVICE for x (and rhs)        */
   int x0;            /* ATS_X0_*: where the initial guess comes from          */
   int sched;         /* ATS_SCHED_*: tick path or resident solver (0 = AUTO)  */
@@ -307,8 +307,9 @@ typedef struct {
   int launches;              /* tick-kernel launches                              */
   int ticks;                 /* ticks enqueued                                    */
   double res_ms, res_bytes;  /* resident solver launch (all its steps) and the    */
-                             /* algorithmic bytes of its steps, counted per step  */
-                             /* kind as for the tick kernels                      */
+                             /* method's minimal traffic over them: 10 words per  */
+                             /* cell and CG iteration, 5 FP64 words per cell and  */
+                             /* refinement pass (most of it stays on chip)        */
   int res_launches;          /* resident-solver launches                          */
   int res_solves;            /* solves taken by the resident solver               */
   double res_span_ms;        /* first resident solve's start to the last one's end */
@@ -438,9 +439,26 @@ ats_status ats_hierarchy_get_state(ats_hierarchy *h, int level, double *E, int m
  * ATS_ORDER_COARSE_FIRST this level is solved first, then the finer levels
  * take their substeps with this level's value linear in time.  Every solve is
  * ats_solve with opts; stats accumulates iterations over all solves and keeps
- * the worst status and residuals. */
+ * the worst status and residuals.
+ * opts->use_graph = 2: every level solve's tick loop is one graph launch and
+ * no solve is waited for; the step's result records are read once at its end.
+ * opts->use_graph = 3: the whole step -- restriction, ghost gathers, operator
+ * builds, the level solves with their device loops, flux stores and the
+ * copy of the result records -- is one graph: one launch and one host wait
+ * per step.  A call takes the step as with 2 and then captures it when no
+ * graph is held for the same level, dt and options, or when the hierarchy's
+ * configuration (set_interface, set_fld, set_power_law) or the context's
+ * device allocations changed since the capture; every other call replays the
+ * graph.  The results are bitwise those of use_graph = 2.  A step whose
+ * solves fail is not captured; a failure in a replayed step is reported as
+ * with 2.  If the capture itself fails, the step has still been taken and the
+ * call returns ATS_ERR_CUDA. */
 ats_status ats_level_advance(ats_hierarchy *h, int level, double dt, const ats_solve_opts *opts,
                              ats_solve_stats *stats);
+/* The step graph of use_graph = 3: *held = 1 while a captured step is kept;
+ * *captures / *replays: steps captured / replayed since the hierarchy was
+ * created.  Any output pointer may be NULL. */
+ats_status ats_hierarchy_graph_stats(ats_hierarchy *h, int *held, int64_t *captures, int64_t *replays);
 /* Host-only (no device): the interface faces the hierarchy derives for one
  * level.  Call with NULL arrays to get n_face first.  rel is ATS_REL_FINER
  * (src_cell = refined cell of the same level), ATS_REL_COARSER (src_cell =

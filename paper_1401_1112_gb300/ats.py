@@ -169,6 +169,8 @@ _SIGS = [
     ("ats_level_advance", ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ats_solve_opts),
                                          ctypes.POINTER(ats_solve_stats)]),
     ("ats_hierarchy_set_fld", ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_double, ctypes.c_int]),
+    ("ats_hierarchy_graph_stats", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_int64)]),
     ("ats_hierarchy_get_temperature", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
     ("ats_hierarchy_set_power_law", ctypes.c_int, [P, ctypes.c_double, ctypes.c_double]),
     ("ats_hierarchy_plan_faces", ctypes.c_int, [ctypes.POINTER(ats_hierarchy_desc), ctypes.c_int,
@@ -606,6 +608,14 @@ def ats_level_advance(h, level, dt, opts: Optional[ats_solve_opts] = None):
     return code, st.as_dict()
 
 
+def ats_hierarchy_graph_stats(h):
+    """The step graph of use_graph = 3: {"held", "captures", "replays"}."""
+    held, cap, rep = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ats_hierarchy_graph_stats(h, ctypes.byref(held), ctypes.byref(cap), ctypes.byref(rep)),
+           "ats_hierarchy_graph_stats")
+    return {"held": bool(held.value), "captures": cap.value, "replays": rep.value}
+
+
 def ats_hierarchy_plan_faces(levels, level, order=ATS_ORDER_FINE_FIRST, walls=None):
     """Host-only: (cell, dir, rel, src_cell) arrays of the interface faces the
     library derives for one level."""
@@ -768,6 +778,9 @@ class Hierarchy:
 
     def advance(self, level, dt, **opts):
         return ats_level_advance(self.handle, level, dt, make_opts(**opts))
+
+    def graph_stats(self):
+        return ats_hierarchy_graph_stats(self.handle)
 
     def close(self):
         if self.handle:

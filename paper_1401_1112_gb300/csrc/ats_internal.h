@@ -290,19 +290,23 @@ struct DeferredRec {
 // one graph (use_graph = 2 is forced): x_dev is the device initial guess and
 // solution, d_rec (device) receives the result.  Nothing waits on the host.
 // check_every / max_ticks: the loop's interval and tick bound, for
-// deferred_result.
+// deferred_result.  capture: the context stream is under stream capture; the
+// level's plan, its device loop and its start state must then be resident
+// from an earlier run of the same solve (else ATS_ERR_INVALID_ARG, nothing
+// enqueued), and the loop is added to the captured graph.
 ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opts *opts, DeferredRec *d_rec,
-                                int *check_every, int64_t *max_ticks);
+                                int *check_every, int64_t *max_ticks, bool capture = false);
 // Status and statistics of a deferred solve from a host copy of its record.
 ats_status deferred_result(const DeferredRec &r, int check_every, int64_t max_ticks, ats_solve_stats *out);
-// A graph holding one WHILE conditional node (default value 1, assigned at
-// every launch); body: the node's (empty) body graph to capture into.
-cudaError_t make_while_graph(cudaGraph_t *graph, cudaGraph_t *body, cudaGraphConditionalHandle *handle);
-// Condition kernel of the device-side tick loop (a WHILE graph node): counts
-// the intervals in *chunks and sets h to continue while n_active > 0 and
-// fewer than max_chunks intervals have run.
-cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const int *n_active, int *chunks, int max_chunks,
-                             cudaStream_t st);
+// Add to `graph` (standalone, or the graph of a stream under capture), after
+// deps[0 .. n_deps), the device-side tick loop: a WHILE conditional node whose
+// body runs `interval` (one poll interval of ticks, cloned into the body) and
+// then a condition kernel that counts the intervals in *chunks and continues
+// while *n_active > 0 and fewer than max_chunks intervals have run.  The
+// handle's default value 1 is assigned at every launch of the graph, so the
+// body runs once before the first test.  node_out: the conditional node.
+cudaError_t add_while_loop(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t n_deps, cudaGraph_t interval,
+                           const int *n_active, int *chunks, int max_chunks, cudaGraphNode_t *node_out);
 // out[i] = 2 x[i] - E[i] (the Crank-Nicolson step from its backward-Euler half step).
 cudaError_t launch_cn_extrapolate(int64_t N, const double *x, const double *E, double *out, cudaStream_t st);
 // E^n of a Crank-Nicolson operator build of L (null for backward Euler).
@@ -337,6 +341,10 @@ ats_status abi_exception() noexcept;
 ats_status ctx_alloc(ats_context *ctx, size_t bytes, void **out);
 void ctx_free(ats_context *ctx, void *p);
 cudaStream_t ctx_stream(const ats_context *ctx);
+// Counter bumped by every allocation, free and host upload of solve-plan state
+// in the context: equal values before and after mean nothing a captured graph
+// refers to has moved or been rewritten from the host.
+uint64_t ctx_epoch(const ats_context *ctx);
 int ctx_device(const ats_context *ctx);
 
 // Interface faces of one level of a hierarchy (hierarchy.cpp): leaf faces whose

@@ -177,6 +177,19 @@ struct ats_hierarchy {
   int rec_cap = 0, n_recs = 0;
   std::vector<std::pair<int, int64_t>> rec_meta;  // interval, tick bound per record
   bool deferred = false;
+  // use_graph = 3: the whole step as one graph.  It is captured right after a
+  // deferred run of the same step (which leaves every plan, device loop and
+  // start state resident) and replayed while the step's arguments, the
+  // hierarchy's configuration (gen) and the context's epoch are unchanged
+  bool capturing = false;
+  uint64_t gen = 0;  // bumped by every change of the hierarchy's configuration
+  cudaGraphExec_t step_exec = nullptr;
+  int step_level = -1;
+  double step_dt = 0.0;
+  ats_solve_opts step_opts{};
+  uint64_t step_gen = 0, step_epoch = 0;
+  int64_t n_captures = 0, n_replays = 0;
+  std::vector<std::pair<int, int64_t>> step_meta;  // rec_meta of the captured step
 };
 
 namespace {
@@ -191,6 +204,7 @@ namespace {
   } while (0)
 
 void hierarchy_free(ats_hierarchy *H) {
+  if (H->step_exec) cudaGraphExecDestroy(H->step_exec);
   ctx_free(H->ctx, H->d_wall);
   ctx_free(H->ctx, H->d_recs);
   if (H->h_recs) cudaFreeHost(H->h_recs);
@@ -263,7 +277,7 @@ ats_status solve_level(ats_hierarchy *H, int l, double dt, double theta, const a
     }
     int ce = 0;
     int64_t mt = 0;
-    s = level_solve_deferred(h.lvl, h.E, &o, H->d_recs + H->n_recs, &ce, &mt);
+    s = level_solve_deferred(h.lvl, h.E, &o, H->d_recs + H->n_recs, &ce, &mt, H->capturing);
     if (s != ATS_OK) return s;
     H->rec_meta[H->n_recs++] = {ce, mt};
   } else {
@@ -313,6 +327,131 @@ ats_status advance(ats_hierarchy *H, int l, double dt, double theta1, const ats_
     if ((s = advance(H, l + 1, 0.5 * dt, 1.0, opts, acc)) != ATS_OK) return s;
     if ((s = restrict_into(H, l)) != ATS_OK) return s;
   }
+  return ATS_OK;
+}
+
+// Room for the result records of one step from `level`: at most 2^(levels
+// below) + 1 solves.
+ats_status ensure_records(ats_hierarchy *H, int level) {
+  const int n_lv = (int)H->lv.size();
+  const int need = (1 << std::min(30, n_lv - level)) + 1;
+  if (need > H->rec_cap) {
+    ctx_free(H->ctx, H->d_recs);
+    H->d_recs = nullptr;
+    if (H->h_recs) cudaFreeHost(H->h_recs);
+    H->h_recs = nullptr;
+    H->rec_cap = 0;
+    void *p = nullptr;
+    ats_status s0 = ctx_alloc(H->ctx, sizeof(DeferredRec) * need, &p);
+    if (s0 != ATS_OK) return s0;
+    H->d_recs = (DeferredRec *)p;
+    if (cudaMallocHost(&H->h_recs, sizeof(DeferredRec) * need) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("ats_level_advance: pinned allocation failed");
+      return ATS_ERR_OOM;
+    }
+    H->rec_cap = need;
+  }
+  H->rec_meta.assign(H->rec_cap, {0, 0});
+  H->n_recs = 0;
+  return ATS_OK;
+}
+
+// Fold the host copies of n result records (h_recs) into acc; s: the status
+// of the step so far, returned with the first failing solve's error.
+ats_status fold_records(const ats_hierarchy *H, const std::vector<std::pair<int, int64_t>> &meta, int n,
+                        ats_solve_stats &acc, ats_status s) {
+  for (int k = 0; k < n; ++k) {
+    ats_solve_stats st1;
+    const ats_status r = deferred_result(H->h_recs[k], meta[k].first, meta[k].second, &st1);
+    acc.iterations += st1.iterations;
+    acc.refinements += st1.refinements;
+    acc.ticks += st1.ticks;
+    acc.r0_norm = std::max(acc.r0_norm, st1.r0_norm);
+    acc.res_norm = std::max(acc.res_norm, st1.res_norm);
+    acc.x_norm = std::max(acc.x_norm, st1.x_norm);
+    acc.err_bound = std::max(acc.err_bound, st1.err_bound);
+    if (r < 0 ? acc.status >= 0 : acc.status == ATS_OK) acc.status = r;
+    if (r < 0 && s >= 0) s = r;
+  }
+  return s;
+}
+
+// One step from `level`: with deferred solves (use_graph >= 2) every solve is
+// enqueued without a host wait and the records are read once at the end.
+ats_status run_step(ats_hierarchy *H, int level, double dt, const ats_solve_opts *opts, bool deferred,
+                    ats_solve_stats &acc) {
+  H->deferred = deferred;
+  if (deferred) {
+    ats_status s0 = ensure_records(H, level);
+    if (s0 != ATS_OK) {
+      H->deferred = false;
+      return s0;
+    }
+  }
+  ats_status s = advance(H, level, dt, 1.0, opts, &acc);
+  if (deferred) {
+    H->deferred = false;
+    cudaStream_t st = ctx_stream(H->ctx);
+    if (H->n_recs > 0)
+      H_TRY(cudaMemcpyAsync(H->h_recs, H->d_recs, sizeof(DeferredRec) * H->n_recs, cudaMemcpyDeviceToHost, st));
+    H_TRY(cudaStreamSynchronize(st));
+    s = fold_records(H, H->rec_meta, H->n_recs, acc, s);
+  }
+  return s;
+}
+
+// Record the step just taken (the same level, dt and options) as one graph:
+// every enqueue of a deferred step -- restriction, ghost gather, operator
+// builds, the level solves with their device loops, flux stores -- and the
+// copy of the result records to the host.  Nothing runs while it is captured.
+ats_status capture_step(ats_hierarchy *H, int level, double dt, const ats_solve_opts *opts) {
+  cudaStream_t st = ctx_stream(H->ctx);
+  if (H->step_exec) {
+    cudaGraphExecDestroy(H->step_exec);
+    H->step_exec = nullptr;
+  }
+  const uint64_t epoch0 = ctx_epoch(H->ctx);
+  ats_status s = ensure_records(H, level);
+  if (s != ATS_OK) return s;
+  H_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  H->deferred = true;
+  H->capturing = true;
+  s = advance(H, level, dt, 1.0, opts, nullptr);
+  H->capturing = false;
+  H->deferred = false;
+  cudaError_t err = cudaSuccess;
+  if (s == ATS_OK && H->n_recs > 0)
+    err = cudaMemcpyAsync(H->h_recs, H->d_recs, sizeof(DeferredRec) * H->n_recs, cudaMemcpyDeviceToHost, st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  if (err == cudaSuccess) err = e2;
+  if (s == ATS_OK && err == cudaSuccess) err = cudaGraphInstantiate(&H->step_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (s == ATS_OK && err != cudaSuccess) {
+    cudaGetLastError();
+    H->step_exec = nullptr;
+    set_error(std::string("ats_level_advance: step graph: ") + cudaGetErrorString(err));
+    s = ATS_ERR_CUDA;
+  }
+  if (s != ATS_OK) {
+    if (H->step_exec) cudaGraphExecDestroy(H->step_exec);
+    H->step_exec = nullptr;
+    return s;
+  }
+  if (ctx_epoch(H->ctx) != epoch0) {  // the capture needed an allocation or upload
+    cudaGraphExecDestroy(H->step_exec);
+    H->step_exec = nullptr;
+    set_error("ats_level_advance: step graph: the step changed device state while it was captured");
+    return ATS_ERR_CUDA;
+  }
+  H->step_level = level;
+  H->step_dt = dt;
+  H->step_opts = *opts;
+  H->step_gen = H->gen;
+  H->step_epoch = epoch0;
+  H->step_meta.assign(H->rec_meta.begin(), H->rec_meta.begin() + H->n_recs);
+  ++H->n_captures;
   return ATS_OK;
 }
 
@@ -512,6 +651,7 @@ ats_status ats_hierarchy_set_power_law(ats_hierarchy *H, double K0, double a) {
       return ATS_ERR_INVALID_ARG;
     }
     H->power_law = true;
+    ++H->gen;
     H->pl_K0 = K0;
     H->pl_a = a;
     return ATS_OK;
@@ -551,6 +691,7 @@ ats_status ats_hierarchy_set_interface(ats_hierarchy *H, int kind, double alpha)
     }
     H_TRY(cudaStreamSynchronize(st));
     H->iface_kind = kind;
+    ++H->gen;
     H->iface_alpha = a;
     return ATS_OK;
   } catch (...) {
@@ -631,6 +772,7 @@ ats_status ats_hierarchy_set_fld(ats_hierarchy *H, int level, const double *rho,
     bool all = true;
     for (const HLevel &x : H->lv) all = all && x.rho != nullptr;
     H->fld = all;
+    ++H->gen;
     return ATS_OK;
   } catch (...) {
     return ats::abi_exception();
@@ -681,53 +823,29 @@ ats_status ats_level_advance(ats_hierarchy *H, int level, double dt, const ats_s
     std::memset(&acc, 0, sizeof(acc));
     acc.status = ATS_OK;
     cudaSetDevice(ctx_device(H->ctx));
-    // use_graph = 2: every level solve is one graph launch (device-driven tick
-    // loop) and none is waited for; the step's records are read once at the
-    // end, so a failing solve is reported after the whole step has run
-    H->deferred = opts && opts->use_graph == 2;
-    if (H->deferred) {
-      const int n_lv = (int)H->lv.size();
-      const int need = (1 << std::min(30, n_lv - level)) + 1;  // at most 2^(levels below) solves
-      if (need > H->rec_cap) {
-        ctx_free(H->ctx, H->d_recs);
-        H->d_recs = nullptr;
-        if (H->h_recs) cudaFreeHost(H->h_recs);
-        H->h_recs = nullptr;
-        H->rec_cap = 0;
-        void *p = nullptr;
-        ats_status s0 = ctx_alloc(H->ctx, sizeof(DeferredRec) * need, &p);
-        if (s0 != ATS_OK) return s0;
-        H->d_recs = (DeferredRec *)p;
-        if (cudaMallocHost(&H->h_recs, sizeof(DeferredRec) * need) != cudaSuccess) {
-          cudaGetLastError();
-          set_error("ats_level_advance: pinned allocation failed");
-          return ATS_ERR_OOM;
+    const int ug = opts ? opts->use_graph : 0;
+    ats_status s;
+    if (ug == 3) {
+      // use_graph = 3: replay the step's graph while it is current; else take
+      // the step with deferred solves, then capture it for the next call
+      const bool current = H->step_exec && H->step_level == level && H->step_dt == dt &&
+                           std::memcmp(&H->step_opts, opts, sizeof(*opts)) == 0 && H->step_gen == H->gen &&
+                           H->step_epoch == ctx_epoch(H->ctx);
+      if (current) {
+        cudaStream_t st = ctx_stream(H->ctx);
+        H_TRY(cudaGraphLaunch(H->step_exec, st));
+        H_TRY(cudaStreamSynchronize(st));
+        ++H->n_replays;
+        s = fold_records(H, H->step_meta, (int)H->step_meta.size(), acc, ATS_OK);
+      } else {
+        s = run_step(H, level, dt, opts, true, acc);
+        if (s >= 0) {
+          const ats_status sc = capture_step(H, level, dt, opts);
+          if (sc != ATS_OK) s = sc;
         }
-        H->rec_cap = need;
       }
-      H->rec_meta.assign(H->rec_cap, {0, 0});
-      H->n_recs = 0;
-    }
-    ats_status s = advance(H, level, dt, 1.0, opts, &acc);
-    if (H->deferred) {
-      cudaStream_t st = ctx_stream(H->ctx);
-      if (H->n_recs > 0)
-        H_TRY(cudaMemcpyAsync(H->h_recs, H->d_recs, sizeof(DeferredRec) * H->n_recs, cudaMemcpyDeviceToHost, st));
-      H_TRY(cudaStreamSynchronize(st));
-      for (int k = 0; k < H->n_recs; ++k) {
-        ats_solve_stats st1;
-        const ats_status r = deferred_result(H->h_recs[k], H->rec_meta[k].first, H->rec_meta[k].second, &st1);
-        acc.iterations += st1.iterations;
-        acc.refinements += st1.refinements;
-        acc.ticks += st1.ticks;
-        acc.r0_norm = std::max(acc.r0_norm, st1.r0_norm);
-        acc.res_norm = std::max(acc.res_norm, st1.res_norm);
-        acc.x_norm = std::max(acc.x_norm, st1.x_norm);
-        acc.err_bound = std::max(acc.err_bound, st1.err_bound);
-        if (r < 0 ? acc.status >= 0 : acc.status == ATS_OK) acc.status = r;
-        if (r < 0 && s >= 0) s = r;
-      }
-      H->deferred = false;
+    } else {
+      s = run_step(H, level, dt, opts, ug == 2, acc);
     }
     // errors first; else the first warning of the step's solves
     if (s == ATS_OK && acc.status > 0) s = acc.status;
@@ -736,6 +854,17 @@ ats_status ats_level_advance(ats_hierarchy *H, int level, double dt, const ats_s
   } catch (...) {
     return ats::abi_exception();
   }
+}
+
+ats_status ats_hierarchy_graph_stats(ats_hierarchy *H, int *held, int64_t *captures, int64_t *replays) {
+  if (!H) {
+    set_error("ats_hierarchy_graph_stats: null hierarchy");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (held) *held = H->step_exec ? 1 : 0;
+  if (captures) *captures = H->n_captures;
+  if (replays) *replays = H->n_replays;
+  return ATS_OK;
 }
 
 }  // extern "C"

@@ -25,37 +25,34 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int *__restrict_
 
 }  // namespace
 
-cudaError_t make_while_graph(cudaGraph_t *graph, cudaGraph_t *body, cudaGraphConditionalHandle *handle) {
-  *graph = nullptr;
-  *body = nullptr;
-  cudaGraph_t g = nullptr;
-  cudaError_t err = cudaGraphCreate(&g, 0);
-  if (err != cudaSuccess) return err;
+cudaError_t add_while_loop(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t n_deps, cudaGraph_t interval,
+                           const int *n_active, int *chunks, int max_chunks, cudaGraphNode_t *node_out) {
+  // the handle's default value 1, assigned at every launch of the graph, runs
+  // the body once before the first test
   cudaGraphConditionalHandle h;
-  err = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaError_t err = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  if (err != cudaSuccess) return err;
   cudaGraphNodeParams np = {};
-  if (err == cudaSuccess) {
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    err = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
-  }
-  if (err != cudaSuccess) {
-    cudaGraphDestroy(g);
-    return err;
-  }
-  *graph = g;
-  *body = np.conditional.phGraph_out[0];
-  *handle = h;
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((err = cudaGraphAddNode(&node, graph, deps, nullptr, n_deps, &np)) != cudaSuccess) return err;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  // body: the interval (cloned), then the condition kernel
+  cudaGraphNode_t ticks, cond;
+  if ((err = cudaGraphAddChildGraphNode(&ticks, body, nullptr, 0, interval)) != cudaSuccess) return err;
+  void *args[4] = {&h, &n_active, &chunks, &max_chunks};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void *)k_loop_cond;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  if ((err = cudaGraphAddKernelNode(&cond, body, &ticks, 1, &kp)) != cudaSuccess) return err;
+  *node_out = node;
   return cudaSuccess;
-}
-
-cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, const int *n_active, int *chunks, int max_chunks,
-                             cudaStream_t st) {
-  k_loop_cond<<<1, 1, 0, st>>>(h, n_active, chunks, max_chunks);
-  return cudaGetLastError();
 }
 
 }  // namespace ats

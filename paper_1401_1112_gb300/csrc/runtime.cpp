@@ -55,6 +55,10 @@ struct ats_context {
   cudaStream_t stream = nullptr;
   int num_sms = 0;
   std::unordered_map<void *, size_t> allocs;
+  // bumped by every allocation, free and host upload of solve-plan state, so
+  // that a graph recorded over plans of this context can tell whether what it
+  // captured is still in place
+  uint64_t epoch = 0;
 };
 
 struct Plan;
@@ -123,6 +127,7 @@ ats_status dev_alloc(ats_context *ctx, size_t bytes, void **out) {
   }
   ctx->allocs[p] = bytes;
   ctx->used += bytes;
+  ++ctx->epoch;
   *out = p;
   return ATS_OK;
 }
@@ -137,6 +142,7 @@ ats_status dev_alloc_t(ats_context *ctx, size_t count, P **out) {
 
 void dev_free(ats_context *ctx, void *p) {
   if (!p) return;
+  ++ctx->epoch;
   auto it = ctx->allocs.find(p);
   if (it != ctx->allocs.end()) {
     ctx->used -= it->second;
@@ -156,6 +162,7 @@ namespace ats {
 ats_status ctx_alloc(ats_context *ctx, size_t bytes, void **out) { return dev_alloc(ctx, bytes, out); }
 void ctx_free(ats_context *ctx, void *p) { dev_free(ctx, p); }
 cudaStream_t ctx_stream(const ats_context *ctx) { return ctx->stream; }
+uint64_t ctx_epoch(const ats_context *ctx) { return ctx->epoch; }
 const int32_t *level_nbr(const ats_level *L) { return L->nbr; }
 double *level_x64(ats_level *L) { return L->x64; }
 const double *level_cn_base(const ats_level *L) { return L->cn_base; }
@@ -208,8 +215,17 @@ struct Plan {
   // use_graph = 2: the whole tick loop as one graph (WHILE node over one
   // interval of ticks); d_loop counts the intervals run
   cudaGraphExec_t loop_exec = nullptr;
+  cudaGraph_t loop_ticks = nullptr;  // the loop's body: one interval of ticks
   int *d_loop = nullptr;
   int loop_max = 0;
+  // start-of-run state kept on the device (the solves' initial scalars, the
+  // active count, the tick control block), and the host image last uploaded;
+  // the x pointers last uploaded to d_src / d_dst.  A run whose start state
+  // and pointers are already resident copies them device to device only
+  unsigned char *d_init = nullptr;
+  std::vector<unsigned char> h_init;
+  std::vector<const double *> h_src;
+  std::vector<double *> h_dst;
   bool profiling = false;
   // two sets (by poll slot) of: chunk start, then kTickEvents per tick of a
   // chunk, so that one interval runs while the other's events are read
@@ -299,6 +315,8 @@ ats_solve_opts normalize(const ats_solve_opts *in) {
   if (o.max_refine <= 0) o.max_refine = 40;
   if (!(o.inner_rtol > 0.0)) o.inner_rtol = 1e-5;
   if (o.check_every <= 0) o.check_every = 16;
+  // 3 (a hierarchy step as one graph) is 2 for a solve on its own
+  if (o.use_graph > 2) o.use_graph = 2;
   return o;
 }
 
@@ -388,6 +406,8 @@ void plan_free(Plan *P) {
   dev_free(ctx, P->d_queue);
   dev_free(ctx, P->d_heads);
   dev_free(ctx, P->d_tsolve);
+  dev_free(ctx, P->d_init);
+  if (P->loop_ticks) cudaGraphDestroy(P->loop_ticks);
   if (P->join2) cudaEventDestroy(P->join2);
   if (P->aux2) cudaStreamDestroy(P->aux2);
   for (auto e : P->res_ev)
@@ -428,6 +448,7 @@ ats_status plan_upload_queues(Plan *P) {
   if (!bq.empty())
     CUDA_TRY(cudaMemcpyAsync(P->d_queue, bq.data(), sizeof(int32_t) * bq.size(), cudaMemcpyHostToDevice,
                              P->ctx->stream));
+  ++P->ctx->epoch;
   return ATS_OK;
 }
 
@@ -810,7 +831,8 @@ cudaError_t timed_ticks(Plan *P, const TickArgs &ta, cudaStream_t st, int k, boo
 // The device-driven loop of use_graph = 2: a graph holding one WHILE node
 // whose body is one interval of ticks followed by the condition kernel.  The
 // handle's default value 1 runs the body once per launch before the first
-// test.  Built once per plan (the interval bound is fixed by the options).
+// test.  The interval graph is captured once per plan; the loop graph is
+// built once per interval bound (fixed by the options).
 ats_status plan_ensure_loop(Plan *P, int max_chunks) {
   if (P->loop_exec && P->loop_max == max_chunks) return ATS_OK;
   if (P->loop_exec) {
@@ -824,22 +846,25 @@ ats_status plan_ensure_loop(Plan *P, int max_chunks) {
     if (s != ATS_OK) return s;
     CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
   }
-  cudaGraph_t g = nullptr, body = nullptr;
-  cudaGraphConditionalHandle h;
-  cudaError_t err = make_while_graph(&g, &body, &h);
-  if (err == cudaSuccess) {
-    err = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  cudaError_t err = cudaSuccess;
+  if (!P->loop_ticks) {
+    err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
       TickArgs ta = P->targs;
       ta.cells = nullptr;
       for (int t = 0; t < P->opts.check_every && err == cudaSuccess; ++t)
         err = launch_tick(P->fp64, P->paper, ta, P->grids, st, &P->fj, nullptr, true);
-      if (err == cudaSuccess) err = launch_loop_cond(h, P->d_active, P->d_loop, max_chunks, st);
       cudaGraph_t out = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(st, &out);
       if (err == cudaSuccess) err = e2;
+      if (err == cudaSuccess) P->loop_ticks = out;
+      else if (out) cudaGraphDestroy(out);
     }
   }
+  cudaGraph_t g = nullptr;
+  if (err == cudaSuccess) err = cudaGraphCreate(&g, 0);
+  cudaGraphNode_t node;
+  if (err == cudaSuccess) err = add_while_loop(g, nullptr, 0, P->loop_ticks, P->d_active, P->d_loop, max_chunks, &node);
   if (err == cudaSuccess) err = cudaGraphInstantiate(&P->loop_exec, g, 0);
   if (g) cudaGraphDestroy(g);
   if (err != cudaSuccess) {
@@ -849,6 +874,30 @@ ats_status plan_ensure_loop(Plan *P, int max_chunks) {
     return ATS_ERR_CUDA;
   }
   P->loop_max = max_chunks;
+  return ATS_OK;
+}
+
+// Enqueue the device loop of P (built by plan_ensure_loop) on st: a launch of
+// its graph, or, while st is under capture, the same WHILE node added to the
+// graph being captured (a graph launch cannot sit inside another graph when
+// it holds a conditional node).
+ats_status plan_enqueue_loop(Plan *P, cudaStream_t st, bool capture) {
+  if (!capture) {
+    CUDA_TRY(cudaGraphLaunch(P->loop_exec, st));
+    return ATS_OK;
+  }
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t n_deps = 0;
+  CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &n_deps));
+  if (cs != cudaStreamCaptureStatusActive) {
+    set_error("device loop: the stream is not under capture");
+    return ATS_ERR_CUDA;
+  }
+  cudaGraphNode_t node;
+  CUDA_TRY(add_while_loop(g, deps, n_deps, P->loop_ticks, P->d_active, P->d_loop, P->loop_max, &node));
+  CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
   return ATS_OK;
 }
 
@@ -947,8 +996,12 @@ void plan_bytes(const Plan *P, const unsigned long long cells[kCellCounters], do
 // rebuilt since the plan was made, copy x in (device x is read in place,
 // host x goes through one staging buffer, one copy per run of levels whose
 // host arrays are contiguous), reset every solve's state and the work lists.
-// off: [n + 1] offsets of the levels in the staging buffer.
-ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off) {
+// off: [n + 1] offsets of the levels in the staging buffer.  The start state
+// and the x pointers are uploaded only when they differ from what the device
+// holds; the reset itself is device to device.  capture: st is under stream
+// capture, so nothing may come from the host (device x only, and every
+// upload already resident, else ATS_ERR_INVALID_ARG).
+ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off, bool capture = false) {
   ats_context *ctx = P->ctx;
   cudaStream_t st = ctx->stream;
   const int n = P->n;
@@ -973,7 +1026,16 @@ ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off
       stale = true;
     }
   }
+  if (stale && capture) {
+    set_error("graph capture: a level was rebuilt with another time step since its last solve");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (!dev && capture) {
+    set_error("graph capture: host-memory solves cannot be captured");
+    return ATS_ERR_INVALID_ARG;
+  }
   if (stale) {
+    ++ctx->epoch;
     CUDA_TRY(cudaMemcpyAsync(P->d_solves, P->h_solves.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice, st));
     ats_status sq = plan_upload_queues(P);  // the work estimates follow dt
     if (sq != ATS_OK) return sq;
@@ -1009,24 +1071,54 @@ ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off
     dst[k] = dev ? x_inout[k] : P->d_xstage + off[k];
     src[k] = x0_e ? P->levels[k]->E_dev : dst[k];
   }
-  CUDA_TRY(cudaMemcpyAsync(P->d_src, src.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(P->d_dst, dst.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+  if (src != P->h_src || dst != P->h_dst) {
+    if (capture) {
+      set_error("graph capture: the solve's x is not the one of its last run");
+      return ATS_ERR_INVALID_ARG;
+    }
+    ++ctx->epoch;
+    P->h_src = src;
+    P->h_dst = dst;
+    CUDA_TRY(cudaMemcpyAsync(P->d_src, P->h_src.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(P->d_dst, P->h_dst.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+  }
   CUDA_TRY(launch_init(P->fp64, P->d_solves, P->d_items, P->n_items, P->d_src, P->grid, st));
-  CUDA_TRY(cudaMemcpyAsync(P->d_sc, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(P->d_final, P->h_sc.data(), sizeof(SolveScalars) * n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, 2 * kCellCounters * sizeof(unsigned long long), st));
-  // only the tick-path solves count as active for the tick loop
-  CUDA_TRY(cudaMemcpyAsync(P->d_active, &P->n_tick, sizeof(int), cudaMemcpyHostToDevice, st));
+  // the start state: every solve's scalars (live and final copies), the
+  // active count (only the tick-path solves count for the tick loop) and the
+  // tick control block (every item of every tick-path solve starts in the
+  // refinement phase, r0 = b - A x0)
+  const size_t sc_b = sizeof(SolveScalars) * n;
+  const size_t ctl_at = (sc_b + sizeof(int) + 15) / 16 * 16;
+  std::vector<unsigned char> img(ctl_at + sizeof(TickCtl), 0);
+  std::memcpy(img.data(), P->h_sc.data(), sc_b);
+  std::memcpy(img.data() + sc_b, &P->n_tick, sizeof(int));
   {
-    // every item of every tick-path solve starts in the refinement phase (r0 = b - A x0)
     TickCtl c0;
     std::memset(&c0, 0, sizeof(c0));
     c0.count[0][kRefine] = P->n_tick_items;
-    if (P->n_tick_items > 0)
-      CUDA_TRY(cudaMemcpyAsync(P->d_lists + (size_t)kRefine * P->n_items, P->d_ident,
-                               sizeof(int32_t) * P->n_tick_items, cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(P->d_ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    std::memcpy(img.data() + ctl_at, &c0, sizeof(c0));
   }
+  if (img != P->h_init) {
+    if (capture) {
+      set_error("graph capture: the solves' start state is not resident");
+      return ATS_ERR_INVALID_ARG;
+    }
+    if (!P->d_init) {
+      ats_status s2 = dev_alloc_t(ctx, img.size(), &P->d_init);
+      if (s2 != ATS_OK) return s2;
+    }
+    ++ctx->epoch;
+    P->h_init = img;
+    CUDA_TRY(cudaMemcpyAsync(P->d_init, P->h_init.data(), img.size(), cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(cudaMemcpyAsync(P->d_sc, P->d_init, sc_b, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_final, P->d_init, sc_b, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(P->d_cells, 0, 2 * kCellCounters * sizeof(unsigned long long), st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_active, P->d_init + sc_b, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  if (P->n_tick_items > 0)
+    CUDA_TRY(cudaMemcpyAsync(P->d_lists + (size_t)kRefine * P->n_items, P->d_ident,
+                             sizeof(int32_t) * P->n_tick_items, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(P->d_ctl, P->d_init + ctl_at, sizeof(TickCtl), cudaMemcpyDeviceToDevice, st));
   P->op_ms = P->ref_ms = P->upd_ms = 0.0;
   P->res_ms = P->res_bytes = 0.0;
   P->launches = 0;
@@ -1144,9 +1236,14 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, P->res_ev[0], P->res_ev[1]));
       P->res_ms = ms;
-      double ob = 0, rb = 0, ub = 0;
-      plan_bytes(P, cells + kCellCounters, &ob, &rb, &ub);
-      P->res_bytes = ob + rb + ub;
+      // the minimal traffic of the method, as if every vector were streamed
+      // from memory: 10 words per cell and CG iteration (read p, K, x, r, q,
+      // D^-1; write q, x, r, p) and 5 FP64 words per cell and refinement pass
+      // (read x, b, K; write r, D) -- the resident solver keeps most of it
+      // on chip, so its DRAM traffic is far lower
+      const unsigned long long *rc = cells + kCellCounters;
+      const double w = P->fp64 ? 8.0 : 4.0;
+      P->res_bytes = 10.0 * w * (double)(rc[0] + rc[4]) + 40.0 * (double)rc[1];
       // the launch's timeline: span from the first solve's start to the last
       // one's end, the longest solve, and the fraction of the launch's
       // CTA-time spent inside solves
@@ -1702,7 +1799,7 @@ ats_status ats_solve(ats_level *L, const double *rhs, double *x_inout, const ats
 namespace ats {
 
 ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opts *opts, DeferredRec *d_rec,
-                                int *check_every, int64_t *max_ticks) {
+                                int *check_every, int64_t *max_ticks, bool capture) {
   if (!L || !x_dev || !d_rec || !L->built) {
     set_error("deferred solve: bad argument or level operator not built");
     return ATS_ERR_INVALID_ARG;
@@ -1714,8 +1811,13 @@ ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opt
   CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   ats_status s;
-  if (L->solo && (std::memcmp(&L->solo->opts, &o, sizeof(o)) != 0 ||
-                  L->solo->fp64 != (o.precision == ATS_PREC_FP64))) {
+  const bool stale_plan = L->solo && (std::memcmp(&L->solo->opts, &o, sizeof(o)) != 0 ||
+                                      L->solo->fp64 != (o.precision == ATS_PREC_FP64));
+  if (capture && (!L->solo || stale_plan)) {
+    set_error("graph capture: the level has no plan for these options");
+    return ATS_ERR_INVALID_ARG;
+  }
+  if (stale_plan) {
     plan_free(L->solo);
     L->solo = nullptr;
   }
@@ -1728,16 +1830,20 @@ ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opt
   P->profiling = false;
   std::vector<int64_t> off;
   double *xs[1] = {x_dev};
-  s = plan_begin(P, xs, off);
+  s = plan_begin(P, xs, off, capture);
   const int64_t mt = plan_max_ticks(P);
   const int max_chunks = (int)std::min<int64_t>((mt + o.check_every - 1) / o.check_every, 1 << 30);
+  if (capture && s == ATS_OK && (!P->d_loop || (P->n_tick > 0 && (!P->loop_exec || P->loop_max != max_chunks)))) {
+    set_error("graph capture: the level's device loop is not built");
+    s = ATS_ERR_INVALID_ARG;
+  }
   if (s == ATS_OK && P->n_tick > 0) s = plan_ensure_loop(P, max_chunks);
   if (s == ATS_OK && !P->d_loop) s = dev_alloc_t(ctx, 1, &P->d_loop);
   if (s == ATS_OK) s = plan_launch_resident(P, false);
   P->profiling = prof;
   if (s != ATS_OK) return s;
   CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
-  if (P->n_tick > 0) CUDA_TRY(cudaGraphLaunch(P->loop_exec, st));
+  if (P->n_tick > 0 && (s = plan_enqueue_loop(P, st, capture)) != ATS_OK) return s;
   CUDA_TRY(cudaMemsetAsync(&d_rec->neg, 0, sizeof(int), st));
   CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, &d_rec->neg, P->grid, st));
   CUDA_TRY(cudaMemcpyAsync(&d_rec->sc, P->d_final, sizeof(SolveScalars), cudaMemcpyDeviceToDevice, st));
