@@ -727,15 +727,34 @@ def _serve_oracle_check(job):
             "within_bound": bool(err <= 1.0001 * bound + 1e-14 * float(np.linalg.norm(xr)))}
 
 
+def _build_stream(pool, reqs, ks, window=64):
+    """(k, built request) for k in ks, in order, built on the pool's
+    processes at most `window` requests ahead of use, so the host holds a
+    bounded number of built requests whatever the stream's length."""
+    import collections
+    import itertools
+
+    it = iter(ks)
+    pend = collections.deque((k, pool.apply_async(W.build_request, (reqs[k],))) for k in itertools.islice(it, window))
+    while pend:
+        k, r = pend.popleft()
+        for k2 in itertools.islice(it, 1):
+            pend.append((k2, pool.apply_async(W.build_request, (reqs[k2],))))
+        yield k, r.get()
+
+
 def run_serve(args, ats, device):
     """Served request stream (the served workload: Poisson arrivals of level
     solves, cells log-uniform 16^3 .. serve_max_cells, Dirichlet / Neumann /
     Robin walls, tol 1e-6 or 1e-10 on the residual rule; the first
-    serve_requests requests of its 2 000).  The requests are built on every
-    host core before anything is timed.  Then:
-      * the plain per-solve FP64 path's service time for each request (level
-        creation, operator build and solve, one at a time) gives its capacity,
-        and the arrivals are paced at 0.8 x that capacity;
+    serve_requests requests of its 2 000).  Requests are built on every host
+    core while the stream runs, a bounded number ahead of their arrival (a
+    built request is the client's data: the timed service starts at its
+    submission).  Then:
+      * the plain per-solve FP64 path's service time (level creation,
+        operator build and solve, one at a time) on the first up to 240
+        requests gives its capacity, and the arrivals are paced at 0.8 x that
+        capacity;
       * the continuous-batching server (mixed precision) serves the arrivals,
         with the serve_budget_gb device budget and again with a 4 GB budget
         (admission limited by memory);
@@ -746,106 +765,117 @@ def run_serve(args, ats, device):
         smallest of at least 128^3 cells) is checked against the oracle.
     Reports p50 / p99 latency (submission to result) and throughput."""
     import multiprocessing as mp
-    import threading
 
     reqs = W.served_requests(n_req=args.serve_requests, seed=1405, hi_cells=args.serve_max_cells)
-    t_build = time.perf_counter()
-    with mp.get_context("spawn").Pool(max(1, min(len(reqs), os.cpu_count() or 1))) as pool:
-        built = pool.map(W.build_request, reqs, chunksize=1)
-    build_s = time.perf_counter() - t_build
+    n = len(reqs)
+    octs = np.array([r["octs"] for r in reqs])
+    order = np.argsort(octs)
+    sample = {int(order[0]), int(order[n // 2])}
+    big = [k for k in order if 8 * octs[k] >= 128 ** 3]
+    if big:
+        sample.add(int(big[0]))
+    kept = {}
 
-    def fp64_serve_one(ctx, k):
-        lv, st = built[k]
+    def fp64_serve_one(ctx, built, tol):
+        lv, st = built
         L = ats.Level(ctx, lv)
         L.build(st.dt, st.K, st.E, face_E=st.face_E, face_F=st.face_F)
         x = st.E.copy()
-        code, _ = L.solve(x, tol=reqs[k]["tol"], precision=ats.ATS_PREC_FP64)
+        code, _ = L.solve(x, tol=tol, precision=ats.ATS_PREC_FP64)
         L.close()
         if code < 0:  # a warning (ATS_WARN_NEGATIVE) is a result
             raise RuntimeError("fp64 served solve failed")
 
-    # plain per-solve FP64: service time of every request (level, build, solve)
-    svc = []
-    with ats.Context(device) as ctx:
-        fp64_serve_one(ctx, 0)  # warm-up
-        for k in range(len(reqs)):
-            t0 = time.perf_counter()
-            fp64_serve_one(ctx, k)
-            svc.append(time.perf_counter() - t0)
-    svc = np.array(svc)
-    cap = len(svc) / svc.sum()
-    lam = 0.8 * cap
-    arrivals = np.array([r["t"] for r in reqs]) * (reqs[-1]["id"] + 1) / reqs[-1]["t"] / lam
+    cores = max(1, (os.cpu_count() or 2) - 2)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        # plain per-solve FP64: service time of the first requests (level, build, solve)
+        n_cal = min(n, 240)
+        svc = []
+        with ats.Context(device) as ctx:
+            for k, b in _build_stream(pool, reqs, range(n_cal)):
+                if k == 0:
+                    fp64_serve_one(ctx, b, reqs[k]["tol"])  # warm-up
+                t0 = time.perf_counter()
+                fp64_serve_one(ctx, b, reqs[k]["tol"])
+                svc.append(time.perf_counter() - t0)
+        svc = np.array(svc)
+        cap = len(svc) / svc.sum()
+        lam = 0.8 * cap
+        arrivals = np.array([r["t"] for r in reqs]) * (reqs[-1]["id"] + 1) / reqs[-1]["t"] / lam
 
-    def server_run(budget_bytes, keep_x):
-        srv = ats.Server(device, mem_budget_bytes=int(budget_bytes), precision=ats.ATS_PREC_MIXED, check_every=4)
-        tickets = [None] * len(reqs)
-        t_start = time.perf_counter()
+        def server_run(budget_bytes, keep):
+            srv = ats.Server(device, mem_budget_bytes=int(budget_bytes), precision=ats.ATS_PREC_MIXED,
+                             check_every=4)
+            tickets = [None] * n
+            n_cell = [0] * n
+            cells = [0]
+            t_start = time.perf_counter()
 
-        def submitter():
-            for k, ((lv, st), r) in enumerate(zip(built, reqs)):
+            def submitter():
+                for k, (lv, st) in _build_stream(pool, reqs, range(n)):
+                    delay = arrivals[k] - (time.perf_counter() - t_start)
+                    if delay > 0:
+                        time.sleep(delay)
+                    n_cell[k] = lv.n_cell
+                    cells[0] += lv.n_cell
+                    if k in keep:
+                        kept[k] = (lv, st)
+                    tickets[k] = srv.submit(lv, st, tol=reqs[k]["tol"])
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            lat, xs, rn = [], {}, {}
+            errs = 0
+            for k in range(n):
+                while tickets[k] is None:
+                    time.sleep(0.0002)
+                code, x, res = srv.wait(tickets[k], n_cell[k])
+                errs += code < 0
+                lat.append(res["latency_us"] / 1e3)
+                if k in keep:
+                    xs[k] = x
+                    rn[k] = res["stats"]["res_norm"]
+            t_end = time.perf_counter()
+            th.join()
+            st_srv = srv.stats()
+            srv.close()
+            lat = np.array(lat)
+            return {"throughput": round(n / (t_end - t_start), 2), "unit": UNIT,
+                    "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                    "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                    "errors": int(errs), "peak_resident": st_srv["peak_resident"],
+                    "budget_gb": round(budget_bytes / (1 << 30), 1), "cells_mean": round(cells[0] / n)}, xs, rn
+
+        served, xs, rn = server_run(args.serve_budget_gb * (1 << 30), sample)
+        served_small, _, _ = server_run(4 * (1 << 30), set())
+
+        # the plain per-solve FP64 path serving the same arrivals, one at a time
+        fin = np.zeros(n)
+        with ats.Context(device) as ctx:
+            t_start = None
+            for k, b in _build_stream(pool, reqs, range(n)):
+                if t_start is None:
+                    fp64_serve_one(ctx, b, reqs[k]["tol"])  # warm-up
+                    t_start = time.perf_counter()
                 delay = arrivals[k] - (time.perf_counter() - t_start)
                 if delay > 0:
                     time.sleep(delay)
-                tickets[k] = srv.submit(lv, st, tol=r["tol"])
-
-        th = threading.Thread(target=submitter)
-        th.start()
-        lat, xs, rn = [], {}, {}
-        errs = 0
-        for k, ((lv, st), r) in enumerate(zip(built, reqs)):
-            while tickets[k] is None:
-                time.sleep(0.0002)
-            code, x, res = srv.wait(tickets[k], lv.n_cell)
-            errs += code < 0
-            lat.append(res["latency_us"] / 1e3)
-            if k in keep_x:
-                xs[k] = x
-                rn[k] = res["stats"]["res_norm"]
-        t_end = time.perf_counter()
-        th.join()
-        st_srv = srv.stats()
-        srv.close()
-        lat = np.array(lat)
-        return {"throughput": round(len(reqs) / (t_end - t_start), 2), "unit": UNIT,
-                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                "errors": int(errs), "peak_resident": st_srv["peak_resident"],
-                "budget_gb": round(budget_bytes / (1 << 30), 1)}, xs, rn
-
-    sizes = np.array([lv.n_cell for lv, _ in built])
-    order = np.argsort(sizes)
-    sample = {int(order[0]), int(order[len(order) // 2])}
-    big = [k for k in order if sizes[k] >= 128 ** 3]
-    if big:
-        sample.add(int(big[0]))
-    served, xs, rn = server_run(args.serve_budget_gb * (1 << 30), sample)
-    served_small, _, _ = server_run(4 * (1 << 30), set())
-
-    # the plain per-solve FP64 path serving the same arrivals, one at a time
-    fin = np.zeros(len(reqs))
-    with ats.Context(device) as ctx:
-        fp64_serve_one(ctx, 0)  # warm-up
-        t_start = time.perf_counter()
-        for k in range(len(reqs)):
-            delay = arrivals[k] - (time.perf_counter() - t_start)
-            if delay > 0:
-                time.sleep(delay)
-            fp64_serve_one(ctx, k)
-            fin[k] = time.perf_counter() - t_start
-        t_end = time.perf_counter()
-    lat64 = (fin - arrivals) * 1e3
+                fp64_serve_one(ctx, b, reqs[k]["tol"])
+                fin[k] = time.perf_counter() - t_start
+            t_end = time.perf_counter()
+        lat64 = (fin - arrivals) * 1e3
 
     checks = []
     if not args.no_cpu:
         with mp.get_context("spawn").Pool(max(1, len(sample))) as pool:
-            checks = pool.map(_serve_oracle_check, [(built[k], xs[k], rn[k]) for k in sorted(sample)], chunksize=1)
+            checks = pool.map(_serve_oracle_check, [(kept[k], xs[k], rn[k]) for k in sorted(sample)], chunksize=1)
 
     return {
-        "requests": len(reqs), "of": 2000, "max_cells": int(args.serve_max_cells),
-        "cells_mean": round(float(sizes.mean())), "build_s": round(build_s, 1),
+        "requests": n, "of": 2000, "max_cells": int(args.serve_max_cells),
         "arrival_rate_per_s": round(lam, 2), **served,
         "budget_4gb": served_small,
-        "fp64_per_solve": {"capacity": round(cap, 2), "throughput": round(len(reqs) / (t_end - t_start), 2),
+        "fp64_per_solve": {"capacity": round(cap, 2), "capacity_sample": int(n_cal),
+                           "throughput": round(n / (t_end - t_start), 2),
                            "p50_ms": round(float(np.percentile(lat64, 50)), 3),
                            "p99_ms": round(float(np.percentile(lat64, 99)), 3),
                            "path": "plain per-solve FP64 (level, build, solve), one request at a time in arrival "

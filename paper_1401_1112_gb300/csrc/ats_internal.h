@@ -207,20 +207,23 @@ struct ResArgs {
   int *tq_head;
   unsigned long long *cells;
   unsigned long long *t_solve;  // [n_solves][2] %globaltimer at a solve's start and end (profiling), or null
-  int cap;                      // shared-memory form: octs per CTA kept in shared memory
+  int cap;                      // shared-memory form: octs per CTA kept in shared memory (0: none)
 };
-// One resident launch on st: clusters of `cluster` CTAs of `threads` threads
-// (256 or 512), `grid` CTAs in all (a multiple of `cluster`) when the cluster
-// queue is not empty, else `grid` single CTAs.
+// One resident launch on st of the FP64 solver (CG state in global memory):
+// clusters of `cluster` CTAs of `threads` threads (256 or 512), `grid` CTAs
+// in all (a multiple of `cluster`) when the cluster queue is not empty, else
+// `grid` single CTAs.  fp64 = false: cudaErrorInvalidValue (the FP32-bulk
+// solver is launch_resident_smem).
 cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st,
                             bool cta_only = false);
 // Clusters of that shape resident at once on the current device (0: none).
 int resident_max_clusters(bool fp64, int threads, int cluster);
 // CTAs of the single-CTA kernel resident per SM.
 int resident_cta_blocks(bool fp64, int threads);
-// The resident solver with each CTA's K, z, p in shared memory (FP32 bulk):
-// a.cap octs per CTA (resident_smem_cap gives the largest that fits), one
-// CTA per SM; the same queue and grid conventions as launch_resident.
+// The resident solver of FP32-bulk solves with each CTA's K, z, p in shared
+// memory: a.cap octs per CTA (resident_smem_cap gives the largest that fits;
+// 0 keeps every array in global memory, with the same arithmetic), one CTA
+// per SM; the same queue and grid conventions as launch_resident.
 // cta_only: the single-CTA kernel only (the CTA queue), e.g. on the SMs a
 // concurrent cluster launch leaves free.
 cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st,

@@ -2071,8 +2071,9 @@ extern __shared__ __align__(128) unsigned char res2_smem[];
 // Two layouts of a CTA's shared memory, chosen per solve from the size of the
 // CTA's share: all six arrays K, z, p, D, q, e for up to kRes2Cap6 octs, or
 // K, z, p only (D, q, e in global memory) for up to kRes2Cap3 octs.  Each
-// array is eight cell planes of cap + 1 floats (oct `cap`: the stand-in
-// neighbour), followed by the 16-byte neighbour codes of the octs.
+// array is four pair planes (cells 2k, 2k+1 of each oct side by side) of
+// cap + 1 octs (oct `cap`: the stand-in neighbour), followed by the 16-byte
+// neighbour codes of the octs.
 constexpr int kRes2Cap3 = 2048;
 constexpr int kRes2Cap6 = 1100;
 constexpr size_t kRes2SmemBytes = (size_t)24 * (kRes2Cap3 + 1) * 4 + (size_t)kRes2Cap3 * 16;
@@ -2090,7 +2091,7 @@ template <int kCap, int kCapD>
 struct Res2Ctx {
   static constexpr int cap = kCap;    // octs of the CTA's share whose K, z, p are in shared memory
   static constexpr int capD = kCapD;  // ... whose D, q, e are (kCap or 0)
-  static constexpr uint32_t S = (uint32_t)(kCap + 1) * 4u;  // bytes of one cell plane
+  static constexpr uint32_t S = (uint32_t)(kCap + 1) * 8u;  // bytes of one pair plane
   uint32_t sK, sZ, sP, sD, sQ, sE, sC;  // shared-window addresses of this CTA's planes and codes
   int chunk;                // octs per CTA of the group
   int lo;                   // first oct of this CTA
@@ -2098,10 +2099,14 @@ struct Res2Ctx {
 };
 using Res2Six = Res2Ctx<kRes2Cap6, kRes2Cap6>;
 using Res2Three = Res2Ctx<kRes2Cap3, 0>;
+using Res2Global = Res2Ctx<0, 0>;  // every array in global memory (the stand-in row only in shared)
 
-// The eight cells of an oct from the planes of an array, a = the array's
-// address + 4 x the oct's local index (this CTA's shared memory, or, with the
-// _c forms, another CTA's through its shared::cluster address).
+// The eight cells of an oct from the pair planes of an array: pair plane k
+// holds cells 2k and 2k+1 of every oct (8 bytes per oct, S bytes per plane),
+// a = the array's address + 8 x the oct's local index (this CTA's shared
+// memory, or, with the _c forms, another CTA's through its shared::cluster
+// address).  Two cells per access halve the shared-memory instructions of the
+// own rows and of the y and z faces.
 __device__ __forceinline__ float ldsf(uint32_t a) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
@@ -2112,21 +2117,33 @@ __device__ __forceinline__ float ldscf(uint32_t a) {
   asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
   return v;
 }
+template <bool kRemote>
+__device__ __forceinline__ void lds2(uint32_t a, float &x, float &y) {
+  if (kRemote) asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+  else asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+}
 __device__ __forceinline__ void lds_cells(uint32_t a, uint32_t S, float (&v)[8]) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = ldsf(a + c * S);
+  for (int k = 0; k < 4; ++k) lds2<false>(a + k * S, v[2 * k], v[2 * k + 1]);
 }
 __device__ __forceinline__ void sts_cells(uint32_t a, uint32_t S, const float (&v)[8]) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) asm volatile("st.shared.f32 [%0], %1;" ::"r"(a + c * S), "f"(v[c]) : "memory");
+  for (int k = 0; k < 4; ++k)
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a + k * S), "f"(v[2 * k]), "f"(v[2 * k + 1]) : "memory");
 }
-// The four cells facing across axis A (those with bit A equal to NB).
+// The four cells facing across axis A (those with bit A equal to NB): one
+// cell of each pair across x, two whole pairs across y or z.
 template <int A, int NB, bool kRemote>
 __device__ __forceinline__ void lds_face(uint32_t a, uint32_t S, float (&v)[8]) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    if (((c >> A) & 1) != NB) continue;
-    v[c] = kRemote ? ldscf(a + c * S) : ldsf(a + c * S);
+  for (int k = 0; k < 4; ++k) {
+    if (A == 0) {
+      const uint32_t ak = a + k * S + 4u * NB;
+      v[2 * k + NB] = kRemote ? ldscf(ak) : ldsf(ak);
+    } else {
+      if ((((2 * k) >> A) & 1) != NB) continue;
+      lds2<kRemote>(a + k * S, v[2 * k], v[2 * k + 1]);
+    }
   }
 }
 
@@ -2160,7 +2177,7 @@ __device__ __forceinline__ Nb nb_of_global(const Cx &cx, int g) {
     return n;
   }
   n.r = (unsigned)r;
-  n.off = (uint32_t)l * 4u;
+  n.off = (uint32_t)l * 8u;
   n.kind = n.r == cx.cr ? 1 : 2;
   return n;
 }
@@ -2195,7 +2212,7 @@ __device__ __forceinline__ void res2_nbs(const Cx &cx, const SolveDev &sd, int o
         n = nb_of_global(cx, g);
       } else {
         n.r = c >> 12;
-        n.off = (uint32_t)(c & 0xFFF) * 4u;
+        n.off = (uint32_t)(c & 0xFFF) * 8u;
         n.kind = n.r == cx.cr ? 1 : 2;
       }
     }
@@ -2227,14 +2244,14 @@ __device__ __forceinline__ void res2_face(const Nb &n, uint32_t arr, uint32_t S,
 template <class Cx>
 __device__ __forceinline__ void res2_own(const Cx &cx, uint32_t arr, int cap, int l, const float *garr, int o,
                                          bool coherent, float (&v)[8]) {
-  if (l < cap) lds_cells(arr + (uint32_t)l * 4u, cx.S, v);
+  if (l < cap) lds_cells(arr + (uint32_t)l * 8u, cx.S, v);
   else if (coherent) ldc8(garr + 8 * o, v);
   else ld8_ro(garr + 8 * o, v);
 }
 template <class Cx>
 __device__ __forceinline__ void res2_own_store(const Cx &cx, uint32_t arr, int cap, int l, float *garr, int o,
                                                const float (&v)[8]) {
-  if (l < cap) sts_cells(arr + (uint32_t)l * 4u, cx.S, v);
+  if (l < cap) sts_cells(arr + (uint32_t)l * 8u, cx.S, v);
   else st8(garr + 8 * o, v);
 }
 
@@ -2310,14 +2327,14 @@ template <bool kCluster, class Cx>
 __device__ __forceinline__ float res2_op_oct_fast(const Cx &cx, const SolveDev &sd, int o, int l,
                                                   const uint32_t (&w)[3], float h) {
   float K[8], p[8], d[8];
-  lds_cells(cx.sK + (uint32_t)l * 4u, cx.S, K);
-  lds_cells(cx.sP + (uint32_t)l * 4u, cx.S, p);
+  lds_cells(cx.sK + (uint32_t)l * 8u, cx.S, K);
+  lds_cells(cx.sP + (uint32_t)l * 8u, cx.S, p);
   res2_own(cx, cx.sD, cx.capD, l, (const float *)sd.dg, o, true, d);
   uint32_t aK[6], aP[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
-    const uint32_t off = (c & 0xFFFu) * 4u;
+    const uint32_t off = (c & 0xFFFu) * 8u;
     if (kCluster) {
       aK[k] = cl_map_s(cx.sK + off, c >> 12);
       aP[k] = cl_map_s(cx.sP + off, c >> 12);
@@ -2427,7 +2444,7 @@ __device__ __forceinline__ void res2_xpe_oct(const Cx &cx, const SolveDev &sd, i
   }
   float e[8], z0[8];
   double xv[8];
-  lds_cells(cx.sE + (uint32_t)l * 4u, cx.S, e);
+  lds_cells(cx.sE + (uint32_t)l * 8u, cx.S, e);
   ldc8(sd.x64 + 8 * o, xv);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -2435,7 +2452,7 @@ __device__ __forceinline__ void res2_xpe_oct(const Cx &cx, const SolveDev &sd, i
     z0[c] = 0.f;
   }
   st8(sd.x64 + 8 * o, xv);
-  sts_cells(cx.sE + (uint32_t)l * 4u, cx.S, z0);
+  sts_cells(cx.sE + (uint32_t)l * 8u, cx.S, z0);
 }
 
 // One solve by one group, the CG state of its first octs in shared memory in
@@ -2464,12 +2481,12 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
   cx.cr = cr;
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(res2_smem);
   cx.sK = base;
-  cx.sZ = base + 8u * cx.S;
-  cx.sP = base + 16u * cx.S;
-  cx.sD = base + 24u * cx.S;  // the six-array layout only
-  cx.sQ = base + 32u * cx.S;
-  cx.sE = base + 40u * cx.S;
-  cx.sC = base + (six ? 48u : 24u) * cx.S;
+  cx.sZ = base + 4u * cx.S;
+  cx.sP = base + 8u * cx.S;
+  cx.sD = base + 12u * cx.S;  // the six-array layout only
+  cx.sQ = base + 16u * cx.S;
+  cx.sE = base + 20u * cx.S;
+  cx.sC = base + (six ? 24u : 12u) * cx.S;
   const int hi = min(n, cx.lo + cx.chunk);
   const int o0 = cx.lo + (int)threadIdx.x, stride = (int)blockDim.x;
   // stage in: K and the neighbour codes of the octs kept in shared memory
@@ -2482,21 +2499,21 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
       m1[c] = -1.f;
       z0[c] = 0.f;
     }
-    sts_cells(cx.sK + (uint32_t)cx.cap * 4u, cx.S, m1);
-    sts_cells(cx.sZ + (uint32_t)cx.cap * 4u, cx.S, z0);
-    sts_cells(cx.sP + (uint32_t)cx.cap * 4u, cx.S, z0);
+    sts_cells(cx.sK + (uint32_t)cx.cap * 8u, cx.S, m1);
+    sts_cells(cx.sZ + (uint32_t)cx.cap * 8u, cx.S, z0);
+    sts_cells(cx.sP + (uint32_t)cx.cap * 8u, cx.S, z0);
   }
   const uint16_t code_none = (uint16_t)((cr << 12) | (unsigned)cx.cap);
   for (int o = o0; o < hi && o - cx.lo < cx.cap; o += stride) {
     const int l = o - cx.lo;
     float K[8];
     ld8_ro((const float *)sd.KT + 8 * o, K);
-    sts_cells(cx.sK + (uint32_t)l * 4u, cx.S, K);
+    sts_cells(cx.sK + (uint32_t)l * 8u, cx.S, K);
     if (l < cx.capD) {  // the correction of the first inner solve starts at zero
       float z0[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) z0[c] = 0.f;
-      sts_cells(cx.sE + (uint32_t)l * 4u, cx.S, z0);
+      sts_cells(cx.sE + (uint32_t)l * 8u, cx.S, z0);
     }
     int g[6];
     load_nbr6(sd.nbr, o, g);
@@ -2644,16 +2661,19 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
 
 // One solve by one group: all six arrays in shared memory when the CTA's
 // share fits, else K, z and p (the share's size decides, the arithmetic is
-// the same).
-template <bool kCluster>
+// the same); kGlobal: every array in global memory (a kernel of its own, so
+// that the shared-memory kernels keep their register allocation).
+template <bool kCluster, bool kGlobal>
 __device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
   const unsigned cs = kCluster ? cl_size() : 1u;
   const int n = a.solves[s].n_oct;
   const int chunk = (int)((n + (int)cs - 1) / (int)cs);
-  if (chunk <= kRes2Cap6) res2_solve_l<kCluster, Res2Six>(a, s, sh, buf);
+  if (kGlobal) res2_solve_l<kCluster, Res2Global>(a, s, sh, buf);
+  else if (chunk <= kRes2Cap6) res2_solve_l<kCluster, Res2Six>(a, s, sh, buf);
   else res2_solve_l<kCluster, Res2Three>(a, s, sh, buf);
 }
 
+template <bool kGlobal>
 __device__ void res2_cta_loop(const ResArgs &a, ResShared<float> &sh, int &buf) {
   for (;;) {
     __syncthreads();  // every thread has read the previous task and left the previous solve
@@ -2663,13 +2683,13 @@ __device__ void res2_cta_loop(const ResArgs &a, ResShared<float> &sh, int &buf) 
     if (t >= a.n_tq) break;
     int s = a.tq[t];
     if (!idx_ok(s, a.n_solves)) continue;
-    res2_solve<false>(a, s, sh, buf);
+    res2_solve<false, kGlobal>(a, s, sh, buf);
   }
 }
 
 }  // namespace
 
-template <int NT>
+template <int NT, bool kGlobal>
 __global__ void __launch_bounds__(NT, 1) k_res2_cluster(ResArgs a) {
   __shared__ ResShared<float> sh;
   int buf = 0;
@@ -2683,17 +2703,17 @@ __global__ void __launch_bounds__(NT, 1) k_res2_cluster(ResArgs a) {
     const int t = sh.task;
     if (t >= a.n_cq) break;
     const int s = a.cq[t];
-    if (idx_ok(s, a.n_solves)) res2_solve<true>(a, s, sh, buf);
+    if (idx_ok(s, a.n_solves)) res2_solve<true, kGlobal>(a, s, sh, buf);
     cl_sync();  // every CTA is done with the shared rows before the next stage-in rewrites them
   }
-  res2_cta_loop(a, sh, buf);
+  res2_cta_loop<kGlobal>(a, sh, buf);
 }
 
-template <int NT>
+template <int NT, bool kGlobal>
 __global__ void __launch_bounds__(NT, 1) k_res2_cta(ResArgs a) {
   __shared__ ResShared<float> sh;
   int buf = 0;
-  res2_cta_loop(a, sh, buf);
+  res2_cta_loop<kGlobal>(a, sh, buf);
 }
 
 template <typename T, int NT>
@@ -2756,13 +2776,13 @@ static int res_cta_blocks_t() {
   return b;
 }
 
-template <int NT>
-static cudaError_t res2_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
+template <int NT, bool kG>
+static cudaError_t res2_launch_k(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
   const size_t smem = kRes2SmemBytes;
   if (a.n_cq > 0 && !cta_only) {
-    cudaError_t e = cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_res2_cluster<NT, kG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && cluster > 8)
-      e = cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      e = cudaFuncSetAttribute(k_res2_cluster<NT, kG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -2776,21 +2796,27 @@ static cudaError_t res2_launch_t(int cluster, int grid, const ResArgs &a, cudaSt
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_res2_cluster<NT>, a);
+    return cudaLaunchKernelEx(&cfg, k_res2_cluster<NT, kG>, a);
   }
-  cudaError_t e = cudaFuncSetAttribute(k_res2_cta<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_res2_cta<NT, kG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_res2_cta<NT><<<grid, NT, smem, st>>>(a);
+  k_res2_cta<NT, kG><<<grid, NT, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int NT>
+static cudaError_t res2_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
+  return a.cap == 0 ? res2_launch_k<NT, true>(cluster, grid, a, st, cta_only)
+                    : res2_launch_k<NT, false>(cluster, grid, a, st, cta_only);
 }
 
 template <int NT>
 static int res2_clusters_t(int cluster, int cap) {
   (void)cap;
   const size_t smem = kRes2SmemBytes;
-  if (cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_res2_cluster<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       (cluster > 8 &&
-       cudaFuncSetAttribute(k_res2_cluster<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+       cudaFuncSetAttribute(k_res2_cluster<NT, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
     cudaGetLastError();
     return 0;
   }
@@ -2806,7 +2832,7 @@ static int res2_clusters_t(int cluster, int cap) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_res2_cluster<NT>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, k_res2_cluster<NT, false>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -2820,8 +2846,8 @@ static int res2_cap_t(int device) {
   int optin = 0;
   cudaFuncAttributes fa, fb;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
-      cudaFuncGetAttributes(&fa, k_res2_cluster<NT>) != cudaSuccess ||
-      cudaFuncGetAttributes(&fb, k_res2_cta<NT>) != cudaSuccess) {
+      cudaFuncGetAttributes(&fa, k_res2_cluster<NT, false>) != cudaSuccess ||
+      cudaFuncGetAttributes(&fb, k_res2_cta<NT, false>) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -2831,13 +2857,14 @@ static int res2_cap_t(int device) {
 
 cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
   if (a.n_cq + a.n_tq <= 0) return cudaSuccess;
-  if (cluster < 1 || cluster > kMaxCluster || grid <= 0 || a.cap != kRes2Cap3) return cudaErrorInvalidValue;
+  if (cluster < 1 || cluster > kMaxCluster || grid <= 0 || (a.cap != kRes2Cap3 && a.cap != 0))
+    return cudaErrorInvalidValue;
   return threads >= 512 ? res2_launch_t<512>(cluster, grid, a, st, cta_only)
                         : res2_launch_t<256>(cluster, grid, a, st, cta_only);
 }
 
 int resident_smem_clusters(int threads, int cluster, int cap) {
-  if (cluster < 1 || cluster > kMaxCluster || cap <= 0) return 0;
+  if (cluster < 1 || cluster > kMaxCluster || cap < 0) return 0;
   return threads >= 512 ? res2_clusters_t<512>(cluster, cap) : res2_clusters_t<256>(cluster, cap);
 }
 
@@ -2849,22 +2876,20 @@ cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const
                             bool cta_only) {
   if (a.n_cq + a.n_tq <= 0) return cudaSuccess;
   if (cluster < 1 || cluster > kMaxCluster || grid <= 0) return cudaErrorInvalidValue;
-  if (fp64)
-    return threads >= 512 ? res_launch_t<double, 512>(cluster, grid, a, st, cta_only)
-                          : res_launch_t<double, 256>(cluster, grid, a, st, cta_only);
-  return threads >= 512 ? res_launch_t<float, 512>(cluster, grid, a, st, cta_only)
-                        : res_launch_t<float, 256>(cluster, grid, a, st, cta_only);
+  if (!fp64) return cudaErrorInvalidValue;  // FP32 bulk: launch_resident_smem
+  return threads >= 512 ? res_launch_t<double, 512>(cluster, grid, a, st, cta_only)
+                        : res_launch_t<double, 256>(cluster, grid, a, st, cta_only);
 }
 
 int resident_max_clusters(bool fp64, int threads, int cluster) {
   if (cluster < 1 || cluster > kMaxCluster) return 0;
-  if (fp64) return threads >= 512 ? res_clusters_t<double, 512>(cluster) : res_clusters_t<double, 256>(cluster);
-  return threads >= 512 ? res_clusters_t<float, 512>(cluster) : res_clusters_t<float, 256>(cluster);
+  if (!fp64) return 0;
+  return threads >= 512 ? res_clusters_t<double, 512>(cluster) : res_clusters_t<double, 256>(cluster);
 }
 
 int resident_cta_blocks(bool fp64, int threads) {
-  if (fp64) return threads >= 512 ? res_cta_blocks_t<double, 512>() : res_cta_blocks_t<double, 256>();
-  return threads >= 512 ? res_cta_blocks_t<float, 512>() : res_cta_blocks_t<float, 256>();
+  if (!fp64) return 0;
+  return threads >= 512 ? res_cta_blocks_t<double, 512>() : res_cta_blocks_t<double, 256>();
 }
 
 }  // namespace ats

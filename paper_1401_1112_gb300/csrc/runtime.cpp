@@ -570,10 +570,13 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
                                  ? INT64_MAX
                                  : (o.res_max_octs > 0 ? o.res_max_octs : (P->fp64 ? 2048 : 16384));
     const double big_work = o.res_big_work > 0 ? (double)o.res_big_work : 50000.0;
-    P->res_smem = !P->fp64 && o.res_state == 0;
+    // FP32 bulk: the shared-memory kernel, its CG state in shared memory
+    // (res_state 0, where the device has room) or in global memory (cap 0);
+    // FP64: the global-memory kernel
+    P->res_smem = !P->fp64;
     if (P->res_smem) {
-      P->res_cap = resident_smem_cap(P->res_threads, ctx->device);
-      if (P->res_cap <= 0) P->res_smem = false;
+      P->res_cap = o.res_state == 0 ? resident_smem_cap(P->res_threads, ctx->device) : 0;
+      if (P->res_cap < 0) P->res_cap = 0;
     }
     auto max_clusters = [&](int cl) {
       if (cl <= 0) return 0;
