@@ -195,6 +195,15 @@ typedef struct {
 #define ATS_SCHED_AUTO 0     /* resident solver for levels up to res_max_octs octs */
 #define ATS_SCHED_TICK 1     /* the tick path for every level                    */
 #define ATS_SCHED_RESIDENT 2 /* the resident solver for every level              */
+#define ATS_SCHED_GRID 3     /* as AUTO, and levels above res_max_octs (FP32 bulk) */
+        /* on the whole-GPU form of the resident solver: one cooperative launch, one */
+        /* CTA per SM, each CTA's run of octs with its K, z, p in shared memory, the */
+        /* faces across runs and the per-step sums through global memory, steps   */
+        /* ordered by a grid barrier whose waits give up after a bounded number of */
+        /* polls (the solve then ends with ATS_ERR_TIMEOUT); such levels run one   */
+        /* after another, after the other resident solves.  Measured slower than   */
+        /* the tick path on the GB300 at 32 768 - 262 144 octs (the grid barrier   */
+        /* and sums cost ~4 us each), so it is not the default.                   */
 
 /* initial guess of a solve (ats_solve_opts.x0) */
 #define ATS_X0_GIVEN 0 /* x_inout holds the initial guess on entry (default) */
@@ -567,6 +576,17 @@ ats_status ats_layout_neighbors(const ats_level_desc *desc, int32_t *nbr);
  * the call synchronises the device.  The default build has no checks and
  * sets *count = -1.  Errors: ATS_ERR_INVALID_ARG (null count), ATS_ERR_CUDA. */
 ats_status ats_bounds_violations(int device, long long *count);
+/* Self-test of the whole-GPU resident solver's grid barrier (the wait every
+ * CTA of its cooperative launch passes between CG steps): `ctas` CTAs (0 =
+ * one per SM) wait for ctas + extra arrivals.  extra = 0: every wait ends
+ * normally; extra > 0: no wait can end normally, and each must give up by
+ * itself after its bounded number of polls (about 0.2 s) and raise the
+ * solver's give-up flag -- the path that ends a solve with ATS_ERR_TIMEOUT
+ * instead of hanging the GPU.  *n_normal / *n_gave_up count the CTAs by how
+ * their wait ended, *ms is the launch's device time.  Errors:
+ * ATS_ERR_INVALID_ARG (null outputs, negative counts, more CTAs than SMs),
+ * ATS_ERR_CUDA (also when the flag disagrees with the waits). */
+ats_status ats_grid_barrier_selftest(int device, int ctas, int extra, int *n_normal, int *n_gave_up, double *ms);
 
 #ifdef __cplusplus
 }

@@ -80,7 +80,7 @@ class ats_hierarchy_desc(ctypes.Structure):
 
 
 ATS_ORDER_FINE_FIRST, ATS_ORDER_COARSE_FIRST = 0, 1
-ATS_SCHED_AUTO, ATS_SCHED_TICK, ATS_SCHED_RESIDENT = 0, 1, 2
+ATS_SCHED_AUTO, ATS_SCHED_TICK, ATS_SCHED_RESIDENT, ATS_SCHED_GRID = 0, 1, 2, 3
 
 
 class ats_kernel_stats(ctypes.Structure):
@@ -184,6 +184,8 @@ _SIGS = [
     ("ats_solve_noalloc", ctypes.c_int, [ctypes.c_int, P, ctypes.c_int64, P, P, P, ctypes.c_double, P, P,
                                          ctypes.c_double, ctypes.c_int, ctypes.POINTER(ats_solve_stats)]),
     ("ats_bounds_violations", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
+    ("ats_grid_barrier_selftest", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
 ]
 
 ATS_NOALLOC_MAX_CELLS = 262144
@@ -495,6 +497,15 @@ def ats_status_string(code: int) -> str:
 
 def ats_last_error() -> str:
     return lib().ats_last_error().decode(errors="replace")
+
+
+def ats_grid_barrier_selftest(device: int = 0, ctas: int = 0, extra: int = 0):
+    """One grid barrier of the whole-GPU resident solver alone: {"normal",
+    "gave_up", "ms"} (CTAs whose wait ended normally / gave up)."""
+    a, b, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().ats_grid_barrier_selftest(device, ctas, extra, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)),
+           "ats_grid_barrier_selftest")
+    return {"normal": a.value, "gave_up": b.value, "ms": t.value}
 
 
 def ats_bounds_violations(device: int = 0) -> int:

@@ -208,6 +208,17 @@ struct ResArgs {
   unsigned long long *cells;
   unsigned long long *t_solve;  // [n_solves][2] %globaltimer at a solve's start and end (profiling), or null
   int cap;                      // shared-memory form: octs per CTA kept in shared memory (0: none)
+  // whole-GPU form (launch_resident_grid): every CTA of one cooperative
+  // launch works on gq[0], gq[1], ... in turn; gbar = {arrivals, generation}
+  // of its grid barrier (zeroed before the launch), gpart = [2][grid + 1][3]
+  // (hi, lo) pairs: per buffer, each CTA's partial sums, then the totals;
+  // *gerr set when a barrier wait gave up
+  const int32_t *gq;
+  int n_gq;
+  unsigned *gbar;
+  float *gpart;
+  int *gerr;
+  int g_expect;  // arrivals a grid barrier waits for (0: every CTA of the launch)
 };
 // One resident launch on st of the FP64 solver (CG state in global memory):
 // clusters of `cluster` CTAs of `threads` threads (256 or 512), `grid` CTAs
@@ -230,6 +241,19 @@ cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResAr
                                  bool cta_only = false);
 int resident_smem_clusters(int threads, int cluster, int cap);
 int resident_smem_cap(int threads, int device);
+// The whole-GPU form of the shared-memory solver (FP32 bulk, 512-thread CTAs
+// only): one cooperative launch of `grid` CTAs (at most resident_grid_ctas,
+// 0 for other CTA sizes) solves gq[0, n_gq) one
+// level at a time, each level split into `grid` contiguous runs; sums and
+// steps go through global memory and a grid barrier whose waits end after a
+// bounded number of polls (then *gerr is set and the solve ends with
+// ATS_ERR_TIMEOUT).
+cudaError_t launch_resident_grid(int threads, int grid, const ResArgs &a, cudaStream_t st);
+int resident_grid_ctas(int threads, int device);
+// One grid barrier of that form alone (cooperative launch of `grid` CTAs of 32
+// threads) waiting for a.g_expect arrivals: out[cta] = 1 when its wait ended
+// normally, 0 when it gave up (and *a.gerr = 1).  a.gbar, a.gerr zeroed first.
+cudaError_t launch_grid_barrier_probe(int grid, const ResArgs &a, int *out, cudaStream_t st);
 
 // Start of a solve: e = 0 on every cell of every item, and x64 = src[solve]
 // where src (device array of device pointers) is non-null for that solve.

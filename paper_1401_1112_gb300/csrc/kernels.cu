@@ -37,7 +37,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <stdint.h>
+#include <vector>
 
 #include "ats_internal.h"
 
@@ -2096,6 +2098,8 @@ struct Res2Ctx {
   int chunk;                // octs per CTA of the group
   int lo;                   // first oct of this CTA
   unsigned cr;              // this CTA's rank in the group (0 for one CTA)
+  unsigned crc;             // the rank neighbour codes give this CTA's octs (cr in a cluster, else 0)
+  bool grid;                // a whole-GPU group: octs of other CTAs are read from global memory
 };
 using Res2Six = Res2Ctx<kRes2Cap6, kRes2Cap6>;
 using Res2Three = Res2Ctx<kRes2Cap3, 0>;
@@ -2178,14 +2182,15 @@ __device__ __forceinline__ Nb nb_of_global(const Cx &cx, int g) {
   }
   n.r = (unsigned)r;
   n.off = (uint32_t)l * 8u;
-  n.kind = n.r == cx.cr ? 1 : 2;
+  n.kind = n.r == cx.cr ? 1 : (cx.grid ? 3 : 2);
   return n;
 }
 template <class Cx>
 __device__ __forceinline__ uint16_t code_of_global(const Cx &cx, int g) {
   if (g < 0) return kCodeNone;
   const int r = g / cx.chunk, l = g - r * cx.chunk;
-  return l >= cx.cap ? kCodeGlobal : (uint16_t)((r << 12) | l);
+  if (l >= cx.cap || (cx.grid && (unsigned)r != cx.cr)) return kCodeGlobal;
+  return (uint16_t)(((cx.grid ? 0u : (unsigned)r) << 12) | (unsigned)l);
 }
 
 // The six neighbours of own oct o (local index l).
@@ -2213,7 +2218,7 @@ __device__ __forceinline__ void res2_nbs(const Cx &cx, const SolveDev &sd, int o
       } else {
         n.r = c >> 12;
         n.off = (uint32_t)(c & 0xFFF) * 8u;
-        n.kind = n.r == cx.cr ? 1 : 2;
+        n.kind = n.r == cx.crc ? 1 : 2;
       }
     }
   } else {
@@ -2387,6 +2392,8 @@ __device__ __forceinline__ float res2_op_any(const Cx &cx, const SolveDev &sd, i
 }
 
 // Step 1 on own oct o: p = z + beta p (first: p = z).
+// In a whole-GPU group the new p also goes to the global array, where the
+// other CTAs read the faces they need.
 template <class Cx>
 __device__ __forceinline__ void res2_dir_oct(const Cx &cx, const SolveDev &sd, int o, bool first, float beta) {
   const int l = o - cx.lo;
@@ -2396,6 +2403,7 @@ __device__ __forceinline__ void res2_dir_oct(const Cx &cx, const SolveDev &sd, i
 #pragma unroll
   for (int c = 0; c < 8; ++c) p[c] = first ? z[c] : fmaf(beta, p[c], z[c]);
   res2_own_store(cx, cx.sP, cx.cap, l, (float *)sd.p0, o, p);
+  if (cx.grid && l < cx.cap) st8((float *)sd.p0 + 8 * o, p);
 }
 
 // Step 3 on own oct o: r = D z - alpha q, z = r / D, e += alpha p.
@@ -2455,14 +2463,195 @@ __device__ __forceinline__ void res2_xpe_oct(const Cx &cx, const SolveDev &sd, i
   sts_cells(cx.sE + (uint32_t)l * 8u, cx.S, z0);
 }
 
+// ---- whole-GPU group: grid barrier and sums through global memory -------
+// Polls of the barrier's generation word before a wait gives up: with the
+// back-off (at most 128 ns of sleep between polls) a wait ends within about
+// half a second whatever happens to the other CTAs; a barrier of a running
+// solve takes microseconds.
+constexpr long long kGridSpinLimit = 1ll << 21;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// The grid barrier's generation poll, run by one thread of a CTA that has
+// arrived and was not the last: wait with a short back-off until the
+// generation moves past g.  Returns false when it gave up (then *gerr = 1).
+__device__ __forceinline__ bool grid_wait(const ResArgs &a, unsigned g) {
+  const unsigned *gen = a.gbar + 1;
+  unsigned ns = 16;
+  for (long long it = 0; ld_acquire_u32(gen) == g; ++it) {
+    if (it >= kGridSpinLimit) {
+      atomicOr(a.gerr, 1);
+      return false;
+    }
+    __nanosleep(ns);
+    if (ns < 128) ns <<= 1;
+  }
+  return true;
+}
+
+// Every CTA of the cooperative launch waits here until all have arrived; the
+// CTA's global writes before it are visible to every CTA after it.  Thread 0
+// reads the generation and arrives with an acquire-release add (after the
+// CTA barrier, so it releases the CTA's writes); the last arrival resets the
+// counter and publishes generation + 1, the others poll for it.  Returns
+// false in every thread of a CTA whose wait gave up.
+__device__ bool grid_sync(const ResArgs &a, int *flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned *cnt = a.gbar, *gen = a.gbar + 1;
+    const unsigned g = ld_acquire_u32(gen);
+    const unsigned expect = a.g_expect > 0 ? (unsigned)a.g_expect : gridDim.x;
+    int ok = 1;
+    if (atom_add_acq_rel_u32(cnt, 1u) == expect - 1) {
+      atomicExch(cnt, 0u);
+      st_release_u32(gen, g + 1);
+    } else {
+      ok = grid_wait(a, g) ? 1 : 0;
+    }
+    *flag = ok;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+
+// Sums of NA accumulators over every CTA of the launch.  Each CTA's total
+// (the same shuffle trees as a cluster's) goes to its slot of gpart (buffer
+// `buf`) and the CTA arrives at the grid barrier; the last CTA to arrive
+// merges the slots in rank order -- lane j takes ranks j, j + 32, ..., every
+// load issued before the merges -- with a shuffle tree, writes the totals
+// to the buffer's total slot and then opens the barrier; the others read the
+// totals once it is open.  All CTAs hold bitwise the same totals.  Thread 0
+// ends with them in `out`; the return value (thread 0) is false when its
+// wait gave up.  Slots and totals alternate between two buffers, written
+// again only after a barrier every reader has passed.
+constexpr int kGridMaxPerLane = 8;  // up to 256 CTAs in the launch
+template <int NA>
+__device__ bool grid_sum(Acc<float> (&a)[NA], ResShared<float> &sh, const ResArgs &ra, int &buf,
+                         Acc<float> (&out)[NA]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NA; ++k) warp_reduce_acc(a[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NA; ++k) sh.red[warp][k] = a[k];
+  }
+  __syncthreads();
+  int ok = 1;
+  if (warp == 0) {
+    Acc<float> m[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      if (lane < nw) m[k] = sh.red[lane][k];
+      warp_reduce_acc(m[k]);
+    }
+    const unsigned G = gridDim.x;
+    float *slots = ra.gpart + (size_t)buf * (G + 1) * 6;  // [G] CTA slots, then the totals
+    float *totals = slots + (size_t)G * 6;
+    unsigned g = 0;
+    int last = 0;
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        slots[blockIdx.x * 6 + 2 * k] = m[k].s;
+        slots[blockIdx.x * 6 + 2 * k + 1] = m[k].c;
+      }
+      unsigned *cnt = ra.gbar;
+      g = ld_acquire_u32(ra.gbar + 1);
+      const unsigned expect = ra.g_expect > 0 ? (unsigned)ra.g_expect : G;
+      last = atom_add_acq_rel_u32(cnt, 1u) == expect - 1;
+    }
+    last = __shfl_sync(kFull, last, 0);
+    __syncwarp();
+    if (last) {
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        float vs[kGridMaxPerLane], vc[kGridMaxPerLane];
+#pragma unroll
+        for (int i = 0; i < kGridMaxPerLane; ++i) {
+          const unsigned r = (unsigned)lane + 32u * i;
+          vs[i] = r < G ? __ldcg(slots + r * 6 + 2 * k) : 0.f;
+          vc[i] = r < G ? __ldcg(slots + r * 6 + 2 * k + 1) : 0.f;
+        }
+        Acc<float> t;
+#pragma unroll
+        for (int i = 0; i < kGridMaxPerLane; ++i) {
+          Acc<float> v;
+          v.s = vs[i];
+          v.c = vc[i];
+          t.merge(v);
+        }
+        warp_reduce_acc(t);
+        if (lane == 0) {
+          totals[2 * k] = t.s;
+          totals[2 * k + 1] = t.c;
+          out[k] = t;
+        }
+      }
+      if (lane == 0) {
+        atomicExch(ra.gbar, 0u);
+        st_release_u32(ra.gbar + 1, g + 1);
+      }
+    } else if (lane == 0) {
+      ok = grid_wait(ra, g) ? 1 : 0;
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          out[k].s = __ldcg(totals + 2 * k);
+          out[k].c = __ldcg(totals + 2 * k + 1);
+        }
+      }
+    }
+  }
+  buf ^= 1;
+  return ok != 0;
+}
+
+// The group's sum and barrier for group kind kG (0 one CTA, 1 a cluster, 2
+// the whole GPU); only the whole-GPU forms can fail: the sum reports it to
+// thread 0 (which holds the totals), the barrier to every thread.
+template <int NA, int kG>
+__device__ __forceinline__ bool res2_sum(Acc<float> (&acc)[NA], ResShared<float> &sh, const ResArgs &a, int &buf,
+                                         Acc<float> (&tot)[NA]) {
+  if (kG == 2) return grid_sum<NA>(acc, sh, a, buf, tot);
+  group_sum<float, NA, kG == 1>(acc, sh, buf, tot);
+  return true;
+}
+template <int kG>
+__device__ __forceinline__ bool res2_barrier(const ResArgs &a, ResShared<float> &sh) {
+  if (kG == 2) return grid_sync(a, &sh.task);
+  group_barrier<kG == 1>();
+  return true;
+}
+// A whole-GPU barrier gave up (thread 0): the solve ends with ATS_ERR_TIMEOUT.
+__device__ __forceinline__ void res2_timeout(ResState &st) {
+  st.status = ATS_ERR_TIMEOUT;
+  st.phase = kDone;
+}
+
 // One solve by one group, the CG state of its first octs in shared memory in
-// the layout Cx.
-template <bool kCluster, class Cx>
-__device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
+// the layout Cx.  kG: 0 one CTA, 1 a cluster, 2 the whole GPU (every CTA of
+// a cooperative launch).  Returns false when a grid barrier wait gave up (the solve then
+// ends with ATS_ERR_TIMEOUT).
+template <int kG, class Cx>
+__device__ bool res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
+  constexpr bool kCluster = kG == 1;
   constexpr int wd = (int)(sizeof(SolveDev) / 8);
   for (int w = threadIdx.x; w < wd; w += blockDim.x)
     reinterpret_cast<unsigned long long *>(&sh.sd)[w] = reinterpret_cast<const unsigned long long *>(a.solves + s)[w];
-  const unsigned cs = kCluster ? cl_size() : 1u, cr = kCluster ? cl_rank() : 0u;
+  const unsigned cs = kG == 2 ? gridDim.x : (kCluster ? cl_size() : 1u);
+  const unsigned cr = kG == 2 ? blockIdx.x : (kCluster ? cl_rank() : 0u);
   if (threadIdx.x == 0) {
     ResState z;
     memset(&z, 0, sizeof(z));
@@ -2479,6 +2668,8 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
   const bool six = Cx::capD > 0;
   cx.lo = min(n, (int)cr * cx.chunk);
   cx.cr = cr;
+  cx.crc = kCluster ? cr : 0u;
+  cx.grid = kG == 2;
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(res2_smem);
   cx.sK = base;
   cx.sZ = base + 4u * cx.S;
@@ -2503,7 +2694,7 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
     sts_cells(cx.sZ + (uint32_t)cx.cap * 8u, cx.S, z0);
     sts_cells(cx.sP + (uint32_t)cx.cap * 8u, cx.S, z0);
   }
-  const uint16_t code_none = (uint16_t)((cr << 12) | (unsigned)cx.cap);
+  const uint16_t code_none = (uint16_t)((cx.crc << 12) | (unsigned)cx.cap);
   for (int o = o0; o < hi && o - cx.lo < cx.cap; o += stride) {
     const int l = o - cx.lo;
     float K[8];
@@ -2539,8 +2730,9 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
     if (phase == kRefine) {
       Acc<float> acc[3], tot[3];
       for (int o = o0; o < hi; o += stride) res2_ref_oct(cx, sd, o, want_x, acc[0], acc[1], acc[2]);
-      group_sum<float, 3, kCluster>(acc, sh, buf, tot);
-      if (threadIdx.x == 0) {
+      const bool ok = res2_sum<3, kG>(acc, sh, a, buf, tot);
+      if (threadIdx.x == 0 && !ok) res2_timeout(sh.st);
+      if (threadIdx.x == 0 && ok) {
         ResState &st = sh.st;
         const double rnorm = sqrt(tot[0].get()), xnorm = sqrt(tot[1].get()), rz = tot[2].get();
         if (st.refines == 0) st.r0 = rnorm;
@@ -2579,14 +2771,18 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
       const bool first = sh.st.first != 0;
       const float beta = sh.st.betaf;
       for (int o = o0; o < hi; o += stride) res2_dir_oct(cx, sd, o, first, beta);
-      group_barrier<kCluster>();
+      if (!res2_barrier<kG>(a, sh)) {
+        if (threadIdx.x == 0) res2_timeout(sh.st);
+        break;
+      }
     }
     // step 2: q = (I + dt A) p, sum p.q
     {
       Acc<float> acc[1], tot[1];
       for (int o = o0; o < hi; o += stride) acc[0].add_value(res2_op_any<kCluster>(cx, sd, o, h));
-      group_sum<float, 1, kCluster>(acc, sh, buf, tot);
-      if (threadIdx.x == 0) {
+      const bool ok = res2_sum<1, kG>(acc, sh, a, buf, tot);
+      if (threadIdx.x == 0 && !ok) res2_timeout(sh.st);
+      if (threadIdx.x == 0 && ok) {
         ResState &st = sh.st;
         st.n_op += 1;
         st.n_first += st.first ? 1 : 0;
@@ -2605,8 +2801,9 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
         acc[0].add_value(lrz);
         acc[1].add_value(lrr);
       }
-      group_sum<float, 2, kCluster>(acc, sh, buf, tot);
-      if (threadIdx.x == 0) {
+      const bool ok = res2_sum<2, kG>(acc, sh, a, buf, tot);
+      if (threadIdx.x == 0 && !ok) res2_timeout(sh.st);
+      if (threadIdx.x == 0 && ok) {
         ResState &st = sh.st;
         st.iters += 1;
         st.inner_iters += 1;
@@ -2625,11 +2822,17 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
       }
       __syncthreads();
     }
+    if (sh.st.phase == kDone) break;
     if (sh.st.phase == kRefine) {
       for (int o = o0; o < hi; o += stride) res2_xpe_oct(cx, sd, o);
-      group_barrier<kCluster>();
+      if (!res2_barrier<kG>(a, sh)) {
+        if (threadIdx.x == 0) res2_timeout(sh.st);
+        break;
+      }
     }
   }
+  __syncthreads();  // thread 0's last state update is seen by all
+  const bool alive = sh.st.status != ATS_ERR_TIMEOUT;
   if (threadIdx.x == 0 && cr == 0) {
     const ResState &st = sh.st;
     SolveScalars f;
@@ -2657,20 +2860,21 @@ __device__ void res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
       atomicAdd(a.cells + 3, N * (unsigned long long)st.n_xpe);
     }
   }
+  return alive;
 }
 
 // One solve by one group: all six arrays in shared memory when the CTA's
 // share fits, else K, z and p (the share's size decides, the arithmetic is
 // the same); kGlobal: every array in global memory (a kernel of its own, so
 // that the shared-memory kernels keep their register allocation).
-template <bool kCluster, bool kGlobal>
-__device__ void res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
-  const unsigned cs = kCluster ? cl_size() : 1u;
+template <int kG, bool kGlobal>
+__device__ bool res2_solve(const ResArgs &a, int s, ResShared<float> &sh, int &buf) {
+  const unsigned cs = kG == 2 ? gridDim.x : (kG == 1 ? cl_size() : 1u);
   const int n = a.solves[s].n_oct;
   const int chunk = (int)((n + (int)cs - 1) / (int)cs);
-  if (kGlobal) res2_solve_l<kCluster, Res2Global>(a, s, sh, buf);
-  else if (chunk <= kRes2Cap6) res2_solve_l<kCluster, Res2Six>(a, s, sh, buf);
-  else res2_solve_l<kCluster, Res2Three>(a, s, sh, buf);
+  if (kGlobal) return res2_solve_l<kG, Res2Global>(a, s, sh, buf);
+  if (chunk <= kRes2Cap6) return res2_solve_l<kG, Res2Six>(a, s, sh, buf);
+  return res2_solve_l<kG, Res2Three>(a, s, sh, buf);
 }
 
 template <bool kGlobal>
@@ -2683,7 +2887,7 @@ __device__ void res2_cta_loop(const ResArgs &a, ResShared<float> &sh, int &buf) 
     if (t >= a.n_tq) break;
     int s = a.tq[t];
     if (!idx_ok(s, a.n_solves)) continue;
-    res2_solve<false, kGlobal>(a, s, sh, buf);
+    res2_solve<0, kGlobal>(a, s, sh, buf);
   }
 }
 
@@ -2703,7 +2907,7 @@ __global__ void __launch_bounds__(NT, 1) k_res2_cluster(ResArgs a) {
     const int t = sh.task;
     if (t >= a.n_cq) break;
     const int s = a.cq[t];
-    if (idx_ok(s, a.n_solves)) res2_solve<true, kGlobal>(a, s, sh, buf);
+    if (idx_ok(s, a.n_solves)) res2_solve<1, kGlobal>(a, s, sh, buf);
     cl_sync();  // every CTA is done with the shared rows before the next stage-in rewrites them
   }
   res2_cta_loop<kGlobal>(a, sh, buf);
@@ -2714,6 +2918,30 @@ __global__ void __launch_bounds__(NT, 1) k_res2_cta(ResArgs a) {
   __shared__ ResShared<float> sh;
   int buf = 0;
   res2_cta_loop<kGlobal>(a, sh, buf);
+}
+
+// The whole-GPU form: every CTA of one cooperative launch takes part in
+// every solve of the grid queue, in queue order.  After a barrier wait gave
+// up, the remaining solves are not started: CTA 0 records them as timed out.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_res2_grid(ResArgs a) {
+  __shared__ ResShared<float> sh;
+  int buf = 0;
+  bool alive = true;
+  for (int t = 0; t < a.n_gq; ++t) {
+    const int s = a.gq[t];
+    if (!idx_ok(s, a.n_solves)) continue;
+    if (alive) {
+      alive = res2_solve<2, false>(a, s, sh, buf);
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+      SolveScalars f;
+      memset(&f, 0, sizeof(f));
+      f.phase = kDone;
+      f.status = ATS_ERR_TIMEOUT;
+      a.final_sc[s] = f;
+    }
+    __syncthreads();  // every thread has left the solve before the next stage-in
+  }
 }
 
 template <typename T, int NT>
@@ -2872,6 +3100,72 @@ int resident_smem_cap(int threads, int device) {
   return threads >= 512 ? res2_cap_t<512>(device) : res2_cap_t<256>(device);
 }
 
+template <int NT>
+static cudaError_t res2_grid_launch_t(int grid, const ResArgs &a, cudaStream_t st) {
+  const size_t smem = kRes2SmemBytes;
+  cudaError_t e = cudaFuncSetAttribute(k_res2_grid<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_res2_grid<NT>, a);
+}
+
+template <int NT>
+static int res2_grid_ctas_t(int device) {
+  int b = 0, sms = 0;
+  if (cudaFuncSetAttribute(k_res2_grid<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRes2SmemBytes) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_res2_grid<NT>, NT, kRes2SmemBytes) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b * sms;
+}
+
+cudaError_t launch_resident_grid(int threads, int grid, const ResArgs &a, cudaStream_t st) {
+  if (a.n_gq <= 0) return cudaSuccess;
+  if (threads != 512 || grid <= 0 || grid > 32 * kGridMaxPerLane || a.cap != kRes2Cap3 || !a.gbar || !a.gpart ||
+      !a.gerr)
+    return cudaErrorInvalidValue;
+  return res2_grid_launch_t<512>(grid, a, st);
+}
+
+int resident_grid_ctas(int threads, int device) {
+  if (threads != 512) return 0;  // compiled for 512-thread CTAs only
+  return std::min(32 * kGridMaxPerLane, res2_grid_ctas_t<512>(device));
+}
+
+// One grid barrier of the whole-GPU form on its own, every CTA recording
+// whether its wait ended normally (out[cta] = 1) or gave up (0).
+__global__ void k_grid_barrier_probe(ResArgs a, int *out) {
+  __shared__ int flag;
+  const bool ok = grid_sync(a, &flag);
+  if (threadIdx.x == 0) out[blockIdx.x] = ok ? 1 : 0;
+}
+
+cudaError_t launch_grid_barrier_probe(int grid, const ResArgs &a, int *out, cudaStream_t st) {
+  if (grid <= 0 || !a.gbar || !a.gerr || !out) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_grid_barrier_probe, a, out);
+}
+
 cudaError_t launch_resident(bool fp64, int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st,
                             bool cta_only) {
   if (a.n_cq + a.n_tq <= 0) return cudaSuccess;
@@ -2917,4 +3211,68 @@ extern "C" ats_status ats_bounds_violations(int device, long long *count) {
   *count = -1;
 #endif
   return ATS_OK;
+}
+
+// One grid barrier of the whole-GPU solver, alone: `ctas` CTAs (0: one per
+// SM) wait for ctas + extra arrivals.  With extra > 0 nothing ever completes
+// the barrier, so every wait must give up on its own.
+extern "C" ats_status ats_grid_barrier_selftest(int device, int ctas, int extra, int *n_normal, int *n_gave_up,
+                                                double *ms) {
+  if (ctas < 0 || extra < 0 || !n_normal || !n_gave_up || !ms) return ATS_ERR_INVALID_ARG;
+  int sms = 0;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return ATS_ERR_CUDA;
+  }
+  const int grid = ctas > 0 ? ctas : sms;
+  if (grid > sms) return ATS_ERR_INVALID_ARG;  // one 32-thread CTA per SM is always co-resident
+  unsigned *bar = nullptr;
+  int *gerr = nullptr, *out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaMalloc(&bar, 2 * sizeof(unsigned));
+  if (err == cudaSuccess) err = cudaMalloc(&gerr, sizeof(int));
+  if (err == cudaSuccess) err = cudaMalloc(&out, sizeof(int) * grid);
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess) err = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (err == cudaSuccess) err = cudaMemsetAsync(gerr, 0, sizeof(int), st);
+  if (err == cudaSuccess) err = cudaMemsetAsync(out, 0xFF, sizeof(int) * grid, st);
+  ats::ResArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.gbar = bar;
+  a.gerr = gerr;
+  a.g_expect = grid + extra;
+  if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+  if (err == cudaSuccess) err = ats::launch_grid_barrier_probe(grid, a, out, st);
+  if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  std::vector<int> h(grid, -1);
+  int flag = 0;
+  float t = 0.f;
+  if (err == cudaSuccess) err = cudaMemcpy(h.data(), out, sizeof(int) * grid, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaMemcpy(&flag, gerr, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(bar);
+  cudaFree(gerr);
+  cudaFree(out);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return ATS_ERR_CUDA;
+  }
+  int normal = 0, gave_up = 0;
+  for (int v : h) {
+    normal += v == 1;
+    gave_up += v == 0;
+  }
+  *n_normal = normal;
+  *n_gave_up = gave_up;
+  *ms = (double)t;
+  // every wait that gave up must have raised the flag
+  return (gave_up > 0) == (flag != 0) ? ATS_OK : ATS_ERR_CUDA;
 }

@@ -244,11 +244,18 @@ struct Plan {
   // cluster solves, then the CTA solves, each by estimated work, largest first
   std::vector<int8_t> mode;
   int n_bq = 0, n_cq = 0, n_tq = 0, n_tick = 0, n_tick_items = 0;
+  // mode 4: the whole-GPU form (one cooperative launch of res_grid_all CTAs
+  // takes these solves one after another); its barrier, partial sums and
+  // give-up flag
+  int n_gq = 0, res_grid_all = 0;
+  unsigned *d_gbar = nullptr;
+  float *d_gpart = nullptr;
+  int *d_gerr = nullptr;
   int res_threads = 512, res_cluster = 8, res_cluster_big = 16, res_grid = 0, res_grid_big = 0;
   bool res_smem = false;  // K, z, p of each CTA's octs in shared memory (FP32 bulk)
   int res_cap = 0;        // octs per CTA kept in shared memory
   int res_fill = 0;       // single CTAs launched beside the clusters on the SMs they leave
-  int32_t *d_queue = nullptr;   // [n_bq + n_cq + n_tq]
+  int32_t *d_queue = nullptr;   // [n_bq + n_cq + n_tq + n_gq]
   int *d_heads = nullptr;       // [3] next position of each queue
   cudaStream_t aux2 = nullptr;  // the third concurrent resident launch
   cudaEvent_t join2 = nullptr;
@@ -405,6 +412,9 @@ void plan_free(Plan *P) {
   dev_free(ctx, P->d_xstage);
   dev_free(ctx, P->d_queue);
   dev_free(ctx, P->d_heads);
+  dev_free(ctx, P->d_gbar);
+  dev_free(ctx, P->d_gpart);
+  dev_free(ctx, P->d_gerr);
   dev_free(ctx, P->d_tsolve);
   dev_free(ctx, P->d_init);
   if (P->loop_ticks) cudaGraphDestroy(P->loop_ticks);
@@ -429,11 +439,12 @@ double est_work(const ats_level *L) {
 // Upload the resident queues of P in work order: big-cluster solves, cluster
 // solves, CTA solves.
 ats_status plan_upload_queues(Plan *P) {
-  std::vector<int32_t> bq, cq, tq;
+  std::vector<int32_t> bq, cq, tq, gq;
   for (int k = 0; k < P->n; ++k) {
     if (P->mode[k] == 3) bq.push_back(k);
     if (P->mode[k] == 1) cq.push_back(k);
     if (P->mode[k] == 2) tq.push_back(k);
+    if (P->mode[k] == 4) gq.push_back(k);
   }
   auto by_work = [&](std::vector<int32_t> &q) {
     std::vector<double> w(P->n, 0.0);
@@ -445,6 +456,7 @@ ats_status plan_upload_queues(Plan *P) {
   by_work(tq);
   bq.insert(bq.end(), cq.begin(), cq.end());
   bq.insert(bq.end(), tq.begin(), tq.end());
+  bq.insert(bq.end(), gq.begin(), gq.end());
   if (!bq.empty())
     CUDA_TRY(cudaMemcpyAsync(P->d_queue, bq.data(), sizeof(int32_t) * bq.size(), cudaMemcpyHostToDevice,
                              P->ctx->stream));
@@ -472,7 +484,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     set_error("bad x0");
     return ATS_ERR_INVALID_ARG;
   }
-  if (o.sched < ATS_SCHED_AUTO || o.sched > ATS_SCHED_RESIDENT || (o.res_threads != 0 && o.res_threads != 256 &&
+  if (o.sched < ATS_SCHED_AUTO || o.sched > ATS_SCHED_GRID || (o.res_threads != 0 && o.res_threads != 256 &&
       o.res_threads != 512) || o.res_cluster < 0 || o.res_cluster > 16 || o.res_max_octs < 0 || o.res_state < 0 ||
       o.res_state > 1 || o.res_cluster_big > 16 || o.res_big_work < 0) {
     set_error("bad resident-solver options (sched 0..2, res_threads 0/256/512, res_cluster and res_cluster_big "
@@ -583,10 +595,19 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       return P->res_smem ? resident_smem_clusters(P->res_threads, cl, P->res_cap)
                          : resident_max_clusters(P->fp64, P->res_threads, cl);
     };
+    // levels above the limit: the whole-GPU form when asked for (FP32 bulk,
+    // K, z, p of each CTA's run in shared memory), else the tick path
+    const int grid_all = (o.sched == ATS_SCHED_GRID && P->res_smem && P->res_cap > 0)
+                             ? resident_grid_ctas(P->res_threads, ctx->device)
+                             : 0;
     P->mode.assign(n, 0);
     for (int k = 0; k < n; ++k) {
       const int64_t no = P->levels[k]->n_oct;
-      if (!res_ok || no > max_octs) continue;
+      if (!res_ok) continue;
+      if (no > max_octs) {
+        if (grid_all > 0) P->mode[k] = 4;
+        continue;
+      }
       P->mode[k] = no <= cta_octs ? 2 : ((P->res_cluster_big > 0 && est_work(P->levels[k]) > big_work) ? 3 : 1);
     }
     int clA = 0, clB = 0;  // clusters of each size that fit the device at once
@@ -609,7 +630,9 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       P->n_cq += P->mode[k] == 1;
       P->n_tq += P->mode[k] == 2;
       P->n_tick += P->mode[k] == 0;
-      const double w = P->mode[k] ? est_work(P->levels[k]) : 0.0;
+      P->n_gq += P->mode[k] == 4;
+      if (P->mode[k] == 0 || P->mode[k] == 4) continue;
+      const double w = est_work(P->levels[k]);
       (P->mode[k] == 3 ? wA : P->mode[k] == 1 ? wB : wC) += w;
     }
     // the CTA slots of the device, shared by the launches in proportion to
@@ -634,6 +657,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     P->res_grid_big = kA * P->res_cluster_big;
     P->res_grid = P->n_bq + P->n_cq > 0 ? kB * P->res_cluster : slots;
     if (P->n_tq > 0 && P->n_bq + P->n_cq > 0) P->res_fill = std::max(0, slots - P->res_grid - P->res_grid_big);
+    if (P->n_gq > 0) P->res_grid_all = grid_all;
   }
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
   P->grid = std::max(1, std::min(P->n_items, bps * ctx->num_sms));
@@ -645,7 +669,10 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, 3 * (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 2 * kCellCounters, &P->d_cells)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, std::max(1, P->n_bq + P->n_cq + P->n_tq), &P->d_queue)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, std::max(1, P->n_bq + P->n_cq + P->n_tq + P->n_gq), &P->d_queue)) != ATS_OK ||
+      (P->n_gq > 0 && (s = dev_alloc_t(ctx, 2, &P->d_gbar)) != ATS_OK) ||
+      (P->n_gq > 0 && (s = dev_alloc_t(ctx, 12 * ((size_t)P->res_grid_all + 1), &P->d_gpart)) != ATS_OK) ||
+      (P->n_gq > 0 && (s = dev_alloc_t(ctx, 1, &P->d_gerr)) != ATS_OK) ||
       (s = dev_alloc_t(ctx, 3, &P->d_heads)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 4 * (size_t)P->n_items, &P->d_lists)) != ATS_OK ||
       (s = dev_alloc_t(ctx, (size_t)P->n_items, &P->d_ident)) != ATS_OK ||
@@ -722,7 +749,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
 // plan's two side streams, all three forked from and joined back into the
 // context stream (profiling: between the two timing events).
 ats_status plan_launch_resident(Plan *P, bool prof) {
-  if (P->n_bq + P->n_cq + P->n_tq == 0) return ATS_OK;
+  if (P->n_bq + P->n_cq + P->n_tq + P->n_gq == 0) return ATS_OK;
   cudaStream_t st = P->ctx->stream;
   ResArgs ra;
   std::memset(&ra, 0, sizeof(ra));
@@ -755,6 +782,7 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
     bool cta_only;
   };
   std::vector<L> ls;
+  const bool part = P->n_bq + P->n_cq + P->n_tq > 0;  // any solve for the cluster / CTA launches
   if (P->n_bq > 0) {
     ResArgs a = ra;
     a.cq = P->d_queue;
@@ -769,7 +797,7 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
     a.cq_head = P->d_heads + 1;
     ls.push_back({P->res_cluster, P->res_grid, a, false});
   }
-  if (ls.empty()) {
+  if (ls.empty() && part) {
     ResArgs a = ra;
     a.cq = P->d_queue;
     a.n_cq = 0;
@@ -792,8 +820,20 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
     if (i > 0) CUDA_TRY(cudaEventRecord(joins[i - 1], s2));
   }
   for (size_t i = 1; i < ls.size(); ++i) CUDA_TRY(cudaStreamWaitEvent(st, joins[i - 1], 0));
+  // the whole-GPU solves after the others (the cooperative launch needs every SM)
+  if (P->n_gq > 0) {
+    ResArgs a = ra;
+    a.gq = P->d_queue + P->n_bq + P->n_cq + P->n_tq;
+    a.n_gq = P->n_gq;
+    a.gbar = P->d_gbar;
+    a.gpart = P->d_gpart;
+    a.gerr = P->d_gerr;
+    CUDA_TRY(cudaMemsetAsync(P->d_gbar, 0, 2 * sizeof(unsigned), st));
+    CUDA_TRY(cudaMemsetAsync(P->d_gerr, 0, sizeof(int), st));
+    CUDA_TRY(launch_resident_grid(P->res_threads, P->res_grid_all, a, st));
+  }
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[1], st));
-  P->res_launches += (int)ls.size();
+  P->res_launches += (int)ls.size() + (P->n_gq > 0 ? 1 : 0);
   return ATS_OK;
 }
 
@@ -1235,7 +1275,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   }
   if (P->profiling) {
     plan_bytes(P, cells, &P->op_bytes, &P->ref_bytes, &P->upd_bytes);
-    if (P->n_bq + P->n_cq + P->n_tq > 0) {
+    if (P->n_bq + P->n_cq + P->n_tq + P->n_gq > 0) {
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, P->res_ev[0], P->res_ev[1]));
       P->res_ms = ms;
@@ -1260,7 +1300,10 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
         t0 = std::min(t0, ts[2 * k]);
         t1 = std::max(t1, ts[2 * k + 1]);
         const double d = (double)(ts[2 * k + 1] - ts[2 * k]) * 1e-6;
-        busy += d * (P->mode[k] == 1 ? P->res_cluster : P->mode[k] == 3 ? P->res_cluster_big : 1);
+        busy += d * (P->mode[k] == 1   ? P->res_cluster
+                     : P->mode[k] == 3 ? P->res_cluster_big
+                     : P->mode[k] == 4 ? P->res_grid_all
+                                       : 1);
         if (d > longest) {
           longest = d;
           P->res_longest = k;
@@ -1271,7 +1314,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
       for (int q = 0; q < 3; ++q) P->res_end_ms[q] = 0.0;
       for (int k = 0; k < n; ++k) {
         if (P->mode[k] == 0 || ts[2 * k + 1] < ts[2 * k] || t1 <= t0) continue;
-        const int q = P->mode[k] == 3 ? 0 : P->mode[k] == 1 ? 1 : 2;
+        const int q = (P->mode[k] == 3 || P->mode[k] == 4) ? 0 : P->mode[k] == 1 ? 1 : 2;
         P->res_end_ms[q] = std::max(P->res_end_ms[q], (double)(ts[2 * k + 1] - t0) * 1e-6);
       }
       P->res_longest_ms = longest;
@@ -2365,7 +2408,7 @@ ats_status ats_batch_kernel_stats(const ats_batch *B, ats_kernel_stats *out) {
     out->res_ms = P->res_ms;
     out->res_bytes = P->res_bytes;
     out->res_launches = P->res_launches;
-    out->res_solves = P->n_bq + P->n_cq + P->n_tq;
+    out->res_solves = P->n_bq + P->n_cq + P->n_tq + P->n_gq;
     out->res_span_ms = P->res_span_ms;
     out->res_longest_ms = P->res_longest_ms;
     out->res_occupancy = P->res_occupancy;
