@@ -248,6 +248,18 @@ struct Plan {
   // takes these solves one after another); its barrier, partial sums and
   // give-up flag
   int n_gq = 0, res_grid_all = 0;
+  // the split of the device's CTA slots between the three resident launches:
+  // clusters of each size that fit at once, the slots, and whether the split
+  // follows measured per-class SM-time (after a completed run) or the
+  // estimates
+  int res_clA = 0, res_clB = 0, res_slots = 0;
+  bool res_split_measured = false;
+  // measured duration (ns) of each resident solve in the last completed run;
+  // the queues are ordered by it (largest first) once every solve of a queue
+  // has one, uploaded again at the next start (queue_dirty)
+  std::vector<double> res_meas;
+  bool queue_dirty = false;
+  std::vector<int32_t> h_queue;  // the queue order last uploaded
   unsigned *d_gbar = nullptr;
   float *d_gpart = nullptr;
   int *d_gerr = nullptr;
@@ -262,7 +274,7 @@ struct Plan {
   cudaEvent_t res_ev[2] = {nullptr, nullptr};
   double res_ms = 0.0, res_bytes = 0.0;
   int res_launches = 0;
-  unsigned long long *d_tsolve = nullptr;  // [n][2] per-solve start / end (profiling)
+  unsigned long long *d_tsolve = nullptr;  // [n][2] per-solve start / end of the resident solves
   double res_span_ms = 0.0, res_longest_ms = 0.0, res_occupancy = 0.0, res_end_ms[3] = {0.0, 0.0, 0.0};
   int res_longest = -1;
 };
@@ -448,7 +460,9 @@ ats_status plan_upload_queues(Plan *P) {
   }
   auto by_work = [&](std::vector<int32_t> &q) {
     std::vector<double> w(P->n, 0.0);
-    for (int32_t k : q) w[k] = est_work(P->levels[k]);
+    bool meas = !P->res_meas.empty();
+    for (int32_t k : q) meas = meas && P->res_meas[k] > 0.0;
+    for (int32_t k : q) w[k] = meas ? P->res_meas[k] : est_work(P->levels[k]);
     std::stable_sort(q.begin(), q.end(), [&](int32_t a, int32_t b) { return w[a] > w[b]; });
   };
   by_work(bq);
@@ -457,11 +471,70 @@ ats_status plan_upload_queues(Plan *P) {
   bq.insert(bq.end(), cq.begin(), cq.end());
   bq.insert(bq.end(), tq.begin(), tq.end());
   bq.insert(bq.end(), gq.begin(), gq.end());
+  if (bq == P->h_queue) return ATS_OK;  // already on the device
+  P->h_queue = bq;
   if (!bq.empty())
-    CUDA_TRY(cudaMemcpyAsync(P->d_queue, bq.data(), sizeof(int32_t) * bq.size(), cudaMemcpyHostToDevice,
+    CUDA_TRY(cudaMemcpyAsync(P->d_queue, P->h_queue.data(), sizeof(int32_t) * bq.size(), cudaMemcpyHostToDevice,
                              P->ctx->stream));
   ++P->ctx->epoch;
   return ATS_OK;
+}
+
+// The CTA slots of the device, shared by the resident launches in proportion
+// to their queues' work wA (big clusters), wB (clusters), wC (single CTAs):
+// the single CTAs get at least their share (so the largest of them start at
+// once), the big clusters theirs in whole clusters, and the clusters every
+// remaining whole cluster; what is left runs single CTAs beside them.  A
+// cluster that has emptied its queue goes on with single-CTA solves.
+void plan_split(Plan *P, double wA, double wB, double wC) {
+  const int slots = P->res_slots, clA = P->res_clA, clB = P->res_clB;
+  const double wsum = std::max(1e-300, wA + wB + wC);
+  int kA = 0, kB = 0;
+  const int c_min = P->n_tq > 0 ? std::max(1, (int)std::ceil(slots * wC / wsum)) : 0;
+  if (P->n_bq > 0) kA = std::max(1, std::min(clA, (int)std::lround(slots * wA / wsum / P->res_cluster_big)));
+  if (P->n_bq > 0 && P->n_cq == 0)
+    kA = std::max(kA, std::min(clA, (slots - c_min) / P->res_cluster_big));
+  if (P->n_cq > 0)
+    kB = std::max(1, std::min(clB, (slots - kA * P->res_cluster_big - c_min) / P->res_cluster));
+  while (kA * P->res_cluster_big + kB * P->res_cluster + c_min > slots && (kA > 1 || kB > 1)) {
+    if (kA * P->res_cluster_big >= kB * P->res_cluster && kA > 1) --kA;
+    else if (kB > 1) --kB;
+    else --kA;
+  }
+  P->res_grid_big = kA * P->res_cluster_big;
+  P->res_grid = P->n_bq + P->n_cq > 0 ? kB * P->res_cluster : slots;
+  P->res_fill = (P->n_tq > 0 && P->n_bq + P->n_cq > 0) ? std::max(0, slots - P->res_grid - P->res_grid_big) : 0;
+}
+
+// After a completed run: the SM-time each class of resident solves took
+// (each solve's duration times its group's CTAs), from the solves' start and
+// end stamps; with two classes or more, the next run splits the slots by it.
+// Which group and layout a solve takes does not change, so neither do its
+// results.
+void plan_adapt_split(Plan *P, const std::vector<unsigned long long> &ts) {
+  double w[3] = {0.0, 0.0, 0.0};
+  int present = 0, measured = 0;
+  const int cls[3] = {P->n_bq, P->n_cq, P->n_tq};
+  for (int q = 0; q < 3; ++q) present += cls[q] > 0;
+  if (present < 1 || P->n < 2) return;
+  for (int k = 0; k < P->n; ++k) {
+    const int m = P->mode[k];
+    if (m < 1 || m > 3 || ts[2 * k + 1] <= ts[2 * k]) continue;
+    const double d = (double)(ts[2 * k + 1] - ts[2 * k]);
+    if (m == 3) w[0] += d * P->res_cluster_big;
+    else if (m == 1) w[1] += d * P->res_cluster;
+    else w[2] += d;
+  }
+  for (int q = 0; q < 3; ++q) measured += (cls[q] > 0 && w[q] > 0.0);
+  // each queue in the order of the measured durations (largest first)
+  P->res_meas.assign(P->n, 0.0);
+  for (int k = 0; k < P->n; ++k)
+    if (P->mode[k] >= 1 && P->mode[k] <= 3 && ts[2 * k + 1] > ts[2 * k])
+      P->res_meas[k] = (double)(ts[2 * k + 1] - ts[2 * k]);
+  P->queue_dirty = true;
+  if (measured != present) return;
+  plan_split(P, w[0], w[1], w[2]);
+  P->res_split_measured = true;
 }
 
 ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const ats_solve_opts *opts_in,
@@ -635,28 +708,13 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       const double w = est_work(P->levels[k]);
       (P->mode[k] == 3 ? wA : P->mode[k] == 1 ? wB : wC) += w;
     }
-    // the CTA slots of the device, shared by the launches in proportion to
-    // their queues' estimated work: big clusters, clusters (whole clusters,
-    // at least one when the queue is not empty) and single CTAs (at least
-    // their share, so the largest of them start at once); a cluster that has
-    // emptied its queue goes on with single-CTA solves
+    // the first split follows the estimated work; after each completed run,
+    // the measured SM-time of each class (plan_adapt_split)
     const int cta_per_sm = P->res_smem ? 1 : std::max(1, resident_cta_blocks(P->fp64, P->res_threads));
-    const int slots = cta_per_sm * ctx->num_sms;
-    const double wsum = std::max(1e-300, wA + wB + wC);
-    int kA = 0, kB = 0;
-    if (P->n_bq > 0) kA = std::max(1, std::min(clA, (int)std::lround(slots * wA / wsum / P->res_cluster_big)));
-    if (P->n_cq > 0) kB = std::max(1, std::min(clB, (int)std::lround(slots * wB / wsum / P->res_cluster)));
-    if (P->n_bq > 0 && P->n_cq == 0) kA = std::max(kA, std::min(clA, (int)((slots * (1.0 - wC / wsum)) / P->res_cluster_big)));
-    if (P->n_cq > 0 && P->n_bq == 0) kB = std::max(kB, std::min(clB, (int)((slots * (1.0 - wC / wsum)) / P->res_cluster)));
-    const int c_min = P->n_tq > 0 ? (int)std::ceil(slots * wC / wsum) : 0;
-    while (kA * P->res_cluster_big + kB * P->res_cluster + c_min > slots && (kA > 1 || kB > 1)) {
-      if (kA * P->res_cluster_big >= kB * P->res_cluster && kA > 1) --kA;
-      else if (kB > 1) --kB;
-      else --kA;
-    }
-    P->res_grid_big = kA * P->res_cluster_big;
-    P->res_grid = P->n_bq + P->n_cq > 0 ? kB * P->res_cluster : slots;
-    if (P->n_tq > 0 && P->n_bq + P->n_cq > 0) P->res_fill = std::max(0, slots - P->res_grid - P->res_grid_big);
+    P->res_slots = cta_per_sm * ctx->num_sms;
+    P->res_clA = clA;
+    P->res_clB = clB;
+    plan_split(P, wA, wB, wC);
     if (P->n_gq > 0) P->res_grid_all = grid_all;
   }
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
@@ -670,6 +728,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 2 * kCellCounters, &P->d_cells)) != ATS_OK ||
       (s = dev_alloc_t(ctx, std::max(1, P->n_bq + P->n_cq + P->n_tq + P->n_gq), &P->d_queue)) != ATS_OK ||
+      (P->n_bq + P->n_cq + P->n_tq + P->n_gq > 0 && (s = dev_alloc_t(ctx, 2 * (size_t)n, &P->d_tsolve)) != ATS_OK) ||
       (P->n_gq > 0 && (s = dev_alloc_t(ctx, 2, &P->d_gbar)) != ATS_OK) ||
       (P->n_gq > 0 && (s = dev_alloc_t(ctx, 12 * ((size_t)P->res_grid_all + 1), &P->d_gpart)) != ATS_OK) ||
       (P->n_gq > 0 && (s = dev_alloc_t(ctx, 1, &P->d_gerr)) != ATS_OK) ||
@@ -761,12 +820,10 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   ra.n_solves = P->n;
   ra.cg_scalars = P->opts.cg_scalars ? 1 : 0;
   ra.cells = prof ? P->d_cells + kCellCounters : nullptr;
-  if (prof && !P->d_tsolve) {
-    ats_status sa = dev_alloc_t(P->ctx, 2 * (size_t)P->n, &P->d_tsolve);
-    if (sa != ATS_OK) return sa;
-  }
-  if (prof) CUDA_TRY(cudaMemsetAsync(P->d_tsolve, 0, 2 * sizeof(unsigned long long) * P->n, st));
-  ra.t_solve = prof ? P->d_tsolve : nullptr;
+  // every resident solve stamps its start and end (the split of the next run
+  // follows them; profiling reads the timeline)
+  if (P->d_tsolve) CUDA_TRY(cudaMemsetAsync(P->d_tsolve, 0, 2 * sizeof(unsigned long long) * P->n, st));
+  ra.t_solve = P->d_tsolve;
   ra.cap = P->res_cap;
   CUDA_TRY(cudaMemsetAsync(P->d_heads, 0, 3 * sizeof(int), st));
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[0], st));
@@ -1080,8 +1137,13 @@ ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off
   if (stale) {
     ++ctx->epoch;
     CUDA_TRY(cudaMemcpyAsync(P->d_solves, P->h_solves.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice, st));
-    ats_status sq = plan_upload_queues(P);  // the work estimates follow dt
+    P->res_meas.clear();  // the work estimates follow dt
+    P->queue_dirty = true;
+  }
+  if (P->queue_dirty && !capture) {
+    ats_status sq = plan_upload_queues(P);
     if (sq != ATS_OK) return sq;
+    P->queue_dirty = false;
   }
   // copy-in of x: device x is read in place; host x goes through one staging
   // buffer, one copy per run of levels whose host arrays are contiguous
@@ -1321,6 +1383,12 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
       P->res_occupancy =
           P->res_span_ms > 0 ? busy / (P->res_span_ms * (P->res_grid + P->res_grid_big + P->res_fill)) : 0.0;
     }
+  }
+  // the next run's split of the slots between the resident launches
+  if (P->n_bq + P->n_cq + P->n_tq > 0 && P->d_tsolve) {
+    std::vector<unsigned long long> ts(2 * (size_t)n);
+    CUDA_TRY(cudaMemcpy(ts.data(), P->d_tsolve, sizeof(unsigned long long) * ts.size(), cudaMemcpyDeviceToHost));
+    plan_adapt_split(P, ts);
   }
   ats_status first_err = ATS_OK, first_warn = ATS_OK;
   for (int k = 0; k < n; ++k) {
