@@ -166,12 +166,13 @@ typedef struct {
                      /* distributed shared memory; default), 1 = global      */
                      /* memory (L2).  The FP64 bulk always uses global.      */
   int res_cluster_big; /* resident solver: CTAs per cluster for the levels    */
-                     /* whose estimated work exceeds res_big_work (0 = 16;  */
-                     /* < 0 = none: they take res_cluster)                  */
+                     /* whose runs on res_cluster CTAs would not fit their   */
+                     /* shared memory, or whose estimated work exceeds       */
+                     /* res_big_work (0 = 16; < 0 = none: res_cluster)       */
   int res_big_work;  /* resident solver: a level of more than res_cta_octs   */
-                     /* octs takes the larger clusters when its estimated   */
-                     /* work n_oct min(sqrt(1 + 8 h), 4 n_oct^(1/3)), h =   */
-                     /* dt / (2 dx^2), exceeds this (0 = 50000)             */
+                     /* octs also takes the larger clusters when its        */
+                     /* estimated work n_oct min(sqrt(1 + 8 h), 4 n_oct^(1/3)),*/
+                     /* h = dt / (2 dx^2), exceeds this (0 = no work rule)   */
 } ats_solve_opts;
 
 /* scheduling of a solve (ats_solve_opts.sched).  Which path a level takes
@@ -184,13 +185,15 @@ typedef struct {
  *   Resident solver: a solve runs from its first residual pass to its
  *   certificate inside one persistent launch, on one thread-block cluster of
  *   res_cluster CTAs (per-step sums exchanged through distributed shared
- *   memory, steps ordered by the hardware cluster barrier) of res_cluster
- *   CTAs, or of res_cluster_big CTAs for a level whose estimated work
- *   exceeds res_big_work, or on one CTA when the level has at most
+ *   memory, steps ordered by the hardware cluster barrier), or of
+ *   res_cluster_big CTAs for a level whose runs on res_cluster CTAs would
+ *   not fit their shared memory (or whose estimated work exceeds
+ *   res_big_work when set), or on one CTA when the level has at most
  *   res_cta_octs octs; clusters and CTAs take solves from work queues ordered
- *   by estimated work (largest first); the two cluster sizes and the single
- *   CTAs run as concurrent launches sharing the SMs in proportion to their
- *   queues' estimated work.  Not for the paper stopping rule (ATS_STOP_PAPER
+ *   by estimated work (largest first; after a completed run of a batch, by
+ *   the measured durations); the two cluster sizes and the single CTAs run as
+ *   concurrent launches sharing the SMs in proportion to their queues'
+ *   estimated work (after a completed run, their measured SM-time).  Not for the paper stopping rule (ATS_STOP_PAPER
  *   takes the tick path). */
 #define ATS_SCHED_AUTO 0     /* resident solver for levels up to res_max_octs octs */
 #define ATS_SCHED_TICK 1     /* the tick path for every level                    */

@@ -654,7 +654,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
     const int64_t max_octs = o.sched == ATS_SCHED_RESIDENT
                                  ? INT64_MAX
                                  : (o.res_max_octs > 0 ? o.res_max_octs : (P->fp64 ? 2048 : 16384));
-    const double big_work = o.res_big_work > 0 ? (double)o.res_big_work : 50000.0;
+    const double big_work = o.res_big_work > 0 ? (double)o.res_big_work : HUGE_VAL;  // 0: no work rule
     // FP32 bulk: the shared-memory kernel, its CG state in shared memory
     // (res_state 0, where the device has room) or in global memory (cap 0);
     // FP64: the global-memory kernel
@@ -681,7 +681,11 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
         if (grid_all > 0) P->mode[k] = 4;
         continue;
       }
-      P->mode[k] = no <= cta_octs ? 2 : ((P->res_cluster_big > 0 && est_work(P->levels[k]) > big_work) ? 3 : 1);
+      // a level whose runs on res_cluster CTAs would not fit their shared
+      // memory takes the big clusters too
+      const bool spills = P->res_cap > 0 && no > (int64_t)P->res_cluster * P->res_cap;
+      P->mode[k] = no <= cta_octs ? 2
+                                  : ((P->res_cluster_big > 0 && (est_work(P->levels[k]) > big_work || spills)) ? 3 : 1);
     }
     int clA = 0, clB = 0;  // clusters of each size that fit the device at once
     bool anyA = false, anyB = false;
