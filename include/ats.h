@@ -166,13 +166,18 @@ typedef struct {
                      /* distributed shared memory; default), 1 = global      */
                      /* memory (L2).  The FP64 bulk always uses global.      */
   int res_cluster_big; /* resident solver: CTAs per cluster for the levels    */
-                     /* whose runs on res_cluster CTAs would not fit their   */
-                     /* shared memory, or whose estimated work exceeds       */
-                     /* res_big_work (0 = 16; < 0 = none: res_cluster)       */
+                     /* whose runs on res_cluster_mid CTAs would not fit     */
+                     /* their shared memory, or whose estimated work         */
+                     /* exceeds res_big_work (0 = 16; < 0 = none)           */
   int res_big_work;  /* resident solver: a level of more than res_cta_octs   */
                      /* octs also takes the larger clusters when its        */
                      /* estimated work n_oct min(sqrt(1 + 8 h), 4 n_oct^(1/3)),*/
                      /* h = dt / (2 dx^2), exceeds this (0 = no work rule)   */
+  int res_cluster_mid; /* resident solver: CTAs per cluster for the levels    */
+                     /* whose runs on res_cluster CTAs would not fit their   */
+                     /* shared memory but whose runs on this many would     */
+                     /* (0 = 8; < 0 = none: they take res_cluster_big);     */
+                     /* used only between res_cluster and res_cluster_big   */
 } ats_solve_opts;
 
 /* scheduling of a solve (ats_solve_opts.sched).  Which path a level takes
@@ -185,13 +190,13 @@ typedef struct {
  *   Resident solver: a solve runs from its first residual pass to its
  *   certificate inside one persistent launch, on one thread-block cluster of
  *   res_cluster CTAs (per-step sums exchanged through distributed shared
- *   memory, steps ordered by the hardware cluster barrier), or of
- *   res_cluster_big CTAs for a level whose runs on res_cluster CTAs would
- *   not fit their shared memory (or whose estimated work exceeds
- *   res_big_work when set), or on one CTA when the level has at most
- *   res_cta_octs octs; clusters and CTAs take solves from work queues ordered
+ *   memory, steps ordered by the hardware cluster barrier); a level whose
+ *   runs on res_cluster CTAs would not fit their shared memory takes the
+ *   smallest of res_cluster_mid and res_cluster_big CTAs whose runs fit (or
+ *   res_cluster_big when its estimated work exceeds res_big_work, when
+ *   set); a level of at most res_cta_octs octs runs on one CTA; clusters and CTAs take solves from work queues ordered
  *   by estimated work (largest first; after a completed run of a batch, by
- *   the measured durations); the two cluster sizes and the single CTAs run as
+ *   the measured durations); the cluster sizes and the single CTAs run as
  *   concurrent launches sharing the SMs in proportion to their queues'
  *   estimated work (after a completed run, their measured SM-time).  Not for the paper stopping rule (ATS_STOP_PAPER
  *   takes the tick path). */
@@ -331,7 +336,8 @@ typedef struct {
   int res_grid;              /* CTAs of the resident launches                      */
   double res_end_ms[3];      /* end of the last big-cluster / cluster / one-CTA    */
                              /* solve, from the first resident solve's start       */
-  int res_grids[3];          /* CTAs of the big-cluster, cluster, one-CTA launches  */
+  int res_grids[3];          /* CTAs of the big- and middle-cluster, cluster and    */
+                             /* one-CTA launches                                  */
 } ats_kernel_stats;
 ats_status ats_batch_set_profiling(ats_batch *batch, int on);
 ats_status ats_batch_kernel_stats(const ats_batch *batch, ats_kernel_stats *out);

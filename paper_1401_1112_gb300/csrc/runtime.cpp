@@ -244,6 +244,7 @@ struct Plan {
   // cluster solves, then the CTA solves, each by estimated work, largest first
   std::vector<int8_t> mode;
   int n_bq = 0, n_cq = 0, n_tq = 0, n_tick = 0, n_tick_items = 0;
+  int n_mq = 0;  // mode 5: the middle clusters (res_cluster_mid CTAs)
   // mode 4: the whole-GPU form (one cooperative launch of res_grid_all CTAs
   // takes these solves one after another); its barrier, partial sums and
   // give-up flag
@@ -252,7 +253,7 @@ struct Plan {
   // clusters of each size that fit at once, the slots, and whether the split
   // follows measured per-class SM-time (after a completed run) or the
   // estimates
-  int res_clA = 0, res_clB = 0, res_slots = 0;
+  int res_clA = 0, res_clB = 0, res_clM = 0, res_slots = 0;
   bool res_split_measured = false;
   // measured duration (ns) of each resident solve in the last completed run;
   // the queues are ordered by it (largest first) once every solve of a queue
@@ -264,13 +265,14 @@ struct Plan {
   float *d_gpart = nullptr;
   int *d_gerr = nullptr;
   int res_threads = 512, res_cluster = 8, res_cluster_big = 16, res_grid = 0, res_grid_big = 0;
+  int res_cluster_mid = 8, res_grid_mid = 0;
   bool res_smem = false;  // K, z, p of each CTA's octs in shared memory (FP32 bulk)
   int res_cap = 0;        // octs per CTA kept in shared memory
   int res_fill = 0;       // single CTAs launched beside the clusters on the SMs they leave
-  int32_t *d_queue = nullptr;   // [n_bq + n_cq + n_tq + n_gq]
-  int *d_heads = nullptr;       // [3] next position of each queue
-  cudaStream_t aux2 = nullptr;  // the third concurrent resident launch
-  cudaEvent_t join2 = nullptr;
+  int32_t *d_queue = nullptr;   // [n_bq + n_mq + n_cq + n_tq + n_gq]
+  int *d_heads = nullptr;       // [4] next position of each queue: big, cluster, CTA, middle
+  cudaStream_t aux2 = nullptr, aux3 = nullptr;  // the third and fourth concurrent resident launches
+  cudaEvent_t join2 = nullptr, join3 = nullptr;
   cudaEvent_t res_ev[2] = {nullptr, nullptr};
   double res_ms = 0.0, res_bytes = 0.0;
   int res_launches = 0;
@@ -432,6 +434,8 @@ void plan_free(Plan *P) {
   if (P->loop_ticks) cudaGraphDestroy(P->loop_ticks);
   if (P->join2) cudaEventDestroy(P->join2);
   if (P->aux2) cudaStreamDestroy(P->aux2);
+  if (P->join3) cudaEventDestroy(P->join3);
+  if (P->aux3) cudaStreamDestroy(P->aux3);
   for (auto e : P->res_ev)
     if (e) cudaEventDestroy(e);
   if (P->h_active) cudaFreeHost(P->h_active);
@@ -451,9 +455,10 @@ double est_work(const ats_level *L) {
 // Upload the resident queues of P in work order: big-cluster solves, cluster
 // solves, CTA solves.
 ats_status plan_upload_queues(Plan *P) {
-  std::vector<int32_t> bq, cq, tq, gq;
+  std::vector<int32_t> bq, mq, cq, tq, gq;
   for (int k = 0; k < P->n; ++k) {
     if (P->mode[k] == 3) bq.push_back(k);
+    if (P->mode[k] == 5) mq.push_back(k);
     if (P->mode[k] == 1) cq.push_back(k);
     if (P->mode[k] == 2) tq.push_back(k);
     if (P->mode[k] == 4) gq.push_back(k);
@@ -466,8 +471,10 @@ ats_status plan_upload_queues(Plan *P) {
     std::stable_sort(q.begin(), q.end(), [&](int32_t a, int32_t b) { return w[a] > w[b]; });
   };
   by_work(bq);
+  by_work(mq);
   by_work(cq);
   by_work(tq);
+  bq.insert(bq.end(), mq.begin(), mq.end());
   bq.insert(bq.end(), cq.begin(), cq.end());
   bq.insert(bq.end(), tq.begin(), tq.end());
   bq.insert(bq.end(), gq.begin(), gq.end());
@@ -481,59 +488,83 @@ ats_status plan_upload_queues(Plan *P) {
 }
 
 // The CTA slots of the device, shared by the resident launches in proportion
-// to their queues' work wA (big clusters), wB (clusters), wC (single CTAs):
-// the single CTAs get at least their share (so the largest of them start at
-// once), the big clusters theirs in whole clusters, and the clusters every
-// remaining whole cluster; what is left runs single CTAs beside them.  A
-// cluster that has emptied its queue goes on with single-CTA solves.
-void plan_split(Plan *P, double wA, double wB, double wC) {
-  const int slots = P->res_slots, clA = P->res_clA, clB = P->res_clB;
-  const double wsum = std::max(1e-300, wA + wB + wC);
-  int kA = 0, kB = 0;
-  const int c_min = P->n_tq > 0 ? std::max(1, (int)std::ceil(slots * wC / wsum)) : 0;
-  if (P->n_bq > 0) kA = std::max(1, std::min(clA, (int)std::lround(slots * wA / wsum / P->res_cluster_big)));
-  if (P->n_bq > 0 && P->n_cq == 0)
-    kA = std::max(kA, std::min(clA, (slots - c_min) / P->res_cluster_big));
-  if (P->n_cq > 0)
-    kB = std::max(1, std::min(clB, (slots - kA * P->res_cluster_big - c_min) / P->res_cluster));
-  while (kA * P->res_cluster_big + kB * P->res_cluster + c_min > slots && (kA > 1 || kB > 1)) {
-    if (kA * P->res_cluster_big >= kB * P->res_cluster && kA > 1) --kA;
-    else if (kB > 1) --kB;
-    else --kA;
+// to their queues' work w[0] (big clusters), w[1] (middle clusters), w[2]
+// (clusters), w[3] (single CTAs): the single CTAs get at least their share
+// (so the largest of them start at once), the big and middle clusters theirs
+// in whole clusters, and the smallest cluster class present every remaining
+// whole cluster; what is left runs single CTAs beside them.  A cluster that
+// has emptied its queue goes on with single-CTA solves.
+void plan_split(Plan *P, const double (&w)[4]) {
+  const int slots = P->res_slots;
+  const int size[3] = {P->res_cluster_big, P->res_cluster_mid, P->res_cluster};
+  const int lim[3] = {P->res_clA, P->res_clM, P->res_clB};
+  const int cnt[3] = {P->n_bq, P->n_mq, P->n_cq};
+  const double wsum = std::max(1e-300, w[0] + w[1] + w[2] + w[3]);
+  const int c_min = P->n_tq > 0 ? std::max(1, (int)std::ceil(slots * w[3] / wsum)) : 0;
+  int k[3] = {0, 0, 0};
+  int last = -1;  // the smallest cluster class present takes the remainder
+  for (int q = 0; q < 3; ++q)
+    if (cnt[q] > 0) last = q;
+  int used = c_min;
+  for (int q = 0; q < 3; ++q) {
+    if (cnt[q] <= 0 || q == last) continue;
+    k[q] = std::max(1, std::min(lim[q], (int)std::lround(slots * w[q] / wsum / size[q])));
+    used += k[q] * size[q];
   }
-  P->res_grid_big = kA * P->res_cluster_big;
-  P->res_grid = P->n_bq + P->n_cq > 0 ? kB * P->res_cluster : slots;
-  P->res_fill = (P->n_tq > 0 && P->n_bq + P->n_cq > 0) ? std::max(0, slots - P->res_grid - P->res_grid_big) : 0;
+  if (last >= 0) k[last] = std::max(1, std::min(lim[last], (slots - used) / size[last]));
+  auto total = [&] { return k[0] * size[0] + k[1] * size[1] + k[2] * size[2] + c_min; };
+  while (total() > slots) {
+    int q_max = -1;
+    for (int q = 0; q < 3; ++q)
+      if (k[q] > 1 && (q_max < 0 || k[q] * size[q] > k[q_max] * size[q_max])) q_max = q;
+    if (q_max < 0) break;
+    --k[q_max];
+  }
+  P->res_grid_big = k[0] * size[0];
+  P->res_grid_mid = k[1] * size[1];
+  const bool clusters = P->n_bq + P->n_mq + P->n_cq > 0;
+  P->res_grid = clusters ? k[2] * size[2] : slots;
+  P->res_fill = (P->n_tq > 0 && clusters)
+                    ? std::max(0, slots - P->res_grid - P->res_grid_big - P->res_grid_mid)
+                    : 0;
+}
+
+// CTAs of each solve's group, by mode
+int group_ctas(const Plan *P, int mode) {
+  switch (mode) {
+    case 1: return P->res_cluster;
+    case 3: return P->res_cluster_big;
+    case 4: return P->res_grid_all;
+    case 5: return P->res_cluster_mid;
+    default: return 1;
+  }
 }
 
 // After a completed run: the SM-time each class of resident solves took
 // (each solve's duration times its group's CTAs), from the solves' start and
-// end stamps; with two classes or more, the next run splits the slots by it.
-// Which group and layout a solve takes does not change, so neither do its
-// results.
+// end stamps; the next run splits the slots by it and orders each queue by
+// the measured durations.  Which group and layout a solve takes does not
+// change, so neither do its results.
 void plan_adapt_split(Plan *P, const std::vector<unsigned long long> &ts) {
-  double w[3] = {0.0, 0.0, 0.0};
+  double w[4] = {0.0, 0.0, 0.0, 0.0};
   int present = 0, measured = 0;
-  const int cls[3] = {P->n_bq, P->n_cq, P->n_tq};
-  for (int q = 0; q < 3; ++q) present += cls[q] > 0;
+  const int cls[4] = {P->n_bq, P->n_mq, P->n_cq, P->n_tq};
+  for (int q = 0; q < 4; ++q) present += cls[q] > 0;
   if (present < 1 || P->n < 2) return;
+  auto class_of = [](int m) { return m == 3 ? 0 : m == 5 ? 1 : m == 1 ? 2 : m == 2 ? 3 : -1; };
   for (int k = 0; k < P->n; ++k) {
-    const int m = P->mode[k];
-    if (m < 1 || m > 3 || ts[2 * k + 1] <= ts[2 * k]) continue;
-    const double d = (double)(ts[2 * k + 1] - ts[2 * k]);
-    if (m == 3) w[0] += d * P->res_cluster_big;
-    else if (m == 1) w[1] += d * P->res_cluster;
-    else w[2] += d;
+    const int q = class_of(P->mode[k]);
+    if (q < 0 || ts[2 * k + 1] <= ts[2 * k]) continue;
+    w[q] += (double)(ts[2 * k + 1] - ts[2 * k]) * group_ctas(P, P->mode[k]);
   }
-  for (int q = 0; q < 3; ++q) measured += (cls[q] > 0 && w[q] > 0.0);
+  for (int q = 0; q < 4; ++q) measured += (cls[q] > 0 && w[q] > 0.0);
   // each queue in the order of the measured durations (largest first)
   P->res_meas.assign(P->n, 0.0);
   for (int k = 0; k < P->n; ++k)
-    if (P->mode[k] >= 1 && P->mode[k] <= 3 && ts[2 * k + 1] > ts[2 * k])
-      P->res_meas[k] = (double)(ts[2 * k + 1] - ts[2 * k]);
+    if (class_of(P->mode[k]) >= 0 && ts[2 * k + 1] > ts[2 * k]) P->res_meas[k] = (double)(ts[2 * k + 1] - ts[2 * k]);
   P->queue_dirty = true;
   if (measured != present) return;
-  plan_split(P, w[0], w[1], w[2]);
+  plan_split(P, w);
   P->res_split_measured = true;
 }
 
@@ -559,9 +590,9 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   }
   if (o.sched < ATS_SCHED_AUTO || o.sched > ATS_SCHED_GRID || (o.res_threads != 0 && o.res_threads != 256 &&
       o.res_threads != 512) || o.res_cluster < 0 || o.res_cluster > 16 || o.res_max_octs < 0 || o.res_state < 0 ||
-      o.res_state > 1 || o.res_cluster_big > 16 || o.res_big_work < 0) {
-    set_error("bad resident-solver options (sched 0..2, res_threads 0/256/512, res_cluster and res_cluster_big "
-              "up to 16, res_state 0/1)");
+      o.res_state > 1 || o.res_cluster_big > 16 || o.res_big_work < 0 || o.res_cluster_mid > 16) {
+    set_error("bad resident-solver options (sched 0..3, res_threads 0/256/512, res_cluster, res_cluster_mid and "
+              "res_cluster_big up to 16, res_state 0/1)");
     return ATS_ERR_INVALID_ARG;
   }
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -645,6 +676,10 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   P->res_threads = o.res_threads > 0 ? o.res_threads : (P->fp64 ? 256 : 512);
   P->res_cluster = o.res_cluster > 0 ? o.res_cluster : 4;
   P->res_cluster_big = o.res_cluster_big == 0 ? 16 : (o.res_cluster_big < 0 ? 0 : o.res_cluster_big);
+  P->res_cluster_mid = o.res_cluster_mid == 0 ? 8 : (o.res_cluster_mid < 0 ? 0 : o.res_cluster_mid);
+  // a middle size only between the two others
+  if (P->res_cluster_mid <= P->res_cluster || (P->res_cluster_big > 0 && P->res_cluster_mid >= P->res_cluster_big))
+    P->res_cluster_mid = 0;
   {
     const bool res_ok = o.sched != ATS_SCHED_TICK && o.stop_rule != ATS_STOP_PAPER;
     const int64_t cta_octs = o.res_cta_octs == 0 ? 2048 : o.res_cta_octs;
@@ -682,43 +717,52 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
         continue;
       }
       // a level whose runs on res_cluster CTAs would not fit their shared
-      // memory takes the big clusters too
-      const bool spills = P->res_cap > 0 && no > (int64_t)P->res_cluster * P->res_cap;
-      P->mode[k] = no <= cta_octs ? 2
-                                  : ((P->res_cluster_big > 0 && (est_work(P->levels[k]) > big_work || spills)) ? 3 : 1);
+      // memory takes the smallest larger cluster whose runs fit (the middle
+      // size, else the big one); the work rule sends it to the big clusters
+      const auto fits = [&](int cl) { return P->res_cap <= 0 || no <= (int64_t)cl * P->res_cap; };
+      if (no <= cta_octs) P->mode[k] = 2;
+      else if (P->res_cluster_big > 0 && est_work(P->levels[k]) > big_work) P->mode[k] = 3;
+      else if (fits(P->res_cluster)) P->mode[k] = 1;
+      else if (P->res_cluster_mid > 0 && fits(P->res_cluster_mid)) P->mode[k] = 5;
+      else P->mode[k] = P->res_cluster_big > 0 ? 3 : 1;
     }
-    int clA = 0, clB = 0;  // clusters of each size that fit the device at once
-    bool anyA = false, anyB = false;
+    int clA = 0, clM = 0, clB = 0;  // clusters of each size that fit the device at once
+    bool anyA = false, anyM = false, anyB = false;
     for (int k = 0; k < n; ++k) {
       anyA = anyA || P->mode[k] == 3;
+      anyM = anyM || P->mode[k] == 5;
       anyB = anyB || P->mode[k] == 1;
     }
     if (anyA) clA = max_clusters(P->res_cluster_big);
-    if (anyB || (anyA && clA <= 0)) clB = max_clusters(P->res_cluster);
+    if (anyM || (anyA && clA <= 0)) clM = max_clusters(P->res_cluster_mid);
+    if (anyB || anyM || anyA) clB = max_clusters(P->res_cluster);
     // a cluster shape that does not fit this device: its levels take the
     // smaller clusters, or the tick path
     for (int k = 0; k < n; ++k) {
-      if (P->mode[k] == 3 && clA <= 0) P->mode[k] = 1;
+      if (P->mode[k] == 3 && clA <= 0) P->mode[k] = P->res_cluster_mid > 0 ? 5 : 1;
+      if (P->mode[k] == 5 && clM <= 0) P->mode[k] = 1;
       if (P->mode[k] == 1 && clB <= 0) P->mode[k] = 0;
     }
-    double wA = 0, wB = 0, wC = 0;
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = 0; k < n; ++k) {
       P->n_bq += P->mode[k] == 3;
+      P->n_mq += P->mode[k] == 5;
       P->n_cq += P->mode[k] == 1;
       P->n_tq += P->mode[k] == 2;
       P->n_tick += P->mode[k] == 0;
       P->n_gq += P->mode[k] == 4;
       if (P->mode[k] == 0 || P->mode[k] == 4) continue;
-      const double w = est_work(P->levels[k]);
-      (P->mode[k] == 3 ? wA : P->mode[k] == 1 ? wB : wC) += w;
+      const int q = P->mode[k] == 3 ? 0 : P->mode[k] == 5 ? 1 : P->mode[k] == 1 ? 2 : 3;
+      w[q] += est_work(P->levels[k]);
     }
     // the first split follows the estimated work; after each completed run,
     // the measured SM-time of each class (plan_adapt_split)
     const int cta_per_sm = P->res_smem ? 1 : std::max(1, resident_cta_blocks(P->fp64, P->res_threads));
     P->res_slots = cta_per_sm * ctx->num_sms;
     P->res_clA = clA;
+    P->res_clM = clM;
     P->res_clB = clB;
-    plan_split(P, wA, wB, wC);
+    plan_split(P, w);
     if (P->n_gq > 0) P->res_grid_all = grid_all;
   }
   const int bps = tick_blocks_per_sm(P->fp64, P->paper);
@@ -731,12 +775,13 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, 3 * (size_t)P->n_items * kNumPartials, &P->d_partials)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_active)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 2 * kCellCounters, &P->d_cells)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, std::max(1, P->n_bq + P->n_cq + P->n_tq + P->n_gq), &P->d_queue)) != ATS_OK ||
-      (P->n_bq + P->n_cq + P->n_tq + P->n_gq > 0 && (s = dev_alloc_t(ctx, 2 * (size_t)n, &P->d_tsolve)) != ATS_OK) ||
+      (s = dev_alloc_t(ctx, std::max(1, P->n_bq + P->n_mq + P->n_cq + P->n_tq + P->n_gq), &P->d_queue)) != ATS_OK ||
+      (P->n_bq + P->n_mq + P->n_cq + P->n_tq + P->n_gq > 0 &&
+       (s = dev_alloc_t(ctx, 2 * (size_t)n, &P->d_tsolve)) != ATS_OK) ||
       (P->n_gq > 0 && (s = dev_alloc_t(ctx, 2, &P->d_gbar)) != ATS_OK) ||
       (P->n_gq > 0 && (s = dev_alloc_t(ctx, 12 * ((size_t)P->res_grid_all + 1), &P->d_gpart)) != ATS_OK) ||
       (P->n_gq > 0 && (s = dev_alloc_t(ctx, 1, &P->d_gerr)) != ATS_OK) ||
-      (s = dev_alloc_t(ctx, 3, &P->d_heads)) != ATS_OK ||
+      (s = dev_alloc_t(ctx, 4, &P->d_heads)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 4 * (size_t)P->n_items, &P->d_lists)) != ATS_OK ||
       (s = dev_alloc_t(ctx, (size_t)P->n_items, &P->d_ident)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 1, &P->d_ctl)) != ATS_OK ||
@@ -802,6 +847,8 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   CUDA_TRY(cudaEventCreate(&P->res_ev[1]));
   CUDA_TRY(cudaStreamCreateWithFlags(&P->aux2, cudaStreamNonBlocking));
   CUDA_TRY(cudaEventCreateWithFlags(&P->join2, cudaEventDisableTiming));
+  CUDA_TRY(cudaStreamCreateWithFlags(&P->aux3, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&P->join3, cudaEventDisableTiming));
   CUDA_TRY(cudaStreamSynchronize(st));
   *out = P;
   return ATS_OK;
@@ -812,13 +859,13 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
 // plan's two side streams, all three forked from and joined back into the
 // context stream (profiling: between the two timing events).
 ats_status plan_launch_resident(Plan *P, bool prof) {
-  if (P->n_bq + P->n_cq + P->n_tq + P->n_gq == 0) return ATS_OK;
+  if (P->n_bq + P->n_mq + P->n_cq + P->n_tq + P->n_gq == 0) return ATS_OK;
   cudaStream_t st = P->ctx->stream;
   ResArgs ra;
   std::memset(&ra, 0, sizeof(ra));
   ra.solves = P->d_solves;
   ra.final_sc = P->d_final;
-  ra.tq = P->d_queue + P->n_bq + P->n_cq;
+  ra.tq = P->d_queue + P->n_bq + P->n_mq + P->n_cq;
   ra.n_tq = P->n_tq;
   ra.tq_head = P->d_heads + 2;
   ra.n_solves = P->n;
@@ -829,7 +876,7 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   if (P->d_tsolve) CUDA_TRY(cudaMemsetAsync(P->d_tsolve, 0, 2 * sizeof(unsigned long long) * P->n, st));
   ra.t_solve = P->d_tsolve;
   ra.cap = P->res_cap;
-  CUDA_TRY(cudaMemsetAsync(P->d_heads, 0, 3 * sizeof(int), st));
+  CUDA_TRY(cudaMemsetAsync(P->d_heads, 0, 4 * sizeof(int), st));
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[0], st));
   auto launch = [&](int cluster, int grid, const ResArgs &a, cudaStream_t s2, bool cta_only) -> cudaError_t {
     return P->res_smem ? launch_resident_smem(P->res_threads, cluster, grid, a, s2, cta_only)
@@ -843,7 +890,7 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
     bool cta_only;
   };
   std::vector<L> ls;
-  const bool part = P->n_bq + P->n_cq + P->n_tq > 0;  // any solve for the cluster / CTA launches
+  const bool part = P->n_bq + P->n_mq + P->n_cq + P->n_tq > 0;  // any solve for the cluster / CTA launches
   if (P->n_bq > 0) {
     ResArgs a = ra;
     a.cq = P->d_queue;
@@ -851,9 +898,16 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
     a.cq_head = P->d_heads;
     ls.push_back({P->res_cluster_big, P->res_grid_big, a, false});
   }
-  if (P->n_cq > 0) {
+  if (P->n_mq > 0) {
     ResArgs a = ra;
     a.cq = P->d_queue + P->n_bq;
+    a.n_cq = P->n_mq;
+    a.cq_head = P->d_heads + 3;
+    ls.push_back({P->res_cluster_mid, P->res_grid_mid, a, false});
+  }
+  if (P->n_cq > 0) {
+    ResArgs a = ra;
+    a.cq = P->d_queue + P->n_bq + P->n_mq;
     a.n_cq = P->n_cq;
     a.cq_head = P->d_heads + 1;
     ls.push_back({P->res_cluster, P->res_grid, a, false});
@@ -871,8 +925,8 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
     a.cq_head = P->d_heads;
     ls.push_back({1, P->res_fill, a, true});
   }
-  cudaStream_t side[2] = {P->fj.aux, P->aux2};
-  cudaEvent_t joins[2] = {P->fj.join, P->join2};
+  cudaStream_t side[3] = {P->fj.aux, P->aux2, P->aux3};
+  cudaEvent_t joins[3] = {P->fj.join, P->join2, P->join3};
   if (ls.size() > 1) CUDA_TRY(cudaEventRecord(P->fj.fork, st));
   for (size_t i = 0; i < ls.size(); ++i) {
     cudaStream_t s2 = i == 0 ? st : side[i - 1];
@@ -884,7 +938,7 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   // the whole-GPU solves after the others (the cooperative launch needs every SM)
   if (P->n_gq > 0) {
     ResArgs a = ra;
-    a.gq = P->d_queue + P->n_bq + P->n_cq + P->n_tq;
+    a.gq = P->d_queue + P->n_bq + P->n_mq + P->n_cq + P->n_tq;
     a.n_gq = P->n_gq;
     a.gbar = P->d_gbar;
     a.gpart = P->d_gpart;
@@ -1341,7 +1395,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   }
   if (P->profiling) {
     plan_bytes(P, cells, &P->op_bytes, &P->ref_bytes, &P->upd_bytes);
-    if (P->n_bq + P->n_cq + P->n_tq + P->n_gq > 0) {
+    if (P->n_bq + P->n_mq + P->n_cq + P->n_tq + P->n_gq > 0) {
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, P->res_ev[0], P->res_ev[1]));
       P->res_ms = ms;
@@ -1366,10 +1420,7 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
         t0 = std::min(t0, ts[2 * k]);
         t1 = std::max(t1, ts[2 * k + 1]);
         const double d = (double)(ts[2 * k + 1] - ts[2 * k]) * 1e-6;
-        busy += d * (P->mode[k] == 1   ? P->res_cluster
-                     : P->mode[k] == 3 ? P->res_cluster_big
-                     : P->mode[k] == 4 ? P->res_grid_all
-                                       : 1);
+        busy += d * group_ctas(P, P->mode[k]);
         if (d > longest) {
           longest = d;
           P->res_longest = k;
@@ -1380,16 +1431,18 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
       for (int q = 0; q < 3; ++q) P->res_end_ms[q] = 0.0;
       for (int k = 0; k < n; ++k) {
         if (P->mode[k] == 0 || ts[2 * k + 1] < ts[2 * k] || t1 <= t0) continue;
-        const int q = (P->mode[k] == 3 || P->mode[k] == 4) ? 0 : P->mode[k] == 1 ? 1 : 2;
+        const int q = (P->mode[k] == 3 || P->mode[k] == 4 || P->mode[k] == 5) ? 0 : P->mode[k] == 1 ? 1 : 2;
         P->res_end_ms[q] = std::max(P->res_end_ms[q], (double)(ts[2 * k + 1] - t0) * 1e-6);
       }
       P->res_longest_ms = longest;
       P->res_occupancy =
-          P->res_span_ms > 0 ? busy / (P->res_span_ms * (P->res_grid + P->res_grid_big + P->res_fill)) : 0.0;
+          P->res_span_ms > 0
+              ? busy / (P->res_span_ms * (P->res_grid + P->res_grid_big + P->res_grid_mid + P->res_fill))
+              : 0.0;
     }
   }
   // the next run's split of the slots between the resident launches
-  if (P->n_bq + P->n_cq + P->n_tq > 0 && P->d_tsolve) {
+  if (P->n_bq + P->n_mq + P->n_cq + P->n_tq > 0 && P->d_tsolve) {
     std::vector<unsigned long long> ts(2 * (size_t)n);
     CUDA_TRY(cudaMemcpy(ts.data(), P->d_tsolve, sizeof(unsigned long long) * ts.size(), cudaMemcpyDeviceToHost));
     plan_adapt_split(P, ts);
@@ -2401,7 +2454,7 @@ ats_status ats_batch_autotune(ats_batch *B, double *const *x_inout, const int *t
             cands.push_back(o);
           }
       }
-      if (P->n_bq + P->n_cq + P->n_tq > 0) {
+      if (P->n_bq + P->n_mq + P->n_cq + P->n_tq > 0) {
         // (threads per CTA, cluster size, one-CTA limit, big-cluster size; -1 = none)
         static const int kShapes[][4] = {{512, 4, 2048, 16}, {512, 8, 2048, 16}, {512, 8, 2048, -1},
                                          {256, 4, 2048, 16}, {512, 4, 1024, 16}, {512, 2, 2048, 16},
@@ -2480,14 +2533,14 @@ ats_status ats_batch_kernel_stats(const ats_batch *B, ats_kernel_stats *out) {
     out->res_ms = P->res_ms;
     out->res_bytes = P->res_bytes;
     out->res_launches = P->res_launches;
-    out->res_solves = P->n_bq + P->n_cq + P->n_tq + P->n_gq;
+    out->res_solves = P->n_bq + P->n_mq + P->n_cq + P->n_tq + P->n_gq;
     out->res_span_ms = P->res_span_ms;
     out->res_longest_ms = P->res_longest_ms;
     out->res_occupancy = P->res_occupancy;
     out->res_longest = P->res_longest;
-    out->res_grid = P->res_grid + P->res_grid_big + P->res_fill;
+    out->res_grid = P->res_grid + P->res_grid_big + P->res_grid_mid + P->res_fill;
     for (int q = 0; q < 3; ++q) out->res_end_ms[q] = P->res_end_ms[q];
-    out->res_grids[0] = P->res_grid_big;
+    out->res_grids[0] = P->res_grid_big + P->res_grid_mid;
     out->res_grids[1] = P->res_grid;
     out->res_grids[2] = P->res_fill;
     return ATS_OK;
