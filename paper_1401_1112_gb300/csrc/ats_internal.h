@@ -236,9 +236,10 @@ int resident_cta_blocks(bool fp64, int threads);
 // 0 keeps every array in global memory, with the same arithmetic), one CTA
 // per SM; the same queue and grid conventions as launch_resident.
 // cta_only: the single-CTA kernel only (the CTA queue), e.g. on the SMs a
-// concurrent cluster launch leaves free.
+// concurrent cluster launch leaves free.  priority: the launch's scheduling
+// priority (cudaLaunchAttributePriority; lower numbers first, 0 = default).
 cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st,
-                                 bool cta_only = false);
+                                 bool cta_only = false, int priority = 0);
 int resident_smem_clusters(int threads, int cluster, int cap);
 int resident_smem_cap(int threads, int device);
 // The whole-GPU form of the shared-memory solver (FP32 bulk, 512-thread CTAs
@@ -249,6 +250,10 @@ int resident_smem_cap(int threads, int device);
 // bounded number of polls (then *gerr is set and the solve ends with
 // ATS_ERR_TIMEOUT).
 cudaError_t launch_resident_grid(int threads, int grid, const ResArgs &a, cudaStream_t st);
+// A one-thread kernel on st that returns after about ns nanoseconds (bounded
+// by a fixed number of clock reads): the work queued behind it on st starts
+// that much later.
+cudaError_t launch_hold(unsigned long long ns, cudaStream_t st);
 int resident_grid_ctas(int threads, int device);
 // One grid barrier of that form alone (cooperative launch of `grid` CTAs of 32
 // threads) waiting for a.g_expect arrivals: out[cta] = 1 when its wait ended

@@ -3005,8 +3005,12 @@ static int res_cta_blocks_t() {
 }
 
 template <int NT, bool kG>
-static cudaError_t res2_launch_k(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
+static cudaError_t res2_launch_k(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only,
+                                 int priority) {
   const size_t smem = kRes2SmemBytes;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = priority;
   if (a.n_cq > 0 && !cta_only) {
     cudaError_t e = cudaFuncSetAttribute(k_res2_cluster<NT, kG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && cluster > 8)
@@ -3017,25 +3021,31 @@ static cudaError_t res2_launch_k(int cluster, int grid, const ResArgs &a, cudaSt
     cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = (unsigned)cluster;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k_res2_cluster<NT, kG>, a);
   }
   cudaError_t e = cudaFuncSetAttribute(k_res2_cta<NT, kG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_res2_cta<NT, kG><<<grid, NT, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_res2_cta<NT, kG>, a);
 }
 
 template <int NT>
-static cudaError_t res2_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
-  return a.cap == 0 ? res2_launch_k<NT, true>(cluster, grid, a, st, cta_only)
-                    : res2_launch_k<NT, false>(cluster, grid, a, st, cta_only);
+static cudaError_t res2_launch_t(int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only,
+                                 int priority) {
+  return a.cap == 0 ? res2_launch_k<NT, true>(cluster, grid, a, st, cta_only, priority)
+                    : res2_launch_k<NT, false>(cluster, grid, a, st, cta_only, priority);
 }
 
 template <int NT>
@@ -3083,12 +3093,13 @@ static int res2_cap_t(int device) {
   return (size_t)optin >= stat + kRes2SmemBytes ? kRes2Cap3 : 0;
 }
 
-cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only) {
+cudaError_t launch_resident_smem(int threads, int cluster, int grid, const ResArgs &a, cudaStream_t st, bool cta_only,
+                                 int priority) {
   if (a.n_cq + a.n_tq <= 0) return cudaSuccess;
   if (cluster < 1 || cluster > kMaxCluster || grid <= 0 || (a.cap != kRes2Cap3 && a.cap != 0))
     return cudaErrorInvalidValue;
-  return threads >= 512 ? res2_launch_t<512>(cluster, grid, a, st, cta_only)
-                        : res2_launch_t<256>(cluster, grid, a, st, cta_only);
+  return threads >= 512 ? res2_launch_t<512>(cluster, grid, a, st, cta_only, priority)
+                        : res2_launch_t<256>(cluster, grid, a, st, cta_only, priority);
 }
 
 int resident_smem_clusters(int threads, int cluster, int cap) {
@@ -3129,6 +3140,19 @@ static int res2_grid_ctas_t(int device) {
     return 0;
   }
   return b * sms;
+}
+
+// A one-thread kernel that returns after `ns` nanoseconds of %globaltimer
+// (or after 2^20 reads of it, whichever comes first): it holds back the work
+// queued behind it on its stream.
+__global__ void k_hold(unsigned long long ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (int it = 0; it < (1 << 20) && globaltimer_ns() - t0 < ns; ++it) __nanosleep(256);
+}
+
+cudaError_t launch_hold(unsigned long long ns, cudaStream_t st) {
+  k_hold<<<1, 1, 0, st>>>(ns);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_resident_grid(int threads, int grid, const ResArgs &a, cudaStream_t st) {

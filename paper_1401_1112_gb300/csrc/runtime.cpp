@@ -878,8 +878,21 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   ra.cap = P->res_cap;
   CUDA_TRY(cudaMemsetAsync(P->d_heads, 0, 4 * sizeof(int), st));
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[0], st));
+  // the larger clusters first: they need that many free SMs of one GPC at
+  // once, so their CTAs are scheduled ahead of the smaller groups' (launch
+  // priorities from the device's greatest down, single CTAs at the default)
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+    cudaGetLastError();
+    prio_least = prio_greatest = 0;
+  }
   auto launch = [&](int cluster, int grid, const ResArgs &a, cudaStream_t s2, bool cta_only) -> cudaError_t {
-    return P->res_smem ? launch_resident_smem(P->res_threads, cluster, grid, a, s2, cta_only)
+    const int rank = cta_only                                                   ? 3
+                     : (P->res_cluster_big > 0 && cluster >= P->res_cluster_big) ? 0
+                     : (P->res_cluster_mid > 0 && cluster >= P->res_cluster_mid) ? 1
+                                                                                 : 2;
+    const int prio = cta_only ? 0 : std::min(prio_least, prio_greatest + rank);
+    return P->res_smem ? launch_resident_smem(P->res_threads, cluster, grid, a, s2, cta_only, prio)
                        : launch_resident(P->fp64, P->res_threads, cluster, grid, a, s2, cta_only);
   };
   // the launches in order: big clusters, clusters, single CTAs (the first
@@ -931,6 +944,10 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   for (size_t i = 0; i < ls.size(); ++i) {
     cudaStream_t s2 = i == 0 ? st : side[i - 1];
     if (i > 0) CUDA_TRY(cudaStreamWaitEvent(s2, P->fj.fork, 0));
+    // the launches after the first start a little later: a cluster needs that
+    // many free SMs of one GPC, and the largest clusters (the first launch)
+    // are placed before smaller groups can take SMs in their GPCs
+    if (i > 0) CUDA_TRY(launch_hold(20000ull * i, s2));
     CUDA_TRY(launch(ls[i].cluster, ls[i].grid, ls[i].a, s2, ls[i].cta_only));
     if (i > 0) CUDA_TRY(cudaEventRecord(joins[i - 1], s2));
   }
