@@ -327,7 +327,7 @@ typedef struct {
                              /* method's minimal traffic over them: 10 words per  */
                              /* cell and CG iteration, 5 FP64 words per cell and  */
                              /* refinement pass (most of it stays on chip)        */
-  int res_launches;          /* resident-solver launches                          */
+  int res_launches;          /* resident-solver launches (with their hold kernels) */
   int res_solves;            /* solves taken by the resident solver               */
   double res_span_ms;        /* first resident solve's start to the last one's end */
   double res_longest_ms;     /* the longest resident solve                         */

@@ -965,7 +965,8 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
     CUDA_TRY(launch_resident_grid(P->res_threads, P->res_grid_all, a, st));
   }
   if (prof) CUDA_TRY(cudaEventRecord(P->res_ev[1], st));
-  P->res_launches += (int)ls.size() + (P->n_gq > 0 ? 1 : 0);
+  // the resident kernels, the hold kernels before the later ones, the whole-GPU launch
+  P->res_launches += (int)ls.size() + std::max(0, (int)ls.size() - 1) + (P->n_gq > 0 ? 1 : 0);
   return ATS_OK;
 }
 
