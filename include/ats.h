@@ -138,7 +138,7 @@ typedef struct {
   int precision;     /* ATS_PREC_*                                            */
   int max_iter;      /* cap on CG iterations per solve (0 = 20000)            */
   int max_refine;    /* cap on FP64 residual passes (0 = 40)                 */
-  double inner_rtol; /* mixed: residual reduction per inner FP32 solve (0 = 1e-5) */
+  double inner_rtol; /* mixed: residual reduction per inner FP32 solve (0 = 1e-6) */
   int tile_octs;     /* octs per work item, multiple of 32 (0 = the size rule: */
                      /* about one item per CTA of the stencil kernel's grid, */
                      /* 256..1024; ats_batch_autotune tunes it per batch)    */

@@ -312,7 +312,7 @@ void fill_defaults(ats_solve_opts *o) {
   o->precision = ATS_PREC_FP64;
   o->max_iter = 20000;
   o->max_refine = 40;
-  o->inner_rtol = 1e-5;
+  o->inner_rtol = 1e-6;
   o->tile_octs = 0;
   o->check_every = 16;
   o->use_graph = 0;
@@ -334,7 +334,7 @@ ats_solve_opts normalize(const ats_solve_opts *in) {
   if (!(o.tol > 0.0)) o.tol = 1e-10;
   if (o.max_iter <= 0) o.max_iter = 20000;
   if (o.max_refine <= 0) o.max_refine = 40;
-  if (!(o.inner_rtol > 0.0)) o.inner_rtol = 1e-5;
+  if (!(o.inner_rtol > 0.0)) o.inner_rtol = 1e-6;
   if (o.check_every <= 0) o.check_every = 16;
   // 3 (a hierarchy step as one graph) is 2 for a solve on its own
   if (o.use_graph > 2) o.use_graph = 2;
