@@ -182,8 +182,8 @@ __device__ __forceinline__ void warp_reduce_acc(Acc<double> &a) {
 // 256-bit global accesses (sm_100 and later): the 32 bytes of an FP32 oct are
 // one request (one L1 sector access instead of two 16-byte halves), an FP64
 // oct is two.  Every oct base is 32-byte aligned: vectors are whole octs in
-// device allocations aligned to 256 bytes (user pointers are checked on the
-// host).  Read-only loads use the non-coherent path and may be scheduled
+// device allocations aligned to 256 bytes (a caller's array is read or
+// written with them only after its alignment was checked).  Read-only loads use the non-coherent path and may be scheduled
 // freely; loads of data this kernel also writes are volatile so that they
 // stay ordered with the stores.
 __device__ __forceinline__ void ld8_ro(const float *__restrict__ p, float (&v)[8]) {
@@ -1529,6 +1529,13 @@ cudaError_t launch_admit(const TickArgs &a, const int32_t *slots, int n_new, cud
 // solve start / end over the work list
 // ---------------------------------------------------------------------------
 
+// Whether a caller's array can take the 32-byte oct vectors.
+__device__ __forceinline__ bool oct_aligned(const void *p) { return ((uintptr_t)p & 31u) == 0; }
+
+// Start of a solve on its work items, one oct per thread: e = 0, and x64 =
+// src[solve] (Crank-Nicolson: the guess of E^{n+1} is turned into the guess
+// of the half-step root (x + E^n) / 2) where src is given.  The caller's
+// arrays take 32-byte vectors when aligned, else one cell per access.
 template <typename T>
 __global__ void k_init(const SolveDev *__restrict__ solves, const WorkItem *__restrict__ items,
                        int n_items, const double *const *__restrict__ src) {
@@ -1536,16 +1543,38 @@ __global__ void k_init(const SolveDev *__restrict__ solves, const WorkItem *__re
     const WorkItem item = items[it];
     const SolveDev &sd = solves[item.solve];
     const double *xs = src ? src[item.solve] : nullptr;
-    T *e = (T *)sd.e;
-    const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item_octs(item, sd) * 8;
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-      e[b + k] = T(0);
-      // Crank-Nicolson: x is a guess of E^{n+1}, the half-step root is (x + E^n) / 2
-      if (xs) sd.x64[b + k] = sd.cn_base ? 0.5 * (xs[b + k] + sd.cn_base[b + k]) : xs[b + k];
+    const bool vec = oct_aligned(xs) && oct_aligned(sd.cn_base);
+    const int o_end = item.oct_begin + item_octs(item, sd);
+    for (int o = item.oct_begin + (int)threadIdx.x; o < o_end; o += blockDim.x) {
+      T z0[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) z0[c] = T(0);
+      st8((T *)sd.e + 8 * (int64_t)o, z0);
+      if (!xs) continue;
+      double v[8];
+      if (vec) {
+        ld8_ro(xs + 8 * (int64_t)o, v);
+        if (sd.cn_base) {
+          double cb[8];
+          ld8_ro(sd.cn_base + 8 * (int64_t)o, cb);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) v[c] = 0.5 * (v[c] + cb[c]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int64_t k = 8 * (int64_t)o + c;
+          v[c] = sd.cn_base ? 0.5 * (xs[k] + sd.cn_base[k]) : xs[k];
+        }
+      }
+      st8(sd.x64 + 8 * (int64_t)o, v);
     }
   }
 }
 
+// End of a solve on its work items, one oct per thread: dst[solve] = x64
+// (Crank-Nicolson: 2 x64 - E^n), and neg[solve] = 1 when a value is below
+// zero (the warning of the solve).
 __global__ void k_final(const SolveDev *__restrict__ solves, const WorkItem *__restrict__ items,
                         int n_items, double *const *__restrict__ dst, int *__restrict__ neg) {
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -1553,12 +1582,31 @@ __global__ void k_final(const SolveDev *__restrict__ solves, const WorkItem *__r
     double *xd = dst[item.solve];
     if (!xd) continue;
     const SolveDev &sd = solves[item.solve];
-    const int64_t b = (int64_t)item.oct_begin * 8, n = (int64_t)item_octs(item, sd) * 8;
-    bool below = false;  // a negative energy in the result (the warning of the solve)
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-      const double v = sd.cn_base ? 2.0 * sd.x64[b + k] - sd.cn_base[b + k] : sd.x64[b + k];
-      xd[b + k] = v;
-      below = below || v < 0.0;
+    const bool vec = oct_aligned(xd) && oct_aligned(sd.cn_base);
+    const int o_end = item.oct_begin + item_octs(item, sd);
+    bool below = false;
+    for (int o = item.oct_begin + (int)threadIdx.x; o < o_end; o += blockDim.x) {
+      double v[8];
+      ld8_rw(sd.x64 + 8 * (int64_t)o, v);
+      if (sd.cn_base) {
+        double cb[8];
+        if (vec) {
+          ld8_ro(sd.cn_base + 8 * (int64_t)o, cb);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) cb[c] = sd.cn_base[8 * (int64_t)o + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = 2.0 * v[c] - cb[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) below = below || v[c] < 0.0;
+      if (vec) {
+        st8(xd + 8 * (int64_t)o, v);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) xd[8 * (int64_t)o + c] = v[c];
+      }
     }
     if (__syncthreads_or(below) && neg && threadIdx.x == 0) atomicOr(neg + item.solve, 1);
   }
