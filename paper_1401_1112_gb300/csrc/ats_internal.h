@@ -125,13 +125,11 @@ struct CoefArgs {
   int64_t n_xd;         // diagonal-extra records (bounds of xrec)
   int64_t n_face;       // interface descriptors (bounds of rec_face entries)
 };
-// K, diagonal extras, b and the FP64 face coefficients C64, one thread per oct
-// (32-byte vectors when the caller's arrays are aligned, else cell by cell).
+// K, diagonal extras, b and the FP64 face coefficients C64, one thread per cell.
 cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st);
 // One launch for many levels after zeroing the levels' error flags (flags:
 // device array of device pointers): block b of kCoefThreads threads builds
-// octs of level blk_level[b], starting at (b - blk_first[level]) * kCoefThreads,
-// one oct per thread.
+// cells of level blk_level[b], starting at (b - blk_first[level]) * kCoefThreads.
 constexpr int kCoefThreads = 256;
 cudaError_t launch_coef_build_batch(const CoefArgs *args, const int32_t *blk_level, const int32_t *blk_first,
                                     int n_blocks, int n, int *const *flags, cudaStream_t st);

@@ -1136,136 +1136,20 @@ __device__ __forceinline__ void coef_cell(const CoefArgs &a, int64_t i) {
   if (!ok) atomicOr(a.err_flag, 1);
 }
 
-// The eight cells of own oct o at once, the same arithmetic per cell as
-// coef_cell (so the same bits): K, E (and s, src) read as 32-byte vectors,
-// K64, K32, b64, the face coefficients and the diagonal extras written so;
-// only the facing cells of the +x, +y, +z neighbours and the interface
-// records are read one by one.  The caller's K, E_old, s and src must be
-// 32-byte aligned.
-__device__ __forceinline__ void coef_oct_vec(const CoefArgs &a, int64_t o) {
-  const unsigned lb = a.leaf ? (unsigned)a.leaf[o] : 0xFFu;
-  int xr = a.xrec[o];
-  if (xr >= 0 && !idx_ok(xr, a.n_xd)) xr = -1;
-  int fr = a.frec[o];
-  if (fr >= 0 && !idx_ok(fr, a.n_rec)) fr = -1;
-  double K[8], E[8], S[8], R[8];
-  ld8_ro(a.K + 8 * o, K);
-  ld8_ro(a.E_old + 8 * o, E);
-  if (a.s) ld8_ro(a.s + 8 * o, S);
-  if (a.src) ld8_ro(a.src + 8 * o, R);
-  // the +a neighbour's facing cells and their leaf bits
-  double Kn[3][8];
-  unsigned ln[3];
-  bool has[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const int bit = 1 << ax;
-    const int n = a.nbr[6 * o + 2 * ax + 1];
-    has[ax] = n >= 0 && idx_ok(n, a.n_oct);
-    ln[ax] = has[ax] ? (a.leaf ? (unsigned)a.leaf[n] : 0xFFu) : 0u;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      Kn[ax][c] = 0.0;
-      if ((c & bit) && has[ax]) Kn[ax][c] = a.K[8 * (int64_t)n + (c ^ bit)];
-    }
-  }
-  double K64[8], b64[8], xd64[8], C[3][8];
-  float K32[8], xd32[8];
-  bool ok_all = true;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const bool leaf = (lb >> c) & 1;
-    const double Kc = leaf ? K[c] : 0.0;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      const int bit = 1 << ax;
-      const int cj = c ^ bit;
-      double Cf = 0.0;
-      if (!(c & bit)) {
-        if (leaf && ((lb >> cj) & 1)) Cf = a.h * (Kc + K[cj]);
-      } else if (leaf && has[ax] && ((ln[ax] >> cj) & 1)) {
-        Cf = a.h * (Kc + Kn[ax][c]);
-      }
-      C[ax][c] = Cf;
-    }
-    if (!leaf) {
-      K64[c] = -1.0;
-      K32[c] = -1.0f;
-      b64[c] = 0.0;
-      xd64[c] = 0.0;
-      xd32[c] = 0.0f;
-      continue;
-    }
-    bool ok = (Kc > 0.0) && isfinite(Kc) && isfinite(E[c]);
-    double xd = a.s ? S[c] : 0.0;
-    ok = ok && isfinite(xd) && xd >= 0.0;
-    double rhs = E[c] + (a.src ? a.src_scale * R[c] : 0.0);
-    if (fr >= 0) {
-      for (int dir = 0; dir < 6; ++dir) {
-        const int f = a.rec_face[(int64_t)fr * 48 + c * 6 + dir];
-        if (f < 0 || !idx_ok(f, a.n_face)) continue;
-        const double Kf = a.face_K ? a.face_K[f] : Kc;
-        const double Enb = a.face_E ? a.face_E[f] : 0.0;
-        const double F = a.face_F ? a.src_scale * a.face_F[f] : 0.0;
-        const double alpha = a.face_alpha ? a.face_alpha[f] : 1.0;
-        ok = ok && (Kf > 0.0) && isfinite(Kf) && isfinite(Enb) && isfinite(F);
-        const double factor = (a.face_rel[f] == ATS_REL_COARSER) ? (2.0 / 3.0) : 1.0;
-        const double Cf = factor * a.h * (Kc + Kf);
-        const int kind = a.face_kind[f];
-        if (kind == ATS_FACE_DIRICHLET) {
-          xd += Cf;
-          rhs += Cf * Enb;
-        } else if (kind == ATS_FACE_NEUMANN) {
-          rhs += F;
-        } else {
-          xd += alpha * Cf;
-          rhs += alpha * Cf * Enb + (1.0 - alpha) * F;
-        }
-      }
-    }
-    K64[c] = Kc;
-    K32[c] = (float)Kc;
-    b64[c] = rhs;
-    xd64[c] = xd;
-    xd32[c] = (float)xd;
-    ok_all = ok_all && ok;
-  }
-  st8(a.K64 + 8 * o, K64);
-  st8(a.K32 + 8 * o, K32);
-  st8(a.b64 + 8 * o, b64);
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) st8(a.C64 + (3 * o + ax) * 8, C[ax]);
-  if (xr >= 0) {
-    st8(a.xd64 + (int64_t)xr * 8, xd64);
-    st8(a.xd32 + (int64_t)xr * 8, xd32);
-  }
-  if (!ok_all) atomicOr(a.err_flag, 1);
-}
-
-// One oct: the vector form when the caller's arrays allow it, else cell by cell.
-__device__ __forceinline__ void coef_oct(const CoefArgs &a, int64_t o) {
-  const bool vec = ((((uintptr_t)a.K) | ((uintptr_t)a.E_old) | ((uintptr_t)a.s) | ((uintptr_t)a.src)) & 31u) == 0;
-  if (vec) {
-    coef_oct_vec(a, o);
-  } else {
-    for (int c = 0; c < 8; ++c) coef_cell(a, 8 * o + c);
-  }
-}
-
 __global__ void k_coef_build(CoefArgs a) {
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= a.n_oct) return;
-  coef_oct(a, o);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 8 * a.n_oct) return;
+  coef_cell(a, i);
 }
 
 // All levels of a batch in one launch: block b belongs to level
-// blk_level[b] and covers its octs from (b - blk_first[level]) * blockDim.
+// blk_level[b] and covers its cells from (b - blk_first[level]) * blockDim.
 __global__ void k_coef_build_batch(const CoefArgs *__restrict__ args, const int32_t *__restrict__ blk_level,
                                    const int32_t *__restrict__ blk_first) {
   const int k = blk_level[blockIdx.x];
   const CoefArgs &a = args[k];
-  const int64_t o = (int64_t)(blockIdx.x - blk_first[k]) * blockDim.x + threadIdx.x;
-  if (o < a.n_oct) coef_oct(a, o);
+  const int64_t i = (int64_t)(blockIdx.x - blk_first[k]) * blockDim.x + threadIdx.x;
+  if (i < 8 * a.n_oct) coef_cell(a, i);
 }
 
 // The FP64 face coefficients of cell i = 8 o + c: for each axis a, the face
@@ -1334,8 +1218,9 @@ cudaError_t launch_gather_flags(const int *const *flags, int n, int *out, cudaSt
 }
 
 cudaError_t launch_coef_build(const CoefArgs &a, cudaStream_t st) {
+  const int64_t N = 8 * a.n_oct;
   const int threads = 256;
-  const int64_t blocks = (a.n_oct + threads - 1) / threads;
+  const int64_t blocks = (N + threads - 1) / threads;
   k_coef_build<<<(unsigned)blocks, threads, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -2283,7 +2283,7 @@ ats_status ats_batch_build_operators(ats_batch *B, const ats_coef_desc *coefs) {
       if ((s = dev_alloc_t(ctx, n, &B->d_args)) != ATS_OK) return s;
       std::vector<int32_t> first(n + 1, 0), level;
       for (int k = 0; k < n; ++k) {
-        const int64_t nb = (P->levels[k]->n_oct + kCoefThreads - 1) / kCoefThreads;
+        const int64_t nb = (P->levels[k]->N + kCoefThreads - 1) / kCoefThreads;
         first[k + 1] = first[k] + (int32_t)nb;
         for (int64_t b = 0; b < nb; ++b) level.push_back(k);
       }
