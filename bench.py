@@ -274,7 +274,7 @@ def run_ours(args, rank, world, local):
     # --res-max-octs octs; the batch's largest has 32 768)
     batch = ats.Batch(ctx, levels, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
                       use_graph=1, check_every=args.check_every, mem=ats.ATS_MEM_DEVICE, tile_octs=args.tile,
-                      inner_rtol=args.inner_rtol, res_max_octs=args.res_max_octs)
+                      inner_rtol=args.inner_rtol, res_max_octs=args.res_max_octs, cg_form=args.cg_form)
     coefs = batch.prepare_coefs([coef_kwargs(k) for k in range(n)])
 
     def build_ops():
@@ -292,7 +292,7 @@ def run_ours(args, rank, world, local):
     tile_octs = tune["tile_octs"] if tune else args.tile
     check_every = tune["check_every"] if tune else args.check_every
     # the resident shape of the tuned plan, for the other batches of this run
-    res_shape = dict(res_max_octs=args.res_max_octs)
+    res_shape = dict(res_max_octs=args.res_max_octs, cg_form=args.cg_form)
     if tune:
         res_shape.update(res_threads=tune["chosen"]["res_threads"], res_cluster=tune["chosen"]["res_cluster"],
                          res_cta_octs=tune["chosen"]["res_cta_octs"])
@@ -1123,6 +1123,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--res-max-octs", type=int, default=32768,
                     help="levels up to this many octs take the resident solver (0 = the library default)")
+    ap.add_argument("--cg-form", type=int, default=0,
+                    help="resident CG step: 1 = q from p after a group barrier, 2 = q by recurrence (0 = default)")
     ap.add_argument("--serve-requests", type=int, default=240,
                     help="requests of the served stream's 2 000 (the first N, same arrival process)")
     ap.add_argument("--serve-max-cells", type=int, default=256 ** 3)

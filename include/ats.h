@@ -154,7 +154,8 @@ typedef struct {
   int res_cta_octs;  /* resident solver: a level of at most this many octs is */
                      /* solved by one CTA alone (0 = 2048, < 0 = never)      */
   int res_max_octs;  /* ATS_SCHED_AUTO: levels above this many octs take the  */
-                     /* tick path (0 = 16384 for ATS_PREC_MIXED, 2048 for    */
+                     /* whole-GPU form or the tick path (see ATS_SCHED_AUTO) */
+                     /* (0 = 16384 for ATS_PREC_MIXED, 2048 for              */
                      /* ATS_PREC_FP64)                                       */
   int cg_scalars;    /* resident solver, mixed precision: the CG step's alpha,  */
                      /* beta and inner convergence test from the error-free   */
@@ -178,6 +179,15 @@ typedef struct {
                      /* shared memory but whose runs on this many would     */
                      /* (0 = 8; < 0 = none: they take res_cluster_big);     */
                      /* used only between res_cluster and res_cluster_big   */
+  int cg_form;       /* resident solver, mixed precision: how each CG step    */
+                     /* forms q = (I + dt A) p (Sect. 3.3.4).  1 = from the   */
+                     /* new p, after a group barrier that makes every CTA's   */
+                     /* p visible; 2 = by the recurrence                      */
+                     /* q = (I + dt A) z + beta q_prev (equal in exact         */
+                     /* arithmetic, since p = z + beta p_prev): z is final at */
+                     /* the previous step's group sum, so the step needs no   */
+                     /* barrier -- two group synchronisations per step        */
+                     /* instead of three.  0 = the default (2)                */
 } ats_solve_opts;
 
 /* scheduling of a solve (ats_solve_opts.sched).  Which path a level takes
@@ -200,18 +210,19 @@ typedef struct {
  *   concurrent launches sharing the SMs in proportion to their queues'
  *   estimated work (after a completed run, their measured SM-time).  Not for the paper stopping rule (ATS_STOP_PAPER
  *   takes the tick path). */
-#define ATS_SCHED_AUTO 0     /* resident solver for levels up to res_max_octs octs */
+#define ATS_SCHED_AUTO 0     /* resident solver for levels up to res_max_octs octs; */
+        /* above it, FP32 bulk: the whole-GPU form (see ATS_SCHED_GRID) for a level */
+        /* of at most 1 100 octs per CTA of that form (167 200 octs on 152 SMs),    */
+        /* the tick path for larger levels and for FP64                             */
 #define ATS_SCHED_TICK 1     /* the tick path for every level                    */
 #define ATS_SCHED_RESIDENT 2 /* the resident solver for every level              */
-#define ATS_SCHED_GRID 3     /* as AUTO, and levels above res_max_octs (FP32 bulk) */
-        /* on the whole-GPU form of the resident solver: one cooperative launch, one */
-        /* CTA per SM, each CTA's run of octs with its K, z, p in shared memory, the */
-        /* faces across runs and the per-step sums through global memory, steps   */
-        /* ordered by a grid barrier whose waits give up after a bounded number of */
-        /* polls (the solve then ends with ATS_ERR_TIMEOUT); such levels run one   */
-        /* after another, after the other resident solves.  Measured slower than   */
-        /* the tick path on the GB300 at 32 768 - 262 144 octs (the grid barrier   */
-        /* and sums cost ~4 us each), so it is not the default.                   */
+#define ATS_SCHED_GRID 3     /* as AUTO, and every level above res_max_octs (FP32  */
+        /* bulk) on the whole-GPU form of the resident solver: one cooperative     */
+        /* launch, one CTA per SM, each CTA's run of octs with its CG arrays in     */
+        /* shared memory, the faces across runs and the per-step sums through       */
+        /* global memory, steps ordered by a grid barrier whose waits give up after */
+        /* a bounded number of polls (the solve then ends with ATS_ERR_TIMEOUT);    */
+        /* such levels run one after another, after the other resident solves.     */
 
 /* initial guess of a solve (ats_solve_opts.x0) */
 #define ATS_X0_GIVEN 0 /* x_inout holds the initial guess on entry (default) */

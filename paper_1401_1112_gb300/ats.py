@@ -71,7 +71,7 @@ class ats_solve_opts(ctypes.Structure):
         ("res_cluster", ctypes.c_int), ("res_cta_octs", ctypes.c_int), ("res_max_octs", ctypes.c_int),
         ("cg_scalars", ctypes.c_int), ("res_state", ctypes.c_int), ("res_cluster_big", ctypes.c_int),
         ("res_big_work", ctypes.c_int),
-        ("res_cluster_mid", ctypes.c_int),
+        ("res_cluster_mid", ctypes.c_int), ("cg_form", ctypes.c_int),
     ]
 
 
@@ -277,7 +277,7 @@ def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, m
               inner_rtol=0.0, tile_octs=0, check_every=0, use_graph=0, mem=ATS_MEM_HOST,
               x0=ATS_X0_GIVEN, sched=ATS_SCHED_AUTO, res_threads=0, res_cluster=0, res_cta_octs=0,
               res_max_octs=0, cg_scalars=0, res_state=0, res_cluster_big=0, res_big_work=0,
-              res_cluster_mid=0) -> ats_solve_opts:
+              res_cluster_mid=0, cg_form=0) -> ats_solve_opts:
     o = ats_solve_opts()
     lib().ats_default_opts(ctypes.byref(o))
     o.tol = tol
@@ -305,6 +305,7 @@ def make_opts(tol=1e-10, stop_rule=ATS_STOP_RESIDUAL, precision=ATS_PREC_FP64, m
     o.res_cluster_big = res_cluster_big
     o.res_big_work = res_big_work
     o.res_cluster_mid = res_cluster_mid
+    o.cg_form = cg_form
     return o
 
 

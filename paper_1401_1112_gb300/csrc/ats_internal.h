@@ -203,16 +203,17 @@ struct ResArgs {
   const int32_t *tq;
   int n_cq, n_tq, n_solves;
   int cg_scalars;  // FP32 bulk: 0 = step decisions in FP32 from the rounded totals, 1 = in FP64
+  int q_recur;     // FP32 bulk: 1 = q = (I + dt A) z + beta q_prev (no barrier), 0 = q = (I + dt A) p
   int *cq_head;
   int *tq_head;
   unsigned long long *cells;
   unsigned long long *t_solve;  // [n_solves][2] %globaltimer at a solve's start and end (profiling), or null
   int cap;                      // shared-memory form: octs per CTA kept in shared memory (0: none)
   // whole-GPU form (launch_resident_grid): every CTA of one cooperative
-  // launch works on gq[0], gq[1], ... in turn; gbar = {arrivals, generation}
-  // of its grid barrier (zeroed before the launch), gpart = [2][grid + 1][3]
-  // (hi, lo) pairs: per buffer, each CTA's partial sums, then the totals;
-  // *gerr set when a barrier wait gave up
+  // launch works on gq[0], gq[1], ... in turn; gbar[0] = the arrivals at
+  // its grid barriers so far (zeroed before the launch; gbar[1] unused),
+  // gpart = [2][grid + 1][3] (hi, lo) pairs: per buffer, each CTA's partial
+  // sums (the last row unused); *gerr set when a barrier wait gave up
   const int32_t *gq;
   int n_gq;
   unsigned *gbar;
@@ -255,6 +256,9 @@ cudaError_t launch_resident_grid(int threads, int grid, const ResArgs &a, cudaSt
 // that much later.
 cudaError_t launch_hold(unsigned long long ns, cudaStream_t st);
 int resident_grid_ctas(int threads, int device);
+// Octs per CTA up to which the shared-memory solver keeps all six CG arrays
+// (K, z, p, D, q, e) of a CTA's run in shared memory.
+int resident_six_cap();
 // One grid barrier of that form alone (cooperative launch of `grid` CTAs of 32
 // threads) waiting for a.g_expect arrivals: out[cta] = 1 when its wait ended
 // normally, 0 when it gave up (and *a.gerr = 1).  a.gbar, a.gerr zeroed first.

@@ -2111,11 +2111,18 @@ __global__ void __launch_bounds__(NT, ResMinBlocks<T, NT>::value) k_res_cta(ResA
 // global memory.  Octs beyond a CTA's capacity use the level's global arrays.  Where an oct's values live does not change what is computed, so
 // the capacity does not enter the arithmetic.
 //
-// A CG iteration reads its neighbours' p instead of recomputing it:
+// A CG iteration takes one of two forms (cg_form), equal in exact
+// arithmetic.  From p, three group synchronisations:
 //   1. p = z + beta p on the own octs (an inner solve's first: p = z), then
 //      a group barrier;
-//   2. q = (I + dt A) p, the sum p.q;
+//   2. q = (I + dt A) p from the own and the neighbours' p, the sum p.q;
 //   3. r = D z - alpha q, z = D^-1 r, e += alpha p, the sums r.z and r.r.
+// By the q recurrence, two: since p = z + beta p_prev,
+// (I + dt A) p = (I + dt A) z + beta q_prev, and z -- the only array a step
+// reads from the neighbours -- is final once step 3's sum has passed:
+//   1+2. w = (I + dt A) z, p = z + beta p, q = w + beta q (first: p = z,
+//        q = w) in one pass, the sum p.q;
+//   3.   as above.
 
 extern __shared__ __align__(128) unsigned char res2_smem[];
 // Two layouts of a CTA's shared memory, chosen per solve from the size of the
@@ -2148,6 +2155,7 @@ struct Res2Ctx {
   unsigned cr;              // this CTA's rank in the group (0 for one CTA)
   unsigned crc;             // the rank neighbour codes give this CTA's octs (cr in a cluster, else 0)
   bool grid;                // a whole-GPU group: octs of other CTAs are read from global memory
+  bool qrec;                // q by the recurrence: neighbours read z (published globally in a whole-GPU group)
 };
 using Res2Six = Res2Ctx<kRes2Cap6, kRes2Cap6>;
 using Res2Three = Res2Ctx<kRes2Cap3, 0>;
@@ -2308,14 +2316,14 @@ __device__ __forceinline__ void res2_own_store(const Cx &cx, uint32_t arr, int c
   else st8(garr + 8 * o, v);
 }
 
-template <int DIR, class Cx>
+template <int DIR, bool kRec, class Cx>
 __device__ __forceinline__ void res2_op_face(const Cx &cx, const SolveDev &sd, const Nb &n, float h,
                                              const float (&K)[8], float (&off)[8]) {
   constexpr int A = DIR >> 1, S = DIR & 1, NB = 1 - S;
   if (n.kind == 0) return;
   float Kn[8], Pn[8];
   res2_face<A, NB>(n, cx.sK, cx.S, (const float *)sd.KT, false, Kn);
-  res2_face<A, NB>(n, cx.sP, cx.S, (const float *)sd.p0, true, Pn);
+  res2_face<A, NB>(n, kRec ? cx.sZ : cx.sP, cx.S, (const float *)(kRec ? sd.z : sd.p0), true, Pn);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (((c >> A) & 1) != S) continue;
@@ -2325,36 +2333,74 @@ __device__ __forceinline__ void res2_op_face(const Cx &cx, const SolveDev &sd, c
   }
 }
 
-// Step 2 on own oct o: q = D p - sum C p_nb; returns the oct's p.q.
-template <class Cx>
-__device__ __forceinline__ float res2_op_oct(const Cx &cx, const SolveDev &sd, int o, float h) {
+// The end of step 2 on own oct o, from the stencil's off-diagonal part off
+// of v (the value array the stencil read) and the diagonal d.  q = D p - off
+// when v = p.  With the q recurrence v = z: w = D z - off, then
+// p = z + beta p_prev and q = w + beta q_prev (an inner solve's first step:
+// p = z, q = w).  q is zero on non-leaf cells; stores q (and p), returns p.q
+// over the leaf cells.
+template <bool kRec, class Cx>
+__device__ __forceinline__ float res2_op_end(const Cx &cx, const SolveDev &sd, int o, int l, const float (&K)[8],
+                                             const float (&v)[8], const float (&d)[8], const float (&off)[8],
+                                             bool first, float beta) {
+  float local = 0.f, qv[8];
+  if (!kRec) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float q = d[c] * v[c] - off[c];
+      const bool leaf = K[c] >= 0.f;
+      if (leaf) local = fmaf(v[c], q, local);
+      qv[c] = leaf ? q : 0.f;
+    }
+    res2_own_store(cx, cx.sQ, cx.capD, l, (float *)sd.q, o, qv);
+    return local;
+  }
+  float pp[8], pv[8];
+  if (first) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) pp[c] = qv[c] = 0.f;
+  } else {
+    res2_own(cx, cx.sP, cx.cap, l, (const float *)sd.p0, o, true, pp);
+    res2_own(cx, cx.sQ, cx.capD, l, (const float *)sd.q, o, true, qv);
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float w = d[c] * v[c] - off[c];
+    const float pn = first ? v[c] : fmaf(beta, pp[c], v[c]);
+    const float qn = first ? w : fmaf(beta, qv[c], w);
+    const bool leaf = K[c] >= 0.f;
+    if (leaf) local = fmaf(pn, qn, local);
+    qv[c] = leaf ? qn : 0.f;
+    pv[c] = pn;
+  }
+  res2_own_store(cx, cx.sP, cx.cap, l, (float *)sd.p0, o, pv);
+  res2_own_store(cx, cx.sQ, cx.capD, l, (float *)sd.q, o, qv);
+  return local;
+}
+
+// Step 2 on own oct o: the stencil of v (p, or z with the q recurrence) from
+// the own and the neighbours' rows, then res2_op_end; returns the oct's p.q.
+template <bool kRec, class Cx>
+__device__ __forceinline__ float res2_op_oct(const Cx &cx, const SolveDev &sd, int o, float h, bool first,
+                                             float beta) {
   const int l = o - cx.lo;
-  float K[8], p[8], d[8];
+  float K[8], v[8], d[8];
   res2_own(cx, cx.sK, cx.cap, l, (const float *)sd.KT, o, false, K);
-  res2_own(cx, cx.sP, cx.cap, l, (const float *)sd.p0, o, true, p);
+  res2_own(cx, kRec ? cx.sZ : cx.sP, cx.cap, l, (const float *)(kRec ? sd.z : sd.p0), o, true, v);
   res2_own(cx, cx.sD, cx.capD, l, (const float *)sd.dg, o, true, d);
   Nb nb[6];
   res2_nbs(cx, sd, o, l, nb);
   float off[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) off[c] = 0.f;
-  in_oct_faces(K, p, h, off);
-  res2_op_face<0>(cx, sd, nb[0], h, K, off);
-  res2_op_face<1>(cx, sd, nb[1], h, K, off);
-  res2_op_face<2>(cx, sd, nb[2], h, K, off);
-  res2_op_face<3>(cx, sd, nb[3], h, K, off);
-  res2_op_face<4>(cx, sd, nb[4], h, K, off);
-  res2_op_face<5>(cx, sd, nb[5], h, K, off);
-  float local = 0.f, qv[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float q = d[c] * p[c] - off[c];
-    const bool leaf = K[c] >= 0.f;
-    if (leaf) local = fmaf(p[c], q, local);
-    qv[c] = leaf ? q : 0.f;
-  }
-  res2_own_store(cx, cx.sQ, cx.capD, l, (float *)sd.q, o, qv);
-  return local;
+  in_oct_faces(K, v, h, off);
+  res2_op_face<0, kRec>(cx, sd, nb[0], h, K, off);
+  res2_op_face<1, kRec>(cx, sd, nb[1], h, K, off);
+  res2_op_face<2, kRec>(cx, sd, nb[2], h, K, off);
+  res2_op_face<3, kRec>(cx, sd, nb[3], h, K, off);
+  res2_op_face<4, kRec>(cx, sd, nb[4], h, K, off);
+  res2_op_face<5, kRec>(cx, sd, nb[5], h, K, off);
+  return res2_op_end<kRec>(cx, sd, o, l, K, v, d, off, first, beta);
 }
 
 // Step 2 on own oct o of the shared rows whose six neighbours are all in
@@ -2376,52 +2422,45 @@ __device__ __forceinline__ void res2_fast_face(uint32_t aK, uint32_t aP, uint32_
   }
 }
 
-template <bool kCluster, class Cx>
+template <bool kCluster, bool kRec, class Cx>
 __device__ __forceinline__ float res2_op_oct_fast(const Cx &cx, const SolveDev &sd, int o, int l,
-                                                  const uint32_t (&w)[3], float h) {
-  float K[8], p[8], d[8];
+                                                  const uint32_t (&w)[3], float h, bool first, float beta) {
+  const uint32_t sV = kRec ? cx.sZ : cx.sP;
+  float K[8], v[8], d[8];
   lds_cells(cx.sK + (uint32_t)l * 8u, cx.S, K);
-  lds_cells(cx.sP + (uint32_t)l * 8u, cx.S, p);
+  lds_cells(sV + (uint32_t)l * 8u, cx.S, v);
   res2_own(cx, cx.sD, cx.capD, l, (const float *)sd.dg, o, true, d);
-  uint32_t aK[6], aP[6];
+  uint32_t aK[6], aV[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const uint32_t c = (w[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
     const uint32_t off = (c & 0xFFFu) * 8u;
     if (kCluster) {
       aK[k] = cl_map_s(cx.sK + off, c >> 12);
-      aP[k] = cl_map_s(cx.sP + off, c >> 12);
+      aV[k] = cl_map_s(sV + off, c >> 12);
     } else {
       aK[k] = cx.sK + off;
-      aP[k] = cx.sP + off;
+      aV[k] = sV + off;
     }
   }
   float off[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) off[c] = 0.f;
-  in_oct_faces(K, p, h, off);
-  res2_fast_face<0, kCluster>(aK[0], aP[0], cx.S, h, K, off);
-  res2_fast_face<1, kCluster>(aK[1], aP[1], cx.S, h, K, off);
-  res2_fast_face<2, kCluster>(aK[2], aP[2], cx.S, h, K, off);
-  res2_fast_face<3, kCluster>(aK[3], aP[3], cx.S, h, K, off);
-  res2_fast_face<4, kCluster>(aK[4], aP[4], cx.S, h, K, off);
-  res2_fast_face<5, kCluster>(aK[5], aP[5], cx.S, h, K, off);
-  float local = 0.f, qv[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float q = d[c] * p[c] - off[c];
-    const bool leaf = K[c] >= 0.f;
-    if (leaf) local = fmaf(p[c], q, local);
-    qv[c] = leaf ? q : 0.f;
-  }
-  res2_own_store(cx, cx.sQ, cx.capD, l, (float *)sd.q, o, qv);
-  return local;
+  in_oct_faces(K, v, h, off);
+  res2_fast_face<0, kCluster>(aK[0], aV[0], cx.S, h, K, off);
+  res2_fast_face<1, kCluster>(aK[1], aV[1], cx.S, h, K, off);
+  res2_fast_face<2, kCluster>(aK[2], aV[2], cx.S, h, K, off);
+  res2_fast_face<3, kCluster>(aK[3], aV[3], cx.S, h, K, off);
+  res2_fast_face<4, kCluster>(aK[4], aV[4], cx.S, h, K, off);
+  res2_fast_face<5, kCluster>(aK[5], aV[5], cx.S, h, K, off);
+  return res2_op_end<kRec>(cx, sd, o, l, K, v, d, off, first, beta);
 }
 
 // Step 2 on own oct o: the branch-free form when its row and every
 // neighbour's are in shared memory, else the general one.
-template <bool kCluster, class Cx>
-__device__ __forceinline__ float res2_op_any(const Cx &cx, const SolveDev &sd, int o, float h) {
+template <bool kCluster, bool kRec, class Cx>
+__device__ __forceinline__ float res2_op_any(const Cx &cx, const SolveDev &sd, int o, float h, bool first,
+                                             float beta) {
   const int l = o - cx.lo;
   if (l < cx.cap) {
     uint32_t w0, w1, w2, pad;
@@ -2433,10 +2472,10 @@ __device__ __forceinline__ float res2_op_any(const Cx &cx, const SolveDev &sd, i
                             ((w1 >> 16) == gl) | ((w2 & 0xFFFFu) == gl) | ((w2 >> 16) == gl);
     if (!any_global) {
       const uint32_t w[3] = {w0, w1, w2};
-      return res2_op_oct_fast<kCluster>(cx, sd, o, l, w, h);
+      return res2_op_oct_fast<kCluster, kRec>(cx, sd, o, l, w, h, first, beta);
     }
   }
-  return res2_op_oct(cx, sd, o, h);
+  return res2_op_oct<kRec>(cx, sd, o, h, first, beta);
 }
 
 // Step 1 on own oct o: p = z + beta p (first: p = z).
@@ -2475,6 +2514,7 @@ __device__ __forceinline__ void res2_upd_oct(const Cx &cx, const SolveDev &sd, i
     e[c] += alpha * p[c];
   }
   res2_own_store(cx, cx.sZ, cx.cap, l, (float *)sd.z, o, z);
+  if (cx.qrec && cx.grid && l < cx.cap) st8((float *)sd.z + 8 * o, z);
   res2_own_store(cx, cx.sE, cx.capD, l, (float *)sd.e, o, e);
 }
 
@@ -2486,6 +2526,7 @@ __device__ __forceinline__ void res2_ref_oct(const Cx &cx, const SolveDev &sd, i
   float zo[8], dv[8];
   ref_oct_values<float, true>(sd, o, want_x, rr, xx, rz, zo, dv);
   res2_own_store(cx, cx.sZ, cx.cap, o - cx.lo, (float *)sd.z, o, zo);
+  if (cx.qrec && cx.grid && o - cx.lo < cx.cap) st8((float *)sd.z + 8 * o, zo);
   res2_own_store(cx, cx.sD, cx.capD, o - cx.lo, (float *)sd.dg, o, dv);
 }
 
@@ -2512,7 +2553,7 @@ __device__ __forceinline__ void res2_xpe_oct(const Cx &cx, const SolveDev &sd, i
 }
 
 // ---- whole-GPU group: grid barrier and sums through global memory -------
-// Polls of the barrier's generation word before a wait gives up: with the
+// Polls of the barrier's arrival counter before a wait gives up: with the
 // back-off (at most 128 ns of sleep between polls) a wait ends within about
 // half a second whatever happens to the other CTAs; a barrier of a running
 // solve takes microseconds.
@@ -2523,52 +2564,52 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
   unsigned old;
   asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
   return old;
 }
 
-// The grid barrier's generation poll, run by one thread of a CTA that has
-// arrived and was not the last: wait with a short back-off until the
-// generation moves past g.  Returns false when it gave up (then *gerr = 1).
-__device__ __forceinline__ bool grid_wait(const ResArgs &a, unsigned g) {
-  const unsigned *gen = a.gbar + 1;
+// The grid barrier, run by warp 0 of each CTA after a CTA barrier (so that
+// lane 0's release covers the whole CTA's writes).  Arrivals go to one
+// counter (gbar[0], zero at the launch) that only grows: no CTA arrives at
+// barrier k + 1 before barrier k is complete, so the counter's value before
+// an arrival, `old`, lies in [k E, (k + 1) E) (E = arrivals per barrier) and
+// barrier k is complete once the counter reaches (k + 1) E.  Lane 0 arrives
+// with an acquire-release add; the last arrival knows it is complete (its
+// other lanes read after lane 0's acquire and a warp barrier), the others
+// poll the counter with every lane's acquire loads and a short back-off.
+// Returns false, in every lane, when the wait gave up (then *gerr = 1).
+__device__ bool grid_arrive_wait(const ResArgs &a) {
+  const unsigned expect = a.g_expect > 0 ? (unsigned)a.g_expect : gridDim.x;
+  const int lane = threadIdx.x & 31;
+  unsigned old = 0;
+  if (lane == 0) old = atom_add_acq_rel_u32(a.gbar, 1u);
+  old = __shfl_sync(kFull, old, 0);
+  __syncwarp();
+  const unsigned target = (old / expect + 1u) * expect;
+  if (old + 1u == target) return true;
   unsigned ns = 16;
-  for (long long it = 0; ld_acquire_u32(gen) == g; ++it) {
+  for (long long it = 0;; ++it) {
+    const unsigned v = ld_acquire_u32(a.gbar);
+    if (__all_sync(kFull, (int)(v - target) >= 0)) return true;
     if (it >= kGridSpinLimit) {
-      atomicOr(a.gerr, 1);
+      if (lane == 0) atomicOr(a.gerr, 1);
       return false;
     }
     __nanosleep(ns);
     if (ns < 128) ns <<= 1;
   }
-  return true;
 }
 
 // Every CTA of the cooperative launch waits here until all have arrived; the
-// CTA's global writes before it are visible to every CTA after it.  Thread 0
-// reads the generation and arrives with an acquire-release add (after the
-// CTA barrier, so it releases the CTA's writes); the last arrival resets the
-// counter and publishes generation + 1, the others poll for it.  Returns
+// CTA's global writes before it are visible to every CTA after it.  Returns
 // false in every thread of a CTA whose wait gave up.
 __device__ bool grid_sync(const ResArgs &a, int *flag) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned *cnt = a.gbar, *gen = a.gbar + 1;
-    const unsigned g = ld_acquire_u32(gen);
-    const unsigned expect = a.g_expect > 0 ? (unsigned)a.g_expect : gridDim.x;
-    int ok = 1;
-    if (atom_add_acq_rel_u32(cnt, 1u) == expect - 1) {
-      atomicExch(cnt, 0u);
-      st_release_u32(gen, g + 1);
-    } else {
-      ok = grid_wait(a, g) ? 1 : 0;
-    }
-    *flag = ok;
+  if (threadIdx.x < 32) {
+    const bool ok = grid_arrive_wait(a);
+    if (threadIdx.x == 0) *flag = ok ? 1 : 0;
   }
   __syncthreads();
   return *flag != 0;
@@ -2576,14 +2617,13 @@ __device__ bool grid_sync(const ResArgs &a, int *flag) {
 
 // Sums of NA accumulators over every CTA of the launch.  Each CTA's total
 // (the same shuffle trees as a cluster's) goes to its slot of gpart (buffer
-// `buf`) and the CTA arrives at the grid barrier; the last CTA to arrive
-// merges the slots in rank order -- lane j takes ranks j, j + 32, ..., every
-// load issued before the merges -- with a shuffle tree, writes the totals
-// to the buffer's total slot and then opens the barrier; the others read the
-// totals once it is open.  All CTAs hold bitwise the same totals.  Thread 0
-// ends with them in `out`; the return value (thread 0) is false when its
-// wait gave up.  Slots and totals alternate between two buffers, written
-// again only after a barrier every reader has passed.
+// `buf`) before the CTA arrives at the grid barrier; once the barrier is
+// complete, warp 0 of every CTA merges all slots in rank order -- lane j
+// takes ranks j, j + 32, ..., every load issued before the merges -- with a
+// shuffle tree, so all CTAs hold bitwise the same totals.  Thread 0 ends
+// with them in `out`; the return value (thread 0) is false when its wait gave
+// up.  The slots alternate between two buffers: a buffer is written again
+// only two sums later, after a barrier that every reader has passed.
 constexpr int kGridMaxPerLane = 8;  // up to 256 CTAs in the launch
 template <int NA>
 __device__ bool grid_sum(Acc<float> (&a)[NA], ResShared<float> &sh, const ResArgs &ra, int &buf,
@@ -2596,7 +2636,7 @@ __device__ bool grid_sum(Acc<float> (&a)[NA], ResShared<float> &sh, const ResArg
     for (int k = 0; k < NA; ++k) sh.red[warp][k] = a[k];
   }
   __syncthreads();
-  int ok = 1;
+  bool ok = true;
   if (warp == 0) {
     Acc<float> m[NA];
 #pragma unroll
@@ -2605,24 +2645,16 @@ __device__ bool grid_sum(Acc<float> (&a)[NA], ResShared<float> &sh, const ResArg
       warp_reduce_acc(m[k]);
     }
     const unsigned G = gridDim.x;
-    float *slots = ra.gpart + (size_t)buf * (G + 1) * 6;  // [G] CTA slots, then the totals
-    float *totals = slots + (size_t)G * 6;
-    unsigned g = 0;
-    int last = 0;
+    float *slots = ra.gpart + (size_t)buf * (G + 1) * 6;  // [G] CTA slots of 3 (hi, lo) pairs
     if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < NA; ++k) {
         slots[blockIdx.x * 6 + 2 * k] = m[k].s;
         slots[blockIdx.x * 6 + 2 * k + 1] = m[k].c;
       }
-      unsigned *cnt = ra.gbar;
-      g = ld_acquire_u32(ra.gbar + 1);
-      const unsigned expect = ra.g_expect > 0 ? (unsigned)ra.g_expect : G;
-      last = atom_add_acq_rel_u32(cnt, 1u) == expect - 1;
     }
-    last = __shfl_sync(kFull, last, 0);
-    __syncwarp();
-    if (last) {
+    ok = grid_arrive_wait(ra);
+    if (ok) {
 #pragma unroll
       for (int k = 0; k < NA; ++k) {
         float vs[kGridMaxPerLane], vc[kGridMaxPerLane];
@@ -2641,29 +2673,12 @@ __device__ bool grid_sum(Acc<float> (&a)[NA], ResShared<float> &sh, const ResArg
           t.merge(v);
         }
         warp_reduce_acc(t);
-        if (lane == 0) {
-          totals[2 * k] = t.s;
-          totals[2 * k + 1] = t.c;
-          out[k] = t;
-        }
-      }
-      if (lane == 0) {
-        atomicExch(ra.gbar, 0u);
-        st_release_u32(ra.gbar + 1, g + 1);
-      }
-    } else if (lane == 0) {
-      ok = grid_wait(ra, g) ? 1 : 0;
-      if (ok) {
-#pragma unroll
-        for (int k = 0; k < NA; ++k) {
-          out[k].s = __ldcg(totals + 2 * k);
-          out[k].c = __ldcg(totals + 2 * k + 1);
-        }
+        if (lane == 0) out[k] = t;
       }
     }
   }
   buf ^= 1;
-  return ok != 0;
+  return ok;
 }
 
 // The group's sum and barrier for group kind kG (0 one CTA, 1 a cluster, 2
@@ -2718,6 +2733,7 @@ __device__ bool res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
   cx.cr = cr;
   cx.crc = kCluster ? cr : 0u;
   cx.grid = kG == 2;
+  cx.qrec = a.q_recur != 0;
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(res2_smem);
   cx.sK = base;
   cx.sZ = base + 4u * cx.S;
@@ -2814,20 +2830,25 @@ __device__ bool res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
       __syncthreads();
       continue;
     }
-    // step 1: the new direction on the own octs, then every CTA waits
+    // steps 1 and 2: the new direction p and q = (I + dt A) p, the sum p.q.
+    // From p: p on the own octs, a group barrier (the neighbours' p), the
+    // stencil of p.  By the recurrence: one pass, the stencil of z (final
+    // since the last group sum) and p, q from their previous values.
     {
       const bool first = sh.st.first != 0;
       const float beta = sh.st.betaf;
-      for (int o = o0; o < hi; o += stride) res2_dir_oct(cx, sd, o, first, beta);
-      if (!res2_barrier<kG>(a, sh)) {
-        if (threadIdx.x == 0) res2_timeout(sh.st);
-        break;
-      }
-    }
-    // step 2: q = (I + dt A) p, sum p.q
-    {
       Acc<float> acc[1], tot[1];
-      for (int o = o0; o < hi; o += stride) acc[0].add_value(res2_op_any<kCluster>(cx, sd, o, h));
+      if (cx.qrec) {
+        for (int o = o0; o < hi; o += stride) acc[0].add_value(res2_op_any<kCluster, true>(cx, sd, o, h, first, beta));
+      } else {
+        for (int o = o0; o < hi; o += stride) res2_dir_oct(cx, sd, o, first, beta);
+        if (!res2_barrier<kG>(a, sh)) {
+          if (threadIdx.x == 0) res2_timeout(sh.st);
+          break;
+        }
+        for (int o = o0; o < hi; o += stride)
+          acc[0].add_value(res2_op_any<kCluster, false>(cx, sd, o, h, first, beta));
+      }
       const bool ok = res2_sum<1, kG>(acc, sh, a, buf, tot);
       if (threadIdx.x == 0 && !ok) res2_timeout(sh.st);
       if (threadIdx.x == 0 && ok) {
@@ -3210,6 +3231,8 @@ cudaError_t launch_resident_grid(int threads, int grid, const ResArgs &a, cudaSt
     return cudaErrorInvalidValue;
   return res2_grid_launch_t<512>(grid, a, st);
 }
+
+int resident_six_cap() { return kRes2Cap6; }
 
 int resident_grid_ctas(int threads, int device) {
   if (threads != 512) return 0;  // compiled for 512-thread CTAs only

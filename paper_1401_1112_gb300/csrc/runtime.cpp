@@ -590,9 +590,10 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
   }
   if (o.sched < ATS_SCHED_AUTO || o.sched > ATS_SCHED_GRID || (o.res_threads != 0 && o.res_threads != 256 &&
       o.res_threads != 512) || o.res_cluster < 0 || o.res_cluster > 16 || o.res_max_octs < 0 || o.res_state < 0 ||
-      o.res_state > 1 || o.res_cluster_big > 16 || o.res_big_work < 0 || o.res_cluster_mid > 16) {
+      o.res_state > 1 || o.res_cluster_big > 16 || o.res_big_work < 0 || o.res_cluster_mid > 16 || o.cg_form < 0 ||
+      o.cg_form > 2) {
     set_error("bad resident-solver options (sched 0..3, res_threads 0/256/512, res_cluster, res_cluster_mid and "
-              "res_cluster_big up to 16, res_state 0/1)");
+              "res_cluster_big up to 16, res_state 0/1, cg_form 0..2)");
     return ATS_ERR_INVALID_ARG;
   }
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -703,17 +704,18 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       return P->res_smem ? resident_smem_clusters(P->res_threads, cl, P->res_cap)
                          : resident_max_clusters(P->fp64, P->res_threads, cl);
     };
-    // levels above the limit: the whole-GPU form when asked for (FP32 bulk,
-    // K, z, p of each CTA's run in shared memory), else the tick path
-    const int grid_all = (o.sched == ATS_SCHED_GRID && P->res_smem && P->res_cap > 0)
-                             ? resident_grid_ctas(P->res_threads, ctx->device)
-                             : 0;
+    // levels above the limit: the whole-GPU form (FP32 bulk, each CTA's run
+    // in shared memory) when asked for, and with ATS_SCHED_AUTO when the runs
+    // on its CTAs keep all six arrays in shared memory; else the tick path
+    const bool grid_ok = (o.sched == ATS_SCHED_GRID || o.sched == ATS_SCHED_AUTO) && P->res_smem && P->res_cap > 0;
+    const int grid_all = grid_ok ? resident_grid_ctas(P->res_threads, ctx->device) : 0;
+    const int64_t grid_auto_octs = (int64_t)grid_all * std::min(P->res_cap, resident_six_cap());
     P->mode.assign(n, 0);
     for (int k = 0; k < n; ++k) {
       const int64_t no = P->levels[k]->n_oct;
       if (!res_ok) continue;
       if (no > max_octs) {
-        if (grid_all > 0) P->mode[k] = 4;
+        if (grid_all > 0 && (o.sched == ATS_SCHED_GRID || no <= grid_auto_octs)) P->mode[k] = 4;
         continue;
       }
       // a level whose runs on res_cluster CTAs would not fit their shared
@@ -870,6 +872,7 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   ra.tq_head = P->d_heads + 2;
   ra.n_solves = P->n;
   ra.cg_scalars = P->opts.cg_scalars ? 1 : 0;
+  ra.q_recur = P->opts.cg_form == 1 ? 0 : 1;
   ra.cells = prof ? P->d_cells + kCellCounters : nullptr;
   // every resident solve stamps its start and end (the split of the next run
   // follows them; profiling reads the timeline)

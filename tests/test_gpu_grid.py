@@ -86,25 +86,30 @@ def _solve(ats, ctx, lv, st, **kw):
                          ids=["just-above-limit", "51k-octs", "beyond-shared-capacity"])
 def test_box_levels_match_oracle(ats, ctx, dims):
     """17 408, 51 200 and 313 600 octs: the largest splits into runs of 2 064
-    octs, 16 more than a CTA keeps in shared memory."""
+    octs, 16 more than a CTA keeps in shared memory.  Both forms of the CG
+    step (the neighbours' p after a barrier, or their z with the q
+    recurrence)."""
     rng = np.random.default_rng(sum(dims))
     lv, st = _box(rng, dims, 1.0 / (2 * max(dims)))
     assert lv.n_oct > 16384
-    code, stats, x = _solve(ats, ctx, lv, st)
-    assert code == 0, stats
-    assert stats["err_bound"] <= TOL
-    assert _rel(x, _oracle_x(lv, st)) <= PAR
+    xr = _oracle_x(lv, st)
+    for form in (1, 2):
+        code, stats, x = _solve(ats, ctx, lv, st, cg_form=form)
+        assert code == 0, stats
+        assert stats["err_bound"] <= TOL
+        assert _rel(x, xr) <= PAR
 
 
+@pytest.mark.parametrize("form", [1, 2], ids=["q-from-p", "q-recurrence"])
 @pytest.mark.parametrize("seed", [21, 22, 23])
-def test_irregular_levels_more_ctas_than_octs(ats, ctx, seed):
+def test_irregular_levels_more_ctas_than_octs(ats, ctx, seed, form):
     """Unions of random oct boxes (tens to hundreds of octs) with non-leaf
     cells and every interface kind, sent to the whole-GPU form by a limit of
     8 octs: most CTAs own one oct or none and still take part in every
     barrier and sum; non-leaf cells keep their values."""
     lv, st = W.random_amr_level(seed, n_box=4, box_hi=8)
     assert lv.n_oct > 8
-    code, stats, x = _solve(ats, ctx, lv, st, res_max_octs=8)
+    code, stats, x = _solve(ats, ctx, lv, st, res_max_octs=8, cg_form=form)
     assert code == 0, stats
     assert _rel(x, _oracle_x(lv, st)) <= PAR
     nl = ~lv.leaf_cells()
@@ -170,16 +175,20 @@ def test_several_whole_gpu_levels_in_one_batch(ats, ctx):
 
 
 def test_grid_and_tick_paths_agree(ats, ctx):
-    """A large level on the whole-GPU form, on the tick path (the default for
-    it) and with both forced: each within the parity bound of the oracle
-    (their arithmetic differs, so not bitwise)."""
+    """A large level on the whole-GPU form (forced, and the default for a
+    level whose runs keep all six arrays in shared memory) and on the tick
+    path: each within the parity bound of the oracle (their arithmetic
+    differs, so not bitwise); the default gives the forced form's bits."""
     rng = np.random.default_rng(8)
     lv, st = _box(rng, (32, 32, 20), 1.0 / 64)
     xr = _oracle_x(lv, st)
+    xs = []
     for sched in (ats.ATS_SCHED_GRID, ats.ATS_SCHED_AUTO, ats.ATS_SCHED_TICK):
         code, stats, x = _solve(ats, ctx, lv, st, sched=sched)
         assert code == 0, stats
         assert _rel(x, xr) <= PAR
+        xs.append(x)
+    np.testing.assert_array_equal(xs[0], xs[1])
 
 
 def test_grid_barrier_waits_are_bounded(ats):

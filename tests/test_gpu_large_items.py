@@ -84,16 +84,21 @@ def big_level():
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("tile", [0, 384, 512, 1024])
 def test_large_level_matches_oracle(ats, ctx, big_level, prec, tile):
+    """The tick path at the default and explicit item sizes; with the default
+    scheduler, mixed precision, the level (at most 1 100 octs per SM) takes
+    the whole-GPU form, which must match too."""
     lv, st, xr = big_level
     assert lv.n_oct > 155_000
     L = ats.Level(ctx, lv)
     L.build(st.dt, st.K, st.E, **_faces(st))
-    x = st.E.copy()
     P = ats.ATS_PREC_FP64 if prec == "fp64" else ats.ATS_PREC_MIXED
-    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, tile_octs=tile)
-    assert code == 0, stats
-    assert stats["err_bound"] <= TOL
-    assert _rel(x, xr) <= PAR
+    scheds = [ats.ATS_SCHED_TICK] + ([ats.ATS_SCHED_AUTO] if tile == 0 else [])
+    for sc in scheds:
+        x = st.E.copy()
+        code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=P, tile_octs=tile, sched=sc)
+        assert code == 0, stats
+        assert stats["err_bound"] <= TOL
+        assert _rel(x, xr) <= PAR
     L.close()
 
 

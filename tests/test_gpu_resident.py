@@ -12,7 +12,8 @@ solution's error by its residual, and they differ by at most 1e-10 relative.
 Covered: every interface kind and non-leaf cells, every resident shape (one
 CTA; clusters of 1, 2, 4, 8 and 16 CTAs; 256 and 512 threads), levels with
 many octs per thread, ragged batches (bitwise alone vs in the batch, and run
-to run), the FP32-scalar variant, degenerate and capped solves.
+to run), the FP32-scalar variant, both forms of the CG step (q from p, or by
+recurrence), degenerate and capped solves.
 """
 import numpy as np
 import pytest
@@ -169,6 +170,47 @@ def test_state_in_shared_or_global_memory_same_bits(ats, ctx):
         np.testing.assert_array_equal(res[0][0], res[1][0])
         assert res[0][1] == res[1][1]
         L.close()
+
+
+@pytest.mark.parametrize("form", [1, 2], ids=["q-from-p", "q-recurrence"])
+def test_cg_forms_match_oracle(ats, ctx, form):
+    """Both forms of the CG step (q = (I + dt A) p after a group barrier, or
+    q = (I + dt A) z + beta q_prev without one) on one CTA, 4- and 16-CTA
+    clusters, within and beyond the shared capacity (24 000 octs on one CTA),
+    with every interface kind and non-leaf cells: each refines to the
+    certificate and matches the oracle; where the CTA keeps its state does not
+    change the bits; the two forms' iteration counts stay close."""
+    rng = np.random.default_rng(6060 + form)
+    for o, cta, cl in ((60, 1 << 30, 1), (3000, -1, 4), (24000, -1, 16), (24000, 1 << 30, 1)):
+        lv, st = W.random_box_solve(rng, o, dt_lo=10.0, dt_hi=100.0, robin=True)
+        xr = _oracle_x(lv, st)
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, **_faces(st))
+        res = {}
+        for f, rs in ((form, 0), (form, 1), (3 - form, 0)):
+            x = st.E.copy()
+            code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                                  sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=cta, res_cluster=cl, res_state=rs,
+                                  cg_form=f)
+            assert code == 0, stats
+            assert _rel(x, xr) <= PAR
+            res[(f, rs)] = (x, stats["iterations"])
+        np.testing.assert_array_equal(res[(form, 0)][0], res[(form, 1)][0])
+        a, b = res[(form, 0)][1], res[(3 - form, 0)][1]
+        assert abs(a - b) <= max(4, 0.1 * b), (a, b)
+        L.close()
+    lv, st = W.random_amr_level(31, n_box=4, box_hi=8)
+    xr = _oracle_x(lv, st)
+    L = ats.Level(ctx, lv)
+    L.build(st.dt, st.K, st.E, **_faces(st))
+    x = st.E.copy()
+    code, stats = L.solve(x, tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED,
+                          sched=ats.ATS_SCHED_RESIDENT, res_cta_octs=-1, res_cluster=4, cg_form=form)
+    assert code == 0, stats
+    assert _rel(x, xr) <= PAR
+    nl = ~lv.leaf_cells()
+    np.testing.assert_array_equal(x[nl], st.E[nl])
+    L.close()
 
 
 @pytest.mark.parametrize("prec", PRECS)
