@@ -354,6 +354,16 @@ __device__ __forceinline__ void op_face(int n, const T *__restrict__ KT, const T
 // face coefficients C = h (K_i + K_j) (row A of this oct for the in-oct pairs
 // and the +A face, row A of the -A neighbour for the -A face), and the FP32
 // diagonal sums of the bulk precision.
+// The approximate reciprocal of the hardware (PTX rcp.approx, within one
+// ulp): for the Jacobi step z = D^-1 r of the resident solver's FP32 bulk, one
+// fixed value per cell for a whole inner solve, so the preconditioner stays
+// a positive diagonal matrix.  D >= 1, so flushing subnormals changes nothing.
+__device__ __forceinline__ float rcp_approx(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+
 template <int A, typename T, bool kCoh = false>
 __device__ __forceinline__ void ref_axis(const SolveDev &sd, int o, const int (&nb)[6], const T *__restrict__ KT,
                                          T hT, const T (&KTo)[8], const double (&xv)[8], double (&acc)[8],
@@ -411,7 +421,9 @@ __device__ __forceinline__ void ref_axis(const SolveDev &sd, int o, const int (&
 // CG kernels of the following inner solve.  Norms for the stopping test (r.r,
 // x.x) and r.z are accumulated with compensated bulk-precision dots.
 // The values of one oct (zo = z, dv = D); op_refine_oct stores them.
-template <typename T, bool kCoh = false>
+// kRcp (FP32 bulk): z = r x rcp(D_T) instead of the rounded quotient, the
+// form the resident solver's CG steps use.
+template <typename T, bool kCoh = false, bool kRcp = false>
 __device__ __forceinline__ void ref_oct_values(const SolveDev &sd, int o, bool want_x, Acc<T> &rr, Acc<T> &xx,
                                                Acc<T> &rz, T (&zo)[8], T (&dv)[8]) {
   const T *__restrict__ KT = (const T *)sd.KT;
@@ -452,7 +464,9 @@ __device__ __forceinline__ void ref_oct_values(const SolveDev &sd, int o, bool w
     // D in the bulk precision, kept for the CG kernels of the following
     // inner solve
     const T dT = T(1) + (rec >= 0 ? (mixed ? xdT[c] : (T)xd[c]) : T(0)) + dsT[c];
-    const T zc = rT / dT;
+    T zc;
+    if constexpr (kRcp && sizeof(T) == 4) zc = rT * rcp_approx(dT);
+    else zc = rT / dT;
     zo[c] = leaf ? zc : T(0);
     dv[c] = leaf ? dT : T(1);
     if (leaf) {
@@ -2316,6 +2330,33 @@ __device__ __forceinline__ void res2_own_store(const Cx &cx, uint32_t arr, int c
   else st8(garr + 8 * o, v);
 }
 
+// The resident solver keeps K scaled by h = dt / (2 dx^2) (rounded once per
+// cell; the sign, which marks leaf cells, is kept), so a face's coupling is
+// C = hK_i + hK_j.  Values read from the level's global K are scaled the same
+// way where they are used, so where a value lives does not change the bits.
+__device__ __forceinline__ void res2_scale_K(float h, float (&K)[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) K[c] *= h;
+}
+
+// The in-oct faces of the resident solver's stencil (K scaled by h).  Unlike
+// in_oct_faces it takes no leaf test: every array the stencil reads (p, z)
+// is zero on non-leaf cells and in the stand-in row, so a coupling to such a
+// cell adds C x 0 (C finite); a non-leaf cell's own row is zeroed afterwards.
+__device__ __forceinline__ void res2_in_oct(const float (&K)[8], const float (&v)[8], float (&off)[8]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c & (1 << a)) continue;
+      const int d = c | (1 << a);
+      const float C = K[c] + K[d];
+      off[c] = fmaf(C, v[d], off[c]);
+      off[d] = fmaf(C, v[c], off[d]);
+    }
+  }
+}
+
 template <int DIR, bool kRec, class Cx>
 __device__ __forceinline__ void res2_op_face(const Cx &cx, const SolveDev &sd, const Nb &n, float h,
                                              const float (&K)[8], float (&off)[8]) {
@@ -2323,13 +2364,13 @@ __device__ __forceinline__ void res2_op_face(const Cx &cx, const SolveDev &sd, c
   if (n.kind == 0) return;
   float Kn[8], Pn[8];
   res2_face<A, NB>(n, cx.sK, cx.S, (const float *)sd.KT, false, Kn);
+  if (n.kind == 3) res2_scale_K(h, Kn);
   res2_face<A, NB>(n, kRec ? cx.sZ : cx.sP, cx.S, (const float *)(kRec ? sd.z : sd.p0), true, Pn);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (((c >> A) & 1) != S) continue;
     const int j = c ^ (1 << A);
-    const float C = (Kn[j] >= 0.f) ? h * (K[c] + Kn[j]) : 0.f;
-    off[c] += C * Pn[j];
+    off[c] = fmaf(K[c] + Kn[j], Pn[j], off[c]);  // Pn is zero on non-leaf cells (see res2_in_oct)
   }
 }
 
@@ -2386,6 +2427,7 @@ __device__ __forceinline__ float res2_op_oct(const Cx &cx, const SolveDev &sd, i
   const int l = o - cx.lo;
   float K[8], v[8], d[8];
   res2_own(cx, cx.sK, cx.cap, l, (const float *)sd.KT, o, false, K);
+  if (l >= cx.cap) res2_scale_K(h, K);
   res2_own(cx, kRec ? cx.sZ : cx.sP, cx.cap, l, (const float *)(kRec ? sd.z : sd.p0), o, true, v);
   res2_own(cx, cx.sD, cx.capD, l, (const float *)sd.dg, o, true, d);
   Nb nb[6];
@@ -2393,7 +2435,7 @@ __device__ __forceinline__ float res2_op_oct(const Cx &cx, const SolveDev &sd, i
   float off[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) off[c] = 0.f;
-  in_oct_faces(K, v, h, off);
+  res2_in_oct(K, v, off);
   res2_op_face<0, kRec>(cx, sd, nb[0], h, K, off);
   res2_op_face<1, kRec>(cx, sd, nb[1], h, K, off);
   res2_op_face<2, kRec>(cx, sd, nb[2], h, K, off);
@@ -2417,8 +2459,7 @@ __device__ __forceinline__ void res2_fast_face(uint32_t aK, uint32_t aP, uint32_
   for (int c = 0; c < 8; ++c) {
     if (((c >> A) & 1) != S) continue;
     const int j = c ^ (1 << A);
-    const float C = (Kn[j] >= 0.f) ? h * (K[c] + Kn[j]) : 0.f;
-    off[c] += C * Pn[j];
+    off[c] = fmaf(K[c] + Kn[j], Pn[j], off[c]);  // Pn is zero on non-leaf cells (see res2_in_oct)
   }
 }
 
@@ -2446,7 +2487,7 @@ __device__ __forceinline__ float res2_op_oct_fast(const Cx &cx, const SolveDev &
   float off[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) off[c] = 0.f;
-  in_oct_faces(K, v, h, off);
+  res2_in_oct(K, v, off);
   res2_fast_face<0, kCluster>(aK[0], aV[0], cx.S, h, K, off);
   res2_fast_face<1, kCluster>(aK[1], aV[1], cx.S, h, K, off);
   res2_fast_face<2, kCluster>(aK[2], aV[2], cx.S, h, K, off);
@@ -2493,7 +2534,7 @@ __device__ __forceinline__ void res2_dir_oct(const Cx &cx, const SolveDev &sd, i
   if (cx.grid && l < cx.cap) st8((float *)sd.p0 + 8 * o, p);
 }
 
-// Step 3 on own oct o: r = D z - alpha q, z = r / D, e += alpha p.
+// Step 3 on own oct o: r = D z - alpha q, z = r x rcp(D), e += alpha p.
 template <class Cx>
 __device__ __forceinline__ void res2_upd_oct(const Cx &cx, const SolveDev &sd, int o, float alpha, float &lrz,
                                              float &lrr) {
@@ -2507,7 +2548,7 @@ __device__ __forceinline__ void res2_upd_oct(const Cx &cx, const SolveDev &sd, i
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const float r = d[c] * z[c] - alpha * q[c];
-    const float zn = r / d[c];
+    const float zn = r * rcp_approx(d[c]);
     lrz = fmaf(r, zn, lrz);
     lrr = fmaf(r, r, lrr);
     z[c] = zn;
@@ -2524,7 +2565,7 @@ template <class Cx>
 __device__ __forceinline__ void res2_ref_oct(const Cx &cx, const SolveDev &sd, int o, bool want_x, Acc<float> &rr,
                                              Acc<float> &xx, Acc<float> &rz) {
   float zo[8], dv[8];
-  ref_oct_values<float, true>(sd, o, want_x, rr, xx, rz, zo, dv);
+  ref_oct_values<float, true, true>(sd, o, want_x, rr, xx, rz, zo, dv);
   res2_own_store(cx, cx.sZ, cx.cap, o - cx.lo, (float *)sd.z, o, zo);
   if (cx.qrec && cx.grid && o - cx.lo < cx.cap) st8((float *)sd.z + 8 * o, zo);
   res2_own_store(cx, cx.sD, cx.capD, o - cx.lo, (float *)sd.dg, o, dv);
@@ -2744,7 +2785,8 @@ __device__ bool res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
   cx.sC = base + (six ? 24u : 12u) * cx.S;
   const int hi = min(n, cx.lo + cx.chunk);
   const int o0 = cx.lo + (int)threadIdx.x, stride = (int)blockDim.x;
-  // stage in: K and the neighbour codes of the octs kept in shared memory
+  const float h = (float)sd.h;
+  // stage in: K (scaled by h) and the neighbour codes of the octs kept in shared memory
   // (read by other CTAs only after the first sum's cluster barrier), and the
   // stand-in row a face without a neighbour points to
   if (threadIdx.x == 0) {
@@ -2763,6 +2805,7 @@ __device__ bool res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
     const int l = o - cx.lo;
     float K[8];
     ld8_ro((const float *)sd.KT + 8 * o, K);
+    res2_scale_K(h, K);
     sts_cells(cx.sK + (uint32_t)l * 8u, cx.S, K);
     if (l < cx.capD) {  // the correction of the first inner solve starts at zero
       float z0[8];
@@ -2785,7 +2828,6 @@ __device__ bool res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
                  "r"(w2), "r"(0u)
                  : "memory");
   }
-  const float h = (float)sd.h;
   const bool want_x = sd.stop_rule == ATS_STOP_CERTIFIED;
   const bool f32 = a.cg_scalars == 0;
   for (;;) {
