@@ -220,6 +220,12 @@ struct ResArgs {
   float *gpart;
   int *gerr;
   int g_expect;  // arrivals a grid barrier waits for (0: every CTA of the launch)
+  // FP32-bulk kernels: where each solve's result goes (x, or 2 x' - E^n for
+  // Crank-Nicolson), written by the solve's own CTAs when it ends; null for
+  // the solves whose result k_final writes.  neg[s] is set when a written
+  // value is negative.
+  double *const *x_out;
+  int *neg;
 };
 // One resident launch on st of the FP64 solver (CG state in global memory):
 // clusters of `cluster` CTAs of `threads` threads (256 or 512), `grid` CTAs

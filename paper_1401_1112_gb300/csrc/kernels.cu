@@ -2744,6 +2744,39 @@ __device__ __forceinline__ void res2_timeout(ResState &st) {
   st.phase = kDone;
 }
 
+// The result of a solve on this CTA's octs [lo, hi), as k_final writes it:
+// x (Crank-Nicolson: 2 x' - E^n) to xd, which may be device memory or host
+// memory the device can write (then the result reaches the host while other
+// solves still run).  *neg is set when a value is negative.
+__device__ void res2_copy_out(const SolveDev &sd, double *xd, int lo, int hi, int *neg) {
+  const bool vec = oct_aligned(xd) && oct_aligned(sd.cn_base);
+  bool below = false;
+  for (int o = lo + (int)threadIdx.x; o < hi; o += blockDim.x) {
+    double v[8];
+    ld8_rw(sd.x64 + 8 * (int64_t)o, v);
+    if (sd.cn_base) {
+      double cb[8];
+      if (vec) {
+        ld8_ro(sd.cn_base + 8 * (int64_t)o, cb);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) cb[c] = sd.cn_base[8 * (int64_t)o + c];
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v[c] = 2.0 * v[c] - cb[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) below = below || v[c] < 0.0;
+    if (vec) {
+      st8(xd + 8 * (int64_t)o, v);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) xd[8 * (int64_t)o + c] = v[c];
+    }
+  }
+  if (__syncthreads_or(below) && neg && threadIdx.x == 0) atomicOr(neg, 1);
+}
+
 // One solve by one group, the CG state of its first octs in shared memory in
 // the layout Cx.  kG: 0 one CTA, 1 a cluster, 2 the whole GPU (every CTA of
 // a cooperative launch).  Returns false when a grid barrier wait gave up (the solve then
@@ -2944,6 +2977,9 @@ __device__ bool res2_solve_l(const ResArgs &a, int s, ResShared<float> &sh, int 
   }
   __syncthreads();  // thread 0's last state update is seen by all
   const bool alive = sh.st.status != ATS_ERR_TIMEOUT;
+  // the result of the own octs (each CTA updated only its own octs' x)
+  double *xd = a.x_out ? a.x_out[s] : nullptr;
+  if (xd) res2_copy_out(sd, xd, cx.lo, hi, a.neg ? a.neg + s : nullptr);
   if (threadIdx.x == 0 && cr == 0) {
     const ResState &st = sh.st;
     SolveScalars f;

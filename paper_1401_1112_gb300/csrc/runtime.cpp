@@ -205,7 +205,8 @@ struct Plan {
   int **d_flag_ptrs = nullptr;     // [n] the levels' error flags
   int *d_flags = nullptr;          // [n] gathered flags, then [n] negative-result flags
   const double **d_src = nullptr;  // [n] device pointers for x copy-in (or null)
-  double **d_dst = nullptr;        // [n] device pointers for x copy-out (or null)
+  double **d_dst = nullptr;        // [n] device pointers for x copy-out by k_final (or null)
+  double **d_rdst = nullptr;       // [n] ... by the FP32-bulk resident kernels at a solve's end (or null)
   double *d_xstage = nullptr;      // [sum N] host x staged on the device (host-memory solves)
   int *h_active = nullptr;         // pinned [2]: one per poll slot
   std::vector<SolveDev> h_solves;
@@ -225,7 +226,13 @@ struct Plan {
   unsigned char *d_init = nullptr;
   std::vector<unsigned char> h_init;
   std::vector<const double *> h_src;
-  std::vector<double *> h_dst;
+  std::vector<double *> h_dst, h_rdst;
+  // host-memory solves: the last host x pointers seen, whether the device
+  // can write each directly (pinned), and the pointers copy_runs copies back
+  // (null where the resident kernel wrote the host array itself)
+  std::vector<double *> h_xhost, h_xdev;
+  std::vector<char> h_xdirect;
+  std::vector<double *> h_copyback;
   bool profiling = false;
   // two sets (by poll slot) of: chunk start, then kTickEvents per tick of a
   // chunk, so that one interval runs while the other's events are read
@@ -423,6 +430,7 @@ void plan_free(Plan *P) {
   dev_free(ctx, P->d_flags);
   dev_free(ctx, P->d_src);
   dev_free(ctx, P->d_dst);
+  dev_free(ctx, P->d_rdst);
   dev_free(ctx, P->d_xstage);
   dev_free(ctx, P->d_queue);
   dev_free(ctx, P->d_heads);
@@ -790,7 +798,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
       (s = dev_alloc_t(ctx, n, &P->d_flag_ptrs)) != ATS_OK ||
       (s = dev_alloc_t(ctx, 2 * (size_t)n, &P->d_flags)) != ATS_OK ||
       (s = dev_alloc_t(ctx, n, &P->d_src)) != ATS_OK ||
-      (s = dev_alloc_t(ctx, n, &P->d_dst)) != ATS_OK) {
+      (s = dev_alloc_t(ctx, n, &P->d_dst)) != ATS_OK || (s = dev_alloc_t(ctx, n, &P->d_rdst)) != ATS_OK) {
     plan_free(P);
     return s;
   }
@@ -860,7 +868,7 @@ ats_status plan_create(ats_context *ctx, ats_level *const *levels, int n, const 
 // clusters on the context stream, the clusters and the single CTAs on the
 // plan's two side streams, all three forked from and joined back into the
 // context stream (profiling: between the two timing events).
-ats_status plan_launch_resident(Plan *P, bool prof) {
+ats_status plan_launch_resident(Plan *P, bool prof, int *neg) {
   if (P->n_bq + P->n_mq + P->n_cq + P->n_tq + P->n_gq == 0) return ATS_OK;
   cudaStream_t st = P->ctx->stream;
   ResArgs ra;
@@ -872,6 +880,8 @@ ats_status plan_launch_resident(Plan *P, bool prof) {
   ra.tq_head = P->d_heads + 2;
   ra.n_solves = P->n;
   ra.cg_scalars = P->opts.cg_scalars ? 1 : 0;
+  ra.x_out = P->res_smem ? P->d_rdst : nullptr;
+  ra.neg = neg;
   ra.q_recur = P->opts.cg_form == 1 ? 0 : 1;
   ra.cells = prof ? P->d_cells + kCellCounters : nullptr;
   // every resident solve stamps its start and end (the split of the next run
@@ -1251,11 +1261,41 @@ ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off
       if (s2 != ATS_OK) return s2;
     }
   }
-  for (int k = 0; k < n; ++k) {
-    dst[k] = dev ? x_inout[k] : P->d_xstage + off[k];
-    src[k] = x0_e ? P->levels[k]->E_dev : dst[k];
+  // where each result goes: the FP32-bulk resident kernels write their
+  // solves' results themselves as each solve ends -- into device x, into host
+  // x directly when the device can write it (pinned), else into the staging
+  // buffer -- and k_final writes the others; copy_runs brings back the staged
+  // host results
+  if (!dev) {
+    std::vector<double *> hx(x_inout, x_inout + n);
+    if (hx != P->h_xhost) {
+      P->h_xhost = hx;
+      P->h_xdev.assign(n, nullptr);
+      P->h_xdirect.assign(n, 0);
+      for (int k = 0; k < n; ++k) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, hx[k]) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+          P->h_xdev[k] = (double *)pa.devicePointer;
+          P->h_xdirect[k] = 1;
+        }
+        cudaGetLastError();
+      }
+    }
   }
-  if (src != P->h_src || dst != P->h_dst) {
+  std::vector<double *> rdst(n, nullptr);
+  P->h_copyback.assign(n, nullptr);
+  for (int k = 0; k < n; ++k) {
+    double *stage = dev ? x_inout[k] : P->d_xstage + off[k];
+    src[k] = x0_e ? P->levels[k]->E_dev : stage;
+    const int m = P->mode[k];
+    const bool res_out = P->res_smem && (m == 1 || m == 2 || m == 3 || m == 5);
+    const bool direct = !dev && res_out && P->h_xdirect[k];
+    dst[k] = res_out ? nullptr : stage;
+    rdst[k] = res_out ? (direct ? P->h_xdev[k] : stage) : nullptr;
+    if (!dev && !direct) P->h_copyback[k] = x_inout[k];
+  }
+  if (src != P->h_src || dst != P->h_dst || rdst != P->h_rdst) {
     if (capture) {
       set_error("graph capture: the solve's x is not the one of its last run");
       return ATS_ERR_INVALID_ARG;
@@ -1263,8 +1303,10 @@ ats_status plan_begin(Plan *P, double *const *x_inout, std::vector<int64_t> &off
     ++ctx->epoch;
     P->h_src = src;
     P->h_dst = dst;
+    P->h_rdst = rdst;
     CUDA_TRY(cudaMemcpyAsync(P->d_src, P->h_src.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(P->d_dst, P->h_dst.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(P->d_rdst, P->h_rdst.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, st));
   }
   CUDA_TRY(launch_init(P->fp64, P->d_solves, P->d_items, P->n_items, P->d_src, P->grid, st));
   // the start state: every solve's scalars (live and final copies), the
@@ -1336,8 +1378,10 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   int64_t ticks = 0;
   ats_status s;
   bool timed_out = false;
-  // the resident solves: one launch runs every one of them to its end
-  if ((s = plan_launch_resident(P, P->profiling)) != ATS_OK) return s;
+  // the resident solves: one launch runs every one of them to its end (and
+  // writes their results; the negative-result flags are zeroed first)
+  CUDA_TRY(cudaMemsetAsync(P->d_flags + n, 0, sizeof(int) * n, st));
+  if ((s = plan_launch_resident(P, P->profiling, P->d_flags + n)) != ATS_OK) return s;
   // use_graph = 2 (not while profiling: the timing events cannot sit in a
   // conditional body): the whole loop is one graph launch, ended on the device
   const bool device_loop = P->opts.use_graph == 2 && !P->profiling && P->n_tick > 0;
@@ -1387,11 +1431,10 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   drain_slot = poll_slot;
   drain_n = pending;
   }
-  // copy-out
-  CUDA_TRY(cudaMemsetAsync(P->d_flags + n, 0, sizeof(int) * n, st));
+  // copy-out (k_final: the results the resident kernels did not write)
   CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, P->d_flags + n, P->grid, st));
   if (!dev) {
-    ats_status s2 = copy_runs(st, false, P->d_xstage, off.data(), n, x_inout);
+    ats_status s2 = copy_runs(st, false, P->d_xstage, off.data(), n, P->h_copyback.data());
     if (s2 != ATS_OK) return s2;
   }
   std::vector<SolveScalars> sc(n);
@@ -2031,12 +2074,19 @@ ats_status level_solve_deferred(ats_level *L, double *x_dev, const ats_solve_opt
   }
   if (s == ATS_OK && P->n_tick > 0) s = plan_ensure_loop(P, max_chunks);
   if (s == ATS_OK && !P->d_loop) s = dev_alloc_t(ctx, 1, &P->d_loop);
-  if (s == ATS_OK) s = plan_launch_resident(P, false);
+  if (s == ATS_OK) {
+    const cudaError_t e = cudaMemsetAsync(&d_rec->neg, 0, sizeof(int), st);
+    if (e != cudaSuccess) {
+      set_error(std::string("CUDA error: ") + cudaGetErrorString(e) + " zeroing the negative-result flag");
+      s = ATS_ERR_CUDA;
+    } else {
+      s = plan_launch_resident(P, false, &d_rec->neg);
+    }
+  }
   P->profiling = prof;
   if (s != ATS_OK) return s;
   CUDA_TRY(cudaMemsetAsync(P->d_loop, 0, sizeof(int), st));
   if (P->n_tick > 0 && (s = plan_enqueue_loop(P, st, capture)) != ATS_OK) return s;
-  CUDA_TRY(cudaMemsetAsync(&d_rec->neg, 0, sizeof(int), st));
   CUDA_TRY(launch_final(P->d_solves, P->d_items, P->n_items, P->d_dst, &d_rec->neg, P->grid, st));
   CUDA_TRY(cudaMemcpyAsync(&d_rec->sc, P->d_final, sizeof(SolveScalars), cudaMemcpyDeviceToDevice, st));
   CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, 1, &d_rec->flag, st));

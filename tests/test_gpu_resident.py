@@ -13,7 +13,8 @@ Covered: every interface kind and non-leaf cells, every resident shape (one
 CTA; clusters of 1, 2, 4, 8 and 16 CTAs; 256 and 512 threads), levels with
 many octs per thread, ragged batches (bitwise alone vs in the batch, and run
 to run), the FP32-scalar variant, both forms of the CG step (q from p, or by
-recurrence), degenerate and capped solves.
+recurrence), results written by the resident kernels into device, pinned and
+pageable host memory, degenerate and capped solves.
 """
 import numpy as np
 import pytest
@@ -211,6 +212,69 @@ def test_cg_forms_match_oracle(ats, ctx, form):
     nl = ~lv.leaf_cells()
     np.testing.assert_array_equal(x[nl], st.E[nl])
     L.close()
+
+
+@pytest.mark.parametrize("integ", ["backward-euler", "crank-nicolson"])
+def test_results_written_where_each_solve_ends(ats, ctx, integ):
+    """Each FP32-bulk resident solve writes its own result when it ends: into
+    device x, straight into pinned host x (while the other solves still run),
+    or into the staging buffer for pageable host x; k_final writes the
+    results of the other solves (here a level on the whole-GPU form).  All
+    three memory kinds give bitwise the same x (Crank-Nicolson: 2 x' - E^n),
+    the same statuses (Crank-Nicolson may warn of a negative value, which the
+    resident kernels flag as k_final does), and the backward-Euler results
+    match the oracle."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(909)
+    solves = [W.random_box_solve(rng, o, robin=True) for o in (40, 3000, 12000, 24000)]
+    I = ats.ATS_INTEGRATOR_BACKWARD_EULER if integ == "backward-euler" else ats.ATS_INTEGRATOR_CRANK_NICOLSON
+    levels = []
+    for lv, st in solves:
+        L = ats.Level(ctx, lv)
+        L.build(st.dt, st.K, st.E, integrator=I, **_faces(st))
+        levels.append(L)
+    opts = dict(tol=TOL, stop_rule=ats.ATS_STOP_CERTIFIED, precision=ats.ATS_PREC_MIXED, use_graph=1,
+                res_max_octs=20000)
+    outs, codes = [], []
+
+    def run(B, xs):
+        code, stats = B.solve(xs)
+        assert code >= 0, stats
+        codes.append((code, [st["status"] for st in stats]))
+
+    B = ats.Batch(ctx, levels, mem=ats.ATS_MEM_HOST, **opts)
+    xs = [st.E.copy() for _, st in solves]
+    run(B, xs)
+    outs.append(xs)
+    sizes = [lv.n_cell for lv, _ in solves]
+    buf = torch.empty(sum(sizes), dtype=torch.float64).pin_memory().numpy()
+    views, at = [], 0
+    for (lv, st), n in zip(solves, sizes):
+        views.append(buf[at:at + n])
+        views[-1][:] = st.E
+        at += n
+    for _ in range(2):  # the second run reuses the plan's pointer tables
+        run(B, views)
+        outs.append([v.copy() for v in views])
+        for v, (_, st) in zip(views, solves):
+            v[:] = st.E
+    B.close()
+    B = ats.Batch(ctx, levels, mem=ats.ATS_MEM_DEVICE, **opts)
+    dx = [torch.from_numpy(st.E.copy()).cuda() for _, st in solves]
+    run(B, dx)
+    torch.cuda.synchronize()
+    outs.append([t.cpu().numpy() for t in dx])
+    B.close()
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            np.testing.assert_array_equal(a, b)
+    assert all(c == codes[0] for c in codes)
+    if integ == "backward-euler":
+        assert codes[0][0] == 0
+        for (lv, st), x in zip(solves, outs[0]):
+            assert _rel(x, _oracle_x(lv, st)) <= PAR
+    for L in levels:
+        L.close()
 
 
 @pytest.mark.parametrize("prec", PRECS)
