@@ -1160,8 +1160,15 @@ __global__ void k_coef_build(CoefArgs a) {
 // blk_level[b] and covers its cells from (b - blk_first[level]) * blockDim.
 __global__ void k_coef_build_batch(const CoefArgs *__restrict__ args, const int32_t *__restrict__ blk_level,
                                    const int32_t *__restrict__ blk_first) {
+  // the block's level arguments, copied once into shared memory: every
+  // thread reads a dozen of their fields
+  static_assert(sizeof(CoefArgs) % 8 == 0, "CoefArgs is copied as 8-byte words");
+  __shared__ unsigned long long sa[sizeof(CoefArgs) / 8];
   const int k = blk_level[blockIdx.x];
-  const CoefArgs &a = args[k];
+  const unsigned long long *src = reinterpret_cast<const unsigned long long *>(args + k);
+  for (int w = threadIdx.x; w < (int)(sizeof(CoefArgs) / 8); w += blockDim.x) sa[w] = src[w];
+  __syncthreads();
+  const CoefArgs &a = *reinterpret_cast<const CoefArgs *>(sa);
   const int64_t i = (int64_t)(blockIdx.x - blk_first[k]) * blockDim.x + threadIdx.x;
   if (i < 8 * a.n_oct) coef_cell(a, i);
 }
