@@ -1359,6 +1359,21 @@ int64_t plan_max_ticks(const Plan *P) {
   return 2 * ((int64_t)P->opts.max_iter + 2 * ((int64_t)P->opts.max_refine + 2)) + 2 * P->opts.check_every;
 }
 
+// After a plan's launches, an error return first waits for the work already
+// queued on the stream: the resident kernels write each solve's result into
+// the caller's array (pinned host memory included) when the solve ends, and
+// must not do so after the call has returned.
+struct DrainOnReturn {
+  cudaStream_t st;
+  bool armed;
+  ~DrainOnReturn() {
+    if (armed) {
+      cudaStreamSynchronize(st);
+      cudaGetLastError();
+    }
+  }
+};
+
 // Run a plan to completion: x_inout[k] (host or device per opts.mem) is the
 // initial guess and receives the result.  A right-hand-side override is the
 // caller's: ats_solve writes it into the level's b before and restores b after.
@@ -1381,6 +1396,10 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
   // the resident solves: one launch runs every one of them to its end (and
   // writes their results; the negative-result flags are zeroed first)
   CUDA_TRY(cudaMemsetAsync(P->d_flags + n, 0, sizeof(int) * n, st));
+  // the host copies of the solves' scalars and flags outlive the drain
+  std::vector<SolveScalars> sc(n);
+  std::vector<int> flags(2 * n, 0);
+  DrainOnReturn drain{st, true};
   if ((s = plan_launch_resident(P, P->profiling, P->d_flags + n)) != ATS_OK) return s;
   // use_graph = 2 (not while profiling: the timing events cannot sit in a
   // conditional body): the whole loop is one graph launch, ended on the device
@@ -1437,14 +1456,13 @@ ats_status plan_run(Plan *P, double *const *x_inout, ats_solve_stats *stats) {
     ats_status s2 = copy_runs(st, false, P->d_xstage, off.data(), n, P->h_copyback.data());
     if (s2 != ATS_OK) return s2;
   }
-  std::vector<SolveScalars> sc(n);
   CUDA_TRY(cudaMemcpyAsync(sc.data(), P->d_final, sizeof(SolveScalars) * n, cudaMemcpyDeviceToHost, st));
   unsigned long long cells[2 * kCellCounters] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // tick kernels, resident launch
   if (P->profiling) CUDA_TRY(cudaMemcpyAsync(cells, P->d_cells, sizeof(cells), cudaMemcpyDeviceToHost, st));
-  std::vector<int> flags(2 * n, 0);
   CUDA_TRY(launch_gather_flags(P->d_flag_ptrs, n, P->d_flags, st));
   CUDA_TRY(cudaMemcpyAsync(flags.data(), P->d_flags, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  drain.armed = false;
   if (P->profiling) {
     for (int k = 0; k < drain_n; ++k, drain_slot ^= 1) {
       ats_status s3 = plan_collect_events(P, drain_slot);
