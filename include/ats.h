@@ -30,6 +30,9 @@
  * the caller's.  Per-step arrays may be host or device pointers, as the
  * caller's `mem` field says (ATS_MEM_HOST / ATS_MEM_DEVICE); device pointers
  * are borrowed for the call and used in stream order on the context's stream.
+ * A host x that the device can address (pinned or registered memory) may be
+ * written by the device during a solve call, as each solve ends; the call
+ * returns (also on an error) only after every such write.
  *
  * Errors: every entry point returns an ats_status; 0 is success, < 0 an
  * error, > 0 a warning.  No C++ exception crosses this boundary.
